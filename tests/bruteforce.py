@@ -1,0 +1,262 @@
+"""Independent brute-force step for tiny grids (test helper, pins the oracle).
+
+Nothing here uses the oracle's closed forms.  The physical flux is the velocity moment
+of a Gaussian distribution (zero heat flux closure, Sec. 2) computed by Gauss-Hermite
+quadrature; the primitive Jacobian A = (dU/dW)^-1 dF/dW comes from complex-step
+differentiation of that flux; wave speeds are numerical eigenvalues of A; eigenvectors
+are numerical null spaces of (A - lambda I).  Inside a degenerate eigenspace the basis
+is fixed by the axis-aligned convention of the paper's printed eigenvectors (eq
+righteigvec): the basis vectors restrict to unit vectors on the transverse velocity
+components (shear waves) and on (rho, P_t1t1, P_t1t2, P_t2t2) (contact waves).  The MC
+limiter is odd and positively homogeneous, so any per-vector scaling gives the same step.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+_gh_x, _gh_w = np.polynomial.hermite_e.hermegauss(3)
+_gh_w = _gh_w / _gh_w.sum()
+TI = {(0, 0): 4, (0, 1): 5, (0, 2): 6, (1, 1): 7, (1, 2): 8, (2, 2): 9}
+
+
+def tidx(i, j):
+    return TI[(min(i, j), max(i, j))]
+
+
+def _chol3(S):
+    """Cholesky of a (possibly complex-symmetric) 3x3 matrix, without conjugation."""
+    L = np.zeros((3, 3), dtype=S.dtype)
+    for i in range(3):
+        for j in range(i + 1):
+            s = S[i, j] - sum(L[i, k] * L[j, k] for k in range(j))
+            L[i, j] = np.sqrt(s) if i == j else s / L[j, j]
+    return L
+
+
+def cons(W):
+    W = np.asarray(W)
+    U = np.zeros(10, dtype=W.dtype)
+    rho, u = W[0], W[1:4]
+    U[0] = rho
+    U[1:4] = rho * u
+    for i in range(3):
+        for j in range(i, 3):
+            U[tidx(i, j)] = W[tidx(i, j)] + rho * u[i] * u[j]
+    return U
+
+
+def flux_gh(W, d):
+    """Flux along d as moments of f = rho N(u, P/rho): rho<v_d>, rho<v_i v_d>, rho<v_i v_j v_d>."""
+    W = np.asarray(W)
+    rho, u = W[0], W[1:4]
+    S = np.empty((3, 3), dtype=W.dtype)
+    for i in range(3):
+        for j in range(3):
+            S[i, j] = W[tidx(i, j)] / rho
+    L = _chol3(S)
+    F = np.zeros(10, dtype=W.dtype)
+    for a, wa in zip(_gh_x, _gh_w):
+        for b, wb in zip(_gh_x, _gh_w):
+            for c, wc in zip(_gh_x, _gh_w):
+                v = u + L @ np.array([a, b, c])
+                w = wa * wb * wc * rho
+                F[0] += w * v[d]
+                for i in range(3):
+                    F[1 + i] += w * v[i] * v[d]
+                    for j in range(i, 3):
+                        F[tidx(i, j)] += w * v[i] * v[j] * v[d]
+    return F
+
+
+def jac_cs(fun, W, h=1e-30):
+    """Complex-step Jacobian d fun / d W (exact to rounding)."""
+    W = np.asarray(W, dtype=np.float64)
+    J = np.zeros((10, 10))
+    for k in range(10):
+        Wc = W.astype(np.complex128)
+        Wc[k] += 1j * h
+        J[:, k] = np.imag(fun(Wc)) / h
+    return J
+
+
+def prim_jacobian(W, d):
+    dU = jac_cs(cons, W)
+    dF = jac_cs(lambda w: flux_gh(w, d), W)
+    return np.linalg.solve(dU, dF)
+
+
+def _free_sets(d):
+    t = [a for a in range(3) if a != d]
+    shear = [1 + t[0], 1 + t[1]]
+    contact = [0, tidx(t[0], t[0]), tidx(t[0], t[1]), tidx(t[1], t[1])]
+    return shear, contact
+
+
+def eigen(W, d):
+    """(A, lam, R) with numerically computed eigen-decomposition (columns of R)."""
+    A = prim_jacobian(W, d)
+    lam = np.sort(np.linalg.eigvals(A).real)
+    groups = []
+    for v in lam:
+        if groups and abs(v - groups[-1][0]) < 1e-7 * (1 + abs(v)):
+            groups[-1][1] += 1
+        else:
+            groups.append([v, 1])
+    shear, contact = _free_sets(d)
+    cols, lams = [], []
+    for v, m in groups:
+        M = A - v * np.eye(10)
+        _, s, Vt = np.linalg.svd(M)
+        N = Vt[-m:].T  # null space basis
+        if m == 1:
+            B = N
+        else:
+            S = contact if m == 4 else shear
+            B = N @ np.linalg.inv(N[S, :])
+        for k in range(m):
+            cols.append(B[:, k])
+            lams.append(v)
+    return A, np.array(lams), np.array(cols).T
+
+
+def mc(dL, dC, dR):
+    out = np.zeros_like(dC)
+    ok = dL * dR > 0
+    m = np.minimum(np.minimum(2 * np.abs(dL), np.abs(dC)), 2 * np.abs(dR))
+    out[ok] = np.sign(dC[ok]) * m[ok]
+    return out
+
+
+def prim(U):
+    W = np.zeros(10)
+    rho = U[0]
+    W[0] = rho
+    W[1:4] = U[1:4] / rho
+    for i in range(3):
+        for j in range(i, 3):
+            W[tidx(i, j)] = U[tidx(i, j)] - rho * W[1 + i] * W[1 + j]
+    return W
+
+
+def recon(Wm, W0, Wp, d, dtdx):
+    A, lam, R = eigen(W0, d)
+    Linv = np.linalg.inv(R)
+    dL, dR, dC = W0 - Wm, Wp - W0, 0.5 * (Wp - Wm)
+    dm = R @ mc(Linv @ dL, Linv @ dC, Linv @ dR)
+    hi = W0 + 0.5 * dm - 0.5 * dtdx * (A @ dm)
+    lo = W0 - 0.5 * dm - 0.5 * dtdx * (A @ dm)
+    nn = tidx(d, d)
+    if not (hi[0] > 0 and lo[0] > 0 and hi[nn] > 0 and lo[nn] > 0):
+        hi, lo = W0.copy(), W0.copy()
+    return lo, hi
+
+
+def speeds(W, d):
+    lam = np.linalg.eigvals(prim_jacobian(W, d)).real
+    return lam.min(), lam.max()
+
+
+def hll(WL, WR, d):
+    aL, bL = speeds(WL, d)
+    aR, bR = speeds(WR, d)
+    SL, SR = min(aL, aR), max(bL, bR)
+    FL, FR = flux_gh(WL, d).real, flux_gh(WR, d).real
+    if SL >= 0:
+        return FL
+    if SR <= 0:
+        return FR
+    UL, UR = cons(WL), cons(WR)
+    return (SR * FL - SL * FR + SL * SR * (UR - UL)) / (SR - SL)
+
+
+def _pad_line(Uline, bclo, bchi, d):
+    """Two ghost cells each side along a line of conserved states (n, 10)."""
+    n = Uline.shape[0]
+    out = np.zeros((n + 4, 10))
+    out[2:-2] = Uline
+    flip = np.ones(10)
+    flip[1 + d] = -1
+    for t in range(3):
+        if t != d:
+            flip[tidx(d, t)] = -1
+    for g in (1, 2):
+        # lower side: ghost index -g
+        if bclo == 0:
+            out[2 - g] = Uline[n - g]
+        elif bclo == 1:
+            out[2 - g] = Uline[0]
+        else:
+            out[2 - g] = Uline[g - 1] * flip
+        if bchi == 0:
+            out[n + 1 + g] = Uline[g - 1]
+        elif bchi == 1:
+            out[n + 1 + g] = Uline[n - 1]
+        else:
+            out[n + 1 + g] = Uline[n - g] * flip
+    return out
+
+
+def step(U, ndim, dx, bc, dt, phi=None):
+    """One unsplit step on a tiny grid.  U: [10][nz][ny][nx]; bc: ((lo,hi),...)."""
+    U = np.asarray(U, dtype=np.float64)
+    dU = np.zeros_like(U)
+    nz, ny, nx = U.shape[1:]
+    shape = (nx, ny, nz)
+    for d in range(ndim):
+        other = [a for a in range(3) if a != d]
+        for j1 in range(shape[other[0]]):
+            for j2 in range(shape[other[1]]):
+                idx = [None, None, None]
+                idx[other[0]], idx[other[1]] = j1, j2
+                line = []
+                for i in range(shape[d]):
+                    idx[d] = i
+                    line.append(U[:, idx[2], idx[1], idx[0]])
+                P = _pad_line(np.array(line), bc[d][0], bc[d][1], d)
+                Wl = [prim(u) for u in P]
+                n = shape[d]
+                faces = [recon(Wl[k - 1], Wl[k], Wl[k + 1], d, dt / dx[d]) for k in range(1, n + 3)]
+                # faces[k-1] = (lo, hi) of padded cell k, cell i <-> padded i+2
+                for i in range(n):
+                    Fm = hll(faces[i][1], faces[i + 1][0], d)
+                    Fp = hll(faces[i + 1][1], faces[i + 2][0], d)
+                    idx[d] = i
+                    dU[:, idx[2], idx[1], idx[0]] -= (Fp - Fm) / dx[d]
+    Un = U + dt * dU
+    if phi is not None:
+        g = [1 if d < ndim else 0 for d in range(3)]
+        for z in range(nz):
+            for y in range(ny):
+                for x in range(nx):
+                    c = (z + g[2], y + g[1], x + g[0])
+                    a = np.zeros(3)
+                    for d in range(ndim):
+                        e = [0, 0, 0]
+                        e[2 - d] = 1
+                        cp = tuple(c[k] + e[k] for k in range(3))
+                        cm = tuple(c[k] - e[k] for k in range(3))
+                        a[d] = -(phi[cp] - phi[cm]) / (2 * dx[d])
+                    u = Un[:, z, y, x]
+                    m_old = u[1:4].copy()
+                    m_new = m_old + dt * u[0] * a
+                    mbar = 0.5 * (m_old + m_new)
+                    for i in range(3):
+                        for j in range(i, 3):
+                            u[tidx(i, j)] += dt * (mbar[i] * a[j] + a[i] * mbar[j])
+                    u[1:4] = m_new
+    return Un
+
+
+def cfl_dt(U, ndim, dx, cfl):
+    nz, ny, nx = U.shape[1:]
+    smax = 0.0
+    for z in range(nz):
+        for y in range(ny):
+            for x in range(nx):
+                W = prim(U[:, z, y, x])
+                s = 0.0
+                for d in range(ndim):
+                    a, b = speeds(W, d)
+                    s += max(abs(a), abs(b)) / dx[d]
+                smax = max(smax, s)
+    return cfl / smax
