@@ -1,0 +1,223 @@
+/*
+ * msh.h -- C ABI of libmsh, a GB300 (sm_103a) solver for the collisionless Boltzmann
+ * moment equations (BME) of Mitchell, Vorobyov & Hensler, arXiv:1210.5246.
+ *
+ * The operation behind every call is one Godunov finite-volume step of the ten moment
+ * equations (Sec. 2, eqs contin, moment, dispers, closed with zero heat flux):
+ * characteristic-traced MUSCL-Hancock reconstruction on the eigenvectors of the
+ * primitive Jacobian (Sec. 3.3, eqs jacobian, eigenvalues, righteigvec, lefteigvec,
+ * extended to ten variables), an HLL Riemann flux with the fast speed
+ * sqrt(3 P_nn / rho) (Sec. 3.2 eq soundspeed, Sec. 3.3), an unsplit conservative
+ * update, the gravity source applied after the hydro step (operator splitting, last
+ * paragraph of Sec. 3.3) and a CFL time-step reduction.
+ *
+ * Conventions shared by all calls
+ * -------------------------------
+ * State layout: structure of arrays [10][nz][ny][nx], x fastest, no ghost cells, in
+ * the grid's precision (float for MSH_FP32, double for MSH_FP64).  Component order:
+ *   conserved U = (rho, m_x, m_y, m_z, E_xx, E_xy, E_xz, E_yy, E_yz, E_zz)
+ *   primitive W = (rho, u_x, u_y, u_z, P_xx, P_xy, P_xz, P_yy, P_yz, P_zz)
+ * with m = rho u and E_ij = P_ij + rho u_i u_j (Sec. 2, below eq dispers).
+ * Unused dimensions have n = 1 (1D: n = {nx,1,1}; 2D: n = {nx,ny,1}).
+ *
+ * Memory: `where` = MSH_HOST means a host pointer (pageable or pinned), MSH_DEVICE a
+ * device pointer on the current CUDA device.  The caller keeps ownership of every
+ * pointer it passes; the library copies what it needs before returning (or, for
+ * device pointers, in stream order on the grid's stream).  The library owns the
+ * buffers behind a handle until msh_destroy / msh_batch_destroy.
+ *
+ * Errors: every call returns an msh_status.  On error nothing is written to the
+ * caller's output arguments and msh_last_error() (thread-local) describes the cause.
+ * No C++ exception crosses the ABI.  There is no CPU fallback: without a usable CUDA
+ * device the calls that need one return MSH_E_CUDA.
+ */
+#ifndef MSH_H
+#define MSH_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t msh_status;
+#define MSH_OK 0
+#define MSH_E_INVALID_ARG 1   /* bad size, pointer, enum or order of arguments          */
+#define MSH_E_CUDA 2          /* a CUDA runtime call failed (message has the CUDA error) */
+#define MSH_E_NOMEM 3         /* device or pinned allocation failed                     */
+#define MSH_E_REALIZABILITY 4 /* rho <= 0 or P not positive definite in some cell       */
+#define MSH_E_TIMEOUT 5       /* a bounded device-side wait ran out                     */
+#define MSH_E_STATE 6         /* call made in the wrong order (e.g. step before state)  */
+
+#define MSH_BC_PERIODIC 0     /* wrap-around                                            */
+#define MSH_BC_OUTFLOW 1      /* zero-gradient copy of the edge cell                    */
+#define MSH_BC_REFLECT 2      /* mirror; negates m_n and E_nt (t != n) of the image     */
+
+#define MSH_FP32 0
+#define MSH_FP64 1
+
+#define MSH_HOST 0
+#define MSH_DEVICE 1
+
+#define MSH_CONSERVED 0
+#define MSH_PRIMITIVE 1
+
+typedef struct msh_grid msh_grid;
+typedef struct msh_batch msh_batch;
+
+/* Description of the last error on the calling thread ("" if none).  The pointer stays
+ * valid until the next msh_* call on this thread. */
+const char *msh_last_error(void);
+
+/* Library version, major*10000 + minor*100 + patch. */
+int32_t msh_version(void);
+
+/*
+ * Create a uniform grid (the paper's Sec. 3.1 block of cells without AMR).
+ *   ndim      1, 2 or 3
+ *   n[3]      cells per dimension, n[d] >= 2 for d < ndim, n[d] == 1 otherwise
+ *   lo, hi    domain corners; hi[d] > lo[d] for d < ndim (cell width (hi-lo)/n)
+ *   bc[6]     bc[2d] lower, bc[2d+1] upper boundary of dimension d (MSH_BC_*); a
+ *             periodic side must be paired with a periodic side
+ *   precision MSH_FP32 or MSH_FP64 (arithmetic and storage of the state)
+ *   cfl       Courant number C in (0, 1]: dt = C / max sum_d (|u_d| + sqrt(3 P_dd/rho))/dx_d
+ *   stream    cudaStream_t to run on, or NULL for a stream the grid creates and owns
+ * Allocates two state buffers, reduction scratch and control block on the current
+ * device.  *out receives the handle.
+ */
+msh_status msh_init_grid(msh_grid **out, int32_t ndim, const int64_t n[3], const double lo[3],
+                         const double hi[3], const int32_t bc[6], int32_t precision, double cfl,
+                         void *stream);
+
+/* Release everything the grid owns.  NULL is accepted. */
+msh_status msh_destroy(msh_grid *g);
+
+/*
+ * Copy a state into the grid (and reset nothing else: time and step count are kept).
+ *   U     [10][nz][ny][nx] in the grid precision, conserved or primitive (kind)
+ * Rejects a state with rho <= 0 or non positive-definite P (Sylvester minors) with
+ * MSH_E_REALIZABILITY, leaving the previous state in place.  Computes the CFL time
+ * step of the new state.
+ */
+msh_status msh_set_state(msh_grid *g, const void *U, int32_t where, int32_t kind);
+
+/* Copy the current state out ([10][nz][ny][nx], grid precision, conserved or primitive). */
+msh_status msh_get_state(msh_grid *g, void *U, int32_t where, int32_t kind);
+
+/* Set the simulation time and step counter (e.g. when resuming from a saved state). */
+msh_status msh_set_time(msh_grid *g, double t, int64_t step);
+
+/* Current simulation time (accumulated in FP64) and number of steps taken. */
+msh_status msh_get_time(msh_grid *g, double *t, int64_t *step);
+
+/*
+ * External gravitational potential Phi at cell centres, including one ghost layer on
+ * each active dimension: [nz+2gz][ny+2gy][nx+2gx] doubles, g = 1 for active dims, 0
+ * otherwise.  The acceleration a = -grad Phi is taken by central differences and applied
+ * after the hydro update (Sec. 3.3, operator splitting; sources of eqs moment/dispers):
+ * m += dt rho a, E += dt (mbar a^T + a mbar^T), mbar = (m_before + m_after)/2.
+ * phi == NULL removes gravity.  The library copies the array.
+ */
+msh_status msh_set_potential(msh_grid *g, const double *phi, int32_t where);
+
+/*
+ * One step with dt = min(CFL dt of the current state, dt_max).  *dt_taken (may be NULL)
+ * receives the step size.  Returns MSH_E_REALIZABILITY (and keeps the new state, so it
+ * can be inspected) if the step produced a non-realizable cell.
+ */
+msh_status msh_step(msh_grid *g, double dt_max, double *dt_taken);
+
+/*
+ * Advance until t_end (the last step is clipped to land on t_end exactly) or until
+ * max_steps more steps were taken.  Steps are launched from CUDA graphs with the time
+ * control on the device; the host synchronises only to test for completion.
+ * *steps (may be NULL) receives the number of steps taken by this call, *t_out (may be
+ * NULL) the final time.  Stops early with MSH_E_REALIZABILITY on a non-realizable cell.
+ */
+msh_status msh_run(msh_grid *g, double t_end, int64_t max_steps, int64_t *steps, double *t_out);
+
+/*
+ * FP64 totals of the ten conserved fields over the grid (pairwise reduced, fixed order)
+ * as of the last step or set_state, realizability flag (1 = every cell has rho > 0 and
+ * P positive definite) and the first offending cell's linear index (-1 if none).
+ * Any output pointer may be NULL.
+ */
+msh_status msh_diagnostics(msh_grid *g, double totals[10], int32_t *realizable, int64_t *first_bad);
+
+/*
+ * Record the dt of every following step into a device-side history of `capacity`
+ * entries (0 disables and frees it).  Needed by msh_adjoint_run's callers that replay a
+ * forward run.  msh_get_dt_history copies at most `capacity` entries (host pointer) and
+ * returns the number recorded in *count.
+ */
+msh_status msh_set_recording(msh_grid *g, int64_t capacity);
+msh_status msh_get_dt_history(msh_grid *g, double *dts, int64_t capacity, int64_t *count);
+
+/*
+ * Tile shape of the 2D/3D step kernel: rows per thread block (4, 8 or 16) and z planes
+ * streamed per block (3D only, >= 1).  msh_autotune times the candidates on this grid's
+ * current state (without changing it) and keeps the fastest; the chosen values are
+ * returned in *rows / *zchunk (may be NULL).
+ */
+msh_status msh_set_tiling(msh_grid *g, int32_t rows, int32_t zchunk);
+msh_status msh_get_tiling(msh_grid *g, int32_t *rows, int32_t *zchunk);
+msh_status msh_autotune(msh_grid *g, int32_t *rows, int32_t *zchunk);
+
+/*
+ * Kernel timing: with profiling on, msh_run brackets every step-kernel launch with CUDA
+ * events on the grid's stream (recorded inside the run's CUDA graph) and accumulates
+ * their elapsed times.  msh_get_profile returns the summed step-kernel time in ms and
+ * the number of timed launches since profiling was switched on.
+ */
+msh_status msh_set_profiling(msh_grid *g, int32_t on);
+msh_status msh_get_profile(msh_grid *g, double *step_kernel_ms, int64_t *launches);
+
+/*
+ * Discrete adjoint (vector-Jacobian product) of `nsteps` forward steps taken from U0
+ * with the frozen time-step schedule dt_sched[nsteps] (host doubles), limiter branches,
+ * HLL branches and face-state fallbacks frozen at their forward values:
+ *     dL_dU0 = (d U_N / d U_0)^T dL_dUN.
+ *   U0, dL_dUN, dL_dU0   [10][nz][ny][nx] in the grid precision, located per `where`;
+ *                        if kind == MSH_PRIMITIVE, U0 is primitive and dL_dU0 is the
+ *                        gradient with respect to the primitive initial state
+ *   K                    checkpoint interval (>= 1): the forward states are stored every
+ *                        K steps and recomputed in between during the reverse sweep
+ * Uses the grid's potential and boundaries; does not change the grid's state or time.
+ */
+msh_status msh_adjoint_run(msh_grid *g, const void *U0, int64_t nsteps, const double *dt_sched,
+                           int32_t K, const void *dL_dUN, void *dL_dU0, int32_t where,
+                           int32_t kind);
+
+/*
+ * Batched independent 1D Riemann problems ("tubes") on [0, 1] with the interface at 0.5
+ * and outflow boundaries, each advanced to its own t_end with its own CFL time step.
+ *   ntubes           number of tubes (>= 1)
+ *   len[ntubes]      cells per tube, 4 <= len <= 4096 (host)
+ *   WL, WR           [ntubes][10] primitive left / right states (host doubles)
+ *   t_end[ntubes]    final times (host doubles, > 0)
+ *   precision        MSH_FP32 or MSH_FP64
+ * The tubes are stored back to back, [10][sum len] (tube k starts at the prefix sum of
+ * len).  msh_batch_run advances all tubes in one persistent launch captured in a CUDA
+ * graph; thread blocks take tubes longest first from a device work queue.  threads is
+ * the block size (0 = autotuned: the fastest of the candidates on a warm-up run).
+ * max_steps caps the steps of each tube (MSH_E_TIMEOUT if a tube hits it before t_end).
+ */
+msh_status msh_batch_init(msh_batch **out, int32_t ntubes, const int32_t *len, const double *WL,
+                          const double *WR, const double *t_end, int32_t precision, double cfl,
+                          void *stream);
+msh_status msh_batch_reset(msh_batch *b);
+msh_status msh_batch_run(msh_batch *b, int32_t threads, int64_t max_steps);
+/* One tube per launch sequence: the same tubes advanced with one step-kernel launch per
+ * step (the baseline the persistent form is compared with).  tubes == NULL runs all. */
+msh_status msh_batch_run_per_tube(msh_batch *b, const int32_t *tubes, int32_t count,
+                                  int64_t max_steps);
+msh_status msh_batch_get_state(msh_batch *b, void *U, int32_t where, int32_t kind);
+/* steps[ntubes] and t[ntubes] (host, either may be NULL); *cell_updates = sum steps*len. */
+msh_status msh_batch_info(msh_batch *b, int64_t *steps, double *t, int64_t *cell_updates);
+msh_status msh_batch_destroy(msh_batch *b);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MSH_H */

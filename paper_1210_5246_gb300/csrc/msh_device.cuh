@@ -1,0 +1,262 @@
+// msh_device.cuh -- per-cell and per-face device arithmetic of the BME Godunov step.
+//
+// Everything here works on one 10-vector in registers.  The reconstruction and the flux
+// are written in the "local frame" of a sweep direction: the normal axis is moved to
+// the x slot, the two transverse axes keep their natural order.  In that frame the
+// eigen-system is the ten-variable extension of the paper's x-direction system
+// (Sec. 3.3, eqs jacobian, eigenvalues, righteigvec, lefteigvec):
+//   eigenvalues  u -+ cf, u -+ cs (twice each), u (four contact waves),
+//   cf = sqrt(3 P_xx / rho), cs = sqrt(P_xx / rho),
+// and the projections below are its closed-form sparse left/right eigenvectors.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace msh {
+
+constexpr int NV = 10;
+
+// Primitive/conserved component that sits at local slot k for sweep direction D.
+// D = 0: (rho, u, v, w, Pxx, Pxy, Pxz, Pyy, Pyz, Pzz)
+// D = 1: normal y, transverse (x, z);  D = 2: normal z, transverse (x, y).
+template <int D> struct Frame;
+template <> struct Frame<0> {
+  static __device__ __forceinline__ constexpr int g(int k) { return k; }
+};
+template <> struct Frame<1> {
+  static __device__ __forceinline__ constexpr int g(int k) {
+    return k == 1 ? 2 : k == 2 ? 1 : k == 4 ? 7 : k == 6 ? 8 : k == 7 ? 4 : k == 8 ? 6 : k;
+  }
+};
+template <> struct Frame<2> {
+  static __device__ __forceinline__ constexpr int g(int k) {
+    return k == 1 ? 3 : k == 2 ? 1 : k == 3 ? 2 : k == 4 ? 9 : k == 5 ? 6 : k == 6 ? 8
+         : k == 7 ? 4 : k == 8 ? 5 : k == 9 ? 7 : k;
+  }
+};
+
+// ---------------------------------------------------------------- conversions
+// E_ij = P_ij + rho u_i u_j (Sec. 2).  The FP32 path recomputes a diagonal dispersion
+// in FP64 when the kinetic part cancels more than 99.9 % of E_ii, i.e. where P_ii/rho
+// approaches realizability loss.
+template <typename T> __device__ __forceinline__ T diag_fix(T P, T E, T m, T rho) { return P; }
+template <> __device__ __forceinline__ float diag_fix<float>(float P, float E, float m, float rho) {
+  if (P < 1.0e-3f * E) {
+    double r = (double)E - (double)m * (double)m / (double)rho;
+    return (float)r;
+  }
+  return P;
+}
+
+template <typename T>
+__device__ __forceinline__ void cons_to_prim(const T (&U)[NV], T (&W)[NV]) {
+  const T rho = U[0];
+  const T ir = T(1) / rho;
+  const T u = U[1] * ir, v = U[2] * ir, w = U[3] * ir;
+  W[0] = rho; W[1] = u; W[2] = v; W[3] = w;
+  W[4] = diag_fix<T>(U[4] - U[1] * u, U[4], U[1], rho);
+  W[5] = U[5] - U[1] * v;
+  W[6] = U[6] - U[1] * w;
+  W[7] = diag_fix<T>(U[7] - U[2] * v, U[7], U[2], rho);
+  W[8] = U[8] - U[2] * w;
+  W[9] = diag_fix<T>(U[9] - U[3] * w, U[9], U[3], rho);
+}
+
+template <typename T>
+__device__ __forceinline__ void prim_to_cons(const T (&W)[NV], T (&U)[NV]) {
+  const T rho = W[0];
+  const T mx = rho * W[1], my = rho * W[2], mz = rho * W[3];
+  U[0] = rho; U[1] = mx; U[2] = my; U[3] = mz;
+  U[4] = W[4] + mx * W[1];
+  U[5] = W[5] + mx * W[2];
+  U[6] = W[6] + mx * W[3];
+  U[7] = W[7] + my * W[2];
+  U[8] = W[8] + my * W[3];
+  U[9] = W[9] + mz * W[3];
+}
+
+// rho > 0 and P positive definite by its leading principal minors.
+template <typename T> __device__ __forceinline__ bool realizable(const T (&W)[NV]) {
+  const T m1 = W[4];
+  const T m2 = W[4] * W[7] - W[5] * W[5];
+  const T m3 = W[4] * (W[7] * W[9] - W[8] * W[8]) - W[5] * (W[5] * W[9] - W[8] * W[6]) +
+               W[6] * (W[5] * W[8] - W[7] * W[6]);
+  return W[0] > T(0) && m1 > T(0) && m2 > T(0) && m3 > T(0);
+}
+
+// ----------------------------------------------------------- reconstruction
+// MC limiter on one characteristic amplitude, dC = (dL + dR)/2 by linearity of L.
+template <typename T> __device__ __forceinline__ T mc_limit(T dl, T dr) {
+  const T dc = T(0.5) * (dl + dr);
+  const T m = fmin(fmin(T(2) * fabs(dl), fabs(dc)), T(2) * fabs(dr));
+  return (dl * dr > T(0)) ? copysign(m, dc) : T(0);
+}
+
+// Eigen-quantities of the local-frame state w0 shared by projection and back-projection.
+template <typename T> struct Eig {
+  T rho, u, Pxx, Pxy, Pxz, Pyy, Pyz, Pzz;
+  T cf, cs, a, b, ip, icf2, ics2;
+  __device__ __forceinline__ void init(const T (&w)[NV]) {
+    rho = w[0]; u = w[1];
+    Pxx = w[4]; Pxy = w[5]; Pxz = w[6]; Pyy = w[7]; Pyz = w[8]; Pzz = w[9];
+    ip = T(1) / Pxx;
+    cs = sqrt(Pxx / rho);
+    cf = sqrt(T(3) * Pxx / rho);
+    a = Pxy * ip;
+    b = Pxz * ip;
+    icf2 = T(0.5) / cf;
+    ics2 = T(0.5) / cs;
+  }
+  // characteristic amplitudes c = L d in wave order
+  // (f-, sv-, sw-, c_rho, c_yy, c_yz, c_zz, sv+, sw+, f+)
+  __device__ __forceinline__ void project(const T (&d)[NV], T (&c)[NV]) const {
+    const T e = d[4] * ip * T(1.0 / 3.0);
+    const T t1 = d[1] * icf2, t2 = T(0.5) * e;
+    c[0] = t2 - t1;
+    c[9] = t2 + t1;
+    const T qv = (d[2] - a * d[1]) * ics2, rv = T(0.5) * (d[5] - a * d[4]) * ip;
+    c[1] = rv - qv;
+    c[7] = rv + qv;
+    const T qw = (d[3] - b * d[1]) * ics2, rw = T(0.5) * (d[6] - b * d[4]) * ip;
+    c[2] = rw - qw;
+    c[8] = rw + qw;
+    c[3] = d[0] - rho * e;
+    c[4] = d[7] - T(2) * a * d[5] + (T(4) * a * Pxy - Pyy) * e;
+    c[5] = d[8] - b * d[5] - a * d[6] + (T(4) * a * Pxz - Pyz) * e;
+    c[6] = d[9] - T(2) * b * d[6] + (T(4) * b * Pxz - Pzz) * e;
+  }
+  // primitive vector R c
+  __device__ __forceinline__ void back(const T (&c)[NV], T (&o)[NV]) const {
+    const T A = c[9] + c[0], B = (c[9] - c[0]) * cf;
+    const T C = c[7] + c[1], Dv = (c[7] - c[1]) * cs;
+    const T E = c[8] + c[2], Fw = (c[8] - c[2]) * cs;
+    o[0] = rho * A + c[3];
+    o[1] = B;
+    o[2] = a * B + Dv;
+    o[3] = b * B + Fw;
+    o[4] = T(3) * Pxx * A;
+    o[5] = T(3) * Pxy * A + Pxx * C;
+    o[6] = T(3) * Pxz * A + Pxx * E;
+    o[7] = (Pyy + T(2) * a * Pxy) * A + T(2) * Pxy * C + c[4];
+    o[8] = (Pyz + T(2) * a * Pxz) * A + Pxz * C + Pxy * E + c[5];
+    o[9] = (Pzz + T(2) * b * Pxz) * A + T(2) * Pxz * E + c[6];
+  }
+};
+
+// Reconstruction of one cell along the sweep direction, in the local frame.
+//   wm, w0, wp   primitive states of cells i-1, i, i+1
+//   nu           dt / (2 dx)
+// Output: face states lo (at i-1/2) and hi (at i+1/2):
+//   dw^m = R mc(L dw_L, L dw_R);   w0 -+ dw^m/2 - nu A dw^m,   A dw^m = R Lambda mc(...)
+// If a face state has rho <= 0 or P_nn <= 0 both revert to w0 (first order).
+template <typename T>
+__device__ __forceinline__ void reconstruct(const T (&wm)[NV], const T (&w0)[NV], const T (&wp)[NV],
+                                            T nu, T (&lo)[NV], T (&hi)[NV]) {
+  Eig<T> E;
+  E.init(w0);
+  T d[NV], cl[NV], cr[NV];
+#pragma unroll
+  for (int k = 0; k < NV; k++) d[k] = w0[k] - wm[k];
+  E.project(d, cl);
+#pragma unroll
+  for (int k = 0; k < NV; k++) d[k] = wp[k] - w0[k];
+  E.project(d, cr);
+  T m[NV];
+#pragma unroll
+  for (int k = 0; k < NV; k++) m[k] = mc_limit(cl[k], cr[k]);
+  // wave speeds relative to u: (-cf, -cs, -cs, 0, 0, 0, 0, cs, cs, cf)
+  T lm[NV];
+  lm[0] = -E.cf * m[0]; lm[1] = -E.cs * m[1]; lm[2] = -E.cs * m[2];
+  lm[3] = T(0); lm[4] = T(0); lm[5] = T(0); lm[6] = T(0);
+  lm[7] = E.cs * m[7]; lm[8] = E.cs * m[8]; lm[9] = E.cf * m[9];
+  T dw[NV], g[NV];
+  E.back(m, dw);   // limited primitive slope dw^m
+  E.back(lm, g);   // A dw^m - u dw^m
+#pragma unroll
+  for (int k = 0; k < NV; k++) {
+    const T adw = E.u * dw[k] + g[k];
+    const T pred = w0[k] - nu * adw;
+    hi[k] = pred + T(0.5) * dw[k];
+    lo[k] = pred - T(0.5) * dw[k];
+  }
+  const bool ok = hi[0] > T(0) && lo[0] > T(0) && hi[4] > T(0) && lo[4] > T(0);
+  if (!ok) {
+#pragma unroll
+    for (int k = 0; k < NV; k++) { hi[k] = w0[k]; lo[k] = w0[k]; }
+  }
+}
+
+// Conserved vector and normal flux of a local-frame primitive state (eqs contin,
+// moment, dispers: rho u_n; rho u_i u_n + P_in; E_ij u_n + P_in u_j + P_jn u_i).
+template <typename T>
+__device__ __forceinline__ void phys(const T (&w)[NV], T (&U)[NV], T (&F)[NV]) {
+  const T r = w[0], u = w[1], v = w[2], ww = w[3];
+  const T Pxx = w[4], Pxy = w[5], Pxz = w[6], Pyy = w[7], Pyz = w[8], Pzz = w[9];
+  const T mx = r * u, my = r * v, mz = r * ww;
+  U[0] = r; U[1] = mx; U[2] = my; U[3] = mz;
+  U[4] = Pxx + mx * u; U[5] = Pxy + mx * v; U[6] = Pxz + mx * ww;
+  U[7] = Pyy + my * v; U[8] = Pyz + my * ww; U[9] = Pzz + mz * ww;
+  F[0] = mx;
+  F[1] = mx * u + Pxx;
+  F[2] = my * u + Pxy;
+  F[3] = mz * u + Pxz;
+  F[4] = (U[4] + T(2) * Pxx) * u;
+  F[5] = (U[5] + Pxy) * u + Pxx * v;
+  F[6] = (U[6] + Pxz) * u + Pxx * ww;
+  F[7] = U[7] * u + T(2) * Pxy * v;
+  F[8] = U[8] * u + Pxy * ww + Pxz * v;
+  F[9] = U[9] * u + T(2) * Pxz * ww;
+}
+
+// HLL flux between local-frame face states wl | wr with signal speeds
+// S_L = min(u_L - cf_L, u_R - cf_R), S_R = max(u_L + cf_L, u_R + cf_R).
+template <typename T>
+__device__ __forceinline__ void hll(const T (&wl)[NV], const T (&wr)[NV], T (&F)[NV]) {
+  T Ul[NV], Fl[NV], Ur[NV], Fr[NV];
+  phys(wl, Ul, Fl);
+  phys(wr, Ur, Fr);
+  const T cl = sqrt(T(3) * wl[4] / wl[0]);
+  const T cr = sqrt(T(3) * wr[4] / wr[0]);
+  const T SL = fmin(wl[1] - cl, wr[1] - cr);
+  const T SR = fmax(wl[1] + cl, wr[1] + cr);
+  if (SL >= T(0)) {
+#pragma unroll
+    for (int k = 0; k < NV; k++) F[k] = Fl[k];
+  } else if (SR <= T(0)) {
+#pragma unroll
+    for (int k = 0; k < NV; k++) F[k] = Fr[k];
+  } else {
+    const T inv = T(1) / (SR - SL);
+    const T sls = SL * SR;
+#pragma unroll
+    for (int k = 0; k < NV; k++) F[k] = (SR * Fl[k] - SL * Fr[k] + sls * (Ur[k] - Ul[k])) * inv;
+  }
+}
+
+// ------------------------------------------------------------- boundaries
+enum { BC_PERIODIC = 0, BC_OUTFLOW = 1, BC_REFLECT = 2 };
+
+// Map a (possibly ghost) index onto the grid.  mirror = reflect image.  The result is
+// clamped into [0, n) so that tile overhang beyond the ghost layers stays in bounds.
+__device__ __forceinline__ int map_index(int i, int n, int bclo, int bchi, bool &mirror) {
+  mirror = false;
+  if (i < 0) {
+    if (bclo == BC_PERIODIC) i += n;
+    else if (bclo == BC_OUTFLOW) i = 0;
+    else { i = -1 - i; mirror = true; }
+  } else if (i >= n) {
+    if (bchi == BC_PERIODIC) i -= n;
+    else if (bchi == BC_OUTFLOW) i = n - 1;
+    else { i = 2 * n - 1 - i; mirror = true; }
+  }
+  return min(max(i, 0), n - 1);
+}
+
+// Sign flips of a mirrored image across a face normal to d: m_d and E_dt (t != d).
+__device__ __forceinline__ unsigned flip_mask(int d) {
+  return d == 0 ? ((1u << 1) | (1u << 5) | (1u << 6))
+       : d == 1 ? ((1u << 2) | (1u << 5) | (1u << 8))
+                : ((1u << 3) | (1u << 6) | (1u << 8));
+}
+
+}  // namespace msh

@@ -1,0 +1,591 @@
+// msh_host.cu -- C ABI of libmsh: grid lifecycle, state transfer, step/run control.
+//
+// A grid owns two state buffers (ping-pong by step parity), a device control block
+// (time, dt, step counter, stop flags), per-block reduction partials and a cached CUDA
+// graph holding kGraphSteps consecutive (step, finalize) launch pairs.  msh_run launches
+// that graph until the device control block reports completion; kernels of a finished
+// run return immediately, so over-launching past t_end is harmless.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/msh.h"
+#include "msh_internal.h"
+
+using namespace msh;
+
+namespace {
+
+thread_local std::string g_err;
+
+msh_status fail(msh_status s, const char *fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return s;
+}
+
+#define CUDA_TRY(expr)                                                                     \
+  do {                                                                                     \
+    cudaError_t e_ = (expr);                                                               \
+    if (e_ != cudaSuccess) {                                                               \
+      if (e_ == cudaErrorMemoryAllocation) return fail(MSH_E_NOMEM, "%s: %s", #expr, cudaGetErrorString(e_)); \
+      return fail(MSH_E_CUDA, "%s: %s", #expr, cudaGetErrorString(e_));                    \
+    }                                                                                      \
+  } while (0)
+
+constexpr int kGraphSteps = 16;
+
+}  // namespace
+
+struct msh_grid {
+  int ndim = 0;
+  int64_t n[3] = {1, 1, 1};
+  double lo[3] = {0, 0, 0}, hi[3] = {1, 1, 1}, dx[3] = {1, 1, 1};
+  int32_t bc[6] = {0, 0, 0, 0, 0, 0};
+  int prec = MSH_FP64;
+  double cfl = 0.5;
+  size_t N = 0;           // cells
+  size_t esize = 8;       // bytes per element
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  void *U[2] = {nullptr, nullptr};
+  double *phi = nullptr;
+  Ctrl *ctrl = nullptr;   // device
+  Ctrl *hctrl = nullptr;  // pinned host mirror
+  Partial *part = nullptr;
+  int part_cap = 0;
+  double *hist = nullptr;
+  int64_t hist_cap = 0;
+  bool has_state = false;
+  int rows = 8, zchunk = 32;
+  cudaGraphExec_t graph = nullptr;
+  // profiling: events around every step-kernel launch inside the graph
+  bool profiling = false;
+  std::vector<cudaEvent_t> ev;
+  double prof_ms = 0.0;
+  int64_t prof_launches = 0;
+};
+
+// ---------------------------------------------------------------- helpers
+namespace {
+
+template <typename T> StepArgs<T> make_args(msh_grid *g) {
+  StepArgs<T> a;
+  a.U[0] = (T *)g->U[0];
+  a.U[1] = (T *)g->U[1];
+  a.phi = g->phi;
+  a.ctrl = g->ctrl;
+  a.part = g->part;
+  a.nx = (int)g->n[0];
+  a.ny = (int)g->n[1];
+  a.nz = (int)g->n[2];
+  for (int i = 0; i < 6; i++) a.bc[i] = g->bc[i];
+  for (int i = 0; i < 3; i++) a.dx[i] = g->dx[i];
+  a.zchunk = g->zchunk;
+  return a;
+}
+
+int blocks_for(msh_grid *g, int rows, int zchunk) {
+  if (g->prec == MSH_FP32) return step_blocks<float>(g->ndim, rows, (int)g->n[0], (int)g->n[1], (int)g->n[2], zchunk);
+  return step_blocks<double>(g->ndim, rows, (int)g->n[0], (int)g->n[1], (int)g->n[2], zchunk);
+}
+
+msh_status ensure_partials(msh_grid *g, int need) {
+  if (need <= g->part_cap) return MSH_OK;
+  if (g->part) cudaFree(g->part);
+  g->part = nullptr;
+  g->part_cap = 0;
+  CUDA_TRY(cudaMalloc(&g->part, sizeof(Partial) * (size_t)need));
+  g->part_cap = need;
+  return MSH_OK;
+}
+
+void drop_graph(msh_grid *g) {
+  if (g->graph) cudaGraphExecDestroy(g->graph);
+  g->graph = nullptr;
+}
+
+msh_status launch_one_step(msh_grid *g, int ev_slot) {
+  int nb = 0;
+  cudaError_t e;
+  if (g->profiling && ev_slot >= 0) CUDA_TRY(cudaEventRecord(g->ev[2 * ev_slot], g->stream));
+  if (g->prec == MSH_FP32) e = launch_step<float>(make_args<float>(g), g->ndim, g->rows, g->stream, &nb);
+  else e = launch_step<double>(make_args<double>(g), g->ndim, g->rows, g->stream, &nb);
+  if (e != cudaSuccess) return fail(MSH_E_CUDA, "step kernel launch: %s", cudaGetErrorString(e));
+  if (g->profiling && ev_slot >= 0) CUDA_TRY(cudaEventRecord(g->ev[2 * ev_slot + 1], g->stream));
+  e = launch_finalize(g->ctrl, g->part, nb, 0, g->stream);
+  if (e != cudaSuccess) return fail(MSH_E_CUDA, "finalize launch: %s", cudaGetErrorString(e));
+  return MSH_OK;
+}
+
+msh_status build_graph(msh_grid *g) {
+  if (g->graph) return MSH_OK;
+  msh_status st = ensure_partials(g, blocks_for(g, g->rows, g->zchunk));
+  if (st) return st;
+  cudaGraph_t graph;
+  CUDA_TRY(cudaStreamBeginCapture(g->stream, cudaStreamCaptureModeThreadLocal));
+  for (int i = 0; i < kGraphSteps; i++) {
+    st = launch_one_step(g, i);
+    if (st) {
+      cudaStreamEndCapture(g->stream, &graph);
+      if (graph) cudaGraphDestroy(graph);
+      return st;
+    }
+  }
+  CUDA_TRY(cudaStreamEndCapture(g->stream, &graph));
+  cudaError_t e = cudaGraphInstantiate(&g->graph, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) return fail(MSH_E_CUDA, "graph instantiate: %s", cudaGetErrorString(e));
+  return MSH_OK;
+}
+
+msh_status read_ctrl(msh_grid *g) {
+  CUDA_TRY(cudaMemcpyAsync(g->hctrl, g->ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, g->stream));
+  CUDA_TRY(cudaStreamSynchronize(g->stream));
+  return MSH_OK;
+}
+
+void collect_profile(msh_grid *g, int slots) {
+  if (!g->profiling) return;
+  for (int i = 0; i < slots; i++) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, g->ev[2 * i], g->ev[2 * i + 1]) == cudaSuccess) {
+      g->prof_ms += ms;
+      g->prof_launches += 1;
+    }
+  }
+}
+
+// Scan the buffer `which` and run the finalize kernel in mode 1 (no time advance).
+msh_status prime(msh_grid *g, int which) {
+  msh_status st = ensure_partials(g, kScanBlocks);
+  if (st) return st;
+  cudaError_t e;
+  if (g->prec == MSH_FP32)
+    e = launch_scan<float>((const float *)g->U[which], g->N, (int)g->n[0], (int)g->n[1], g->ndim, g->dx, g->part,
+                           kScanBlocks, g->stream);
+  else
+    e = launch_scan<double>((const double *)g->U[which], g->N, (int)g->n[0], (int)g->n[1], g->ndim, g->dx,
+                            g->part, kScanBlocks, g->stream);
+  if (e != cudaSuccess) return fail(MSH_E_CUDA, "scan launch: %s", cudaGetErrorString(e));
+  e = launch_finalize(g->ctrl, g->part, kScanBlocks, 1, g->stream);
+  if (e != cudaSuccess) return fail(MSH_E_CUDA, "finalize launch: %s", cudaGetErrorString(e));
+  return read_ctrl(g);
+}
+
+int cur_buf(msh_grid *g) { return (int)(g->hctrl->step & 1); }
+
+}  // namespace
+
+// ------------------------------------------------------------------- ABI
+extern "C" {
+
+const char *msh_last_error(void) { return g_err.c_str(); }
+
+int32_t msh_version(void) { return 10000; }
+
+msh_status msh_init_grid(msh_grid **out, int32_t ndim, const int64_t n[3], const double lo[3],
+                         const double hi[3], const int32_t bc[6], int32_t precision, double cfl, void *stream) {
+  g_err.clear();
+  if (!out || !n || !lo || !hi || !bc) return fail(MSH_E_INVALID_ARG, "null argument");
+  if (ndim < 1 || ndim > 3) return fail(MSH_E_INVALID_ARG, "ndim must be 1, 2 or 3 (got %d)", ndim);
+  if (precision != MSH_FP32 && precision != MSH_FP64) return fail(MSH_E_INVALID_ARG, "bad precision %d", precision);
+  if (!(cfl > 0.0 && cfl <= 1.0)) return fail(MSH_E_INVALID_ARG, "cfl must be in (0, 1] (got %g)", cfl);
+  for (int d = 0; d < 3; d++) {
+    if (d < ndim) {
+      if (n[d] < 2) return fail(MSH_E_INVALID_ARG, "n[%d] must be >= 2", d);
+      if (!(hi[d] > lo[d])) return fail(MSH_E_INVALID_ARG, "hi[%d] must exceed lo[%d]", d, d);
+      for (int s = 0; s < 2; s++)
+        if (bc[2 * d + s] < 0 || bc[2 * d + s] > 2) return fail(MSH_E_INVALID_ARG, "bad bc[%d]", 2 * d + s);
+      if ((bc[2 * d] == MSH_BC_PERIODIC) != (bc[2 * d + 1] == MSH_BC_PERIODIC))
+        return fail(MSH_E_INVALID_ARG, "periodic boundary of dim %d must be paired", d);
+    } else if (n[d] != 1) {
+      return fail(MSH_E_INVALID_ARG, "n[%d] must be 1 for an unused dimension", d);
+    }
+  }
+  const double cells = (double)n[0] * (double)n[1] * (double)n[2];
+  if (cells * 10.0 > 2147483647.0 * 8.0) return fail(MSH_E_INVALID_ARG, "grid too large");
+  if (n[0] > (1 << 30) || n[1] > (1 << 30) || n[2] > (1 << 30)) return fail(MSH_E_INVALID_ARG, "grid too large");
+  int dev_count = 0;
+  if (cudaGetDeviceCount(&dev_count) != cudaSuccess || dev_count == 0)
+    return fail(MSH_E_CUDA, "no CUDA device available (libmsh has no CPU path)");
+  msh_grid *g = new (std::nothrow) msh_grid();
+  if (!g) return fail(MSH_E_NOMEM, "host allocation");
+  g->ndim = ndim;
+  for (int d = 0; d < 3; d++) {
+    g->n[d] = n[d];
+    g->lo[d] = d < ndim ? lo[d] : 0.0;
+    g->hi[d] = d < ndim ? hi[d] : 1.0;
+    g->dx[d] = (g->hi[d] - g->lo[d]) / (double)n[d];
+  }
+  for (int i = 0; i < 6; i++) g->bc[i] = (i < 2 * ndim) ? bc[i] : MSH_BC_PERIODIC;
+  g->prec = precision;
+  g->esize = precision == MSH_FP32 ? 4 : 8;
+  g->cfl = cfl;
+  g->N = (size_t)n[0] * n[1] * n[2];
+  g->zchunk = (int)std::min<int64_t>(32, n[2]);
+  g->rows = 8;
+  auto cleanup = [&](msh_status s) {
+    msh_destroy(g);
+    return s;
+  };
+  cudaError_t e;
+  if (stream) {
+    g->stream = (cudaStream_t)stream;
+  } else {
+    e = cudaStreamCreateWithFlags(&g->stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return cleanup(fail(MSH_E_CUDA, "stream create: %s", cudaGetErrorString(e)));
+    g->own_stream = true;
+  }
+  const size_t bytes = g->N * 10 * g->esize;
+  for (int b = 0; b < 2; b++) {
+    e = cudaMalloc(&g->U[b], bytes);
+    if (e != cudaSuccess) return cleanup(fail(MSH_E_NOMEM, "state buffer (%zu bytes): %s", bytes, cudaGetErrorString(e)));
+  }
+  e = cudaMalloc(&g->ctrl, sizeof(Ctrl));
+  if (e != cudaSuccess) return cleanup(fail(MSH_E_NOMEM, "control block: %s", cudaGetErrorString(e)));
+  e = cudaMallocHost(&g->hctrl, sizeof(Ctrl));
+  if (e != cudaSuccess) return cleanup(fail(MSH_E_NOMEM, "pinned control block: %s", cudaGetErrorString(e)));
+  memset(g->hctrl, 0, sizeof(Ctrl));
+  g->hctrl->cfl = cfl;
+  g->hctrl->t_end = INFINITY;
+  g->hctrl->dt_max = INFINITY;
+  g->hctrl->done = 1;
+  g->hctrl->first_bad = -1;
+  e = cudaMemcpyAsync(g->ctrl, g->hctrl, sizeof(Ctrl), cudaMemcpyHostToDevice, g->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);
+  if (e != cudaSuccess) return cleanup(fail(MSH_E_CUDA, "control init: %s", cudaGetErrorString(e)));
+  msh_status st = ensure_partials(g, std::max(kScanBlocks, blocks_for(g, g->rows, g->zchunk)));
+  if (st) return cleanup(st);
+  *out = g;
+  return MSH_OK;
+}
+
+msh_status msh_destroy(msh_grid *g) {
+  if (!g) return MSH_OK;
+  if (g->stream) cudaStreamSynchronize(g->stream);
+  drop_graph(g);
+  for (auto &e : g->ev) cudaEventDestroy(e);
+  for (int b = 0; b < 2; b++)
+    if (g->U[b]) cudaFree(g->U[b]);
+  if (g->phi) cudaFree(g->phi);
+  if (g->ctrl) cudaFree(g->ctrl);
+  if (g->hctrl) cudaFreeHost(g->hctrl);
+  if (g->part) cudaFree(g->part);
+  if (g->hist) cudaFree(g->hist);
+  if (g->own_stream && g->stream) cudaStreamDestroy(g->stream);
+  delete g;
+  return MSH_OK;
+}
+
+msh_status msh_set_state(msh_grid *g, const void *U, int32_t where, int32_t kind) {
+  g_err.clear();
+  if (!g || !U) return fail(MSH_E_INVALID_ARG, "null argument");
+  if (where != MSH_HOST && where != MSH_DEVICE) return fail(MSH_E_INVALID_ARG, "bad where");
+  if (kind != MSH_CONSERVED && kind != MSH_PRIMITIVE) return fail(MSH_E_INVALID_ARG, "bad kind");
+  const int cur = cur_buf(g), nxt = cur ^ 1;
+  const size_t bytes = g->N * 10 * g->esize;
+  CUDA_TRY(cudaMemcpyAsync(g->U[nxt], U, bytes, where == MSH_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice,
+                           g->stream));
+  if (kind == MSH_PRIMITIVE) {
+    cudaError_t e = g->prec == MSH_FP32 ? launch_convert<float>((float *)g->U[nxt], g->N, 0, g->stream)
+                                        : launch_convert<double>((double *)g->U[nxt], g->N, 0, g->stream);
+    if (e != cudaSuccess) return fail(MSH_E_CUDA, "convert: %s", cudaGetErrorString(e));
+  }
+  msh_status st = prime(g, nxt);
+  if (st) return st;
+  if (!g->hctrl->realizable) {
+    const int64_t bad = g->hctrl->first_bad;
+    // restore the control block's view of the old state
+    if (g->has_state) prime(g, cur);
+    return fail(MSH_E_REALIZABILITY, "state not realizable at cell %lld (rho <= 0 or P not SPD)", (long long)bad);
+  }
+  CUDA_TRY(cudaMemcpyAsync(g->U[cur], g->U[nxt], bytes, cudaMemcpyDeviceToDevice, g->stream));
+  CUDA_TRY(cudaStreamSynchronize(g->stream));
+  g->has_state = true;
+  return MSH_OK;
+}
+
+msh_status msh_get_state(msh_grid *g, void *U, int32_t where, int32_t kind) {
+  g_err.clear();
+  if (!g || !U) return fail(MSH_E_INVALID_ARG, "null argument");
+  if (where != MSH_HOST && where != MSH_DEVICE) return fail(MSH_E_INVALID_ARG, "bad where");
+  if (kind != MSH_CONSERVED && kind != MSH_PRIMITIVE) return fail(MSH_E_INVALID_ARG, "bad kind");
+  if (!g->has_state) return fail(MSH_E_STATE, "no state set");
+  const int cur = cur_buf(g), nxt = cur ^ 1;
+  const size_t bytes = g->N * 10 * g->esize;
+  const void *src = g->U[cur];
+  if (kind == MSH_PRIMITIVE) {
+    CUDA_TRY(cudaMemcpyAsync(g->U[nxt], g->U[cur], bytes, cudaMemcpyDeviceToDevice, g->stream));
+    cudaError_t e = g->prec == MSH_FP32 ? launch_convert<float>((float *)g->U[nxt], g->N, 1, g->stream)
+                                        : launch_convert<double>((double *)g->U[nxt], g->N, 1, g->stream);
+    if (e != cudaSuccess) return fail(MSH_E_CUDA, "convert: %s", cudaGetErrorString(e));
+    src = g->U[nxt];
+  }
+  CUDA_TRY(cudaMemcpyAsync(U, src, bytes, where == MSH_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice,
+                           g->stream));
+  CUDA_TRY(cudaStreamSynchronize(g->stream));
+  return MSH_OK;
+}
+
+msh_status msh_set_time(msh_grid *g, double t, int64_t step) {
+  g_err.clear();
+  if (!g) return fail(MSH_E_INVALID_ARG, "null grid");
+  if (step < 0 || !std::isfinite(t)) return fail(MSH_E_INVALID_ARG, "bad time or step");
+  if (((step ^ g->hctrl->step) & 1) && g->has_state) {
+    // keep the current state in the buffer the new parity selects
+    const size_t bytes = g->N * 10 * g->esize;
+    const int cur = cur_buf(g);
+    CUDA_TRY(cudaMemcpyAsync(g->U[cur ^ 1], g->U[cur], bytes, cudaMemcpyDeviceToDevice, g->stream));
+  }
+  g->hctrl->t = t;
+  g->hctrl->step = step;
+  CUDA_TRY(cudaMemcpyAsync(g->ctrl, g->hctrl, sizeof(Ctrl), cudaMemcpyHostToDevice, g->stream));
+  CUDA_TRY(cudaStreamSynchronize(g->stream));
+  return MSH_OK;
+}
+
+msh_status msh_get_time(msh_grid *g, double *t, int64_t *step) {
+  g_err.clear();
+  if (!g) return fail(MSH_E_INVALID_ARG, "null grid");
+  if (t) *t = g->hctrl->t;
+  if (step) *step = g->hctrl->step;
+  return MSH_OK;
+}
+
+msh_status msh_set_potential(msh_grid *g, const double *phi, int32_t where) {
+  g_err.clear();
+  if (!g) return fail(MSH_E_INVALID_ARG, "null grid");
+  drop_graph(g);
+  if (!phi) {
+    if (g->phi) cudaFree(g->phi);
+    g->phi = nullptr;
+    return MSH_OK;
+  }
+  if (where != MSH_HOST && where != MSH_DEVICE) return fail(MSH_E_INVALID_ARG, "bad where");
+  size_t cnt = 1;
+  for (int d = 0; d < 3; d++) cnt *= (size_t)(g->n[d] + (d < g->ndim ? 2 : 0));
+  if (!g->phi) CUDA_TRY(cudaMalloc(&g->phi, cnt * sizeof(double)));
+  CUDA_TRY(cudaMemcpyAsync(g->phi, phi, cnt * sizeof(double),
+                           where == MSH_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, g->stream));
+  CUDA_TRY(cudaStreamSynchronize(g->stream));
+  return MSH_OK;
+}
+
+msh_status msh_step(msh_grid *g, double dt_max, double *dt_taken) {
+  g_err.clear();
+  if (!g) return fail(MSH_E_INVALID_ARG, "null grid");
+  if (!g->has_state) return fail(MSH_E_STATE, "msh_step before msh_set_state");
+  if (!(dt_max > 0.0)) return fail(MSH_E_INVALID_ARG, "dt_max must be > 0");
+  msh_status st = ensure_partials(g, blocks_for(g, g->rows, g->zchunk));
+  if (st) return st;
+  const double t0 = g->hctrl->t;
+  cudaError_t e = launch_run_start(g->ctrl, INFINITY, 1, dt_max, g->stream);
+  if (e != cudaSuccess) return fail(MSH_E_CUDA, "run start: %s", cudaGetErrorString(e));
+  st = launch_one_step(g, -1);
+  if (st) return st;
+  st = read_ctrl(g);
+  if (st) return st;
+  if (dt_taken) *dt_taken = g->hctrl->t - t0;
+  if (g->hctrl->status == MSH_E_REALIZABILITY)
+    return fail(MSH_E_REALIZABILITY, "step produced a non-realizable cell %lld", (long long)g->hctrl->first_bad);
+  return MSH_OK;
+}
+
+msh_status msh_run(msh_grid *g, double t_end, int64_t max_steps, int64_t *steps, double *t_out) {
+  g_err.clear();
+  if (!g) return fail(MSH_E_INVALID_ARG, "null grid");
+  if (!g->has_state) return fail(MSH_E_STATE, "msh_run before msh_set_state");
+  if (max_steps < 0 || std::isnan(t_end)) return fail(MSH_E_INVALID_ARG, "bad t_end or max_steps");
+  msh_status st = build_graph(g);
+  if (st) return st;
+  const int64_t s0 = g->hctrl->step;
+  cudaError_t e = launch_run_start(g->ctrl, t_end, max_steps, INFINITY, g->stream);
+  if (e != cudaSuccess) return fail(MSH_E_CUDA, "run start: %s", cudaGetErrorString(e));
+  const int64_t max_launch = max_steps / kGraphSteps + 2;
+  for (int64_t it = 0;; it++) {
+    if (it > max_launch) return fail(MSH_E_STATE, "run did not terminate (device control inconsistent)");
+    CUDA_TRY(cudaGraphLaunch(g->graph, g->stream));
+    st = read_ctrl(g);
+    if (st) return st;
+    collect_profile(g, kGraphSteps);
+    if (g->hctrl->done) break;
+  }
+  if (steps) *steps = g->hctrl->step - s0;
+  if (t_out) *t_out = g->hctrl->t;
+  if (g->hctrl->status == MSH_E_REALIZABILITY)
+    return fail(MSH_E_REALIZABILITY, "non-realizable cell %lld at step %lld", (long long)g->hctrl->first_bad,
+                (long long)g->hctrl->step);
+  return MSH_OK;
+}
+
+msh_status msh_diagnostics(msh_grid *g, double totals[10], int32_t *realizable, int64_t *first_bad) {
+  g_err.clear();
+  if (!g) return fail(MSH_E_INVALID_ARG, "null grid");
+  if (!g->has_state) return fail(MSH_E_STATE, "no state set");
+  if (totals) memcpy(totals, g->hctrl->totals, sizeof(double) * 10);
+  if (realizable) *realizable = g->hctrl->realizable;
+  if (first_bad) *first_bad = g->hctrl->first_bad;
+  return MSH_OK;
+}
+
+msh_status msh_set_recording(msh_grid *g, int64_t capacity) {
+  g_err.clear();
+  if (!g || capacity < 0) return fail(MSH_E_INVALID_ARG, "bad argument");
+  CUDA_TRY(cudaStreamSynchronize(g->stream));
+  if (g->hist) cudaFree(g->hist);
+  g->hist = nullptr;
+  g->hist_cap = 0;
+  if (capacity > 0) {
+    CUDA_TRY(cudaMalloc(&g->hist, sizeof(double) * (size_t)capacity));
+    g->hist_cap = capacity;
+  }
+  g->hctrl->hist = g->hist;
+  g->hctrl->hist_cap = g->hist_cap;
+  g->hctrl->hist_base = g->hctrl->step;
+  CUDA_TRY(cudaMemcpyAsync(g->ctrl, g->hctrl, sizeof(Ctrl), cudaMemcpyHostToDevice, g->stream));
+  CUDA_TRY(cudaStreamSynchronize(g->stream));
+  return MSH_OK;
+}
+
+msh_status msh_get_dt_history(msh_grid *g, double *dts, int64_t capacity, int64_t *count) {
+  g_err.clear();
+  if (!g || capacity < 0 || (capacity > 0 && !dts)) return fail(MSH_E_INVALID_ARG, "bad argument");
+  int64_t n = g->hist ? g->hctrl->step - g->hctrl->hist_base : 0;
+  if (n > g->hist_cap) n = g->hist_cap;
+  if (n < 0) n = 0;
+  const int64_t m = n < capacity ? n : capacity;
+  if (m > 0) {
+    CUDA_TRY(cudaMemcpyAsync(dts, g->hist, sizeof(double) * (size_t)m, cudaMemcpyDeviceToHost, g->stream));
+    CUDA_TRY(cudaStreamSynchronize(g->stream));
+  }
+  if (count) *count = n;
+  return MSH_OK;
+}
+
+msh_status msh_set_tiling(msh_grid *g, int32_t rows, int32_t zchunk) {
+  g_err.clear();
+  if (!g) return fail(MSH_E_INVALID_ARG, "null grid");
+  if (rows != 4 && rows != 8 && rows != 16) return fail(MSH_E_INVALID_ARG, "rows must be 4, 8 or 16");
+  if (zchunk < 1) return fail(MSH_E_INVALID_ARG, "zchunk must be >= 1");
+  if (g->ndim < 3) zchunk = 1;
+  if (zchunk > g->n[2]) zchunk = (int)g->n[2];
+  msh_status st = ensure_partials(g, blocks_for(g, rows, zchunk));
+  if (st) return st;
+  if (rows != g->rows || zchunk != g->zchunk) drop_graph(g);
+  g->rows = rows;
+  g->zchunk = zchunk;
+  return MSH_OK;
+}
+
+msh_status msh_get_tiling(msh_grid *g, int32_t *rows, int32_t *zchunk) {
+  g_err.clear();
+  if (!g) return fail(MSH_E_INVALID_ARG, "null grid");
+  if (rows) *rows = g->rows;
+  if (zchunk) *zchunk = g->zchunk;
+  return MSH_OK;
+}
+
+// Time each tile shape on copies of the current state (the state, time and step
+// counter are restored afterwards) and keep the fastest.
+msh_status msh_autotune(msh_grid *g, int32_t *rows_out, int32_t *zchunk_out) {
+  g_err.clear();
+  if (!g) return fail(MSH_E_INVALID_ARG, "null grid");
+  if (!g->has_state) return fail(MSH_E_STATE, "msh_autotune before msh_set_state");
+  if (g->ndim == 1) {
+    if (rows_out) *rows_out = g->rows;
+    if (zchunk_out) *zchunk_out = g->zchunk;
+    return MSH_OK;
+  }
+  const size_t bytes = g->N * 10 * g->esize;
+  const int cur = cur_buf(g);
+  void *save = nullptr;
+  CUDA_TRY(cudaMalloc(&save, bytes));
+  Ctrl saved_ctrl = *g->hctrl;
+  msh_status st = MSH_OK;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  std::vector<std::pair<int, int>> cands;
+  const int rows_c[3] = {4, 8, 16};
+  const int zc_c[4] = {8, 16, 32, 64};
+  for (int r : rows_c) {
+    if (g->ndim == 2) cands.push_back({r, 1});
+    else
+      for (int z : zc_c)
+        if (z <= g->n[2]) cands.push_back({r, z});
+  }
+  float best = 1e30f;
+  std::pair<int, int> best_c = {g->rows, g->zchunk};
+  const int reps = 3;
+  if (cudaMemcpyAsync(save, g->U[cur], bytes, cudaMemcpyDeviceToDevice, g->stream) != cudaSuccess ||
+      cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+    st = fail(MSH_E_CUDA, "autotune setup: %s", cudaGetErrorString(cudaGetLastError()));
+  }
+  const bool prof = g->profiling;
+  g->profiling = false;
+  for (size_t i = 0; st == MSH_OK && i < cands.size(); i++) {
+    st = msh_set_tiling(g, cands[i].first, cands[i].second);
+    if (st) break;
+    cudaError_t e = launch_run_start(g->ctrl, INFINITY, 1 << 30, INFINITY, g->stream);
+    for (int w = 0; st == MSH_OK && w < 1; w++) st = launch_one_step(g, -1);
+    if (st == MSH_OK) e = cudaEventRecord(e0, g->stream);
+    for (int w = 0; st == MSH_OK && w < reps; w++) st = launch_one_step(g, -1);
+    if (st == MSH_OK) e = cudaEventRecord(e1, g->stream);
+    if (st == MSH_OK && e == cudaSuccess) e = cudaEventSynchronize(e1);
+    float ms = 0.f;
+    if (st == MSH_OK && e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    if (st == MSH_OK && e != cudaSuccess) st = fail(MSH_E_CUDA, "autotune timing: %s", cudaGetErrorString(e));
+    if (st == MSH_OK && ms < best) {
+      best = ms;
+      best_c = cands[i];
+    }
+    // restore state and control block for the next candidate
+    if (st == MSH_OK) {
+      *g->hctrl = saved_ctrl;
+      e = cudaMemcpyAsync(g->ctrl, g->hctrl, sizeof(Ctrl), cudaMemcpyHostToDevice, g->stream);
+      if (e == cudaSuccess) e = cudaMemcpyAsync(g->U[cur], save, bytes, cudaMemcpyDeviceToDevice, g->stream);
+      if (e != cudaSuccess) st = fail(MSH_E_CUDA, "autotune restore: %s", cudaGetErrorString(e));
+    }
+  }
+  g->profiling = prof;
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  cudaStreamSynchronize(g->stream);
+  cudaFree(save);
+  if (st) return st;
+  st = msh_set_tiling(g, best_c.first, best_c.second);
+  if (st) return st;
+  if (rows_out) *rows_out = g->rows;
+  if (zchunk_out) *zchunk_out = g->zchunk;
+  return MSH_OK;
+}
+
+msh_status msh_set_profiling(msh_grid *g, int32_t on) {
+  g_err.clear();
+  if (!g) return fail(MSH_E_INVALID_ARG, "null grid");
+  if (on && g->ev.empty()) {
+    g->ev.resize(2 * kGraphSteps);
+    for (auto &e : g->ev) CUDA_TRY(cudaEventCreate(&e));
+  }
+  if ((bool)on != g->profiling) drop_graph(g);
+  g->profiling = on != 0;
+  g->prof_ms = 0.0;
+  g->prof_launches = 0;
+  return MSH_OK;
+}
+
+msh_status msh_get_profile(msh_grid *g, double *step_kernel_ms, int64_t *launches) {
+  g_err.clear();
+  if (!g) return fail(MSH_E_INVALID_ARG, "null grid");
+  if (step_kernel_ms) *step_kernel_ms = g->prof_ms;
+  if (launches) *launches = g->prof_launches;
+  return MSH_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,55 @@
+// msh_internal.h -- shared host/device declarations of libmsh (not part of the ABI).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace msh {
+
+// Device-resident time control of a grid.  The step kernels read dt and the buffer
+// parity from here; the finalize kernel writes the next dt, so a run needs no host
+// round trip per step.
+struct Ctrl {
+  double t, t_next, t_end, dt, dt_max, dt_cfl, cfl;
+  int64_t step, max_step, first_bad, hist_cap, hist_base;
+  int32_t done, status, realizable, pad;
+  double totals[10];
+  double *hist;
+};
+
+// Per-thread-block partial reductions written by the step and scan kernels.
+struct Partial {
+  double diag[10];
+  double smax;
+  long long bad;
+};
+
+template <typename T> struct StepArgs {
+  T *U[2];              // ping-pong state buffers, source = U[step & 1]
+  const double *phi;    // potential with one ghost layer, or nullptr
+  Ctrl *ctrl;
+  Partial *part;
+  int nx, ny, nz;
+  int bc[6];
+  double dx[3];
+  int zchunk;
+};
+
+constexpr int kTile1D = 128;   // threads per block of the 1D step kernel
+constexpr int kTileX = 30;     // interior cells per warp row of the 2D/3D kernel
+constexpr int kFinalizeThreads = 256;
+
+// launchers (msh_step.cu)
+template <typename T> cudaError_t launch_step(const StepArgs<T> &a, int ndim, int rows, cudaStream_t s,
+                                              int *nblocks_out);
+template <typename T> int step_blocks(int ndim, int rows, int nx, int ny, int nz, int zchunk);
+template <typename T> size_t step_smem(int ndim, int rows);
+template <typename T> cudaError_t launch_scan(const T *U, size_t N, int nx, int ny, int ndim,
+                                              const double *dx, Partial *part, int nparts,
+                                              cudaStream_t s);
+cudaError_t launch_finalize(Ctrl *ctrl, const Partial *part, int nparts, int mode, cudaStream_t s);
+cudaError_t launch_run_start(Ctrl *ctrl, double t_end, int64_t max_steps, double dt_max, cudaStream_t s);
+template <typename T> cudaError_t launch_convert(T *U, size_t N, int to_primitive, cudaStream_t s);
+
+constexpr int kScanBlocks = 608;  // 4 x 152 SMs
+
+}  // namespace msh

@@ -1,8 +1,9 @@
 """Independent brute-force step for tiny grids (test helper, pins the oracle).
 
 Nothing here uses the oracle's closed forms.  The physical flux is the velocity moment
-of a Gaussian distribution (zero heat flux closure, Sec. 2) computed by Gauss-Hermite
-quadrature; the primitive Jacobian A = (dU/dW)^-1 dF/dW comes from complex-step
+of a Gaussian distribution (zero heat flux closure, Sec. 2), by Gauss-Hermite quadrature
+(``flux_gh``) or Isserlis' theorem (``flux_moments``, pinned to the quadrature); the
+primitive Jacobian A = (dU/dW)^-1 dF/dW comes from complex-step
 differentiation of that flux; wave speeds are numerical eigenvalues of A; eigenvectors
 are numerical null spaces of (A - lambda I).  Inside a degenerate eigenspace the basis
 is fixed by the axis-aligned convention of the paper's printed eigenvectors (eq
@@ -68,6 +69,23 @@ def flux_gh(W, d):
     return F
 
 
+def flux_moments(W, d):
+    """Same moments from Isserlis' theorem for a Gaussian with mean u, covariance S = P/rho:
+    <v_i v_j v_k> = u_i u_j u_k + u_i S_jk + u_j S_ik + u_k S_ij.  Polynomial in W, so it
+    also holds for the non-positive-definite face states a Hancock predictor can produce
+    (the quadrature needs a Cholesky factor)."""
+    W = np.asarray(W)
+    rho, u = W[0], W[1:4]
+    S = [[W[tidx(i, j)] / rho for j in range(3)] for i in range(3)]
+    F = np.zeros(10, dtype=W.dtype)
+    F[0] = rho * u[d]
+    for i in range(3):
+        F[1 + i] = rho * (u[i] * u[d] + S[i][d])
+        for j in range(i, 3):
+            F[tidx(i, j)] = rho * (u[i] * u[j] * u[d] + u[i] * S[j][d] + u[j] * S[i][d] + u[d] * S[i][j])
+    return F
+
+
 def jac_cs(fun, W, h=1e-30):
     """Complex-step Jacobian d fun / d W (exact to rounding)."""
     W = np.asarray(W, dtype=np.float64)
@@ -81,7 +99,7 @@ def jac_cs(fun, W, h=1e-30):
 
 def prim_jacobian(W, d):
     dU = jac_cs(cons, W)
-    dF = jac_cs(lambda w: flux_gh(w, d), W)
+    dF = jac_cs(lambda w: flux_moments(w, d), W)
     return np.linalg.solve(dU, dF)
 
 
@@ -160,7 +178,7 @@ def hll(WL, WR, d):
     aL, bL = speeds(WL, d)
     aR, bR = speeds(WR, d)
     SL, SR = min(aL, aR), max(bL, bR)
-    FL, FR = flux_gh(WL, d).real, flux_gh(WR, d).real
+    FL, FR = flux_moments(WL, d).real, flux_moments(WR, d).real
     if SL >= 0:
         return FL
     if SR <= 0:

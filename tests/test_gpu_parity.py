@@ -1,0 +1,257 @@
+"""GPU (libmsh through the C ABI) against the FP64 oracle on the same seeded inputs.
+
+FP64: relative L_inf <= 1e-10 per field after the full run.  FP32: relative L1 <= 2e-4 on
+density and <= 5e-4 on each P_ij against the FP64 oracle run from the FP32-rounded
+initial state.  Sizes are chosen so that the oracle finishes in seconds while the grids
+still span several thread-block tiles (30 x (rows-2) cells in x-y, z chunks) and end in
+ragged tiles."""
+import numpy as np
+import pytest
+
+from tests.parity import assert_fp32, assert_fp64
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def msh():
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1210_5246_gb300 import msh as m
+    m.load()
+    return m
+
+
+@pytest.fixture(scope="module")
+def I():
+    from paper_1210_5246_gb300 import inputs
+    return inputs
+
+
+def _oracle_grid(oracle, p):
+    return oracle.Grid(p.n, p.lo, p.hi, p.bc, p.cfl)
+
+
+def _run_both(msh, oracle, p, precision, steps=None, t_end=np.inf, rows=None, zchunk=None):
+    g = msh.Grid.from_problem(p, precision)
+    if rows is not None:
+        g.set_tiling(rows, zchunk or 1)
+    W = p.W.astype(np.float32) if precision == msh.FP32 else p.W
+    g.set_state(W, msh.PRIMITIVE)
+    max_steps = steps if steps is not None else (1 << 62)
+    ns, t = g.run(t_end, max_steps)
+    U = g.get_state().astype(np.float64)
+    Wg = g.get_state(msh.PRIMITIVE).astype(np.float64)
+    og = _oracle_grid(oracle, p)
+    U0 = oracle.prim_to_cons(W.astype(np.float64))
+    Uo, no, to, rc, _ = oracle.run(og, U0, t_end, max_steps=max_steps, phi=p.phi)
+    g.close()
+    return U, Wg, Uo, oracle.cons_to_prim(Uo), (ns, t), (no, to, rc)
+
+
+# ------------------------------------------------------------------- 1D Sod
+def test_sod_fp64_full_run(msh, oracle, I):
+    """256 cells, outflow, CFL 0.8 to t = 0.2 (the 1D shock-tube workload)."""
+    p = I.sod(256)
+    U, Wg, Uo, Wo, (ns, t), (no, to, rc) = _run_both(msh, oracle, p, msh.FP64, t_end=p.t_end)
+    assert rc == 0 and ns == no and t == to == p.t_end
+    assert_fp64(U, Uo, what="sod fp64")
+
+
+def test_sod_fp32_full_run(msh, oracle, I):
+    p = I.sod(256)
+    U, Wg, Uo, Wo, (ns, t), (no, to, rc) = _run_both(msh, oracle, p, msh.FP32, t_end=p.t_end)
+    assert t == p.t_end
+    assert_fp32(Wg, Wo, what="sod fp32")
+
+
+def test_paper_sod_200_cells(msh, oracle, I):
+    """The paper's own shock tube: 200 cells to t = 0.1 (Sec. 4.1)."""
+    p = I.sod(200, t_end=0.1)
+    U, Wg, Uo, Wo, (ns, t), (no, to, rc) = _run_both(msh, oracle, p, msh.FP64, t_end=p.t_end)
+    assert ns == no
+    assert_fp64(U, Uo, what="sod200")
+
+
+@pytest.mark.parametrize("n,bc", [(2, (2, 2)), (5, (0, 0)), (127, (1, 2)), (300, (2, 1)), (1001, (0, 0))])
+def test_1d_ragged_and_boundaries(msh, oracle, n, bc):
+    rng = np.random.default_rng(n)
+    W = np.zeros((10, 1, 1, n))
+    W[0] = np.exp(rng.uniform(-0.5, 0.5, n))
+    W[1:4] = rng.uniform(-0.3, 0.3, (3, 1, 1, n))
+    W[4], W[7], W[9] = 0.8, 0.6, 0.5
+    W[5] = rng.uniform(-0.1, 0.1, n)
+    W[6] = rng.uniform(-0.1, 0.1, n)
+    W[8] = rng.uniform(-0.05, 0.05, n)
+    g = msh.Grid((n,), (0.0,), (1.0,), (bc,), 0.7, msh.FP64)
+    g.set_state(W, msh.PRIMITIVE)
+    g.run(max_steps=7)
+    og = oracle.Grid((n,), (0.0,), (1.0,), (bc,), 0.7)
+    Uo = oracle.run(og, oracle.prim_to_cons(W), np.inf, max_steps=7)[0]
+    assert_fp64(g.get_state(), Uo, what=f"1d n={n}")
+    g.close()
+
+
+# ---------------------------------------------------------------- 2D blast
+@pytest.mark.parametrize("rows", [4, 8, 16])
+def test_blast_fp64(msh, oracle, I, rows):
+    """Anisotropic-stress blast, 97 x 97 periodic (4 ragged x tiles), 20 steps."""
+    p = I.blast(n=97, nsteps=20)
+    U, Wg, Uo, Wo, (ns, t), (no, to, rc) = _run_both(msh, oracle, p, msh.FP64, steps=20, rows=rows)
+    assert ns == no == 20 and abs(t - to) <= 1e-14 * to
+    assert_fp64(U, Uo, what=f"blast fp64 rows={rows}")
+
+
+def test_blast_fp32(msh, oracle, I):
+    p = I.blast(n=97, nsteps=20)
+    U, Wg, Uo, Wo, _, _ = _run_both(msh, oracle, p, msh.FP32, steps=20)
+    assert_fp32(Wg, Wo, what="blast fp32")
+
+
+@pytest.mark.parametrize("shape,bc", [((31, 7), ((1, 1), (2, 2))), ((64, 33), ((2, 1), (0, 0))),
+                                      ((2, 2), ((0, 0), (0, 0))), ((61, 45), ((2, 2), (1, 2)))])
+def test_2d_shapes_and_boundaries(msh, oracle, shape, bc):
+    nx, ny = shape
+    rng = np.random.default_rng(nx * 100 + ny)
+    W = np.zeros((10, 1, ny, nx))
+    W[0] = np.exp(rng.uniform(-0.5, 0.5, (1, ny, nx)))
+    W[1:4] = rng.uniform(-0.3, 0.3, (3, 1, ny, nx))
+    W[4], W[7], W[9] = 0.8, 0.7, 0.5
+    W[5] = rng.uniform(-0.1, 0.1, (1, ny, nx))
+    W[6] = rng.uniform(-0.1, 0.1, (1, ny, nx))
+    W[8] = rng.uniform(-0.1, 0.1, (1, ny, nx))
+    g = msh.Grid(shape, (0.0, 0.0), (1.0, 2.0), bc, 0.5, msh.FP64)
+    g.set_state(W, msh.PRIMITIVE)
+    g.run(max_steps=5)
+    og = oracle.Grid(shape, (0.0, 0.0), (1.0, 2.0), bc, 0.5)
+    Uo = oracle.run(og, oracle.prim_to_cons(W), np.inf, max_steps=5)[0]
+    assert_fp64(g.get_state(), Uo, what=f"2d {shape} {bc}")
+    g.close()
+
+
+# ---------------------------------------------------------------- 3D box
+@pytest.mark.parametrize("rows,zchunk", [(8, 32), (4, 5), (16, 7)])
+def test_turb_fp64(msh, oracle, I, rows, zchunk):
+    """Turbulent periodic box, 24^3, 6 steps, several tile shapes and z chunks."""
+    p = I.turb(n=24, nsteps=6)
+    U, Wg, Uo, Wo, (ns, t), (no, to, rc) = _run_both(msh, oracle, p, msh.FP64, steps=6, rows=rows,
+                                                     zchunk=zchunk)
+    assert ns == no == 6
+    assert_fp64(U, Uo, what=f"turb fp64 {rows}/{zchunk}")
+
+
+def test_turb_fp32(msh, oracle, I):
+    p = I.turb(n=32, nsteps=10)
+    U, Wg, Uo, Wo, _, _ = _run_both(msh, oracle, p, msh.FP32, steps=10)
+    assert_fp32(Wg, Wo, what="turb fp32")
+
+
+@pytest.mark.parametrize("shape,bc", [((33, 17, 9), ((1, 2), (2, 1), (0, 0))),
+                                      ((5, 40, 3), ((2, 2), (0, 0), (1, 1))),
+                                      ((2, 2, 2), ((0, 0), (0, 0), (0, 0)))])
+def test_3d_shapes_and_boundaries(msh, oracle, shape, bc):
+    nx, ny, nz = shape
+    rng = np.random.default_rng(nx + 7 * ny + 31 * nz)
+    W = np.zeros((10, nz, ny, nx))
+    W[0] = np.exp(rng.uniform(-0.5, 0.5, (nz, ny, nx)))
+    W[1:4] = rng.uniform(-0.3, 0.3, (3, nz, ny, nx))
+    W[4], W[7], W[9] = 0.8, 0.7, 0.6
+    for k in (5, 6, 8):
+        W[k] = rng.uniform(-0.1, 0.1, (nz, ny, nx))
+    g = msh.Grid(shape, (0, 0, 0), (1, 1.5, 0.5), bc, 0.5, msh.FP64)
+    g.set_tiling(8, 4)
+    g.set_state(W, msh.PRIMITIVE)
+    g.run(max_steps=4)
+    og = oracle.Grid(shape, (0, 0, 0), (1, 1.5, 0.5), bc, 0.5)
+    Uo = oracle.run(og, oracle.prim_to_cons(W), np.inf, max_steps=4)[0]
+    assert_fp64(g.get_state(), Uo, what=f"3d {shape}")
+    g.close()
+
+
+# ------------------------------------------------------------------ 2D disc
+def test_disc_gravity_fp64(msh, oracle, I):
+    """Stellar disc in the fixed logarithmic potential, 64^2, 20 steps (gravity source)."""
+    p = I.disc(n=64, nsteps=20)
+    U, Wg, Uo, Wo, (ns, t), (no, to, rc) = _run_both(msh, oracle, p, msh.FP64, steps=20)
+    assert ns == no == 20
+    assert_fp64(U, Uo, what="disc fp64")
+
+
+def test_disc_gravity_fp32(msh, oracle, I):
+    p = I.disc(n=64, nsteps=20)
+    U, Wg, Uo, Wo, _, _ = _run_both(msh, oracle, p, msh.FP32, steps=20)
+    assert_fp32(Wg, Wo, what="disc fp32")
+
+
+# ------------------------------------------------------- step / time control
+def test_step_dt_and_clip(msh, oracle, I):
+    p = I.sod(64, t_end=0.05)
+    g = msh.Grid.from_problem(p, msh.FP64)
+    g.set_state(p.W, msh.PRIMITIVE)
+    og = _oracle_grid(oracle, p)
+    U0 = oracle.prim_to_cons(p.W)
+    dt_cfl = oracle.cfl_dt(og, U0)
+    dt = g.step()
+    assert abs(dt - dt_cfl) <= 1e-15 * dt_cfl
+    dt2 = g.step(dt_max=1e-4)
+    assert dt2 == 1e-4
+    steps, t = g.run(t_end=0.05)
+    assert t == 0.05
+    assert g.time() == (0.05, steps + 2)
+    g.close()
+
+
+def test_dt_history_matches_oracle(msh, oracle, I):
+    p = I.sod(128, t_end=0.1)
+    g = msh.Grid.from_problem(p, msh.FP64)
+    g.set_state(p.W, msh.PRIMITIVE)
+    g.set_recording(1000)
+    ns, t = g.run(p.t_end)
+    h = g.dt_history()
+    og = _oracle_grid(oracle, p)
+    _, no, _, _, ho = oracle.run(og, oracle.prim_to_cons(p.W), p.t_end, record=True)
+    assert len(h) == ns == no
+    np.testing.assert_allclose(h, ho, rtol=1e-12)
+    assert abs(h.sum() - t) < 1e-14
+    g.close()
+
+
+def test_conservation_periodic_gpu(msh, I):
+    """All ten totals conserved to round-off on a periodic grid (FP64 diagnostics)."""
+    p = I.turb(n=40, nsteps=10)
+    g = msh.Grid.from_problem(p, msh.FP64)
+    g.set_state(p.W, msh.PRIMITIVE)
+    t0, ok0, _ = g.diagnostics()
+    g.run(max_steps=10)
+    t1, ok1, bad = g.diagnostics()
+    assert ok0 and ok1 and bad == -1
+    scale = np.array([t0[0]] * 4 + [abs(t0[4]) + abs(t0[7]) + abs(t0[9])] * 6)
+    assert np.all(np.abs(t1 - t0) / scale < 1e-13), (t1 - t0) / scale
+    g.close()
+
+
+def test_rejects_non_realizable_state(msh):
+    g = msh.Grid((8,), (0.0,), (1.0,), ((1, 1),), 0.5, msh.FP64)
+    W = np.zeros((10, 1, 1, 8))
+    W[0], W[4], W[7], W[9] = 1.0, 1.0, 1.0, 1.0
+    g.set_state(W, msh.PRIMITIVE)
+    bad = W.copy()
+    bad[0, 0, 0, 3] = -1.0
+    with pytest.raises(msh.MshError) as ei:
+        g.set_state(bad, msh.PRIMITIVE)
+    assert ei.value.status == msh.MSH_E_REALIZABILITY and "cell 3" in str(ei.value)
+    np.testing.assert_allclose(g.get_state(msh.PRIMITIVE), W)  # previous state kept
+    g.close()
+
+
+def test_invalid_arguments(msh):
+    with pytest.raises(msh.MshError) as ei:
+        msh.Grid((8, 8), (0, 0), (1, 1), ((0, 1), (0, 0)), 0.5)
+    assert ei.value.status == msh.MSH_E_INVALID_ARG
+    with pytest.raises(msh.MshError):
+        msh.Grid((8,), (0,), (1,), ((1, 1),), 1.5)
+    g = msh.Grid((8,), (0,), (1,), ((1, 1),), 0.5)
+    with pytest.raises(msh.MshError) as ei:
+        g.step()
+    assert ei.value.status == msh.MSH_E_STATE
+    g.close()
