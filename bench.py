@@ -1,0 +1,327 @@
+#!/usr/bin/env python3
+"""Benchmark of the BME Godunov step on one or more GB300s.
+
+Workload: the 3D turbulent periodic box, 256^3 cells, FP32 arithmetic (lognormal density,
+k^-2 Gaussian random velocity, random SPD stress per cell; seeded synthetic input).  One
+bench step = one full step of the hot path (boundary mapping, reconstruction, HLL fluxes
+in x/y/z, unsplit update, CFL reduction, FP64 totals, realizability) on the whole grid.
+
+Metric: cell-updates/s (whole job; N ranks each advance their own replica of the box, so
+scaling is weak).  `value` is device time with the state resident in HBM (the 671 MB FP32
+state is larger than the 129 MB L2, so no flush is needed between steps); `e2e` is the
+same metric through the public C ABI with host buffers (pinned upload of the state, one
+step, download of the result, every step).  `roofline` relates the step kernel's
+algorithmic bytes (read U^n + write U^{n+1}: 80 B per cell in FP32) per launch to its
+CUDA-event duration and the measured HBM bandwidth.
+
+--impl reference times the FP64 CPU oracle on the same workload (a 128^3 periodic crop
+per step, so the run stays within a few minutes).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N_BOX = 256
+BYTES_PER_CELL = {"f32": 80, "f64": 160}   # read U^n + write U^{n+1}, 10 fields each
+PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "step_tile_fp32_turb256.md")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    ap.add_argument("--n", type=int, default=N_BOX)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--fp32-only", action="store_true", help="skip the FP64 measurement")
+    ap.add_argument("--tiling", default=None, help="rows,zchunk instead of autotuning (e.g. 8,32)")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1210_5246_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        if f.endswith((".cu", ".cuh", ".h")):
+            h.update(open(os.path.join(csrc, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def measured_traffic(n_cells):
+    """DRAM bytes per launch of the step kernel from the committed ncu summary, scaled to
+    the workload's cell count; None if absent or taken on different kernel sources."""
+    try:
+        txt = open(PROFILE_SUMMARY).read()
+    except OSError:
+        return None
+    rec = None
+    for line in txt.splitlines():
+        if line.startswith("traffic_record:"):
+            rec = json.loads(line.split(":", 1)[1])
+    if not rec or rec.get("source_hash") != kernel_source_hash():
+        return None
+    return rec["dram_bytes_per_cell"] * n_cells
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(index), f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "50"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return None
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+        self.f.flush()
+        rows = []
+        for line in open(self.f.name):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 9 and parts[1].replace(".", "").isdigit():
+                rows.append(parts)
+        os.unlink(self.f.name)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": float(rows[0][2]),
+                "reasons": reasons, "samples": len(rows)}
+
+
+def peaks():
+    try:
+        p = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        return float(p["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def make_workload(n):
+    from paper_1210_5246_gb300 import inputs
+    return inputs.turb(n=n, nsteps=50)
+
+
+# ----------------------------------------------------------------------- GPU arm
+def run_gpu(args):
+    import torch
+    import torch.distributed as dist
+    rank, world, local = dist_env()
+    if world > 1:
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        dist.init_process_group(backend)
+    torch.cuda.set_device(local)
+    import __graft_entry__
+    if rank == 0 or world == 1:
+        __graft_entry__.build()
+    if world > 1:
+        dist.barrier()
+        __graft_entry__.build()
+    from paper_1210_5246_gb300 import msh
+
+    p = make_workload(args.n)
+    ncells = int(np.prod(p.n))
+    stream = torch.cuda.current_stream()
+    W32 = torch.from_numpy(p.W.astype(np.float32)).cuda()
+    W64 = None if args.fp32_only else torch.from_numpy(p.W).cuda()
+
+    def timed(precision, Wdev, steps, warmup, profile):
+        g = msh.Grid.from_problem(p, precision, stream=stream.cuda_stream)
+        g.set_state(Wdev, msh.PRIMITIVE)
+        if args.tiling:
+            g.set_tiling(*[int(v) for v in args.tiling.split(",")])
+        else:
+            g.autotune()
+        g.run(max_steps=warmup)
+        g.set_state(Wdev, msh.PRIMITIVE)          # time the workload's first K steps
+        g.set_time(0.0, 0)
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        sampler = ClockSampler(local) if profile else None
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ns, _ = g.run(max_steps=steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        clocks = sampler.stop() if sampler else None
+        ms = e0.elapsed_time(e1)
+        kern_ms, kern_n = None, None
+        if profile:
+            # the same K steps again, launched eagerly with CUDA events around each step kernel
+            g.set_state(Wdev, msh.PRIMITIVE)
+            g.set_time(0.0, 0)
+            g.set_profiling(True)
+            g.run(max_steps=steps)
+            torch.cuda.synchronize()
+            kern_ms, kern_n = g.profile()
+        tiling = g.tiling()
+        _, ok, _ = g.diagnostics()
+        g.close()
+        assert ns == steps and ok
+        return ms, kern_ms, kern_n, clocks, tiling
+
+    ms32, kms, kn, clocks, tiling = timed(msh.FP32, W32, args.steps, args.warmup, True)
+    steps64 = max(1, min(args.steps, 20))
+    if args.fp32_only:
+        ms64, tiling64 = float("nan"), None
+    else:
+        ms64, _, _, _, tiling64 = timed(msh.FP64, W64, steps64, args.warmup, False)
+
+    # end to end through the C ABI with host buffers: upload, one step, download
+    e2e = None
+    if not args.no_e2e:
+        host_in = torch.from_numpy(p.W.astype(np.float32)).pin_memory()
+        host_out = torch.empty_like(host_in).pin_memory()
+        g = msh.Grid.from_problem(p, msh.FP32, stream=stream.cuda_stream)
+        g.set_tiling(*tiling)
+        k_e2e = max(3, min(args.steps, 10))
+
+        def one():
+            g.set_state(host_in.numpy(), msh.PRIMITIVE)
+            g.run(max_steps=1)
+            g.get_state(msh.PRIMITIVE, out=host_out.numpy())
+        for _ in range(2):
+            one()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(k_e2e):
+            one()
+        torch.cuda.synchronize()
+        dt_e2e = time.perf_counter() - t0
+        g.close()
+        nbytes = ncells * 10 * 4
+        e2e = {"value": ncells * k_e2e / dt_e2e, "unit": "cell-updates/s",
+               "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes}
+
+    # max over ranks of the timed region
+    if world > 1:
+        t = torch.tensor([ms32], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms32 = float(t.item())
+    value = world * ncells * args.steps / (ms32 * 1e-3)
+    value64 = ncells * steps64 / (ms64 * 1e-3) if not args.fp32_only else None
+
+    hbm, peak_kind = peaks()
+    avg_kernel_s = (kms / kn) * 1e-3
+    achieved = BYTES_PER_CELL["f32"] * ncells / avg_kernel_s / 1e9
+    traffic = measured_traffic(ncells)
+    graph_launches = math.ceil(args.steps / 16) * 16 * 2 + 1  # (step, finalize) pairs + run start
+    out = {
+        "metric": "cell-updates/s", "value": value, "unit": "cell-updates/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms32 / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded k^-2 Gaussian random fields)",
+        "config": {"workload": f"turbulent periodic box {args.n}^3, FP32, CFL 0.5, steps 1..{args.steps}",
+                   "cells": ncells, "parallelism": f"replicas x{world}",
+                   "l2": "state (671 MB) larger than L2; no flush", "tiling": list(tiling)},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                     "frac": achieved / hbm, "traffic": traffic,
+                     "kernel": "step_tile_kernel<float,3>", "peak_source": peak_kind,
+                     "kernel_ms": kms / kn, "bytes_per_cell": BYTES_PER_CELL["f32"]},
+        "fp64": None if args.fp32_only else {
+            "value": value64, "unit": "cell-updates/s", "steps": steps64, "ms_per_step": ms64 / steps64,
+            "tiling": list(tiling64), "hbm_frac": BYTES_PER_CELL["f64"] * value64 / 1e9 / hbm},
+        "gpu_launches": graph_launches,
+        "clocks": clocks,
+        "e2e": e2e,
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(p)
+    if world > 1:
+        dist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(out))
+
+
+def cpu_baseline(p):
+    """The oracle as it stands: one full-size FP64 step of the same workload."""
+    from oracle import oracle
+    og = oracle.Grid(p.n, p.lo, p.hi, p.bc, p.cfl)
+    U = oracle.prim_to_cons(p.W)
+    dt = oracle.cfl_dt(og, U)
+    t0 = time.perf_counter()
+    oracle.step(og, U, dt)
+    el = time.perf_counter() - t0
+    ncells = int(np.prod(p.n))
+    return {"value": ncells / el, "unit": "cell-updates/s", "cores": oracle.num_threads(),
+            "kind": "oracle", "sample": f"one FP64 step of the full {p.n[0]}^3 box ({el:.1f} s)"}
+
+
+# ------------------------------------------------------------------ reference arm
+def run_reference(args):
+    rank, world, local = dist_env()
+    if rank != 0:
+        return
+    from oracle import oracle
+    from paper_1210_5246_gb300 import inputs
+    oracle.build()
+    p = make_workload(args.n)
+    m = min(128, args.n)
+    Wc = np.ascontiguousarray(p.W[:, :m, :m, :m])
+    og = oracle.Grid((m, m, m), (0, 0, 0), (m / args.n,) * 3, ((0, 0),) * 3, p.cfl)
+    U = oracle.prim_to_cons(Wc)
+    for _ in range(args.warmup):
+        U = oracle.step(og, U, oracle.cfl_dt(og, U))
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        U = oracle.step(og, U, oracle.cfl_dt(og, U))
+    el = time.perf_counter() - t0
+    v = m ** 3 * args.steps / el
+    cores = oracle.num_threads()
+    print(json.dumps({
+        "impl": "reference", "metric": "cell-updates/s", "value": v, "unit": "cell-updates/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": el * 1e3 / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded k^-2 Gaussian random fields)",
+        "config": {"workload": f"turbulent periodic box {args.n}^3 (each step: FP64 oracle step of a "
+                               f"{m}^3 periodic crop)", "cells": m ** 3},
+        "cpu_baseline": {"value": v, "unit": "cell-updates/s", "cores": cores, "kind": "oracle",
+                         "sample": f"{m}^3 crop, {args.steps} steps"},
+        "e2e": {"value": v, "unit": "cell-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+if __name__ == "__main__":
+    a = parse()
+    if a.impl == "reference":
+        run_reference(a)
+    else:
+        run_gpu(a)

@@ -164,9 +164,9 @@ msh_status msh_get_tiling(msh_grid *g, int32_t *rows, int32_t *zchunk);
 msh_status msh_autotune(msh_grid *g, int32_t *rows, int32_t *zchunk);
 
 /*
- * Kernel timing: with profiling on, msh_run brackets every step-kernel launch with CUDA
- * events on the grid's stream (recorded inside the run's CUDA graph) and accumulates
- * their elapsed times.  msh_get_profile returns the summed step-kernel time in ms and
+ * Kernel timing: with profiling on, msh_run launches the same kernels without the CUDA
+ * graph and brackets every step-kernel launch with CUDA events on the grid's stream,
+ * accumulating their elapsed times.  msh_get_profile returns the summed step-kernel time in ms and
  * the number of timed launches since profiling was switched on.
  */
 msh_status msh_set_profiling(msh_grid *g, int32_t on);

@@ -233,6 +233,48 @@ __device__ __forceinline__ void hll(const T (&wl)[NV], const T (&wr)[NV], T (&F)
   }
 }
 
+// ---------------------------------------------------------- accumulators
+// Per-thread running sums of the conserved totals.  FP64 states add in FP64; FP32 states
+// add exactly in float-float (Knuth's TwoSum keeps the rounding error of every add), so
+// the FP64 totals need no FP64 arithmetic per cell (FP64 throughput is a small fraction
+// of FP32 on this GPU).
+template <typename T> struct Acc {
+  double v[NV];
+  __device__ __forceinline__ void zero() {
+#pragma unroll
+    for (int k = 0; k < NV; k++) v[k] = 0.0;
+  }
+  __device__ __forceinline__ void add(const T (&x)[NV]) {
+#pragma unroll
+    for (int k = 0; k < NV; k++) v[k] += x[k];
+  }
+  __device__ __forceinline__ void get(double (&o)[NV]) const {
+#pragma unroll
+    for (int k = 0; k < NV; k++) o[k] = v[k];
+  }
+};
+template <> struct Acc<float> {
+  float hi[NV], lo[NV];
+  __device__ __forceinline__ void zero() {
+#pragma unroll
+    for (int k = 0; k < NV; k++) { hi[k] = 0.f; lo[k] = 0.f; }
+  }
+  __device__ __forceinline__ void add(const float (&x)[NV]) {
+#pragma unroll
+    for (int k = 0; k < NV; k++) {
+      const float s = __fadd_rn(hi[k], x[k]);
+      const float bb = __fsub_rn(s, hi[k]);
+      const float err = __fadd_rn(__fsub_rn(hi[k], __fsub_rn(s, bb)), __fsub_rn(x[k], bb));
+      hi[k] = s;
+      lo[k] = __fadd_rn(lo[k], err);
+    }
+  }
+  __device__ __forceinline__ void get(double (&o)[NV]) const {
+#pragma unroll
+    for (int k = 0; k < NV; k++) o[k] = (double)hi[k] + (double)lo[k];
+  }
+};
+
 // ------------------------------------------------------------- boundaries
 enum { BC_PERIODIC = 0, BC_OUTFLOW = 1, BC_REFLECT = 2 };
 

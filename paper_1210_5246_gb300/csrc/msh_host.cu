@@ -21,6 +21,13 @@ namespace {
 
 thread_local std::string g_err;
 
+// Reset the per-thread error text and any stale non-sticky CUDA error, so that the
+// cudaGetLastError() after a kernel launch reports only that launch.
+void begin() {
+  g_err.clear();
+  (void)cudaGetLastError();
+}
+
 msh_status fail(msh_status s, const char *fmt, ...) {
   char buf[512];
   va_list ap;
@@ -56,7 +63,8 @@ struct msh_grid {
   cudaStream_t stream = nullptr;
   bool own_stream = false;
   void *U[2] = {nullptr, nullptr};
-  double *phi = nullptr;
+  double *phi = nullptr;  // potential as given (with ghost layer)
+  void *acc = nullptr;    // -grad Phi, [3][N] in the state precision
   Ctrl *ctrl = nullptr;   // device
   Ctrl *hctrl = nullptr;  // pinned host mirror
   Partial *part = nullptr;
@@ -66,7 +74,7 @@ struct msh_grid {
   bool has_state = false;
   int rows = 8, zchunk = 32;
   cudaGraphExec_t graph = nullptr;
-  // profiling: events around every step-kernel launch inside the graph
+  // profiling: eager launches with events around every step-kernel launch
   bool profiling = false;
   std::vector<cudaEvent_t> ev;
   double prof_ms = 0.0;
@@ -80,7 +88,7 @@ template <typename T> StepArgs<T> make_args(msh_grid *g) {
   StepArgs<T> a;
   a.U[0] = (T *)g->U[0];
   a.U[1] = (T *)g->U[1];
-  a.phi = g->phi;
+  a.acc = (const T *)g->acc;
   a.ctrl = g->ctrl;
   a.part = g->part;
   a.nx = (int)g->n[0];
@@ -159,6 +167,8 @@ void collect_profile(msh_grid *g, int slots) {
     if (cudaEventElapsedTime(&ms, g->ev[2 * i], g->ev[2 * i + 1]) == cudaSuccess) {
       g->prof_ms += ms;
       g->prof_launches += 1;
+    } else {
+      (void)cudaGetLastError();
     }
   }
 }
@@ -193,7 +203,7 @@ int32_t msh_version(void) { return 10000; }
 
 msh_status msh_init_grid(msh_grid **out, int32_t ndim, const int64_t n[3], const double lo[3],
                          const double hi[3], const int32_t bc[6], int32_t precision, double cfl, void *stream) {
-  g_err.clear();
+  begin();
   if (!out || !n || !lo || !hi || !bc) return fail(MSH_E_INVALID_ARG, "null argument");
   if (ndim < 1 || ndim > 3) return fail(MSH_E_INVALID_ARG, "ndim must be 1, 2 or 3 (got %d)", ndim);
   if (precision != MSH_FP32 && precision != MSH_FP64) return fail(MSH_E_INVALID_ARG, "bad precision %d", precision);
@@ -276,6 +286,7 @@ msh_status msh_destroy(msh_grid *g) {
   for (int b = 0; b < 2; b++)
     if (g->U[b]) cudaFree(g->U[b]);
   if (g->phi) cudaFree(g->phi);
+  if (g->acc) cudaFree(g->acc);
   if (g->ctrl) cudaFree(g->ctrl);
   if (g->hctrl) cudaFreeHost(g->hctrl);
   if (g->part) cudaFree(g->part);
@@ -286,7 +297,7 @@ msh_status msh_destroy(msh_grid *g) {
 }
 
 msh_status msh_set_state(msh_grid *g, const void *U, int32_t where, int32_t kind) {
-  g_err.clear();
+  begin();
   if (!g || !U) return fail(MSH_E_INVALID_ARG, "null argument");
   if (where != MSH_HOST && where != MSH_DEVICE) return fail(MSH_E_INVALID_ARG, "bad where");
   if (kind != MSH_CONSERVED && kind != MSH_PRIMITIVE) return fail(MSH_E_INVALID_ARG, "bad kind");
@@ -314,7 +325,7 @@ msh_status msh_set_state(msh_grid *g, const void *U, int32_t where, int32_t kind
 }
 
 msh_status msh_get_state(msh_grid *g, void *U, int32_t where, int32_t kind) {
-  g_err.clear();
+  begin();
   if (!g || !U) return fail(MSH_E_INVALID_ARG, "null argument");
   if (where != MSH_HOST && where != MSH_DEVICE) return fail(MSH_E_INVALID_ARG, "bad where");
   if (kind != MSH_CONSERVED && kind != MSH_PRIMITIVE) return fail(MSH_E_INVALID_ARG, "bad kind");
@@ -336,7 +347,7 @@ msh_status msh_get_state(msh_grid *g, void *U, int32_t where, int32_t kind) {
 }
 
 msh_status msh_set_time(msh_grid *g, double t, int64_t step) {
-  g_err.clear();
+  begin();
   if (!g) return fail(MSH_E_INVALID_ARG, "null grid");
   if (step < 0 || !std::isfinite(t)) return fail(MSH_E_INVALID_ARG, "bad time or step");
   if (((step ^ g->hctrl->step) & 1) && g->has_state) {
@@ -353,7 +364,7 @@ msh_status msh_set_time(msh_grid *g, double t, int64_t step) {
 }
 
 msh_status msh_get_time(msh_grid *g, double *t, int64_t *step) {
-  g_err.clear();
+  begin();
   if (!g) return fail(MSH_E_INVALID_ARG, "null grid");
   if (t) *t = g->hctrl->t;
   if (step) *step = g->hctrl->step;
@@ -361,50 +372,58 @@ msh_status msh_get_time(msh_grid *g, double *t, int64_t *step) {
 }
 
 msh_status msh_set_potential(msh_grid *g, const double *phi, int32_t where) {
-  g_err.clear();
+  begin();
   if (!g) return fail(MSH_E_INVALID_ARG, "null grid");
   drop_graph(g);
   if (!phi) {
     if (g->phi) cudaFree(g->phi);
+    if (g->acc) cudaFree(g->acc);
     g->phi = nullptr;
+    g->acc = nullptr;
     return MSH_OK;
   }
   if (where != MSH_HOST && where != MSH_DEVICE) return fail(MSH_E_INVALID_ARG, "bad where");
   size_t cnt = 1;
   for (int d = 0; d < 3; d++) cnt *= (size_t)(g->n[d] + (d < g->ndim ? 2 : 0));
   if (!g->phi) CUDA_TRY(cudaMalloc(&g->phi, cnt * sizeof(double)));
+  if (!g->acc) CUDA_TRY(cudaMalloc(&g->acc, 3 * g->N * g->esize));
   CUDA_TRY(cudaMemcpyAsync(g->phi, phi, cnt * sizeof(double),
                            where == MSH_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, g->stream));
+  cudaError_t e = g->prec == MSH_FP32
+                      ? launch_gravity_field<float>(g->phi, (float *)g->acc, g->ndim, (int)g->n[0], (int)g->n[1],
+                                                    (int)g->n[2], g->dx, g->stream)
+                      : launch_gravity_field<double>(g->phi, (double *)g->acc, g->ndim, (int)g->n[0], (int)g->n[1],
+                                                     (int)g->n[2], g->dx, g->stream);
+  if (e != cudaSuccess) return fail(MSH_E_CUDA, "gravity field: %s", cudaGetErrorString(e));
   CUDA_TRY(cudaStreamSynchronize(g->stream));
   return MSH_OK;
 }
 
 msh_status msh_step(msh_grid *g, double dt_max, double *dt_taken) {
-  g_err.clear();
+  begin();
   if (!g) return fail(MSH_E_INVALID_ARG, "null grid");
   if (!g->has_state) return fail(MSH_E_STATE, "msh_step before msh_set_state");
   if (!(dt_max > 0.0)) return fail(MSH_E_INVALID_ARG, "dt_max must be > 0");
   msh_status st = ensure_partials(g, blocks_for(g, g->rows, g->zchunk));
   if (st) return st;
-  const double t0 = g->hctrl->t;
   cudaError_t e = launch_run_start(g->ctrl, INFINITY, 1, dt_max, g->stream);
   if (e != cudaSuccess) return fail(MSH_E_CUDA, "run start: %s", cudaGetErrorString(e));
   st = launch_one_step(g, -1);
   if (st) return st;
   st = read_ctrl(g);
   if (st) return st;
-  if (dt_taken) *dt_taken = g->hctrl->t - t0;
+  if (dt_taken) *dt_taken = g->hctrl->dt_last;
   if (g->hctrl->status == MSH_E_REALIZABILITY)
     return fail(MSH_E_REALIZABILITY, "step produced a non-realizable cell %lld", (long long)g->hctrl->first_bad);
   return MSH_OK;
 }
 
 msh_status msh_run(msh_grid *g, double t_end, int64_t max_steps, int64_t *steps, double *t_out) {
-  g_err.clear();
+  begin();
   if (!g) return fail(MSH_E_INVALID_ARG, "null grid");
   if (!g->has_state) return fail(MSH_E_STATE, "msh_run before msh_set_state");
   if (max_steps < 0 || std::isnan(t_end)) return fail(MSH_E_INVALID_ARG, "bad t_end or max_steps");
-  msh_status st = build_graph(g);
+  msh_status st = g->profiling ? ensure_partials(g, blocks_for(g, g->rows, g->zchunk)) : build_graph(g);
   if (st) return st;
   const int64_t s0 = g->hctrl->step;
   cudaError_t e = launch_run_start(g->ctrl, t_end, max_steps, INFINITY, g->stream);
@@ -412,7 +431,15 @@ msh_status msh_run(msh_grid *g, double t_end, int64_t max_steps, int64_t *steps,
   const int64_t max_launch = max_steps / kGraphSteps + 2;
   for (int64_t it = 0;; it++) {
     if (it > max_launch) return fail(MSH_E_STATE, "run did not terminate (device control inconsistent)");
-    CUDA_TRY(cudaGraphLaunch(g->graph, g->stream));
+    if (g->profiling) {
+      // profiled runs launch the same kernels eagerly, bracketed by events
+      for (int i = 0; i < kGraphSteps; i++) {
+        st = launch_one_step(g, i);
+        if (st) return st;
+      }
+    } else {
+      CUDA_TRY(cudaGraphLaunch(g->graph, g->stream));
+    }
     st = read_ctrl(g);
     if (st) return st;
     collect_profile(g, kGraphSteps);
@@ -427,7 +454,7 @@ msh_status msh_run(msh_grid *g, double t_end, int64_t max_steps, int64_t *steps,
 }
 
 msh_status msh_diagnostics(msh_grid *g, double totals[10], int32_t *realizable, int64_t *first_bad) {
-  g_err.clear();
+  begin();
   if (!g) return fail(MSH_E_INVALID_ARG, "null grid");
   if (!g->has_state) return fail(MSH_E_STATE, "no state set");
   if (totals) memcpy(totals, g->hctrl->totals, sizeof(double) * 10);
@@ -437,7 +464,7 @@ msh_status msh_diagnostics(msh_grid *g, double totals[10], int32_t *realizable, 
 }
 
 msh_status msh_set_recording(msh_grid *g, int64_t capacity) {
-  g_err.clear();
+  begin();
   if (!g || capacity < 0) return fail(MSH_E_INVALID_ARG, "bad argument");
   CUDA_TRY(cudaStreamSynchronize(g->stream));
   if (g->hist) cudaFree(g->hist);
@@ -456,7 +483,7 @@ msh_status msh_set_recording(msh_grid *g, int64_t capacity) {
 }
 
 msh_status msh_get_dt_history(msh_grid *g, double *dts, int64_t capacity, int64_t *count) {
-  g_err.clear();
+  begin();
   if (!g || capacity < 0 || (capacity > 0 && !dts)) return fail(MSH_E_INVALID_ARG, "bad argument");
   int64_t n = g->hist ? g->hctrl->step - g->hctrl->hist_base : 0;
   if (n > g->hist_cap) n = g->hist_cap;
@@ -471,7 +498,7 @@ msh_status msh_get_dt_history(msh_grid *g, double *dts, int64_t capacity, int64_
 }
 
 msh_status msh_set_tiling(msh_grid *g, int32_t rows, int32_t zchunk) {
-  g_err.clear();
+  begin();
   if (!g) return fail(MSH_E_INVALID_ARG, "null grid");
   if (rows != 4 && rows != 8 && rows != 16) return fail(MSH_E_INVALID_ARG, "rows must be 4, 8 or 16");
   if (zchunk < 1) return fail(MSH_E_INVALID_ARG, "zchunk must be >= 1");
@@ -486,7 +513,7 @@ msh_status msh_set_tiling(msh_grid *g, int32_t rows, int32_t zchunk) {
 }
 
 msh_status msh_get_tiling(msh_grid *g, int32_t *rows, int32_t *zchunk) {
-  g_err.clear();
+  begin();
   if (!g) return fail(MSH_E_INVALID_ARG, "null grid");
   if (rows) *rows = g->rows;
   if (zchunk) *zchunk = g->zchunk;
@@ -496,7 +523,7 @@ msh_status msh_get_tiling(msh_grid *g, int32_t *rows, int32_t *zchunk) {
 // Time each tile shape on copies of the current state (the state, time and step
 // counter are restored afterwards) and keep the fastest.
 msh_status msh_autotune(msh_grid *g, int32_t *rows_out, int32_t *zchunk_out) {
-  g_err.clear();
+  begin();
   if (!g) return fail(MSH_E_INVALID_ARG, "null grid");
   if (!g->has_state) return fail(MSH_E_STATE, "msh_autotune before msh_set_state");
   if (g->ndim == 1) {
@@ -567,7 +594,7 @@ msh_status msh_autotune(msh_grid *g, int32_t *rows_out, int32_t *zchunk_out) {
 }
 
 msh_status msh_set_profiling(msh_grid *g, int32_t on) {
-  g_err.clear();
+  begin();
   if (!g) return fail(MSH_E_INVALID_ARG, "null grid");
   if (on && g->ev.empty()) {
     g->ev.resize(2 * kGraphSteps);
@@ -581,7 +608,7 @@ msh_status msh_set_profiling(msh_grid *g, int32_t on) {
 }
 
 msh_status msh_get_profile(msh_grid *g, double *step_kernel_ms, int64_t *launches) {
-  g_err.clear();
+  begin();
   if (!g) return fail(MSH_E_INVALID_ARG, "null grid");
   if (step_kernel_ms) *step_kernel_ms = g->prof_ms;
   if (launches) *launches = g->prof_launches;

@@ -9,7 +9,7 @@ namespace msh {
 // parity from here; the finalize kernel writes the next dt, so a run needs no host
 // round trip per step.
 struct Ctrl {
-  double t, t_next, t_end, dt, dt_max, dt_cfl, cfl;
+  double t, t_next, t_end, dt, dt_max, dt_cfl, cfl, dt_last;
   int64_t step, max_step, first_bad, hist_cap, hist_base;
   int32_t done, status, realizable, pad;
   double totals[10];
@@ -25,7 +25,7 @@ struct Partial {
 
 template <typename T> struct StepArgs {
   T *U[2];              // ping-pong state buffers, source = U[step & 1]
-  const double *phi;    // potential with one ghost layer, or nullptr
+  const T *acc;         // gravitational acceleration -grad Phi, [3][N], or nullptr
   Ctrl *ctrl;
   Partial *part;
   int nx, ny, nz;
@@ -49,6 +49,8 @@ template <typename T> cudaError_t launch_scan(const T *U, size_t N, int nx, int 
 cudaError_t launch_finalize(Ctrl *ctrl, const Partial *part, int nparts, int mode, cudaStream_t s);
 cudaError_t launch_run_start(Ctrl *ctrl, double t_end, int64_t max_steps, double dt_max, cudaStream_t s);
 template <typename T> cudaError_t launch_convert(T *U, size_t N, int to_primitive, cudaStream_t s);
+template <typename T> cudaError_t launch_gravity_field(const double *phi, T *acc, int ndim, int nx, int ny, int nz,
+                                                       const double *dx, cudaStream_t s);
 
 constexpr int kScanBlocks = 608;  // 4 x 152 SMs
 

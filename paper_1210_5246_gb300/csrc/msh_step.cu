@@ -60,49 +60,59 @@ __device__ __forceinline__ void block_partial(double (&diag)[NV], double smax, l
   }
 }
 
+// Sum over active dims of (|u_d| + sqrt(3 P_dd / rho)) / dx_d: the CFL signal-speed sum.
+template <typename T, int NDIM>
+__device__ __forceinline__ T speed_sum(const T (&W)[NV], T idx, T idy, T idz) {
+  const T ir3 = T(3) / W[0];
+  T s = (fabs(W[1]) + sqrt(W[4] * ir3)) * idx;
+  if (NDIM > 1) s += (fabs(W[2]) + sqrt(W[7] * ir3)) * idy;
+  if (NDIM > 2) s += (fabs(W[3]) + sqrt(W[9] * ir3)) * idz;
+  return s;
+}
+
 // Per-cell tail of the step: gravity source, store, next-dt speed, realizability, totals.
 template <typename T, int NDIM>
 __device__ __forceinline__ void finish_cell(const StepArgs<T> &a, const T *__restrict__ Us,
-                                            T *__restrict__ Ud, size_t N, size_t c, int x, int y, int z,
-                                            const T (&acc)[NV], T dt, double (&diag)[NV],
-                                            double &smax, long long &bad) {
+                                            T *__restrict__ Ud, size_t N, size_t c,
+                                            const T (&acc)[NV], T dt, T idx, T idy, T idz, Acc<T> &diag,
+                                            T &smax, long long &bad) {
   T Un[NV];
 #pragma unroll
   for (int k = 0; k < NV; k++) Un[k] = Us[k * N + c] + dt * acc[k];
-  if (a.phi != nullptr) {
-    // a = -grad Phi (central differences), m += dt rho a, E += dt (mbar a^T + a mbar^T)
-    const int gxp = 1, gyp = NDIM > 1 ? 1 : 0, gzp = NDIM > 2 ? 1 : 0;
-    const long px = a.nx + 2 * gxp, py = a.ny + 2 * gyp;
-    const long ctr = ((long)(z + gzp) * py + (y + gyp)) * px + (x + gxp);
-    T acc_g[3] = {T(0), T(0), T(0)};
-    acc_g[0] = (T)(-(a.phi[ctr + 1] - a.phi[ctr - 1]) / (2.0 * a.dx[0]));
-    if (NDIM > 1) acc_g[1] = (T)(-(a.phi[ctr + px] - a.phi[ctr - px]) / (2.0 * a.dx[1]));
-    if (NDIM > 2) acc_g[2] = (T)(-(a.phi[ctr + px * py] - a.phi[ctr - px * py]) / (2.0 * a.dx[2]));
+  if (a.acc != nullptr) {
+    // a = -grad Phi: m += dt rho a, E += dt (mbar a^T + a mbar^T), mbar = (m* + m^{n+1})/2
+    T g[3] = {T(0), T(0), T(0)};
+    g[0] = a.acc[c];
+    if (NDIM > 1) g[1] = a.acc[N + c];
+    if (NDIM > 2) g[2] = a.acc[2 * N + c];
     T mb[3];
 #pragma unroll
     for (int i = 0; i < 3; i++) {
-      const T mn = Un[1 + i] + dt * Un[0] * acc_g[i];
+      const T mn = Un[1 + i] + dt * Un[0] * g[i];
       mb[i] = T(0.5) * (Un[1 + i] + mn);
       Un[1 + i] = mn;
     }
-    Un[4] += dt * T(2) * mb[0] * acc_g[0];
-    Un[5] += dt * (mb[0] * acc_g[1] + acc_g[0] * mb[1]);
-    Un[6] += dt * (mb[0] * acc_g[2] + acc_g[0] * mb[2]);
-    Un[7] += dt * T(2) * mb[1] * acc_g[1];
-    Un[8] += dt * (mb[1] * acc_g[2] + acc_g[1] * mb[2]);
-    Un[9] += dt * T(2) * mb[2] * acc_g[2];
+    Un[4] += dt * T(2) * mb[0] * g[0];
+    Un[5] += dt * (mb[0] * g[1] + g[0] * mb[1]);
+    Un[6] += dt * (mb[0] * g[2] + g[0] * mb[2]);
+    Un[7] += dt * T(2) * mb[1] * g[1];
+    Un[8] += dt * (mb[1] * g[2] + g[1] * mb[2]);
+    Un[9] += dt * T(2) * mb[2] * g[2];
   }
 #pragma unroll
   for (int k = 0; k < NV; k++) Ud[k * N + c] = Un[k];
   T W[NV];
   cons_to_prim(Un, W);
   if (!realizable(W)) bad = min(bad, (long long)c);
-  double s = (fabs((double)W[1]) + sqrt(3.0 * (double)W[4] / (double)W[0])) / a.dx[0];
-  if (NDIM > 1) s += (fabs((double)W[2]) + sqrt(3.0 * (double)W[7] / (double)W[0])) / a.dx[1];
-  if (NDIM > 2) s += (fabs((double)W[3]) + sqrt(3.0 * (double)W[9] / (double)W[0])) / a.dx[2];
-  smax = fmax(smax, s);
-#pragma unroll
-  for (int k = 0; k < NV; k++) diag[k] += (double)Un[k];
+  smax = fmax(smax, speed_sum<T, NDIM>(W, idx, idy, idz));
+  diag.add(Un);
+}
+
+template <typename T, int NT>
+__device__ __forceinline__ void write_partial(const Acc<T> &diag, T smax, long long bad, Partial *out) {
+  double d[NV];
+  diag.get(d);
+  block_partial<NT>(d, (double)smax, bad, out);
 }
 
 // ------------------------------------------------------------------ 1D kernel
@@ -155,19 +165,18 @@ __global__ void __launch_bounds__(kTile1D) step1d_kernel(StepArgs<T> a) {
     for (int k = 0; k < NV; k++) sH[k][t] = F[k];
   }
   __syncthreads();
-  double diag[NV];
-#pragma unroll
-  for (int k = 0; k < NV; k++) diag[k] = 0.0;
-  double smax = 0.0;
+  Acc<T> diag;
+  diag.zero();
+  T smax = T(0);
   long long bad = LLONG_MAX;
   const int gx = x0 - 1 + t;
   if (t >= 1 && t <= B - 2 && gx < nx) {
     T acc[NV];
 #pragma unroll
     for (int k = 0; k < NV; k++) acc[k] = (F[k] - sH[k][t + 1]) * idx;
-    finish_cell<T, 1>(a, Us, Ud, N, (size_t)gx, gx, 0, 0, acc, dt, diag, smax, bad);
+    finish_cell<T, 1>(a, Us, Ud, N, (size_t)gx, acc, dt, idx, T(0), T(0), diag, smax, bad);
   }
-  block_partial<B>(diag, smax, bad, a.part + blockIdx.x);
+  write_partial<T, B>(diag, smax, bad, a.part + blockIdx.x);
 }
 
 // -------------------------------------------------------------- 2D/3D kernel
@@ -280,10 +289,9 @@ __global__ void __launch_bounds__(32 * BY) step_tile_kernel(StepArgs<T> a) {
     }
   };
 
-  double diag[NV];
-#pragma unroll
-  for (int k = 0; k < NV; k++) diag[k] = 0.0;
-  double smax = 0.0;
+  Acc<T> diag;
+  diag.zero();
+  T smax = T(0);
   long long bad = LLONG_MAX;
 
   if (NDIM == 2) {
@@ -293,7 +301,7 @@ __global__ void __launch_bounds__(32 * BY) step_tile_kernel(StepArgs<T> a) {
 #pragma unroll
     for (int k = 0; k < NV; k++) acc[k] = T(0);
     sweep_xy(sW, acc);
-    if (valid) finish_cell<T, NDIM>(a, Us, Ud, N, (size_t)gy * nx + gx, gx, gy, 0, acc, dt, diag, smax, bad);
+    if (valid) finish_cell<T, NDIM>(a, Us, Ud, N, (size_t)gy * nx + gx, acc, dt, idx, idy, idz, diag, smax, bad);
   } else {
     const int z0 = blockIdx.z * a.zchunk;
     const int z1 = min(z0 + a.zchunk, nz);
@@ -347,7 +355,7 @@ __global__ void __launch_bounds__(32 * BY) step_tile_kernel(StepArgs<T> a) {
         }
       }
       if (valid)
-        finish_cell<T, NDIM>(a, Us, Ud, N, ((size_t)z * ny + gy) * nx + gx, gx, gy, z, acc, dt, diag,
+        finish_cell<T, NDIM>(a, Us, Ud, N, ((size_t)z * ny + gy) * nx + gx, acc, dt, idx, idy, idz, diag,
                              smax, bad);
       __syncthreads();
       if (z + 1 < z1) {
@@ -356,20 +364,19 @@ __global__ void __launch_bounds__(32 * BY) step_tile_kernel(StepArgs<T> a) {
       }
     }
   }
-  block_partial<32 * BY>(diag, smax, bad,
-                         a.part + ((size_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x);
+  write_partial<T, 32 * BY>(diag, smax, bad,
+                            a.part + ((size_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x);
 }
 
 // ----------------------------------------------------------------- scan kernel
 // Partials (totals, max signal speed sum, first non-realizable cell) of a state.
-template <typename T>
-__global__ void __launch_bounds__(256) scan_kernel(const T *__restrict__ U, size_t N, int nx, int ny,
-                                                   int ndim, double dx0, double dx1, double dx2,
+template <typename T, int NDIM>
+__global__ void __launch_bounds__(256) scan_kernel(const T *__restrict__ U, size_t N, T idx, T idy, T idz,
                                                    Partial *part) {
   double diag[NV];
 #pragma unroll
   for (int k = 0; k < NV; k++) diag[k] = 0.0;
-  double smax = 0.0;
+  T smax = T(0);
   long long bad = LLONG_MAX;
   for (size_t c = (size_t)blockIdx.x * blockDim.x + threadIdx.x; c < N; c += (size_t)gridDim.x * blockDim.x) {
     T Uc[NV], W[NV];
@@ -377,14 +384,28 @@ __global__ void __launch_bounds__(256) scan_kernel(const T *__restrict__ U, size
     for (int k = 0; k < NV; k++) Uc[k] = U[k * N + c];
     cons_to_prim(Uc, W);
     if (!realizable(W)) bad = min(bad, (long long)c);
-    double s = (fabs((double)W[1]) + sqrt(3.0 * (double)W[4] / (double)W[0])) / dx0;
-    if (ndim > 1) s += (fabs((double)W[2]) + sqrt(3.0 * (double)W[7] / (double)W[0])) / dx1;
-    if (ndim > 2) s += (fabs((double)W[3]) + sqrt(3.0 * (double)W[9] / (double)W[0])) / dx2;
-    smax = fmax(smax, s);
+    smax = fmax(smax, speed_sum<T, NDIM>(W, idx, idy, idz));
 #pragma unroll
     for (int k = 0; k < NV; k++) diag[k] += (double)Uc[k];
   }
-  block_partial<256>(diag, smax, bad, part + blockIdx.x);
+  block_partial<256>(diag, (double)smax, bad, part + blockIdx.x);
+}
+
+// Acceleration a = -grad Phi by central differences from the potential with one ghost
+// layer, stored [3][N] in the state's precision.
+template <typename T>
+__global__ void gravity_field_kernel(const double *__restrict__ phi, T *__restrict__ acc, int ndim, int nx,
+                                     int ny, int nz, double dx0, double dx1, double dx2) {
+  const size_t N = (size_t)nx * ny * nz;
+  const int gy = ndim > 1 ? 1 : 0, gz = ndim > 2 ? 1 : 0;
+  const long px = nx + 2, py = ny + 2 * gy;
+  for (size_t c = (size_t)blockIdx.x * blockDim.x + threadIdx.x; c < N; c += (size_t)gridDim.x * blockDim.x) {
+    const long x = (long)(c % nx), y = (long)((c / nx) % ny), z = (long)(c / ((size_t)nx * ny));
+    const long ctr = ((z + gz) * py + (y + gy)) * px + (x + 1);
+    acc[c] = (T)(-(phi[ctr + 1] - phi[ctr - 1]) / (2.0 * dx0));
+    acc[N + c] = ndim > 1 ? (T)(-(phi[ctr + px] - phi[ctr - px]) / (2.0 * dx1)) : T(0);
+    acc[2 * N + c] = ndim > 2 ? (T)(-(phi[ctr + px * py] - phi[ctr - px * py]) / (2.0 * dx2)) : T(0);
+  }
 }
 
 // -------------------------------------------------------- finalize and plan
@@ -446,6 +467,7 @@ __global__ void __launch_bounds__(kFinalizeThreads) finalize_kernel(Ctrl *ctrl, 
   }
   const int64_t hi_ = c->step - c->hist_base;
   if (c->hist != nullptr && hi_ >= 0 && hi_ < c->hist_cap) c->hist[hi_] = c->dt;
+  c->dt_last = c->dt;
   c->t = c->t_next;
   c->step += 1;
   if (!c->realizable) {
@@ -530,7 +552,17 @@ cudaError_t launch_step(const StepArgs<T> &a, int ndim, int rows, cudaStream_t s
 template <typename T>
 cudaError_t launch_scan(const T *U, size_t N, int nx, int ny, int ndim, const double *dx, Partial *part,
                         int nparts, cudaStream_t s) {
-  scan_kernel<T><<<nparts, 256, 0, s>>>(U, N, nx, ny, ndim, dx[0], dx[1], dx[2], part);
+  const T ix = (T)(1.0 / dx[0]), iy = (T)(1.0 / dx[1]), iz = (T)(1.0 / dx[2]);
+  if (ndim == 1) scan_kernel<T, 1><<<nparts, 256, 0, s>>>(U, N, ix, iy, iz, part);
+  else if (ndim == 2) scan_kernel<T, 2><<<nparts, 256, 0, s>>>(U, N, ix, iy, iz, part);
+  else scan_kernel<T, 3><<<nparts, 256, 0, s>>>(U, N, ix, iy, iz, part);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_gravity_field(const double *phi, T *acc, int ndim, int nx, int ny, int nz, const double *dx,
+                                 cudaStream_t s) {
+  gravity_field_kernel<T><<<kScanBlocks, 256, 0, s>>>(phi, acc, ndim, nx, ny, nz, dx[0], dx[1], dx[2]);
   return cudaGetLastError();
 }
 
@@ -556,7 +588,8 @@ template <typename T> cudaError_t launch_convert(T *U, size_t N, int to_primitiv
   template size_t step_smem<T>(int, int);                                                            \
   template cudaError_t launch_scan<T>(const T *, size_t, int, int, int, const double *, Partial *, int, \
                                       cudaStream_t);                                                 \
-  template cudaError_t launch_convert<T>(T *, size_t, int, cudaStream_t);
+  template cudaError_t launch_convert<T>(T *, size_t, int, cudaStream_t);                            \
+  template cudaError_t launch_gravity_field<T>(const double *, T *, int, int, int, int, const double *, cudaStream_t);
 MSH_INST(float)
 MSH_INST(double)
 
