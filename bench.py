@@ -158,9 +158,11 @@ def run_gpu(args):
 
     p = make_workload(args.n)
     ncells = int(np.prod(p.n))
-    stream = torch.cuda.current_stream()
+    # one dedicated stream: the library launches on it and the CUDA events are recorded on it
+    stream = torch.cuda.Stream()
     W32 = torch.from_numpy(p.W.astype(np.float32)).cuda()
     W64 = None if args.fp32_only else torch.from_numpy(p.W).cuda()
+    torch.cuda.synchronize()
 
     def timed(precision, Wdev, steps, warmup, profile):
         g = msh.Grid.from_problem(p, precision, stream=stream.cuda_stream)

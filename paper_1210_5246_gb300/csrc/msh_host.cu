@@ -67,6 +67,8 @@ struct msh_grid {
   void *acc = nullptr;    // -grad Phi, [3][N] in the state precision
   Ctrl *ctrl = nullptr;   // device
   Ctrl *hctrl = nullptr;  // pinned host mirror
+  int32_t *hdone = nullptr;                       // pinned completion flags of two batches
+  cudaEvent_t ev_done[2] = {nullptr, nullptr};
   Partial *part = nullptr;
   int part_cap = 0;
   double *hist = nullptr;
@@ -263,6 +265,12 @@ msh_status msh_init_grid(msh_grid **out, int32_t ndim, const int64_t n[3], const
   if (e != cudaSuccess) return cleanup(fail(MSH_E_NOMEM, "control block: %s", cudaGetErrorString(e)));
   e = cudaMallocHost(&g->hctrl, sizeof(Ctrl));
   if (e != cudaSuccess) return cleanup(fail(MSH_E_NOMEM, "pinned control block: %s", cudaGetErrorString(e)));
+  e = cudaMallocHost(&g->hdone, 2 * sizeof(int32_t));
+  if (e != cudaSuccess) return cleanup(fail(MSH_E_NOMEM, "pinned flags: %s", cudaGetErrorString(e)));
+  for (auto &ev : g->ev_done) {
+    e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+    if (e != cudaSuccess) return cleanup(fail(MSH_E_CUDA, "event create: %s", cudaGetErrorString(e)));
+  }
   memset(g->hctrl, 0, sizeof(Ctrl));
   g->hctrl->cfl = cfl;
   g->hctrl->t_end = INFINITY;
@@ -289,6 +297,9 @@ msh_status msh_destroy(msh_grid *g) {
   if (g->acc) cudaFree(g->acc);
   if (g->ctrl) cudaFree(g->ctrl);
   if (g->hctrl) cudaFreeHost(g->hctrl);
+  if (g->hdone) cudaFreeHost(g->hdone);
+  for (auto &e : g->ev_done)
+    if (e) cudaEventDestroy(e);
   if (g->part) cudaFree(g->part);
   if (g->hist) cudaFree(g->hist);
   if (g->own_stream && g->stream) cudaStreamDestroy(g->stream);
@@ -428,22 +439,48 @@ msh_status msh_run(msh_grid *g, double t_end, int64_t max_steps, int64_t *steps,
   const int64_t s0 = g->hctrl->step;
   cudaError_t e = launch_run_start(g->ctrl, t_end, max_steps, INFINITY, g->stream);
   if (e != cudaSuccess) return fail(MSH_E_CUDA, "run start: %s", cudaGetErrorString(e));
-  const int64_t max_launch = max_steps / kGraphSteps + 2;
-  for (int64_t it = 0;; it++) {
-    if (it > max_launch) return fail(MSH_E_STATE, "run did not terminate (device control inconsistent)");
-    if (g->profiling) {
-      // profiled runs launch the same kernels eagerly, bracketed by events
+  // at most this many batches of kGraphSteps steps can be needed
+  const int64_t need = (max_steps + kGraphSteps - 1) / kGraphSteps;
+  if (g->profiling) {
+    // profiled runs launch the same kernels eagerly, bracketed by events
+    for (int64_t it = 0;; it++) {
+      if (it > need) return fail(MSH_E_STATE, "run did not terminate (device control inconsistent)");
       for (int i = 0; i < kGraphSteps; i++) {
         st = launch_one_step(g, i);
         if (st) return st;
       }
-    } else {
-      CUDA_TRY(cudaGraphLaunch(g->graph, g->stream));
+      st = read_ctrl(g);
+      if (st) return st;
+      collect_profile(g, kGraphSteps);
+      if (g->hctrl->done) break;
+    }
+  } else if (max_steps < kGraphSteps) {
+    // short runs: exactly max_steps launch pairs, no speculative batch
+    for (int64_t i = 0; i < max_steps; i++) {
+      st = launch_one_step(g, -1);
+      if (st) return st;
     }
     st = read_ctrl(g);
     if (st) return st;
-    collect_profile(g, kGraphSteps);
-    if (g->hctrl->done) break;
+  } else {
+    // Two graph batches in flight: launch batch it, then wait for the completion flag of
+    // batch it-1, so the GPU never idles while the host polls.  Batches launched after
+    // the run finished return immediately on the device.
+    for (int64_t it = 0;; it++) {
+      if (it > need + 1) return fail(MSH_E_STATE, "run did not terminate (device control inconsistent)");
+      if (it < need) {
+        CUDA_TRY(cudaGraphLaunch(g->graph, g->stream));
+        CUDA_TRY(cudaMemcpyAsync(&g->hdone[it & 1], &g->ctrl->done, sizeof(int32_t), cudaMemcpyDeviceToHost,
+                                 g->stream));
+        CUDA_TRY(cudaEventRecord(g->ev_done[it & 1], g->stream));
+      }
+      if (it >= 1) {
+        CUDA_TRY(cudaEventSynchronize(g->ev_done[(it - 1) & 1]));
+        if (g->hdone[(it - 1) & 1] || it >= need) break;
+      }
+    }
+    st = read_ctrl(g);
+    if (st) return st;
   }
   if (steps) *steps = g->hctrl->step - s0;
   if (t_out) *t_out = g->hctrl->t;
