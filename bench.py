@@ -191,9 +191,13 @@ def run_gpu(args):
             g.set_state(Wdev, msh.PRIMITIVE)
             g.set_time(0.0, 0)
             g.set_profiling(True)
+            e0.record(stream)
             g.run(max_steps=steps)
+            e1.record(stream)
             torch.cuda.synchronize()
-            kern_ms, kern_n = g.profile()
+            kern_ms, fin_ms, kern_n = g.profile()
+            timed.fin_ms = fin_ms / max(kern_n, 1)
+            timed.eager_ms = e0.elapsed_time(e1)
         tiling = g.tiling()
         _, ok, _ = g.diagnostics()
         g.close()
@@ -257,7 +261,8 @@ def run_gpu(args):
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                      "frac": achieved / hbm, "traffic": traffic,
                      "kernel": "step_tile_kernel<float,3>", "peak_source": peak_kind,
-                     "kernel_ms": kms / kn, "bytes_per_cell": BYTES_PER_CELL["f32"]},
+                     "kernel_ms": kms / kn, "bytes_per_cell": BYTES_PER_CELL["f32"],
+                     "eager_ms_per_step": timed.eager_ms / args.steps, "finalize_ms": timed.fin_ms},
         "fp64": None if args.fp32_only else {
             "value": value64, "unit": "cell-updates/s", "steps": steps64, "ms_per_step": ms64 / steps64,
             "tiling": list(tiling64), "hbm_frac": BYTES_PER_CELL["f64"] * value64 / 1e9 / hbm},

@@ -166,11 +166,12 @@ msh_status msh_autotune(msh_grid *g, int32_t *rows, int32_t *zchunk);
 /*
  * Kernel timing: with profiling on, msh_run launches the same kernels without the CUDA
  * graph and brackets every step-kernel launch with CUDA events on the grid's stream,
- * accumulating their elapsed times.  msh_get_profile returns the summed step-kernel time in ms and
- * the number of timed launches since profiling was switched on.
+ * accumulating their elapsed times.  msh_get_profile returns the summed step-kernel time,
+ * the summed time from each step kernel's end to its finalize kernel's end (both in
+ * ms) and the number of timed launches since profiling was switched on.
  */
 msh_status msh_set_profiling(msh_grid *g, int32_t on);
-msh_status msh_get_profile(msh_grid *g, double *step_kernel_ms, int64_t *launches);
+msh_status msh_get_profile(msh_grid *g, double *step_kernel_ms, double *finalize_ms, int64_t *launches);
 
 /*
  * Discrete adjoint (vector-Jacobian product) of `nsteps` forward steps taken from U0

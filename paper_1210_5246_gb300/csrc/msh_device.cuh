@@ -35,6 +35,17 @@ template <> struct Frame<2> {
   }
 };
 
+// ---------------------------------------------------------- fast arithmetic
+// FP32: hardware approximate reciprocal and reciprocal square root (a few ulp, far
+// inside the FP32 tolerances); FP64: IEEE division and square root.
+template <typename T> __device__ __forceinline__ T frcp(T x) { return T(1) / x; }
+template <> __device__ __forceinline__ float frcp<float>(float x) { return __fdividef(1.0f, x); }
+template <typename T> __device__ __forceinline__ T frsqrt(T x) { return T(1) / sqrt(x); }
+template <> __device__ __forceinline__ float frsqrt<float>(float x) { return rsqrtf(x); }
+// sqrt(p / r) for p, r > 0
+template <typename T> __device__ __forceinline__ T sqrt_ratio(T p, T r) { return sqrt(p / r); }
+template <> __device__ __forceinline__ float sqrt_ratio<float>(float p, float r) { return p * rsqrtf(p * r); }
+
 // ---------------------------------------------------------------- conversions
 // E_ij = P_ij + rho u_i u_j (Sec. 2).  The FP32 path recomputes a diagonal dispersion
 // in FP64 when the kinetic part cancels more than 99.9 % of E_ii, i.e. where P_ii/rho
@@ -51,7 +62,7 @@ template <> __device__ __forceinline__ float diag_fix<float>(float P, float E, f
 template <typename T>
 __device__ __forceinline__ void cons_to_prim(const T (&U)[NV], T (&W)[NV]) {
   const T rho = U[0];
-  const T ir = T(1) / rho;
+  const T ir = frcp(rho);
   const T u = U[1] * ir, v = U[2] * ir, w = U[3] * ir;
   W[0] = rho; W[1] = u; W[2] = v; W[3] = w;
   W[4] = diag_fix<T>(U[4] - U[1] * u, U[4], U[1], rho);
@@ -99,13 +110,15 @@ template <typename T> struct Eig {
   __device__ __forceinline__ void init(const T (&w)[NV]) {
     rho = w[0]; u = w[1];
     Pxx = w[4]; Pxy = w[5]; Pxz = w[6]; Pyy = w[7]; Pyz = w[8]; Pzz = w[9];
-    ip = T(1) / Pxx;
-    cs = sqrt(Pxx / rho);
-    cf = sqrt(T(3) * Pxx / rho);
+    ip = frcp(Pxx);
+    const T q = Pxx * frcp(rho);         // P_xx / rho
+    const T rs = frsqrt(q);              // 1 / cs
+    cs = q * rs;
+    cf = T(1.7320508075688772) * cs;
     a = Pxy * ip;
     b = Pxz * ip;
-    icf2 = T(0.5) / cf;
-    ics2 = T(0.5) / cs;
+    icf2 = T(0.28867513459481287) * rs;  // 1 / (2 cf)
+    ics2 = T(0.5) * rs;                  // 1 / (2 cs)
   }
   // characteristic amplitudes c = L d in wave order
   // (f-, sv-, sw-, c_rho, c_yy, c_yz, c_zz, sv+, sw+, f+)
@@ -215,8 +228,8 @@ __device__ __forceinline__ void hll(const T (&wl)[NV], const T (&wr)[NV], T (&F)
   T Ul[NV], Fl[NV], Ur[NV], Fr[NV];
   phys(wl, Ul, Fl);
   phys(wr, Ur, Fr);
-  const T cl = sqrt(T(3) * wl[4] / wl[0]);
-  const T cr = sqrt(T(3) * wr[4] / wr[0]);
+  const T cl = T(1.7320508075688772) * sqrt_ratio(wl[4], wl[0]);
+  const T cr = T(1.7320508075688772) * sqrt_ratio(wr[4], wr[0]);
   const T SL = fmin(wl[1] - cl, wr[1] - cr);
   const T SR = fmax(wl[1] + cl, wr[1] + cr);
   if (SL >= T(0)) {
@@ -226,7 +239,7 @@ __device__ __forceinline__ void hll(const T (&wl)[NV], const T (&wr)[NV], T (&F)
 #pragma unroll
     for (int k = 0; k < NV; k++) F[k] = Fr[k];
   } else {
-    const T inv = T(1) / (SR - SL);
+    const T inv = frcp(SR - SL);
     const T sls = SL * SR;
 #pragma unroll
     for (int k = 0; k < NV; k++) F[k] = (SR * Fl[k] - SL * Fr[k] + sls * (Ur[k] - Ul[k])) * inv;

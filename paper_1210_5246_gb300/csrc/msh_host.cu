@@ -18,15 +18,19 @@
 using namespace msh;
 
 namespace {
-
 thread_local std::string g_err;
+}  // namespace
 
-// Reset the per-thread error text and any stale non-sticky CUDA error, so that the
-// cudaGetLastError() after a kernel launch reports only that launch.
-void begin() {
+void msh::clear_error() {
   g_err.clear();
   (void)cudaGetLastError();
 }
+
+void msh::set_error_text(const char *msg) { g_err = msg; }
+
+namespace {
+
+void begin() { clear_error(); }
 
 msh_status fail(msh_status s, const char *fmt, ...) {
   char buf[512];
@@ -79,7 +83,8 @@ struct msh_grid {
   // profiling: eager launches with events around every step-kernel launch
   bool profiling = false;
   std::vector<cudaEvent_t> ev;
-  double prof_ms = 0.0;
+  double prof_ms = 0.0;      // summed step-kernel time
+  double prof_fin_ms = 0.0;  // summed time from the step kernel's end to the finalize kernel's end
   int64_t prof_launches = 0;
 };
 
@@ -125,13 +130,14 @@ void drop_graph(msh_grid *g) {
 msh_status launch_one_step(msh_grid *g, int ev_slot) {
   int nb = 0;
   cudaError_t e;
-  if (g->profiling && ev_slot >= 0) CUDA_TRY(cudaEventRecord(g->ev[2 * ev_slot], g->stream));
+  if (g->profiling && ev_slot >= 0) CUDA_TRY(cudaEventRecord(g->ev[3 * ev_slot], g->stream));
   if (g->prec == MSH_FP32) e = launch_step<float>(make_args<float>(g), g->ndim, g->rows, g->stream, &nb);
   else e = launch_step<double>(make_args<double>(g), g->ndim, g->rows, g->stream, &nb);
   if (e != cudaSuccess) return fail(MSH_E_CUDA, "step kernel launch: %s", cudaGetErrorString(e));
-  if (g->profiling && ev_slot >= 0) CUDA_TRY(cudaEventRecord(g->ev[2 * ev_slot + 1], g->stream));
+  if (g->profiling && ev_slot >= 0) CUDA_TRY(cudaEventRecord(g->ev[3 * ev_slot + 1], g->stream));
   e = launch_finalize(g->ctrl, g->part, nb, 0, g->stream);
   if (e != cudaSuccess) return fail(MSH_E_CUDA, "finalize launch: %s", cudaGetErrorString(e));
+  if (g->profiling && ev_slot >= 0) CUDA_TRY(cudaEventRecord(g->ev[3 * ev_slot + 2], g->stream));
   return MSH_OK;
 }
 
@@ -166,8 +172,11 @@ void collect_profile(msh_grid *g, int slots) {
   if (!g->profiling) return;
   for (int i = 0; i < slots; i++) {
     float ms = 0.f;
-    if (cudaEventElapsedTime(&ms, g->ev[2 * i], g->ev[2 * i + 1]) == cudaSuccess) {
+    float ms2 = 0.f;
+    if (cudaEventElapsedTime(&ms, g->ev[3 * i], g->ev[3 * i + 1]) == cudaSuccess &&
+        cudaEventElapsedTime(&ms2, g->ev[3 * i + 1], g->ev[3 * i + 2]) == cudaSuccess) {
       g->prof_ms += ms;
+      g->prof_fin_ms += ms2;
       g->prof_launches += 1;
     } else {
       (void)cudaGetLastError();
@@ -445,13 +454,15 @@ msh_status msh_run(msh_grid *g, double t_end, int64_t max_steps, int64_t *steps,
     // profiled runs launch the same kernels eagerly, bracketed by events
     for (int64_t it = 0;; it++) {
       if (it > need) return fail(MSH_E_STATE, "run did not terminate (device control inconsistent)");
+      const int64_t before = g->hctrl->step;
       for (int i = 0; i < kGraphSteps; i++) {
         st = launch_one_step(g, i);
         if (st) return st;
       }
       st = read_ctrl(g);
       if (st) return st;
-      collect_profile(g, kGraphSteps);
+      // only the launches that took a step count (the tail after completion returns at once)
+      collect_profile(g, (int)(g->hctrl->step - before));
       if (g->hctrl->done) break;
     }
   } else if (max_steps < kGraphSteps) {
@@ -634,20 +645,22 @@ msh_status msh_set_profiling(msh_grid *g, int32_t on) {
   begin();
   if (!g) return fail(MSH_E_INVALID_ARG, "null grid");
   if (on && g->ev.empty()) {
-    g->ev.resize(2 * kGraphSteps);
+    g->ev.resize(3 * kGraphSteps);
     for (auto &e : g->ev) CUDA_TRY(cudaEventCreate(&e));
   }
   if ((bool)on != g->profiling) drop_graph(g);
   g->profiling = on != 0;
   g->prof_ms = 0.0;
+  g->prof_fin_ms = 0.0;
   g->prof_launches = 0;
   return MSH_OK;
 }
 
-msh_status msh_get_profile(msh_grid *g, double *step_kernel_ms, int64_t *launches) {
+msh_status msh_get_profile(msh_grid *g, double *step_kernel_ms, double *finalize_ms, int64_t *launches) {
   begin();
   if (!g) return fail(MSH_E_INVALID_ARG, "null grid");
   if (step_kernel_ms) *step_kernel_ms = g->prof_ms;
+  if (finalize_ms) *finalize_ms = g->prof_fin_ms;
   if (launches) *launches = g->prof_launches;
   return MSH_OK;
 }

@@ -54,4 +54,10 @@ template <typename T> cudaError_t launch_gravity_field(const double *phi, T *acc
 
 constexpr int kScanBlocks = 608;  // 4 x 152 SMs
 
+// Thread-local error text behind msh_last_error(), shared by every translation unit.
+// clear_error() also resets a stale non-sticky CUDA error so that the cudaGetLastError()
+// after a launch reports only that launch.
+void clear_error();
+void set_error_text(const char *msg);
+
 }  // namespace msh

@@ -63,10 +63,11 @@ __device__ __forceinline__ void block_partial(double (&diag)[NV], double smax, l
 // Sum over active dims of (|u_d| + sqrt(3 P_dd / rho)) / dx_d: the CFL signal-speed sum.
 template <typename T, int NDIM>
 __device__ __forceinline__ T speed_sum(const T (&W)[NV], T idx, T idy, T idz) {
-  const T ir3 = T(3) / W[0];
-  T s = (fabs(W[1]) + sqrt(W[4] * ir3)) * idx;
-  if (NDIM > 1) s += (fabs(W[2]) + sqrt(W[7] * ir3)) * idy;
-  if (NDIM > 2) s += (fabs(W[3]) + sqrt(W[9] * ir3)) * idz;
+  const T r3 = T(3) * frcp(W[0]);
+  T s = (fabs(W[1]) + sqrt_ratio(W[4], W[0]) * T(1.7320508075688772)) * idx;
+  if (NDIM > 1) s += (fabs(W[2]) + sqrt_ratio(W[7], W[0]) * T(1.7320508075688772)) * idy;
+  if (NDIM > 2) s += (fabs(W[3]) + sqrt_ratio(W[9], W[0]) * T(1.7320508075688772)) * idz;
+  (void)r3;
   return s;
 }
 
@@ -187,7 +188,7 @@ __device__ __forceinline__ void gather(const T *__restrict__ pl, int sy, int sx,
 }
 
 template <typename T, int NDIM, int BY>
-__global__ void __launch_bounds__(32 * BY) step_tile_kernel(StepArgs<T> a) {
+__global__ void __launch_bounds__(32 * BY, (BY <= 8 ? 2 : 1)) step_tile_kernel(StepArgs<T> a) {
   constexpr int SX = 34, SY = BY + 2;
   constexpr int NPL = (NDIM == 3) ? 3 : 1;
   constexpr int PL = NV * SY * SX;

@@ -58,7 +58,7 @@ SIGNATURES = {
     "msh_get_tiling": [_vp, _P(_i32), _P(_i32)],
     "msh_autotune": [_vp, _P(_i32), _P(_i32)],
     "msh_set_profiling": [_vp, _i32],
-    "msh_get_profile": [_vp, _P(_dbl), _P(_i64)],
+    "msh_get_profile": [_vp, _P(_dbl), _P(_dbl), _P(_i64)],
     "msh_adjoint_run": [_vp, _vp, _i64, _P(_dbl), _i32, _vp, _vp, _i32, _i32],
     "msh_batch_init": [_P(_vp), _i32, _P(_i32), _P(_dbl), _P(_dbl), _P(_dbl), _i32, _dbl, _vp],
     "msh_batch_reset": [_vp],
@@ -261,10 +261,12 @@ class Grid:
         _check(load().msh_set_profiling(self.h, int(bool(on))))
 
     def profile(self):
+        """(summed step-kernel ms, summed finalize ms, timed launches) since profiling began."""
         ms = C.c_double(0.0)
+        fin = C.c_double(0.0)
         n = C.c_int64(0)
-        _check(load().msh_get_profile(self.h, C.byref(ms), C.byref(n)))
-        return ms.value, n.value
+        _check(load().msh_get_profile(self.h, C.byref(ms), C.byref(fin), C.byref(n)))
+        return ms.value, fin.value, n.value
 
     # -- adjoint --------------------------------------------------------------
     def adjoint_run(self, U0, dt_sched, dL_dUN, K=50, kind=CONSERVED, out=None):

@@ -1,0 +1,138 @@
+"""Batched 1D Riemann tubes (one persistent launch) against the FP64 oracle, tube by tube."""
+import numpy as np
+import pytest
+
+from tests.parity import assert_fp32, assert_fp64
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def msh():
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1210_5246_gb300 import msh as m
+    m.load()
+    return m
+
+
+def _random_tubes(lengths, seed):
+    from paper_1210_5246_gb300 import inputs
+    t = inputs.tubes(ntubes=len(lengths), seed=seed)
+    t.length = np.asarray(lengths, dtype=np.int32)
+    return t
+
+
+def _oracle_tube(oracle, tubes, k, dtype=np.float64):
+    n = int(tubes.length[k])
+    W = tubes.initial_tube(k).astype(dtype).astype(np.float64)
+    g = oracle.Grid((n,), (0.0,), (1.0,), ((1, 1),), tubes.cfl)
+    U, steps, t, rc, _ = oracle.run(g, oracle.prim_to_cons(W), tubes.t_end)
+    return U.reshape(10, n), steps, t, rc
+
+
+LENGTHS = [4, 5, 17, 64, 127, 128, 129, 255, 256, 257, 300, 513, 1025, 2048]
+
+
+def test_batch_fp64_matches_oracle(msh, oracle):
+    tubes = _random_tubes(LENGTHS, seed=41)
+    b = msh.Batch(tubes.length, tubes.WL, tubes.WR, tubes.t_end, tubes.cfl, msh.FP64)
+    b.run(threads=256)
+    U = b.get_state()
+    steps, t, cu = b.info()
+    for k in range(len(LENGTHS)):
+        Uo, so, to, rc = _oracle_tube(oracle, tubes, k)
+        assert rc == 0 and steps[k] == so and t[k] == to == tubes.t_end
+        assert_fp64(b.tube(U, k), Uo, what=f"tube {k} (len {LENGTHS[k]})")
+    assert cu == int((steps * tubes.length).sum())
+    b.close()
+
+
+def test_batch_fp32_matches_oracle(msh, oracle):
+    tubes = _random_tubes(LENGTHS, seed=42)
+    b = msh.Batch(tubes.length, tubes.WL, tubes.WR, tubes.t_end, tubes.cfl, msh.FP32)
+    b.run(threads=128)
+    W = b.get_state(msh.PRIMITIVE).astype(np.float64)
+    for k in range(len(LENGTHS)):
+        Uo, _, _, _ = _oracle_tube(oracle, tubes, k, np.float32)
+        assert_fp32(b.tube(W, k), oracle.cons_to_prim(Uo), what=f"tube {k}")
+    b.close()
+
+
+def test_block_sizes_and_autotune_agree_bitwise(msh):
+    tubes = _random_tubes([37, 400, 1000, 129, 2048, 6], seed=43)
+    out = []
+    for nt in (128, 256, 512, 0):
+        b = msh.Batch(tubes.length, tubes.WL, tubes.WR, tubes.t_end, tubes.cfl, msh.FP32)
+        b.run(threads=nt)
+        out.append(b.get_state())
+        b.close()
+    for o in out[1:]:
+        np.testing.assert_array_equal(o, out[0])
+
+
+def test_per_tube_launches_match_batch(msh):
+    tubes = _random_tubes([64, 300, 129, 1000], seed=44)
+    b1 = msh.Batch(tubes.length, tubes.WL, tubes.WR, tubes.t_end, tubes.cfl, msh.FP64)
+    b1.run()
+    b2 = msh.Batch(tubes.length, tubes.WL, tubes.WR, tubes.t_end, tubes.cfl, msh.FP64)
+    b2.run_per_tube()
+    s1, t1, _ = b1.info()
+    s2, t2, _ = b2.info()
+    np.testing.assert_array_equal(s1, s2)
+    np.testing.assert_array_equal(t1, t2)
+    assert_fp64(b2.get_state(), b1.get_state(), tol=1e-12, what="per-tube vs batch")
+    b1.close()
+    b2.close()
+
+
+def test_reset_reproduces_run(msh):
+    tubes = _random_tubes([100, 200], seed=45)
+    b = msh.Batch(tubes.length, tubes.WL, tubes.WR, tubes.t_end, tubes.cfl, msh.FP32)
+    b.run(threads=256)
+    a = b.get_state()
+    b.reset()
+    b.run(threads=256)
+    np.testing.assert_array_equal(b.get_state(), a)
+    b.close()
+
+
+def test_step_cap_reports_timeout(msh):
+    tubes = _random_tubes([200], seed=46)
+    b = msh.Batch(tubes.length, tubes.WL, tubes.WR, tubes.t_end, tubes.cfl, msh.FP32)
+    with pytest.raises(msh.MshError) as ei:
+        b.run(threads=128, max_steps=3)
+    assert ei.value.status == msh.MSH_E_TIMEOUT
+    b.close()
+
+
+def test_rejects_bad_tubes(msh):
+    from paper_1210_5246_gb300 import inputs
+    t = inputs.tubes(ntubes=2, seed=47)
+    with pytest.raises(msh.MshError):
+        msh.Batch(np.array([3, 10]), t.WL, t.WR, t.t_end)
+    bad = t.WL.copy()
+    bad[1, 0] = -1.0
+    with pytest.raises(msh.MshError) as ei:
+        msh.Batch(t.length.clip(4, 100), bad, t.WR, t.t_end)
+    assert ei.value.status == msh.MSH_E_REALIZABILITY
+
+
+def test_full_workload_4096_tubes(msh, oracle):
+    """The full batched workload (4096 tubes, 128..2048 cells, FP32, t = 0.1): every tube
+    reaches t_end; the longest, shortest and a seeded sample match the oracle."""
+    from paper_1210_5246_gb300 import inputs
+    tubes = inputs.tubes()
+    b = msh.Batch(tubes.length, tubes.WL, tubes.WR, tubes.t_end, tubes.cfl, msh.FP32)
+    b.run()
+    steps, t, cu = b.info()
+    assert np.all(t == tubes.t_end)
+    W = b.get_state(msh.PRIMITIVE).astype(np.float64)
+    assert np.all(W[0] > 0) and np.all(W[4] > 0)
+    rng = np.random.default_rng(4)
+    pick = {int(np.argmax(tubes.length)), int(np.argmin(tubes.length))} | set(rng.choice(4096, 4, replace=False).tolist())
+    for k in sorted(pick):
+        Uo, so, to, rc = _oracle_tube(oracle, tubes, k, np.float32)
+        assert abs(int(steps[k]) - so) <= 1
+        assert_fp32(b.tube(W, k), oracle.cons_to_prim(Uo), what=f"tube {k}")
+    b.close()
