@@ -31,6 +31,8 @@
  *   - limiter returns 0 when dw_L * dw_R <= 0;
  *   - face state fallback: if a Hancock face state of a cell has rho <= 0 or
  *     P_nn <= 0, both face states of that cell in that direction revert to W_i;
+ *   - a-posteriori fallback: cells whose second-order update is not realizable get
+ *     first-order face states on all their faces and the step is recomputed;
  *   - CFL: dt = C / max_cells sum_d (|u_d| + sqrt(3 P_dd/rho)) / dx_d;
  *   - gravity: a = -grad(Phi) by central differences, m += dt rho a,
  *     E += dt (mbar a^T + a mbar^T) with mbar the mean of m before/after.
@@ -391,10 +393,24 @@ double og_cfl_dt(const og_grid *G, const double *U)
     return G->cfl / smax;
 }
 
+/* Realizability of one conserved state: rho > 0 and P positive definite. */
+static int cell_realizable(const double *Uc)
+{
+    if (!(Uc[0] > 0.0)) return 0;
+    double W[NV];
+    cons_to_prim(Uc, W);
+    double m1 = W[4];
+    double m2 = W[4] * W[7] - W[5] * W[5];
+    double m3 = W[4] * (W[7] * W[9] - W[8] * W[8]) - W[5] * (W[5] * W[9] - W[8] * W[6]) +
+                W[6] * (W[5] * W[8] - W[7] * W[6]);
+    return m1 > 0.0 && m2 > 0.0 && m3 > 0.0;
+}
+
 /* -------------------------------------------------------------- a1 - a8 --- */
-/* One step of size dt from U to Unew ([NV][nz][ny][nx]).  phi: NULL or the
- * potential with one ghost layer on active dims ([nz+2gz][ny+2gy][nx+2gx]). */
-int og_step(const og_grid *Gr, const double *U, const double *phi, double dt, double *Unew)
+/* One pass of the step.  flag: NULL, or per padded cell 1 where the faces of that
+ * cell take first-order face states (the cell-centred W on both sides). */
+static int step_pass(const og_grid *Gr, const double *U, const double *phi, double dt,
+                     const unsigned char *flag, double *Unew)
 {
     og_pad P = make_pad(Gr);
     int64_t N = P.n[0] * P.n[1] * P.n[2];
@@ -431,6 +447,20 @@ int og_step(const og_grid *Gr, const double *U, const double *phi, double dt, do
                     }
                     og_reconstruct(Wc[0], Wc[1], Wc[2], d, dtdx,
                                    lo + NV * (i + 1), hi + NV * (i + 1));
+                }
+                if (flag) {
+                    /* first-order states on every face that touches a flagged cell */
+                    for (int64_t i = -1; i < nd; i++) {
+                        int64_t ca[3], cb[3];
+                        ca[d] = i; ca[a1] = j1; ca[a2] = j2;
+                        cb[d] = i + 1; cb[a1] = j1; cb[a2] = j2;
+                        int64_t pa = pidx(&P, ca[0], ca[1], ca[2]), pb = pidx(&P, cb[0], cb[1], cb[2]);
+                        if (!(flag[pa] || flag[pb])) continue;
+                        for (int k = 0; k < NV; k++) {
+                            hi[NV * (i + 1) + k] = Wp[k * NP + pa];
+                            lo[NV * (i + 2) + k] = Wp[k * NP + pb];
+                        }
+                    }
                 }
                 /* faces i-1/2 for i = 0 .. nd, flux difference into dU */
                 double Fm[NV], Fp[NV];
@@ -476,6 +506,49 @@ int og_step(const og_grid *Gr, const double *U, const double *phi, double dt, do
     free(G);
     free(Wp);
     free(dU);
+    return 0;
+}
+
+/* One step of size dt from U to Unew ([NV][nz][ny][nx]).  phi: NULL or the
+ * potential with one ghost layer on active dims ([nz+2gz][ny+2gy][nx+2gx]).
+ * A-posteriori fallback (reading; the paper is silent on positivity): if the
+ * second-order update leaves a cell non-realizable, the step is recomputed from U
+ * with first-order face states on every face of every such cell (MOOD-style
+ * detection, Clain, Diot & Loubere 2011); face fluxes stay shared, so the update
+ * stays conservative.  Cells still non-realizable after that are left for the
+ * caller's realizability check.  Returns 0, or 1 on allocation failure. */
+int og_step(const og_grid *Gr, const double *U, const double *phi, double dt, double *Unew)
+{
+    if (step_pass(Gr, U, phi, dt, NULL, Unew)) return 1;
+    og_pad P = make_pad(Gr);
+    int64_t N = P.n[0] * P.n[1] * P.n[2];
+    int64_t NP = P.p[0] * P.p[1] * P.p[2];
+    unsigned char *bad = (unsigned char *)calloc((size_t)N, 1);
+    if (!bad) return 1;
+    int64_t nbad = 0;
+    for (int64_t c = 0; c < N; c++) {
+        double Uc[NV];
+        for (int k = 0; k < NV; k++) Uc[k] = Unew[k * N + c];
+        if (!cell_realizable(Uc)) { bad[c] = 1; nbad++; }
+    }
+    if (nbad > 0) {
+        /* flags on the padded grid: a ghost cell carries the flag of its source cell */
+        unsigned char *flag = (unsigned char *)calloc((size_t)NP, 1);
+        if (!flag) { free(bad); return 1; }
+        for (int64_t z = -P.g[2]; z < P.n[2] + P.g[2]; z++)
+            for (int64_t y = -P.g[1]; y < P.n[1] + P.g[1]; y++)
+                for (int64_t x = -P.g[0]; x < P.n[0] + P.g[0]; x++) {
+                    int64_t c[3] = {x, y, z}, s[3];
+                    int mir;
+                    for (int d = 0; d < 3; d++)
+                        s[d] = ghost_src(c[d], P.n[d], Gr->bc[2 * d], Gr->bc[2 * d + 1], &mir);
+                    flag[pidx(&P, x, y, z)] = bad[(s[2] * P.n[1] + s[1]) * P.n[0] + s[0]];
+                }
+        int rc = step_pass(Gr, U, phi, dt, flag, Unew);
+        free(flag);
+        if (rc) { free(bad); return 1; }
+    }
+    free(bad);
     return 0;
 }
 
@@ -593,4 +666,11 @@ void og_cons_to_prim_arr(const double *U, double *W, int64_t N)
         cons_to_prim(u, w);
         for (int k = 0; k < NV; k++) W[k * N + c] = w[k];
     }
+}
+
+/* The step without the a-posteriori fallback (for tests of the fallback itself). */
+int og_step_second_order_only(const og_grid *Gr, const double *U, const double *phi, double dt,
+                              double *Unew)
+{
+    return step_pass(Gr, U, phi, dt, NULL, Unew);
 }

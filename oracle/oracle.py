@@ -54,6 +54,8 @@ def _load():
             lib.og_step.restype = C.c_int
             lib.og_cfl_dt.argtypes = [gp, dp]
             lib.og_cfl_dt.restype = C.c_double
+            lib.og_step_second_order_only.argtypes = [gp, dp, dp, C.c_double, dp]
+            lib.og_step_second_order_only.restype = C.c_int
             lib.og_run.argtypes = [gp, dp, dp, C.c_double, C.c_double, C.c_int64, C.c_double,
                                    dp, C.POINTER(C.c_int64), dp]
             lib.og_run.restype = C.c_int
@@ -147,6 +149,17 @@ def step(grid: Grid, U, dt, phi=None):
     rc = _load().og_step(C.byref(grid._g), _p(U), None if ph is None else _p(ph), float(dt),
                          _p(out))
     if rc:
+        raise MemoryError("oracle step failed to allocate")
+    return out
+
+
+def step_second_order_only(grid: Grid, U, dt, phi=None):
+    """The step without the a-posteriori first-order fallback."""
+    U = _f64(U).reshape(grid.shape)
+    out = np.empty_like(U)
+    ph = None if phi is None else _f64(phi).reshape(grid.phi_shape())
+    if _load().og_step_second_order_only(C.byref(grid._g), _p(U), None if ph is None else _p(ph),
+                                         float(dt), _p(out)):
         raise MemoryError("oracle step failed to allocate")
     return out
 

@@ -156,6 +156,14 @@ def prim(U):
     return W
 
 
+def realizable(U):
+    if not U[0] > 0:
+        return False
+    W = prim(U)
+    P = np.array([[W[4], W[5], W[6]], [W[5], W[7], W[8]], [W[6], W[8], W[9]]])
+    return bool(P[0, 0] > 0 and np.linalg.det(P[:2, :2]) > 0 and np.linalg.det(P) > 0)
+
+
 def recon(Wm, W0, Wp, d, dtdx):
     A, lam, R = eigen(W0, d)
     Linv = np.linalg.inv(R)
@@ -215,7 +223,22 @@ def _pad_line(Uline, bclo, bchi, d):
 
 
 def step(U, ndim, dx, bc, dt, phi=None):
-    """One unsplit step on a tiny grid.  U: [10][nz][ny][nx]; bc: ((lo,hi),...)."""
+    """One unsplit step on a tiny grid, with the a-posteriori fallback: if the second-order
+    update leaves cells non-realizable, recompute with first-order face states on every
+    face of those cells."""
+    Un = _step_pass(U, ndim, dx, bc, dt, phi, None)
+    nz, ny, nx = Un.shape[1:]
+    bad = np.zeros((nz, ny, nx), dtype=bool)
+    for z in range(nz):
+        for y in range(ny):
+            for x in range(nx):
+                bad[z, y, x] = not realizable(Un[:, z, y, x])
+    if bad.any():
+        Un = _step_pass(U, ndim, dx, bc, dt, phi, bad)
+    return Un
+
+
+def _step_pass(U, ndim, dx, bc, dt, phi, bad):
     U = np.asarray(U, dtype=np.float64)
     dU = np.zeros_like(U)
     nz, ny, nx = U.shape[1:]
@@ -233,7 +256,22 @@ def step(U, ndim, dx, bc, dt, phi=None):
                 P = _pad_line(np.array(line), bc[d][0], bc[d][1], d)
                 Wl = [prim(u) for u in P]
                 n = shape[d]
-                faces = [recon(Wl[k - 1], Wl[k], Wl[k + 1], d, dt / dx[d]) for k in range(1, n + 3)]
+                faces = [list(recon(Wl[k - 1], Wl[k], Wl[k + 1], d, dt / dx[d])) for k in range(1, n + 3)]
+                if bad is not None:
+                    # flag of padded cell k (k = i + 2 for cell i), ghosts take their source cell's
+                    def flag(k):
+                        i = k - 2
+                        if i < 0:
+                            i = i + n if bc[d][0] == 0 else (0 if bc[d][0] == 1 else -1 - i)
+                        elif i >= n:
+                            i = i - n if bc[d][1] == 0 else (n - 1 if bc[d][1] == 1 else 2 * n - 1 - i)
+                        idx2 = list(idx)
+                        idx2[d] = i
+                        return bad[idx2[2], idx2[1], idx2[0]]
+                    for k in range(1, n + 2):  # face between padded cells k and k+1
+                        if flag(k) or flag(k + 1):
+                            faces[k - 1][1] = Wl[k].copy()
+                            faces[k][0] = Wl[k + 1].copy()
                 # faces[k-1] = (lo, hi) of padded cell k, cell i <-> padded i+2
                 for i in range(n):
                     Fm = hll(faces[i][1], faces[i + 1][0], d)

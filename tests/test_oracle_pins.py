@@ -412,3 +412,46 @@ def test_bruteforce_tiny_grids(oracle, case, seed):
         assert np.max(np.abs(A - B) / scale) < 1e-11
         U = A
         dt = oracle.cfl_dt(g, U)
+
+
+# ------------------------------------------------------- a-posteriori fallback
+def _extreme_tiny(seed, n=8):
+    rng = np.random.default_rng(seed)
+    W = np.zeros((10, 1, 1, n))
+    W[0] = np.exp(rng.uniform(np.log(0.05), np.log(20), n))
+    W[1] = rng.uniform(-1.5, 1.5, n)
+    for c in range(n):
+        L = np.tril(rng.normal(0, 0.3, (3, 3)))
+        L[np.diag_indices(3)] = rng.uniform(0.1, 1, 3)
+        P = L @ L.T
+        W[4:, 0, 0, c] = [P[0, 0], P[0, 1], P[0, 2], P[1, 1], P[1, 2], P[2, 2]]
+    return W
+
+
+@pytest.mark.parametrize("seed", [1, 13, 31])
+def test_fallback_restores_realizability_and_matches_bruteforce(oracle, seed):
+    """Extreme 8-cell states where the second-order update leaves a cell non-realizable:
+    the step with the first-order fallback is realizable, conserves every total on the
+    periodic grid, and equals the independent brute-force step with the same fallback."""
+    W = _extreme_tiny(seed)
+    g = oracle.Grid((8,), (0,), (1,), ((0, 0),), 0.8)
+    U = oracle.prim_to_cons(W)
+    dt = oracle.cfl_dt(g, U)
+    assert not oracle.diagnostics(g, oracle.step_second_order_only(g, U, dt))[1]
+    A = oracle.step(g, U, dt)
+    tot0 = oracle.diagnostics(g, U)[0]
+    tot1, ok, _ = oracle.diagnostics(g, A)
+    assert ok
+    assert np.all(np.abs(tot1 - tot0) <= 1e-13 * np.abs(tot0).max())
+    B = BF.step(U, 1, [1 / 8] * 3, ((0, 0),), dt)
+    scale = np.abs(B).reshape(10, -1).max(axis=1)[:, None, None, None] + 1e-300
+    assert np.max(np.abs(A - B) / scale) < 1e-11
+
+
+def test_fallback_inactive_on_smooth_data(oracle):
+    """Where the second-order update is realizable the fallback changes nothing."""
+    p = I.blast(n=24, nsteps=1)
+    g = grid_of(oracle, p)
+    U = oracle.prim_to_cons(p.W)
+    dt = oracle.cfl_dt(g, U)
+    np.testing.assert_array_equal(oracle.step(g, U, dt), oracle.step_second_order_only(g, U, dt))
