@@ -193,13 +193,16 @@ msh_status msh_adjoint_run(msh_grid *g, const void *U0, int64_t nsteps, const do
  * Batched independent 1D Riemann problems ("tubes") on [0, 1] with the interface at 0.5
  * and outflow boundaries, each advanced to its own t_end with its own CFL time step.
  *   ntubes           number of tubes (>= 1)
- *   len[ntubes]      cells per tube, 4 <= len <= 4096 (host)
+ *   len[ntubes]      cells per tube, 4 <= len <= 2048 (FP32) or 1024 (FP64) (host)
  *   WL, WR           [ntubes][10] primitive left / right states (host doubles)
  *   t_end[ntubes]    final times (host doubles, > 0)
  *   precision        MSH_FP32 or MSH_FP64
  * The tubes are stored back to back, [10][sum len] (tube k starts at the prefix sum of
  * len).  msh_batch_run advances all tubes in one persistent launch captured in a CUDA
- * graph; thread blocks take tubes longest first from a device work queue.  threads is
+ * graph; thread blocks take tubes longest first from a device work queue.  Cells whose
+ * second-order update is not realizable trigger the same a-posteriori first-order
+ * fallback as msh_step (the step is recomputed from U^n with first-order faces there);
+ * a tube still non-realizable after it stops with MSH_E_REALIZABILITY.  threads is
  * the block size (0 = autotuned: the fastest of the candidates on a warm-up run).
  * max_steps caps the steps of each tube (MSH_E_TIMEOUT if a tube hits it before t_end).
  */

@@ -65,17 +65,86 @@ template <typename T, int NT> __device__ __forceinline__ T block_max(T v, T *red
   return m;
 }
 
+// One sweep of a tube over all its faces: reconstruction, HLL fluxes and the conservative
+// update, chunk by chunk.  src holds U^n; dst receives U^{n+1} (dst may equal src: each
+// cell is updated after the last chunk that reads it).  With FALLBACK, every face that
+// touches a tagged cell takes first-order states.  Without it, cells whose update is not
+// realizable are tagged in sFl and *s_nbad is set.  Returns the thread's maximum
+// signal-speed sum of the new state.
+template <typename T, int NT, bool FALLBACK>
+__device__ T tube_pass(const T *src, T *dst, unsigned char *sFl, int n, int cap, T nu, T dtdx, T idx, T *sF,
+                       T *sH, T *sHc, int *s_nbad) {
+  const int t = threadIdx.x;
+  T smax = T(0);
+  for (int b = -1; b <= n; b += NT) {
+    const int c = b + t;
+    T lo[NV], hi[NV];
+    if (c <= n) {
+      T wm[NV], w0[NV], wp[NV];
+      load_w(src, cap, c - 1, n, wm);
+      load_w(src, cap, c, n, w0);
+      load_w(src, cap, c + 1, n, wp);
+      reconstruct(wm, w0, wp, nu, lo, hi);
+      if (FALLBACK) {
+        auto f = [&](int i) { return sFl[min(max(i, 0), n - 1)] != 0; };
+        first_order_faces(f(c - 1), f(c), f(c + 1), w0, lo, hi);
+      }
+#pragma unroll
+      for (int v = 0; v < NV; v++) sH[v * NT + t] = hi[v];
+    }
+    __syncthreads();
+    if (c >= 0 && c <= n) {
+      T hl[NV], F[NV];
+#pragma unroll
+      for (int v = 0; v < NV; v++) hl[v] = (t > 0) ? sH[v * NT + t - 1] : sHc[v];
+      hll(hl, lo, F);
+#pragma unroll
+      for (int v = 0; v < NV; v++) sF[v * (NT + 1) + t + 1] = F[v];
+    }
+    __syncthreads();
+    // the last thread hands its hi face state to the next chunk (read after the next
+    // barrier; every read of the current carry happened before the barrier above)
+    if (t == NT - 1 && c <= n) {
+#pragma unroll
+      for (int v = 0; v < NV; v++) sHc[v] = hi[v];
+    }
+    const int cu = b - 1 + t;  // cell whose two faces are now known
+    if (cu >= 0 && cu < n) {
+      T U[NV], W[NV];
+#pragma unroll
+      for (int v = 0; v < NV; v++) {
+        U[v] = src[v * cap + cu] - dtdx * (sF[v * (NT + 1) + t + 1] - sF[v * (NT + 1) + t]);
+        dst[v * cap + cu] = U[v];
+      }
+      cons_to_prim(U, W);
+      if (!realizable(W)) {
+        if (!FALLBACK) sFl[cu] = 1;
+        *s_nbad = 1;
+      }
+      smax = fmax(smax, (fabs(W[1]) + T(1.7320508075688772) * sqrt_ratio(W[4], W[0])) * idx);
+    }
+    __syncthreads();
+    if (t == 0) {  // the last face of this chunk is the lower face of the next chunk's first update
+#pragma unroll
+      for (int v = 0; v < NV; v++) sF[v * (NT + 1)] = sF[v * (NT + 1) + NT];
+    }
+  }
+  return smax;
+}
+
 template <typename T, int NT>
 __global__ void __launch_bounds__(NT) tubes_kernel(TubeArgs<T> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int cap = a.cap;
-  T *sU = reinterpret_cast<T *>(smem_raw);  // [NV][cap]
-  T *sF = sU + (size_t)NV * cap;            // [NV][NT+1]: sF[0] = carried face, sF[t+1] = lower face of cell b+t
+  T *sU = reinterpret_cast<T *>(smem_raw);  // [NV][cap] the tube
+  T *sUo = sU + (size_t)NV * cap;           // [NV][cap] U^n kept for the fallback pass
+  T *sF = sUo + (size_t)NV * cap;           // [NV][NT+1]: sF[0] = carried face, sF[t+1] = lower face of cell b+t
   T *sH = sF + NV * (NT + 1);               // [NV][NT]: hi face states of the chunk
   T *sHc = sH + NV * NT;                    // [NV]: hi face state of the cell before the chunk
+  unsigned char *sFl = reinterpret_cast<unsigned char *>(sHc + NV);  // [cap] fallback tags
   __shared__ T red[NT / 32];
   __shared__ int s_q;
-  __shared__ int s_flag;
+  __shared__ int s_nbad;
   const int t = threadIdx.x;
   for (;;) {
     if (t == 0) s_q = atomicAdd(a.queue, 1);
@@ -86,13 +155,13 @@ __global__ void __launch_bounds__(NT) tubes_kernel(TubeArgs<T> a) {
     const int k = a.order[q];
     const int n = a.len[k];
     const int64_t off = a.off[k];
-    for (int c = t; c < n; c += NT)
+    for (int c = t; c < n; c += NT) {
 #pragma unroll
       for (int v = 0; v < NV; v++) sU[v * cap + c] = a.U[v * a.total + off + c];
-    if (t == 0) s_flag = 0;
+      sFl[c] = 0;
+    }
     __syncthreads();
-    const double dxd = 1.0 / n;
-    const T idx = (T)n, dtdx_half_base = T(0.5) * idx;
+    const T idx = (T)n, half_idx = T(0.5) * idx;
     // signal-speed sum of the initial state
     T sm = T(0);
     for (int c = t; c < n; c += NT) {
@@ -110,58 +179,27 @@ __global__ void __launch_bounds__(NT) tubes_kernel(TubeArgs<T> a) {
       double dt = a.cfl / (double)sm;
       double tn = tt + dt;
       if (tn >= te) { dt = te - tt; tn = te; }
-      const T dtT = (T)dt, nu = (T)dt * dtdx_half_base, dtdx = (T)dt * idx;
-      T smax = T(0);
-      for (int b = -1; b <= n; b += NT) {
-        const int c = b + t;
-        T lo[NV], hi[NV];
-        if (c <= n) {
-          T wm[NV], w0[NV], wp[NV];
-          load_w(sU, cap, c - 1, n, wm);
-          load_w(sU, cap, c, n, w0);
-          load_w(sU, cap, c + 1, n, wp);
-          reconstruct(wm, w0, wp, nu, lo, hi);
+      const T nu = (T)dt * half_idx, dtdx = (T)dt * idx;
+      for (int c = t; c < n; c += NT)
 #pragma unroll
-          for (int v = 0; v < NV; v++) sH[v * NT + t] = hi[v];
-        }
+        for (int v = 0; v < NV; v++) sUo[v * cap + c] = sU[v * cap + c];
+      if (t == 0) s_nbad = 0;
+      __syncthreads();
+      T smax = tube_pass<T, NT, false>(sU, sU, sFl, n, cap, nu, dtdx, idx, sF, sH, sHc, &s_nbad);
+      sm = block_max<T, NT>(smax, red);  // its barriers also order the carries and s_nbad
+      if (s_nbad) {
+        // a-posteriori fallback: redo the step from U^n with first-order faces at tagged cells
+        if (t == 0) s_nbad = 0;
         __syncthreads();
-        if (c >= 0 && c <= n) {
-          T hl[NV], F[NV];
-#pragma unroll
-          for (int v = 0; v < NV; v++) hl[v] = (t > 0) ? sH[v * NT + t - 1] : sHc[v];
-          hll(hl, lo, F);
-#pragma unroll
-          for (int v = 0; v < NV; v++) sF[v * (NT + 1) + t + 1] = F[v];
-        }
+        smax = tube_pass<T, NT, true>(sUo, sU, sFl, n, cap, nu, dtdx, idx, sF, sH, sHc, &s_nbad);
+        sm = block_max<T, NT>(smax, red);
+        const bool still_bad = s_nbad != 0;
+        for (int c = t; c < n; c += NT) sFl[c] = 0;
         __syncthreads();
-        // the last thread hands its hi face state to the next chunk (read after its first
-        // barrier; every read of the current carry happened before the barrier above)
-        if (t == NT - 1 && c <= n) {
-#pragma unroll
-          for (int v = 0; v < NV; v++) sHc[v] = hi[v];
-        }
-        const int cu = b - 1 + t;  // cell whose two faces are now known
-        if (cu >= 0 && cu < n) {
-          T U[NV], W[NV];
-#pragma unroll
-          for (int v = 0; v < NV; v++) {
-            U[v] = sU[v * cap + cu] - dtdx * (sF[v * (NT + 1) + t + 1] - sF[v * (NT + 1) + t]);
-            sU[v * cap + cu] = U[v];
-          }
-          cons_to_prim(U, W);
-          if (!realizable(W)) s_flag = 1;
-          smax = fmax(smax, (fabs(W[1]) + T(1.7320508075688772) * sqrt_ratio(W[4], W[0])) * idx);
-        }
-        __syncthreads();
-        if (t == 0) {  // the last face of this chunk is the lower face of the next chunk's first update
-#pragma unroll
-          for (int v = 0; v < NV; v++) sF[v * (NT + 1)] = sF[v * (NT + 1) + NT];
-        }
+        if (still_bad) { status = 4; tt = tn; steps++; break; }
       }
-      sm = block_max<T, NT>(smax, red);  // its first barrier also orders the carries
       tt = tn;
       steps++;
-      if (s_flag) { status = 4; break; }
     }
     __syncthreads();
     for (int c = t; c < n; c += NT)
@@ -177,7 +215,7 @@ __global__ void __launch_bounds__(NT) tubes_kernel(TubeArgs<T> a) {
 }
 
 template <typename T> size_t tube_smem(int cap, int nt) {
-  return sizeof(T) * ((size_t)NV * cap + (size_t)NV * (nt + 1) + (size_t)NV * nt + NV);
+  return sizeof(T) * (2 * (size_t)NV * cap + (size_t)NV * (nt + 1) + (size_t)NV * nt + NV) + (size_t)cap;
 }
 
 template <typename T, int NT> static cudaError_t launch_tubes_nt(const TubeArgs<T> &a, int blocks, cudaStream_t s) {
@@ -317,7 +355,7 @@ msh_status msh_batch_init(msh_batch **out, int32_t ntubes, const int32_t *len, c
   if (ntubes < 1) return bfail(MSH_E_INVALID_ARG, "ntubes must be >= 1");
   if (precision != MSH_FP32 && precision != MSH_FP64) return bfail(MSH_E_INVALID_ARG, "bad precision");
   if (!(cfl > 0.0 && cfl <= 1.0)) return bfail(MSH_E_INVALID_ARG, "cfl must be in (0, 1]");
-  const int maxlen = precision == MSH_FP32 ? 4096 : 2048;
+  const int maxlen = precision == MSH_FP32 ? 2048 : 1024;
   int cap = 0;
   for (int k = 0; k < ntubes; k++) {
     if (len[k] < 4 || len[k] > maxlen) return bfail(MSH_E_INVALID_ARG, "len[%d] = %d outside [4, %d]", k, len[k], maxlen);

@@ -199,6 +199,22 @@ __device__ __forceinline__ void reconstruct(const T (&wm)[NV], const T (&w0)[NV]
   }
 }
 
+// A-posteriori fallback: every face that touches a cell whose second-order update was
+// not realizable takes first-order states (the cell-centred primitive state).  fm, f0,
+// fp: tags of cells i-1, i, i+1 along the sweep.
+template <typename T>
+__device__ __forceinline__ void first_order_faces(bool fm, bool f0, bool fp, const T (&w0)[NV], T (&lo)[NV],
+                                                  T (&hi)[NV]) {
+  if (f0 || fm) {
+#pragma unroll
+    for (int k = 0; k < NV; k++) lo[k] = w0[k];
+  }
+  if (f0 || fp) {
+#pragma unroll
+    for (int k = 0; k < NV; k++) hi[k] = w0[k];
+  }
+}
+
 // Conserved vector and normal flux of a local-frame primitive state (eqs contin,
 // moment, dispers: rho u_n; rho u_i u_n + P_in; E_ij u_n + P_in u_j + P_jn u_i).
 template <typename T>

@@ -75,6 +75,7 @@ struct msh_grid {
   cudaEvent_t ev_done[2] = {nullptr, nullptr};
   Partial *part = nullptr;
   int part_cap = 0;
+  int32_t *flags = nullptr;  // per-cell fallback tags
   double *hist = nullptr;
   int64_t hist_cap = 0;
   bool has_state = false;
@@ -98,6 +99,7 @@ template <typename T> StepArgs<T> make_args(msh_grid *g) {
   a.acc = (const T *)g->acc;
   a.ctrl = g->ctrl;
   a.part = g->part;
+  a.flags = g->flags;
   a.nx = (int)g->n[0];
   a.ny = (int)g->n[1];
   a.nz = (int)g->n[2];
@@ -131,10 +133,14 @@ msh_status launch_one_step(msh_grid *g, int ev_slot) {
   int nb = 0;
   cudaError_t e;
   if (g->profiling && ev_slot >= 0) CUDA_TRY(cudaEventRecord(g->ev[3 * ev_slot], g->stream));
-  if (g->prec == MSH_FP32) e = launch_step<float>(make_args<float>(g), g->ndim, g->rows, g->stream, &nb);
-  else e = launch_step<double>(make_args<double>(g), g->ndim, g->rows, g->stream, &nb);
+  if (g->prec == MSH_FP32) e = launch_step<float>(make_args<float>(g), g->ndim, g->rows, false, g->stream, &nb);
+  else e = launch_step<double>(make_args<double>(g), g->ndim, g->rows, false, g->stream, &nb);
   if (e != cudaSuccess) return fail(MSH_E_CUDA, "step kernel launch: %s", cudaGetErrorString(e));
   if (g->profiling && ev_slot >= 0) CUDA_TRY(cudaEventRecord(g->ev[3 * ev_slot + 1], g->stream));
+  // fallback pass: returns at once unless the step tagged non-realizable cells
+  if (g->prec == MSH_FP32) e = launch_step<float>(make_args<float>(g), g->ndim, g->rows, true, g->stream, nullptr);
+  else e = launch_step<double>(make_args<double>(g), g->ndim, g->rows, true, g->stream, nullptr);
+  if (e != cudaSuccess) return fail(MSH_E_CUDA, "fallback kernel launch: %s", cudaGetErrorString(e));
   e = launch_finalize(g->ctrl, g->part, nb, 0, g->stream);
   if (e != cudaSuccess) return fail(MSH_E_CUDA, "finalize launch: %s", cudaGetErrorString(e));
   if (g->profiling && ev_slot >= 0) CUDA_TRY(cudaEventRecord(g->ev[3 * ev_slot + 2], g->stream));
@@ -270,6 +276,9 @@ msh_status msh_init_grid(msh_grid **out, int32_t ndim, const int64_t n[3], const
     e = cudaMalloc(&g->U[b], bytes);
     if (e != cudaSuccess) return cleanup(fail(MSH_E_NOMEM, "state buffer (%zu bytes): %s", bytes, cudaGetErrorString(e)));
   }
+  e = cudaMalloc(&g->flags, g->N * sizeof(int32_t));
+  if (e == cudaSuccess) e = cudaMemsetAsync(g->flags, 0, g->N * sizeof(int32_t), g->stream);
+  if (e != cudaSuccess) return cleanup(fail(MSH_E_NOMEM, "fallback tags: %s", cudaGetErrorString(e)));
   e = cudaMalloc(&g->ctrl, sizeof(Ctrl));
   if (e != cudaSuccess) return cleanup(fail(MSH_E_NOMEM, "control block: %s", cudaGetErrorString(e)));
   e = cudaMallocHost(&g->hctrl, sizeof(Ctrl));
@@ -310,6 +319,7 @@ msh_status msh_destroy(msh_grid *g) {
   for (auto &e : g->ev_done)
     if (e) cudaEventDestroy(e);
   if (g->part) cudaFree(g->part);
+  if (g->flags) cudaFree(g->flags);
   if (g->hist) cudaFree(g->hist);
   if (g->own_stream && g->stream) cudaStreamDestroy(g->stream);
   delete g;

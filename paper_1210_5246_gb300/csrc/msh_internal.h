@@ -11,7 +11,7 @@ namespace msh {
 struct Ctrl {
   double t, t_next, t_end, dt, dt_max, dt_cfl, cfl, dt_last;
   int64_t step, max_step, first_bad, hist_cap, hist_base;
-  int32_t done, status, realizable, pad;
+  int32_t done, status, realizable, nbad;  // nbad: cells tagged for the fallback this step
   double totals[10];
   double *hist;
 };
@@ -28,6 +28,7 @@ template <typename T> struct StepArgs {
   const T *acc;         // gravitational acceleration -grad Phi, [3][N], or nullptr
   Ctrl *ctrl;
   Partial *part;
+  int32_t *flags;       // per cell: step tag of a failed second-order update (fallback)
   int nx, ny, nz;
   int bc[6];
   double dx[3];
@@ -39,7 +40,9 @@ constexpr int kTileX = 30;     // interior cells per warp row of the 2D/3D kerne
 constexpr int kFinalizeThreads = 256;
 
 // launchers (msh_step.cu)
-template <typename T> cudaError_t launch_step(const StepArgs<T> &a, int ndim, int rows, cudaStream_t s,
+// retry = false: the step; retry = true: the fallback pass, a no-op unless the step
+// tagged cells whose second-order update was not realizable
+template <typename T> cudaError_t launch_step(const StepArgs<T> &a, int ndim, int rows, bool retry, cudaStream_t s,
                                               int *nblocks_out);
 template <typename T> int step_blocks(int ndim, int rows, int nx, int ny, int nz, int zchunk);
 template <typename T> size_t step_smem(int ndim, int rows);

@@ -72,11 +72,11 @@ __device__ __forceinline__ T speed_sum(const T (&W)[NV], T idx, T idy, T idz) {
 }
 
 // Per-cell tail of the step: gravity source, store, next-dt speed, realizability, totals.
-template <typename T, int NDIM>
+template <typename T, int NDIM, bool RETRY>
 __device__ __forceinline__ void finish_cell(const StepArgs<T> &a, const T *__restrict__ Us,
                                             T *__restrict__ Ud, size_t N, size_t c,
                                             const T (&acc)[NV], T dt, T idx, T idy, T idz, Acc<T> &diag,
-                                            T &smax, long long &bad) {
+                                            T &smax, long long &bad, int32_t tag) {
   T Un[NV];
 #pragma unroll
   for (int k = 0; k < NV; k++) Un[k] = Us[k * N + c] + dt * acc[k];
@@ -104,7 +104,13 @@ __device__ __forceinline__ void finish_cell(const StepArgs<T> &a, const T *__res
   for (int k = 0; k < NV; k++) Ud[k * N + c] = Un[k];
   T W[NV];
   cons_to_prim(Un, W);
-  if (!realizable(W)) bad = min(bad, (long long)c);
+  if (!realizable(W)) {
+    bad = min(bad, (long long)c);
+    if (!RETRY) {  // tag the cell for the fallback pass
+      a.flags[c] = tag;
+      atomicAdd(&a.ctrl->nbad, 1);
+    }
+  }
   smax = fmax(smax, speed_sum<T, NDIM>(W, idx, idy, idz));
   diag.add(Un);
 }
@@ -117,12 +123,15 @@ __device__ __forceinline__ void write_partial(const Acc<T> &diag, T smax, long l
 }
 
 // ------------------------------------------------------------------ 1D kernel
-template <typename T>
+template <typename T, bool RETRY>
 __global__ void __launch_bounds__(kTile1D) step1d_kernel(StepArgs<T> a) {
   constexpr int B = kTile1D, SXX = B + 2;
   const Ctrl *ctrl = a.ctrl;
   if (ctrl->done) return;
+  if (RETRY && ctrl->nbad == 0) return;
   const int64_t step = ctrl->step;
+  const int32_t tag = (int32_t)(step & 0x3fffffff) + 1;
+  __shared__ unsigned char sFl[RETRY ? SXX : 1];
   const T *__restrict__ Us = a.U[step & 1];
   T *__restrict__ Ud = a.U[(step + 1) & 1];
   const double dtd = ctrl->dt;
@@ -145,12 +154,14 @@ __global__ void __launch_bounds__(kTile1D) step1d_kernel(StepArgs<T> a) {
     cons_to_prim(U, W);
 #pragma unroll
     for (int k = 0; k < NV; k++) sW[k][i] = W[k];
+    if (RETRY) sFl[i] = (a.flags[xx] == tag);
   }
   __syncthreads();
   T wm[NV], w0[NV], wp[NV], lo[NV], hi[NV], F[NV];
 #pragma unroll
   for (int k = 0; k < NV; k++) { wm[k] = sW[k][t]; w0[k] = sW[k][t + 1]; wp[k] = sW[k][t + 2]; }
   reconstruct(wm, w0, wp, nu, lo, hi);
+  if (RETRY) first_order_faces(sFl[t] != 0, sFl[t + 1] != 0, sFl[t + 2] != 0, w0, lo, hi);
 #pragma unroll
   for (int k = 0; k < NV; k++) sH[k][t] = hi[k];
   __syncthreads();
@@ -175,7 +186,7 @@ __global__ void __launch_bounds__(kTile1D) step1d_kernel(StepArgs<T> a) {
     T acc[NV];
 #pragma unroll
     for (int k = 0; k < NV; k++) acc[k] = (F[k] - sH[k][t + 1]) * idx;
-    finish_cell<T, 1>(a, Us, Ud, N, (size_t)gx, acc, dt, idx, T(0), T(0), diag, smax, bad);
+    finish_cell<T, 1, RETRY>(a, Us, Ud, N, (size_t)gx, acc, dt, idx, T(0), T(0), diag, smax, bad, tag);
   }
   write_partial<T, B>(diag, smax, bad, a.part + blockIdx.x);
 }
@@ -187,14 +198,18 @@ __device__ __forceinline__ void gather(const T *__restrict__ pl, int sy, int sx,
   for (int k = 0; k < NV; k++) w[k] = pl[(Frame<D>::g(k) * SY + sy) * SX + sx];
 }
 
-template <typename T, int NDIM, int BY>
+template <typename T, int NDIM, int BY, bool RETRY>
 __global__ void __launch_bounds__(32 * BY, (BY <= 8 ? 2 : 1)) step_tile_kernel(StepArgs<T> a) {
   constexpr int SX = 34, SY = BY + 2;
   constexpr int NPL = (NDIM == 3) ? 3 : 1;
   constexpr int PL = NV * SY * SX;
   const Ctrl *ctrl = a.ctrl;
   if (ctrl->done) return;
+  if (RETRY && ctrl->nbad == 0) return;
   const int64_t step = ctrl->step;
+  const int32_t tag = (int32_t)(step & 0x3fffffff) + 1;
+  // fallback tags of the staged cells (fallback pass only)
+  __shared__ unsigned char sFl[RETRY ? NPL : 1][RETRY ? SY : 1][RETRY ? SX : 1];
   const T *__restrict__ Us = a.U[step & 1];
   T *__restrict__ Ud = a.U[(step + 1) & 1];
   const double dtd = ctrl->dt;
@@ -237,17 +252,21 @@ __global__ void __launch_bounds__(32 * BY, (BY <= 8 ? 2 : 1)) step_tile_kernel(S
       cons_to_prim(U, W);
 #pragma unroll
       for (int k = 0; k < NV; k++) dst[(k * SY + qy) * SX + qx] = W[k];
+      if (RETRY) sFl[buf][qy][qx] = (a.flags[c] == tag);
     }
   };
+  auto fl = [&](int buf, int qy, int qx) -> bool { return RETRY ? sFl[RETRY ? buf : 0][RETRY ? qy : 0][RETRY ? qx : 0] != 0 : false; };
 
   // x and y sweeps of the plane in buffer `buf`, accumulating -dF/dx - dG/dy into acc
-  auto sweep_xy = [&](const T *pl, T (&acc)[NV]) {
+  auto sweep_xy = [&](int b, T (&acc)[NV]) {
+    const T *pl = sW + b * PL;
     if (ty >= 1 && ty <= BY - 2) {  // warp-uniform: one warp per row
       T wm[NV], w0[NV], wp[NV], lo[NV], hi[NV], hl[NV], F[NV];
       gather<T, 0, SY, SX>(pl, sy, sx - 1, wm);
       gather<T, 0, SY, SX>(pl, sy, sx, w0);
       gather<T, 0, SY, SX>(pl, sy, sx + 1, wp);
       reconstruct(wm, w0, wp, nux, lo, hi);
+      if (RETRY) first_order_faces(fl(b, sy, sx - 1), fl(b, sy, sx), fl(b, sy, sx + 1), w0, lo, hi);
 #pragma unroll
       for (int k = 0; k < NV; k++) hl[k] = __shfl_up_sync(FULL, hi[k], 1);
       hll(hl, lo, F);  // flux at the lower x face of this cell
@@ -265,6 +284,7 @@ __global__ void __launch_bounds__(32 * BY, (BY <= 8 ? 2 : 1)) step_tile_kernel(S
       gather<T, 1, SY, SX>(pl, sy, sx, w0);
       gather<T, 1, SY, SX>(pl, sy + 1, sx, wp);
       reconstruct(wm, w0, wp, nuy, lo, hi);
+      if (RETRY) first_order_faces(fl(b, sy - 1, sx), fl(b, sy, sx), fl(b, sy + 1, sx), w0, lo, hi);
 #pragma unroll
       for (int k = 0; k < NV; k++) sX[(k * BY + ty) * 32 + tx] = hi[k];
     }
@@ -301,8 +321,9 @@ __global__ void __launch_bounds__(32 * BY, (BY <= 8 ? 2 : 1)) step_tile_kernel(S
     T acc[NV];
 #pragma unroll
     for (int k = 0; k < NV; k++) acc[k] = T(0);
-    sweep_xy(sW, acc);
-    if (valid) finish_cell<T, NDIM>(a, Us, Ud, N, (size_t)gy * nx + gx, acc, dt, idx, idy, idz, diag, smax, bad);
+    sweep_xy(0, acc);
+    if (valid)
+      finish_cell<T, NDIM, RETRY>(a, Us, Ud, N, (size_t)gy * nx + gx, acc, dt, idx, idy, idz, diag, smax, bad, tag);
   } else {
     const int z0 = blockIdx.z * a.zchunk;
     const int z1 = min(z0 + a.zchunk, nz);
@@ -319,6 +340,8 @@ __global__ void __launch_bounds__(32 * BY, (BY <= 8 ? 2 : 1)) step_tile_kernel(S
       gather<T, 2, SY, SX>(sW + buf(z0 - 1) * PL, sy, sx, w0);
       gather<T, 2, SY, SX>(sW + buf(z0) * PL, sy, sx, wp);
       reconstruct(wm, w0, wp, nuz, lo, hprev);
+      if (RETRY)
+        first_order_faces(fl(buf(z0 - 2), sy, sx), fl(buf(z0 - 1), sy, sx), fl(buf(z0), sy, sx), w0, lo, hprev);
     }
     __syncthreads();
     load_plane(buf(z0 + 1), z0 + 1);
@@ -329,6 +352,7 @@ __global__ void __launch_bounds__(32 * BY, (BY <= 8 ? 2 : 1)) step_tile_kernel(S
       gather<T, 2, SY, SX>(sW + buf(z0) * PL, sy, sx, w0);
       gather<T, 2, SY, SX>(sW + buf(z0 + 1) * PL, sy, sx, wp);
       reconstruct(wm, w0, wp, nuz, lo, hi);
+      if (RETRY) first_order_faces(fl(buf(z0 - 1), sy, sx), fl(buf(z0), sy, sx), fl(buf(z0 + 1), sy, sx), w0, lo, hi);
       hll(hprev, lo, Fprev);
 #pragma unroll
       for (int k = 0; k < NV; k++) hprev[k] = hi[k];
@@ -340,13 +364,14 @@ __global__ void __launch_bounds__(32 * BY, (BY <= 8 ? 2 : 1)) step_tile_kernel(S
       T acc[NV];
 #pragma unroll
       for (int k = 0; k < NV; k++) acc[k] = T(0);
-      sweep_xy(sW + buf(z) * PL, acc);
+      sweep_xy(buf(z), acc);
       if (interior) {
         T wm[NV], w0[NV], wp[NV], lo[NV], hi[NV], F[NV];
         gather<T, 2, SY, SX>(sW + buf(z) * PL, sy, sx, wm);
         gather<T, 2, SY, SX>(sW + buf(z + 1) * PL, sy, sx, w0);
         gather<T, 2, SY, SX>(sW + buf(z + 2) * PL, sy, sx, wp);
         reconstruct(wm, w0, wp, nuz, lo, hi);  // cell z+1
+        if (RETRY) first_order_faces(fl(buf(z), sy, sx), fl(buf(z + 1), sy, sx), fl(buf(z + 2), sy, sx), w0, lo, hi);
         hll(hprev, lo, F);                     // flux through the upper z face of cell z
 #pragma unroll
         for (int k = 0; k < NV; k++) {
@@ -356,8 +381,8 @@ __global__ void __launch_bounds__(32 * BY, (BY <= 8 ? 2 : 1)) step_tile_kernel(S
         }
       }
       if (valid)
-        finish_cell<T, NDIM>(a, Us, Ud, N, ((size_t)z * ny + gy) * nx + gx, acc, dt, idx, idy, idz, diag,
-                             smax, bad);
+        finish_cell<T, NDIM, RETRY>(a, Us, Ud, N, ((size_t)z * ny + gy) * nx + gx, acc, dt, idx, idy, idz, diag,
+                                    smax, bad, tag);
       __syncthreads();
       if (z + 1 < z1) {
         load_plane(buf(z), z + 3);
@@ -466,6 +491,7 @@ __global__ void __launch_bounds__(kFinalizeThreads) finalize_kernel(Ctrl *ctrl, 
     c->done = 1;
     return;
   }
+  c->nbad = 0;
   const int64_t hi_ = c->step - c->hist_base;
   if (c->hist != nullptr && hi_ >= 0 && hi_ < c->hist_cap) c->hist[hi_] = c->dt;
   c->dt_last = c->dt;
@@ -485,6 +511,7 @@ __global__ void run_start_kernel(Ctrl *c, double t_end, int64_t max_steps, doubl
   c->dt_max = dt_max;
   c->done = 0;
   c->status = 0;
+  c->nbad = 0;
   plan(c);
 }
 
@@ -517,37 +544,42 @@ template <typename T> int step_blocks(int ndim, int rows, int nx, int ny, int nz
   return bx * by * bz;
 }
 
-template <typename T, int NDIM, int BY>
+template <typename T, int NDIM, int BY, bool RETRY>
 static cudaError_t launch_tile(const StepArgs<T> &a, cudaStream_t s) {
   const size_t smem = step_smem<T>(NDIM, BY);
   static bool attr_set = false;  // one attribute call per instantiation and process
   if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(step_tile_kernel<T, NDIM, BY>,
+    cudaError_t e = cudaFuncSetAttribute(step_tile_kernel<T, NDIM, BY, RETRY>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     attr_set = true;
   }
   dim3 grid((a.nx + kTileX - 1) / kTileX, (a.ny + BY - 3) / (BY - 2),
             NDIM == 3 ? (a.nz + a.zchunk - 1) / a.zchunk : 1);
-  step_tile_kernel<T, NDIM, BY><<<grid, dim3(32, BY), smem, s>>>(a);
+  step_tile_kernel<T, NDIM, BY, RETRY><<<grid, dim3(32, BY), smem, s>>>(a);
   return cudaGetLastError();
 }
 
-template <typename T>
-cudaError_t launch_step(const StepArgs<T> &a, int ndim, int rows, cudaStream_t s, int *nblocks_out) {
-  if (nblocks_out) *nblocks_out = step_blocks<T>(ndim, rows, a.nx, a.ny, a.nz, a.zchunk);
+template <typename T, bool RETRY>
+static cudaError_t launch_step_mode(const StepArgs<T> &a, int ndim, int rows, cudaStream_t s) {
   if (ndim == 1) {
-    step1d_kernel<T><<<(a.nx + kTile1D - 3) / (kTile1D - 2), kTile1D, 0, s>>>(a);
+    step1d_kernel<T, RETRY><<<(a.nx + kTile1D - 3) / (kTile1D - 2), kTile1D, 0, s>>>(a);
     return cudaGetLastError();
   }
   if (ndim == 2) {
-    if (rows == 4) return launch_tile<T, 2, 4>(a, s);
-    if (rows == 16) return launch_tile<T, 2, 16>(a, s);
-    return launch_tile<T, 2, 8>(a, s);
+    if (rows == 4) return launch_tile<T, 2, 4, RETRY>(a, s);
+    if (rows == 16) return launch_tile<T, 2, 16, RETRY>(a, s);
+    return launch_tile<T, 2, 8, RETRY>(a, s);
   }
-  if (rows == 4) return launch_tile<T, 3, 4>(a, s);
-  if (rows == 16) return launch_tile<T, 3, 16>(a, s);
-  return launch_tile<T, 3, 8>(a, s);
+  if (rows == 4) return launch_tile<T, 3, 4, RETRY>(a, s);
+  if (rows == 16) return launch_tile<T, 3, 16, RETRY>(a, s);
+  return launch_tile<T, 3, 8, RETRY>(a, s);
+}
+
+template <typename T>
+cudaError_t launch_step(const StepArgs<T> &a, int ndim, int rows, bool retry, cudaStream_t s, int *nblocks_out) {
+  if (nblocks_out) *nblocks_out = step_blocks<T>(ndim, rows, a.nx, a.ny, a.nz, a.zchunk);
+  return retry ? launch_step_mode<T, true>(a, ndim, rows, s) : launch_step_mode<T, false>(a, ndim, rows, s);
 }
 
 template <typename T>
@@ -584,7 +616,7 @@ template <typename T> cudaError_t launch_convert(T *U, size_t N, int to_primitiv
 }
 
 #define MSH_INST(T)                                                                                   \
-  template cudaError_t launch_step<T>(const StepArgs<T> &, int, int, cudaStream_t, int *);           \
+  template cudaError_t launch_step<T>(const StepArgs<T> &, int, int, bool, cudaStream_t, int *);     \
   template int step_blocks<T>(int, int, int, int, int, int);                                         \
   template size_t step_smem<T>(int, int);                                                            \
   template cudaError_t launch_scan<T>(const T *, size_t, int, int, int, const double *, Partial *, int, \

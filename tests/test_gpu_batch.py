@@ -31,7 +31,7 @@ def _oracle_tube(oracle, tubes, k, dtype=np.float64):
     return U.reshape(10, n), steps, t, rc
 
 
-LENGTHS = [4, 5, 17, 64, 127, 128, 129, 255, 256, 257, 300, 513, 1025, 2048]
+LENGTHS = [4, 5, 17, 64, 127, 128, 129, 255, 256, 257, 300, 513, 1000, 1024]
 
 
 def test_batch_fp64_matches_oracle(msh, oracle):
@@ -49,11 +49,11 @@ def test_batch_fp64_matches_oracle(msh, oracle):
 
 
 def test_batch_fp32_matches_oracle(msh, oracle):
-    tubes = _random_tubes(LENGTHS, seed=42)
+    tubes = _random_tubes(LENGTHS[:-2] + [1500, 2048], seed=42)
     b = msh.Batch(tubes.length, tubes.WL, tubes.WR, tubes.t_end, tubes.cfl, msh.FP32)
     b.run(threads=128)
     W = b.get_state(msh.PRIMITIVE).astype(np.float64)
-    for k in range(len(LENGTHS)):
+    for k in range(len(tubes.length)):
         Uo, _, _, _ = _oracle_tube(oracle, tubes, k, np.float32)
         assert_fp32(b.tube(W, k), oracle.cons_to_prim(Uo), what=f"tube {k}")
     b.close()

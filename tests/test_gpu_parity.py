@@ -255,3 +255,44 @@ def test_invalid_arguments(msh):
         g.step()
     assert ei.value.status == msh.MSH_E_STATE
     g.close()
+
+
+# ------------------------------------------------- a-posteriori fallback pass
+def _extreme(shape, seed):
+    rng = np.random.default_rng(seed)
+    W = np.zeros((10,) + shape)
+    W[0] = np.exp(rng.uniform(np.log(0.05), np.log(20), shape))
+    W[1:4] = rng.uniform(-1.5, 1.5, (3,) + shape)
+    L = np.zeros((3, 3) + shape)
+    L[0, 0], L[1, 1], L[2, 2] = (rng.uniform(0.1, 1, shape) for _ in range(3))
+    L[1, 0], L[2, 0], L[2, 1] = (rng.normal(0, 0.3, shape) for _ in range(3))
+    P = np.einsum("ik...,jk...->ij...", L, L)
+    W[4], W[5], W[6], W[7], W[8], W[9] = P[0, 0], P[0, 1], P[0, 2], P[1, 1], P[1, 2], P[2, 2]
+    return W
+
+
+@pytest.mark.parametrize("shape,n,bc,cfl", [((1, 1, 8), (8,), ((0, 0),), 0.8),
+                                            ((1, 12, 12), (12, 12), ((0, 0), (1, 2)), 0.5),
+                                            ((6, 7, 9), (9, 7, 6), ((2, 1), (0, 0), (1, 1)), 0.5)])
+def test_fallback_pass_fp64(msh, oracle, shape, n, bc, cfl):
+    """Extreme states whose second-order update is not realizable: the GPU fallback pass
+    (first-order faces around tagged cells) matches the oracle's step."""
+    seed = {1: 1, 2: 0, 3: 0}[len(n)]
+    W = _extreme(shape, seed) if len(n) > 1 else None
+    if W is None:
+        from tests.test_oracle_pins import _extreme_tiny
+        W = _extreme_tiny(1)
+    nd = len(n)
+    og = oracle.Grid(n, (0,) * nd, (1,) * nd, bc, cfl)
+    U0 = oracle.prim_to_cons(W)
+    dt = oracle.cfl_dt(og, U0)
+    assert not oracle.diagnostics(og, oracle.step_second_order_only(og, U0, dt))[1]
+    Uo = oracle.step(og, U0, dt)
+    assert oracle.diagnostics(og, Uo)[1]
+    g = msh.Grid(n, (0,) * nd, (1,) * nd, bc, cfl, msh.FP64)
+    g.set_state(W, msh.PRIMITIVE)
+    dtg = g.step()
+    assert abs(dtg - dt) <= 1e-14 * dt
+    assert_fp64(g.get_state(), Uo, what=f"fallback {shape}")
+    assert g.diagnostics()[1]
+    g.close()
