@@ -164,19 +164,31 @@ class Tubes:
 def tubes(ntubes=4096, nmin=128, nmax=2048, t_end=0.1, cfl=0.8, seed=4):
     """Batched Riemann problems: lengths log-uniform in [nmin, nmax]; per side rho
     log-uniform [0.1, 10], u_x uniform [-1, 1], u_y = u_z = 0, P = L L^T (diagonal
-    U[0.1, 1], off-diagonal N(0, 0.2))."""
+    U[0.1, 1], off-diagonal N(0, 0.2)); draws whose exact solution contains vacuum are
+    redrawn."""
     rng = np.random.Generator(np.random.PCG64(seed))
     length = np.rint(np.exp(rng.uniform(math.log(nmin), math.log(nmax), ntubes))).astype(np.int32)
-    states = []
-    for _ in range(2):
-        W = np.zeros((ntubes, 10))
-        W[:, 0] = np.exp(rng.uniform(math.log(0.1), math.log(10.0), ntubes))
-        W[:, 1] = rng.uniform(-1.0, 1.0, ntubes)
-        P = _spd_field(rng, (ntubes,), 0.1, 1.0, 0.2)
+
+    def draw(m):
+        W = np.zeros((m, 10))
+        W[:, 0] = np.exp(rng.uniform(math.log(0.1), math.log(10.0), m))
+        W[:, 1] = rng.uniform(-1.0, 1.0, m)
+        P = _spd_field(rng, (m,), 0.1, 1.0, 0.2)
         for c, v in zip((4, 5, 6, 7, 8, 9), P):
             W[:, c] = v
-        states.append(W)
-    return Tubes(length, states[0], states[1], t_end, cfl)
+        return W
+
+    WL, WR = draw(ntubes), draw(ntubes)
+    # Riemann problems whose exact solution contains vacuum (the two states separate faster
+    # than the sum of their fast speeds, u_R - u_L >= cf_L + cf_R with cf = sqrt(3 P_xx/rho))
+    # are redrawn: zero density is outside the moment closure's validity.
+    while True:
+        cf = lambda W: np.sqrt(3.0 * W[:, 4] / W[:, 0])
+        vac = np.where(WR[:, 1] - WL[:, 1] >= cf(WL) + cf(WR))[0]
+        if len(vac) == 0:
+            break
+        WL[vac], WR[vac] = draw(len(vac)), draw(len(vac))
+    return Tubes(length, WL, WR, t_end, cfl)
 
 
 # ---------------------------------------------------------------------------- disc
