@@ -32,7 +32,9 @@
  *   - face state fallback: if a Hancock face state of a cell has rho <= 0 or
  *     P_nn <= 0, both face states of that cell in that direction revert to W_i;
  *   - a-posteriori fallback: cells whose second-order update is not realizable get
- *     first-order face states on all their faces and the step is recomputed;
+ *     first-order face states on all their faces and the step is recomputed; cells
+ *     still failing join the tagged set and the step is recomputed again (at most
+ *     OG_FALLBACK_PASSES passes);
  *   - CFL: dt = C / max_cells sum_d (|u_d| + sqrt(3 P_dd/rho)) / dx_d;
  *   - gravity: a = -grad(Phi) by central differences, m += dt rho a,
  *     E += dt (mbar a^T + a mbar^T) with mbar the mean of m before/after.
@@ -46,6 +48,8 @@
 #endif
 
 #define NV 10
+/* maximum number of a-posteriori fallback passes per step */
+#define OG_FALLBACK_PASSES 4
 /* conserved order: rho, m_x, m_y, m_z, E_xx, E_xy, E_xz, E_yy, E_yz, E_zz
  * primitive order: rho, u_x, u_y, u_z, P_xx, P_xy, P_xz, P_yy, P_yz, P_zz   */
 
@@ -531,10 +535,14 @@ int og_step(const og_grid *Gr, const double *U, const double *phi, double dt, do
         for (int k = 0; k < NV; k++) Uc[k] = Unew[k * N + c];
         if (!cell_realizable(Uc)) { bad[c] = 1; nbad++; }
     }
-    if (nbad > 0) {
-        /* flags on the padded grid: a ghost cell carries the flag of its source cell */
-        unsigned char *flag = (unsigned char *)calloc((size_t)NP, 1);
+    /* Each fallback pass adds the cells that are still non-realizable to the tagged set,
+     * so the first-order region grows until the update is realizable (at most
+     * OG_FALLBACK_PASSES passes). */
+    unsigned char *flag = NULL;
+    for (int pass = 0; nbad > 0 && pass < OG_FALLBACK_PASSES; pass++) {
+        if (!flag) flag = (unsigned char *)calloc((size_t)NP, 1);
         if (!flag) { free(bad); return 1; }
+        /* flags on the padded grid: a ghost cell carries the flag of its source cell */
         for (int64_t z = -P.g[2]; z < P.n[2] + P.g[2]; z++)
             for (int64_t y = -P.g[1]; y < P.n[1] + P.g[1]; y++)
                 for (int64_t x = -P.g[0]; x < P.n[0] + P.g[0]; x++) {
@@ -544,10 +552,15 @@ int og_step(const og_grid *Gr, const double *U, const double *phi, double dt, do
                         s[d] = ghost_src(c[d], P.n[d], Gr->bc[2 * d], Gr->bc[2 * d + 1], &mir);
                     flag[pidx(&P, x, y, z)] = bad[(s[2] * P.n[1] + s[1]) * P.n[0] + s[0]];
                 }
-        int rc = step_pass(Gr, U, phi, dt, flag, Unew);
-        free(flag);
-        if (rc) { free(bad); return 1; }
+        if (step_pass(Gr, U, phi, dt, flag, Unew)) { free(flag); free(bad); return 1; }
+        nbad = 0;
+        for (int64_t c = 0; c < N; c++) {
+            double Uc[NV];
+            for (int k = 0; k < NV; k++) Uc[k] = Unew[k * N + c];
+            if (!cell_realizable(Uc) && !bad[c]) { bad[c] = 1; nbad++; }
+        }
     }
+    free(flag);
     free(bad);
     return 0;
 }

@@ -246,11 +246,23 @@ def realizable(U):
     return (U[0] > 0) & (W[4] > 0) & (m2 > 0) & (m3 > 0)
 
 
+FALLBACK_PASSES = 4
+
+
 def step(U, ndim, dx, bc, dt, phi=None):
-    """The step with the a-posteriori first-order fallback (flags frozen from the first pass)."""
+    """The step with the a-posteriori first-order fallback: cells whose update is not
+    realizable are tagged and the step recomputed with first-order faces around them, the
+    tagged set growing for at most FALLBACK_PASSES passes.  The tags are found without
+    gradients and are frozen in the differentiated pass."""
     with torch.no_grad():
-        first = step_pass(U.detach(), ndim, dx, bc, dt, phi)
-        bad = ~realizable(first)
+        out = step_pass(U.detach(), ndim, dx, bc, dt, phi)
+        bad = torch.zeros(U.shape[1:], dtype=torch.bool)
+        for _ in range(FALLBACK_PASSES):
+            new = ~realizable(out) & ~bad
+            if not bool(new.any()):
+                break
+            bad = bad | new
+            out = step_pass(U.detach(), ndim, dx, bc, dt, phi, bad)
     if bool(bad.any()):
         return step_pass(U, ndim, dx, bc, dt, phi, bad)
     return step_pass(U, ndim, dx, bc, dt, phi)

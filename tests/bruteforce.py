@@ -229,11 +229,15 @@ def step(U, ndim, dx, bc, dt, phi=None):
     Un = _step_pass(U, ndim, dx, bc, dt, phi, None)
     nz, ny, nx = Un.shape[1:]
     bad = np.zeros((nz, ny, nx), dtype=bool)
-    for z in range(nz):
-        for y in range(ny):
-            for x in range(nx):
-                bad[z, y, x] = not realizable(Un[:, z, y, x])
-    if bad.any():
+    for _ in range(5):  # the first check plus at most four fallback passes
+        new = np.zeros_like(bad)
+        for z in range(nz):
+            for y in range(ny):
+                for x in range(nx):
+                    new[z, y, x] = (not realizable(Un[:, z, y, x])) and not bad[z, y, x]
+        if not new.any() or _ == 4:
+            break
+        bad |= new
         Un = _step_pass(U, ndim, dx, bc, dt, phi, bad)
     return Un
 
