@@ -68,12 +68,12 @@ template <typename T, int NT> __device__ __forceinline__ T block_max(T v, T *red
 // One sweep of a tube over all its faces: reconstruction, HLL fluxes and the conservative
 // update, chunk by chunk.  src holds U^n; dst receives U^{n+1} (dst may equal src: each
 // cell is updated after the last chunk that reads it).  With FALLBACK, every face that
-// touches a tagged cell takes first-order states.  Without it, cells whose update is not
-// realizable are tagged in sFl and *s_nbad is set.  Returns the thread's maximum
-// signal-speed sum of the new state.
+// touches a cell tagged by an earlier pass (sFl == 2) takes first-order states.  Cells whose
+// update is not realizable and that carry no active tag are tagged (sFl = 1) and *s_nbad
+// is set.  Returns the thread's maximum signal-speed sum of the new state.
 template <typename T, int NT, bool FALLBACK>
 __device__ T tube_pass(const T *src, T *dst, unsigned char *sFl, int n, int cap, T nu, T dtdx, T idx, T *sF,
-                       T *sH, T *sHc, int *s_nbad) {
+                       T *sH, T *sHc, int *s_nbad, int *s_any) {
   const int t = threadIdx.x;
   T smax = T(0);
   for (int b = -1; b <= n; b += NT) {
@@ -85,8 +85,8 @@ __device__ T tube_pass(const T *src, T *dst, unsigned char *sFl, int n, int cap,
       load_w(src, cap, c, n, w0);
       load_w(src, cap, c + 1, n, wp);
       reconstruct(wm, w0, wp, nu, lo, hi);
-      if (FALLBACK) {
-        auto f = [&](int i) { return sFl[min(max(i, 0), n - 1)] != 0; };
+      if (FALLBACK) {  // tags of earlier passes (value 2) are active in this pass
+        auto f = [&](int i) { return sFl[min(max(i, 0), n - 1)] == 2; };
         first_order_faces(f(c - 1), f(c), f(c + 1), w0, lo, hi);
       }
 #pragma unroll
@@ -118,8 +118,11 @@ __device__ T tube_pass(const T *src, T *dst, unsigned char *sFl, int n, int cap,
       }
       cons_to_prim(U, W);
       if (!realizable(W)) {
-        if (!FALLBACK) sFl[cu] = 1;
-        *s_nbad = 1;
+        *s_any = 1;
+        if (sFl[cu] != 2) {  // newly failing cell: tag it for the next pass
+          sFl[cu] = 1;
+          *s_nbad = 1;
+        }
       }
       smax = fmax(smax, (fabs(W[1]) + T(1.7320508075688772) * sqrt_ratio(W[4], W[0])) * idx);
     }
@@ -144,7 +147,7 @@ __global__ void __launch_bounds__(NT) tubes_kernel(TubeArgs<T> a) {
   unsigned char *sFl = reinterpret_cast<unsigned char *>(sHc + NV);  // [cap] fallback tags
   __shared__ T red[NT / 32];
   __shared__ int s_q;
-  __shared__ int s_nbad;
+  __shared__ int s_nbad, s_any;
   const int t = threadIdx.x;
   for (;;) {
     if (t == 0) s_q = atomicAdd(a.queue, 1);
@@ -183,21 +186,26 @@ __global__ void __launch_bounds__(NT) tubes_kernel(TubeArgs<T> a) {
       for (int c = t; c < n; c += NT)
 #pragma unroll
         for (int v = 0; v < NV; v++) sUo[v * cap + c] = sU[v * cap + c];
-      if (t == 0) s_nbad = 0;
+      if (t == 0) { s_nbad = 0; s_any = 0; }
       __syncthreads();
-      T smax = tube_pass<T, NT, false>(sU, sU, sFl, n, cap, nu, dtdx, idx, sF, sH, sHc, &s_nbad);
+      T smax = tube_pass<T, NT, false>(sU, sU, sFl, n, cap, nu, dtdx, idx, sF, sH, sHc, &s_nbad, &s_any);
       sm = block_max<T, NT>(smax, red);  // its barriers also order the carries and s_nbad
-      if (s_nbad) {
-        // a-posteriori fallback: redo the step from U^n with first-order faces at tagged cells
-        if (t == 0) s_nbad = 0;
+      // a-posteriori fallback: redo the step from U^n with first-order faces at every tagged
+      // cell; cells still failing are tagged too (at most kFallbackPasses passes)
+      for (int pass = 1; pass <= kFallbackPasses && s_nbad; pass++) {
         __syncthreads();
-        smax = tube_pass<T, NT, true>(sUo, sU, sFl, n, cap, nu, dtdx, idx, sF, sH, sHc, &s_nbad);
+        if (t == 0) { s_nbad = 0; s_any = 0; }
+        __syncthreads();
+        for (int c = t; c < n; c += NT)
+          if (sFl[c] == 1) sFl[c] = 2;  // tags of earlier passes become active
+        __syncthreads();
+        smax = tube_pass<T, NT, true>(sUo, sU, sFl, n, cap, nu, dtdx, idx, sF, sH, sHc, &s_nbad, &s_any);
         sm = block_max<T, NT>(smax, red);
-        const bool still_bad = s_nbad != 0;
-        for (int c = t; c < n; c += NT) sFl[c] = 0;
-        __syncthreads();
-        if (still_bad) { status = 4; tt = tn; steps++; break; }
       }
+      const bool still_bad = s_any != 0;  // some cell of the last pass is not realizable
+      for (int c = t; c < n; c += NT) sFl[c] = 0;
+      __syncthreads();
+      if (still_bad) { status = 4; tt = tn; steps++; break; }
       tt = tn;
       steps++;
     }

@@ -106,6 +106,7 @@ template <typename T> StepArgs<T> make_args(msh_grid *g) {
   for (int i = 0; i < 6; i++) a.bc[i] = g->bc[i];
   for (int i = 0; i < 3; i++) a.dx[i] = g->dx[i];
   a.zchunk = g->zchunk;
+  a.level = 0;
   return a;
 }
 
@@ -137,10 +138,19 @@ msh_status launch_one_step(msh_grid *g, int ev_slot) {
   else e = launch_step<double>(make_args<double>(g), g->ndim, g->rows, false, g->stream, &nb);
   if (e != cudaSuccess) return fail(MSH_E_CUDA, "step kernel launch: %s", cudaGetErrorString(e));
   if (g->profiling && ev_slot >= 0) CUDA_TRY(cudaEventRecord(g->ev[3 * ev_slot + 1], g->stream));
-  // fallback pass: returns at once unless the step tagged non-realizable cells
-  if (g->prec == MSH_FP32) e = launch_step<float>(make_args<float>(g), g->ndim, g->rows, true, g->stream, nullptr);
-  else e = launch_step<double>(make_args<double>(g), g->ndim, g->rows, true, g->stream, nullptr);
-  if (e != cudaSuccess) return fail(MSH_E_CUDA, "fallback kernel launch: %s", cudaGetErrorString(e));
+  // fallback passes: each returns at once unless the previous pass tagged new cells
+  for (int level = 1; level <= kFallbackPasses; level++) {
+    if (g->prec == MSH_FP32) {
+      StepArgs<float> a = make_args<float>(g);
+      a.level = level;
+      e = launch_step<float>(a, g->ndim, g->rows, true, g->stream, nullptr);
+    } else {
+      StepArgs<double> a = make_args<double>(g);
+      a.level = level;
+      e = launch_step<double>(a, g->ndim, g->rows, true, g->stream, nullptr);
+    }
+    if (e != cudaSuccess) return fail(MSH_E_CUDA, "fallback kernel launch: %s", cudaGetErrorString(e));
+  }
   e = launch_finalize(g->ctrl, g->part, nb, 0, g->stream);
   if (e != cudaSuccess) return fail(MSH_E_CUDA, "finalize launch: %s", cudaGetErrorString(e));
   if (g->profiling && ev_slot >= 0) CUDA_TRY(cudaEventRecord(g->ev[3 * ev_slot + 2], g->stream));

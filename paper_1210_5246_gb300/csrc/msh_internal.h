@@ -5,13 +5,17 @@
 
 namespace msh {
 
+// A-posteriori fallback passes per step (see the step kernels).
+constexpr int kFallbackPasses = 4;
+
 // Device-resident time control of a grid.  The step kernels read dt and the buffer
 // parity from here; the finalize kernel writes the next dt, so a run needs no host
 // round trip per step.
 struct Ctrl {
   double t, t_next, t_end, dt, dt_max, dt_cfl, cfl, dt_last;
   int64_t step, max_step, first_bad, hist_cap, hist_base;
-  int32_t done, status, realizable, nbad;  // nbad: cells tagged for the fallback this step
+  int32_t done, status, realizable, pad;
+  int32_t nbad[kFallbackPasses + 1];  // cells newly tagged by pass p of this step (p = 0: the step)
   double totals[10];
   double *hist;
 };
@@ -28,7 +32,8 @@ template <typename T> struct StepArgs {
   const T *acc;         // gravitational acceleration -grad Phi, [3][N], or nullptr
   Ctrl *ctrl;
   Partial *part;
-  int32_t *flags;       // per cell: step tag of a failed second-order update (fallback)
+  int32_t *flags;       // per cell: 8 * step tag + pass of a failed update (fallback)
+  int level;            // 0: the step; p >= 1: fallback pass p
   int nx, ny, nz;
   int bc[6];
   double dx[3];

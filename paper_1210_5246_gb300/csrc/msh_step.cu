@@ -106,9 +106,11 @@ __device__ __forceinline__ void finish_cell(const StepArgs<T> &a, const T *__res
   cons_to_prim(Un, W);
   if (!realizable(W)) {
     bad = min(bad, (long long)c);
-    if (!RETRY) {  // tag the cell for the fallback pass
-      a.flags[c] = tag;
-      atomicAdd(&a.ctrl->nbad, 1);
+    // tag the cell for the next fallback pass (a cell tagged by an earlier pass keeps its tag)
+    const int32_t f = a.flags[c];
+    if (!((f >> 3) == tag && (f & 7) < a.level)) {
+      a.flags[c] = tag * 8 + a.level;
+      atomicAdd(&a.ctrl->nbad[a.level], 1);
     }
   }
   smax = fmax(smax, speed_sum<T, NDIM>(W, idx, idy, idz));
@@ -122,15 +124,22 @@ __device__ __forceinline__ void write_partial(const Acc<T> &diag, T smax, long l
   block_partial<NT>(d, (double)smax, bad, out);
 }
 
+// A cell takes first-order faces in fallback pass `level` if an earlier pass of this step
+// tagged it.  Tags written during the current pass are ignored, so every thread block of
+// a pass sees the same tagged set.
+__device__ __forceinline__ bool tagged(int32_t f, int32_t tag, int level) {
+  return (f >> 3) == tag && (f & 7) < level;
+}
+
 // ------------------------------------------------------------------ 1D kernel
 template <typename T, bool RETRY>
 __global__ void __launch_bounds__(kTile1D) step1d_kernel(StepArgs<T> a) {
   constexpr int B = kTile1D, SXX = B + 2;
   const Ctrl *ctrl = a.ctrl;
   if (ctrl->done) return;
-  if (RETRY && ctrl->nbad == 0) return;
+  if (RETRY && ctrl->nbad[a.level - 1] == 0) return;
   const int64_t step = ctrl->step;
-  const int32_t tag = (int32_t)(step & 0x3fffffff) + 1;
+  const int32_t tag = (int32_t)(step & 0x0fffffff) + 1;
   __shared__ unsigned char sFl[RETRY ? SXX : 1];
   const T *__restrict__ Us = a.U[step & 1];
   T *__restrict__ Ud = a.U[(step + 1) & 1];
@@ -154,7 +163,7 @@ __global__ void __launch_bounds__(kTile1D) step1d_kernel(StepArgs<T> a) {
     cons_to_prim(U, W);
 #pragma unroll
     for (int k = 0; k < NV; k++) sW[k][i] = W[k];
-    if (RETRY) sFl[i] = (a.flags[xx] == tag);
+    if (RETRY) sFl[i] = tagged(a.flags[xx], tag, a.level);
   }
   __syncthreads();
   T wm[NV], w0[NV], wp[NV], lo[NV], hi[NV], F[NV];
@@ -205,9 +214,9 @@ __global__ void __launch_bounds__(32 * BY, (BY <= 8 ? 2 : 1)) step_tile_kernel(S
   constexpr int PL = NV * SY * SX;
   const Ctrl *ctrl = a.ctrl;
   if (ctrl->done) return;
-  if (RETRY && ctrl->nbad == 0) return;
+  if (RETRY && ctrl->nbad[a.level - 1] == 0) return;
   const int64_t step = ctrl->step;
-  const int32_t tag = (int32_t)(step & 0x3fffffff) + 1;
+  const int32_t tag = (int32_t)(step & 0x0fffffff) + 1;
   // fallback tags of the staged cells (fallback pass only)
   __shared__ unsigned char sFl[RETRY ? NPL : 1][RETRY ? SY : 1][RETRY ? SX : 1];
   const T *__restrict__ Us = a.U[step & 1];
@@ -252,7 +261,7 @@ __global__ void __launch_bounds__(32 * BY, (BY <= 8 ? 2 : 1)) step_tile_kernel(S
       cons_to_prim(U, W);
 #pragma unroll
       for (int k = 0; k < NV; k++) dst[(k * SY + qy) * SX + qx] = W[k];
-      if (RETRY) sFl[buf][qy][qx] = (a.flags[c] == tag);
+      if (RETRY) sFl[buf][qy][qx] = tagged(a.flags[c], tag, a.level);
     }
   };
   auto fl = [&](int buf, int qy, int qx) -> bool { return RETRY ? sFl[RETRY ? buf : 0][RETRY ? qy : 0][RETRY ? qx : 0] != 0 : false; };
@@ -491,7 +500,7 @@ __global__ void __launch_bounds__(kFinalizeThreads) finalize_kernel(Ctrl *ctrl, 
     c->done = 1;
     return;
   }
-  c->nbad = 0;
+  for (int p = 0; p <= kFallbackPasses; p++) c->nbad[p] = 0;
   const int64_t hi_ = c->step - c->hist_base;
   if (c->hist != nullptr && hi_ >= 0 && hi_ < c->hist_cap) c->hist[hi_] = c->dt;
   c->dt_last = c->dt;
@@ -511,7 +520,7 @@ __global__ void run_start_kernel(Ctrl *c, double t_end, int64_t max_steps, doubl
   c->dt_max = dt_max;
   c->done = 0;
   c->status = 0;
-  c->nbad = 0;
+  for (int p = 0; p <= kFallbackPasses; p++) c->nbad[p] = 0;
   plan(c);
 }
 

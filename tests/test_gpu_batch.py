@@ -136,3 +136,29 @@ def test_full_workload_4096_tubes(msh, oracle):
         assert abs(int(steps[k]) - so) <= 1
         assert_fp32(b.tube(W, k), oracle.cons_to_prim(Uo), what=f"tube {k}")
     b.close()
+
+
+def test_iterated_fallback_tube_fp64(msh, oracle):
+    """Tube 3519 of the batched workload (density ratio 33, P_xx = 0.016 on the light side)
+    needs more than one fallback pass: the batch kernel and the 1D grid kernel both match
+    the oracle run to t_end."""
+    from paper_1210_5246_gb300 import inputs
+    full = inputs.tubes()
+    k = 3519
+    tubes = _random_tubes([int(full.length[k])], seed=48)
+    tubes.WL[0], tubes.WR[0] = full.WL[k], full.WR[k]
+    Uo, so, to, rc = _oracle_tube(oracle, tubes, 0)
+    assert rc == 0 and to == tubes.t_end
+    b = msh.Batch(tubes.length, tubes.WL, tubes.WR, tubes.t_end, tubes.cfl, msh.FP64)
+    b.run(threads=128)
+    steps, t, _ = b.info()
+    assert steps[0] == so and t[0] == to
+    assert_fp64(b.tube(b.get_state(), 0), Uo, what="batch tube 3519")
+    b.close()
+    n = int(tubes.length[0])
+    g = msh.Grid((n,), (0.0,), (1.0,), ((1, 1),), tubes.cfl, msh.FP64)
+    g.set_state(tubes.initial_tube(0), msh.PRIMITIVE)
+    ns, tg = g.run(tubes.t_end)
+    assert ns == so and tg == to
+    assert_fp64(g.get_state(), Uo.reshape(10, 1, 1, n), what="grid tube 3519")
+    g.close()
