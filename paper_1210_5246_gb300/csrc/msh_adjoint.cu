@@ -1,0 +1,569 @@
+// msh_adjoint.cu -- discrete adjoint of the step (msh_adjoint_run).
+//
+// Reverse step n maps lam^{n+1} = dL/dU^{n+1} to lam^n = dL/dU^n for the frozen time step
+// dt_n, with every branch of the forward step frozen (MC limiter selection, face-state
+// fallback, HLL branch and min/max of the signal speeds, a-posteriori fallback tags):
+//   1. lam* = G^T lam^{n+1}           gravity source (linear in U* for a fixed -grad Phi)
+//   2. per direction d:
+//      face pass   F^bar = (dt/dx)(lam*_j - lam*_{j-1}) through the HLL flux at face j-1/2
+//                  -> adjoints of the face states hi_{j-1}, lo_j
+//      cell pass   reconstruction of cell j reversed -> adjoints of W_{j-1}, W_j, W_{j+1}
+//      gather      summed onto the padded primitive adjoint (deterministic, no atomics)
+//   3. fold        lam^n_i = lam*_i + (dW/dU)^T W^bar_i, plus the ghost images of cell i
+//                  (periodic wrap, outflow copy, reflect mirror with its sign flips)
+// Forward states are checkpointed every K steps and recomputed segment by segment during
+// the reverse sweep; the forward step is re-run before its reverse only when it tagged
+// cells for the a-posteriori fallback, to restore its tags.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include "../../include/msh.h"
+#include "msh_adjoint.cuh"
+#include "msh_device.cuh"
+#include "msh_internal.h"
+
+namespace msh {
+
+template <typename T> struct AdjArgs {
+  const T *U;          // U^n [NV][N]
+  const T *lam;        // lam^{n+1}
+  T *ls;               // lam*
+  T *out;              // lam^n
+  const T *acc;        // -grad Phi [3][N] or nullptr
+  const int32_t *flags;
+  const Ctrl *ctrl;    // fallback pass counters of the re-run forward step
+  int32_t tag;
+  T *HB, *LB;          // face-state adjoints [NV][Next], local frame of the sweep
+  T *GM, *G0, *GP;     // reconstruction adjoints to cells j-1, j, j+1 [NV][Next], global order
+  T *Wb;               // primitive adjoint on the padded grid [NV][Npad]
+  int n[3], ndim, bc[6];
+  double dx[3], dt;
+  int d;               // sweep direction
+};
+
+__device__ __forceinline__ int last_pass(const Ctrl *c) {
+  int p = 0;
+  for (int q = 1; q <= kFallbackPasses; q++) {
+    if (c->nbad[q - 1] > 0) p = q;
+    else break;
+  }
+  return p;
+}
+
+// extended index along d: cells j in [-1, n_d] along d, interior along the other dims
+struct ExtIdx {
+  int n[3], d;
+  __device__ __forceinline__ size_t count() const {
+    return (size_t)(n[0] + (d == 0 ? 2 : 0)) * (n[1] + (d == 1 ? 2 : 0)) * (n[2] + (d == 2 ? 2 : 0));
+  }
+  __device__ __forceinline__ void coords(size_t e, int (&c)[3]) const {
+    const int m0 = n[0] + (d == 0 ? 2 : 0), m1 = n[1] + (d == 1 ? 2 : 0);
+    c[0] = (int)(e % m0);
+    c[1] = (int)((e / m0) % m1);
+    c[2] = (int)(e / ((size_t)m0 * m1));
+    c[d] -= 1;
+  }
+  __device__ __forceinline__ size_t index(const int (&c)[3]) const {
+    const int m0 = n[0] + (d == 0 ? 2 : 0), m1 = n[1] + (d == 1 ? 2 : 0);
+    int q[3] = {c[0], c[1], c[2]};
+    q[d] += 1;
+    return ((size_t)q[2] * m1 + q[1]) * m0 + q[0];
+  }
+};
+
+// padded index: 2 ghost layers on every active dim
+__device__ __forceinline__ size_t pad_index(const int (&n)[3], int ndim, const int (&c)[3]) {
+  const int g0 = 2, g1 = ndim > 1 ? 2 : 0, g2 = ndim > 2 ? 2 : 0;
+  const int p0 = n[0] + 2 * g0, p1 = n[1] + 2 * g1;
+  return ((size_t)(c[2] + g2) * p1 + (c[1] + g1)) * p0 + (c[0] + g0);
+}
+
+// conserved state, mirror mask and tag of a (possibly ghost) cell
+template <typename T>
+__device__ __forceinline__ size_t load_cell(const AdjArgs<T> &a, const int (&c)[3], T (&U)[NV], unsigned &flip) {
+  int m[3];
+  flip = 0u;
+  for (int e = 0; e < 3; e++) {
+    if (e < a.ndim) {
+      bool mir;
+      m[e] = map_index(c[e], a.n[e], a.bc[2 * e], a.bc[2 * e + 1], mir);
+      if (mir) flip ^= flip_mask(e);
+    } else {
+      m[e] = 0;
+    }
+  }
+  const size_t N = (size_t)a.n[0] * a.n[1] * a.n[2];
+  const size_t idx = ((size_t)m[2] * a.n[1] + m[1]) * a.n[0] + m[0];
+#pragma unroll
+  for (int k = 0; k < NV; k++) {
+    const T v = a.U[k * N + idx];
+    U[k] = ((flip >> k) & 1u) ? -v : v;
+  }
+  return idx;
+}
+
+template <typename T, int D>
+__device__ __forceinline__ void local_w(const AdjArgs<T> &a, int (&c)[3], int j, T (&w)[NV], bool &tagged_cell,
+                                        int pass) {
+  c[D] = j;
+  T U[NV], W[NV];
+  unsigned flip;
+  const size_t idx = load_cell(a, c, U, flip);
+  cons_to_prim(U, W);
+#pragma unroll
+  for (int k = 0; k < NV; k++) w[k] = W[Frame<D>::g(k)];
+  const int32_t f = a.flags[idx];
+  tagged_cell = (f >> 3) == a.tag && (f & 7) < pass;
+}
+
+template <typename T>
+__global__ void adj_lamstar_kernel(AdjArgs<T> a) {
+  const size_t N = (size_t)a.n[0] * a.n[1] * a.n[2];
+  for (size_t c = (size_t)blockIdx.x * blockDim.x + threadIdx.x; c < N; c += (size_t)gridDim.x * blockDim.x) {
+    T lam[NV], ls[NV];
+#pragma unroll
+    for (int k = 0; k < NV; k++) lam[k] = a.lam[k * N + c];
+    if (a.acc) {
+      T g[3] = {a.acc[c], a.acc[N + c], a.acc[2 * N + c]};
+      gravity_vjp(g, (T)a.dt, lam, ls);
+    } else {
+#pragma unroll
+      for (int k = 0; k < NV; k++) ls[k] = lam[k];
+    }
+#pragma unroll
+    for (int k = 0; k < NV; k++) a.ls[k * N + c] = ls[k];
+  }
+}
+
+// face pass: thread per extended cell j, handling the face j-1/2
+template <typename T, int D>
+__global__ void adj_face_kernel(AdjArgs<T> a) {
+  const ExtIdx X{{a.n[0], a.n[1], a.n[2]}, D};
+  const size_t Ne = X.count();
+  const size_t N = (size_t)a.n[0] * a.n[1] * a.n[2];
+  const int pass = last_pass(a.ctrl);
+  const int nd = a.n[D];
+  const T nu = (T)(0.5 * a.dt / a.dx[D]);
+  const T dtdx = (T)(a.dt / a.dx[D]);
+  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < Ne; e += (size_t)gridDim.x * blockDim.x) {
+    int c[3];
+    X.coords(e, c);
+    const int j = c[D];
+    if (j == nd) {  // no face above the last ghost cell
+      int cc[3] = {c[0], c[1], c[2]};
+#pragma unroll
+      for (int k = 0; k < NV; k++) a.HB[k * Ne + X.index(cc)] = T(0);
+    }
+    if (j < 0) {
+#pragma unroll
+      for (int k = 0; k < NV; k++) a.LB[k * Ne + e] = T(0);
+      continue;
+    }
+    // face states hi_{j-1} and lo_j
+    T w[4][NV];
+    bool f[4];
+    for (int o = 0; o < 4; o++) local_w<T, D>(a, c, j - 2 + o, w[o], f[o], pass);
+    c[D] = j;
+    T lo0[NV], hi0[NV], lo1[NV], hi1[NV];
+    reconstruct(w[0], w[1], w[2], nu, lo0, hi0);  // cell j-1
+    first_order_faces(f[0], f[1], f[2], w[1], lo0, hi0);
+    reconstruct(w[1], w[2], w[3], nu, lo1, hi1);  // cell j
+    first_order_faces(f[1], f[2], f[3], w[2], lo1, hi1);
+    // flux adjoint: U*_{j-1} -= (dt/dx) F, U*_j += (dt/dx) F (ghost cells are not updated)
+    T Fb[NV];
+    const size_t cj = ((size_t)c[2] * a.n[1] + c[1]) * a.n[0] + c[0];
+    int cm[3] = {c[0], c[1], c[2]};
+    cm[D] = j - 1;
+    const size_t cjm = ((size_t)cm[2] * a.n[1] + cm[1]) * a.n[0] + cm[0];
+#pragma unroll
+    for (int k = 0; k < NV; k++) {
+      const int gk = Frame<D>::g(k);
+      const T lj = (j < nd) ? a.ls[gk * N + cj] : T(0);
+      const T ljm = (j >= 1) ? a.ls[gk * N + cjm] : T(0);
+      Fb[k] = dtdx * (lj - ljm);
+    }
+    T hb[NV], lb[NV];
+#pragma unroll
+    for (int k = 0; k < NV; k++) { hb[k] = T(0); lb[k] = T(0); }
+    hll_vjp(hi0, lo1, Fb, hb, lb);
+    const size_t em = X.index(cm);
+#pragma unroll
+    for (int k = 0; k < NV; k++) {
+      a.HB[k * Ne + em] = hb[k];
+      a.LB[k * Ne + e] = lb[k];
+    }
+  }
+}
+
+// cell pass: thread per extended cell j, reverse of its reconstruction
+template <typename T, int D>
+__global__ void adj_cell_kernel(AdjArgs<T> a) {
+  const ExtIdx X{{a.n[0], a.n[1], a.n[2]}, D};
+  const size_t Ne = X.count();
+  const int pass = last_pass(a.ctrl);
+  const T nu = (T)(0.5 * a.dt / a.dx[D]);
+  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < Ne; e += (size_t)gridDim.x * blockDim.x) {
+    int c[3];
+    X.coords(e, c);
+    const int j = c[D];
+    T wm[NV], w0[NV], wp[NV];
+    bool fm, f0, fp;
+    local_w<T, D>(a, c, j - 1, wm, fm, pass);
+    local_w<T, D>(a, c, j, w0, f0, pass);
+    local_w<T, D>(a, c, j + 1, wp, fp, pass);
+    T lb[NV], hb[NV], gm[NV], g0[NV], gp[NV];
+#pragma unroll
+    for (int k = 0; k < NV; k++) {
+      lb[k] = a.LB[k * Ne + e];
+      hb[k] = a.HB[k * Ne + e];
+      gm[k] = g0[k] = gp[k] = T(0);
+    }
+    reconstruct_vjp(wm, w0, wp, nu, fm, f0, fp, lb, hb, gm, g0, gp);
+#pragma unroll
+    for (int k = 0; k < NV; k++) {
+      const int gk = Frame<D>::g(k);
+      a.GM[gk * Ne + e] = gm[k];
+      a.G0[gk * Ne + e] = g0[k];
+      a.GP[gk * Ne + e] = gp[k];
+    }
+  }
+}
+
+// gather: padded positions p in [-2, n_d+1] along d (interior along the other dims)
+template <typename T, int D>
+__global__ void adj_gather_kernel(AdjArgs<T> a) {
+  const ExtIdx X{{a.n[0], a.n[1], a.n[2]}, D};
+  const size_t Ne = X.count();
+  int m[3] = {a.n[0], a.n[1], a.n[2]};
+  m[D] += 4;
+  const size_t Ng = (size_t)m[0] * m[1] * m[2];
+  int np[3] = {a.n[0], a.n[1], a.n[2]};
+  int g[3] = {2, a.ndim > 1 ? 2 : 0, a.ndim > 2 ? 2 : 0};
+  const size_t Npad = (size_t)(np[0] + 2 * g[0]) * (np[1] + 2 * g[1]) * (np[2] + 2 * g[2]);
+  const int nd = a.n[D];
+  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < Ng; e += (size_t)gridDim.x * blockDim.x) {
+    int c[3] = {(int)(e % m[0]), (int)((e / m[0]) % m[1]), (int)(e / ((size_t)m[0] * m[1]))};
+    c[D] -= 2;
+    const int p = c[D];
+    T s[NV];
+#pragma unroll
+    for (int k = 0; k < NV; k++) s[k] = T(0);
+    int q[3] = {c[0], c[1], c[2]};
+    if (p - 1 >= -1 && p - 1 <= nd) {
+      q[D] = p - 1;
+      const size_t i = X.index(q);
+#pragma unroll
+      for (int k = 0; k < NV; k++) s[k] += a.GP[k * Ne + i];
+    }
+    if (p >= -1 && p <= nd) {
+      q[D] = p;
+      const size_t i = X.index(q);
+#pragma unroll
+      for (int k = 0; k < NV; k++) s[k] += a.G0[k * Ne + i];
+    }
+    if (p + 1 >= -1 && p + 1 <= nd) {
+      q[D] = p + 1;
+      const size_t i = X.index(q);
+#pragma unroll
+      for (int k = 0; k < NV; k++) s[k] += a.GM[k * Ne + i];
+    }
+    const size_t pi = pad_index(a.n, a.ndim, c);
+#pragma unroll
+    for (int k = 0; k < NV; k++) a.Wb[k * Npad + pi] += s[k];
+  }
+}
+
+// fold: lam^n_i = lam*_i + (dW/dU)^T Wb_i + images of ghost cells whose source is i
+template <typename T>
+__global__ void adj_fold_kernel(AdjArgs<T> a) {
+  const size_t N = (size_t)a.n[0] * a.n[1] * a.n[2];
+  int g[3] = {2, a.ndim > 1 ? 2 : 0, a.ndim > 2 ? 2 : 0};
+  const size_t Npad = (size_t)(a.n[0] + 2 * g[0]) * (a.n[1] + 2 * g[1]) * (a.n[2] + 2 * g[2]);
+  for (size_t ci = (size_t)blockIdx.x * blockDim.x + threadIdx.x; ci < N; ci += (size_t)gridDim.x * blockDim.x) {
+    int c[3] = {(int)(ci % a.n[0]), (int)((ci / a.n[0]) % a.n[1]), (int)(ci / ((size_t)a.n[0] * a.n[1]))};
+    T U[NV], Ub[NV], Wb[NV];
+#pragma unroll
+    for (int k = 0; k < NV; k++) {
+      U[k] = a.U[k * N + ci];
+      Ub[k] = T(0);
+    }
+    size_t pi = pad_index(a.n, a.ndim, c);
+#pragma unroll
+    for (int k = 0; k < NV; k++) Wb[k] = a.Wb[k * Npad + pi];
+    cons_to_prim_vjp(U, Wb, Ub);
+    for (int d = 0; d < a.ndim; d++) {
+      const int nd = a.n[d];
+      const int ghosts[4] = {-2, -1, nd, nd + 1};
+      for (int gi = 0; gi < 4; gi++) {
+        bool mir;
+        const int src = map_index(ghosts[gi], nd, a.bc[2 * d], a.bc[2 * d + 1], mir);
+        if (src != c[d]) continue;
+        int q[3] = {c[0], c[1], c[2]};
+        q[d] = ghosts[gi];
+        const size_t qi = pad_index(a.n, a.ndim, q);
+        const unsigned flip = mir ? flip_mask(d) : 0u;
+        T Ug[NV], Ugb[NV], Wgb[NV];
+#pragma unroll
+        for (int k = 0; k < NV; k++) {
+          Ug[k] = ((flip >> k) & 1u) ? -U[k] : U[k];
+          Ugb[k] = T(0);
+          Wgb[k] = a.Wb[k * Npad + qi];
+        }
+        cons_to_prim_vjp(Ug, Wgb, Ugb);
+#pragma unroll
+        for (int k = 0; k < NV; k++) Ub[k] += ((flip >> k) & 1u) ? -Ugb[k] : Ugb[k];
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < NV; k++) a.out[k * N + ci] = a.ls[k * N + ci] + Ub[k];
+  }
+}
+
+// dL/dW0 = (dU/dW)^T dL/dU0 at the primitive initial state W
+template <typename T>
+__global__ void adj_prim_kernel(const T *W, const T *Ub, T *Wb, size_t N) {
+  for (size_t c = (size_t)blockIdx.x * blockDim.x + threadIdx.x; c < N; c += (size_t)gridDim.x * blockDim.x) {
+    T w[NV], ub[NV], wb[NV];
+#pragma unroll
+    for (int k = 0; k < NV; k++) {
+      w[k] = W[k * N + c];
+      ub[k] = Ub[k * N + c];
+      wb[k] = T(0);
+    }
+    prim_to_cons_vjp(w, ub, wb);
+#pragma unroll
+    for (int k = 0; k < NV; k++) Wb[k * N + c] = wb[k];
+  }
+}
+
+// control of the adjoint's forward steps: fixed dt, step tag, optional skip
+__global__ void adj_setup_kernel(Ctrl *c, int64_t step, double dt, const int32_t *had_tags) {
+  c->step = step;
+  c->dt = dt;
+  c->done = had_tags ? (had_tags[step] == 0) : 0;
+  for (int p = 0; p <= kFallbackPasses; p++) c->nbad[p] = 0;
+}
+
+__global__ void adj_record_kernel(const Ctrl *c, int32_t *had_tags, int64_t step) {
+  had_tags[step] = c->nbad[0] > 0;
+}
+
+}  // namespace msh
+
+// ======================================================================= host
+using namespace msh;
+
+namespace {
+
+msh_status afail(msh_status s, const char *fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  set_error_text(buf);
+  return s;
+}
+
+#define A_TRY(expr)                                                                             \
+  do {                                                                                          \
+    cudaError_t e_ = (expr);                                                                    \
+    if (e_ != cudaSuccess) {                                                                    \
+      st = afail(e_ == cudaErrorMemoryAllocation ? MSH_E_NOMEM : MSH_E_CUDA, "%s: %s", #expr,   \
+                 cudaGetErrorString(e_));                                                       \
+      goto done;                                                                                \
+    }                                                                                           \
+  } while (0)
+
+int grid_blocks(size_t n) {
+  const size_t b = (n + 255) / 256;
+  return (int)(b < 4096 ? (b > 0 ? b : 1) : 4096);
+}
+
+template <typename T>
+cudaError_t forward_step(msh_grid *g, Ctrl *ctl, Partial *part, T *src, T *dst, int64_t step, double dt,
+                         const int32_t *had_tags) {
+  adj_setup_kernel<<<1, 1, 0, g->stream>>>(ctl, step, dt, had_tags);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  StepArgs<T> a;
+  a.U[step & 1] = src;
+  a.U[(step + 1) & 1] = dst;
+  a.acc = (const T *)g->acc;
+  a.ctrl = ctl;
+  a.part = part;
+  a.flags = g->flags;
+  a.nx = (int)g->n[0];
+  a.ny = (int)g->n[1];
+  a.nz = (int)g->n[2];
+  for (int i = 0; i < 6; i++) a.bc[i] = g->bc[i];
+  for (int i = 0; i < 3; i++) a.dx[i] = g->dx[i];
+  a.zchunk = g->zchunk;
+  for (int level = 0; level <= kFallbackPasses; level++) {
+    a.level = level;
+    e = launch_step<T>(a, g->ndim, g->rows, level > 0, g->stream, nullptr);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+template <typename T>
+msh_status adjoint_impl(msh_grid *g, const void *U0, int64_t nsteps, const double *dts, int K, const void *lamN,
+                        void *lam0, int where, int kind) {
+  msh_status st = MSH_OK;
+  const size_t N = g->N;
+  const size_t S = N * NV * sizeof(T);
+  const cudaMemcpyKind in_kind = where == MSH_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+  const cudaMemcpyKind out_kind = where == MSH_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+  const int64_t nck = nsteps > 0 ? (nsteps + K - 1) / K : 1;
+  size_t Ne_max = 0;
+  for (int d = 0; d < g->ndim; d++) Ne_max = std::max(Ne_max, N / g->n[d] * (g->n[d] + 2));
+  size_t Npad = 1;
+  for (int d = 0; d < 3; d++) Npad *= (size_t)(g->n[d] + (d < g->ndim ? 4 : 0));
+  const int nb = std::max(step_blocks<T>(g->ndim, g->rows, (int)g->n[0], (int)g->n[1], (int)g->n[2], g->zchunk),
+                          1);
+  T *ck = nullptr, *seg = nullptr, *la = nullptr, *lb = nullptr, *ls = nullptr, *scratch = nullptr;
+  T *HB = nullptr, *LB = nullptr, *GM = nullptr, *G0 = nullptr, *GP = nullptr, *Wb = nullptr, *W0 = nullptr;
+  Ctrl *ctl = nullptr;
+  Partial *part = nullptr;
+  int32_t *had = nullptr;
+  A_TRY(cudaMalloc(&ck, S * nck));
+  A_TRY(cudaMalloc(&seg, S * (size_t)K));
+  A_TRY(cudaMalloc(&la, S));
+  A_TRY(cudaMalloc(&lb, S));
+  A_TRY(cudaMalloc(&ls, S));
+  A_TRY(cudaMalloc(&scratch, S));
+  A_TRY(cudaMalloc(&HB, Ne_max * NV * sizeof(T)));
+  A_TRY(cudaMalloc(&LB, Ne_max * NV * sizeof(T)));
+  A_TRY(cudaMalloc(&GM, Ne_max * NV * sizeof(T)));
+  A_TRY(cudaMalloc(&G0, Ne_max * NV * sizeof(T)));
+  A_TRY(cudaMalloc(&GP, Ne_max * NV * sizeof(T)));
+  A_TRY(cudaMalloc(&Wb, Npad * NV * sizeof(T)));
+  A_TRY(cudaMalloc(&ctl, sizeof(Ctrl)));
+  A_TRY(cudaMalloc(&part, sizeof(Partial) * (size_t)nb));
+  A_TRY(cudaMalloc(&had, sizeof(int32_t) * (size_t)std::max<int64_t>(nsteps, 1)));
+  A_TRY(cudaMemcpyAsync(ctl, g->hctrl, sizeof(Ctrl), cudaMemcpyHostToDevice, g->stream));
+  // fallback tags are step numbers: start from a clean slate (and leave one behind)
+  A_TRY(cudaMemsetAsync(g->flags, 0, N * sizeof(int32_t), g->stream));
+  // initial state (primitive input converted on the device)
+  A_TRY(cudaMemcpyAsync(ck, U0, S, in_kind, g->stream));
+  if (kind == MSH_PRIMITIVE) {
+    A_TRY(cudaMalloc(&W0, S));
+    A_TRY(cudaMemcpyAsync(W0, ck, S, cudaMemcpyDeviceToDevice, g->stream));
+    A_TRY(launch_convert<T>(ck, N, 0, g->stream));
+  }
+  // forward sweep: checkpoints every K steps, record which steps tagged fallback cells
+  {
+    T *cur = ck, *nxt = scratch;
+    A_TRY(cudaMemcpyAsync(seg, ck, S, cudaMemcpyDeviceToDevice, g->stream));
+    cur = seg;
+    for (int64_t s = 0; s < nsteps; s++) {
+      T *dst = (cur == seg) ? scratch : seg;
+      A_TRY(forward_step<T>(g, ctl, part, cur, dst, s, dts[s], nullptr));
+      adj_record_kernel<<<1, 1, 0, g->stream>>>(ctl, had, s);
+      A_TRY(cudaGetLastError());
+      cur = dst;
+      if ((s + 1) % K == 0 && s + 1 < nsteps)
+        A_TRY(cudaMemcpyAsync(ck + (size_t)((s + 1) / K) * N * NV, cur, S, cudaMemcpyDeviceToDevice, g->stream));
+    }
+    (void)nxt;
+  }
+  // reverse sweep
+  A_TRY(cudaMemcpyAsync(la, lamN, S, in_kind, g->stream));
+  for (int64_t sg = nck - 1; sg >= 0 && nsteps > 0; sg--) {
+    const int64_t n0 = sg * K, n1 = std::min<int64_t>(n0 + K, nsteps);
+    // recompute the segment's states U^{n0} .. U^{n1-1}
+    A_TRY(cudaMemcpyAsync(seg, ck + (size_t)sg * N * NV, S, cudaMemcpyDeviceToDevice, g->stream));
+    for (int64_t n = n0; n + 1 < n1; n++)
+      A_TRY(forward_step<T>(g, ctl, part, seg + (size_t)(n - n0) * N * NV, seg + (size_t)(n - n0 + 1) * N * NV, n,
+                            dts[n], nullptr));
+    for (int64_t n = n1 - 1; n >= n0; n--) {
+      T *Un = seg + (size_t)(n - n0) * N * NV;
+      // restore the fallback tags of step n (a no-op unless it tagged cells)
+      A_TRY(forward_step<T>(g, ctl, part, Un, scratch, n, dts[n], had));
+      AdjArgs<T> a;
+      a.U = Un;
+      a.lam = la;
+      a.ls = ls;
+      a.out = lb;
+      a.acc = (const T *)g->acc;
+      a.flags = g->flags;
+      a.ctrl = ctl;
+      a.tag = (int32_t)(n & 0x0fffffff) + 1;
+      a.HB = HB;
+      a.LB = LB;
+      a.GM = GM;
+      a.G0 = G0;
+      a.GP = GP;
+      a.Wb = Wb;
+      for (int i = 0; i < 3; i++) {
+        a.n[i] = (int)g->n[i];
+        a.dx[i] = g->dx[i];
+      }
+      a.ndim = g->ndim;
+      for (int i = 0; i < 6; i++) a.bc[i] = g->bc[i];
+      a.dt = dts[n];
+      A_TRY(cudaMemsetAsync(Wb, 0, Npad * NV * sizeof(T), g->stream));
+      adj_lamstar_kernel<T><<<grid_blocks(N), 256, 0, g->stream>>>(a);
+      A_TRY(cudaGetLastError());
+      for (int d = 0; d < g->ndim; d++) {
+        a.d = d;
+        const size_t Ne = N / g->n[d] * (g->n[d] + 2);
+        const size_t Ng = N / g->n[d] * (g->n[d] + 4);
+        if (d == 0) {
+          adj_face_kernel<T, 0><<<grid_blocks(Ne), 256, 0, g->stream>>>(a);
+          adj_cell_kernel<T, 0><<<grid_blocks(Ne), 256, 0, g->stream>>>(a);
+          adj_gather_kernel<T, 0><<<grid_blocks(Ng), 256, 0, g->stream>>>(a);
+        } else if (d == 1) {
+          adj_face_kernel<T, 1><<<grid_blocks(Ne), 256, 0, g->stream>>>(a);
+          adj_cell_kernel<T, 1><<<grid_blocks(Ne), 256, 0, g->stream>>>(a);
+          adj_gather_kernel<T, 1><<<grid_blocks(Ng), 256, 0, g->stream>>>(a);
+        } else {
+          adj_face_kernel<T, 2><<<grid_blocks(Ne), 256, 0, g->stream>>>(a);
+          adj_cell_kernel<T, 2><<<grid_blocks(Ne), 256, 0, g->stream>>>(a);
+          adj_gather_kernel<T, 2><<<grid_blocks(Ng), 256, 0, g->stream>>>(a);
+        }
+        A_TRY(cudaGetLastError());
+      }
+      adj_fold_kernel<T><<<grid_blocks(N), 256, 0, g->stream>>>(a);
+      A_TRY(cudaGetLastError());
+      std::swap(la, lb);
+    }
+  }
+  if (kind == MSH_PRIMITIVE) {
+    adj_prim_kernel<T><<<grid_blocks(N), 256, 0, g->stream>>>(W0, la, lb, N);
+    A_TRY(cudaGetLastError());
+    std::swap(la, lb);
+  }
+  A_TRY(cudaMemcpyAsync(lam0, la, S, out_kind, g->stream));
+  A_TRY(cudaStreamSynchronize(g->stream));
+done:
+  cudaMemsetAsync(g->flags, 0, N * sizeof(int32_t), g->stream);
+  cudaStreamSynchronize(g->stream);
+  for (void *p : {(void *)ck, (void *)seg, (void *)la, (void *)lb, (void *)ls, (void *)scratch, (void *)HB,
+                  (void *)LB, (void *)GM, (void *)G0, (void *)GP, (void *)Wb, (void *)W0, (void *)ctl,
+                  (void *)part, (void *)had})
+    if (p) cudaFree(p);
+  return st;
+}
+
+}  // namespace
+
+extern "C" msh_status msh_adjoint_run(msh_grid *g, const void *U0, int64_t nsteps, const double *dt_sched, int32_t K,
+                                      const void *dL_dUN, void *dL_dU0, int32_t where, int32_t kind) {
+  clear_error();
+  if (!g || !U0 || !dL_dUN || !dL_dU0) return afail(MSH_E_INVALID_ARG, "null argument");
+  if (nsteps < 0 || (nsteps > 0 && !dt_sched)) return afail(MSH_E_INVALID_ARG, "bad nsteps or dt schedule");
+  if (K < 1) return afail(MSH_E_INVALID_ARG, "checkpoint interval K must be >= 1");
+  if (where != MSH_HOST && where != MSH_DEVICE) return afail(MSH_E_INVALID_ARG, "bad where");
+  if (kind != MSH_CONSERVED && kind != MSH_PRIMITIVE) return afail(MSH_E_INVALID_ARG, "bad kind");
+  for (int64_t s = 0; s < nsteps; s++)
+    if (!(dt_sched[s] > 0.0) || !std::isfinite(dt_sched[s]))
+      return afail(MSH_E_INVALID_ARG, "dt_sched[%lld] must be finite and > 0", (long long)s);
+  if (g->prec == MSH_FP32)
+    return adjoint_impl<float>(g, U0, nsteps, dt_sched, K, dL_dUN, dL_dU0, where, kind);
+  return adjoint_impl<double>(g, U0, nsteps, dt_sched, K, dL_dUN, dL_dU0, where, kind);
+}

@@ -55,39 +55,6 @@ constexpr int kGraphSteps = 16;
 
 }  // namespace
 
-struct msh_grid {
-  int ndim = 0;
-  int64_t n[3] = {1, 1, 1};
-  double lo[3] = {0, 0, 0}, hi[3] = {1, 1, 1}, dx[3] = {1, 1, 1};
-  int32_t bc[6] = {0, 0, 0, 0, 0, 0};
-  int prec = MSH_FP64;
-  double cfl = 0.5;
-  size_t N = 0;           // cells
-  size_t esize = 8;       // bytes per element
-  cudaStream_t stream = nullptr;
-  bool own_stream = false;
-  void *U[2] = {nullptr, nullptr};
-  double *phi = nullptr;  // potential as given (with ghost layer)
-  void *acc = nullptr;    // -grad Phi, [3][N] in the state precision
-  Ctrl *ctrl = nullptr;   // device
-  Ctrl *hctrl = nullptr;  // pinned host mirror
-  int32_t *hdone = nullptr;                       // pinned completion flags of two batches
-  cudaEvent_t ev_done[2] = {nullptr, nullptr};
-  Partial *part = nullptr;
-  int part_cap = 0;
-  int32_t *flags = nullptr;  // per-cell fallback tags
-  double *hist = nullptr;
-  int64_t hist_cap = 0;
-  bool has_state = false;
-  int rows = 8, zchunk = 32;
-  cudaGraphExec_t graph = nullptr;
-  // profiling: eager launches with events around every step-kernel launch
-  bool profiling = false;
-  std::vector<cudaEvent_t> ev;
-  double prof_ms = 0.0;      // summed step-kernel time
-  double prof_fin_ms = 0.0;  // summed time from the step kernel's end to the finalize kernel's end
-  int64_t prof_launches = 0;
-};
 
 // ---------------------------------------------------------------- helpers
 namespace {
@@ -350,6 +317,8 @@ msh_status msh_set_state(msh_grid *g, const void *U, int32_t where, int32_t kind
                                         : launch_convert<double>((double *)g->U[nxt], g->N, 0, g->stream);
     if (e != cudaSuccess) return fail(MSH_E_CUDA, "convert: %s", cudaGetErrorString(e));
   }
+  // fallback tags are step numbers; a new state must not see tags of an earlier trajectory
+  CUDA_TRY(cudaMemsetAsync(g->flags, 0, g->N * sizeof(int32_t), g->stream));
   msh_status st = prime(g, nxt);
   if (st) return st;
   if (!g->hctrl->realizable) {
@@ -396,6 +365,7 @@ msh_status msh_set_time(msh_grid *g, double t, int64_t step) {
     const int cur = cur_buf(g);
     CUDA_TRY(cudaMemcpyAsync(g->U[cur ^ 1], g->U[cur], bytes, cudaMemcpyDeviceToDevice, g->stream));
   }
+  CUDA_TRY(cudaMemsetAsync(g->flags, 0, g->N * sizeof(int32_t), g->stream));
   g->hctrl->t = t;
   g->hctrl->step = step;
   CUDA_TRY(cudaMemcpyAsync(g->ctrl, g->hctrl, sizeof(Ctrl), cudaMemcpyHostToDevice, g->stream));

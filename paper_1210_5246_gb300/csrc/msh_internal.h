@@ -3,6 +3,10 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <vector>
+
+#include "../../include/msh.h"
+
 namespace msh {
 
 // A-posteriori fallback passes per step (see the step kernels).
@@ -69,3 +73,39 @@ void clear_error();
 void set_error_text(const char *msg);
 
 }  // namespace msh
+
+// Host-side state of a grid handle (the opaque msh_grid of the C ABI).
+
+struct msh_grid {
+  int ndim = 0;
+  int64_t n[3] = {1, 1, 1};
+  double lo[3] = {0, 0, 0}, hi[3] = {1, 1, 1}, dx[3] = {1, 1, 1};
+  int32_t bc[6] = {0, 0, 0, 0, 0, 0};
+  int prec = MSH_FP64;
+  double cfl = 0.5;
+  size_t N = 0;           // cells
+  size_t esize = 8;       // bytes per element
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  void *U[2] = {nullptr, nullptr};
+  double *phi = nullptr;  // potential as given (with ghost layer)
+  void *acc = nullptr;    // -grad Phi, [3][N] in the state precision
+  msh::Ctrl *ctrl = nullptr;   // device
+  msh::Ctrl *hctrl = nullptr;  // pinned host mirror
+  int32_t *hdone = nullptr;                       // pinned completion flags of two batches
+  cudaEvent_t ev_done[2] = {nullptr, nullptr};
+  msh::Partial *part = nullptr;
+  int part_cap = 0;
+  int32_t *flags = nullptr;  // per-cell fallback tags
+  double *hist = nullptr;
+  int64_t hist_cap = 0;
+  bool has_state = false;
+  int rows = 8, zchunk = 32;
+  cudaGraphExec_t graph = nullptr;
+  // profiling: eager launches with events around every step-kernel launch
+  bool profiling = false;
+  std::vector<cudaEvent_t> ev;
+  double prof_ms = 0.0;      // summed step-kernel time
+  double prof_fin_ms = 0.0;  // summed time from the step kernel's end to the finalize kernel's end
+  int64_t prof_launches = 0;
+};
