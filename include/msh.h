@@ -220,6 +220,31 @@ msh_status msh_batch_get_state(msh_batch *b, void *U, int32_t where, int32_t kin
 msh_status msh_batch_info(msh_batch *b, int64_t *steps, double *t, int64_t *cell_updates);
 msh_status msh_batch_destroy(msh_batch *b);
 
+/*
+ * One step of a 1D/2D/3D grid (no gravity) that allocates no memory, for callers that
+ * cannot allocate device memory: code running inside another framework's pre-sized memory
+ * pool, a real-time or embedded host loop that must not enter the allocator, or any code
+ * that owns nothing but the two state buffers it was given.  The paper has no counterpart;
+ * this is a convenience of the library.
+ *   ndim, n, lo, hi, bc, precision, cfl   as for msh_init_grid
+ *   dt_max     the step is dt = min(CFL dt of U_in, dt_max)
+ *   U_in       device pointer, conserved state [10][nz][ny][nx] in the given precision
+ *   U_out      device pointer receiving U after one step (must not alias U_in)
+ *   stream     cudaStream_t to run on (NULL: the default stream); the call synchronises it
+ *   dt_taken   host pointer receiving the step size (may be NULL)
+ * The working memory (control block, reduction partials, fallback tags) is one file-scope
+ * device array of about 5.6 MB that every GPU holds from the moment it loads the library
+ * until the process exits; grids of more than 1,048,576 cells (or needing more than 16384
+ * thread blocks) are rejected with MSH_E_INVALID_ARG.  The first call on a device looks up
+ * that array's device address, so make the first call before any stream capture.  Every
+ * call shares the array: each call clears what must start at zero, and calls that overlap
+ * on the GPU (from other streams or host threads) race on it.  No cudaMalloc, cudaFree or
+ * other allocating routine is called.
+ */
+msh_status msh_step_noalloc(int32_t ndim, const int64_t n[3], const double lo[3], const double hi[3],
+                            const int32_t bc[6], int32_t precision, double cfl, double dt_max,
+                            const void *U_in, void *U_out, void *stream, double *dt_taken);
+
 #ifdef __cplusplus
 }
 #endif

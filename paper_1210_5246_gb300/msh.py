@@ -67,6 +67,7 @@ SIGNATURES = {
     "msh_batch_get_state": [_vp, _vp, _i32, _i32],
     "msh_batch_info": [_vp, _P(_i64), _P(_dbl), _P(_i64)],
     "msh_batch_destroy": [_vp],
+    "msh_step_noalloc": [_i32, _P(_i64), _P(_dbl), _P(_dbl), _P(_i32), _i32, _dbl, _dbl, _vp, _vp, _vp, _P(_dbl)],
 }
 
 
@@ -139,6 +140,22 @@ def msh_run(h, t_end=float("inf"), max_steps=(1 << 62)):
     t = C.c_double(0.0)
     _check(load().msh_run(h, float(t_end), int(max_steps), C.byref(s), C.byref(t)))
     return s.value, t.value
+
+
+def msh_step_noalloc(n, lo, hi, bc, precision, cfl, U_in, U_out, dt_max=float("inf"), stream=None):
+    """One grid step that allocates no memory (see include/msh.h).  U_in and U_out are
+    device tensors (torch, contiguous [10][nz][ny][nx]) of the given precision.
+    Returns the step size."""
+    ndim = len(n)
+    n3 = (C.c_int64 * 3)(*(list(n) + [1] * (3 - ndim)))
+    lo3 = (C.c_double * 3)(*(list(lo) + [0.0] * (3 - ndim)))
+    hi3 = (C.c_double * 3)(*(list(hi) + [1.0] * (3 - ndim)))
+    bc6 = (C.c_int32 * 6)(*([b for pair in bc for b in pair] + [0] * (6 - 2 * ndim)))
+    dt = C.c_double(0.0)
+    _check(load().msh_step_noalloc(ndim, n3, lo3, hi3, bc6, int(precision), float(cfl), float(dt_max),
+                                   C.c_void_p(U_in.data_ptr()), C.c_void_p(U_out.data_ptr()),
+                                   C.c_void_p(stream) if stream else None, C.byref(dt)))
+    return dt.value
 
 
 # ------------------------------------------------------------------ classes
