@@ -220,12 +220,10 @@ def disc_noise(n=512, seed=5):
     return rng.uniform(-1.0, 1.0, (n, n))
 
 
-def disc(n=512, nsteps=2000, cfl=0.5, seed=5, beta=0.0, delta=None, **kw):
-    """2D stellar disc over [-L, L]^2 (outflow) in the fixed logarithmic potential.
-    Sigma = Sigma0 exp(-R/Rd) (1 + delta) with delta = 0.01 xi; in-plane dispersion
-    P = Sigma sigma_R^2 [e_R e_R^T + (1 + beta) e_phi e_phi^T], P_zz = Sigma sigma_R^2;
-    rotation from the Jeans (asymmetric drift) relation
-    v_phi^2 = v_c^2 + sigma_R^2 - sigma_phi^2 + (R/Sigma) d(Sigma sigma_R^2)/dR."""
+def disc_base(n=512, **kw):
+    """Unperturbed fields of the disc on the n x n grid: dict with Sigma (unperturbed
+    surface density), sig2 (sigma_R^2), vc2, jeans = (R/Sigma) d(Sigma sigma_R^2)/dR,
+    cphi, sphi, R, and the parameters."""
     p = dict(DISC_DEFAULTS)
     p.update(kw)
     L = p["L"]
@@ -238,25 +236,42 @@ def disc(n=512, nsteps=2000, cfl=0.5, seed=5, beta=0.0, delta=None, **kw):
     Sigma, sigR, vc2 = disc_profiles(R, **prof)
     h = 1e-5
     f = lambda r: (lambda s, sr, _: s * sr * sr)(*disc_profiles(r, **prof))
-    dfdR = (f(R + h) - f(np.maximum(R - h, 0.0)) ) / (R + h - np.maximum(R - h, 0.0))
-    sig2 = sigR * sigR
-    vphi2 = np.maximum(0.0, vc2 + sig2 - (1.0 + beta) * sig2 + R / Sigma * dfdR)
-    vphi = np.sqrt(vphi2)
+    dfdR = (f(R + h) - f(np.maximum(R - h, 0.0))) / (R + h - np.maximum(R - h, 0.0))
     Rs = np.maximum(R, 1e-30)
-    cphi, sphi = X / Rs, Y / Rs
-    if delta is None:
-        delta = 0.01 * disc_noise(n, seed)
-    S = Sigma * (1.0 + delta)
-    W = np.zeros((10, 1, n, n))
-    W[0, 0] = S
-    W[1, 0] = -vphi * sphi
-    W[2, 0] = vphi * cphi
+    return dict(Sigma=Sigma, sig2=sigR * sigR, vc2=vc2, jeans=R / Sigma * dfdR, cphi=X / Rs, sphi=Y / Rs,
+                R=R, X=X, Y=Y, dx=dx, params=p)
+
+
+def disc_compose(base, delta, beta, xp=np):
+    """Primitive disc state [10, 1, n, n] from the base fields, the perturbation field delta
+    and the anisotropy beta.  Written with the array module ``xp`` (numpy or torch), so the
+    same composition serves the seeded input and a differentiable map of (delta, beta)."""
+    S = base["Sigma"] * (1.0 + delta)
+    sig2 = base["sig2"]
+    vphi = xp.sqrt(xp.clamp(base["vc2"] - beta * sig2 + base["jeans"], min=0.0) if xp is not np
+                   else np.maximum(base["vc2"] - beta * sig2 + base["jeans"], 0.0))
+    c, s = base["cphi"], base["sphi"]
     Pr = S * sig2
     Pp = S * sig2 * (1.0 + beta)
-    W[4, 0] = Pr * cphi * cphi + Pp * sphi * sphi
-    W[5, 0] = (Pr - Pp) * cphi * sphi
-    W[7, 0] = Pr * sphi * sphi + Pp * cphi * cphi
-    W[9, 0] = S * sig2
+    zero = 0.0 * S
+    comps = [S, -vphi * s, vphi * c, zero, Pr * c * c + Pp * s * s, (Pr - Pp) * c * s, zero,
+             Pr * s * s + Pp * c * c, zero, S * sig2]
+    W = xp.stack(comps)
+    return W.reshape((10, 1) + tuple(S.shape))
+
+
+def disc(n=512, nsteps=2000, cfl=0.5, seed=5, beta=0.0, delta=None, **kw):
+    """2D stellar disc over [-L, L]^2 (outflow) in the fixed logarithmic potential.
+    Sigma = Sigma0 exp(-R/Rd) (1 + delta) with delta = 0.01 xi; in-plane dispersion
+    P = Sigma sigma_R^2 [e_R e_R^T + (1 + beta) e_phi e_phi^T], P_zz = Sigma sigma_R^2;
+    rotation from the Jeans (asymmetric drift) relation
+    v_phi^2 = v_c^2 + sigma_R^2 - sigma_phi^2 + (R/Sigma) d(Sigma sigma_R^2)/dR."""
+    base = disc_base(n, **kw)
+    p = base["params"]
+    L = p["L"]
+    if delta is None:
+        delta = 0.01 * disc_noise(n, seed)
+    W = disc_compose(base, delta, beta)
     phi = disc_potential(n, L, p["v0"], p["Rc"])
     bc = ((OUTFLOW, OUTFLOW), (OUTFLOW, OUTFLOW))
     return Problem("disc", W, (-L, -L), (L, L), bc, cfl, nsteps=nsteps, phi=phi,
