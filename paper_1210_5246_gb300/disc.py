@@ -60,7 +60,7 @@ class DiscProblem:
         beta = torch.tensor(float(beta), dtype=torch.float64, device="cuda", requires_grad=True)
         L = self.loss(delta, beta)
         gd, gb = torch.autograd.grad(L, (delta, beta))
-        return float(L), gd, float(gb)
+        return float(L.detach()), gd, float(gb)
 
     def close(self):
         self.grid.close()
