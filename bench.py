@@ -51,6 +51,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--fp32-only", action="store_true", help="skip the FP64 measurement")
     ap.add_argument("--tiling", default=None, help="rows,zchunk instead of autotuning (e.g. 8,32)")
+    ap.add_argument("--suite", action="store_true", help="one JSON line per workload instead of the bench line")
     return ap.parse_args()
 
 
@@ -326,9 +327,138 @@ def run_reference(args):
     }))
 
 
+# ---------------------------------------------------------------------- the suite
+def _oracle_rate(p, steps=1, crop=None):
+    """Oracle cell-updates/s over `steps` FP64 steps of problem p (optionally a crop)."""
+    from oracle import oracle
+    W = p.W if crop is None else np.ascontiguousarray(p.W[(slice(None),) + crop])
+    n = tuple(reversed(W.shape[1:]))[: p.ndim]
+    og = oracle.Grid(n, p.lo, [p.lo[d] + (p.hi[d] - p.lo[d]) * n[d] / p.n[d] for d in range(p.ndim)], p.bc, p.cfl)
+    U = oracle.prim_to_cons(W)
+    phi = None
+    if p.phi is not None and crop is None:
+        phi = p.phi
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        U = oracle.step(og, U, oracle.cfl_dt(og, U), phi=phi)
+    el = time.perf_counter() - t0
+    return int(np.prod(n)) * steps / el, oracle.num_threads(), el
+
+
+def run_suite(args):
+    """One JSON line per workload: GPU cell-updates/s in FP32/FP64, the HBM fraction of the
+    step kernel, the oracle's rate on the host cores, and for the batched tubes and the disc
+    the comparisons the workloads are about (persistent launch vs one launch per step per
+    tube; adjoint vs forward cost)."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1210_5246_gb300 import disc, inputs, msh
+    hbm, _ = peaks()
+    stream = torch.cuda.Stream()
+
+    def emit(d):
+        print(json.dumps(d), flush=True)
+
+    def grid_rate(p, precision, steps, t_end=math.inf):
+        g = msh.Grid.from_problem(p, precision, stream=stream.cuda_stream)
+        W = p.W.astype(np.float32) if precision == msh.FP32 else p.W
+        g.set_state(W, msh.PRIMITIVE)
+        if p.ndim > 1:
+            g.autotune()
+        g.run(t_end, min(steps, 3))
+        g.set_state(W, msh.PRIMITIVE)
+        g.set_time(0.0, 0)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ns, t = g.run(t_end, steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        g.set_state(W, msh.PRIMITIVE)
+        g.set_time(0.0, 0)
+        g.set_profiling(True)
+        g.run(t_end, steps)
+        kms, _, kn = g.profile()
+        g.close()
+        cells = int(np.prod(p.n))
+        bpc = 80 if precision == msh.FP32 else 160
+        return {"value": cells * ns / (ms * 1e-3), "steps": ns, "ms_per_step": ms / ns,
+                "kernel_ms": kms / max(kn, 1), "hbm_frac": bpc * cells / (kms / max(kn, 1) * 1e-3) / 1e9 / hbm}
+
+    # 1D shock tube, FP64, to t = 0.2
+    p = inputs.sod(256)
+    r = grid_rate(p, msh.FP64, 1 << 20, p.t_end)
+    orc, cores, _ = _oracle_rate(p, steps=r["steps"])
+    emit({"workload": "sod 256 cells FP64 to t=0.2", "gpu_fp64": r, "oracle": orc, "oracle_cores": cores})
+    # 2D blast 1024^2, 200 steps
+    p = inputs.blast()
+    r32 = grid_rate(p, msh.FP32, p.nsteps)
+    r64 = grid_rate(p, msh.FP64, p.nsteps)
+    orc, cores, _ = _oracle_rate(p, steps=2)
+    emit({"workload": "blast 1024^2, 200 steps", "gpu_fp32": r32, "gpu_fp64": r64, "oracle": orc,
+          "oracle_cores": cores, "oracle_sample": "2 FP64 steps of the full grid"})
+    # 3D box 256^3, 50 steps
+    p = inputs.turb()
+    r32 = grid_rate(p, msh.FP32, p.nsteps)
+    r64 = grid_rate(p, msh.FP64, 20)
+    orc, cores, _ = _oracle_rate(p, steps=1)
+    emit({"workload": "turb 256^3, 50 steps (FP64: 20)", "gpu_fp32": r32, "gpu_fp64": r64, "oracle": orc,
+          "oracle_cores": cores, "oracle_sample": "1 FP64 step of the full grid",
+          "gpu_fp32_over_oracle": r32["value"] / orc})
+    # batched tubes: one persistent launch vs one launch per step per tube
+    tb = inputs.tubes()
+    b = msh.Batch(tb.length, tb.WL, tb.WR, tb.t_end, tb.cfl, msh.FP32, stream=stream.cuda_stream)
+    b.run()  # autotunes the block size
+    b.reset()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    b.run()
+    torch.cuda.synchronize()
+    el = time.perf_counter() - t0
+    _, _, cu = b.info()
+    sample = np.argsort(tb.length)[:: len(tb.length) // 32][:32]
+    b.reset()
+    b.run_per_tube(sample)  # builds the per-tube grids
+    b.reset()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    b.run_per_tube(sample)
+    torch.cuda.synchronize()
+    el_pt = time.perf_counter() - t0
+    steps_pt, _, _ = b.info()
+    cu_pt = int((steps_pt[sample] * tb.length[sample]).sum())
+    b.close()
+    emit({"workload": "4096 tubes 128..2048 cells FP32 to t=0.1", "persistent": cu / el,
+          "per_tube_launches": cu_pt / el_pt, "per_tube_sample": "32 tubes spread over the length range",
+          "speedup": (cu / el) / (cu_pt / el_pt), "cell_updates": cu, "seconds": el})
+    # differentiable disc: forward and adjoint cost per step
+    D = disc.DiscProblem(n=512, nsteps=2000, precision=msh.FP32, K=50, stream=stream.cuda_stream)
+    L, gd, gb = D.value_and_grad()  # warm-up (builds graphs, allocates)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    W0 = D.initial_state(D.delta0, torch.tensor(0.0, dtype=torch.float64, device="cuda")).float().contiguous()
+    from paper_1210_5246_gb300 import autograd as ag
+    UN = ag.BMERun.apply(W0, D.grid, D.nsteps, D.K)
+    torch.cuda.synchronize()
+    t_fwd = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    L, gd, gb = D.value_and_grad()
+    torch.cuda.synchronize()
+    t_both = time.perf_counter() - t0
+    D.close()
+    cells = 512 * 512
+    emit({"workload": "disc 512^2 FP32, 2000 steps, K=50", "loss": L, "dL_dbeta": gb,
+          "forward_ms_per_step": t_fwd * 1e3 / 2000, "adjoint_ms_per_step": (t_both - t_fwd) * 1e3 / 2000,
+          "adjoint_over_forward": (t_both - t_fwd) / t_fwd, "forward_cell_updates_per_s": cells * 2000 / t_fwd})
+
+
 if __name__ == "__main__":
     a = parse()
     if a.impl == "reference":
         run_reference(a)
+    elif a.suite:
+        run_suite(a)
     else:
         run_gpu(a)
