@@ -13,6 +13,7 @@
 // 3D streams z planes through a three-plane shared-memory ring (2.5D): x and y fluxes
 // come from the current plane, the z flux is carried in registers from plane to plane,
 // so every cell is reconstructed once per direction.
+#include <algorithm>
 #include <cfloat>
 #include <climits>
 
@@ -150,7 +151,9 @@ __global__ void __launch_bounds__(kTile1D) step1d_kernel(StepArgs<T> a) {
   const int t = threadIdx.x;
   const int nx = a.nx;
   const size_t N = (size_t)nx;
-  const int x0 = blockIdx.x * (B - 2);
+  const int ntiles = (nx + B - 3) / (B - 2);
+  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+  const int x0 = tile * (B - 2);
   for (int i = t; i < SXX; i += B) {
     bool mir;
     const int xx = map_index(x0 - 2 + i, nx, a.bc[0], a.bc[1], mir);
@@ -197,7 +200,9 @@ __global__ void __launch_bounds__(kTile1D) step1d_kernel(StepArgs<T> a) {
     for (int k = 0; k < NV; k++) acc[k] = (F[k] - sH[k][t + 1]) * idx;
     finish_cell<T, 1, RETRY>(a, Us, Ud, N, (size_t)gx, acc, dt, idx, T(0), T(0), diag, smax, bad, tag);
   }
-  write_partial<T, B>(diag, smax, bad, a.part + blockIdx.x);
+  write_partial<T, B>(diag, smax, bad, a.part + tile);
+  __syncthreads();  // the next tile reuses the shared arrays
+  }
 }
 
 // -------------------------------------------------------------- 2D/3D kernel
@@ -233,7 +238,14 @@ __global__ void __launch_bounds__(32 * BY, (BY <= 8 ? 2 : 1)) step_tile_kernel(S
   const int tid = ty * 32 + tx;
   const int nx = a.nx, ny = a.ny, nz = a.nz;
   const size_t N = (size_t)nx * ny * nz;
-  const int x0 = blockIdx.x * kTileX, y0 = blockIdx.y * (BY - 2);
+  // One thread block per tile for the step; the fallback passes run on a small grid that
+  // loops over the tiles, so a pass with nothing to do costs only its launch.
+  const int tilesx = (nx + kTileX - 1) / kTileX, tilesy = (ny + BY - 3) / (BY - 2);
+  const int tilesz = NDIM == 3 ? (nz + a.zchunk - 1) / a.zchunk : 1;
+  const int ntiles = tilesx * tilesy * tilesz;
+  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+  const int bxi = tile % tilesx, byi = (tile / tilesx) % tilesy, bzi = tile / (tilesx * tilesy);
+  const int x0 = bxi * kTileX, y0 = byi * (BY - 2);
   const int gx = x0 - 1 + tx, gy = y0 - 1 + ty;
   const int sx = tx + 1, sy = ty + 1;
   const bool interior = tx >= 1 && tx <= kTileX && ty >= 1 && ty <= BY - 2;
@@ -334,7 +346,7 @@ __global__ void __launch_bounds__(32 * BY, (BY <= 8 ? 2 : 1)) step_tile_kernel(S
     if (valid)
       finish_cell<T, NDIM, RETRY>(a, Us, Ud, N, (size_t)gy * nx + gx, acc, dt, idx, idy, idz, diag, smax, bad, tag);
   } else {
-    const int z0 = blockIdx.z * a.zchunk;
+    const int z0 = bzi * a.zchunk;
     const int z1 = min(z0 + a.zchunk, nz);
     auto buf = [](int p) { return ((p % 3) + 3) % 3; };
     // prologue: z face state of cell z0-1 and the flux through its upper face
@@ -399,8 +411,8 @@ __global__ void __launch_bounds__(32 * BY, (BY <= 8 ? 2 : 1)) step_tile_kernel(S
       }
     }
   }
-  write_partial<T, 32 * BY>(diag, smax, bad,
-                            a.part + ((size_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x);
+  write_partial<T, 32 * BY>(diag, smax, bad, a.part + tile);
+  }
 }
 
 // ----------------------------------------------------------------- scan kernel
@@ -539,6 +551,18 @@ __global__ void convert_kernel(T *U, size_t N, int to_primitive) {
 }
 
 // ---------------------------------------------------------------- launchers
+// grid of the fallback passes: two blocks per SM, looping over the tiles
+static int fallback_blocks() {
+  static int blocks = 0;
+  if (blocks == 0) {
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    blocks = 2 * (sms > 0 ? sms : 152);
+  }
+  return blocks;
+}
+
 template <typename T> size_t step_smem(int ndim, int rows) {
   if (ndim == 1) return 0;
   const int npl = ndim == 3 ? 3 : 1;
@@ -563,16 +587,17 @@ static cudaError_t launch_tile(const StepArgs<T> &a, cudaStream_t s) {
     if (e != cudaSuccess) return e;
     attr_set = true;
   }
-  dim3 grid((a.nx + kTileX - 1) / kTileX, (a.ny + BY - 3) / (BY - 2),
-            NDIM == 3 ? (a.nz + a.zchunk - 1) / a.zchunk : 1);
-  step_tile_kernel<T, NDIM, BY, RETRY><<<grid, dim3(32, BY), smem, s>>>(a);
+  const int ntiles = step_blocks<T>(NDIM, BY, a.nx, a.ny, a.nz, a.zchunk);
+  const int blocks = RETRY ? std::min(ntiles, fallback_blocks()) : ntiles;
+  step_tile_kernel<T, NDIM, BY, RETRY><<<blocks, dim3(32, BY), smem, s>>>(a);
   return cudaGetLastError();
 }
 
 template <typename T, bool RETRY>
 static cudaError_t launch_step_mode(const StepArgs<T> &a, int ndim, int rows, cudaStream_t s) {
   if (ndim == 1) {
-    step1d_kernel<T, RETRY><<<(a.nx + kTile1D - 3) / (kTile1D - 2), kTile1D, 0, s>>>(a);
+    const int ntiles = (a.nx + kTile1D - 3) / (kTile1D - 2);
+    step1d_kernel<T, RETRY><<<RETRY ? std::min(ntiles, fallback_blocks()) : ntiles, kTile1D, 0, s>>>(a);
     return cudaGetLastError();
   }
   if (ndim == 2) {
