@@ -56,10 +56,8 @@ def parse():
 
 
 def dist_env():
-    rank = int(os.environ.get("RANK", "0"))
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    return rank, world, local
+    from paper_1210_5246_gb300 import replicas
+    return replicas.dist_env()
 
 
 def kernel_source_hash():
@@ -144,16 +142,15 @@ def make_workload(n):
 def run_gpu(args):
     import torch
     import torch.distributed as dist
+    from paper_1210_5246_gb300 import replicas
     rank, world, local = dist_env()
-    if world > 1:
-        backend = "nccl" if torch.cuda.is_available() else "gloo"
-        dist.init_process_group(backend)
     torch.cuda.set_device(local)
+    replicas.init()
     import __graft_entry__
     if rank == 0 or world == 1:
         __graft_entry__.build()
     if world > 1:
-        dist.barrier()
+        replicas.barrier()
         __graft_entry__.build()
     from paper_1210_5246_gb300 import msh
 
@@ -176,14 +173,14 @@ def run_gpu(args):
         g.set_state(Wdev, msh.PRIMITIVE)          # time the workload's first K steps
         g.set_time(0.0, 0)
         torch.cuda.synchronize()
-        if world > 1:
-            dist.barrier()
+        replicas.barrier()
         sampler = ClockSampler(local) if profile else None
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         ns, _ = g.run(max_steps=steps)
         e1.record(stream)
         torch.cuda.synchronize()
+        replicas.barrier()
         clocks = sampler.stop() if sampler else None
         ms = e0.elapsed_time(e1)
         kern_ms, kern_n = None, None
@@ -238,12 +235,9 @@ def run_gpu(args):
         e2e = {"value": ncells * k_e2e / dt_e2e, "unit": "cell-updates/s",
                "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes}
 
-    # max over ranks of the timed region
-    if world > 1:
-        t = torch.tensor([ms32], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms32 = float(t.item())
-    value = world * ncells * args.steps / (ms32 * 1e-3)
+    # max over ranks of the timed region; every rank advanced its own replica
+    ms32 = replicas.max_over_ranks(ms32)
+    value = replicas.whole_job_rate(ncells * args.steps, ms32 * 1e-3)
     value64 = ncells * steps64 / (ms64 * 1e-3) if not args.fp32_only else None
 
     hbm, peak_kind = peaks()

@@ -1,0 +1,138 @@
+"""Parity at the workloads' full sizes, in the launch configuration the benchmark times
+(autotuned tiling, graph-launched msh_run on a dedicated stream).
+
+* 2D blast, 1024^2 periodic, all 200 steps: FP64 against the oracle (rel L_inf <= 1e-10),
+  FP32 against the oracle run from the FP32-rounded input (rel L1 <= 2e-4 / 5e-4).
+* 3D box, 256^3 periodic: the first 3 steps element by element in FP64 and FP32 (the
+  oracle needs ~3 s per full step on 16 cores); the full 50-step FP32 and FP64 runs by
+  properties that hold at any size: all ten totals conserved to round-off (periodic),
+  every cell realizable, the dt sequence of the first steps equal to the oracle's, and
+  FP32 against FP64 after 50 steps.
+* Disc, 512^2 outflow with gravity, FP32, all 2000 steps against the oracle; FP64 for
+  the first 200 steps.
+"""
+import numpy as np
+import pytest
+
+from tests.parity import assert_fp32, assert_fp64, field_errors
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def env():
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1210_5246_gb300 import inputs, msh
+    msh.load()
+    return msh, inputs, torch.cuda.Stream()
+
+
+def _gpu_run(msh, p, precision, stream, steps, record=0):
+    g = msh.Grid.from_problem(p, precision, stream=stream.cuda_stream)
+    W = p.W.astype(np.float32) if precision == msh.FP32 else p.W
+    g.set_state(W, msh.PRIMITIVE)
+    g.autotune()
+    g.set_state(W, msh.PRIMITIVE)
+    g.set_time(0.0, 0)
+    if record:
+        g.set_recording(record)
+    ns, t = g.run(max_steps=steps)
+    assert ns == steps
+    out = {"U": g.get_state().astype(np.float64), "W": g.get_state(msh.PRIMITIVE).astype(np.float64),
+           "diag": g.diagnostics(), "t": t, "tiling": g.tiling()}
+    if record:
+        out["dts"] = g.dt_history()
+    g.close()
+    return out
+
+
+def _oracle_run(oracle, p, W, steps, record=False):
+    og = oracle.Grid(p.n, p.lo, p.hi, p.bc, p.cfl)
+    U, ns, t, rc, h = oracle.run(og, oracle.prim_to_cons(W.astype(np.float64)), np.inf, max_steps=steps,
+                                 phi=p.phi, record=record)
+    assert rc == 0 and ns == steps
+    return U, t, h
+
+
+# ------------------------------------------------------------------ 2D blast
+def test_blast_1024_fp64_all_steps(env, oracle):
+    msh, I, s = env
+    p = I.blast()
+    G = _gpu_run(msh, p, msh.FP64, s, p.nsteps)
+    Uo, to, _ = _oracle_run(oracle, p, p.W, p.nsteps)
+    assert abs(G["t"] - to) <= 1e-13 * to
+    assert_fp64(G["U"], Uo, what=f"blast 1024^2 fp64 tiling={G['tiling']}")
+
+
+def test_blast_1024_fp32_all_steps(env, oracle):
+    msh, I, s = env
+    p = I.blast()
+    G = _gpu_run(msh, p, msh.FP32, s, p.nsteps)
+    Uo, _, _ = _oracle_run(oracle, p, p.W.astype(np.float32), p.nsteps)
+    assert_fp32(G["W"], oracle.cons_to_prim(Uo), what=f"blast 1024^2 fp32 tiling={G['tiling']}")
+
+
+# ------------------------------------------------------------------- 3D box
+@pytest.fixture(scope="module")
+def box(env):
+    msh, I, s = env
+    return I.turb()
+
+
+def test_box_256_first_steps_elementwise(env, oracle, box):
+    msh, I, s = env
+    p, k = box, 3
+    G64 = _gpu_run(msh, p, msh.FP64, s, k, record=k)
+    Uo, _, ho = _oracle_run(oracle, p, p.W, k, record=True)
+    np.testing.assert_allclose(G64["dts"], ho, rtol=1e-12)
+    assert_fp64(G64["U"], Uo, what=f"box 256^3 fp64, {k} steps")
+    del G64, Uo
+    G32 = _gpu_run(msh, p, msh.FP32, s, k)
+    Uo32, _, _ = _oracle_run(oracle, p, p.W.astype(np.float32), k)
+    assert_fp32(G32["W"], oracle.cons_to_prim(Uo32), what=f"box 256^3 fp32, {k} steps")
+
+
+def test_box_256_full_run_properties(env, box):
+    msh, I, s = env
+    p = box
+    res = {}
+    for prec in (msh.FP64, msh.FP32):
+        g = msh.Grid.from_problem(p, prec, stream=s.cuda_stream)
+        W = p.W.astype(np.float32) if prec == msh.FP32 else p.W
+        g.set_state(W, msh.PRIMITIVE)
+        g.autotune()
+        g.set_state(W, msh.PRIMITIVE)
+        g.set_time(0.0, 0)
+        t0, ok0, _ = g.diagnostics()
+        ns, t = g.run(max_steps=p.nsteps)
+        t1, ok1, bad = g.diagnostics()
+        assert ns == p.nsteps and ok0 and ok1 and bad == -1
+        scale = np.array([abs(t0[0])] * 4 + [abs(t0[4]) + abs(t0[7]) + abs(t0[9])] * 6)
+        # FP64: round-off of 16.7M cells x 50 steps; FP32: the state itself is rounded to
+        # 2^-24 per cell and per step
+        tol = 1e-12 if prec == msh.FP64 else 2e-6
+        drift = np.abs(t1 - t0) / scale
+        assert np.all(drift < tol), (prec, drift)
+        res[prec] = g.get_state(msh.PRIMITIVE).astype(np.float64)
+        g.close()
+    e = field_errors(res[msh.FP32], res[msh.FP64], "l1")
+    assert e[0] <= 2e-4 and max(e[k] for k in (4, 5, 6, 7, 8, 9)) <= 5e-4, e
+
+
+# --------------------------------------------------------------------- disc
+def test_disc_512_fp32_all_steps(env, oracle):
+    msh, I, s = env
+    p = I.disc()
+    G = _gpu_run(msh, p, msh.FP32, s, p.nsteps)
+    Uo, _, _ = _oracle_run(oracle, p, p.W.astype(np.float32), p.nsteps)
+    assert_fp32(G["W"], oracle.cons_to_prim(Uo), what=f"disc 512^2 fp32, {p.nsteps} steps")
+
+
+def test_disc_512_fp64_first_200_steps(env, oracle):
+    msh, I, s = env
+    p = I.disc()
+    G = _gpu_run(msh, p, msh.FP64, s, 200)
+    Uo, _, _ = _oracle_run(oracle, p, p.W, 200)
+    assert_fp64(G["U"], Uo, what="disc 512^2 fp64, 200 steps")
