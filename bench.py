@@ -36,6 +36,15 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 N_BOX = 256
+DATA = {"box": "synthetic (seeded k^-2 Gaussian random fields)",
+        "blast": "synthetic (seeded 1% density noise)", "disc": "synthetic (seeded 1% density perturbation)"}
+# name -> (cells per axis, description, timed kernel)
+WORKLOADS = {
+    "box": (256, "turbulent periodic box {n}^3, FP32, CFL 0.5", "step_tile_kernel<float,3>"),
+    "blast": (1024, "anisotropic-stress blast {n}^2 periodic, FP32, CFL 0.5", "step_strip2d_kernel<float>"),
+    "disc": (512, "stellar disc {n}^2 in a logarithmic potential, outflow, FP32, CFL 0.5",
+             "step_strip2d_kernel<float>"),
+}
 BYTES_PER_CELL = {"f32": 80, "f64": 160}   # read U^n + write U^{n+1}, 10 fields each
 PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "step_tile_fp32_turb256.md")
 
@@ -46,12 +55,16 @@ def parse():
     ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
-    ap.add_argument("--n", type=int, default=N_BOX)
+    ap.add_argument("--workload", default="box", choices=sorted(WORKLOADS),
+                    help="box: 3D turbulent box (the benchmark); blast, disc: the 2D workloads")
+    ap.add_argument("--n", type=int, default=None, help="cells per axis (default: the workload's)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--fp32-only", action="store_true", help="skip the FP64 measurement")
     ap.add_argument("--tiling", default=None, help="rows,zchunk instead of autotuning (e.g. 8,32)")
     ap.add_argument("--suite", action="store_true", help="one JSON line per workload instead of the bench line")
+    ap.add_argument("--only", default=None, choices=["sod", "blast", "box", "tubes", "disc"],
+                    help="with --suite: run one workload (--n and --steps then size it)")
     return ap.parse_args()
 
 
@@ -133,9 +146,13 @@ def peaks():
         return 6800.0, "fallback"
 
 
-def make_workload(n):
+def make_workload(kind, n):
     from paper_1210_5246_gb300 import inputs
-    return inputs.turb(n=n, nsteps=50)
+    if kind == "box":
+        return inputs.turb(n=n, nsteps=50)
+    if kind == "blast":
+        return inputs.blast(n=n)
+    return inputs.disc(n=n)
 
 
 # ----------------------------------------------------------------------- GPU arm
@@ -154,8 +171,11 @@ def run_gpu(args):
         __graft_entry__.build()
     from paper_1210_5246_gb300 import msh
 
-    p = make_workload(args.n)
+    n_axis, desc, kernel_name = WORKLOADS[args.workload]
+    n_axis = args.n or n_axis
+    p = make_workload(args.workload, n_axis)
     ncells = int(np.prod(p.n))
+    state_mb = ncells * 10 * 4 / 1e6
     # one dedicated stream: the library launches on it and the CUDA events are recorded on it
     stream = torch.cuda.Stream()
     W32 = torch.from_numpy(p.W.astype(np.float32)).cuda()
@@ -243,7 +263,7 @@ def run_gpu(args):
     hbm, peak_kind = peaks()
     avg_kernel_s = (kms / kn) * 1e-3
     achieved = BYTES_PER_CELL["f32"] * ncells / avg_kernel_s / 1e9
-    traffic = measured_traffic(ncells)
+    traffic = measured_traffic(ncells) if args.workload == "box" else None
     # per step: step kernel, 4 fallback passes (idle unless cells were tagged), finalize;
     # the graphs hold 16 steps, plus the run-start kernel
     graph_launches = math.ceil(args.steps / 16) * 16 * 6 + 1
@@ -251,13 +271,15 @@ def run_gpu(args):
         "metric": "cell-updates/s", "value": value, "unit": "cell-updates/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms32 / args.steps, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded k^-2 Gaussian random fields)",
-        "config": {"workload": f"turbulent periodic box {args.n}^3, FP32, CFL 0.5, steps 1..{args.steps}",
+        "vs_baseline": None, "dtype": "f32", "data": DATA[args.workload],
+        "config": {"workload": desc.format(n=n_axis) + f", steps 1..{args.steps}",
                    "cells": ncells, "parallelism": f"replicas x{world}",
-                   "l2": "state (671 MB) larger than L2; no flush", "tiling": list(tiling)},
+                   "l2": (f"state ({state_mb:.0f} MB per buffer) larger than L2; no flush" if state_mb > 129
+                          else f"state ({state_mb:.0f} MB per buffer) fits in L2; no flush (L2-assisted)"),
+                   "tiling": list(tiling)},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                      "frac": achieved / hbm, "traffic": traffic,
-                     "kernel": "step_tile_kernel<float,3>", "peak_source": peak_kind,
+                     "kernel": kernel_name, "peak_source": peak_kind,
                      "kernel_ms": kms / kn, "bytes_per_cell": BYTES_PER_CELL["f32"],
                      "eager_ms_per_step": timed.eager_ms / args.steps, "finalize_ms": timed.fin_ms},
         "fp64": None if args.fp32_only else {
@@ -282,7 +304,7 @@ def cpu_baseline(p):
     U = oracle.prim_to_cons(p.W)
     dt = oracle.cfl_dt(og, U)
     t0 = time.perf_counter()
-    oracle.step(og, U, dt)
+    oracle.step(og, U, dt, phi=p.phi)
     el = time.perf_counter() - t0
     ncells = int(np.prod(p.n))
     return {"value": ncells / el, "unit": "cell-updates/s", "cores": oracle.num_threads(),
@@ -297,28 +319,38 @@ def run_reference(args):
     from oracle import oracle
     from paper_1210_5246_gb300 import inputs
     oracle.build()
-    p = make_workload(args.n)
-    m = min(128, args.n)
-    Wc = np.ascontiguousarray(p.W[:, :m, :m, :m])
-    og = oracle.Grid((m, m, m), (0, 0, 0), (m / args.n,) * 3, ((0, 0),) * 3, p.cfl)
+    n_axis, desc, _ = WORKLOADS[args.workload]
+    n_axis = args.n or n_axis
+    p = make_workload(args.workload, n_axis)
+    if args.workload == "box":
+        # each step: a 128^3 periodic crop, so the run stays within a few minutes
+        m = min(128, n_axis)
+        Wc = np.ascontiguousarray(p.W[:, :m, :m, :m])
+        og = oracle.Grid((m, m, m), (0, 0, 0), (m / n_axis,) * 3, ((0, 0),) * 3, p.cfl)
+        cells, sample = m ** 3, f"{m}^3 periodic crop"
+    else:
+        Wc = p.W
+        og = oracle.Grid(p.n, p.lo, p.hi, p.bc, p.cfl)
+        cells, sample = int(np.prod(p.n)), "the full grid"
     U = oracle.prim_to_cons(Wc)
+    phi = p.phi if args.workload == "disc" else None
     for _ in range(args.warmup):
-        U = oracle.step(og, U, oracle.cfl_dt(og, U))
+        U = oracle.step(og, U, oracle.cfl_dt(og, U), phi=phi)
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        U = oracle.step(og, U, oracle.cfl_dt(og, U))
+        U = oracle.step(og, U, oracle.cfl_dt(og, U), phi=phi)
     el = time.perf_counter() - t0
-    v = m ** 3 * args.steps / el
+    v = cells * args.steps / el
     cores = oracle.num_threads()
     print(json.dumps({
         "impl": "reference", "metric": "cell-updates/s", "value": v, "unit": "cell-updates/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": el * 1e3 / args.steps, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded k^-2 Gaussian random fields)",
-        "config": {"workload": f"turbulent periodic box {args.n}^3 (each step: FP64 oracle step of a "
-                               f"{m}^3 periodic crop)", "cells": m ** 3},
+        "vs_baseline": None, "dtype": "f64", "data": DATA[args.workload],
+        "config": {"workload": desc.format(n=n_axis).replace("FP32", "FP64 oracle") + f" (each step: {sample})",
+                   "cells": cells},
         "cpu_baseline": {"value": v, "unit": "cell-updates/s", "cores": cores, "kind": "oracle",
-                         "sample": f"{m}^3 crop, {args.steps} steps"},
+                         "sample": f"{sample}, {args.steps} steps"},
         "e2e": {"value": v, "unit": "cell-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }))
 
@@ -383,27 +415,42 @@ def run_suite(args):
         return {"value": cells * ns / (ms * 1e-3), "steps": ns, "ms_per_step": ms / ns,
                 "kernel_ms": kms / max(kn, 1), "hbm_frac": bpc * cells / (kms / max(kn, 1) * 1e-3) / 1e9 / hbm}
 
+    only = args.only
     # 1D shock tube, FP64, to t = 0.2
-    p = inputs.sod(256)
-    r = grid_rate(p, msh.FP64, 1 << 20, p.t_end)
-    orc, cores, _ = _oracle_rate(p, steps=r["steps"])
-    emit({"workload": "sod 256 cells FP64 to t=0.2", "gpu_fp64": r, "oracle": orc, "oracle_cores": cores})
+    if only in (None, "sod"):
+        p = inputs.sod(args.n or 256)
+        r = grid_rate(p, msh.FP64, 1 << 20, p.t_end)
+        orc, cores, _ = _oracle_rate(p, steps=r["steps"])
+        emit({"workload": f"sod {p.n[0]} cells FP64 to t=0.2", "gpu_fp64": r, "oracle": orc, "oracle_cores": cores})
     # 2D blast 1024^2, 200 steps
-    p = inputs.blast()
-    r32 = grid_rate(p, msh.FP32, p.nsteps)
-    r64 = grid_rate(p, msh.FP64, p.nsteps)
-    orc, cores, _ = _oracle_rate(p, steps=2)
-    emit({"workload": "blast 1024^2, 200 steps", "gpu_fp32": r32, "gpu_fp64": r64, "oracle": orc,
-          "oracle_cores": cores, "oracle_sample": "2 FP64 steps of the full grid"})
+    if only in (None, "blast"):
+        p = inputs.blast(n=args.n or 1024)
+        steps = p.nsteps if only is None else args.steps
+        r32 = grid_rate(p, msh.FP32, steps)
+        r64 = grid_rate(p, msh.FP64, steps)
+        orc, cores, _ = _oracle_rate(p, steps=2)
+        emit({"workload": f"blast {p.n[0]}^2, {steps} steps", "gpu_fp32": r32, "gpu_fp64": r64, "oracle": orc,
+              "oracle_cores": cores, "oracle_sample": "2 FP64 steps of the full grid"})
     # 3D box 256^3, 50 steps
-    p = inputs.turb()
-    r32 = grid_rate(p, msh.FP32, p.nsteps)
-    r64 = grid_rate(p, msh.FP64, 20)
-    orc, cores, _ = _oracle_rate(p, steps=1)
-    emit({"workload": "turb 256^3, 50 steps (FP64: 20)", "gpu_fp32": r32, "gpu_fp64": r64, "oracle": orc,
-          "oracle_cores": cores, "oracle_sample": "1 FP64 step of the full grid",
-          "gpu_fp32_over_oracle": r32["value"] / orc})
-    # batched tubes: one persistent launch vs one launch per step per tube
+    if only in (None, "box"):
+        p = inputs.turb(n=args.n or 256)
+        steps = p.nsteps if only is None else args.steps
+        r32 = grid_rate(p, msh.FP32, steps)
+        r64 = grid_rate(p, msh.FP64, min(steps, 20))
+        orc, cores, _ = _oracle_rate(p, steps=1)
+        emit({"workload": f"turb {p.n[0]}^3, {steps} steps (FP64: {min(steps, 20)})", "gpu_fp32": r32,
+              "gpu_fp64": r64, "oracle": orc, "oracle_cores": cores, "oracle_sample": "1 FP64 step of the full grid",
+              "gpu_fp32_over_oracle": r32["value"] / orc})
+    if only in (None, "tubes"):
+        run_suite_tubes(msh, inputs, stream, emit)
+    if only in (None, "disc"):
+        n = args.n or 512
+        run_suite_disc(msh, disc, stream, emit, n, 2000 if only is None else args.steps)
+
+
+def run_suite_tubes(msh, inputs, stream, emit):
+    """Batched tubes: one persistent launch vs one launch per step per tube."""
+    import torch
     tb = inputs.tubes()
     b = msh.Batch(tb.length, tb.WL, tb.WR, tb.t_end, tb.cfl, msh.FP32, stream=stream.cuda_stream)
     b.run()  # autotunes the block size
@@ -429,14 +476,19 @@ def run_suite(args):
     emit({"workload": "4096 tubes 128..2048 cells FP32 to t=0.1", "persistent": cu / el,
           "per_tube_launches": cu_pt / el_pt, "per_tube_sample": "32 tubes spread over the length range",
           "speedup": (cu / el) / (cu_pt / el_pt), "cell_updates": cu, "seconds": el})
-    # differentiable disc: forward and adjoint cost per step
-    D = disc.DiscProblem(n=512, nsteps=2000, precision=msh.FP32, K=50, stream=stream.cuda_stream)
-    L, gd, gb = D.value_and_grad()  # warm-up (builds graphs, allocates)
+
+
+def run_suite_disc(msh, disc, stream, emit, n, nsteps, K=50):
+    """Differentiable disc: cost per step of the forward run and of the backward
+    (msh_adjoint_run: checkpointed forward, segment recomputation, reverse steps)."""
+    import torch
+    from paper_1210_5246_gb300 import autograd as ag
+    D = disc.DiscProblem(n=n, nsteps=nsteps, precision=msh.FP32, K=K, stream=stream.cuda_stream)
+    D.value_and_grad()  # warm-up (builds graphs, allocates)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     W0 = D.initial_state(D.delta0, torch.tensor(0.0, dtype=torch.float64, device="cuda")).float().contiguous()
-    from paper_1210_5246_gb300 import autograd as ag
-    UN = ag.BMERun.apply(W0, D.grid, D.nsteps, D.K)
+    ag.BMERun.apply(W0, D.grid, D.nsteps, D.K)
     torch.cuda.synchronize()
     t_fwd = time.perf_counter() - t0
     t0 = time.perf_counter()
@@ -444,10 +496,11 @@ def run_suite(args):
     torch.cuda.synchronize()
     t_both = time.perf_counter() - t0
     D.close()
-    cells = 512 * 512
-    emit({"workload": "disc 512^2 FP32, 2000 steps, K=50", "loss": L, "dL_dbeta": gb,
-          "forward_ms_per_step": t_fwd * 1e3 / 2000, "adjoint_ms_per_step": (t_both - t_fwd) * 1e3 / 2000,
-          "adjoint_over_forward": (t_both - t_fwd) / t_fwd, "forward_cell_updates_per_s": cells * 2000 / t_fwd})
+    cells = n * n
+    emit({"workload": f"disc {n}^2 FP32, {nsteps} steps, K={K}", "loss": L, "dL_dbeta": gb,
+          "forward_ms_per_step": t_fwd * 1e3 / nsteps, "adjoint_ms_per_step": (t_both - t_fwd) * 1e3 / nsteps,
+          "adjoint_over_forward": (t_both - t_fwd) / t_fwd, "forward_cell_updates_per_s": cells * nsteps / t_fwd,
+          "adjoint_cell_updates_per_s": cells * nsteps / (t_both - t_fwd)})
 
 
 if __name__ == "__main__":

@@ -154,10 +154,14 @@ msh_status msh_set_recording(msh_grid *g, int64_t capacity);
 msh_status msh_get_dt_history(msh_grid *g, double *dts, int64_t capacity, int64_t *count);
 
 /*
- * Tile shape of the 2D/3D step kernel: rows per thread block (4, 8 or 16) and z planes
- * streamed per block (3D only, >= 1).  msh_autotune times the candidates on this grid's
- * current state (without changing it) and keeps the fastest; the chosen values are
- * returned in *rows / *zchunk (may be NULL).
+ * Tile shape of the 2D/3D step kernels.  3D: `rows` = thread rows per block (4, 8 or 16,
+ * each a warp of 32 cells in x) and `zchunk` = z planes each block streams.  2D: `rows` =
+ * warps per block (4, 8 or 16, each a strip of 28 updated columns) and `zchunk` = grid
+ * rows each warp streams in y.  1D ignores both.  `zchunk` >= 1, clipped to the streamed
+ * axis.  3D FP64 grids take rows 4 or 8 (rows 16 would need more shared memory than a
+ * thread block has).  Defaults: rows 8; zchunk 32 (3D) or 16 (2D).  msh_autotune times
+ * the candidates on this grid's current state (without changing it or the tape) and keeps
+ * the fastest; the chosen values are returned in *rows / *zchunk (may be NULL).
  */
 msh_status msh_set_tiling(msh_grid *g, int32_t rows, int32_t zchunk);
 msh_status msh_get_tiling(msh_grid *g, int32_t *rows, int32_t *zchunk);
@@ -188,6 +192,24 @@ msh_status msh_get_profile(msh_grid *g, double *step_kernel_ms, double *finalize
 msh_status msh_adjoint_run(msh_grid *g, const void *U0, int64_t nsteps, const double *dt_sched,
                            int32_t K, const void *dL_dUN, void *dL_dU0, int32_t where,
                            int32_t kind);
+
+/*
+ * Adjoint tape of a forward run.  msh_set_tape(g, K, max_steps) starts recording at the
+ * grid's current step s0: the step kernel of every step s0 + mK stores its input state
+ * U^{s0+mK} in device memory owned by the grid (ceil(max_steps / K) states), and the
+ * finalize kernel records each step's dt and whether its a-posteriori fallback tagged
+ * cells, for the first max_steps steps.  Recording costs one extra write of the state
+ * every K steps and no launches.  msh_set_state and msh_set_time end the recording (the
+ * memory is kept for the next msh_set_tape); K = 0 frees it.  Needs a state.
+ *
+ * msh_adjoint_tape(g, dL_dUN, dL_dU0, where, kind) is msh_adjoint_run over the recorded
+ * steps s0 .. current step, with U0 = U^{s0} and the recorded dt schedule, without the
+ * forward sweep msh_adjoint_run needs to build its checkpoints.  kind == MSH_PRIMITIVE
+ * returns the gradient with respect to W0 = primitive(U^{s0}).  Errors: MSH_E_STATE if no
+ * tape is being recorded or the run went past max_steps.
+ */
+msh_status msh_set_tape(msh_grid *g, int32_t K, int64_t max_steps);
+msh_status msh_adjoint_tape(msh_grid *g, const void *dL_dUN, void *dL_dU0, int32_t where, int32_t kind);
 
 /*
  * Batched independent 1D Riemann problems ("tubes") on [0, 1] with the interface at 0.5

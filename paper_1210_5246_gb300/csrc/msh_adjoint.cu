@@ -3,17 +3,21 @@
 // Reverse step n maps lam^{n+1} = dL/dU^{n+1} to lam^n = dL/dU^n for the frozen time step
 // dt_n, with every branch of the forward step frozen (MC limiter selection, face-state
 // fallback, HLL branch and min/max of the signal speeds, a-posteriori fallback tags):
-//   1. lam* = G^T lam^{n+1}           gravity source (linear in U* for a fixed -grad Phi)
+//   1. lam* = G^T lam^{n+1}           gravity source (linear in U* for a fixed -grad Phi),
+//                                     evaluated where the passes below need it
 //   2. per direction d:
 //      face pass   F^bar = (dt/dx)(lam*_j - lam*_{j-1}) through the HLL flux at face j-1/2
 //                  -> adjoints of the face states hi_{j-1}, lo_j
 //      cell pass   reconstruction of cell j reversed -> adjoints of W_{j-1}, W_j, W_{j+1}
-//      gather      summed onto the padded primitive adjoint (deterministic, no atomics)
+//      gather      summed onto the padded primitive adjoint (deterministic, no atomics;
+//                  the first direction writes, later ones add)
 //   3. fold        lam^n_i = lam*_i + (dW/dU)^T W^bar_i, plus the ghost images of cell i
 //                  (periodic wrap, outflow copy, reflect mirror with its sign flips)
-// Forward states are checkpointed every K steps and recomputed segment by segment during
-// the reverse sweep; the forward step is re-run before its reverse only when it tagged
-// cells for the a-posteriori fallback, to restore its tags.
+// Forward states are checkpointed every K steps (by a forward sweep here, or by the step
+// kernels of the recorded run: msh_adjoint_tape) and recomputed segment by segment during
+// the reverse sweep.  Which steps tagged cells for the a-posteriori fallback is known on
+// the host: only those steps launch their fallback passes when recomputed, and only those
+// are re-run before their reverse, to restore their tags.
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -30,7 +34,6 @@ namespace msh {
 template <typename T> struct AdjArgs {
   const T *U;          // U^n [NV][N]
   const T *lam;        // lam^{n+1}
-  T *ls;               // lam*
   T *out;              // lam^n
   const T *acc;        // -grad Phi [3][N] or nullptr
   const int32_t *flags;
@@ -119,22 +122,18 @@ __device__ __forceinline__ void local_w(const AdjArgs<T> &a, int (&c)[3], int j,
   tagged_cell = (f >> 3) == a.tag && (f & 7) < pass;
 }
 
+// lam* = G^T lam^{n+1} of cell c (the gravity source's adjoint; identity without gravity)
 template <typename T>
-__global__ void adj_lamstar_kernel(AdjArgs<T> a) {
-  const size_t N = (size_t)a.n[0] * a.n[1] * a.n[2];
-  for (size_t c = (size_t)blockIdx.x * blockDim.x + threadIdx.x; c < N; c += (size_t)gridDim.x * blockDim.x) {
-    T lam[NV], ls[NV];
+__device__ __forceinline__ void lam_star(const AdjArgs<T> &a, size_t N, size_t c, T (&ls)[NV]) {
+  T lam[NV];
 #pragma unroll
-    for (int k = 0; k < NV; k++) lam[k] = a.lam[k * N + c];
-    if (a.acc) {
-      T g[3] = {a.acc[c], a.acc[N + c], a.acc[2 * N + c]};
-      gravity_vjp(g, (T)a.dt, lam, ls);
-    } else {
+  for (int k = 0; k < NV; k++) lam[k] = a.lam[k * N + c];
+  if (a.acc) {
+    const T g[3] = {a.acc[c], a.acc[N + c], a.acc[2 * N + c]};
+    gravity_vjp(g, (T)a.dt, lam, ls);
+  } else {
 #pragma unroll
-      for (int k = 0; k < NV; k++) ls[k] = lam[k];
-    }
-#pragma unroll
-    for (int k = 0; k < NV; k++) a.ls[k * N + c] = ls[k];
+    for (int k = 0; k < NV; k++) ls[k] = lam[k];
   }
 }
 
@@ -178,12 +177,21 @@ __global__ void adj_face_kernel(AdjArgs<T> a) {
     int cm[3] = {c[0], c[1], c[2]};
     cm[D] = j - 1;
     const size_t cjm = ((size_t)cm[2] * a.n[1] + cm[1]) * a.n[0] + cm[0];
+    T lsj[NV], lsm[NV];
+    if (j < nd) lam_star(a, N, cj, lsj);
+    else {
+#pragma unroll
+      for (int k = 0; k < NV; k++) lsj[k] = T(0);
+    }
+    if (j >= 1) lam_star(a, N, cjm, lsm);
+    else {
+#pragma unroll
+      for (int k = 0; k < NV; k++) lsm[k] = T(0);
+    }
 #pragma unroll
     for (int k = 0; k < NV; k++) {
       const int gk = Frame<D>::g(k);
-      const T lj = (j < nd) ? a.ls[gk * N + cj] : T(0);
-      const T ljm = (j >= 1) ? a.ls[gk * N + cjm] : T(0);
-      Fb[k] = dtdx * (lj - ljm);
+      Fb[k] = dtdx * (lsj[gk] - lsm[gk]);
     }
     T hb[NV], lb[NV];
 #pragma unroll
@@ -271,8 +279,15 @@ __global__ void adj_gather_kernel(AdjArgs<T> a) {
       for (int k = 0; k < NV; k++) s[k] += a.GM[k * Ne + i];
     }
     const size_t pi = pad_index(a.n, a.ndim, c);
+    // direction 0 writes every position it covers; a later direction adds where the cell
+    // is inside the grid along D (covered by direction 0) and writes its own ghost layers
+    if (D == 0 || p < 0 || p >= nd) {
 #pragma unroll
-    for (int k = 0; k < NV; k++) a.Wb[k * Npad + pi] += s[k];
+      for (int k = 0; k < NV; k++) a.Wb[k * Npad + pi] = s[k];
+    } else {
+#pragma unroll
+      for (int k = 0; k < NV; k++) a.Wb[k * Npad + pi] += s[k];
+    }
   }
 }
 
@@ -317,8 +332,10 @@ __global__ void adj_fold_kernel(AdjArgs<T> a) {
         for (int k = 0; k < NV; k++) Ub[k] += ((flip >> k) & 1u) ? -Ugb[k] : Ugb[k];
       }
     }
+    T ls[NV];
+    lam_star(a, N, ci, ls);
 #pragma unroll
-    for (int k = 0; k < NV; k++) a.out[k * N + ci] = a.ls[k * N + ci] + Ub[k];
+    for (int k = 0; k < NV; k++) a.out[k * N + ci] = ls[k] + Ub[k];
   }
 }
 
@@ -339,11 +356,11 @@ __global__ void adj_prim_kernel(const T *W, const T *Ub, T *Wb, size_t N) {
   }
 }
 
-// control of the adjoint's forward steps: fixed dt, step tag, optional skip
-__global__ void adj_setup_kernel(Ctrl *c, int64_t step, double dt, const int32_t *had_tags) {
+// control of the adjoint's forward steps: fixed dt and step tag
+__global__ void adj_setup_kernel(Ctrl *c, int64_t step, double dt) {
   c->step = step;
   c->dt = dt;
-  c->done = had_tags ? (had_tags[step] == 0) : 0;
+  c->done = 0;
   for (int p = 0; p <= kFallbackPasses; p++) c->nbad[p] = 0;
 }
 
@@ -383,10 +400,13 @@ int grid_blocks(size_t n) {
   return (int)(b < 4096 ? (b > 0 ? b : 1) : 4096);
 }
 
+// One forward step src -> dst with the fixed dt (no finalize: the schedule is given).  The
+// fallback passes are launched only when `passes` is set, i.e. when the step is known (or
+// not yet known) to tag cells; a step that tagged none recomputes identically without them.
 template <typename T>
 cudaError_t forward_step(msh_grid *g, Ctrl *ctl, Partial *part, T *src, T *dst, int64_t step, double dt,
-                         const int32_t *had_tags) {
-  adj_setup_kernel<<<1, 1, 0, g->stream>>>(ctl, step, dt, had_tags);
+                         bool passes) {
+  adj_setup_kernel<<<1, 1, 0, g->stream>>>(ctl, step, dt);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   StepArgs<T> a;
@@ -402,7 +422,11 @@ cudaError_t forward_step(msh_grid *g, Ctrl *ctl, Partial *part, T *src, T *dst, 
   for (int i = 0; i < 6; i++) a.bc[i] = g->bc[i];
   for (int i = 0; i < 3; i++) a.dx[i] = g->dx[i];
   a.zchunk = g->zchunk;
-  for (int level = 0; level <= kFallbackPasses; level++) {
+  a.ck = nullptr;
+  a.ck_base = 0;
+  a.ck_len = 0;
+  a.ck_K = 1;
+  for (int level = 0; level <= (passes ? kFallbackPasses : 0); level++) {
     a.level = level;
     e = launch_step<T>(a, g->ndim, g->rows, level > 0, g->stream, nullptr);
     if (e != cudaSuccess) return e;
@@ -410,31 +434,32 @@ cudaError_t forward_step(msh_grid *g, Ctrl *ctl, Partial *part, T *src, T *dst, 
   return cudaSuccess;
 }
 
+// Reverse sweep over nsteps steps from the checkpoints ck (U^{mK}, device), the dt
+// schedule and the per-step fallback flags (host).  lamN / lam0 are located per `where`;
+// W0 (device, may be null) is the primitive initial state for kind == MSH_PRIMITIVE.
 template <typename T>
-msh_status adjoint_impl(msh_grid *g, const void *U0, int64_t nsteps, const double *dts, int K, const void *lamN,
-                        void *lam0, int where, int kind) {
+msh_status reverse_sweep(msh_grid *g, const T *ck, int64_t nsteps, const double *dts, const int32_t *had, int K,
+                         const void *lamN, void *lam0, int where, const T *W0) {
   msh_status st = MSH_OK;
   const size_t N = g->N;
   const size_t S = N * NV * sizeof(T);
   const cudaMemcpyKind in_kind = where == MSH_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
   const cudaMemcpyKind out_kind = where == MSH_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
-  const int64_t nck = nsteps > 0 ? (nsteps + K - 1) / K : 1;
+  const int64_t nck = nsteps > 0 ? (nsteps + K - 1) / K : 0;
+  const int64_t seg_len = std::min<int64_t>(K, std::max<int64_t>(nsteps, 1));
   size_t Ne_max = 0;
   for (int d = 0; d < g->ndim; d++) Ne_max = std::max(Ne_max, N / g->n[d] * (g->n[d] + 2));
   size_t Npad = 1;
   for (int d = 0; d < 3; d++) Npad *= (size_t)(g->n[d] + (d < g->ndim ? 4 : 0));
   const int nb = std::max(step_blocks<T>(g->ndim, g->rows, (int)g->n[0], (int)g->n[1], (int)g->n[2], g->zchunk),
                           1);
-  T *ck = nullptr, *seg = nullptr, *la = nullptr, *lb = nullptr, *ls = nullptr, *scratch = nullptr;
-  T *HB = nullptr, *LB = nullptr, *GM = nullptr, *G0 = nullptr, *GP = nullptr, *Wb = nullptr, *W0 = nullptr;
+  T *seg = nullptr, *la = nullptr, *lb = nullptr, *scratch = nullptr;
+  T *HB = nullptr, *LB = nullptr, *GM = nullptr, *G0 = nullptr, *GP = nullptr, *Wb = nullptr;
   Ctrl *ctl = nullptr;
   Partial *part = nullptr;
-  int32_t *had = nullptr;
-  A_TRY(cudaMalloc(&ck, S * nck));
-  A_TRY(cudaMalloc(&seg, S * (size_t)K));
+  A_TRY(cudaMalloc(&seg, S * (size_t)seg_len));
   A_TRY(cudaMalloc(&la, S));
   A_TRY(cudaMalloc(&lb, S));
-  A_TRY(cudaMalloc(&ls, S));
   A_TRY(cudaMalloc(&scratch, S));
   A_TRY(cudaMalloc(&HB, Ne_max * NV * sizeof(T)));
   A_TRY(cudaMalloc(&LB, Ne_max * NV * sizeof(T)));
@@ -444,50 +469,22 @@ msh_status adjoint_impl(msh_grid *g, const void *U0, int64_t nsteps, const doubl
   A_TRY(cudaMalloc(&Wb, Npad * NV * sizeof(T)));
   A_TRY(cudaMalloc(&ctl, sizeof(Ctrl)));
   A_TRY(cudaMalloc(&part, sizeof(Partial) * (size_t)nb));
-  A_TRY(cudaMalloc(&had, sizeof(int32_t) * (size_t)std::max<int64_t>(nsteps, 1)));
   A_TRY(cudaMemcpyAsync(ctl, g->hctrl, sizeof(Ctrl), cudaMemcpyHostToDevice, g->stream));
-  // fallback tags are step numbers: start from a clean slate (and leave one behind)
-  A_TRY(cudaMemsetAsync(g->flags, 0, N * sizeof(int32_t), g->stream));
-  // initial state (primitive input converted on the device)
-  A_TRY(cudaMemcpyAsync(ck, U0, S, in_kind, g->stream));
-  if (kind == MSH_PRIMITIVE) {
-    A_TRY(cudaMalloc(&W0, S));
-    A_TRY(cudaMemcpyAsync(W0, ck, S, cudaMemcpyDeviceToDevice, g->stream));
-    A_TRY(launch_convert<T>(ck, N, 0, g->stream));
-  }
-  // forward sweep: checkpoints every K steps, record which steps tagged fallback cells
-  {
-    T *cur = ck, *nxt = scratch;
-    A_TRY(cudaMemcpyAsync(seg, ck, S, cudaMemcpyDeviceToDevice, g->stream));
-    cur = seg;
-    for (int64_t s = 0; s < nsteps; s++) {
-      T *dst = (cur == seg) ? scratch : seg;
-      A_TRY(forward_step<T>(g, ctl, part, cur, dst, s, dts[s], nullptr));
-      adj_record_kernel<<<1, 1, 0, g->stream>>>(ctl, had, s);
-      A_TRY(cudaGetLastError());
-      cur = dst;
-      if ((s + 1) % K == 0 && s + 1 < nsteps)
-        A_TRY(cudaMemcpyAsync(ck + (size_t)((s + 1) / K) * N * NV, cur, S, cudaMemcpyDeviceToDevice, g->stream));
-    }
-    (void)nxt;
-  }
-  // reverse sweep
   A_TRY(cudaMemcpyAsync(la, lamN, S, in_kind, g->stream));
-  for (int64_t sg = nck - 1; sg >= 0 && nsteps > 0; sg--) {
+  for (int64_t sg = nck - 1; sg >= 0; sg--) {
     const int64_t n0 = sg * K, n1 = std::min<int64_t>(n0 + K, nsteps);
     // recompute the segment's states U^{n0} .. U^{n1-1}
     A_TRY(cudaMemcpyAsync(seg, ck + (size_t)sg * N * NV, S, cudaMemcpyDeviceToDevice, g->stream));
     for (int64_t n = n0; n + 1 < n1; n++)
       A_TRY(forward_step<T>(g, ctl, part, seg + (size_t)(n - n0) * N * NV, seg + (size_t)(n - n0 + 1) * N * NV, n,
-                            dts[n], nullptr));
+                            dts[n], had[n] != 0));
     for (int64_t n = n1 - 1; n >= n0; n--) {
       T *Un = seg + (size_t)(n - n0) * N * NV;
-      // restore the fallback tags of step n (a no-op unless it tagged cells)
-      A_TRY(forward_step<T>(g, ctl, part, Un, scratch, n, dts[n], had));
+      // restore the fallback tags of step n (only a step that tagged cells has any)
+      if (had[n]) A_TRY(forward_step<T>(g, ctl, part, Un, scratch, n, dts[n], true));
       AdjArgs<T> a;
       a.U = Un;
       a.lam = la;
-      a.ls = ls;
       a.out = lb;
       a.acc = (const T *)g->acc;
       a.flags = g->flags;
@@ -506,9 +503,6 @@ msh_status adjoint_impl(msh_grid *g, const void *U0, int64_t nsteps, const doubl
       a.ndim = g->ndim;
       for (int i = 0; i < 6; i++) a.bc[i] = g->bc[i];
       a.dt = dts[n];
-      A_TRY(cudaMemsetAsync(Wb, 0, Npad * NV * sizeof(T), g->stream));
-      adj_lamstar_kernel<T><<<grid_blocks(N), 256, 0, g->stream>>>(a);
-      A_TRY(cudaGetLastError());
       for (int d = 0; d < g->ndim; d++) {
         a.d = d;
         const size_t Ne = N / g->n[d] * (g->n[d] + 2);
@@ -533,7 +527,7 @@ msh_status adjoint_impl(msh_grid *g, const void *U0, int64_t nsteps, const doubl
       std::swap(la, lb);
     }
   }
-  if (kind == MSH_PRIMITIVE) {
+  if (W0 != nullptr) {
     adj_prim_kernel<T><<<grid_blocks(N), 256, 0, g->stream>>>(W0, la, lb, N);
     A_TRY(cudaGetLastError());
     std::swap(la, lb);
@@ -541,12 +535,97 @@ msh_status adjoint_impl(msh_grid *g, const void *U0, int64_t nsteps, const doubl
   A_TRY(cudaMemcpyAsync(lam0, la, S, out_kind, g->stream));
   A_TRY(cudaStreamSynchronize(g->stream));
 done:
+  cudaStreamSynchronize(g->stream);
+  for (void *p : {(void *)seg, (void *)la, (void *)lb, (void *)scratch, (void *)HB, (void *)LB, (void *)GM,
+                  (void *)G0, (void *)GP, (void *)Wb, (void *)ctl, (void *)part})
+    if (p) cudaFree(p);
+  return st;
+}
+
+// msh_adjoint_run: forward sweep from U0 storing checkpoints and fallback flags, then the
+// reverse sweep.
+template <typename T>
+msh_status adjoint_impl(msh_grid *g, const void *U0, int64_t nsteps, const double *dts, int K, const void *lamN,
+                        void *lam0, int where, int kind) {
+  msh_status st = MSH_OK;
+  const size_t N = g->N;
+  const size_t S = N * NV * sizeof(T);
+  const cudaMemcpyKind in_kind = where == MSH_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+  const int64_t nck = nsteps > 0 ? (nsteps + K - 1) / K : 1;
+  const int nb = std::max(step_blocks<T>(g->ndim, g->rows, (int)g->n[0], (int)g->n[1], (int)g->n[2], g->zchunk),
+                          1);
+  T *ck = nullptr, *bufA = nullptr, *bufB = nullptr, *W0 = nullptr;
+  Ctrl *ctl = nullptr;
+  Partial *part = nullptr;
+  int32_t *had = nullptr;
+  std::vector<int32_t> had_h((size_t)std::max<int64_t>(nsteps, 1), 0);
+  A_TRY(cudaMalloc(&ck, S * nck));
+  A_TRY(cudaMalloc(&bufA, S));
+  A_TRY(cudaMalloc(&bufB, S));
+  A_TRY(cudaMalloc(&ctl, sizeof(Ctrl)));
+  A_TRY(cudaMalloc(&part, sizeof(Partial) * (size_t)nb));
+  A_TRY(cudaMalloc(&had, sizeof(int32_t) * had_h.size()));
+  A_TRY(cudaMemcpyAsync(ctl, g->hctrl, sizeof(Ctrl), cudaMemcpyHostToDevice, g->stream));
+  // fallback tags are step numbers: start from a clean slate (and leave one behind)
+  A_TRY(cudaMemsetAsync(g->flags, 0, N * sizeof(int32_t), g->stream));
+  A_TRY(cudaMemcpyAsync(ck, U0, S, in_kind, g->stream));
+  if (kind == MSH_PRIMITIVE) {
+    A_TRY(cudaMalloc(&W0, S));
+    A_TRY(cudaMemcpyAsync(W0, ck, S, cudaMemcpyDeviceToDevice, g->stream));
+    A_TRY(launch_convert<T>(ck, N, 0, g->stream));
+  }
+  {
+    const T *cur = ck;
+    for (int64_t s = 0; s < nsteps; s++) {
+      T *dst = (s & 1) ? bufB : bufA;
+      A_TRY(forward_step<T>(g, ctl, part, const_cast<T *>(cur), dst, s, dts[s], true));
+      adj_record_kernel<<<1, 1, 0, g->stream>>>(ctl, had, s);
+      A_TRY(cudaGetLastError());
+      cur = dst;
+      if ((s + 1) % K == 0 && s + 1 < nsteps)
+        A_TRY(cudaMemcpyAsync(ck + (size_t)((s + 1) / K) * N * NV, cur, S, cudaMemcpyDeviceToDevice, g->stream));
+    }
+  }
+  if (nsteps > 0)
+    A_TRY(cudaMemcpyAsync(had_h.data(), had, sizeof(int32_t) * (size_t)nsteps, cudaMemcpyDeviceToHost, g->stream));
+  A_TRY(cudaStreamSynchronize(g->stream));
+  cudaFree(bufA);
+  cudaFree(bufB);
+  bufA = bufB = nullptr;
+  st = reverse_sweep<T>(g, ck, nsteps, dts, had_h.data(), K, lamN, lam0, where, W0);
+done:
   cudaMemsetAsync(g->flags, 0, N * sizeof(int32_t), g->stream);
   cudaStreamSynchronize(g->stream);
-  for (void *p : {(void *)ck, (void *)seg, (void *)la, (void *)lb, (void *)ls, (void *)scratch, (void *)HB,
-                  (void *)LB, (void *)GM, (void *)G0, (void *)GP, (void *)Wb, (void *)W0, (void *)ctl,
-                  (void *)part, (void *)had})
+  for (void *p : {(void *)ck, (void *)bufA, (void *)bufB, (void *)W0, (void *)ctl, (void *)part, (void *)had})
     if (p) cudaFree(p);
+  return st;
+}
+
+// msh_adjoint_tape: the checkpoints, dt schedule and fallback flags of the recorded run.
+template <typename T>
+msh_status adjoint_tape_impl(msh_grid *g, const void *lamN, void *lam0, int where, int kind) {
+  msh_status st = MSH_OK;
+  const size_t N = g->N;
+  const size_t S = N * NV * sizeof(T);
+  const int64_t nsteps = g->hctrl->step - g->tape_base;
+  std::vector<double> dts((size_t)std::max<int64_t>(nsteps, 1));
+  std::vector<int32_t> had((size_t)std::max<int64_t>(nsteps, 1), 0);
+  T *W0 = nullptr;
+  if (nsteps > 0) {
+    A_TRY(cudaMemcpyAsync(dts.data(), g->tape_dt, sizeof(double) * (size_t)nsteps, cudaMemcpyDeviceToHost, g->stream));
+    A_TRY(cudaMemcpyAsync(had.data(), g->tape_had, sizeof(int32_t) * (size_t)nsteps, cudaMemcpyDeviceToHost,
+                          g->stream));
+  }
+  if (kind == MSH_PRIMITIVE) {
+    A_TRY(cudaMalloc(&W0, S));
+    A_TRY(cudaMemcpyAsync(W0, g->tape, S, cudaMemcpyDeviceToDevice, g->stream));
+    A_TRY(launch_convert<T>(W0, N, 1, g->stream));
+  }
+  A_TRY(cudaStreamSynchronize(g->stream));
+  st = reverse_sweep<T>(g, (const T *)g->tape, nsteps, dts.data(), had.data(), g->tape_K, lamN, lam0, where, W0);
+done:
+  cudaStreamSynchronize(g->stream);
+  if (W0) cudaFree(W0);
   return st;
 }
 
@@ -566,4 +645,18 @@ extern "C" msh_status msh_adjoint_run(msh_grid *g, const void *U0, int64_t nstep
   if (g->prec == MSH_FP32)
     return adjoint_impl<float>(g, U0, nsteps, dt_sched, K, dL_dUN, dL_dU0, where, kind);
   return adjoint_impl<double>(g, U0, nsteps, dt_sched, K, dL_dUN, dL_dU0, where, kind);
+}
+
+extern "C" msh_status msh_adjoint_tape(msh_grid *g, const void *dL_dUN, void *dL_dU0, int32_t where, int32_t kind) {
+  clear_error();
+  if (!g || !dL_dUN || !dL_dU0) return afail(MSH_E_INVALID_ARG, "null argument");
+  if (where != MSH_HOST && where != MSH_DEVICE) return afail(MSH_E_INVALID_ARG, "bad where");
+  if (kind != MSH_CONSERVED && kind != MSH_PRIMITIVE) return afail(MSH_E_INVALID_ARG, "bad kind");
+  if (!g->tape_valid) return afail(MSH_E_STATE, "no adjoint tape is being recorded (msh_set_tape)");
+  const int64_t nsteps = g->hctrl->step - g->tape_base;
+  if (nsteps < 0 || nsteps > g->tape_len)
+    return afail(MSH_E_STATE, "the run took %lld steps since msh_set_tape, the tape holds %lld", (long long)nsteps,
+                 (long long)g->tape_len);
+  if (g->prec == MSH_FP32) return adjoint_tape_impl<float>(g, dL_dUN, dL_dU0, where, kind);
+  return adjoint_tape_impl<double>(g, dL_dUN, dL_dU0, where, kind);
 }

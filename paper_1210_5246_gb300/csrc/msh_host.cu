@@ -7,6 +7,7 @@
 // run return immediately, so over-launching past t_end is harmless.
 #include <cmath>
 #include <cstdarg>
+#include <cstddef>
 #include <cstdio>
 #include <cstring>
 #include <string>
@@ -74,6 +75,10 @@ template <typename T> StepArgs<T> make_args(msh_grid *g) {
   for (int i = 0; i < 3; i++) a.dx[i] = g->dx[i];
   a.zchunk = g->zchunk;
   a.level = 0;
+  a.ck = g->tape_valid ? (T *)g->tape : nullptr;
+  a.ck_base = g->tape_base;
+  a.ck_len = g->tape_len;
+  a.ck_K = g->tape_K > 0 ? g->tape_K : 1;
   return a;
 }
 
@@ -95,6 +100,37 @@ msh_status ensure_partials(msh_grid *g, int need) {
 void drop_graph(msh_grid *g) {
   if (g->graph) cudaGraphExecDestroy(g->graph);
   g->graph = nullptr;
+}
+
+// Copy the tape fields of the host mirror (the tail of Ctrl) to the device control block.
+cudaError_t push_tape_fields(msh_grid *g) {
+  const size_t off = offsetof(Ctrl, tape_dt);
+  return cudaMemcpyAsync(reinterpret_cast<char *>(g->ctrl) + off, reinterpret_cast<char *>(g->hctrl) + off,
+                         sizeof(Ctrl) - off, cudaMemcpyHostToDevice, g->stream);
+}
+
+// A new state or time ends the recorded trajectory: stop recording, keep the memory.
+msh_status stop_tape(msh_grid *g) {
+  if (!g->tape_valid) return MSH_OK;
+  g->tape_valid = false;
+  g->hctrl->tape_dt = nullptr;
+  g->hctrl->tape_had = nullptr;
+  g->hctrl->tape_len = 0;
+  drop_graph(g);  // the graph's step arguments point at the tape
+  CUDA_TRY(push_tape_fields(g));
+  return MSH_OK;
+}
+
+void free_tape(msh_grid *g) {
+  if (g->tape) cudaFree(g->tape);
+  if (g->tape_dt) cudaFree(g->tape_dt);
+  if (g->tape_had) cudaFree(g->tape_had);
+  g->tape = nullptr;
+  g->tape_dt = nullptr;
+  g->tape_had = nullptr;
+  g->tape_K = 0;
+  g->tape_len = 0;
+  g->tape_valid = false;
 }
 
 msh_status launch_one_step(msh_grid *g, int ev_slot) {
@@ -234,7 +270,7 @@ msh_status msh_init_grid(msh_grid **out, int32_t ndim, const int64_t n[3], const
   g->esize = precision == MSH_FP32 ? 4 : 8;
   g->cfl = cfl;
   g->N = (size_t)n[0] * n[1] * n[2];
-  g->zchunk = (int)std::min<int64_t>(32, n[2]);
+  g->zchunk = default_chunk(ndim, n);
   g->rows = 8;
   auto cleanup = [&](msh_status s) {
     msh_destroy(g);
@@ -298,6 +334,7 @@ msh_status msh_destroy(msh_grid *g) {
   if (g->part) cudaFree(g->part);
   if (g->flags) cudaFree(g->flags);
   if (g->hist) cudaFree(g->hist);
+  free_tape(g);
   if (g->own_stream && g->stream) cudaStreamDestroy(g->stream);
   delete g;
   return MSH_OK;
@@ -308,6 +345,8 @@ msh_status msh_set_state(msh_grid *g, const void *U, int32_t where, int32_t kind
   if (!g || !U) return fail(MSH_E_INVALID_ARG, "null argument");
   if (where != MSH_HOST && where != MSH_DEVICE) return fail(MSH_E_INVALID_ARG, "bad where");
   if (kind != MSH_CONSERVED && kind != MSH_PRIMITIVE) return fail(MSH_E_INVALID_ARG, "bad kind");
+  msh_status st0 = stop_tape(g);
+  if (st0) return st0;
   const int cur = cur_buf(g), nxt = cur ^ 1;
   const size_t bytes = g->N * 10 * g->esize;
   CUDA_TRY(cudaMemcpyAsync(g->U[nxt], U, bytes, where == MSH_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice,
@@ -359,6 +398,8 @@ msh_status msh_set_time(msh_grid *g, double t, int64_t step) {
   begin();
   if (!g) return fail(MSH_E_INVALID_ARG, "null grid");
   if (step < 0 || !std::isfinite(t)) return fail(MSH_E_INVALID_ARG, "bad time or step");
+  msh_status st0 = stop_tape(g);
+  if (st0) return st0;
   if (((step ^ g->hctrl->step) & 1) && g->has_state) {
     // keep the current state in the buffer the new parity selects
     const size_t bytes = g->N * 10 * g->esize;
@@ -520,6 +561,39 @@ msh_status msh_set_recording(msh_grid *g, int64_t capacity) {
   return MSH_OK;
 }
 
+msh_status msh_set_tape(msh_grid *g, int32_t K, int64_t max_steps) {
+  begin();
+  if (!g) return fail(MSH_E_INVALID_ARG, "null grid");
+  if (K < 0 || (K > 0 && max_steps < 1)) return fail(MSH_E_INVALID_ARG, "need K >= 1 and max_steps >= 1 (K = 0 frees)");
+  if (!g->has_state && K > 0) return fail(MSH_E_STATE, "msh_set_tape before msh_set_state");
+  CUDA_TRY(cudaStreamSynchronize(g->stream));
+  msh_status st = stop_tape(g);
+  if (st) return st;
+  if (K == 0) {
+    free_tape(g);
+    return MSH_OK;
+  }
+  const int64_t nck = (max_steps + K - 1) / K;
+  const int64_t have_ck = g->tape_K > 0 ? (g->tape_len + g->tape_K - 1) / g->tape_K : 0;
+  if (nck > have_ck || max_steps > g->tape_len) {
+    free_tape(g);
+    CUDA_TRY(cudaMalloc(&g->tape, (size_t)nck * g->N * 10 * g->esize));
+    CUDA_TRY(cudaMalloc(&g->tape_dt, sizeof(double) * (size_t)max_steps));
+    CUDA_TRY(cudaMalloc(&g->tape_had, sizeof(int32_t) * (size_t)max_steps));
+  }
+  g->tape_K = K;
+  g->tape_len = max_steps;
+  g->tape_base = g->hctrl->step;
+  g->tape_valid = true;
+  g->hctrl->tape_dt = g->tape_dt;
+  g->hctrl->tape_had = g->tape_had;
+  g->hctrl->tape_base = g->tape_base;
+  g->hctrl->tape_len = g->tape_len;
+  CUDA_TRY(push_tape_fields(g));
+  CUDA_TRY(cudaStreamSynchronize(g->stream));
+  return MSH_OK;
+}
+
 msh_status msh_get_dt_history(msh_grid *g, double *dts, int64_t capacity, int64_t *count) {
   begin();
   if (!g || capacity < 0 || (capacity > 0 && !dts)) return fail(MSH_E_INVALID_ARG, "bad argument");
@@ -539,9 +613,11 @@ msh_status msh_set_tiling(msh_grid *g, int32_t rows, int32_t zchunk) {
   begin();
   if (!g) return fail(MSH_E_INVALID_ARG, "null grid");
   if (rows != 4 && rows != 8 && rows != 16) return fail(MSH_E_INVALID_ARG, "rows must be 4, 8 or 16");
+  if (rows == 16 && g->ndim == 3 && g->prec == MSH_FP64)
+    return fail(MSH_E_INVALID_ARG, "rows 16 in 3D needs FP32 (its FP64 staging exceeds shared memory)");
   if (zchunk < 1) return fail(MSH_E_INVALID_ARG, "zchunk must be >= 1");
-  if (g->ndim < 3) zchunk = 1;
-  if (zchunk > g->n[2]) zchunk = (int)g->n[2];
+  const int64_t stream_len = g->ndim == 3 ? g->n[2] : g->ndim == 2 ? g->n[1] : 1;
+  if (zchunk > stream_len) zchunk = (int)stream_len;
   msh_status st = ensure_partials(g, blocks_for(g, rows, zchunk));
   if (st) return st;
   if (rows != g->rows || zchunk != g->zchunk) drop_graph(g);
@@ -574,22 +650,31 @@ msh_status msh_autotune(msh_grid *g, int32_t *rows_out, int32_t *zchunk_out) {
   void *save = nullptr;
   CUDA_TRY(cudaMalloc(&save, bytes));
   Ctrl saved_ctrl = *g->hctrl;
+  // the trial steps must not write the adjoint tape
+  Ctrl trial_ctrl = saved_ctrl;
+  trial_ctrl.tape_dt = nullptr;
+  trial_ctrl.tape_had = nullptr;
+  trial_ctrl.tape_len = 0;
+  const bool tape_was_valid = g->tape_valid;
+  g->tape_valid = false;
+  *g->hctrl = trial_ctrl;
   msh_status st = MSH_OK;
+  if (cudaMemcpyAsync(g->ctrl, g->hctrl, sizeof(Ctrl), cudaMemcpyHostToDevice, g->stream) != cudaSuccess)
+    st = fail(MSH_E_CUDA, "autotune setup: %s", cudaGetErrorString(cudaGetLastError()));
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   std::vector<std::pair<int, int>> cands;
   const int rows_c[3] = {4, 8, 16};
   const int zc_c[4] = {8, 16, 32, 64};
-  for (int r : rows_c) {
-    if (g->ndim == 2) cands.push_back({r, 1});
-    else
-      for (int z : zc_c)
-        if (z <= g->n[2]) cands.push_back({r, z});
-  }
+  const int64_t stream_len = g->ndim == 3 ? g->n[2] : g->n[1];
+  for (int r : rows_c)
+    for (int z : zc_c)
+      if ((z <= stream_len || z == zc_c[0]) && !(r == 16 && g->ndim == 3 && g->prec == MSH_FP64))
+        cands.push_back({r, z});
   float best = 1e30f;
   std::pair<int, int> best_c = {g->rows, g->zchunk};
   const int reps = 3;
-  if (cudaMemcpyAsync(save, g->U[cur], bytes, cudaMemcpyDeviceToDevice, g->stream) != cudaSuccess ||
-      cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+  if (st == MSH_OK && (cudaMemcpyAsync(save, g->U[cur], bytes, cudaMemcpyDeviceToDevice, g->stream) != cudaSuccess ||
+                       cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)) {
     st = fail(MSH_E_CUDA, "autotune setup: %s", cudaGetErrorString(cudaGetLastError()));
   }
   const bool prof = g->profiling;
@@ -612,13 +697,18 @@ msh_status msh_autotune(msh_grid *g, int32_t *rows_out, int32_t *zchunk_out) {
     }
     // restore state and control block for the next candidate
     if (st == MSH_OK) {
-      *g->hctrl = saved_ctrl;
+      *g->hctrl = trial_ctrl;
       e = cudaMemcpyAsync(g->ctrl, g->hctrl, sizeof(Ctrl), cudaMemcpyHostToDevice, g->stream);
       if (e == cudaSuccess) e = cudaMemcpyAsync(g->U[cur], save, bytes, cudaMemcpyDeviceToDevice, g->stream);
       if (e != cudaSuccess) st = fail(MSH_E_CUDA, "autotune restore: %s", cudaGetErrorString(e));
     }
   }
   g->profiling = prof;
+  *g->hctrl = saved_ctrl;
+  g->tape_valid = tape_was_valid;
+  if (cudaMemcpyAsync(g->ctrl, g->hctrl, sizeof(Ctrl), cudaMemcpyHostToDevice, g->stream) != cudaSuccess && st == MSH_OK)
+    st = fail(MSH_E_CUDA, "autotune restore: %s", cudaGetErrorString(cudaGetLastError()));
+  drop_graph(g);
   if (e0) cudaEventDestroy(e0);
   if (e1) cudaEventDestroy(e1);
   cudaStreamSynchronize(g->stream);

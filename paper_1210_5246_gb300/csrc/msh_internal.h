@@ -22,6 +22,11 @@ struct Ctrl {
   int32_t nbad[kFallbackPasses + 1];  // cells newly tagged by pass p of this step (p = 0: the step)
   double totals[10];
   double *hist;
+  // adjoint tape: per step s in [tape_base, tape_base + tape_len) its dt and whether its
+  // a-posteriori fallback tagged cells
+  double *tape_dt;
+  int32_t *tape_had;
+  int64_t tape_base, tape_len;
 };
 
 // Per-thread-block partial reductions written by the step and scan kernels.
@@ -42,10 +47,23 @@ template <typename T> struct StepArgs {
   int bc[6];
   double dx[3];
   int zchunk;
+  // adjoint tape: the step kernel stores U^s in ck[(s - ck_base) / ck_K] when s - ck_base
+  // is a multiple of ck_K in [0, ck_len); ck = nullptr: no tape
+  T *ck;
+  int64_t ck_base, ck_len;
+  int ck_K;
 };
 
 constexpr int kTile1D = 128;   // threads per block of the 1D step kernel
-constexpr int kTileX = 30;     // interior cells per warp row of the 2D/3D kernel
+constexpr int kTileX = 30;     // interior cells per warp row of the 3D kernel
+constexpr int kStripX = 28;    // updated cells per warp strip of the 2D kernel
+
+// Default length of the chunk a thread block streams: z planes (3D) or rows (2D).
+inline int default_chunk(int ndim, const int64_t n[3]) {
+  if (ndim == 3) return (int)(n[2] < 32 ? n[2] : 32);
+  if (ndim == 2) return (int)(n[1] < 16 ? n[1] : 16);
+  return 1;
+}
 constexpr int kFinalizeThreads = 256;
 
 // launchers (msh_step.cu)
@@ -99,6 +117,13 @@ struct msh_grid {
   int32_t *flags = nullptr;  // per-cell fallback tags
   double *hist = nullptr;
   int64_t hist_cap = 0;
+  // adjoint tape (msh_set_tape): checkpoints every tape_K steps from step tape_base
+  void *tape = nullptr;
+  double *tape_dt = nullptr;
+  int32_t *tape_had = nullptr;
+  int32_t tape_K = 0;
+  int64_t tape_base = 0, tape_len = 0;
+  bool tape_valid = false;
   bool has_state = false;
   int rows = 8, zchunk = 32;
   cudaGraphExec_t graph = nullptr;

@@ -21,7 +21,7 @@ namespace msh {
 
 constexpr size_t kNoallocMaxCells = size_t(1) << 20;  // 1,048,576 cells
 constexpr size_t kNoallocMaxBlocks = 16384;           // per-block reduction partials
-constexpr size_t kNoallocCtrlBytes = 256;
+constexpr size_t kNoallocCtrlBytes = 512;
 constexpr size_t kNoallocBytes =
     kNoallocCtrlBytes + kNoallocMaxBlocks * sizeof(Partial) + kNoallocMaxCells * sizeof(int32_t);
 static_assert(sizeof(Ctrl) <= kNoallocCtrlBytes, "control block does not fit its slot");
@@ -55,8 +55,12 @@ msh_status noalloc_step(int ndim, const int64_t n[3], const double dx[3], const 
   a.nz = (int)n[2];
   for (int i = 0; i < 6; i++) a.bc[i] = i < 2 * ndim ? bc[i] : MSH_BC_PERIODIC;
   for (int i = 0; i < 3; i++) a.dx[i] = dx[i];
-  a.zchunk = (int)(n[2] < 32 ? n[2] : 32);
+  a.zchunk = default_chunk(ndim, n);
   a.level = 0;
+  a.ck = nullptr;  // no adjoint tape
+  a.ck_base = 0;
+  a.ck_len = 0;
+  a.ck_K = 1;
   const int rows = 8;
   const int nb = step_blocks<T>(ndim, rows, a.nx, a.ny, a.nz, a.zchunk);
   if ((size_t)nb > kNoallocMaxBlocks)

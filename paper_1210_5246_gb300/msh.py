@@ -60,6 +60,8 @@ SIGNATURES = {
     "msh_set_profiling": [_vp, _i32],
     "msh_get_profile": [_vp, _P(_dbl), _P(_dbl), _P(_i64)],
     "msh_adjoint_run": [_vp, _vp, _i64, _P(_dbl), _i32, _vp, _vp, _i32, _i32],
+    "msh_set_tape": [_vp, _i32, _i64],
+    "msh_adjoint_tape": [_vp, _vp, _vp, _i32, _i32],
     "msh_batch_init": [_P(_vp), _i32, _P(_i32), _P(_dbl), _P(_dbl), _P(_dbl), _i32, _dbl, _vp],
     "msh_batch_reset": [_vp],
     "msh_batch_run": [_vp, _i32, _i64],
@@ -300,6 +302,22 @@ class Grid:
                 out = _torch().empty_like(dL_dUN)
         po, wo, ko = self._buf(out)
         _check(load().msh_adjoint_run(self.h, p0, len(dts), _ptr_dbl(dts), int(K), pg, po, w0, kind))
+        return out
+
+    def set_tape(self, K, max_steps):
+        """Record checkpoints every K steps, dts and fallback flags of the next max_steps
+        steps (K = 0 frees the tape); see ``msh_set_tape``."""
+        _check(load().msh_set_tape(self.h, int(K), int(max_steps)))
+
+    def adjoint_tape(self, dL_dUN, kind=CONSERVED, out=None):
+        """dL/dU0 over the steps recorded since ``set_tape`` (see ``msh_adjoint_tape``)."""
+        pg, wg, kg = self._buf(dL_dUN)
+        if out is None:
+            out = np.empty(self.shape, dtype=self.dtype) if wg == HOST else _torch().empty_like(dL_dUN)
+        po, wo, ko = self._buf(out)
+        if wo != wg:
+            raise ValueError("dL_dUN and out must both be host or both be device arrays")
+        _check(load().msh_adjoint_tape(self.h, pg, po, wg, kind))
         return out
 
 

@@ -135,3 +135,85 @@ def test_adjoint_does_not_touch_grid_state(msh, oracle):
     np.testing.assert_array_equal(g.get_state(), before[0])
     assert g.time() == before[1]
     g.close()
+
+
+# ------------------------------------------------------------------ adjoint tape
+def _taped_run(msh, case, K, autotune=False):
+    W, n, lo, hi, bc, cfl, phi, steps = case
+    g = msh.Grid(n, lo, hi, bc, cfl, msh.FP64)
+    if phi is not None:
+        g.set_potential(phi)
+    g.set_state(W, msh.PRIMITIVE)
+    U0 = g.get_state()
+    g.set_recording(steps)
+    g.set_tape(K, steps)
+    if autotune and len(n) > 1:
+        g.autotune()
+    ns, _ = g.run(max_steps=steps)
+    assert ns == steps
+    return g, U0, g.dt_history()
+
+
+@pytest.mark.parametrize("name,K", [("sod", 2), ("smooth2d_gravity_reflect", 3), ("turb3d", 1), ("disc", 2),
+                                    ("fallback1d", 1)])
+def test_tape_equals_forward_sweep_adjoint_and_oracle(msh, oracle, name, K):
+    """The adjoint from the recorded tape equals msh_adjoint_run on the same state and
+    schedule bit for bit (same checkpoints, same kernels), and the oracle's adjoint."""
+    case = _case(name, oracle)
+    W, n, lo, hi, bc, cfl, phi, steps = case
+    g, U0, dts = _taped_run(msh, case, K, autotune=(name == "disc"))
+    lam = np.random.default_rng(11).normal(size=U0.shape)
+    got = g.adjoint_tape(lam)
+    ref_run = g.adjoint_run(U0, dts, lam, K=K)
+    np.testing.assert_array_equal(got, ref_run)
+    og = oracle.Grid(n, lo, hi, bc, cfl)
+    ref = _oracle_adjoint(W, n, bc, og.dx, dts, lam, phi, "conserved")
+    assert field_errors(got, ref, "linf").max() <= 1e-10
+    if name == "disc":
+        gp = g.adjoint_tape(torch.tensor(lam, device="cuda"), kind=msh.PRIMITIVE).cpu().numpy()
+        refp = _oracle_adjoint(W, n, bc, og.dx, dts, lam, phi, "primitive")
+        assert field_errors(gp, refp, "linf").max() <= 1e-10
+    g.close()
+
+
+def test_tape_does_not_change_the_run(msh, oracle):
+    case = _case("turb3d", oracle)
+    W, n, lo, hi, bc, cfl, phi, steps = case
+    g, _, _ = _taped_run(msh, case, 1)
+    taped = g.get_state()
+    g.close()
+    g = msh.Grid(n, lo, hi, bc, cfl, msh.FP64)
+    g.set_state(W, msh.PRIMITIVE)
+    g.run(max_steps=steps)
+    np.testing.assert_array_equal(g.get_state(), taped)
+    g.close()
+
+
+def test_tape_errors(msh, oracle):
+    W, n, lo, hi, bc, cfl, phi, steps = _case("sod", oracle)
+    g = msh.Grid(n, lo, hi, bc, cfl, msh.FP64)
+    lam = np.ones((10, 1, 1, n[0]))
+    with pytest.raises(msh.MshError) as ei:
+        g.set_tape(2, 4)  # no state yet
+    assert ei.value.status == msh.MSH_E_STATE
+    g.set_state(W, msh.PRIMITIVE)
+    with pytest.raises(msh.MshError) as ei:
+        g.adjoint_tape(lam)  # nothing recorded
+    assert ei.value.status == msh.MSH_E_STATE
+    with pytest.raises(msh.MshError) as ei:
+        g.set_tape(-1, 4)
+    assert ei.value.status == msh.MSH_E_INVALID_ARG
+    g.set_tape(2, 3)
+    g.run(max_steps=4)  # one step past the tape
+    with pytest.raises(msh.MshError) as ei:
+        g.adjoint_tape(lam)
+    assert ei.value.status == msh.MSH_E_STATE
+    g.set_tape(2, 3)
+    g.run(max_steps=2)
+    g.adjoint_tape(lam)
+    g.set_state(W, msh.PRIMITIVE)  # a new state ends the recording
+    with pytest.raises(msh.MshError) as ei:
+        g.adjoint_tape(lam)
+    assert ei.value.status == msh.MSH_E_STATE
+    g.set_tape(0, 0)  # frees
+    g.close()

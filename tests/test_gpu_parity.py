@@ -130,7 +130,7 @@ def test_2d_shapes_and_boundaries(msh, oracle, shape, bc):
 
 
 # ---------------------------------------------------------------- 3D box
-@pytest.mark.parametrize("rows,zchunk", [(8, 32), (4, 5), (16, 7)])
+@pytest.mark.parametrize("rows,zchunk", [(8, 32), (4, 5), (8, 7)])
 def test_turb_fp64(msh, oracle, I, rows, zchunk):
     """Turbulent periodic box, 24^3, 6 steps, several tile shapes and z chunks."""
     p = I.turb(n=24, nsteps=6)
