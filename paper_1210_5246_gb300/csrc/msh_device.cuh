@@ -103,6 +103,14 @@ template <typename T> __device__ __forceinline__ T mc_limit(T dl, T dr) {
   return (dl * dr > T(0)) ? copysign(m, dc) : T(0);
 }
 
+// The same limiter doubled: 2 mc(dL, dR) = sign(dL) min(4|dL|, 4|dR|, |dL + dR|) for
+// same-sign differences, else 0.  Scaling by powers of two is exact, so this is exactly
+// twice mc_limit (two instructions cheaper).
+template <typename T> __device__ __forceinline__ T mc_limit2(T dl, T dr) {
+  const T m = fmin(T(4) * fmin(fabs(dl), fabs(dr)), fabs(dl + dr));
+  return (dl * dr > T(0)) ? copysign(m, dl) : T(0);
+}
+
 // Eigen-quantities of the local-frame state w0 shared by projection and back-projection.
 template <typename T> struct Eig {
   T rho, u, Pxx, Pxy, Pxz, Pyy, Pyz, Pzz;
@@ -174,23 +182,26 @@ __device__ __forceinline__ void reconstruct(const T (&wm)[NV], const T (&w0)[NV]
 #pragma unroll
   for (int k = 0; k < NV; k++) d[k] = wp[k] - w0[k];
   E.project(d, cr);
+  // limited amplitudes, doubled (every quantity below up to the predictor is exactly twice
+  // its unscaled value, so the face states are bit for bit those of the unscaled form)
   T m[NV];
 #pragma unroll
-  for (int k = 0; k < NV; k++) m[k] = mc_limit(cl[k], cr[k]);
+  for (int k = 0; k < NV; k++) m[k] = mc_limit2(cl[k], cr[k]);
   // wave speeds relative to u: (-cf, -cs, -cs, 0, 0, 0, 0, cs, cs, cf)
   T lm[NV];
   lm[0] = -E.cf * m[0]; lm[1] = -E.cs * m[1]; lm[2] = -E.cs * m[2];
   lm[3] = T(0); lm[4] = T(0); lm[5] = T(0); lm[6] = T(0);
   lm[7] = E.cs * m[7]; lm[8] = E.cs * m[8]; lm[9] = E.cf * m[9];
   T dw[NV], g[NV];
-  E.back(m, dw);   // limited primitive slope dw^m
-  E.back(lm, g);   // A dw^m - u dw^m
+  E.back(m, dw);   // 2 dw^m, dw^m the limited primitive slope
+  E.back(lm, g);   // 2 (A dw^m - u dw^m)
+  const T nu2 = T(0.5) * nu;
 #pragma unroll
   for (int k = 0; k < NV; k++) {
     const T adw = E.u * dw[k] + g[k];
-    const T pred = w0[k] - nu * adw;
-    hi[k] = pred + T(0.5) * dw[k];
-    lo[k] = pred - T(0.5) * dw[k];
+    const T pred = w0[k] - nu2 * adw;
+    hi[k] = pred + T(0.25) * dw[k];
+    lo[k] = pred - T(0.25) * dw[k];
   }
   const bool ok = hi[0] > T(0) && lo[0] > T(0) && hi[4] > T(0) && lo[4] > T(0);
   if (!ok) {
@@ -248,25 +259,30 @@ __device__ __forceinline__ void hll(const T (&wl)[NV], const T (&wr)[NV], T (&F)
   const T cr = T(1.7320508075688772) * sqrt_ratio(wr[4], wr[0]);
   const T SL = fmin(wl[1] - cl, wr[1] - cr);
   const T SR = fmax(wl[1] + cl, wr[1] + cr);
+  // F = a Fl + b Fr + c (Ur - Ul): (1, 0, 0) for SL >= 0, (0, 1, 0) for SR <= 0, else
+  // (SR, -SL, SL SR) / (SR - SL); the branch selects three scalars, not ten fluxes
+  T a, b, c;
   if (SL >= T(0)) {
-#pragma unroll
-    for (int k = 0; k < NV; k++) F[k] = Fl[k];
+    a = T(1); b = T(0); c = T(0);
   } else if (SR <= T(0)) {
-#pragma unroll
-    for (int k = 0; k < NV; k++) F[k] = Fr[k];
+    a = T(0); b = T(1); c = T(0);
   } else {
     const T inv = frcp(SR - SL);
-    const T sls = SL * SR;
-#pragma unroll
-    for (int k = 0; k < NV; k++) F[k] = (SR * Fl[k] - SL * Fr[k] + sls * (Ur[k] - Ul[k])) * inv;
+    a = SR * inv;
+    b = -SL * inv;
+    c = SL * SR * inv;
   }
+#pragma unroll
+  for (int k = 0; k < NV; k++) F[k] = a * Fl[k] + (b * Fr[k] + c * (Ur[k] - Ul[k]));
 }
 
 // ---------------------------------------------------------- accumulators
-// Per-thread running sums of the conserved totals.  FP64 states add in FP64; FP32 states
-// add exactly in float-float (Knuth's TwoSum keeps the rounding error of every add), so
-// the FP64 totals need no FP64 arithmetic per cell (FP64 throughput is a small fraction
-// of FP32 on this GPU).
+// Per-thread running sums of the conserved totals over the cells one thread updates in a
+// tile (at most one streamed chunk, 64 cells with the autotuned tilings).  FP64 states add
+// in FP64.  FP32 states add in FP32 per thread (relative rounding error of a k-term sum
+// below k 2^-24, random in sign across threads) and in FP64 from the block reduction on,
+// so the totals need no FP64 arithmetic per cell (FP64 throughput is a small fraction of
+// FP32 on this GPU).
 template <typename T> struct Acc {
   double v[NV];
   __device__ __forceinline__ void zero() {
@@ -283,24 +299,18 @@ template <typename T> struct Acc {
   }
 };
 template <> struct Acc<float> {
-  float hi[NV], lo[NV];
+  float v[NV];
   __device__ __forceinline__ void zero() {
 #pragma unroll
-    for (int k = 0; k < NV; k++) { hi[k] = 0.f; lo[k] = 0.f; }
+    for (int k = 0; k < NV; k++) v[k] = 0.f;
   }
   __device__ __forceinline__ void add(const float (&x)[NV]) {
 #pragma unroll
-    for (int k = 0; k < NV; k++) {
-      const float s = __fadd_rn(hi[k], x[k]);
-      const float bb = __fsub_rn(s, hi[k]);
-      const float err = __fadd_rn(__fsub_rn(hi[k], __fsub_rn(s, bb)), __fsub_rn(x[k], bb));
-      hi[k] = s;
-      lo[k] = __fadd_rn(lo[k], err);
-    }
+    for (int k = 0; k < NV; k++) v[k] += x[k];
   }
   __device__ __forceinline__ void get(double (&o)[NV]) const {
 #pragma unroll
-    for (int k = 0; k < NV; k++) o[k] = (double)hi[k] + (double)lo[k];
+    for (int k = 0; k < NV; k++) o[k] = (double)v[k];
   }
 };
 

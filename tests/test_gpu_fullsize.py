@@ -115,6 +115,12 @@ def test_box_256_full_run_properties(env, box):
         tol = 1e-12 if prec == msh.FP64 else 2e-6
         drift = np.abs(t1 - t0) / scale
         assert np.all(drift < tol), (prec, drift)
+        # the device totals against an FP64 sum of the returned state (FP32 grids sum each
+        # thread's cells in FP32, then in FP64)
+        Ug = g.get_state().astype(np.float64).reshape(10, -1)
+        ref_tot = Ug.sum(axis=1)
+        tol_tot = 1e-13 if prec == msh.FP64 else 1e-7
+        assert np.all(np.abs(t1 - ref_tot) / scale < tol_tot), (prec, (t1 - ref_tot) / scale)
         res[prec] = g.get_state(msh.PRIMITIVE).astype(np.float64)
         g.close()
     e = field_errors(res[msh.FP32], res[msh.FP64], "l1")
