@@ -74,11 +74,14 @@ def dist_env():
 
 
 def kernel_source_hash():
-    h = hashlib.sha256()
+    """Hash of the source the 3D step kernel is compiled from: the per-cell arithmetic
+    (msh_device.cuh) and msh_step.cu up to the 2D kernel (helpers and step_tile_kernel)."""
     csrc = os.path.join(ROOT, "paper_1210_5246_gb300", "csrc")
-    for f in sorted(os.listdir(csrc)):
-        if f.endswith((".cu", ".cuh", ".h")):
-            h.update(open(os.path.join(csrc, f), "rb").read())
+    step = open(os.path.join(csrc, "msh_step.cu")).read()
+    cut = step.find("// ---------------------------------------------------------------- 2D kernel")
+    h = hashlib.sha256()
+    h.update(open(os.path.join(csrc, "msh_device.cuh"), "rb").read())
+    h.update(step[: cut if cut >= 0 else len(step)].encode())
     return h.hexdigest()[:16]
 
 
@@ -496,11 +499,19 @@ def run_suite_disc(msh, disc, stream, emit, n, nsteps, K=50):
     torch.cuda.synchronize()
     t_both = time.perf_counter() - t0
     D.close()
+    # the same loss and gradients in FP64 (the FP32 error is stated against them)
+    D64 = disc.DiscProblem(n=n, nsteps=nsteps, precision=msh.FP64, K=K, stream=stream.cuda_stream)
+    L64, gd64, gb64 = D64.value_and_grad()
+    D64.close()
+    gd_rel = float(torch.linalg.norm(gd - gd64) / torch.linalg.norm(gd64))
     cells = n * n
     emit({"workload": f"disc {n}^2 FP32, {nsteps} steps, K={K}", "loss": L, "dL_dbeta": gb,
           "forward_ms_per_step": t_fwd * 1e3 / nsteps, "adjoint_ms_per_step": (t_both - t_fwd) * 1e3 / nsteps,
           "adjoint_over_forward": (t_both - t_fwd) / t_fwd, "forward_cell_updates_per_s": cells * nsteps / t_fwd,
-          "adjoint_cell_updates_per_s": cells * nsteps / (t_both - t_fwd)})
+          "adjoint_cell_updates_per_s": cells * nsteps / (t_both - t_fwd),
+          "fp64": {"loss": L64, "dL_dbeta": gb64},
+          "fp32_error": {"loss_rel": abs(L - L64) / abs(L64), "dL_dbeta_rel": abs(gb - gb64) / abs(gb64),
+                         "dL_ddelta_rel_l2": gd_rel}})
 
 
 if __name__ == "__main__":

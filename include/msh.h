@@ -212,6 +212,38 @@ msh_status msh_set_tape(msh_grid *g, int32_t K, int64_t max_steps);
 msh_status msh_adjoint_tape(msh_grid *g, const void *dL_dUN, void *dL_dU0, int32_t where, int32_t kind);
 
 /*
+ * Slab decomposition: several grids, each owning a slab of one global grid along its last
+ * active axis (z in 3D, y in 2D, x in 1D) plus two halo layers copied from the
+ * neighbouring slabs before every step (the stencil radius of the step is two cells,
+ * Sec. 3.3).  A layer is one index of that axis, with all cells of the other axes.
+ *   msh_get_slab / msh_set_slab   copy `count` layers from layer `start` of the conserved
+ *                                 state to / from buf [10][count][...] in the grid's
+ *                                 precision (host or device per `where`; the caller owns
+ *                                 buf).  After msh_set_slab the next msh_step / msh_run
+ *                                 first recomputes the CFL time step.
+ *   msh_reduce_layers             FP64 totals, CFL dt (cfl / max over the layers of
+ *                                 sum_d (|u_d| + sqrt(3 P_dd/rho))/dx_d) and realizability of
+ *                                 layers [start, start + count) only (a slab without its halo);
+ *                                 any output may be NULL.
+ *   msh_step_dt                   one step with exactly dt (> 0; no CFL limit, no end time);
+ *                                 *tagged_cells (may be NULL) receives the number of cells the
+ *                                 a-posteriori fallback tagged in it.  The fallback couples
+ *                                 cells within a step, so a slab run equals the single-grid run
+ *                                 only for steps in which no rank tagged cells.
+ *   msh_set_cell_width            replaces the cell widths dx[d] (> 0, active dims) that
+ *                                 msh_init_grid derived from (hi - lo) / n: a slab of m
+ *                                 layers takes the global grid's widths exactly, which
+ *                                 (hi - lo) / m cannot always reproduce in floating point.
+ * Errors: MSH_E_INVALID_ARG for layers outside the grid, MSH_E_STATE without a state.
+ */
+msh_status msh_set_cell_width(msh_grid *g, const double dx[3]);
+msh_status msh_get_slab(msh_grid *g, int64_t start, int64_t count, void *buf, int32_t where);
+msh_status msh_set_slab(msh_grid *g, int64_t start, int64_t count, const void *buf, int32_t where);
+msh_status msh_reduce_layers(msh_grid *g, int64_t start, int64_t count, double totals[10], double *dt_cfl,
+                             int32_t *realizable);
+msh_status msh_step_dt(msh_grid *g, double dt, int32_t *tagged_cells);
+
+/*
  * Batched independent 1D Riemann problems ("tubes") on [0, 1] with the interface at 0.5
  * and outflow boundaries, each advanced to its own t_end with its own CFL time step.
  *   ntubes           number of tubes (>= 1)

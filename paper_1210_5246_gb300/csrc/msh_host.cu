@@ -222,6 +222,23 @@ msh_status prime(msh_grid *g, int which) {
 
 int cur_buf(msh_grid *g) { return (int)(g->hctrl->step & 1); }
 
+// After msh_set_slab the planned CFL step belongs to the state before the copy.
+msh_status refresh_dt(msh_grid *g) {
+  if (!g->dt_stale) return MSH_OK;
+  msh_status st = prime(g, cur_buf(g));
+  if (st == MSH_OK) g->dt_stale = false;
+  return st;
+}
+
+// Cells per layer of the last active axis, and the number of layers.
+void layer_geometry(const msh_grid *g, size_t *per_layer, int64_t *layers) {
+  const int ax = g->ndim - 1;
+  size_t p = 1;
+  for (int d = 0; d < ax; d++) p *= (size_t)g->n[d];
+  *per_layer = p;
+  *layers = g->n[ax];
+}
+
 }  // namespace
 
 // ------------------------------------------------------------------- ABI
@@ -334,6 +351,7 @@ msh_status msh_destroy(msh_grid *g) {
   if (g->part) cudaFree(g->part);
   if (g->flags) cudaFree(g->flags);
   if (g->hist) cudaFree(g->hist);
+  if (g->ctrl_aux) cudaFree(g->ctrl_aux);
   free_tape(g);
   if (g->own_stream && g->stream) cudaStreamDestroy(g->stream);
   delete g;
@@ -450,12 +468,38 @@ msh_status msh_set_potential(msh_grid *g, const double *phi, int32_t where) {
   return MSH_OK;
 }
 
+msh_status msh_set_cell_width(msh_grid *g, const double dx[3]) {
+  begin();
+  if (!g || !dx) return fail(MSH_E_INVALID_ARG, "null argument");
+  for (int d = 0; d < g->ndim; d++)
+    if (!(dx[d] > 0.0) || !std::isfinite(dx[d])) return fail(MSH_E_INVALID_ARG, "dx[%d] must be finite and > 0", d);
+  CUDA_TRY(cudaStreamSynchronize(g->stream));
+  drop_graph(g);  // the cell widths are baked into the graph's step arguments
+  for (int d = 0; d < g->ndim; d++) {
+    g->dx[d] = dx[d];
+    g->hi[d] = g->lo[d] + (double)g->n[d] * dx[d];
+  }
+  if (g->phi) {  // the acceleration is a difference quotient of the potential
+    cudaError_t e = g->prec == MSH_FP32
+                        ? launch_gravity_field<float>(g->phi, (float *)g->acc, g->ndim, (int)g->n[0], (int)g->n[1],
+                                                      (int)g->n[2], g->dx, g->stream)
+                        : launch_gravity_field<double>(g->phi, (double *)g->acc, g->ndim, (int)g->n[0], (int)g->n[1],
+                                                       (int)g->n[2], g->dx, g->stream);
+    if (e != cudaSuccess) return fail(MSH_E_CUDA, "gravity field: %s", cudaGetErrorString(e));
+  }
+  if (g->has_state) g->dt_stale = true;  // the CFL step depends on dx
+  CUDA_TRY(cudaStreamSynchronize(g->stream));
+  return MSH_OK;
+}
+
 msh_status msh_step(msh_grid *g, double dt_max, double *dt_taken) {
   begin();
   if (!g) return fail(MSH_E_INVALID_ARG, "null grid");
   if (!g->has_state) return fail(MSH_E_STATE, "msh_step before msh_set_state");
   if (!(dt_max > 0.0)) return fail(MSH_E_INVALID_ARG, "dt_max must be > 0");
-  msh_status st = ensure_partials(g, blocks_for(g, g->rows, g->zchunk));
+  msh_status st = refresh_dt(g);
+  if (st) return st;
+  st = ensure_partials(g, blocks_for(g, g->rows, g->zchunk));
   if (st) return st;
   cudaError_t e = launch_run_start(g->ctrl, INFINITY, 1, dt_max, g->stream);
   if (e != cudaSuccess) return fail(MSH_E_CUDA, "run start: %s", cudaGetErrorString(e));
@@ -474,7 +518,9 @@ msh_status msh_run(msh_grid *g, double t_end, int64_t max_steps, int64_t *steps,
   if (!g) return fail(MSH_E_INVALID_ARG, "null grid");
   if (!g->has_state) return fail(MSH_E_STATE, "msh_run before msh_set_state");
   if (max_steps < 0 || std::isnan(t_end)) return fail(MSH_E_INVALID_ARG, "bad t_end or max_steps");
-  msh_status st = g->profiling ? ensure_partials(g, blocks_for(g, g->rows, g->zchunk)) : build_graph(g);
+  msh_status st = refresh_dt(g);
+  if (st) return st;
+  st = g->profiling ? ensure_partials(g, blocks_for(g, g->rows, g->zchunk)) : build_graph(g);
   if (st) return st;
   const int64_t s0 = g->hctrl->step;
   cudaError_t e = launch_run_start(g->ctrl, t_end, max_steps, INFINITY, g->stream);
@@ -591,6 +637,97 @@ msh_status msh_set_tape(msh_grid *g, int32_t K, int64_t max_steps) {
   g->hctrl->tape_len = g->tape_len;
   CUDA_TRY(push_tape_fields(g));
   CUDA_TRY(cudaStreamSynchronize(g->stream));
+  return MSH_OK;
+}
+
+// ------------------------------------------------------- slab decomposition
+static msh_status copy_slab(msh_grid *g, int64_t start, int64_t count, void *buf, int32_t where, bool to_grid) {
+  if (!g || (!buf && count > 0)) return fail(MSH_E_INVALID_ARG, "null argument");
+  if (where != MSH_HOST && where != MSH_DEVICE) return fail(MSH_E_INVALID_ARG, "bad where");
+  if (!g->has_state) return fail(MSH_E_STATE, "no state set");
+  size_t per = 0;
+  int64_t layers = 0;
+  layer_geometry(g, &per, &layers);
+  if (start < 0 || count < 0 || start + count > layers)
+    return fail(MSH_E_INVALID_ARG, "layers [%lld, %lld) outside [0, %lld)", (long long)start,
+                (long long)(start + count), (long long)layers);
+  if (count == 0) return MSH_OK;
+  char *U = static_cast<char *>(g->U[cur_buf(g)]);
+  const size_t bytes = (size_t)count * per * g->esize;
+  const cudaMemcpyKind kind = to_grid ? (where == MSH_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice)
+                                      : (where == MSH_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice);
+  for (int k = 0; k < 10; k++) {
+    char *dev = U + ((size_t)k * g->N + (size_t)start * per) * g->esize;
+    char *other = static_cast<char *>(buf) + (size_t)k * bytes;
+    CUDA_TRY(cudaMemcpyAsync(to_grid ? dev : other, to_grid ? other : dev, bytes, kind, g->stream));
+  }
+  CUDA_TRY(cudaStreamSynchronize(g->stream));
+  if (to_grid) g->dt_stale = true;
+  return MSH_OK;
+}
+
+msh_status msh_get_slab(msh_grid *g, int64_t start, int64_t count, void *buf, int32_t where) {
+  begin();
+  return copy_slab(g, start, count, buf, where, false);
+}
+
+msh_status msh_set_slab(msh_grid *g, int64_t start, int64_t count, const void *buf, int32_t where) {
+  begin();
+  return copy_slab(g, start, count, const_cast<void *>(buf), where, true);
+}
+
+msh_status msh_reduce_layers(msh_grid *g, int64_t start, int64_t count, double totals[10], double *dt_cfl,
+                             int32_t *realizable) {
+  begin();
+  if (!g) return fail(MSH_E_INVALID_ARG, "null grid");
+  if (!g->has_state) return fail(MSH_E_STATE, "no state set");
+  size_t per = 0;
+  int64_t layers = 0;
+  layer_geometry(g, &per, &layers);
+  if (start < 0 || count < 1 || start + count > layers)
+    return fail(MSH_E_INVALID_ARG, "layers [%lld, %lld) outside [0, %lld) or empty", (long long)start,
+                (long long)(start + count), (long long)layers);
+  if (!g->ctrl_aux) CUDA_TRY(cudaMalloc(&g->ctrl_aux, sizeof(Ctrl)));
+  msh_status st = ensure_partials(g, kScanBlocks);
+  if (st) return st;
+  Ctrl c;
+  memset(&c, 0, sizeof c);
+  c.cfl = g->cfl;
+  CUDA_TRY(cudaMemcpyAsync(g->ctrl_aux, &c, sizeof c, cudaMemcpyHostToDevice, g->stream));
+  const size_t c0 = (size_t)start * per, c1 = (size_t)(start + count) * per;
+  const int which = cur_buf(g);
+  cudaError_t e = g->prec == MSH_FP32
+                      ? launch_scan<float>((const float *)g->U[which], g->N, (int)g->n[0], (int)g->n[1], g->ndim,
+                                           g->dx, g->part, kScanBlocks, g->stream, c0, c1)
+                      : launch_scan<double>((const double *)g->U[which], g->N, (int)g->n[0], (int)g->n[1], g->ndim,
+                                            g->dx, g->part, kScanBlocks, g->stream, c0, c1);
+  if (e == cudaSuccess) e = launch_finalize(g->ctrl_aux, g->part, kScanBlocks, 1, g->stream);
+  if (e != cudaSuccess) return fail(MSH_E_CUDA, "layer reduction: %s", cudaGetErrorString(e));
+  CUDA_TRY(cudaMemcpyAsync(&c, g->ctrl_aux, sizeof c, cudaMemcpyDeviceToHost, g->stream));
+  CUDA_TRY(cudaStreamSynchronize(g->stream));
+  if (totals) memcpy(totals, c.totals, sizeof(double) * 10);
+  if (dt_cfl) *dt_cfl = c.dt_cfl;
+  if (realizable) *realizable = c.realizable;
+  return MSH_OK;
+}
+
+msh_status msh_step_dt(msh_grid *g, double dt, int32_t *tagged_cells) {
+  begin();
+  if (!g) return fail(MSH_E_INVALID_ARG, "null grid");
+  if (!g->has_state) return fail(MSH_E_STATE, "msh_step_dt before msh_set_state");
+  if (!(dt > 0.0) || !std::isfinite(dt)) return fail(MSH_E_INVALID_ARG, "dt must be finite and > 0");
+  msh_status st = ensure_partials(g, blocks_for(g, g->rows, g->zchunk));
+  if (st) return st;
+  cudaError_t e = launch_set_dt(g->ctrl, dt, g->stream);
+  if (e != cudaSuccess) return fail(MSH_E_CUDA, "set dt: %s", cudaGetErrorString(e));
+  st = launch_one_step(g, -1);
+  if (st) return st;
+  st = read_ctrl(g);
+  if (st) return st;
+  g->dt_stale = false;  // the finalize planned from the new state
+  if (tagged_cells) *tagged_cells = g->hctrl->last_tagged;
+  if (g->hctrl->status == MSH_E_REALIZABILITY)
+    return fail(MSH_E_REALIZABILITY, "step produced a non-realizable cell %lld", (long long)g->hctrl->first_bad);
   return MSH_OK;
 }
 

@@ -27,6 +27,8 @@ struct Ctrl {
   double *tape_dt;
   int32_t *tape_had;
   int64_t tape_base, tape_len;
+  int32_t last_tagged;  // cells the a-posteriori fallback tagged in the last step
+  int32_t pad2;
 };
 
 // Per-thread-block partial reductions written by the step and scan kernels.
@@ -73,9 +75,11 @@ template <typename T> cudaError_t launch_step(const StepArgs<T> &a, int ndim, in
                                               int *nblocks_out);
 template <typename T> int step_blocks(int ndim, int rows, int nx, int ny, int nz, int zchunk);
 template <typename T> size_t step_smem(int ndim, int rows);
+// partials of cells [c0, c1) (c1 = 0: all N)
 template <typename T> cudaError_t launch_scan(const T *U, size_t N, int nx, int ny, int ndim,
                                               const double *dx, Partial *part, int nparts,
-                                              cudaStream_t s);
+                                              cudaStream_t s, size_t c0 = 0, size_t c1 = 0);
+cudaError_t launch_set_dt(Ctrl *ctrl, double dt, cudaStream_t s);
 cudaError_t launch_finalize(Ctrl *ctrl, const Partial *part, int nparts, int mode, cudaStream_t s);
 cudaError_t launch_run_start(Ctrl *ctrl, double t_end, int64_t max_steps, double dt_max, cudaStream_t s);
 template <typename T> cudaError_t launch_convert(T *U, size_t N, int to_primitive, cudaStream_t s);
@@ -124,6 +128,10 @@ struct msh_grid {
   int32_t tape_K = 0;
   int64_t tape_base = 0, tape_len = 0;
   bool tape_valid = false;
+  // slab decomposition: a halo copy made the planned CFL step stale; a second control
+  // block for reductions over a range of layers
+  bool dt_stale = false;
+  msh::Ctrl *ctrl_aux = nullptr;
   bool has_state = false;
   int rows = 8, zchunk = 32;
   cudaGraphExec_t graph = nullptr;

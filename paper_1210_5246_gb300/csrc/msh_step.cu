@@ -602,16 +602,17 @@ __global__ void __launch_bounds__(32 * WARPS) step_strip2d_kernel(StepArgs<T> a)
 }
 
 // ----------------------------------------------------------------- scan kernel
-// Partials (totals, max signal speed sum, first non-realizable cell) of a state.
+// Partials (totals, max signal speed sum, first non-realizable cell) of the cells
+// [c0, c1) of a state whose fields are N apart.
 template <typename T, int NDIM>
-__global__ void __launch_bounds__(256) scan_kernel(const T *__restrict__ U, size_t N, T idx, T idy, T idz,
-                                                   Partial *part) {
+__global__ void __launch_bounds__(256) scan_kernel(const T *__restrict__ U, size_t N, size_t c0, size_t c1, T idx,
+                                                   T idy, T idz, Partial *part) {
   double diag[NV];
 #pragma unroll
   for (int k = 0; k < NV; k++) diag[k] = 0.0;
   T smax = T(0);
   long long bad = LLONG_MAX;
-  for (size_t c = (size_t)blockIdx.x * blockDim.x + threadIdx.x; c < N; c += (size_t)gridDim.x * blockDim.x) {
+  for (size_t c = c0 + (size_t)blockIdx.x * blockDim.x + threadIdx.x; c < c1; c += (size_t)gridDim.x * blockDim.x) {
     T Uc[NV], W[NV];
 #pragma unroll
     for (int k = 0; k < NV; k++) Uc[k] = U[k * N + c];
@@ -698,6 +699,7 @@ __global__ void __launch_bounds__(kFinalizeThreads) finalize_kernel(Ctrl *ctrl, 
     c->done = 1;
     return;
   }
+  c->last_tagged = c->nbad[0];
   const int64_t ti = c->step - c->tape_base;
   if (c->tape_dt != nullptr && ti >= 0 && ti < c->tape_len) {
     c->tape_dt[ti] = c->dt;
@@ -715,6 +717,18 @@ __global__ void __launch_bounds__(kFinalizeThreads) finalize_kernel(Ctrl *ctrl, 
     return;
   }
   plan(c);
+}
+
+// One step with a given dt: no CFL limit, no end time.
+__global__ void set_dt_kernel(Ctrl *c, double dt) {
+  c->t_end = INFINITY;
+  c->max_step = INT64_MAX;
+  c->dt_max = INFINITY;
+  c->done = 0;
+  c->status = 0;
+  for (int p = 0; p <= kFallbackPasses; p++) c->nbad[p] = 0;
+  c->dt = dt;
+  c->t_next = c->t + dt;
 }
 
 __global__ void run_start_kernel(Ctrl *c, double t_end, int64_t max_steps, double dt_max) {
@@ -827,11 +841,17 @@ cudaError_t launch_step(const StepArgs<T> &a, int ndim, int rows, bool retry, cu
 
 template <typename T>
 cudaError_t launch_scan(const T *U, size_t N, int nx, int ny, int ndim, const double *dx, Partial *part,
-                        int nparts, cudaStream_t s) {
+                        int nparts, cudaStream_t s, size_t c0, size_t c1) {
   const T ix = (T)(1.0 / dx[0]), iy = (T)(1.0 / dx[1]), iz = (T)(1.0 / dx[2]);
-  if (ndim == 1) scan_kernel<T, 1><<<nparts, 256, 0, s>>>(U, N, ix, iy, iz, part);
-  else if (ndim == 2) scan_kernel<T, 2><<<nparts, 256, 0, s>>>(U, N, ix, iy, iz, part);
-  else scan_kernel<T, 3><<<nparts, 256, 0, s>>>(U, N, ix, iy, iz, part);
+  if (c1 == 0) c1 = N;
+  if (ndim == 1) scan_kernel<T, 1><<<nparts, 256, 0, s>>>(U, N, c0, c1, ix, iy, iz, part);
+  else if (ndim == 2) scan_kernel<T, 2><<<nparts, 256, 0, s>>>(U, N, c0, c1, ix, iy, iz, part);
+  else scan_kernel<T, 3><<<nparts, 256, 0, s>>>(U, N, c0, c1, ix, iy, iz, part);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_set_dt(Ctrl *ctrl, double dt, cudaStream_t s) {
+  set_dt_kernel<<<1, 1, 0, s>>>(ctrl, dt);
   return cudaGetLastError();
 }
 
@@ -863,7 +883,7 @@ template <typename T> cudaError_t launch_convert(T *U, size_t N, int to_primitiv
   template int step_blocks<T>(int, int, int, int, int, int);                                         \
   template size_t step_smem<T>(int, int);                                                            \
   template cudaError_t launch_scan<T>(const T *, size_t, int, int, int, const double *, Partial *, int, \
-                                      cudaStream_t);                                                 \
+                                      cudaStream_t, size_t, size_t);                                 \
   template cudaError_t launch_convert<T>(T *, size_t, int, cudaStream_t);                            \
   template cudaError_t launch_gravity_field<T>(const double *, T *, int, int, int, int, const double *, cudaStream_t);
 MSH_INST(float)

@@ -61,6 +61,11 @@ SIGNATURES = {
     "msh_get_profile": [_vp, _P(_dbl), _P(_dbl), _P(_i64)],
     "msh_adjoint_run": [_vp, _vp, _i64, _P(_dbl), _i32, _vp, _vp, _i32, _i32],
     "msh_set_tape": [_vp, _i32, _i64],
+    "msh_set_cell_width": [_vp, _P(_dbl)],
+    "msh_get_slab": [_vp, _i64, _i64, _vp, _i32],
+    "msh_set_slab": [_vp, _i64, _i64, _vp, _i32],
+    "msh_reduce_layers": [_vp, _i64, _i64, _P(_dbl), _P(_dbl), _P(_i32)],
+    "msh_step_dt": [_vp, _dbl, _P(_i32)],
     "msh_adjoint_tape": [_vp, _vp, _vp, _i32, _i32],
     "msh_batch_init": [_P(_vp), _i32, _P(_i32), _P(_dbl), _P(_dbl), _P(_dbl), _i32, _dbl, _vp],
     "msh_batch_reset": [_vp],
@@ -303,6 +308,58 @@ class Grid:
         po, wo, ko = self._buf(out)
         _check(load().msh_adjoint_run(self.h, p0, len(dts), _ptr_dbl(dts), int(K), pg, po, w0, kind))
         return out
+
+    # -- slab decomposition -------------------------------------------------------
+    def set_cell_width(self, dx):
+        """Cell widths of the active dims (see ``msh_set_cell_width``)."""
+        w = np.zeros(3)
+        w[: len(dx)] = dx
+        _check(load().msh_set_cell_width(self.h, _ptr_dbl(w)))
+
+    def layer_shape(self):
+        """(layers, cells per layer) of the last active axis."""
+        layers = self.n[self.ndim - 1]
+        return layers, int(np.prod(self.n[: self.ndim - 1]))
+
+    def get_slab(self, start, count, out=None):
+        """Layers [start, start+count) of the conserved state as [10, count * cells per layer]
+        (numpy, or a torch CUDA tensor when ``out`` is one)."""
+        _, per = self.layer_shape()
+        if out is None:
+            out = np.empty((10, count * per), dtype=self.dtype)
+        p, w, keep = self._slab_buf(out, count * per)
+        _check(load().msh_get_slab(self.h, int(start), int(count), p, w))
+        return out
+
+    def set_slab(self, start, count, buf):
+        _, per = self.layer_shape()
+        p, w, keep = self._slab_buf(buf, count * per)
+        _check(load().msh_set_slab(self.h, int(start), int(count), p, w))
+
+    def _slab_buf(self, a, cells):
+        if isinstance(a, np.ndarray):
+            a = np.ascontiguousarray(a, dtype=self.dtype)
+            if a.size != 10 * cells:
+                raise ValueError(f"slab buffer must have {10 * cells} elements")
+            return a.ctypes.data_as(C.c_void_p), HOST, a
+        want = _torch().float32 if self.precision == FP32 else _torch().float64
+        if not a.is_contiguous() or a.numel() != 10 * cells or a.dtype != want:
+            raise ValueError("device slab buffer must be contiguous, of the grid's dtype and size")
+        return C.c_void_p(a.data_ptr()), DEVICE, a
+
+    def reduce_layers(self, start, count):
+        """(totals[10], CFL dt, realizable) over layers [start, start+count)."""
+        tot = np.zeros(10)
+        dt = C.c_double(0.0)
+        ok = C.c_int32(0)
+        _check(load().msh_reduce_layers(self.h, int(start), int(count), _ptr_dbl(tot), C.byref(dt), C.byref(ok)))
+        return tot, dt.value, bool(ok.value)
+
+    def step_dt(self, dt):
+        """One step with exactly dt; returns the number of cells the fallback tagged."""
+        tagged = C.c_int32(0)
+        _check(load().msh_step_dt(self.h, float(dt), C.byref(tagged)))
+        return tagged.value
 
     def set_tape(self, K, max_steps):
         """Record checkpoints every K steps, dts and fallback flags of the next max_steps
