@@ -83,15 +83,17 @@ template <typename T> __device__ __forceinline__ T *tape_slot(const StepArgs<T> 
 
 // Per-cell tail of the step: gravity source, store, next-dt speed, realizability, totals;
 // U^n also goes to the tape's checkpoint `ck` when the step has one.
+// U^n of the cell is read from src[k * stride] (the state in global memory, or a staged
+// copy in shared memory).
 template <typename T, int NDIM, bool RETRY>
-__device__ __forceinline__ void finish_cell(const StepArgs<T> &a, const T *__restrict__ Us,
+__device__ __forceinline__ void finish_cell(const StepArgs<T> &a, const T *src, size_t stride,
                                             T *__restrict__ Ud, size_t N, size_t c,
                                             const T (&acc)[NV], T dt, T idx, T idy, T idz, Acc<T> &diag,
                                             T &smax, long long &bad, int32_t tag, T *__restrict__ ck) {
   T Un[NV];
 #pragma unroll
   for (int k = 0; k < NV; k++) {
-    const T u = Us[k * N + c];
+    const T u = src[k * stride];
     if (!RETRY && ck != nullptr) ck[k * N + c] = u;
     Un[k] = u + dt * acc[k];
   }
@@ -212,7 +214,7 @@ __global__ void __launch_bounds__(kTile1D) step1d_kernel(StepArgs<T> a) {
     T acc[NV];
 #pragma unroll
     for (int k = 0; k < NV; k++) acc[k] = (F[k] - sH[k][t + 1]) * idx;
-    finish_cell<T, 1, RETRY>(a, Us, Ud, N, (size_t)gx, acc, dt, idx, T(0), T(0), diag, smax, bad, tag,
+    finish_cell<T, 1, RETRY>(a, Us + gx, N, Ud, N, (size_t)gx, acc, dt, idx, T(0), T(0), diag, smax, bad, tag,
                              RETRY ? nullptr : tape_slot(a, step, N));
   }
   write_partial<T, B>(diag, smax, bad, a.part + tile);
@@ -221,6 +223,11 @@ __global__ void __launch_bounds__(kTile1D) step1d_kernel(StepArgs<T> a) {
 }
 
 // ----------------------------------------------------------------- 3D kernel
+// Raw staging slots of the 3D kernel: four keep U^n of the plane being updated in shared
+// memory (FP32, 16 rows: 224 KB with everything else); two otherwise (the update re-reads
+// U^n from global memory), which keeps two FP32 blocks of 8 rows per SM and FP64 within
+// the shared memory of a block.
+template <typename T, int BY> constexpr int kRawPlanes = (sizeof(T) == 4 && BY == 16) ? 4 : 2;
 // Asynchronous global -> shared copy of one element (cp.async, completion tracked per
 // thread by commit groups).
 template <typename T> __device__ __forceinline__ void cp_async_elem(T *smem, const T *gmem) {
@@ -247,6 +254,7 @@ __global__ void __launch_bounds__(32 * BY, (BY <= 8 ? 2 : 1)) step_tile_kernel(S
   static_assert(NDIM == 3, "the 2D step runs in step_strip2d_kernel");
   constexpr int SX = 34, SY = BY + 2, NQ = SY * SX;
   constexpr int PL = NV * NQ;  // one staged plane, all fields: [NV][SY][SX]
+  constexpr int RAW = kRawPlanes<T, BY>;  // raw staging slots (4: U^n of the update from shared memory)
   const Ctrl *ctrl = a.ctrl;
   if (ctrl->done) return;
   if (RETRY && ctrl->nbad[a.level - 1] == 0) return;
@@ -262,15 +270,16 @@ __global__ void __launch_bounds__(32 * BY, (BY <= 8 ? 2 : 1)) step_tile_kernel(S
   const T nuy = (T)(0.5 * dtd / a.dx[1]), idy = (T)(1.0 / a.dx[1]);
   const T nuz = (T)(0.5 * dtd / a.dx[2]), idz = (T)(1.0 / a.dx[2]);
   T *const ck = RETRY ? nullptr : tape_slot(a, step, (size_t)a.nx * a.ny * a.nz);
-  // shared memory: three primitive planes (ring), two raw conserved planes filled by
-  // cp.async two planes ahead, the y-sweep face states and fluxes, per staged cell the
-  // sign flips of reflect images (bits 0..9) and the fallback tag (bit 16)
+  // shared memory: three primitive planes (ring), RAW raw conserved planes filled by
+  // cp.async one plane ahead, the y-sweep face states and fluxes, per staged cell the sign
+  // flips of reflect images (bits 0..9) and the fallback tag (bit 16)
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T *sW = reinterpret_cast<T *>(smem_raw);
   T *sR = sW + 3 * PL;
-  T *sXh = sR + 2 * PL;          // [NV][BY][32]
+  T *sXh = sR + RAW * PL;        // [NV][BY][32]
   T *sXf = sXh + NV * BY * 32;   // [NV][BY][32]
-  unsigned *sMeta = reinterpret_cast<unsigned *>(sXf + NV * BY * 32);  // [2][NQ]
+  unsigned *sMeta = reinterpret_cast<unsigned *>(sXf + NV * BY * 32);  // [RAW][NQ]
+  auto slot = [](int p) { return ((p % RAW) + RAW) % RAW; };
   const int tx = threadIdx.x, ty = threadIdx.y;
   const int tid = ty * 32 + tx;
   const int nx = a.nx, ny = a.ny, nz = a.nz;
@@ -294,8 +303,8 @@ __global__ void __launch_bounds__(32 * BY, (BY <= 8 ? 2 : 1)) step_tile_kernel(S
   auto stage = [&](int z) {
     bool mz = false;
     const int zz = map_index(z, nz, a.bc[4], a.bc[5], mz);
-    T *dst = sR + (z & 1) * PL;
-    unsigned *meta = sMeta + (z & 1) * NQ;
+    T *dst = sR + slot(z) * PL;
+    unsigned *meta = sMeta + slot(z) * NQ;
     for (int i = tid; i < NQ; i += 32 * BY) {
       const int qy = i / SX, qx = i - qy * SX;
       if (!((qy >= 2 && qy <= BY - 1) || (qx >= 2 && qx <= 31))) continue;
@@ -312,8 +321,8 @@ __global__ void __launch_bounds__(32 * BY, (BY <= 8 ? 2 : 1)) step_tile_kernel(S
     cp_async_commit();
   };
   auto convert = [&](int z) {  // raw plane z -> primitive plane in ring slot z mod 3
-    const T *src = sR + (z & 1) * PL;
-    const unsigned *meta = sMeta + (z & 1) * NQ;
+    const T *src = sR + slot(z) * PL;
+    const unsigned *meta = sMeta + slot(z) * NQ;
     const int b = ((z % 3) + 3) % 3;
     T *dst = sW + b * PL;
     for (int i = tid; i < NQ; i += 32 * BY) {
@@ -350,8 +359,8 @@ __global__ void __launch_bounds__(32 * BY, (BY <= 8 ? 2 : 1)) step_tile_kernel(S
   long long bad = LLONG_MAX;
   const int z0 = bzi * a.zchunk;
   const int z1 = min(z0 + a.zchunk, nz);
-  // prologue: planes z0-2 .. z0+2 converted, z0+3 in flight; the z face state of cell
-  // z0 and the flux through its lower face in registers
+  // prologue: planes z0-2 .. z0+2 converted; the z face state of cell z0 and the flux
+  // through its lower face in registers
   stage(z0 - 2);
   stage(z0 - 1);
   cp_async_wait<0>();
@@ -382,14 +391,10 @@ __global__ void __launch_bounds__(32 * BY, (BY <= 8 ? 2 : 1)) step_tile_kernel(S
   cp_async_wait<0>();
   __syncthreads();  // plane z0-1 is no longer read
   convert(z0 + 2);
-  if (z0 + 3 <= z1 + 1) stage(z0 + 3);
-  else cp_async_commit();
   __syncthreads();
 
   for (int z = z0; z < z1; z++) {
-    // planes z, z+1, z+2 are converted; z+3 is in flight; stage z+4 into the raw slot of z+2
-    if (z + 4 <= z1 + 1) stage(z + 4);
-    else cp_async_commit();
+    // planes z, z+1, z+2 are converted
     const T *pl = sW + buf(z) * PL;
     T acc[NV];
 #pragma unroll
@@ -420,6 +425,9 @@ __global__ void __launch_bounds__(32 * BY, (BY <= 8 ? 2 : 1)) step_tile_kernel(S
       for (int k = 0; k < NV; k++) sXh[(k * BY + ty) * 32 + tx] = hi[k];
     }
     __syncthreads();
+    // Every thread has finished the previous plane: its raw slot (plane z-1 with four
+    // slots, z+1 with two) is free for plane z+3.
+    if (z + 3 <= z1 + 1) stage(z + 3);
     if (ycol && ty >= 1) {  // flux through the lower y face
       T hl[NV];
 #pragma unroll
@@ -444,14 +452,19 @@ __global__ void __launch_bounds__(32 * BY, (BY <= 8 ? 2 : 1)) step_tile_kernel(S
 #pragma unroll
       for (int k = 0; k < NV; k++) acc[Frame<1>::g(k)] += (Fy[k] - sXf[(k * BY + ty + 1) * 32 + tx]) * idy;
     }
-    if (valid)
-      finish_cell<T, NDIM, RETRY>(a, Us, Ud, N, ((size_t)z * ny + gy) * nx + gx, acc, dt, idx, idy, idz, diag,
-                                  smax, bad, tag, ck);
+    if (valid) {
+      const size_t c = ((size_t)z * ny + gy) * nx + gx;
+      if (RAW == 4)  // U^n as staged (an interior cell is never a reflect image)
+        finish_cell<T, NDIM, RETRY>(a, sR + slot(z) * PL + sy * SX + sx, NQ, Ud, N, c, acc, dt, idx, idy, idz,
+                                    diag, smax, bad, tag, ck);
+      else
+        finish_cell<T, NDIM, RETRY>(a, Us + c, N, Ud, N, c, acc, dt, idx, idy, idz, diag, smax, bad, tag, ck);
+    }
     // Plane z is no longer read (every read of the primitive planes precedes the second
     // barrier); plane z+3 replaces it.  The next iteration reads it only after its first
     // barrier, and rewrites sXh / sXf only after every thread has passed this one.
     if (z + 1 < z1) {
-      cp_async_wait<1>();
+      cp_async_wait<0>();
       convert(z + 3);
     }
   }
@@ -585,8 +598,8 @@ __global__ void __launch_bounds__(32 * WARPS) step_strip2d_kernel(StepArgs<T> a)
           }
         }
         if (upd)
-          finish_cell<T, 2, RETRY>(a, Us, Ud, N, (size_t)y * nx + gx, acc, dt, idx, idy, T(0), diag, smax, bad,
-                                   tag, ck);
+          finish_cell<T, 2, RETRY>(a, Us + ((size_t)y * nx + gx), N, Ud, N, (size_t)y * nx + gx, acc, dt, idx, idy,
+                                   T(0), diag, smax, bad, tag, ck);
 #pragma unroll
         for (int k = 0; k < NV; k++) {
           r0[k] = r1[k];
@@ -768,12 +781,13 @@ static int fallback_blocks() {
   return blocks;
 }
 
-// 3D: five staged planes (three primitive, two raw) of NV x (rows+2) x 34, the y-sweep
-// face states and fluxes (2 x NV x rows x 32) and two planes of per-cell flags.
+// 3D: 3 + RAW staged planes (three primitive, RAW raw) of NV x (rows+2) x 34, the y-sweep
+// face states and fluxes (2 x NV x rows x 32) and RAW planes of per-cell flags.
 template <typename T> size_t step_smem(int ndim, int rows) {
   if (ndim < 3) return 0;
   const size_t nq = (size_t)(rows + 2) * 34;
-  return sizeof(T) * ((size_t)5 * NV * nq + (size_t)2 * NV * rows * 32) + 2 * nq * sizeof(unsigned);
+  const size_t raw = rows == 16 ? kRawPlanes<T, 16> : rows == 8 ? kRawPlanes<T, 8> : kRawPlanes<T, 4>;
+  return sizeof(T) * ((3 + raw) * NV * nq + (size_t)2 * NV * rows * 32) + raw * nq * sizeof(unsigned);
 }
 
 template <typename T> int step_blocks(int ndim, int rows, int nx, int ny, int nz, int zchunk) {
