@@ -60,9 +60,12 @@ typedef struct {
     double dx[3];        /* cell widths */
     int32_t bc[6];       /* bc[2d+0] lower face, bc[2d+1] upper face: 0 periodic, 1 outflow, 2 reflect */
     double cfl;
+    int32_t scheme;      /* OG_SCHEME_MH (Sec. 3.3) or OG_SCHEME_KT (Sec. 3.2) */
+    int32_t pad1;
 } og_grid;
 
 enum { OG_PERIODIC = 0, OG_OUTFLOW = 1, OG_REFLECT = 2 };
+enum { OG_SCHEME_MH = 0, OG_SCHEME_KT = 1 };
 
 /* index of the symmetric tensor component (i,j) inside the 10-vector */
 static int tens_idx(int i, int j)
@@ -410,6 +413,33 @@ static int cell_realizable(const double *Uc)
     return m1 > 0.0 && m2 > 0.0 && m3 > 0.0;
 }
 
+/* ---------------------------------------------------------------- a8 ----- */
+/* Gravity source on the updated state Us of cell c: a = -grad Phi by central
+ * differences of the potential (one ghost layer on active dims), m += dt rho a,
+ * E += dt (mbar a^T + a mbar^T) with mbar the mean of m before and after. */
+static void gravity_source(const og_grid *Gr, const double *phi, double dt, int64_t c, double *Us)
+{
+    int64_t n0 = Gr->n[0], n1 = Gr->n[1];
+    int64_t gx = (Gr->ndim > 0), gy = (Gr->ndim > 1), gz = (Gr->ndim > 2);
+    int64_t px = n0 + 2 * gx, py = n1 + 2 * gy;
+    int64_t x = c % n0, y = (c / n0) % n1, z = c / (n0 * n1);
+    double a[3] = {0.0, 0.0, 0.0};
+    int64_t ctr = ((z + gz) * py + (y + gy)) * px + (x + gx);
+    int64_t stride[3] = {1, px, px * py};
+    for (int d = 0; d < Gr->ndim; d++)
+        a[d] = -(phi[ctr + stride[d]] - phi[ctr - stride[d]]) / (2.0 * Gr->dx[d]);
+    double m_star[3], m_new[3], mbar[3];
+    for (int i = 0; i < 3; i++) {
+        m_star[i] = Us[1 + i];
+        m_new[i] = m_star[i] + dt * Us[0] * a[i];
+        mbar[i] = 0.5 * (m_star[i] + m_new[i]);
+    }
+    for (int i = 0; i < 3; i++)
+        for (int j = i; j < 3; j++)
+            Us[tens_idx(i, j)] += dt * (mbar[i] * a[j] + a[i] * mbar[j]);
+    for (int i = 0; i < 3; i++) Us[1 + i] = m_new[i];
+}
+
 /* -------------------------------------------------------------- a1 - a8 --- */
 /* One pass of the step.  flag: NULL, or per padded cell 1 where the faces of that
  * cell take first-order face states (the cell-centred W on both sides). */
@@ -481,30 +511,11 @@ static int step_pass(const og_grid *Gr, const double *U, const double *phi, doub
                 free(hi);
             }
     }
-    int64_t gx = (Gr->ndim > 0), gy = (Gr->ndim > 1), gz = (Gr->ndim > 2);
-    int64_t px = P.n[0] + 2 * gx, py = P.n[1] + 2 * gy;
 #pragma omp parallel for
     for (int64_t c = 0; c < N; c++) {                                  /* a7, a8 */
         double Us[NV];
         for (int k = 0; k < NV; k++) Us[k] = U[k * N + c] + dt * dU[k * N + c];
-        if (phi) {
-            int64_t x = c % P.n[0], y = (c / P.n[0]) % P.n[1], z = c / (P.n[0] * P.n[1]);
-            double a[3] = {0.0, 0.0, 0.0};
-            int64_t ctr = ((z + gz) * py + (y + gy)) * px + (x + gx);
-            int64_t stride[3] = {1, px, px * py};
-            for (int d = 0; d < Gr->ndim; d++)
-                a[d] = -(phi[ctr + stride[d]] - phi[ctr - stride[d]]) / (2.0 * Gr->dx[d]);
-            double m_star[3], m_new[3], mbar[3];
-            for (int i = 0; i < 3; i++) {
-                m_star[i] = Us[1 + i];
-                m_new[i] = m_star[i] + dt * Us[0] * a[i];
-                mbar[i] = 0.5 * (m_star[i] + m_new[i]);
-            }
-            for (int i = 0; i < 3; i++)
-                for (int j = i; j < 3; j++)
-                    Us[tens_idx(i, j)] += dt * (mbar[i] * a[j] + a[i] * mbar[j]);
-            for (int i = 0; i < 3; i++) Us[1 + i] = m_new[i];
-        }
+        if (phi) gravity_source(Gr, phi, dt, c, Us);
         for (int k = 0; k < NV; k++) Unew[k * N + c] = Us[k];
     }
     free(G);
@@ -521,8 +532,11 @@ static int step_pass(const og_grid *Gr, const double *U, const double *phi, doub
  * detection, Clain, Diot & Loubere 2011); face fluxes stay shared, so the update
  * stays conservative.  Cells still non-realizable after that are left for the
  * caller's realizability check.  Returns 0, or 1 on allocation failure. */
+int og_step_kt(const og_grid *Gr, const double *U, const double *phi, double dt, double *Unew);
+
 int og_step(const og_grid *Gr, const double *U, const double *phi, double dt, double *Unew)
 {
+    if (Gr->scheme == OG_SCHEME_KT) return og_step_kt(Gr, U, phi, dt, Unew);
     if (step_pass(Gr, U, phi, dt, NULL, Unew)) return 1;
     og_pad P = make_pad(Gr);
     int64_t N = P.n[0] * P.n[1] * P.n[2];
@@ -563,6 +577,130 @@ int og_step(const og_grid *Gr, const double *U, const double *phi, double dt, do
     free(flag);
     free(bad);
     return 0;
+}
+
+/* ------------------------------------------------------------ KT scheme -- */
+/* The Kurganov-Tadmor central scheme with second-order Runge-Kutta time integration
+ * (Sec. 3.2; Kurganov & Tadmor 2000, eq 4.2):
+ *   du_i/dt = L(u)_i = - sum_d (H_{d,i+1/2} - H_{d,i-1/2}) / dx_d,
+ *   H_{i+1/2} = (f(u+) + f(u-)) / 2 - a_{i+1/2} (u+ - u-) / 2,
+ * u- the value on the left side of face i+1/2 (from cell i), u+ on its right side (from
+ * cell i+1), and a_{i+1/2} the larger spectral radius of df/du at u- and u+ (eq
+ * spectralfreq), which for the BME is |u_n| + sqrt(3 P_nn / rho) (eq soundspeed, gamma = 3).
+ * Readings (the paper defers the rest to KT2000):
+ *   - u-/u+ come from a piecewise-linear reconstruction of the primitive variables,
+ *     component by component, with the MC limiter (the generalised minmod with theta = 2);
+ *     a cell with a face value of rho <= 0 or P_nn <= 0 takes first-order face values;
+ *   - the time integration is Heun's two-stage Runge-Kutta method:
+ *     u1 = u + dt L(u), u_new = (u + u1 + dt L(u1)) / 2;
+ *   - gravity as a8, after the two stages;
+ *   - the CFL rule a9 with the grid's CFL number.                                   */
+void og_kt_reconstruct(const double *Wm, const double *W0, const double *Wp, int d, double *lo, double *hi)
+{
+    for (int k = 0; k < NV; k++) {
+        double s = mc_limit(W0[k] - Wm[k], 0.5 * (Wp[k] - Wm[k]), Wp[k] - W0[k]);
+        hi[k] = W0[k] + 0.5 * s;
+        lo[k] = W0[k] - 0.5 * s;
+    }
+    int nn = tens_idx(d, d);
+    if (!(hi[0] > 0.0 && lo[0] > 0.0 && hi[nn] > 0.0 && lo[nn] > 0.0))
+        for (int k = 0; k < NV; k++) hi[k] = lo[k] = W0[k];
+}
+
+/* KT flux through a face normal to d: WL = u- (left side), WR = u+ (right side). */
+void og_kt_flux(const double *WL, const double *WR, int d, double *H)
+{
+    double FL[NV], FR[NV], UL[NV], UR[NV];
+    og_flux(WL, d, FL);
+    og_flux(WR, d, FR);
+    prim_to_cons(WL, UL);
+    prim_to_cons(WR, UR);
+    int nn = tens_idx(d, d);
+    double aL = fabs(WL[1 + d]) + sqrt(3.0 * WL[nn] / WL[0]);
+    double aR = fabs(WR[1 + d]) + sqrt(3.0 * WR[nn] / WR[0]);
+    double a = fmax(aL, aR);
+    for (int k = 0; k < NV; k++) H[k] = 0.5 * (FR[k] + FL[k]) - 0.5 * a * (UR[k] - UL[k]);
+}
+
+/* dU = L(U), the semi-discrete right-hand side, with the ghost cells of a1. */
+static int kt_rhs(const og_grid *Gr, const double *U, double *dU)
+{
+    og_pad P = make_pad(Gr);
+    int64_t N = P.n[0] * P.n[1] * P.n[2];
+    int64_t NP = P.p[0] * P.p[1] * P.p[2];
+    double *G = (double *)malloc(sizeof(double) * NV * NP);
+    double *Wp = (double *)malloc(sizeof(double) * NV * NP);
+    if (!G || !Wp) { free(G); free(Wp); return 1; }
+    memset(dU, 0, sizeof(double) * NV * N);
+    og_ghost_fill(Gr, U, G);
+#pragma omp parallel for
+    for (int64_t c = 0; c < NP; c++) {
+        double Uc[NV], W[NV];
+        for (int k = 0; k < NV; k++) Uc[k] = G[k * NP + c];
+        cons_to_prim(Uc, W);
+        for (int k = 0; k < NV; k++) Wp[k * NP + c] = W[k];
+    }
+    for (int d = 0; d < Gr->ndim; d++) {
+        int a1 = (d == 0) ? 1 : 0, a2 = (d == 2) ? 1 : 2;
+        int64_t n1 = P.n[a1], n2 = P.n[a2], nd = P.n[d];
+#pragma omp parallel for collapse(2) schedule(dynamic, 4)
+        for (int64_t j2 = 0; j2 < n2; j2++)
+            for (int64_t j1 = 0; j1 < n1; j1++) {
+                double *lo = (double *)malloc(sizeof(double) * NV * (nd + 2));
+                double *hi = (double *)malloc(sizeof(double) * NV * (nd + 2));
+                for (int64_t i = -1; i <= nd; i++) {
+                    double Wc[3][NV];
+                    for (int o = -1; o <= 1; o++) {
+                        int64_t c3[3];
+                        c3[d] = i + o; c3[a1] = j1; c3[a2] = j2;
+                        int64_t pi = pidx(&P, c3[0], c3[1], c3[2]);
+                        for (int k = 0; k < NV; k++) Wc[o + 1][k] = Wp[k * NP + pi];
+                    }
+                    og_kt_reconstruct(Wc[0], Wc[1], Wc[2], d, lo + NV * (i + 1), hi + NV * (i + 1));
+                }
+                double Hm[NV], Hp[NV];
+                og_kt_flux(hi + NV * 0, lo + NV * 1, d, Hm);           /* face -1/2 */
+                for (int64_t i = 0; i < nd; i++) {
+                    og_kt_flux(hi + NV * (i + 1), lo + NV * (i + 2), d, Hp);
+                    int64_t c3[3];
+                    c3[d] = i; c3[a1] = j1; c3[a2] = j2;
+                    int64_t c = (c3[2] * P.n[1] + c3[1]) * P.n[0] + c3[0];
+                    for (int k = 0; k < NV; k++) dU[k * N + c] -= (Hp[k] - Hm[k]) / Gr->dx[d];
+                    memcpy(Hm, Hp, sizeof Hm);
+                }
+                free(lo);
+                free(hi);
+            }
+    }
+    free(G);
+    free(Wp);
+    return 0;
+}
+
+int og_step_kt(const og_grid *Gr, const double *U, const double *phi, double dt, double *Unew)
+{
+    int64_t N = Gr->n[0] * Gr->n[1] * Gr->n[2];
+    double *L0 = (double *)malloc(sizeof(double) * NV * N);
+    double *U1 = (double *)malloc(sizeof(double) * NV * N);
+    int rc = (!L0 || !U1);
+    if (!rc) rc = kt_rhs(Gr, U, L0);
+    if (!rc) {
+        for (int64_t i = 0; i < NV * N; i++) U1[i] = U[i] + dt * L0[i];
+        rc = kt_rhs(Gr, U1, L0);                 /* L0 <- L(U1) */
+    }
+    if (!rc) {
+#pragma omp parallel for
+        for (int64_t c = 0; c < N; c++) {
+            double Us[NV];
+            for (int k = 0; k < NV; k++)
+                Us[k] = 0.5 * (U[k * N + c] + (U1[k * N + c] + dt * L0[k * N + c]));
+            if (phi) gravity_source(Gr, phi, dt, c, Us);
+            for (int k = 0; k < NV; k++) Unew[k * N + c] = Us[k];
+        }
+    }
+    free(L0);
+    free(U1);
+    return rc ? 1 : 0;
 }
 
 /* --------------------------------------------------------------- a10 ----- */

@@ -21,6 +21,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "liboracle.so")
 
 PERIODIC, OUTFLOW, REFLECT = 0, 1, 2
+SCHEME_MH, SCHEME_KT = 0, 1
 NV = 10
 
 _lock = threading.Lock()
@@ -40,7 +41,8 @@ def build(force: bool = False) -> str:
 
 class OgGrid(C.Structure):
     _fields_ = [("ndim", C.c_int32), ("pad0", C.c_int32), ("n", C.c_int64 * 3),
-                ("dx", C.c_double * 3), ("bc", C.c_int32 * 6), ("cfl", C.c_double)]
+                ("dx", C.c_double * 3), ("bc", C.c_int32 * 6), ("cfl", C.c_double),
+                ("scheme", C.c_int32), ("pad1", C.c_int32)]
 
 
 def _load():
@@ -65,6 +67,8 @@ def _load():
             lib.og_ghost_fill.argtypes = [gp, dp, dp]
             lib.og_flux.argtypes = [dp, C.c_int, dp]
             lib.og_hll.argtypes = [dp, dp, C.c_int, dp]
+            lib.og_kt_flux.argtypes = [dp, dp, C.c_int, dp]
+            lib.og_kt_reconstruct.argtypes = [dp, dp, dp, C.c_int, dp, dp]
             lib.og_reconstruct.argtypes = [dp, dp, dp, C.c_int, C.c_double, dp, dp]
             for f in ("og_jacobian_x", "og_right_x", "og_left_x"):
                 getattr(lib, f).argtypes = [dp, dp]
@@ -89,7 +93,9 @@ class Grid:
     """Uniform grid description: ``n`` cells per dim on [lo, hi], boundaries
     ``bc[d] = (lower, upper)`` (PERIODIC / OUTFLOW / REFLECT), CFL number ``cfl``."""
 
-    def __init__(self, n, lo, hi, bc, cfl):
+    def __init__(self, n, lo, hi, bc, cfl, scheme=0):
+        """scheme: SCHEME_MH (MUSCL-Hancock + HLL, Sec. 3.3) or SCHEME_KT (Kurganov-Tadmor
+        + RK2, Sec. 3.2)."""
         n = list(n)
         self.ndim = len(n)
         self.n = tuple(n) + (1,) * (3 - len(n))
@@ -107,6 +113,8 @@ class Grid:
             g.bc[2 * d] = self.bc[d][0]
             g.bc[2 * d + 1] = self.bc[d][1]
         g.cfl = self.cfl
+        g.scheme = int(scheme)
+        self.scheme = int(scheme)
         self._g = g
 
     @property
@@ -222,6 +230,20 @@ def hll(WL, WR, d):
     F = np.empty(NV)
     _load().og_hll(_p(_f64(WL)), _p(_f64(WR)), int(d), _p(F))
     return F
+
+
+def kt_flux(WL, WR, d):
+    """Kurganov-Tadmor flux between the face values WL (left side) and WR (right side)."""
+    F = np.zeros(NV)
+    _load().og_kt_flux(_p(_f64(WL)), _p(_f64(WR)), int(d), _p(F))
+    return F
+
+
+def kt_reconstruct(Wm, W0, Wp, d):
+    """(lo, hi) face values of a cell in the KT scheme (componentwise MC on primitives)."""
+    lo, hi = np.zeros(NV), np.zeros(NV)
+    _load().og_kt_reconstruct(_p(_f64(Wm)), _p(_f64(W0)), _p(_f64(Wp)), int(d), _p(lo), _p(hi))
+    return lo, hi
 
 
 def reconstruct(Wm, W0, Wp, d, dtdx):
