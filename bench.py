@@ -63,7 +63,7 @@ def parse():
     ap.add_argument("--fp32-only", action="store_true", help="skip the FP64 measurement")
     ap.add_argument("--tiling", default=None, help="rows,zchunk instead of autotuning (e.g. 8,32)")
     ap.add_argument("--suite", action="store_true", help="one JSON line per workload instead of the bench line")
-    ap.add_argument("--only", default=None, choices=["sod", "blast", "box", "tubes", "disc"],
+    ap.add_argument("--only", default=None, choices=["sod", "blast", "box", "schemes", "tubes", "disc"],
                     help="with --suite: run one workload (--n and --steps then size it)")
     return ap.parse_args()
 
@@ -391,8 +391,10 @@ def run_suite(args):
     def emit(d):
         print(json.dumps(d), flush=True)
 
-    def grid_rate(p, precision, steps, t_end=math.inf):
+    def grid_rate(p, precision, steps, t_end=math.inf, scheme=0):
         g = msh.Grid.from_problem(p, precision, stream=stream.cuda_stream)
+        if scheme:
+            g.set_scheme(scheme)
         W = p.W.astype(np.float32) if precision == msh.FP32 else p.W
         g.set_state(W, msh.PRIMITIVE)
         if p.ndim > 1:
@@ -444,6 +446,15 @@ def run_suite(args):
         emit({"workload": f"turb {p.n[0]}^3, {steps} steps (FP64: {min(steps, 20)})", "gpu_fp32": r32,
               "gpu_fp64": r64, "oracle": orc, "oracle_cores": cores, "oracle_sample": "1 FP64 step of the full grid",
               "gpu_fp32_over_oracle": r32["value"] / orc})
+    # the two schemes at the same CFL number: time per step (Sec. 4.1 reports the central
+    # scheme about 22 % cheaper than the characteristic one on the CPU)
+    if only in (None, "schemes"):
+        for name, p in (("box", inputs.turb(n=args.n or 256, cfl=0.4)), ("blast", inputs.blast(n=args.n or 1024, cfl=0.4))):
+            steps = 50 if only is None else args.steps
+            mh = grid_rate(p, msh.FP32, steps)
+            kt = grid_rate(p, msh.FP32, steps, scheme=msh.KT)
+            emit({"workload": f"{name} {p.n[0]}^{p.ndim} FP32, CFL 0.4, {steps} steps: MUSCL-Hancock vs Kurganov-Tadmor",
+                  "muscl_hancock": mh, "kurganov_tadmor": kt, "kt_ms_over_mh_ms": kt["ms_per_step"] / mh["ms_per_step"]})
     if only in (None, "tubes"):
         run_suite_tubes(msh, inputs, stream, emit)
     if only in (None, "disc"):

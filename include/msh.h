@@ -56,6 +56,9 @@ typedef int32_t msh_status;
 #define MSH_FP32 0
 #define MSH_FP64 1
 
+#define MSH_SCHEME_MUSCL_HANCOCK 0 /* characteristic MUSCL-Hancock + HLL (Sec. 3.3)     */
+#define MSH_SCHEME_KT 1            /* Kurganov-Tadmor central scheme + RK2 (Sec. 3.2)   */
+
 #define MSH_HOST 0
 #define MSH_DEVICE 1
 
@@ -210,6 +213,22 @@ msh_status msh_adjoint_run(msh_grid *g, const void *U0, int64_t nsteps, const do
  */
 msh_status msh_set_tape(msh_grid *g, int32_t K, int64_t max_steps);
 msh_status msh_adjoint_tape(msh_grid *g, const void *dL_dUN, void *dL_dU0, int32_t where, int32_t kind);
+
+/*
+ * Scheme of the grid's steps (default MSH_SCHEME_MUSCL_HANCOCK).  MSH_SCHEME_KT is the
+ * semi-discrete central scheme of Kurganov & Tadmor (Sec. 3.2, eq 4.2 of their paper):
+ *   du_i/dt = -sum_d (H_{i+1/2} - H_{i-1/2}) / dx_d,
+ *   H_{i+1/2} = (f(u+) + f(u-)) / 2 - a_{i+1/2} (u+ - u-) / 2,
+ * with a_{i+1/2} the larger spectral radius |u_n| + sqrt(3 P_nn / rho) of the two face
+ * values (eqs spectralfreq, soundspeed with gamma = 3), face values from the primitive
+ * variables reconstructed component by component with the MC limiter (first order where a
+ * face value has rho <= 0 or P_nn <= 0), Heun's second-order Runge-Kutta stages
+ * (u1 = u + dt L(u), u_new = (u + u1 + dt L(u1)) / 2), the gravity source after them and
+ * the same CFL rule; it has no a-posteriori fallback.  Selecting it allocates one more
+ * state buffer.  The adjoint (msh_adjoint_run, msh_set_tape) covers MUSCL-Hancock only:
+ * MSH_E_STATE otherwise.
+ */
+msh_status msh_set_scheme(msh_grid *g, int32_t scheme);
 
 /*
  * Slab decomposition: several grids, each owning a slab of one global grid along its last

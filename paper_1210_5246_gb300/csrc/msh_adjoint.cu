@@ -426,6 +426,7 @@ cudaError_t forward_step(msh_grid *g, Ctrl *ctl, Partial *part, T *src, T *dst, 
   a.ck_base = 0;
   a.ck_len = 0;
   a.ck_K = 1;
+  a.U1 = nullptr;
   for (int level = 0; level <= (passes ? kFallbackPasses : 0); level++) {
     a.level = level;
     e = launch_step<T>(a, g->ndim, g->rows, level > 0, g->stream, nullptr);
@@ -642,6 +643,7 @@ extern "C" msh_status msh_adjoint_run(msh_grid *g, const void *U0, int64_t nstep
   for (int64_t s = 0; s < nsteps; s++)
     if (!(dt_sched[s] > 0.0) || !std::isfinite(dt_sched[s]))
       return afail(MSH_E_INVALID_ARG, "dt_sched[%lld] must be finite and > 0", (long long)s);
+  if (g->scheme != MSH_SCHEME_MUSCL_HANCOCK) return afail(MSH_E_STATE, "the adjoint covers the MUSCL-Hancock scheme only");
   if (g->prec == MSH_FP32)
     return adjoint_impl<float>(g, U0, nsteps, dt_sched, K, dL_dUN, dL_dU0, where, kind);
   return adjoint_impl<double>(g, U0, nsteps, dt_sched, K, dL_dUN, dL_dU0, where, kind);

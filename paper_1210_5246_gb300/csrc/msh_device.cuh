@@ -276,6 +276,57 @@ __device__ __forceinline__ void hll(const T (&wl)[NV], const T (&wr)[NV], T (&F)
   for (int k = 0; k < NV; k++) F[k] = a * Fl[k] + (b * Fr[k] + c * (Ur[k] - Ul[k]));
 }
 
+// ------------------------------------------------------- Kurganov-Tadmor
+// Face values of one cell for the central scheme of Sec. 3.2 (local frame): primitive
+// variables reconstructed component by component with the MC limiter (computed doubled:
+// w0 -+ 2mc/4 is exactly w0 -+ mc/2); a face value with rho <= 0 or P_nn <= 0 reverts both
+// faces to w0.
+template <typename T>
+__device__ __forceinline__ void kt_reconstruct(const T (&wm)[NV], const T (&w0)[NV], const T (&wp)[NV],
+                                               T (&lo)[NV], T (&hi)[NV]) {
+#pragma unroll
+  for (int k = 0; k < NV; k++) {
+    const T s2 = mc_limit2(w0[k] - wm[k], wp[k] - w0[k]);
+    hi[k] = w0[k] + T(0.25) * s2;
+    lo[k] = w0[k] - T(0.25) * s2;
+  }
+  const bool ok = hi[0] > T(0) && lo[0] > T(0) && hi[4] > T(0) && lo[4] > T(0);
+  if (!ok) {
+#pragma unroll
+    for (int k = 0; k < NV; k++) { hi[k] = w0[k]; lo[k] = w0[k]; }
+  }
+}
+
+// Central flux H = (f(wl) + f(wr))/2 - a (U(wr) - U(wl))/2 through a face with the value wl
+// on its left side and wr on its right side; a = the larger spectral radius of df/du,
+// |u_n| + sqrt(3 P_nn / rho), of the two (eqs spectralfreq, soundspeed with gamma = 3).
+template <typename T>
+__device__ __forceinline__ void kt_flux(const T (&wl)[NV], const T (&wr)[NV], T (&F)[NV]) {
+  T Ul[NV], Fl[NV], Ur[NV], Fr[NV];
+  phys(wl, Ul, Fl);
+  phys(wr, Ur, Fr);
+  const T al = fabs(wl[1]) + T(1.7320508075688772) * sqrt_ratio(wl[4], wl[0]);
+  const T ar = fabs(wr[1]) + T(1.7320508075688772) * sqrt_ratio(wr[4], wr[0]);
+  const T h = T(0.5) * fmax(al, ar);
+#pragma unroll
+  for (int k = 0; k < NV; k++) F[k] = T(0.5) * (Fr[k] + Fl[k]) - h * (Ur[k] - Ul[k]);
+}
+
+// Scheme of a step kernel: 0 the characteristic MUSCL-Hancock step with HLL (Sec. 3.3);
+// 1 and 2 the two Runge-Kutta stages of the Kurganov-Tadmor scheme (Sec. 3.2).
+template <int SCH, typename T>
+__device__ __forceinline__ void recon(const T (&wm)[NV], const T (&w0)[NV], const T (&wp)[NV], T nu, T (&lo)[NV],
+                                      T (&hi)[NV]) {
+  if constexpr (SCH == 0) reconstruct(wm, w0, wp, nu, lo, hi);
+  else kt_reconstruct(wm, w0, wp, lo, hi);
+}
+
+template <int SCH, typename T>
+__device__ __forceinline__ void face_flux(const T (&wl)[NV], const T (&wr)[NV], T (&F)[NV]) {
+  if constexpr (SCH == 0) hll(wl, wr, F);
+  else kt_flux(wl, wr, F);
+}
+
 // ---------------------------------------------------------- accumulators
 // Per-thread running sums of the conserved totals over the cells one thread updates in a
 // tile (at most one streamed chunk, 64 cells with the autotuned tilings).  FP64 states add

@@ -79,6 +79,7 @@ template <typename T> StepArgs<T> make_args(msh_grid *g) {
   a.ck_base = g->tape_base;
   a.ck_len = g->tape_len;
   a.ck_K = g->tape_K > 0 ? g->tape_K : 1;
+  a.U1 = (T *)g->U1;
   return a;
 }
 
@@ -137,6 +138,20 @@ msh_status launch_one_step(msh_grid *g, int ev_slot) {
   int nb = 0;
   cudaError_t e;
   if (g->profiling && ev_slot >= 0) CUDA_TRY(cudaEventRecord(g->ev[3 * ev_slot], g->stream));
+  if (g->scheme == MSH_SCHEME_KT) {
+    // the two Runge-Kutta stages of the central scheme, then the finalize (no fallback)
+    nb = blocks_for(g, g->rows, g->zchunk);
+    for (int stage = 1; stage <= 2; stage++) {
+      e = g->prec == MSH_FP32 ? launch_step_kt<float>(make_args<float>(g), g->ndim, g->rows, stage, g->stream)
+                              : launch_step_kt<double>(make_args<double>(g), g->ndim, g->rows, stage, g->stream);
+      if (e != cudaSuccess) return fail(MSH_E_CUDA, "central scheme stage %d launch: %s", stage, cudaGetErrorString(e));
+    }
+    if (g->profiling && ev_slot >= 0) CUDA_TRY(cudaEventRecord(g->ev[3 * ev_slot + 1], g->stream));
+    e = launch_finalize(g->ctrl, g->part, nb, 0, g->stream);
+    if (e != cudaSuccess) return fail(MSH_E_CUDA, "finalize launch: %s", cudaGetErrorString(e));
+    if (g->profiling && ev_slot >= 0) CUDA_TRY(cudaEventRecord(g->ev[3 * ev_slot + 2], g->stream));
+    return MSH_OK;
+  }
   if (g->prec == MSH_FP32) e = launch_step<float>(make_args<float>(g), g->ndim, g->rows, false, g->stream, &nb);
   else e = launch_step<double>(make_args<double>(g), g->ndim, g->rows, false, g->stream, &nb);
   if (e != cudaSuccess) return fail(MSH_E_CUDA, "step kernel launch: %s", cudaGetErrorString(e));
@@ -352,6 +367,7 @@ msh_status msh_destroy(msh_grid *g) {
   if (g->flags) cudaFree(g->flags);
   if (g->hist) cudaFree(g->hist);
   if (g->ctrl_aux) cudaFree(g->ctrl_aux);
+  if (g->U1) cudaFree(g->U1);
   free_tape(g);
   if (g->own_stream && g->stream) cudaStreamDestroy(g->stream);
   delete g;
@@ -465,6 +481,19 @@ msh_status msh_set_potential(msh_grid *g, const double *phi, int32_t where) {
                                                      (int)g->n[2], g->dx, g->stream);
   if (e != cudaSuccess) return fail(MSH_E_CUDA, "gravity field: %s", cudaGetErrorString(e));
   CUDA_TRY(cudaStreamSynchronize(g->stream));
+  return MSH_OK;
+}
+
+msh_status msh_set_scheme(msh_grid *g, int32_t scheme) {
+  begin();
+  if (!g) return fail(MSH_E_INVALID_ARG, "null grid");
+  if (scheme != MSH_SCHEME_MUSCL_HANCOCK && scheme != MSH_SCHEME_KT) return fail(MSH_E_INVALID_ARG, "unknown scheme");
+  if (scheme == MSH_SCHEME_KT && g->tape_valid)
+    return fail(MSH_E_STATE, "the adjoint tape covers the MUSCL-Hancock scheme only");
+  CUDA_TRY(cudaStreamSynchronize(g->stream));
+  if (scheme == MSH_SCHEME_KT && !g->U1) CUDA_TRY(cudaMalloc(&g->U1, g->N * 10 * g->esize));
+  if (scheme != g->scheme) drop_graph(g);
+  g->scheme = scheme;
   return MSH_OK;
 }
 
@@ -611,6 +640,8 @@ msh_status msh_set_tape(msh_grid *g, int32_t K, int64_t max_steps) {
   begin();
   if (!g) return fail(MSH_E_INVALID_ARG, "null grid");
   if (K < 0 || (K > 0 && max_steps < 1)) return fail(MSH_E_INVALID_ARG, "need K >= 1 and max_steps >= 1 (K = 0 frees)");
+  if (K > 0 && g->scheme != MSH_SCHEME_MUSCL_HANCOCK)
+    return fail(MSH_E_STATE, "the adjoint covers the MUSCL-Hancock scheme only");
   if (!g->has_state && K > 0) return fail(MSH_E_STATE, "msh_set_tape before msh_set_state");
   CUDA_TRY(cudaStreamSynchronize(g->stream));
   msh_status st = stop_tape(g);

@@ -54,6 +54,7 @@ template <typename T> struct StepArgs {
   T *ck;
   int64_t ck_base, ck_len;
   int ck_K;
+  T *U1;                // the central scheme's first-stage state (nullptr for MUSCL-Hancock)
 };
 
 constexpr int kTile1D = 128;   // threads per block of the 1D step kernel
@@ -73,6 +74,8 @@ constexpr int kFinalizeThreads = 256;
 // tagged cells whose second-order update was not realizable
 template <typename T> cudaError_t launch_step(const StepArgs<T> &a, int ndim, int rows, bool retry, cudaStream_t s,
                                               int *nblocks_out);
+// stage 1 or 2 of the Kurganov-Tadmor scheme (a.U1 must be set)
+template <typename T> cudaError_t launch_step_kt(const StepArgs<T> &a, int ndim, int rows, int stage, cudaStream_t s);
 template <typename T> int step_blocks(int ndim, int rows, int nx, int ny, int nz, int zchunk);
 template <typename T> size_t step_smem(int ndim, int rows);
 // partials of cells [c0, c1) (c1 = 0: all N)
@@ -131,6 +134,8 @@ struct msh_grid {
   // slab decomposition: a halo copy made the planned CFL step stale; a second control
   // block for reductions over a range of layers
   bool dt_stale = false;
+  int scheme = MSH_SCHEME_MUSCL_HANCOCK;
+  void *U1 = nullptr;  // first Runge-Kutta stage of the central scheme
   msh::Ctrl *ctrl_aux = nullptr;
   bool has_state = false;
   int rows = 8, zchunk = 32;

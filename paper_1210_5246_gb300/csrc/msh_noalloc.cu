@@ -61,6 +61,7 @@ msh_status noalloc_step(int ndim, const int64_t n[3], const double dx[3], const 
   a.ck_base = 0;
   a.ck_len = 0;
   a.ck_K = 1;
+  a.U1 = nullptr;
   const int rows = 8;
   const int nb = step_blocks<T>(ndim, rows, a.nx, a.ny, a.nz, a.zchunk);
   if ((size_t)nb > kNoallocMaxBlocks)

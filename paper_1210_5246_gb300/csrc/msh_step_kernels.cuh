@@ -1,0 +1,721 @@
+// msh_step_kernels.cuh -- the step kernels of libmsh and their launch templates.
+//
+// One launch = one full step (or one Runge-Kutta stage of the central scheme): boundary
+// handling by index mapping (guardcells, Sec. 3.1), conserved -> primitive,
+// per-direction reconstruction and face fluxes (characteristic MUSCL-Hancock with HLL,
+// Sec. 3.3; or the Kurganov-Tadmor central scheme, Sec. 3.2), unsplit conservative update,
+// gravity source after the hydro update (Sec. 3.3, last paragraph), and per-block partials
+// of the next CFL time step, the FP64 conserved totals and the realizability check.
+//
+// 3D kernel layout: a thread block is a 32 x ROWS grid of threads covering cells
+// (x0-1 .. x0+30, y0-1 .. y0+ROWS-2); the 30 x (ROWS-2) interior cells are updated, the
+// ring of halo threads reconstructs the neighbours whose face states the interior needs.
+// z planes stream through a three-plane shared-memory ring (2.5D): x and y fluxes come
+// from the current plane, the z flux is carried in registers from plane to plane, so
+// every cell is reconstructed once per direction.  2D: one warp per 32-column strip
+// streamed in y (step_strip2d_kernel).
+//
+// Template parameter SCH: 0 MUSCL-Hancock (the step); 1, 2 the two stages of the central
+// scheme (stage 1 writes U1 = U^n + dt L(U^n), stage 2 sweeps U1 and writes
+// (U^n + U1 + dt L(U1)) / 2 with the source and the partials).
+#pragma once
+#include <algorithm>
+#include <cfloat>
+#include <climits>
+
+#include "msh_device.cuh"
+#include "msh_internal.h"
+
+namespace msh {
+
+constexpr unsigned FULL = 0xffffffffu;
+
+// ------------------------------------------------------------ block partials
+template <int NT>
+__device__ __forceinline__ void block_partial(double (&diag)[NV], double smax, long long bad,
+                                              Partial *out) {
+  __shared__ double red[NT / 32][NV + 1];
+  __shared__ long long redb[NT / 32];
+  const int lane = threadIdx.x & 31;
+  const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+  const int warp = tid >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+    for (int k = 0; k < NV; k++) diag[k] += __shfl_down_sync(FULL, diag[k], o);
+    smax = fmax(smax, __shfl_down_sync(FULL, smax, o));
+    bad = min(bad, __shfl_down_sync(FULL, bad, o));
+  }
+  if (lane == 0) {
+#pragma unroll
+    for (int k = 0; k < NV; k++) red[warp][k] = diag[k];
+    red[warp][NV] = smax;
+    redb[warp] = bad;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    Partial p;
+    for (int k = 0; k < NV; k++) p.diag[k] = 0.0;
+    p.smax = 0.0;
+    p.bad = LLONG_MAX;
+    for (int w = 0; w < NT / 32; w++) {
+      for (int k = 0; k < NV; k++) p.diag[k] += red[w][k];
+      p.smax = fmax(p.smax, red[w][NV]);
+      p.bad = min(p.bad, redb[w]);
+    }
+    *out = p;
+  }
+}
+
+// Sum over active dims of (|u_d| + sqrt(3 P_dd / rho)) / dx_d: the CFL signal-speed sum.
+template <typename T, int NDIM>
+__device__ __forceinline__ T speed_sum(const T (&W)[NV], T idx, T idy, T idz) {
+  const T r3 = T(3) * frcp(W[0]);
+  T s = (fabs(W[1]) + sqrt_ratio(W[4], W[0]) * T(1.7320508075688772)) * idx;
+  if (NDIM > 1) s += (fabs(W[2]) + sqrt_ratio(W[7], W[0]) * T(1.7320508075688772)) * idy;
+  if (NDIM > 2) s += (fabs(W[3]) + sqrt_ratio(W[9], W[0]) * T(1.7320508075688772)) * idz;
+  (void)r3;
+  return s;
+}
+
+// Checkpoint slot of the adjoint tape that step `step` stores U^step into, or nullptr.
+template <typename T> __device__ __forceinline__ T *tape_slot(const StepArgs<T> &a, int64_t step, size_t N) {
+  if (a.ck == nullptr) return nullptr;
+  const int64_t ts = step - a.ck_base;
+  if (ts < 0 || ts >= a.ck_len || ts % a.ck_K != 0) return nullptr;
+  return a.ck + (size_t)(ts / a.ck_K) * NV * N;
+}
+
+// Per-cell tail of the step: gravity source, store, next-dt speed, realizability, totals;
+// U^n also goes to the tape's checkpoint `ck` when the step has one.
+// U^n of the cell is read from src[k * stride] (the state in global memory, or a staged
+// copy in shared memory).
+// SCH 0: U^{n+1} = U^n + dt L (MUSCL-Hancock); SCH 1: U1 = U^n + dt L(U^n) (the first
+// Runge-Kutta stage, stored without sources or partials); SCH 2: U^{n+1} =
+// (U^n + U1 + dt L(U1)) / 2 with src = U1 and un0 = U^n of the cell (fields N apart).
+template <typename T, int NDIM, int SCH, bool RETRY>
+__device__ __forceinline__ void finish_cell(const StepArgs<T> &a, const T *src, size_t stride, const T *un0,
+                                            T *__restrict__ Ud, size_t N, size_t c,
+                                            const T (&acc)[NV], T dt, T idx, T idy, T idz, Acc<T> &diag,
+                                            T &smax, long long &bad, int32_t tag, T *__restrict__ ck) {
+  T Un[NV];
+#pragma unroll
+  for (int k = 0; k < NV; k++) {
+    const T u = src[k * stride];
+    if (SCH == 0 && !RETRY && ck != nullptr) ck[k * N + c] = u;
+    if (SCH == 2) Un[k] = T(0.5) * (un0[k * N] + (u + dt * acc[k]));
+    else Un[k] = u + dt * acc[k];
+  }
+  if (SCH == 1) {
+#pragma unroll
+    for (int k = 0; k < NV; k++) Ud[k * N + c] = Un[k];
+    return;
+  }
+  if (a.acc != nullptr) {
+    // a = -grad Phi: m += dt rho a, E += dt (mbar a^T + a mbar^T), mbar = (m* + m^{n+1})/2
+    T g[3] = {T(0), T(0), T(0)};
+    g[0] = a.acc[c];
+    if (NDIM > 1) g[1] = a.acc[N + c];
+    if (NDIM > 2) g[2] = a.acc[2 * N + c];
+    T mb[3];
+#pragma unroll
+    for (int i = 0; i < 3; i++) {
+      const T mn = Un[1 + i] + dt * Un[0] * g[i];
+      mb[i] = T(0.5) * (Un[1 + i] + mn);
+      Un[1 + i] = mn;
+    }
+    Un[4] += dt * T(2) * mb[0] * g[0];
+    Un[5] += dt * (mb[0] * g[1] + g[0] * mb[1]);
+    Un[6] += dt * (mb[0] * g[2] + g[0] * mb[2]);
+    Un[7] += dt * T(2) * mb[1] * g[1];
+    Un[8] += dt * (mb[1] * g[2] + g[1] * mb[2]);
+    Un[9] += dt * T(2) * mb[2] * g[2];
+  }
+#pragma unroll
+  for (int k = 0; k < NV; k++) Ud[k * N + c] = Un[k];
+  T W[NV];
+  cons_to_prim(Un, W);
+  if (!realizable(W)) {
+    bad = min(bad, (long long)c);
+    if (SCH != 0) goto done;  // the central scheme has no a-posteriori fallback
+    {
+    // tag the cell for the next fallback pass (a cell tagged by an earlier pass keeps its tag)
+    const int32_t f = a.flags[c];
+    if (!((f >> 3) == tag && (f & 7) < a.level)) {
+      a.flags[c] = tag * 8 + a.level;
+      atomicAdd(&a.ctrl->nbad[a.level], 1);
+    }
+    }
+  }
+done:
+  smax = fmax(smax, speed_sum<T, NDIM>(W, idx, idy, idz));
+  diag.add(Un);
+}
+
+template <typename T, int NT>
+__device__ __forceinline__ void write_partial(const Acc<T> &diag, T smax, long long bad, Partial *out) {
+  double d[NV];
+  diag.get(d);
+  block_partial<NT>(d, (double)smax, bad, out);
+}
+
+// A cell takes first-order faces in fallback pass `level` if an earlier pass of this step
+// tagged it.  Tags written during the current pass are ignored, so every thread block of
+// a pass sees the same tagged set.
+__device__ __forceinline__ bool tagged(int32_t f, int32_t tag, int level) {
+  return (f >> 3) == tag && (f & 7) < level;
+}
+
+// ------------------------------------------------------------------ 1D kernel
+template <typename T, int SCH, bool RETRY>
+__global__ void __launch_bounds__(kTile1D) step1d_kernel(StepArgs<T> a) {
+  constexpr int B = kTile1D, SXX = B + 2;
+  const Ctrl *ctrl = a.ctrl;
+  if (ctrl->done) return;
+  if (RETRY && ctrl->nbad[a.level - 1] == 0) return;
+  const int64_t step = ctrl->step;
+  const int32_t tag = (int32_t)(step & 0x0fffffff) + 1;
+  __shared__ unsigned char sFl[RETRY ? SXX : 1];
+  // sweep source, destination and U^n (the second Runge-Kutta stage sweeps U1)
+  const T *__restrict__ U0 = a.U[step & 1];
+  const T *__restrict__ Us = SCH == 2 ? a.U1 : U0;
+  T *__restrict__ Ud = SCH == 1 ? a.U1 : a.U[(step + 1) & 1];
+  const double dtd = ctrl->dt;
+  const T dt = (T)dtd, nu = (T)(0.5 * dtd / a.dx[0]), idx = (T)(1.0 / a.dx[0]);
+  __shared__ T sW[NV][SXX];
+  __shared__ T sH[NV][B];
+  const int t = threadIdx.x;
+  const int nx = a.nx;
+  const size_t N = (size_t)nx;
+  const int ntiles = (nx + B - 3) / (B - 2);
+  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+  const int x0 = tile * (B - 2);
+  for (int i = t; i < SXX; i += B) {
+    bool mir;
+    const int xx = map_index(x0 - 2 + i, nx, a.bc[0], a.bc[1], mir);
+    T U[NV], W[NV];
+#pragma unroll
+    for (int k = 0; k < NV; k++) U[k] = Us[k * N + xx];
+    if (mir) {
+      U[1] = -U[1]; U[5] = -U[5]; U[6] = -U[6];
+    }
+    cons_to_prim(U, W);
+#pragma unroll
+    for (int k = 0; k < NV; k++) sW[k][i] = W[k];
+    if (RETRY) sFl[i] = tagged(a.flags[xx], tag, a.level);
+  }
+  __syncthreads();
+  T wm[NV], w0[NV], wp[NV], lo[NV], hi[NV], F[NV];
+#pragma unroll
+  for (int k = 0; k < NV; k++) { wm[k] = sW[k][t]; w0[k] = sW[k][t + 1]; wp[k] = sW[k][t + 2]; }
+  recon<SCH>(wm, w0, wp, nu, lo, hi);
+  if (RETRY) first_order_faces(sFl[t] != 0, sFl[t + 1] != 0, sFl[t + 2] != 0, w0, lo, hi);
+#pragma unroll
+  for (int k = 0; k < NV; k++) sH[k][t] = hi[k];
+  __syncthreads();
+  if (t >= 1) {
+    T hl[NV];
+#pragma unroll
+    for (int k = 0; k < NV; k++) hl[k] = sH[k][t - 1];
+    face_flux<SCH>(hl, lo, F);
+  }
+  __syncthreads();
+  if (t >= 1) {
+#pragma unroll
+    for (int k = 0; k < NV; k++) sH[k][t] = F[k];
+  }
+  __syncthreads();
+  Acc<T> diag;
+  diag.zero();
+  T smax = T(0);
+  long long bad = LLONG_MAX;
+  const int gx = x0 - 1 + t;
+  if (t >= 1 && t <= B - 2 && gx < nx) {
+    T acc[NV];
+#pragma unroll
+    for (int k = 0; k < NV; k++) acc[k] = (F[k] - sH[k][t + 1]) * idx;
+    finish_cell<T, 1, SCH, RETRY>(a, Us + gx, N, U0 + gx, Ud, N, (size_t)gx, acc, dt, idx, T(0), T(0), diag, smax,
+                                  bad, tag, (RETRY || SCH != 0) ? nullptr : tape_slot(a, step, N));
+  }
+  write_partial<T, B>(diag, smax, bad, a.part + tile);
+  __syncthreads();  // the next tile reuses the shared arrays
+  }
+}
+
+// ----------------------------------------------------------------- 3D kernel
+// Raw staging slots of the 3D kernel: four keep U^n of the plane being updated in shared
+// memory (FP32, 16 rows: 224 KB with everything else); two otherwise (the update re-reads
+// U^n from global memory), which keeps two FP32 blocks of 8 rows per SM and FP64 within
+// the shared memory of a block.
+template <typename T, int BY> constexpr int kRawPlanes = (sizeof(T) == 4 && BY == 16) ? 4 : 2;
+// Asynchronous global -> shared copy of one element (cp.async, completion tracked per
+// thread by commit groups).
+template <typename T> __device__ __forceinline__ void cp_async_elem(T *smem, const T *gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  if constexpr (sizeof(T) == 4)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem) : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+// wait until at most N of this thread's most recent groups are pending
+template <int N> __device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+template <typename T, int D, int SY, int SX>
+__device__ __forceinline__ void gather(const T *__restrict__ pl, int sy, int sx, T (&w)[NV]) {
+#pragma unroll
+  for (int k = 0; k < NV; k++) w[k] = pl[(Frame<D>::g(k) * SY + sy) * SX + sx];
+}
+
+template <typename T, int NDIM, int BY, int SCH, bool RETRY>
+__global__ void __launch_bounds__(32 * BY, (BY <= 8 ? 2 : 1)) step_tile_kernel(StepArgs<T> a) {
+  static_assert(NDIM == 3, "the 2D step runs in step_strip2d_kernel");
+  constexpr int SX = 34, SY = BY + 2, NQ = SY * SX;
+  constexpr int PL = NV * NQ;  // one staged plane, all fields: [NV][SY][SX]
+  constexpr int RAW = kRawPlanes<T, BY>;  // raw staging slots (4: U^n of the update from shared memory)
+  const Ctrl *ctrl = a.ctrl;
+  if (ctrl->done) return;
+  if (RETRY && ctrl->nbad[a.level - 1] == 0) return;
+  const int64_t step = ctrl->step;
+  const int32_t tag = (int32_t)(step & 0x0fffffff) + 1;
+  // fallback tags of the staged cells (fallback pass only)
+  __shared__ unsigned char sFl[RETRY ? 3 : 1][RETRY ? NQ : 1];
+  // sweep source, destination and U^n (the second Runge-Kutta stage sweeps U1)
+  const T *__restrict__ U0 = a.U[step & 1];
+  const T *__restrict__ Us = SCH == 2 ? a.U1 : U0;
+  T *__restrict__ Ud = SCH == 1 ? a.U1 : a.U[(step + 1) & 1];
+  const double dtd = ctrl->dt;
+  const T dt = (T)dtd;
+  const T nux = (T)(0.5 * dtd / a.dx[0]), idx = (T)(1.0 / a.dx[0]);
+  const T nuy = (T)(0.5 * dtd / a.dx[1]), idy = (T)(1.0 / a.dx[1]);
+  const T nuz = (T)(0.5 * dtd / a.dx[2]), idz = (T)(1.0 / a.dx[2]);
+  T *const ck = (RETRY || SCH != 0) ? nullptr : tape_slot(a, step, (size_t)a.nx * a.ny * a.nz);
+  // shared memory: three primitive planes (ring), RAW raw conserved planes filled by
+  // cp.async one plane ahead, the y-sweep face states and fluxes, per staged cell the sign
+  // flips of reflect images (bits 0..9) and the fallback tag (bit 16)
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T *sW = reinterpret_cast<T *>(smem_raw);
+  T *sR = sW + 3 * PL;
+  T *sXh = sR + RAW * PL;        // [NV][BY][32]
+  T *sXf = sXh + NV * BY * 32;   // [NV][BY][32]
+  unsigned *sMeta = reinterpret_cast<unsigned *>(sXf + NV * BY * 32);  // [RAW][NQ]
+  auto slot = [](int p) { return ((p % RAW) + RAW) % RAW; };
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const int tid = ty * 32 + tx;
+  const int nx = a.nx, ny = a.ny, nz = a.nz;
+  const size_t N = (size_t)nx * ny * nz;
+  // One thread block per tile for the step; the fallback passes run on a small grid that
+  // loops over the tiles, so a pass with nothing to do costs only its launch.
+  const int tilesx = (nx + kTileX - 1) / kTileX, tilesy = (ny + BY - 3) / (BY - 2);
+  const int tilesz = (nz + a.zchunk - 1) / a.zchunk;
+  const int ntiles = tilesx * tilesy * tilesz;
+  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+  const int bxi = tile % tilesx, byi = (tile / tilesx) % tilesy, bzi = tile / (tilesx * tilesy);
+  const int x0 = bxi * kTileX, y0 = byi * (BY - 2);
+  const int gx = x0 - 1 + tx, gy = y0 - 1 + ty;
+  const int sx = tx + 1, sy = ty + 1;
+  const bool interior = tx >= 1 && tx <= kTileX && ty >= 1 && ty <= BY - 2;
+  const bool valid = interior && gx < nx && gy < ny;
+
+  // Staged cells: the 34 x (BY+2) box (x0-2 .. x0+31, y0-2 .. y0+BY-1) without its corners.
+  // A thread stages and later converts the same cells, so the copies it waits for are its
+  // own and no barrier separates staging from conversion.
+  auto stage = [&](int z) {
+    bool mz = false;
+    const int zz = map_index(z, nz, a.bc[4], a.bc[5], mz);
+    T *dst = sR + slot(z) * PL;
+    unsigned *meta = sMeta + slot(z) * NQ;
+    for (int i = tid; i < NQ; i += 32 * BY) {
+      const int qy = i / SX, qx = i - qy * SX;
+      if (!((qy >= 2 && qy <= BY - 1) || (qx >= 2 && qx <= 31))) continue;
+      bool mx, my;
+      const int xx = map_index(x0 - 2 + qx, nx, a.bc[0], a.bc[1], mx);
+      const int yy = map_index(y0 - 2 + qy, ny, a.bc[2], a.bc[3], my);
+      const size_t c = ((size_t)zz * ny + yy) * nx + xx;
+#pragma unroll
+      for (int k = 0; k < NV; k++) cp_async_elem(dst + k * NQ + i, Us + k * N + c);
+      unsigned m = (mx ? flip_mask(0) : 0u) ^ (my ? flip_mask(1) : 0u) ^ (mz ? flip_mask(2) : 0u);
+      if (RETRY && tagged(a.flags[c], tag, a.level)) m |= 1u << 16;
+      meta[i] = m;
+    }
+    cp_async_commit();
+  };
+  auto convert = [&](int z) {  // raw plane z -> primitive plane in ring slot z mod 3
+    const T *src = sR + slot(z) * PL;
+    const unsigned *meta = sMeta + slot(z) * NQ;
+    const int b = ((z % 3) + 3) % 3;
+    T *dst = sW + b * PL;
+    for (int i = tid; i < NQ; i += 32 * BY) {
+      const int qy = i / SX, qx = i - qy * SX;
+      if (!((qy >= 2 && qy <= BY - 1) || (qx >= 2 && qx <= 31))) continue;
+      const unsigned m = meta[i];
+      T U[NV], W[NV];
+#pragma unroll
+      for (int k = 0; k < NV; k++) {
+        const T v = src[k * NQ + i];
+        U[k] = ((m >> k) & 1u) ? -v : v;
+      }
+      cons_to_prim(U, W);
+#pragma unroll
+      for (int k = 0; k < NV; k++) dst[k * NQ + i] = W[k];
+      if (RETRY) sFl[RETRY ? b : 0][i] = (m >> 16) & 1u;
+    }
+  };
+  auto buf = [](int p) { return ((p % 3) + 3) % 3; };
+  auto fl = [&](int b, int qy, int qx) -> bool { return RETRY ? sFl[RETRY ? b : 0][qy * SX + qx] != 0 : false; };
+  // z reconstruction of cell p (planes p-1, p, p+1) in the interior threads
+  auto recon_z = [&](int p, T (&lo)[NV], T (&hi)[NV]) {
+    T wm[NV], w0[NV], wp[NV];
+    gather<T, 2, SY, SX>(sW + buf(p - 1) * PL, sy, sx, wm);
+    gather<T, 2, SY, SX>(sW + buf(p) * PL, sy, sx, w0);
+    gather<T, 2, SY, SX>(sW + buf(p + 1) * PL, sy, sx, wp);
+    recon<SCH>(wm, w0, wp, nuz, lo, hi);
+    if (RETRY) first_order_faces(fl(buf(p - 1), sy, sx), fl(buf(p), sy, sx), fl(buf(p + 1), sy, sx), w0, lo, hi);
+  };
+
+  Acc<T> diag;
+  diag.zero();
+  T smax = T(0);
+  long long bad = LLONG_MAX;
+  const int z0 = bzi * a.zchunk;
+  const int z1 = min(z0 + a.zchunk, nz);
+  // prologue: planes z0-2 .. z0+2 converted; the z face state of cell z0 and the flux
+  // through its lower face in registers
+  stage(z0 - 2);
+  stage(z0 - 1);
+  cp_async_wait<0>();
+  convert(z0 - 2);
+  convert(z0 - 1);
+  stage(z0);
+  cp_async_wait<0>();
+  convert(z0);
+  __syncthreads();
+  T hprev[NV], Fprev[NV];
+  if (interior) {
+    T lo[NV];
+    recon_z(z0 - 1, lo, hprev);
+  }
+  stage(z0 + 1);
+  cp_async_wait<0>();
+  __syncthreads();  // plane z0-2 is no longer read
+  convert(z0 + 1);
+  stage(z0 + 2);
+  __syncthreads();
+  if (interior) {
+    T lo[NV], hi[NV];
+    recon_z(z0, lo, hi);
+    face_flux<SCH>(hprev, lo, Fprev);
+#pragma unroll
+    for (int k = 0; k < NV; k++) hprev[k] = hi[k];
+  }
+  cp_async_wait<0>();
+  __syncthreads();  // plane z0-1 is no longer read
+  convert(z0 + 2);
+  __syncthreads();
+
+  for (int z = z0; z < z1; z++) {
+    // planes z, z+1, z+2 are converted
+    const T *pl = sW + buf(z) * PL;
+    T acc[NV];
+#pragma unroll
+    for (int k = 0; k < NV; k++) acc[k] = T(0);
+    if (ty >= 1 && ty <= BY - 2) {  // x sweep, warp-uniform: one warp per row
+      T wm[NV], w0[NV], wp[NV], lo[NV], hi[NV], hl[NV], F[NV];
+      gather<T, 0, SY, SX>(pl, sy, sx - 1, wm);
+      gather<T, 0, SY, SX>(pl, sy, sx, w0);
+      gather<T, 0, SY, SX>(pl, sy, sx + 1, wp);
+      recon<SCH>(wm, w0, wp, nux, lo, hi);
+      if (RETRY) first_order_faces(fl(buf(z), sy, sx - 1), fl(buf(z), sy, sx), fl(buf(z), sy, sx + 1), w0, lo, hi);
+#pragma unroll
+      for (int k = 0; k < NV; k++) hl[k] = __shfl_up_sync(FULL, hi[k], 1);
+      face_flux<SCH>(hl, lo, F);  // flux through the lower x face of this cell
+#pragma unroll
+      for (int k = 0; k < NV; k++) acc[k] += (F[k] - __shfl_down_sync(FULL, F[k], 1)) * idx;
+    }
+    const bool ycol = tx >= 1 && tx <= kTileX;
+    T ylo[NV], Fy[NV];
+    if (ycol) {  // y reconstruction of this cell; its upper face state goes to shared memory
+      T wm[NV], w0[NV], wp[NV], hi[NV];
+      gather<T, 1, SY, SX>(pl, sy - 1, sx, wm);
+      gather<T, 1, SY, SX>(pl, sy, sx, w0);
+      gather<T, 1, SY, SX>(pl, sy + 1, sx, wp);
+      recon<SCH>(wm, w0, wp, nuy, ylo, hi);
+      if (RETRY) first_order_faces(fl(buf(z), sy - 1, sx), fl(buf(z), sy, sx), fl(buf(z), sy + 1, sx), w0, ylo, hi);
+#pragma unroll
+      for (int k = 0; k < NV; k++) sXh[(k * BY + ty) * 32 + tx] = hi[k];
+    }
+    __syncthreads();
+    // Every thread has finished the previous plane: its raw slot (plane z-1 with four
+    // slots, z+1 with two) is free for plane z+3.
+    if (z + 3 <= z1 + 1) stage(z + 3);
+    if (ycol && ty >= 1) {  // flux through the lower y face
+      T hl[NV];
+#pragma unroll
+      for (int k = 0; k < NV; k++) hl[k] = sXh[(k * BY + ty - 1) * 32 + tx];
+      face_flux<SCH>(hl, ylo, Fy);
+#pragma unroll
+      for (int k = 0; k < NV; k++) sXf[(k * BY + ty) * 32 + tx] = Fy[k];
+    }
+    if (interior) {  // z: reconstruct cell z+1, flux through the upper z face of cell z
+      T lo[NV], hi[NV], F[NV];
+      recon_z(z + 1, lo, hi);
+      face_flux<SCH>(hprev, lo, F);
+#pragma unroll
+      for (int k = 0; k < NV; k++) {
+        acc[Frame<2>::g(k)] += (Fprev[k] - F[k]) * idz;
+        hprev[k] = hi[k];
+        Fprev[k] = F[k];
+      }
+    }
+    __syncthreads();
+    if (interior) {
+#pragma unroll
+      for (int k = 0; k < NV; k++) acc[Frame<1>::g(k)] += (Fy[k] - sXf[(k * BY + ty + 1) * 32 + tx]) * idy;
+    }
+    if (valid) {
+      const size_t c = ((size_t)z * ny + gy) * nx + gx;
+      if (RAW == 4)  // the swept state as staged (an interior cell is never a reflect image)
+        finish_cell<T, NDIM, SCH, RETRY>(a, sR + slot(z) * PL + sy * SX + sx, NQ, U0 + c, Ud, N, c, acc, dt, idx,
+                                         idy, idz, diag, smax, bad, tag, ck);
+      else
+        finish_cell<T, NDIM, SCH, RETRY>(a, Us + c, N, U0 + c, Ud, N, c, acc, dt, idx, idy, idz, diag, smax, bad,
+                                         tag, ck);
+    }
+    // Plane z is no longer read (every read of the primitive planes precedes the second
+    // barrier); plane z+3 replaces it.  The next iteration reads it only after its first
+    // barrier, and rewrites sXh / sXf only after every thread has passed this one.
+    if (z + 1 < z1) {
+      cp_async_wait<0>();
+      convert(z + 3);
+    }
+  }
+  cp_async_wait<0>();
+  write_partial<T, 32 * BY>(diag, smax, bad, a.part + tile);
+  __syncthreads();  // the next tile restages every buffer
+  }
+}
+
+// ---------------------------------------------------------------- 2D kernel
+// One warp owns a strip of 32 columns, lane l holding cell x0 - 2 + l, and streams it in
+// y over `ychunk` rows; lanes 2..29 are updated (kStripX = 28 cells per strip).  x faces:
+// warp shuffles of the row held in registers; y faces: a three-row register ring with the
+// face state and flux of the previous row carried, so every cell is reconstructed once
+// per direction.  Warps never wait on one another inside a tile; a thread block of WARPS
+// strips writes one partial.
+template <typename T, int WARPS, int SCH, bool RETRY>
+__global__ void __launch_bounds__(32 * WARPS) step_strip2d_kernel(StepArgs<T> a) {
+  const Ctrl *ctrl = a.ctrl;
+  if (ctrl->done) return;
+  if (RETRY && ctrl->nbad[a.level - 1] == 0) return;
+  const int64_t step = ctrl->step;
+  const int32_t tag = (int32_t)(step & 0x0fffffff) + 1;
+  // sweep source, destination and U^n (the second Runge-Kutta stage sweeps U1)
+  const T *__restrict__ U0 = a.U[step & 1];
+  const T *__restrict__ Us = SCH == 2 ? a.U1 : U0;
+  T *__restrict__ Ud = SCH == 1 ? a.U1 : a.U[(step + 1) & 1];
+  const double dtd = ctrl->dt;
+  const T dt = (T)dtd;
+  const T nux = (T)(0.5 * dtd / a.dx[0]), idx = (T)(1.0 / a.dx[0]);
+  const T nuy = (T)(0.5 * dtd / a.dx[1]), idy = (T)(1.0 / a.dx[1]);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nx = a.nx, ny = a.ny, ych = a.zchunk;
+  const size_t N = (size_t)nx * ny;
+  T *const ck = (RETRY || SCH != 0) ? nullptr : tape_slot(a, step, N);
+  const int stripsx = (nx + kStripX - 1) / kStripX, chunksy = (ny + ych - 1) / ych;
+  const int ntiles = stripsx * chunksy;
+  const int ngroups = (ntiles + WARPS - 1) / WARPS;
+  for (int grp = blockIdx.x; grp < ngroups; grp += gridDim.x) {
+    Acc<T> diag;
+    diag.zero();
+    T smax = T(0);
+    long long bad = LLONG_MAX;
+    const int tile = grp * WARPS + warp;
+    if (tile < ntiles) {  // warp-uniform
+      const int x0 = (tile % stripsx) * kStripX, y0 = (tile / stripsx) * ych;
+      const int y1 = min(y0 + ych, ny);
+      const int gx = x0 - 2 + lane;
+      bool mx;
+      const int xx = map_index(gx, nx, a.bc[0], a.bc[1], mx);
+      const bool upd = lane >= 2 && lane <= kStripX + 1 && gx < nx;
+      // raw conserved row (with the reflect images' sign flips) and its fallback tag
+      auto fetch = [&](int y, T (&U)[NV], bool &fl) {
+        bool my;
+        const int yy = map_index(y, ny, a.bc[2], a.bc[3], my);
+        const unsigned flip = (mx ? flip_mask(0) : 0u) ^ (my ? flip_mask(1) : 0u);
+        const size_t c = (size_t)yy * nx + xx;
+#pragma unroll
+        for (int k = 0; k < NV; k++) {
+          const T v = Us[k * N + c];
+          U[k] = ((flip >> k) & 1u) ? -v : v;
+        }
+        fl = RETRY ? tagged(a.flags[c], tag, a.level) : false;
+      };
+      auto ylocal = [](const T (&w)[NV], T (&o)[NV]) {
+#pragma unroll
+        for (int k = 0; k < NV; k++) o[k] = w[Frame<1>::g(k)];
+      };
+      // ring: rows y, y+1, y+2 (primitive, y local frame) and their tags
+      T r0[NV], r1[NV], r2[NV], hprev[NV], Fprev[NV];
+      bool f0 = false, f1 = false, f2 = false;
+      {
+        T U[NV], w[NV], wa[NV];
+        bool fa;
+        fetch(y0 - 2, U, fa); cons_to_prim(U, w); ylocal(w, wa);
+        fetch(y0 - 1, U, f0); cons_to_prim(U, w); ylocal(w, r0);
+        fetch(y0, U, f1); cons_to_prim(U, w); ylocal(w, r1);
+        fetch(y0 + 1, U, f2); cons_to_prim(U, w); ylocal(w, r2);
+        T lo[NV], hi[NV];
+        recon<SCH>(wa, r0, r1, nuy, lo, hprev);  // cell y0-1
+        if (RETRY) first_order_faces(fa, f0, f1, r0, lo, hprev);
+        recon<SCH>(r0, r1, r2, nuy, lo, hi);     // cell y0
+        if (RETRY) first_order_faces(f0, f1, f2, r1, lo, hi);
+        face_flux<SCH>(hprev, lo, Fprev);                     // flux through y0 - 1/2
+#pragma unroll
+        for (int k = 0; k < NV; k++) {
+          hprev[k] = hi[k];
+          r0[k] = r1[k];
+          r1[k] = r2[k];
+        }
+        f0 = f1;
+        f1 = f2;
+      }
+      for (int y = y0; y < y1; y++) {
+        T Un2[NV];
+        fetch(y + 2, Un2, f2);  // issued before the x sweep hides its latency
+        T acc[NV];
+        {
+          // x sweep of row y: local x frame = natural order
+          T w0[NV], wm[NV], wp[NV], lo[NV], hi[NV], hl[NV], F[NV];
+#pragma unroll
+          for (int k = 0; k < NV; k++) w0[k] = r0[Frame<1>::g(k)];  // Frame<1> is an involution
+#pragma unroll
+          for (int k = 0; k < NV; k++) {
+            wm[k] = __shfl_up_sync(FULL, w0[k], 1);
+            wp[k] = __shfl_down_sync(FULL, w0[k], 1);
+          }
+          recon<SCH>(wm, w0, wp, nux, lo, hi);
+          if (RETRY) {
+            const bool fm = __shfl_up_sync(FULL, f0, 1), fp = __shfl_down_sync(FULL, f0, 1);
+            first_order_faces(fm, f0, fp, w0, lo, hi);
+          }
+#pragma unroll
+          for (int k = 0; k < NV; k++) hl[k] = __shfl_up_sync(FULL, hi[k], 1);
+          face_flux<SCH>(hl, lo, F);  // flux through the lower x face of this cell
+#pragma unroll
+          for (int k = 0; k < NV; k++) acc[k] = (F[k] - __shfl_down_sync(FULL, F[k], 1)) * idx;
+        }
+        {
+          // y: reconstruct cell y+1, flux through y + 1/2
+          T w[NV];
+          cons_to_prim(Un2, w);
+          ylocal(w, r2);
+          T lo[NV], hi[NV], F[NV];
+          recon<SCH>(r0, r1, r2, nuy, lo, hi);
+          if (RETRY) first_order_faces(f0, f1, f2, r1, lo, hi);
+          face_flux<SCH>(hprev, lo, F);
+#pragma unroll
+          for (int k = 0; k < NV; k++) {
+            acc[Frame<1>::g(k)] += (Fprev[k] - F[k]) * idy;
+            hprev[k] = hi[k];
+            Fprev[k] = F[k];
+          }
+        }
+        if (upd)
+          finish_cell<T, 2, SCH, RETRY>(a, Us + ((size_t)y * nx + gx), N, U0 + ((size_t)y * nx + gx), Ud, N,
+                                        (size_t)y * nx + gx, acc, dt, idx, idy, T(0), diag, smax, bad, tag, ck);
+#pragma unroll
+        for (int k = 0; k < NV; k++) {
+          r0[k] = r1[k];
+          r1[k] = r2[k];
+        }
+        f0 = f1;
+        f1 = f2;
+      }
+    }
+    write_partial<T, 32 * WARPS>(diag, smax, bad, a.part + grp);
+    __syncthreads();  // the next group reuses the reduction buffers
+  }
+}
+
+// ---------------------------------------------------------------- launchers
+// grid of the fallback passes: two blocks per SM, looping over the tiles
+inline int fallback_blocks() {
+  static int blocks = 0;
+  if (blocks == 0) {
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    blocks = 2 * (sms > 0 ? sms : 152);
+  }
+  return blocks;
+}
+
+// 3D: 3 + RAW staged planes (three primitive, RAW raw) of NV x (rows+2) x 34, the y-sweep
+// face states and fluxes (2 x NV x rows x 32) and RAW planes of per-cell flags.
+template <typename T> size_t step_smem(int ndim, int rows) {
+  if (ndim < 3) return 0;
+  const size_t nq = (size_t)(rows + 2) * 34;
+  const size_t raw = rows == 16 ? kRawPlanes<T, 16> : rows == 8 ? kRawPlanes<T, 8> : kRawPlanes<T, 4>;
+  return sizeof(T) * ((3 + raw) * NV * nq + (size_t)2 * NV * rows * 32) + raw * nq * sizeof(unsigned);
+}
+
+template <typename T> int step_blocks(int ndim, int rows, int nx, int ny, int nz, int zchunk) {
+  if (ndim == 1) return (nx + kTile1D - 3) / (kTile1D - 2);
+  if (ndim == 2) {
+    const long tiles = (long)((nx + kStripX - 1) / kStripX) * ((ny + zchunk - 1) / zchunk);
+    return (int)((tiles + rows - 1) / rows);
+  }
+  const int bx = (nx + kTileX - 1) / kTileX;
+  const int by = (ny + rows - 3) / (rows - 2);
+  const int bz = ndim == 3 ? (nz + zchunk - 1) / zchunk : 1;
+  return bx * by * bz;
+}
+
+template <typename T, int NDIM, int BY, int SCH, bool RETRY>
+static cudaError_t launch_tile(const StepArgs<T> &a, cudaStream_t s) {
+  if constexpr (sizeof(T) == 8 && BY == 16) {
+    return cudaErrorInvalidConfiguration;  // 326 KB of shared memory: not offered for FP64
+  } else {
+  const size_t smem = step_smem<T>(NDIM, BY);
+  static bool attr_set = false;  // one attribute call per instantiation and process
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(step_tile_kernel<T, NDIM, BY, SCH, RETRY>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
+  const int ntiles = step_blocks<T>(NDIM, BY, a.nx, a.ny, a.nz, a.zchunk);
+  const int blocks = RETRY ? std::min(ntiles, fallback_blocks()) : ntiles;
+  step_tile_kernel<T, NDIM, BY, SCH, RETRY><<<blocks, dim3(32, BY), smem, s>>>(a);
+  return cudaGetLastError();
+  }
+}
+
+template <typename T, int WARPS, int SCH, bool RETRY>
+static cudaError_t launch_strip2d(const StepArgs<T> &a, cudaStream_t s) {
+  const int groups = step_blocks<T>(2, WARPS, a.nx, a.ny, 1, a.zchunk);
+  const int blocks = RETRY ? std::min(groups, fallback_blocks()) : groups;
+  step_strip2d_kernel<T, WARPS, SCH, RETRY><<<blocks, 32 * WARPS, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <typename T, int SCH, bool RETRY>
+static cudaError_t launch_step_mode(const StepArgs<T> &a, int ndim, int rows, cudaStream_t s) {
+  if (ndim == 1) {
+    const int ntiles = (a.nx + kTile1D - 3) / (kTile1D - 2);
+    step1d_kernel<T, SCH, RETRY><<<RETRY ? std::min(ntiles, fallback_blocks()) : ntiles, kTile1D, 0, s>>>(a);
+    return cudaGetLastError();
+  }
+  if (ndim == 2) {
+    if (rows == 4) return launch_strip2d<T, 4, SCH, RETRY>(a, s);
+    if (rows == 16) return launch_strip2d<T, 16, SCH, RETRY>(a, s);
+    return launch_strip2d<T, 8, SCH, RETRY>(a, s);
+  }
+  if (rows == 4) return launch_tile<T, 3, 4, SCH, RETRY>(a, s);
+  if (rows == 16) return launch_tile<T, 3, 16, SCH, RETRY>(a, s);
+  return launch_tile<T, 3, 8, SCH, RETRY>(a, s);
+}
+
+}  // namespace msh

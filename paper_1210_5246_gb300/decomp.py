@@ -2,13 +2,14 @@
 
 The unsplit step (Sec. 3.3) reaches two cells to each side, so a grid cut into slabs
 along its last active axis (z in 3D, y in 2D, x in 1D) advances exactly like the whole grid
-if, before every step, each slab receives two halo layers from each neighbour and all
+if, before every step, each slab receives two halo layers from each neighbour (four for
+the central scheme of Sec. 3.2, whose two Runge-Kutta stages each reach two cells) and all
 slabs take the same dt: the minimum over slabs of the CFL dt of the layers each owns.  The
 conserved totals are the sum over slabs of the owned layers' totals.  This is the only
 place where the path has an exchange step; everything else (independent grids, the
 batched tubes) shards with no collective (see ``replicas``).
 
-A rank's local grid holds its owned layers plus two halo layers on every side that has a
+A rank's local grid holds its owned layers plus the halo layers on every side that has a
 neighbour (both sides when the axis is periodic; none at a non-periodic end of the global
 grid, which keeps the global boundary condition).  A halo side's own boundary condition is
 a placeholder: the cells it affects are halo cells, overwritten by the next exchange.  The
@@ -30,7 +31,13 @@ from dataclasses import dataclass
 
 import numpy as np
 
-HALO = 2  # stencil radius of the step
+HALO = 2  # stencil radius of the MUSCL-Hancock step
+
+
+def halo_width(scheme=0):
+    """Halo layers a slab needs per step: two for the MUSCL-Hancock step; four for the
+    central scheme, whose two Runge-Kutta stages each reach two cells."""
+    return 2 * HALO if scheme == 1 else HALO
 
 
 class FallbackAcrossSlabs(RuntimeError):
@@ -59,14 +66,14 @@ class Slab:
 
 class Slabs:
     """Even partition of ``n`` layers into ``world`` slabs (the first n % world slabs one
-    layer longer), each owning at least HALO layers."""
+    layer longer), each owning at least ``halo`` layers, the halo width of the scheme."""
 
-    def __init__(self, n: int, world: int, periodic: bool):
+    def __init__(self, n: int, world: int, periodic: bool, halo: int = HALO):
         if world < 1:
             raise ValueError("world must be >= 1")
-        if world > 1 and n // world < HALO:
-            raise ValueError(f"{n} layers cannot give {world} slabs of at least {HALO} layers")
-        self.n, self.world, self.periodic = n, world, periodic
+        if world > 1 and n // world < halo:
+            raise ValueError(f"{n} layers cannot give {world} slabs of at least {halo} layers")
+        self.n, self.world, self.periodic, self.halo = n, world, periodic, halo
         base, extra = divmod(n, world)
         self.slabs = []
         s = 0
@@ -77,7 +84,7 @@ class Slabs:
             else:
                 lower = (r - 1) % world if (r > 0 or periodic) else None
                 upper = (r + 1) % world if (r < world - 1 or periodic) else None
-            self.slabs.append(Slab(r, s, c, HALO if lower is not None else 0, HALO if upper is not None else 0,
+            self.slabs.append(Slab(r, s, c, halo if lower is not None else 0, halo if upper is not None else 0,
                                    lower, upper))
             s += c
 
@@ -215,21 +222,22 @@ class SlabDriver:
         return 2 * dst + side
 
     def exchange(self):
-        """Copy HALO owned layers to each neighbour's halo.  Messages to other processes
+        """Copy the halo's width of owned layers to each neighbour's halo.  Messages to other processes
         go out in a fixed order (to the lower neighbour, then to the upper one) and are
         received in the matching order (from the upper neighbour, then the lower one)."""
         S = self.slabs
+        h = S.halo
         sends, recvs, local = [], [], []
         for r, st in self.steppers.items():
             sl = S[r]
             if sl.lower is not None:  # my lowest owned layers -> the lower neighbour's upper halo
-                arr = st.get(sl.lo_halo, HALO)
+                arr = st.get(sl.lo_halo, h)
                 if sl.lower in self.steppers:
                     local.append((sl.lower, 1, arr))
                 else:
                     sends.append((sl.lower, self._tag(sl.lower, 1), arr))
             if sl.upper is not None:  # my highest owned layers -> the upper neighbour's lower halo
-                arr = st.get(sl.lo_halo + sl.count - HALO, HALO)
+                arr = st.get(sl.lo_halo + sl.count - h, h)
                 if sl.upper in self.steppers:
                     local.append((sl.upper, 0, arr))
                 else:
@@ -244,10 +252,10 @@ class SlabDriver:
             got = self.comm.exchange(sends, [(peer, self._tag(r, side), shape, dtype) for peer, r, side in recvs])
         for dst, side, arr in local:
             sl = S[dst]
-            self.steppers[dst].set(0 if side == 0 else sl.lo_halo + sl.count, HALO, arr)
+            self.steppers[dst].set(0 if side == 0 else sl.lo_halo + sl.count, h, arr)
         for peer, r, side in recvs:
             sl = S[r]
-            self.steppers[r].set(0 if side == 0 else sl.lo_halo + sl.count, HALO, got[self._tag(r, side)])
+            self.steppers[r].set(0 if side == 0 else sl.lo_halo + sl.count, h, got[self._tag(r, side)])
 
     def reduce(self):
         """(totals, cfl dt, realizable) over the whole grid."""
@@ -310,8 +318,9 @@ class GridStepper:
         return self.g.step_dt(dt)
 
 
-def make_grid_steppers(msh, n, lo, hi, bc, cfl, precision, U, slabs: Slabs, ranks, phi=None, stream=None):
-    """Local libmsh grids (state set, potential sliced) for the given ranks."""
+def make_grid_steppers(msh, n, lo, hi, bc, cfl, precision, U, slabs: Slabs, ranks, phi=None, stream=None,
+                       scheme=0):
+    """Local libmsh grids (state set, potential sliced, scheme selected) for the given ranks."""
     parts = split_state(U, n, slabs)
     a = len(n) - 1
     periodic = bc[a][0] == 0
@@ -321,6 +330,8 @@ def make_grid_steppers(msh, n, lo, hi, bc, cfl, precision, U, slabs: Slabs, rank
         n_l, lo_l, hi_l, bc_l, dx = local_geometry(n, lo, hi, bc, sl)
         g = msh.Grid(n_l, lo_l, hi_l, bc_l, cfl, precision, stream=stream)
         g.set_cell_width(dx)
+        if scheme:
+            g.set_scheme(scheme)
         if phi is not None:
             g.set_potential(local_potential(phi, n, sl, periodic))
         g.set_state(parts[r].astype(g.dtype), msh.CONSERVED)

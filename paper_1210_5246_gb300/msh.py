@@ -20,6 +20,7 @@ from . import build as _build
 MSH_OK, MSH_E_INVALID_ARG, MSH_E_CUDA, MSH_E_NOMEM, MSH_E_REALIZABILITY, MSH_E_TIMEOUT, MSH_E_STATE = range(7)
 PERIODIC, OUTFLOW, REFLECT = 0, 1, 2
 FP32, FP64 = 0, 1
+MUSCL_HANCOCK, KT = 0, 1
 HOST, DEVICE = 0, 1
 CONSERVED, PRIMITIVE = 0, 1
 
@@ -61,6 +62,7 @@ SIGNATURES = {
     "msh_get_profile": [_vp, _P(_dbl), _P(_dbl), _P(_i64)],
     "msh_adjoint_run": [_vp, _vp, _i64, _P(_dbl), _i32, _vp, _vp, _i32, _i32],
     "msh_set_tape": [_vp, _i32, _i64],
+    "msh_set_scheme": [_vp, _i32],
     "msh_set_cell_width": [_vp, _P(_dbl)],
     "msh_get_slab": [_vp, _i64, _i64, _vp, _i32],
     "msh_set_slab": [_vp, _i64, _i64, _vp, _i32],
@@ -308,6 +310,10 @@ class Grid:
         po, wo, ko = self._buf(out)
         _check(load().msh_adjoint_run(self.h, p0, len(dts), _ptr_dbl(dts), int(K), pg, po, w0, kind))
         return out
+
+    def set_scheme(self, scheme):
+        """MUSCL_HANCOCK (default) or KT (see ``msh_set_scheme``)."""
+        _check(load().msh_set_scheme(self.h, int(scheme)))
 
     # -- slab decomposition -------------------------------------------------------
     def set_cell_width(self, dx):

@@ -203,3 +203,26 @@ def test_two_gloo_ranks_equal_single_grid(oracle, name):
     ref, t_ref = _single(oracle, name)
     assert ns == _problem(name)[-1] and t == t_ref
     np.testing.assert_array_equal(got, ref)
+
+
+def test_kt_slabs_need_four_halo_layers(oracle):
+    """The central scheme's two stages reach four cells: four halo layers reproduce the
+    single grid, two do not."""
+    from paper_1210_5246_gb300 import inputs
+    p = inputs.turb(n=16)
+    n, steps = p.n, 3
+    og = oracle.Grid(n, p.lo, p.hi, p.bc, 0.4, scheme=1)
+    ref, _, t_ref, rc, _ = oracle.run(og, oracle.prim_to_cons(p.W), np.inf, max_steps=steps)
+    for halo, equal in ((decomp.halo_width(1), True), (decomp.HALO, False)):
+        S = decomp.Slabs(n[-1], 3, True, halo=halo)
+        parts = decomp.split_state(oracle.prim_to_cons(p.W), n, S)
+        st = {}
+        for r in range(3):
+            n_l, lo_l, hi_l, bc_l, dx = decomp.local_geometry(n, p.lo, p.hi, p.bc, S[r])
+            stp = OracleStepper(oracle, n_l, lo_l, hi_l, bc_l, 0.4, parts[r], dx)
+            stp.g._g.scheme = 1
+            st[r] = stp
+        drv = decomp.SlabDriver(S, st)
+        ns, t = drv.run(steps)
+        got = decomp.join_owned([st[r].U for r in range(3)], n, S)
+        assert np.array_equal(got, ref.reshape(got.shape)) == equal
