@@ -75,9 +75,10 @@ def dist_env():
 
 def kernel_source_hash():
     """Hash of the source the 3D step kernel is compiled from: the per-cell arithmetic
-    (msh_device.cuh) and msh_step.cu up to the 2D kernel (helpers and step_tile_kernel)."""
+    (msh_device.cuh) and msh_step_kernels.cuh up to the 2D kernel (helpers and
+    step_tile_kernel)."""
     csrc = os.path.join(ROOT, "paper_1210_5246_gb300", "csrc")
-    step = open(os.path.join(csrc, "msh_step.cu")).read()
+    step = open(os.path.join(csrc, "msh_step_kernels.cuh")).read()
     cut = step.find("// ---------------------------------------------------------------- 2D kernel")
     h = hashlib.sha256()
     h.update(open(os.path.join(csrc, "msh_device.cuh"), "rb").read())
