@@ -296,3 +296,33 @@ def test_fallback_pass_fp64(msh, oracle, shape, n, bc, cfl):
     assert_fp64(g.get_state(), Uo, what=f"fallback {shape}")
     assert g.diagnostics()[1]
     g.close()
+
+
+@pytest.mark.parametrize("shape,n,bc,cfl", [((1, 1, 8), (8,), ((0, 0),), 0.8),
+                                            ((1, 12, 12), (12, 12), ((0, 0), (1, 2)), 0.5),
+                                            ((6, 7, 9), (9, 7, 6), ((2, 1), (0, 0), (1, 1)), 0.5)])
+def test_fallback_inside_graphs(msh, oracle, shape, n, bc, cfl):
+    """40 steps through the CUDA graphs of msh_run (16 steps each, every step with its
+    four fallback passes); one or two of the steps tag cells.  The result matches the
+    oracle and, bit for bit, the eager launches of the profiling mode."""
+    seed = {1: 1, 2: 0, 3: 0}[len(n)]
+    if len(n) == 1:
+        from tests.test_oracle_pins import _extreme_tiny
+        W = _extreme_tiny(1)
+    else:
+        W = _extreme(shape, seed)
+    nd = len(n)
+    og = oracle.Grid(n, (0,) * nd, (1,) * nd, bc, cfl)
+    Uo, no, _, rc, _ = oracle.run(og, oracle.prim_to_cons(W), np.inf, max_steps=40)
+    assert rc == 0 and no == 40
+    out = []
+    for profiled in (False, True):
+        g = msh.Grid(n, (0,) * nd, (1,) * nd, bc, cfl, msh.FP64)
+        g.set_profiling(profiled)
+        g.set_state(W, msh.PRIMITIVE)
+        ns, _ = g.run(max_steps=40)
+        assert ns == 40 and g.diagnostics()[1]
+        out.append(g.get_state())
+        g.close()
+    assert_fp64(out[0], Uo, what=f"graph fallback {shape}")
+    np.testing.assert_array_equal(out[0], out[1])
