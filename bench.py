@@ -63,7 +63,7 @@ def parse():
     ap.add_argument("--fp32-only", action="store_true", help="skip the FP64 measurement")
     ap.add_argument("--tiling", default=None, help="rows,zchunk instead of autotuning (e.g. 8,32)")
     ap.add_argument("--suite", action="store_true", help="one JSON line per workload instead of the bench line")
-    ap.add_argument("--only", default=None, choices=["sod", "blast", "box", "schemes", "tubes", "disc"],
+    ap.add_argument("--only", default=None, choices=["sod", "blast", "box", "schemes", "selfgrav", "tubes", "disc"],
                     help="with --suite: run one workload (--n and --steps then size it)")
     return ap.parse_args()
 
@@ -456,6 +456,31 @@ def run_suite(args):
             kt = grid_rate(p, msh.FP32, steps, scheme=msh.KT)
             emit({"workload": f"{name} {p.n[0]}^{p.ndim} FP32, CFL 0.4, {steps} steps: MUSCL-Hancock vs Kurganov-Tadmor",
                   "muscl_hancock": mh, "kurganov_tadmor": kt, "kt_ms_over_mh_ms": kt["ms_per_step"] / mh["ms_per_step"]})
+    # periodic self-gravity: the cost of the FFT Poisson solve and acceleration per step
+    if only in (None, "selfgrav"):
+        p = inputs.turb(n=args.n or 256)
+        steps = 20 if only is None else args.steps
+        base = grid_rate(p, msh.FP32, steps)
+        g = msh.Grid.from_problem(p, msh.FP32, stream=stream.cuda_stream)
+        g.set_self_gravity(1.0)
+        W = p.W.astype(np.float32)
+        g.set_state(W, msh.PRIMITIVE)
+        g.set_tiling(16, 32)
+        g.run(math.inf, 3)
+        g.set_state(W, msh.PRIMITIVE)
+        g.set_time(0.0, 0)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ns, _ = g.run(math.inf, steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / ns
+        g.close()
+        emit({"workload": f"box {p.n[0]}^3 FP32 with periodic self-gravity (G = 1), {steps} steps",
+              "ms_per_step": ms, "without_self_gravity_ms_per_step": base["ms_per_step"],
+              "self_gravity_ms_per_step": ms - base["ms_per_step"],
+              "cell_updates_per_s": int(np.prod(p.n)) * ns / (ms * ns * 1e-3)})
     if only in (None, "tubes"):
         run_suite_tubes(msh, inputs, stream, emit)
     if only in (None, "disc"):

@@ -231,6 +231,20 @@ msh_status msh_adjoint_tape(msh_grid *g, const void *dL_dUN, void *dL_dU0, int32
 msh_status msh_set_scheme(msh_grid *g, int32_t scheme);
 
 /*
+ * Periodic self-gravity with the gravitational constant G (> 0; 0 switches it off).  Needs
+ * periodic boundaries on every active dimension (MSH_E_INVALID_ARG otherwise).  Before every
+ * step the potential of the density of U^n solves the 3-point discrete Poisson equation
+ *   sum_d (Phi_{i+e_d} - 2 Phi_i + Phi_{i-e_d}) / dx_d^2 = 4 pi G (rho_i - mean rho)
+ * by FFT (cuFFT); a^n = -grad Phi^n by central differences, and the step's gravity source
+ * (applied after the hydro update, Sec. 3.3) uses the acceleration interpolated forward in
+ * time from the stored previous one (Sec. 3.3, last paragraph):
+ *   a^{n+1/2} = a^n + (dt_n / (2 dt_{n-1})) (a^n - a^{n-1}),  a^n on a state's first step,
+ * plus -grad of the external potential if one is set.  Works with both schemes; not with
+ * the adjoint (MSH_E_STATE) and not within a slab decomposition (the solve is global).
+ */
+msh_status msh_set_self_gravity(msh_grid *g, double G);
+
+/*
  * Slab decomposition: several grids, each owning a slab of one global grid along its last
  * active axis (z in 3D, y in 2D, x in 1D) plus two halo layers copied from the
  * neighbouring slabs before every step (the stencil radius of the step is two cells,

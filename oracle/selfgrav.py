@@ -44,9 +44,10 @@ def with_ghosts(phi, nd):
     return np.pad(phi, pads, mode="wrap")
 
 
-def run(grid: O.Grid, U, steps, G=1.0, history=None):
+def run(grid: O.Grid, U, steps, G=1.0, history=None, phi_ext=None):
     """``steps`` CFL steps with self-gravity; returns (U, dt list).  ``history`` (a dict,
-    updated in place) carries the previous step's potential and dt across calls."""
+    updated in place) carries the previous step's potential and dt across calls;
+    ``phi_ext`` (with its ghost layer) is an external potential added to the self-potential."""
     nd = grid.ndim
     dx = grid.dx[:nd]
     U = np.array(U, dtype=np.float64).reshape(grid.shape)
@@ -57,7 +58,10 @@ def run(grid: O.Grid, U, steps, G=1.0, history=None):
         phi = poisson_periodic(U[0], dx, G)
         prev = h.get("phi")
         phi_half = phi if prev is None else phi + (dt / (2.0 * h["dt"])) * (phi - prev)
-        U = O.step(grid, U, dt, phi=with_ghosts(phi_half, nd))
+        ph = with_ghosts(phi_half, nd)
+        if phi_ext is not None:
+            ph = ph + np.asarray(phi_ext, dtype=np.float64).reshape(ph.shape)
+        U = O.step(grid, U, dt, phi=ph)
         h["phi"], h["dt"] = phi, dt
         dts.append(dt)
     return U, dts

@@ -64,7 +64,7 @@ template <typename T> StepArgs<T> make_args(msh_grid *g) {
   StepArgs<T> a;
   a.U[0] = (T *)g->U[0];
   a.U[1] = (T *)g->U[1];
-  a.acc = (const T *)g->acc;
+  a.acc = (const T *)(g->sg_G > 0.0 ? g->sg_use : g->acc);
   a.ctrl = g->ctrl;
   a.part = g->part;
   a.flags = g->flags;
@@ -137,6 +137,11 @@ void free_tape(msh_grid *g) {
 msh_status launch_one_step(msh_grid *g, int ev_slot) {
   int nb = 0;
   cudaError_t e;
+  if (g->sg_G > 0.0) {  // the potential of U^n and the step's acceleration
+    e = launch_self_gravity(g, g->stream);
+    if (e == cudaSuccess) e = launch_self_gravity_mark(g, g->stream);
+    if (e != cudaSuccess) return fail(MSH_E_CUDA, "self-gravity: %s", cudaGetErrorString(e));
+  }
   if (g->profiling && ev_slot >= 0) CUDA_TRY(cudaEventRecord(g->ev[3 * ev_slot], g->stream));
   if (g->scheme == MSH_SCHEME_KT) {
     // the two Runge-Kutta stages of the central scheme, then the finalize (no fallback)
@@ -368,6 +373,7 @@ msh_status msh_destroy(msh_grid *g) {
   if (g->hist) cudaFree(g->hist);
   if (g->ctrl_aux) cudaFree(g->ctrl_aux);
   if (g->U1) cudaFree(g->U1);
+  free_self_gravity(g);
   free_tape(g);
   if (g->own_stream && g->stream) cudaStreamDestroy(g->stream);
   delete g;
@@ -401,6 +407,9 @@ msh_status msh_set_state(msh_grid *g, const void *U, int32_t where, int32_t kind
     return fail(MSH_E_REALIZABILITY, "state not realizable at cell %lld (rho <= 0 or P not SPD)", (long long)bad);
   }
   CUDA_TRY(cudaMemcpyAsync(g->U[cur], g->U[nxt], bytes, cudaMemcpyDeviceToDevice, g->stream));
+  // a new state has no previous self-gravity acceleration
+  g->hctrl->sg_hist = 0;
+  CUDA_TRY(cudaMemsetAsync(&g->ctrl->sg_hist, 0, sizeof(int32_t), g->stream));
   CUDA_TRY(cudaStreamSynchronize(g->stream));
   g->has_state = true;
   return MSH_OK;
@@ -443,6 +452,7 @@ msh_status msh_set_time(msh_grid *g, double t, int64_t step) {
   CUDA_TRY(cudaMemsetAsync(g->flags, 0, g->N * sizeof(int32_t), g->stream));
   g->hctrl->t = t;
   g->hctrl->step = step;
+  g->hctrl->sg_hist = 0;
   CUDA_TRY(cudaMemcpyAsync(g->ctrl, g->hctrl, sizeof(Ctrl), cudaMemcpyHostToDevice, g->stream));
   CUDA_TRY(cudaStreamSynchronize(g->stream));
   return MSH_OK;
@@ -494,6 +504,28 @@ msh_status msh_set_scheme(msh_grid *g, int32_t scheme) {
   if (scheme == MSH_SCHEME_KT && !g->U1) CUDA_TRY(cudaMalloc(&g->U1, g->N * 10 * g->esize));
   if (scheme != g->scheme) drop_graph(g);
   g->scheme = scheme;
+  return MSH_OK;
+}
+
+msh_status msh_set_self_gravity(msh_grid *g, double G) {
+  begin();
+  if (!g) return fail(MSH_E_INVALID_ARG, "null grid");
+  if (!(G >= 0.0) || !std::isfinite(G)) return fail(MSH_E_INVALID_ARG, "G must be finite and >= 0");
+  for (int i = 0; i < 2 * g->ndim; i++)
+    if (G > 0.0 && g->bc[i] != MSH_BC_PERIODIC)
+      return fail(MSH_E_INVALID_ARG, "self-gravity needs periodic boundaries on every active dimension");
+  if (G > 0.0 && g->tape_valid) return fail(MSH_E_STATE, "the adjoint tape covers external potentials only");
+  CUDA_TRY(cudaStreamSynchronize(g->stream));
+  drop_graph(g);
+  if (G == 0.0) {
+    free_self_gravity(g);
+    return MSH_OK;
+  }
+  msh_status st = setup_self_gravity(g, G);
+  if (st) return st;
+  g->hctrl->sg_hist = 0;
+  CUDA_TRY(cudaMemsetAsync(&g->ctrl->sg_hist, 0, sizeof(int32_t), g->stream));
+  CUDA_TRY(cudaStreamSynchronize(g->stream));
   return MSH_OK;
 }
 
@@ -642,6 +674,7 @@ msh_status msh_set_tape(msh_grid *g, int32_t K, int64_t max_steps) {
   if (K < 0 || (K > 0 && max_steps < 1)) return fail(MSH_E_INVALID_ARG, "need K >= 1 and max_steps >= 1 (K = 0 frees)");
   if (K > 0 && g->scheme != MSH_SCHEME_MUSCL_HANCOCK)
     return fail(MSH_E_STATE, "the adjoint covers the MUSCL-Hancock scheme only");
+  if (K > 0 && g->sg_G > 0.0) return fail(MSH_E_STATE, "the adjoint covers external potentials only");
   if (!g->has_state && K > 0) return fail(MSH_E_STATE, "msh_set_tape before msh_set_state");
   CUDA_TRY(cudaStreamSynchronize(g->stream));
   msh_status st = stop_tape(g);
@@ -827,6 +860,12 @@ msh_status msh_autotune(msh_grid *g, int32_t *rows_out, int32_t *zchunk_out) {
   g->tape_valid = false;
   *g->hctrl = trial_ctrl;
   msh_status st = MSH_OK;
+  // the trial steps overwrite the stored self-gravity acceleration: keep a copy
+  void *sg_save = nullptr;
+  if (g->sg_G > 0.0 && cudaMalloc(&sg_save, 3 * g->N * g->esize) == cudaSuccess)
+    cudaMemcpyAsync(sg_save, g->sg_prev, 3 * g->N * g->esize, cudaMemcpyDeviceToDevice, g->stream);
+  else if (g->sg_G > 0.0)
+    st = fail(MSH_E_NOMEM, "autotune: no room to keep the self-gravity history");
   if (cudaMemcpyAsync(g->ctrl, g->hctrl, sizeof(Ctrl), cudaMemcpyHostToDevice, g->stream) != cudaSuccess)
     st = fail(MSH_E_CUDA, "autotune setup: %s", cudaGetErrorString(cudaGetLastError()));
   cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -874,6 +913,11 @@ msh_status msh_autotune(msh_grid *g, int32_t *rows_out, int32_t *zchunk_out) {
   g->profiling = prof;
   *g->hctrl = saved_ctrl;
   g->tape_valid = tape_was_valid;
+  if (sg_save) {
+    cudaMemcpyAsync(g->sg_prev, sg_save, 3 * g->N * g->esize, cudaMemcpyDeviceToDevice, g->stream);
+    cudaStreamSynchronize(g->stream);
+    cudaFree(sg_save);
+  }
   if (cudaMemcpyAsync(g->ctrl, g->hctrl, sizeof(Ctrl), cudaMemcpyHostToDevice, g->stream) != cudaSuccess && st == MSH_OK)
     st = fail(MSH_E_CUDA, "autotune restore: %s", cudaGetErrorString(cudaGetLastError()));
   drop_graph(g);

@@ -28,7 +28,7 @@ struct Ctrl {
   int32_t *tape_had;
   int64_t tape_base, tape_len;
   int32_t last_tagged;  // cells the a-posteriori fallback tagged in the last step
-  int32_t pad2;
+  int32_t sg_hist;      // self-gravity: the previous step's acceleration is stored
 };
 
 // Per-thread-block partial reductions written by the step and scan kernels.
@@ -136,6 +136,13 @@ struct msh_grid {
   bool dt_stale = false;
   int scheme = MSH_SCHEME_MUSCL_HANCOCK;
   void *U1 = nullptr;  // first Runge-Kutta stage of the central scheme
+  // periodic self-gravity (msh_set_self_gravity): G > 0 when on, cuFFT plans, the FFT
+  // input / spectrum / potential, the previous and the used acceleration [3][N], and a
+  // device copy of the two state-buffer pointers
+  double sg_G = 0.0;
+  int sg_plan_fwd = 0, sg_plan_inv = 0;
+  void *sg_rho = nullptr, *sg_hat = nullptr, *sg_phi = nullptr, *sg_prev = nullptr, *sg_use = nullptr;
+  void **sg_bufs = nullptr;
   msh::Ctrl *ctrl_aux = nullptr;
   bool has_state = false;
   int rows = 8, zchunk = 32;
@@ -147,3 +154,12 @@ struct msh_grid {
   double prof_fin_ms = 0.0;  // summed time from the step kernel's end to the finalize kernel's end
   int64_t prof_launches = 0;
 };
+
+namespace msh {
+// self-gravity (msh_selfgrav.cu): the per-step potential and acceleration, the history
+// flag, plans and buffers
+cudaError_t launch_self_gravity(msh_grid *g, cudaStream_t s);
+cudaError_t launch_self_gravity_mark(msh_grid *g, cudaStream_t s);
+msh_status setup_self_gravity(msh_grid *g, double G);
+void free_self_gravity(msh_grid *g);
+}  // namespace msh

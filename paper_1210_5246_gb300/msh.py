@@ -63,6 +63,7 @@ SIGNATURES = {
     "msh_adjoint_run": [_vp, _vp, _i64, _P(_dbl), _i32, _vp, _vp, _i32, _i32],
     "msh_set_tape": [_vp, _i32, _i64],
     "msh_set_scheme": [_vp, _i32],
+    "msh_set_self_gravity": [_vp, _dbl],
     "msh_set_cell_width": [_vp, _P(_dbl)],
     "msh_get_slab": [_vp, _i64, _i64, _vp, _i32],
     "msh_set_slab": [_vp, _i64, _i64, _vp, _i32],
@@ -310,6 +311,10 @@ class Grid:
         po, wo, ko = self._buf(out)
         _check(load().msh_adjoint_run(self.h, p0, len(dts), _ptr_dbl(dts), int(K), pg, po, w0, kind))
         return out
+
+    def set_self_gravity(self, G):
+        """Periodic self-gravity with constant G (0: off); see ``msh_set_self_gravity``."""
+        _check(load().msh_set_self_gravity(self.h, float(G)))
 
     def set_scheme(self, scheme):
         """MUSCL_HANCOCK (default) or KT (see ``msh_set_scheme``)."""
