@@ -142,6 +142,7 @@ struct msh_grid {
   double sg_G = 0.0;
   int sg_plan_fwd = 0, sg_plan_inv = 0;
   void *sg_rho = nullptr, *sg_hat = nullptr, *sg_phi = nullptr, *sg_prev = nullptr, *sg_use = nullptr;
+  void *sg_eig = nullptr;  // per-axis Laplacian eigenvalues in the state precision
   void **sg_bufs = nullptr;
   msh::Ctrl *ctrl_aux = nullptr;
   bool has_state = false;

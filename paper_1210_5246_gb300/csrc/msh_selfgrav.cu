@@ -14,6 +14,7 @@
 
 #include <cmath>
 #include <cstdio>
+#include <vector>
 
 #include "../../include/msh.h"
 #include "msh_internal.h"
@@ -44,27 +45,19 @@ __global__ void sg_density_kernel(const Ctrl *ctrl, T *const *U, T *rho, size_t 
     rho[c] = src[c];
 }
 
-// Phi_k = -4 pi G rho_k / k_eff^2 / N on the half spectrum [nz][ny][nx/2+1]
+// Phi_k = -4 pi G rho_k / k_eff^2 / N on the half spectrum [nz][ny][nx/2+1]; eig holds the
+// per-axis Laplacian eigenvalues (2 sin(pi k / n) / dx)^2, x then y then z (built on the
+// host once), c = -4 pi G / N.
 template <typename T, typename C>
-__global__ void sg_scale_kernel(const Ctrl *ctrl, C *hat, int ndim, int nx, int ny, int nz, double dx0, double dx1,
-                                double dx2, double G) {
+__global__ void sg_scale_kernel(const Ctrl *ctrl, C *hat, const T *__restrict__ eig, int nx, int ny, int nz, T c) {
   if (ctrl->done) return;
   const int hx = nx / 2 + 1;
   const size_t M = (size_t)hx * ny * nz;
-  const double N = (double)nx * ny * nz;
+  const T *ex = eig, *ey = eig + hx, *ez = eig + hx + ny;
   for (size_t m = (size_t)blockIdx.x * blockDim.x + threadIdx.x; m < M; m += (size_t)gridDim.x * blockDim.x) {
     const int kx = (int)(m % hx), ky = (int)((m / hx) % ny), kz = (int)(m / ((size_t)hx * ny));
-    const double sx = 2.0 * sin(M_PI * kx / nx) / dx0;
-    double k2 = sx * sx;
-    if (ndim > 1) {
-      const double sy = 2.0 * sin(M_PI * ky / ny) / dx1;
-      k2 += sy * sy;
-    }
-    if (ndim > 2) {
-      const double sz = 2.0 * sin(M_PI * kz / nz) / dx2;
-      k2 += sz * sz;
-    }
-    const T f = (T)(k2 > 0.0 ? -4.0 * M_PI * G / (k2 * N) : 0.0);
+    const T k2 = ex[kx] + ey[ky] + ez[kz];
+    const T f = k2 > T(0) ? c / k2 : T(0);
     hat[m].x *= f;
     hat[m].y *= f;
   }
@@ -122,8 +115,8 @@ template <typename T> cudaError_t sg_launch_impl(msh_grid *g, cudaStream_t s) {
   if (Fft<T>::fwd((cufftHandle)g->sg_plan_fwd, (T *)g->sg_rho, (C *)g->sg_hat) != CUFFT_SUCCESS)
     return cudaErrorUnknown;
   const size_t M = (size_t)(nx / 2 + 1) * ny * nz;
-  sg_scale_kernel<T, C><<<sg_blocks(M), 256, 0, s>>>(g->ctrl, (C *)g->sg_hat, g->ndim, nx, ny, nz, g->dx[0], g->dx[1],
-                                                     g->dx[2], g->sg_G);
+  const T c = (T)(-4.0 * M_PI * g->sg_G / ((double)nx * ny * nz));
+  sg_scale_kernel<T, C><<<sg_blocks(M), 256, 0, s>>>(g->ctrl, (C *)g->sg_hat, (const T *)g->sg_eig, nx, ny, nz, c);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   if (Fft<T>::inv((cufftHandle)g->sg_plan_inv, (C *)g->sg_hat, (T *)g->sg_phi) != CUFFT_SUCCESS)
@@ -147,10 +140,10 @@ cudaError_t launch_self_gravity_mark(msh_grid *g, cudaStream_t s) {
 void free_self_gravity(msh_grid *g) {
   if (g->sg_plan_fwd) cufftDestroy((cufftHandle)g->sg_plan_fwd);
   if (g->sg_plan_inv) cufftDestroy((cufftHandle)g->sg_plan_inv);
-  for (void *p : {g->sg_rho, g->sg_hat, g->sg_phi, g->sg_prev, g->sg_use, (void *)g->sg_bufs})
+  for (void *p : {g->sg_rho, g->sg_hat, g->sg_phi, g->sg_prev, g->sg_use, g->sg_eig, (void *)g->sg_bufs})
     if (p) cudaFree(p);
   g->sg_plan_fwd = g->sg_plan_inv = 0;
-  g->sg_rho = g->sg_hat = g->sg_phi = g->sg_prev = g->sg_use = nullptr;
+  g->sg_rho = g->sg_hat = g->sg_phi = g->sg_prev = g->sg_use = g->sg_eig = nullptr;
   g->sg_bufs = nullptr;
   g->sg_G = 0.0;
 }
@@ -192,6 +185,30 @@ msh_status setup_self_gravity(msh_grid *g, double G) {
   if (e == cudaSuccess) e = cudaMalloc(&g->sg_bufs, 2 * sizeof(void *));
   if (e == cudaSuccess) e = cudaMemcpy(g->sg_bufs, g->U, 2 * sizeof(void *), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemset(g->sg_prev, 0, 3 * N * es);
+  // per-axis eigenvalues of the 3-point Laplacian, (2 sin(pi k / n) / dx)^2 (0 on inactive
+  // axes), x for k = 0 .. nx/2 (the half spectrum), then y, then z
+  if (e == cudaSuccess) {
+    const int hx = nx / 2 + 1;
+    std::vector<double> eig((size_t)hx + ny + nz, 0.0);
+    auto fill = [&](double *out, int count, int n, int d) {
+      for (int k = 0; k < count; k++) {
+        const double sv = d < g->ndim ? 2.0 * std::sin(M_PI * k / n) / g->dx[d] : 0.0;
+        out[k] = sv * sv;
+      }
+    };
+    fill(eig.data(), hx, nx, 0);
+    fill(eig.data() + hx, ny, ny, 1);
+    fill(eig.data() + hx + ny, nz, nz, 2);
+    e = cudaMalloc(&g->sg_eig, eig.size() * es);
+    if (e == cudaSuccess) {
+      if (f32) {
+        std::vector<float> ef(eig.begin(), eig.end());
+        e = cudaMemcpy(g->sg_eig, ef.data(), ef.size() * sizeof(float), cudaMemcpyHostToDevice);
+      } else {
+        e = cudaMemcpy(g->sg_eig, eig.data(), eig.size() * sizeof(double), cudaMemcpyHostToDevice);
+      }
+    }
+  }
   if (e != cudaSuccess) {
     free_self_gravity(g);
     set_error_text(cudaGetErrorString(e));
