@@ -65,7 +65,7 @@ typedef struct {
 } og_grid;
 
 enum { OG_PERIODIC = 0, OG_OUTFLOW = 1, OG_REFLECT = 2 };
-enum { OG_SCHEME_MH = 0, OG_SCHEME_KT = 1 };
+enum { OG_SCHEME_MH = 0, OG_SCHEME_KT = 1, OG_SCHEME_MH_ROE = 2 };
 
 /* index of the symmetric tensor component (i,j) inside the 10-vector */
 static int tens_idx(int i, int j)
@@ -311,6 +311,61 @@ void og_hll(const double *WL, const double *WR, int d, double *F)
     }
 }
 
+/* ------------------------------------------------------ Roe-type flux ---- */
+/* Linearised characteristic upwind flux (Roe 1981) through a face normal to d:
+ *   F = (f(WL) + f(WR)) / 2 - (1/2) (dU/dW)(Wm) R(Wm) |Lambda(Wm)| L(Wm) (WR - WL),
+ * with the eigen-system of the local frame (og_left_x, og_right_x, og_eigenvalues_x).
+ * Readings (no Roe average is known for the ten-moment system): Wm = (WL + WR) / 2, the
+ * primitive jump in place of (dW/dU)(UR - UL), and Harten's entropy fix on the two fast
+ * (genuinely nonlinear) waves: |lambda| -> (lambda^2 + delta^2) / (2 delta) where
+ * |lambda| < delta = 0.1 cf(Wm).  The shear and contact waves are linearly degenerate and
+ * keep |lambda|, so a stationary contact gets no dissipation.                           */
+void og_roe(const double *WL, const double *WR, int d, double *F)
+{
+    const int *p = perm[d];
+    double wm[NV], dw[NV];
+    for (int k = 0; k < NV; k++) {
+        wm[k] = 0.5 * (WL[p[k]] + WR[p[k]]);
+        dw[k] = WR[p[k]] - WL[p[k]];
+    }
+    double L[NV][NV], R[NV][NV], lam[NV], a[NV], dd[NV];
+    og_left_x(wm, L);
+    og_right_x(wm, R);
+    og_eigenvalues_x(wm, lam);
+    matvec(L, dw, a);
+    double delta = 0.1 * sqrt(3.0 * wm[4] / wm[0]);
+    for (int k = 0; k < NV; k++) {
+        double al = fabs(lam[k]);
+        if ((k == 0 || k == NV - 1) && al < delta) al = (lam[k] * lam[k] + delta * delta) / (2.0 * delta);
+        a[k] *= al;
+    }
+    matvec(R, a, dd);
+    /* back to the global order, then through the Jacobian of prim_to_cons at Wm */
+    double Wg[NV], Dg[NV];
+    for (int k = 0; k < NV; k++) {
+        Wg[p[k]] = wm[k];
+        Dg[p[k]] = dd[k];
+    }
+    double dU[NV];
+    dU[0] = Dg[0];
+    for (int i = 0; i < 3; i++) dU[1 + i] = Wg[0] * Dg[1 + i] + Wg[1 + i] * Dg[0];
+    for (int i = 0; i < 3; i++)
+        for (int j = i; j < 3; j++)
+            dU[tens_idx(i, j)] = Dg[tens_idx(i, j)] + Dg[0] * Wg[1 + i] * Wg[1 + j] +
+                                 Wg[0] * (Dg[1 + i] * Wg[1 + j] + Wg[1 + i] * Dg[1 + j]);
+    double FL[NV], FR[NV];
+    og_flux(WL, d, FL);
+    og_flux(WR, d, FR);
+    for (int k = 0; k < NV; k++) F[k] = 0.5 * (FL[k] + FR[k]) - 0.5 * dU[k];
+}
+
+/* face flux of the characteristic scheme: HLL (the hot path) or the Roe-type flux */
+static void face_flux(const og_grid *Gr, const double *WL, const double *WR, int d, double *F)
+{
+    if (Gr->scheme == OG_SCHEME_MH_ROE) og_roe(WL, WR, d, F);
+    else og_hll(WL, WR, d, F);
+}
+
 /* ---------------------------------------------------------------- a1 ----- */
 /* Padded array layout: [NV][pz][py][px] with 2 ghost layers on active dims. */
 typedef struct {
@@ -498,9 +553,9 @@ static int step_pass(const og_grid *Gr, const double *U, const double *phi, doub
                 }
                 /* faces i-1/2 for i = 0 .. nd, flux difference into dU */
                 double Fm[NV], Fp[NV];
-                og_hll(hi + NV * 0, lo + NV * 1, d, Fm);               /* face -1/2 */
+                face_flux(Gr, hi + NV * 0, lo + NV * 1, d, Fm);        /* face -1/2 */
                 for (int64_t i = 0; i < nd; i++) {
-                    og_hll(hi + NV * (i + 1), lo + NV * (i + 2), d, Fp); /* face i+1/2 */
+                    face_flux(Gr, hi + NV * (i + 1), lo + NV * (i + 2), d, Fp); /* face i+1/2 */
                     int64_t c3[3];
                     c3[d] = i; c3[a1] = j1; c3[a2] = j2;
                     int64_t c = (c3[2] * P.n[1] + c3[1]) * P.n[0] + c3[0];

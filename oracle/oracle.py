@@ -21,7 +21,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "liboracle.so")
 
 PERIODIC, OUTFLOW, REFLECT = 0, 1, 2
-SCHEME_MH, SCHEME_KT = 0, 1
+SCHEME_MH, SCHEME_KT, SCHEME_MH_ROE = 0, 1, 2
 NV = 10
 
 _lock = threading.Lock()
@@ -68,6 +68,7 @@ def _load():
             lib.og_flux.argtypes = [dp, C.c_int, dp]
             lib.og_hll.argtypes = [dp, dp, C.c_int, dp]
             lib.og_kt_flux.argtypes = [dp, dp, C.c_int, dp]
+            lib.og_roe.argtypes = [dp, dp, C.c_int, dp]
             lib.og_kt_reconstruct.argtypes = [dp, dp, dp, C.c_int, dp, dp]
             lib.og_reconstruct.argtypes = [dp, dp, dp, C.c_int, C.c_double, dp, dp]
             for f in ("og_jacobian_x", "og_right_x", "og_left_x"):
@@ -94,8 +95,8 @@ class Grid:
     ``bc[d] = (lower, upper)`` (PERIODIC / OUTFLOW / REFLECT), CFL number ``cfl``."""
 
     def __init__(self, n, lo, hi, bc, cfl, scheme=0):
-        """scheme: SCHEME_MH (MUSCL-Hancock + HLL, Sec. 3.3) or SCHEME_KT (Kurganov-Tadmor
-        + RK2, Sec. 3.2)."""
+        """scheme: SCHEME_MH (MUSCL-Hancock + HLL, Sec. 3.3), SCHEME_KT (Kurganov-Tadmor
+        + RK2, Sec. 3.2) or SCHEME_MH_ROE (MUSCL-Hancock with the Roe-type flux)."""
         n = list(n)
         self.ndim = len(n)
         self.n = tuple(n) + (1,) * (3 - len(n))
@@ -229,6 +230,13 @@ def flux(W, d):
 def hll(WL, WR, d):
     F = np.empty(NV)
     _load().og_hll(_p(_f64(WL)), _p(_f64(WR)), int(d), _p(F))
+    return F
+
+
+def roe_flux(WL, WR, d):
+    """Roe-type flux between the face states WL and WR (primitive, global order)."""
+    F = np.zeros(NV)
+    _load().og_roe(_p(_f64(WL)), _p(_f64(WR)), int(d), _p(F))
     return F
 
 

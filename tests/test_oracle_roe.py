@@ -1,0 +1,108 @@
+"""Pins of the oracle's Roe-type flux (the characteristic scheme with a linearised upwind
+flux): consistency F(W, W) = f(W); upwinding (a supersonic state gets the upwind flux
+exactly); a stationary contact is kept exactly (the contact waves have speed 0 and are not
+entropy-fixed) while HLL smears it; the moving contact of the gamma = 3 Sod problem is
+sharper than HLL's; convergence to the exact Sod solution; conservation of every total."""
+import numpy as np
+
+from oracle import exact_riemann
+
+ROE, HLL = 2, 0
+
+
+def _rand_states(rng, m):
+    W = np.zeros((m, 10))
+    W[:, 0] = np.exp(rng.uniform(-1, 1, m))
+    W[:, 1:4] = rng.uniform(-1, 1, (m, 3))
+    for i in range(m):
+        A = np.tril(rng.normal(0, 0.3, (3, 3)))
+        A[np.diag_indices(3)] = rng.uniform(0.3, 1.0, 3)
+        P = A @ A.T
+        W[i, 4:] = [P[0, 0], P[0, 1], P[0, 2], P[1, 1], P[1, 2], P[2, 2]]
+    return W
+
+
+def test_consistency(oracle):
+    for W in _rand_states(np.random.default_rng(1), 20):
+        for d in range(3):
+            np.testing.assert_allclose(oracle.roe_flux(W, W, d), oracle.flux(W, d), rtol=0, atol=1e-15)
+
+
+def test_supersonic_upwinding(oracle):
+    """With every wave speed of the mean state positive (negative), the flux is the left
+    (right) physical flux exactly in linear problems; for close states to O(jump^2)."""
+    rng = np.random.default_rng(2)
+    for W in _rand_states(rng, 8):
+        W = W.copy()
+        W[1] = 3.0 + 3 * np.sqrt(3 * W[4] / W[0])  # u > cf: all waves to the right
+        V = W * (1 + 1e-4 * rng.normal(size=10))
+        F = oracle.roe_flux(W, V, 0)
+        assert np.abs(F - oracle.flux(W, 0)).max() <= 1e-6 * np.abs(oracle.flux(W, 0)).max()
+        W2, V2 = W.copy(), V.copy()
+        W2[1], V2[1] = -W[1], -V[1]
+        F2 = oracle.roe_flux(W2, V2, 0)
+        assert np.abs(F2 - oracle.flux(V2, 0)).max() <= 1e-6 * np.abs(oracle.flux(V2, 0)).max()
+
+
+def _contact(oracle, scheme, n=64, steps=40, u=0.0):
+    W = np.zeros((10, 1, 1, n))
+    x = (np.arange(n) + 0.5) / n
+    W[0, 0, 0] = np.where(np.abs(x - 0.5) < 0.25, 2.0, 0.5)
+    W[1] = u
+    W[4] = W[7] = W[9] = 1.0
+    W[5] = 0.1
+    g = oracle.Grid((n,), (0.0,), (1.0,), ((0, 0),), 0.5, scheme=scheme)
+    U, ns, _, rc, _ = oracle.run(g, oracle.prim_to_cons(W), np.inf, max_steps=steps)
+    assert rc == 0 and ns == steps
+    return oracle.cons_to_prim(U)[0, 0, 0], W[0, 0, 0]
+
+
+def test_stationary_contact_is_exact(oracle):
+    rho, rho0 = _contact(oracle, ROE)
+    np.testing.assert_allclose(rho, rho0, rtol=1e-13)
+    rho_h, _ = _contact(oracle, HLL)
+    assert np.abs(rho_h - rho0).max() > 0.1  # HLL diffuses the same contact
+
+
+def _sod(oracle, n, scheme):
+    from paper_1210_5246_gb300 import inputs
+    p = inputs.sod(n)
+    g = oracle.Grid(p.n, p.lo, p.hi, p.bc, p.cfl, scheme=scheme)
+    U, _, t, rc, _ = oracle.run(g, oracle.prim_to_cons(p.W), p.t_end)
+    assert rc == 0 and t == p.t_end
+    return oracle.cons_to_prim(U).reshape(10, -1), (np.arange(n) + 0.5) / n
+
+
+def _contact_width(W, x):
+    rl, rr = 0.6486437, 0.1707036
+    m = (x > 0.45) & (x < 0.85)
+    r = W[0][m]
+    lo, hi = rr + 0.1 * (rl - rr), rr + 0.9 * (rl - rr)
+    return int(np.sum((r > lo) & (r < hi)))
+
+
+def test_sod_contact_sharper_than_hll(oracle):
+    Wr, x = _sod(oracle, 256, ROE)
+    Wh, _ = _sod(oracle, 256, HLL)
+    assert _contact_width(Wr, x) < _contact_width(Wh, x), (_contact_width(Wr, x), _contact_width(Wh, x))
+
+
+def test_sod_converges_to_exact_gamma3(oracle):
+    errs = []
+    for n in (128, 256, 512):
+        W, x = _sod(oracle, n, ROE)
+        rho, _, _, _ = exact_riemann.sample((x - 0.5) / 0.2, 1.0, 0.0, 1.0, 0.125, 0.0, 0.1, gamma=3.0)
+        errs.append(np.abs(W[0] - rho).mean())
+    assert errs[0] > errs[1] > errs[2] and errs[2] < 5e-3, errs
+
+
+def test_conservation_periodic(oracle):
+    from paper_1210_5246_gb300 import inputs
+    p = inputs.turb(n=12)
+    g = oracle.Grid(p.n, p.lo, p.hi, p.bc, p.cfl, scheme=ROE)
+    U0 = oracle.prim_to_cons(p.W)
+    U, ns, _, rc, _ = oracle.run(g, U0, np.inf, max_steps=5)
+    assert rc == 0 and ns == 5
+    t0, t1 = oracle.diagnostics(g, U0)[0], oracle.diagnostics(g, U)[0]
+    scale = np.array([t0[0]] * 4 + [abs(t0[4]) + abs(t0[7]) + abs(t0[9])] * 6)
+    assert np.all(np.abs(t1 - t0) / scale < 1e-13)
