@@ -56,8 +56,9 @@ typedef int32_t msh_status;
 #define MSH_FP32 0
 #define MSH_FP64 1
 
-#define MSH_SCHEME_MUSCL_HANCOCK 0 /* characteristic MUSCL-Hancock + HLL (Sec. 3.3)     */
-#define MSH_SCHEME_KT 1            /* Kurganov-Tadmor central scheme + RK2 (Sec. 3.2)   */
+#define MSH_SCHEME_MUSCL_HANCOCK 0     /* characteristic MUSCL-Hancock + HLL (Sec. 3.3)     */
+#define MSH_SCHEME_KT 1                /* Kurganov-Tadmor central scheme + RK2 (Sec. 3.2)   */
+#define MSH_SCHEME_MUSCL_HANCOCK_ROE 2 /* characteristic MUSCL-Hancock + Roe-type flux     */
 
 #define MSH_HOST 0
 #define MSH_DEVICE 1
@@ -225,8 +226,12 @@ msh_status msh_adjoint_tape(msh_grid *g, const void *dL_dUN, void *dL_dU0, int32
  * face value has rho <= 0 or P_nn <= 0), Heun's second-order Runge-Kutta stages
  * (u1 = u + dt L(u), u_new = (u + u1 + dt L(u1)) / 2), the gravity source after them and
  * the same CFL rule; it has no a-posteriori fallback.  Selecting it allocates one more
- * state buffer.  The adjoint (msh_adjoint_run, msh_set_tape) covers MUSCL-Hancock only:
- * MSH_E_STATE otherwise.
+ * state buffer.  MSH_SCHEME_MUSCL_HANCOCK_ROE is the characteristic step of Sec. 3.3 with
+ * a Roe-type flux (Roe 1981) in place of HLL:
+ *   F = (f(wl) + f(wr)) / 2 - (dU/dW)(wm) R |Lambda| L (wr - wl) / 2,  wm = (wl + wr) / 2,
+ * the closed-form eigen-system of wm and Harten's entropy fix on the two fast waves
+ * (delta = cf / 10); the a-posteriori fallback as for HLL.  The adjoint (msh_adjoint_run,
+ * msh_set_tape) covers MUSCL-Hancock with HLL only: MSH_E_STATE otherwise.
  */
 msh_status msh_set_scheme(msh_grid *g, int32_t scheme);
 

@@ -359,10 +359,14 @@ void og_roe(const double *WL, const double *WR, int d, double *F)
     for (int k = 0; k < NV; k++) F[k] = 0.5 * (FL[k] + FR[k]) - 0.5 * dU[k];
 }
 
-/* face flux of the characteristic scheme: HLL (the hot path) or the Roe-type flux */
-static void face_flux(const og_grid *Gr, const double *WL, const double *WR, int d, double *F)
+/* Face flux of the characteristic scheme: HLL (the hot path) or the Roe-type flux.  A
+ * face with first-order states in a fallback pass (first != 0) takes HLL in both: the
+ * fallback has to make the update realizable, and a linearised Roe flux is not positively
+ * conservative (Einfeldt, Munz, Roe & Sjogreen 1991) where HLL with bounding wave speeds
+ * is. */
+static void face_flux(const og_grid *Gr, const double *WL, const double *WR, int d, int first, double *F)
 {
-    if (Gr->scheme == OG_SCHEME_MH_ROE) og_roe(WL, WR, d, F);
+    if (Gr->scheme == OG_SCHEME_MH_ROE && !first) og_roe(WL, WR, d, F);
     else og_hll(WL, WR, d, F);
 }
 
@@ -526,6 +530,7 @@ static int step_pass(const og_grid *Gr, const double *U, const double *phi, doub
                 /* pencil along d; face states of cells -1 .. nd */
                 double *lo = (double *)malloc(sizeof(double) * NV * (nd + 2));
                 double *hi = (double *)malloc(sizeof(double) * NV * (nd + 2));
+                unsigned char *first = (unsigned char *)calloc((size_t)(nd + 1), 1); /* face i-1/2 at i */
                 for (int64_t i = -1; i <= nd; i++) {
                     double Wc[3][NV];
                     for (int o = -1; o <= 1; o++) {
@@ -545,6 +550,7 @@ static int step_pass(const og_grid *Gr, const double *U, const double *phi, doub
                         cb[d] = i + 1; cb[a1] = j1; cb[a2] = j2;
                         int64_t pa = pidx(&P, ca[0], ca[1], ca[2]), pb = pidx(&P, cb[0], cb[1], cb[2]);
                         if (!(flag[pa] || flag[pb])) continue;
+                        first[i + 1] = 1;
                         for (int k = 0; k < NV; k++) {
                             hi[NV * (i + 1) + k] = Wp[k * NP + pa];
                             lo[NV * (i + 2) + k] = Wp[k * NP + pb];
@@ -553,9 +559,9 @@ static int step_pass(const og_grid *Gr, const double *U, const double *phi, doub
                 }
                 /* faces i-1/2 for i = 0 .. nd, flux difference into dU */
                 double Fm[NV], Fp[NV];
-                face_flux(Gr, hi + NV * 0, lo + NV * 1, d, Fm);        /* face -1/2 */
+                face_flux(Gr, hi + NV * 0, lo + NV * 1, d, first[0], Fm);        /* face -1/2 */
                 for (int64_t i = 0; i < nd; i++) {
-                    face_flux(Gr, hi + NV * (i + 1), lo + NV * (i + 2), d, Fp); /* face i+1/2 */
+                    face_flux(Gr, hi + NV * (i + 1), lo + NV * (i + 2), d, first[i + 1], Fp); /* face i+1/2 */
                     int64_t c3[3];
                     c3[d] = i; c3[a1] = j1; c3[a2] = j2;
                     int64_t c = (c3[2] * P.n[1] + c3[1]) * P.n[0] + c3[0];
@@ -564,6 +570,7 @@ static int step_pass(const og_grid *Gr, const double *U, const double *phi, doub
                 }
                 free(lo);
                 free(hi);
+                free(first);
             }
     }
 #pragma omp parallel for
@@ -703,6 +710,7 @@ static int kt_rhs(const og_grid *Gr, const double *U, double *dU)
             for (int64_t j1 = 0; j1 < n1; j1++) {
                 double *lo = (double *)malloc(sizeof(double) * NV * (nd + 2));
                 double *hi = (double *)malloc(sizeof(double) * NV * (nd + 2));
+                unsigned char *first = (unsigned char *)calloc((size_t)(nd + 1), 1); /* face i-1/2 at i */
                 for (int64_t i = -1; i <= nd; i++) {
                     double Wc[3][NV];
                     for (int o = -1; o <= 1; o++) {

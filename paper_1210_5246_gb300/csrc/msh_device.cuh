@@ -312,19 +312,88 @@ __device__ __forceinline__ void kt_flux(const T (&wl)[NV], const T (&wr)[NV], T 
   for (int k = 0; k < NV; k++) F[k] = T(0.5) * (Fr[k] + Fl[k]) - h * (Ur[k] - Ul[k]);
 }
 
+// ------------------------------------------------------------ Roe-type flux
+// Linearised characteristic upwind flux (local frame):
+//   F = (f(wl) + f(wr)) / 2 - (dU/dW)(wm) R |Lambda| L (wr - wl) / 2,
+// with wm = (wl + wr) / 2 (no Roe average is known for the ten-moment system), the
+// closed-form eigen-system of wm, and Harten's entropy fix on the two fast waves only:
+// |lambda| -> (lambda^2 + delta^2) / (2 delta) below delta = cf / 10.  The shear and contact
+// waves are linearly degenerate and keep |lambda|, so a stationary contact is not diffused.
+template <typename T>
+__device__ __forceinline__ void roe_flux(const T (&wl)[NV], const T (&wr)[NV], T (&F)[NV]) {
+  T wm[NV], dw[NV];
+#pragma unroll
+  for (int k = 0; k < NV; k++) {
+    wm[k] = T(0.5) * (wl[k] + wr[k]);
+    dw[k] = wr[k] - wl[k];
+  }
+  Eig<T> E;
+  E.init(wm);
+  T c[NV];
+  E.project(dw, c);
+  const T u = E.u, delta = T(0.1) * E.cf;
+  auto fast = [&](T l) {
+    const T al = fabs(l);
+    return al < delta ? (l * l + delta * delta) * (T(0.5) * frcp(delta)) : al;
+  };
+  const T am = fabs(u - E.cs), ap = fabs(u + E.cs), a0 = fabs(u);
+  c[0] *= fast(u - E.cf);
+  c[9] *= fast(u + E.cf);
+  c[1] *= am; c[2] *= am;
+  c[7] *= ap; c[8] *= ap;
+  c[3] *= a0; c[4] *= a0; c[5] *= a0; c[6] *= a0;
+  T d[NV];
+  E.back(c, d);  // primitive dissipation R |Lambda| L dw
+  const T r = wm[0], ux = wm[1], uy = wm[2], uz = wm[3];
+  T dU[NV];      // through the Jacobian of the conserved map at wm
+  dU[0] = d[0];
+  dU[1] = r * d[1] + ux * d[0];
+  dU[2] = r * d[2] + uy * d[0];
+  dU[3] = r * d[3] + uz * d[0];
+  dU[4] = d[4] + d[0] * ux * ux + r * (T(2) * d[1] * ux);
+  dU[5] = d[5] + d[0] * ux * uy + r * (d[1] * uy + ux * d[2]);
+  dU[6] = d[6] + d[0] * ux * uz + r * (d[1] * uz + ux * d[3]);
+  dU[7] = d[7] + d[0] * uy * uy + r * (T(2) * d[2] * uy);
+  dU[8] = d[8] + d[0] * uy * uz + r * (d[2] * uz + uy * d[3]);
+  dU[9] = d[9] + d[0] * uz * uz + r * (T(2) * d[3] * uz);
+  T Ul[NV], Fl[NV], Ur[NV], Fr[NV];
+  phys(wl, Ul, Fl);
+  phys(wr, Ur, Fr);
+#pragma unroll
+  for (int k = 0; k < NV; k++) F[k] = T(0.5) * (Fl[k] + Fr[k]) - T(0.5) * dU[k];
+}
+
 // Scheme of a step kernel: 0 the characteristic MUSCL-Hancock step with HLL (Sec. 3.3);
-// 1 and 2 the two Runge-Kutta stages of the Kurganov-Tadmor scheme (Sec. 3.2).
+// 1 and 2 the two Runge-Kutta stages of the Kurganov-Tadmor scheme (Sec. 3.2); 3 the
+// characteristic step with the Roe-type flux.  0 and 3 have the a-posteriori fallback.
+template <int SCH> constexpr bool kCharacteristic = SCH == 0 || SCH == 3;
+
 template <int SCH, typename T>
 __device__ __forceinline__ void recon(const T (&wm)[NV], const T (&w0)[NV], const T (&wp)[NV], T nu, T (&lo)[NV],
                                       T (&hi)[NV]) {
-  if constexpr (SCH == 0) reconstruct(wm, w0, wp, nu, lo, hi);
+  if constexpr (kCharacteristic<SCH>) reconstruct(wm, w0, wp, nu, lo, hi);
   else kt_reconstruct(wm, w0, wp, lo, hi);
 }
 
 template <int SCH, typename T>
 __device__ __forceinline__ void face_flux(const T (&wl)[NV], const T (&wr)[NV], T (&F)[NV]) {
   if constexpr (SCH == 0) hll(wl, wr, F);
+  else if constexpr (SCH == 3) roe_flux(wl, wr, F);
   else kt_flux(wl, wr, F);
+}
+
+// Flux through a face in a step pass: in a fallback pass (RETRY) a face with first-order
+// states (it touches a tagged cell) takes HLL under the Roe-type scheme too.  The fallback
+// has to make the update realizable; HLL with bounding wave speeds is positively
+// conservative, a linearised Roe flux is not (Einfeldt, Munz, Roe & Sjogreen 1991).
+template <int SCH, bool RETRY, typename T>
+__device__ __forceinline__ void face_flux(const T (&wl)[NV], const T (&wr)[NV], bool first, T (&F)[NV]) {
+  if constexpr (SCH == 3 && RETRY) {
+    if (first) hll(wl, wr, F);
+    else roe_flux(wl, wr, F);
+  } else {
+    face_flux<SCH>(wl, wr, F);
+  }
 }
 
 // ---------------------------------------------------------- accumulators

@@ -157,22 +157,25 @@ msh_status launch_one_step(msh_grid *g, int ev_slot) {
     if (g->profiling && ev_slot >= 0) CUDA_TRY(cudaEventRecord(g->ev[3 * ev_slot + 2], g->stream));
     return MSH_OK;
   }
-  if (g->prec == MSH_FP32) e = launch_step<float>(make_args<float>(g), g->ndim, g->rows, false, g->stream, &nb);
-  else e = launch_step<double>(make_args<double>(g), g->ndim, g->rows, false, g->stream, &nb);
-  if (e != cudaSuccess) return fail(MSH_E_CUDA, "step kernel launch: %s", cudaGetErrorString(e));
-  if (g->profiling && ev_slot >= 0) CUDA_TRY(cudaEventRecord(g->ev[3 * ev_slot + 1], g->stream));
-  // fallback passes: each returns at once unless the previous pass tagged new cells
-  for (int level = 1; level <= kFallbackPasses; level++) {
+  // the characteristic step (HLL or Roe-type flux), then its fallback passes: each returns at
+  // once unless the previous pass tagged new cells
+  const bool roe = g->scheme == MSH_SCHEME_MUSCL_HANCOCK_ROE;
+  for (int level = 0; level <= kFallbackPasses; level++) {
+    const bool retry = level > 0;
     if (g->prec == MSH_FP32) {
       StepArgs<float> a = make_args<float>(g);
       a.level = level;
-      e = launch_step<float>(a, g->ndim, g->rows, true, g->stream, nullptr);
+      e = roe ? launch_step_roe<float>(a, g->ndim, g->rows, retry, g->stream, retry ? nullptr : &nb)
+              : launch_step<float>(a, g->ndim, g->rows, retry, g->stream, retry ? nullptr : &nb);
     } else {
       StepArgs<double> a = make_args<double>(g);
       a.level = level;
-      e = launch_step<double>(a, g->ndim, g->rows, true, g->stream, nullptr);
+      e = roe ? launch_step_roe<double>(a, g->ndim, g->rows, retry, g->stream, retry ? nullptr : &nb)
+              : launch_step<double>(a, g->ndim, g->rows, retry, g->stream, retry ? nullptr : &nb);
     }
-    if (e != cudaSuccess) return fail(MSH_E_CUDA, "fallback kernel launch: %s", cudaGetErrorString(e));
+    if (e != cudaSuccess)
+      return fail(MSH_E_CUDA, "%s kernel launch: %s", retry ? "fallback" : "step", cudaGetErrorString(e));
+    if (level == 0 && g->profiling && ev_slot >= 0) CUDA_TRY(cudaEventRecord(g->ev[3 * ev_slot + 1], g->stream));
   }
   e = launch_finalize(g->ctrl, g->part, nb, 0, g->stream);
   if (e != cudaSuccess) return fail(MSH_E_CUDA, "finalize launch: %s", cudaGetErrorString(e));
@@ -497,9 +500,10 @@ msh_status msh_set_potential(msh_grid *g, const double *phi, int32_t where) {
 msh_status msh_set_scheme(msh_grid *g, int32_t scheme) {
   begin();
   if (!g) return fail(MSH_E_INVALID_ARG, "null grid");
-  if (scheme != MSH_SCHEME_MUSCL_HANCOCK && scheme != MSH_SCHEME_KT) return fail(MSH_E_INVALID_ARG, "unknown scheme");
-  if (scheme == MSH_SCHEME_KT && g->tape_valid)
-    return fail(MSH_E_STATE, "the adjoint tape covers the MUSCL-Hancock scheme only");
+  if (scheme != MSH_SCHEME_MUSCL_HANCOCK && scheme != MSH_SCHEME_KT && scheme != MSH_SCHEME_MUSCL_HANCOCK_ROE)
+    return fail(MSH_E_INVALID_ARG, "unknown scheme");
+  if (scheme != MSH_SCHEME_MUSCL_HANCOCK && g->tape_valid)
+    return fail(MSH_E_STATE, "the adjoint tape covers the MUSCL-Hancock scheme with HLL only");
   CUDA_TRY(cudaStreamSynchronize(g->stream));
   if (scheme == MSH_SCHEME_KT && !g->U1) CUDA_TRY(cudaMalloc(&g->U1, g->N * 10 * g->esize));
   if (scheme != g->scheme) drop_graph(g);

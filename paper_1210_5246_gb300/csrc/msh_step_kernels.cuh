@@ -137,7 +137,7 @@ __device__ __forceinline__ void finish_cell(const StepArgs<T> &a, const T *src, 
   cons_to_prim(Un, W);
   if (!realizable(W)) {
     bad = min(bad, (long long)c);
-    if (SCH != 0) goto done;  // the central scheme has no a-posteriori fallback
+    if (!kCharacteristic<SCH>) goto done;  // the central scheme has no a-posteriori fallback
     {
     // tag the cell for the next fallback pass (a cell tagged by an earlier pass keeps its tag)
     const int32_t f = a.flags[c];
@@ -217,7 +217,7 @@ __global__ void __launch_bounds__(kTile1D) step1d_kernel(StepArgs<T> a) {
     T hl[NV];
 #pragma unroll
     for (int k = 0; k < NV; k++) hl[k] = sH[k][t - 1];
-    face_flux<SCH>(hl, lo, F);
+    face_flux<SCH, RETRY>(hl, lo, RETRY && (sFl[t] | sFl[t + 1]), F);
   }
   __syncthreads();
   if (t >= 1) {
@@ -406,7 +406,7 @@ __global__ void __launch_bounds__(32 * BY, (BY <= 8 ? 2 : 1)) step_tile_kernel(S
   if (interior) {
     T lo[NV], hi[NV];
     recon_z(z0, lo, hi);
-    face_flux<SCH>(hprev, lo, Fprev);
+    face_flux<SCH, RETRY>(hprev, lo, fl(buf(z0 - 1), sy, sx) || fl(buf(z0), sy, sx), Fprev);
 #pragma unroll
     for (int k = 0; k < NV; k++) hprev[k] = hi[k];
   }
@@ -430,7 +430,7 @@ __global__ void __launch_bounds__(32 * BY, (BY <= 8 ? 2 : 1)) step_tile_kernel(S
       if (RETRY) first_order_faces(fl(buf(z), sy, sx - 1), fl(buf(z), sy, sx), fl(buf(z), sy, sx + 1), w0, lo, hi);
 #pragma unroll
       for (int k = 0; k < NV; k++) hl[k] = __shfl_up_sync(FULL, hi[k], 1);
-      face_flux<SCH>(hl, lo, F);  // flux through the lower x face of this cell
+      face_flux<SCH, RETRY>(hl, lo, fl(buf(z), sy, sx - 1) || fl(buf(z), sy, sx), F);  // lower x face
 #pragma unroll
       for (int k = 0; k < NV; k++) acc[k] += (F[k] - __shfl_down_sync(FULL, F[k], 1)) * idx;
     }
@@ -454,14 +454,14 @@ __global__ void __launch_bounds__(32 * BY, (BY <= 8 ? 2 : 1)) step_tile_kernel(S
       T hl[NV];
 #pragma unroll
       for (int k = 0; k < NV; k++) hl[k] = sXh[(k * BY + ty - 1) * 32 + tx];
-      face_flux<SCH>(hl, ylo, Fy);
+      face_flux<SCH, RETRY>(hl, ylo, fl(buf(z), sy - 1, sx) || fl(buf(z), sy, sx), Fy);
 #pragma unroll
       for (int k = 0; k < NV; k++) sXf[(k * BY + ty) * 32 + tx] = Fy[k];
     }
     if (interior) {  // z: reconstruct cell z+1, flux through the upper z face of cell z
       T lo[NV], hi[NV], F[NV];
       recon_z(z + 1, lo, hi);
-      face_flux<SCH>(hprev, lo, F);
+      face_flux<SCH, RETRY>(hprev, lo, fl(buf(z), sy, sx) || fl(buf(z + 1), sy, sx), F);
 #pragma unroll
       for (int k = 0; k < NV; k++) {
         acc[Frame<2>::g(k)] += (Fprev[k] - F[k]) * idz;
@@ -571,7 +571,7 @@ __global__ void __launch_bounds__(32 * WARPS) step_strip2d_kernel(StepArgs<T> a)
         if (RETRY) first_order_faces(fa, f0, f1, r0, lo, hprev);
         recon<SCH>(r0, r1, r2, nuy, lo, hi);     // cell y0
         if (RETRY) first_order_faces(f0, f1, f2, r1, lo, hi);
-        face_flux<SCH>(hprev, lo, Fprev);                     // flux through y0 - 1/2
+        face_flux<SCH, RETRY>(hprev, lo, f0 || f1, Fprev);  // flux through y0 - 1/2
 #pragma unroll
         for (int k = 0; k < NV; k++) {
           hprev[k] = hi[k];
@@ -596,13 +596,15 @@ __global__ void __launch_bounds__(32 * WARPS) step_strip2d_kernel(StepArgs<T> a)
             wp[k] = __shfl_down_sync(FULL, w0[k], 1);
           }
           recon<SCH>(wm, w0, wp, nux, lo, hi);
+          bool fxlo = false;  // the lower x face has first-order states
           if (RETRY) {
             const bool fm = __shfl_up_sync(FULL, f0, 1), fp = __shfl_down_sync(FULL, f0, 1);
             first_order_faces(fm, f0, fp, w0, lo, hi);
+            fxlo = fm || f0;
           }
 #pragma unroll
           for (int k = 0; k < NV; k++) hl[k] = __shfl_up_sync(FULL, hi[k], 1);
-          face_flux<SCH>(hl, lo, F);  // flux through the lower x face of this cell
+          face_flux<SCH, RETRY>(hl, lo, fxlo, F);  // flux through the lower x face of this cell
 #pragma unroll
           for (int k = 0; k < NV; k++) acc[k] = (F[k] - __shfl_down_sync(FULL, F[k], 1)) * idx;
         }
@@ -614,7 +616,7 @@ __global__ void __launch_bounds__(32 * WARPS) step_strip2d_kernel(StepArgs<T> a)
           T lo[NV], hi[NV], F[NV];
           recon<SCH>(r0, r1, r2, nuy, lo, hi);
           if (RETRY) first_order_faces(f0, f1, f2, r1, lo, hi);
-          face_flux<SCH>(hprev, lo, F);
+          face_flux<SCH, RETRY>(hprev, lo, f0 || f1, F);
 #pragma unroll
           for (int k = 0; k < NV; k++) {
             acc[Frame<1>::g(k)] += (Fprev[k] - F[k]) * idy;

@@ -195,6 +195,25 @@ def hll(WL, WR, d):
     return (SR * FL - SL * FR + SL * SR * (UR - UL)) / (SR - SL)
 
 
+def roe(WL, WR, d):
+    """Roe-type flux from the numerically computed eigen-system of the primitive Jacobian at
+    the arithmetic mean state: F = (f_L + f_R)/2 - (1/2) (dU/dW) R |Lambda| R^-1 (W_R - W_L),
+    Harten's fix |l| -> (l^2 + delta^2) / (2 delta) below delta = 0.1 sqrt(3 P_dd / rho) on the
+    slowest and fastest waves only."""
+    Wm = 0.5 * (WL + WR)
+    _, lam, R = eigen(Wm, d)
+    a = np.linalg.solve(R, WR - WL)
+    delta = 0.1 * np.sqrt(3 * Wm[tidx(d, d)] / Wm[0])
+    al = np.abs(lam)
+    for k in (0, len(lam) - 1):
+        if al[k] < delta:
+            al[k] = (lam[k] ** 2 + delta ** 2) / (2 * delta)
+    dW = R @ (al * a)
+    dUdW = jac_cs(cons, Wm).real
+    FL, FR = flux_moments(WL, d).real, flux_moments(WR, d).real
+    return 0.5 * (FL + FR) - 0.5 * dUdW @ dW
+
+
 def _pad_line(Uline, bclo, bchi, d):
     """Two ghost cells each side along a line of conserved states (n, 10)."""
     n = Uline.shape[0]
@@ -222,11 +241,12 @@ def _pad_line(Uline, bclo, bchi, d):
     return out
 
 
-def step(U, ndim, dx, bc, dt, phi=None):
+def step(U, ndim, dx, bc, dt, phi=None, flux="hll"):
     """One unsplit step on a tiny grid, with the a-posteriori fallback: if the second-order
     update leaves cells non-realizable, recompute with first-order face states on every
-    face of those cells."""
-    Un = _step_pass(U, ndim, dx, bc, dt, phi, None)
+    face of those cells.  flux="roe": the Roe-type flux on every face except the
+    first-order faces of a fallback pass, which take HLL."""
+    Un = _step_pass(U, ndim, dx, bc, dt, phi, None, flux)
     nz, ny, nx = Un.shape[1:]
     bad = np.zeros((nz, ny, nx), dtype=bool)
     for _ in range(5):  # the first check plus at most four fallback passes
@@ -238,11 +258,11 @@ def step(U, ndim, dx, bc, dt, phi=None):
         if not new.any() or _ == 4:
             break
         bad |= new
-        Un = _step_pass(U, ndim, dx, bc, dt, phi, bad)
+        Un = _step_pass(U, ndim, dx, bc, dt, phi, bad, flux)
     return Un
 
 
-def _step_pass(U, ndim, dx, bc, dt, phi, bad):
+def _step_pass(U, ndim, dx, bc, dt, phi, bad, flux="hll"):
     U = np.asarray(U, dtype=np.float64)
     dU = np.zeros_like(U)
     nz, ny, nx = U.shape[1:]
@@ -272,14 +292,20 @@ def _step_pass(U, ndim, dx, bc, dt, phi, bad):
                         idx2 = list(idx)
                         idx2[d] = i
                         return bad[idx2[2], idx2[1], idx2[0]]
+                first = set()
+                if bad is not None:
                     for k in range(1, n + 2):  # face between padded cells k and k+1
                         if flag(k) or flag(k + 1):
                             faces[k - 1][1] = Wl[k].copy()
                             faces[k][0] = Wl[k + 1].copy()
+                            first.add(k)
+
+                def F(k):  # flux through the face between padded cells k and k+1
+                    f = roe if flux == "roe" and k not in first else hll
+                    return f(faces[k - 1][1], faces[k][0], d)
                 # faces[k-1] = (lo, hi) of padded cell k, cell i <-> padded i+2
                 for i in range(n):
-                    Fm = hll(faces[i][1], faces[i + 1][0], d)
-                    Fp = hll(faces[i + 1][1], faces[i + 2][0], d)
+                    Fm, Fp = F(i + 1), F(i + 2)
                     idx[d] = i
                     dU[:, idx[2], idx[1], idx[0]] -= (Fp - Fm) / dx[d]
     Un = U + dt * dU

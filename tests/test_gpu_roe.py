@@ -1,0 +1,160 @@
+"""The characteristic step with the Roe-type flux on the GPU against the oracle's: FP64 <=
+1e-10 relative L_inf per field, FP32 within the FP32 tolerances; 1D/2D/3D, every boundary
+kind, tile shapes, gravity, the a-posteriori fallback; a stationary contact stays exact;
+the adjoint refuses the scheme."""
+import numpy as np
+import pytest
+
+from tests.parity import assert_fp32, assert_fp64
+from tests.test_gpu_parity import _extreme
+
+pytestmark = pytest.mark.gpu
+ROE = 2
+
+
+@pytest.fixture(scope="module")
+def env():
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1210_5246_gb300 import inputs, msh
+    msh.load()
+    return msh, inputs
+
+
+def _run(msh, oracle, n, lo, hi, bc, cfl, W, precision, steps=None, t_end=np.inf, phi=None, tiling=None):
+    g = msh.Grid(n, lo, hi, bc, cfl, precision)
+    g.set_scheme(msh.MUSCL_HANCOCK_ROE)
+    if phi is not None:
+        g.set_potential(phi)
+    if tiling:
+        g.set_tiling(*tiling)
+    Wg = W.astype(np.float32) if precision == msh.FP32 else W
+    g.set_state(Wg, msh.PRIMITIVE)
+    ns, t = g.run(t_end, steps if steps is not None else (1 << 62))
+    U, Wout = g.get_state().astype(np.float64), g.get_state(msh.PRIMITIVE).astype(np.float64)
+    g.close()
+    og = oracle.Grid(n, lo, hi, bc, cfl, scheme=ROE)
+    Uo, no, to, rc, _ = oracle.run(og, oracle.prim_to_cons(Wg.astype(np.float64)), t_end,
+                                   max_steps=steps if steps is not None else (1 << 62), phi=phi)
+    assert rc == 0 and ns == no and abs(t - to) <= (1e-13 if precision == msh.FP64 else 1e-5) * to
+    return U, Wout, Uo, oracle.cons_to_prim(Uo)
+
+
+def _random(shape, seed):
+    rng = np.random.default_rng(seed)
+    W = np.zeros((10,) + shape)
+    W[0] = np.exp(rng.uniform(-0.5, 0.5, shape))
+    W[1:4] = rng.uniform(-0.3, 0.3, (3,) + shape)
+    W[4], W[7], W[9] = 0.8, 0.7, 0.6
+    for k in (5, 6, 8):
+        W[k] = rng.uniform(-0.1, 0.1, shape)
+    return W
+
+
+def test_sod(env, oracle):
+    msh, I = env
+    p = I.sod(256)
+    U, _, Uo, _ = _run(msh, oracle, p.n, p.lo, p.hi, p.bc, p.cfl, p.W, msh.FP64, t_end=p.t_end)
+    assert_fp64(U, Uo, what="roe sod fp64")
+    _, W, _, Wo = _run(msh, oracle, p.n, p.lo, p.hi, p.bc, p.cfl, p.W, msh.FP32, t_end=p.t_end)
+    assert_fp32(W, Wo, what="roe sod fp32")
+
+
+@pytest.mark.parametrize("n,bc", [(5, (0, 0)), (127, (1, 2)), (300, (2, 1))])
+def test_1d(env, oracle, n, bc):
+    msh, _ = env
+    U, _, Uo, _ = _run(msh, oracle, (n,), (0.0,), (1.0,), (bc,), 0.5, _random((1, 1, n), n), msh.FP64, steps=7)
+    assert_fp64(U, Uo, what=f"roe 1d {n}")
+
+
+@pytest.mark.parametrize("tiling", [(4, 8), (16, 64)])
+def test_blast(env, oracle, tiling):
+    msh, I = env
+    p = I.blast(n=97, nsteps=15)
+    U, _, Uo, _ = _run(msh, oracle, p.n, p.lo, p.hi, p.bc, p.cfl, p.W, msh.FP64, steps=15, tiling=tiling)
+    assert_fp64(U, Uo, what=f"roe blast {tiling}")
+
+
+def test_blast_fp32(env, oracle):
+    msh, I = env
+    p = I.blast(n=97, nsteps=15)
+    _, W, _, Wo = _run(msh, oracle, p.n, p.lo, p.hi, p.bc, p.cfl, p.W, msh.FP32, steps=15)
+    assert_fp32(W, Wo, what="roe blast fp32")
+
+
+@pytest.mark.parametrize("shape,bc", [((31, 7), ((1, 1), (2, 2))), ((61, 45), ((2, 2), (1, 2)))])
+def test_2d_shapes(env, oracle, shape, bc):
+    msh, _ = env
+    W = _random((1, shape[1], shape[0]), shape[0] * 100 + shape[1])
+    U, _, Uo, _ = _run(msh, oracle, shape, (0.0, 0.0), (1.0, 2.0), bc, 0.5, W, msh.FP64, steps=5)
+    assert_fp64(U, Uo, what=f"roe 2d {shape}")
+
+
+@pytest.mark.parametrize("tiling", [(8, 32), (4, 5)])
+def test_turb(env, oracle, tiling):
+    msh, I = env
+    p = I.turb(n=24, nsteps=5)
+    U, _, Uo, _ = _run(msh, oracle, p.n, p.lo, p.hi, p.bc, p.cfl, p.W, msh.FP64, steps=5, tiling=tiling)
+    assert_fp64(U, Uo, what=f"roe turb {tiling}")
+
+
+def test_turb_fp32_rows16(env, oracle):
+    msh, I = env
+    p = I.turb(n=32, nsteps=8)
+    _, W, _, Wo = _run(msh, oracle, p.n, p.lo, p.hi, p.bc, p.cfl, p.W, msh.FP32, steps=8, tiling=(16, 7))
+    assert_fp32(W, Wo, what="roe turb fp32")
+
+
+def test_3d_shapes(env, oracle):
+    msh, _ = env
+    shape, bc = (33, 17, 9), ((1, 2), (2, 1), (0, 0))
+    W = _random((9, 17, 33), 99)
+    U, _, Uo, _ = _run(msh, oracle, shape, (0, 0, 0), (1, 1.5, 0.5), bc, 0.5, W, msh.FP64, steps=4, tiling=(8, 4))
+    assert_fp64(U, Uo, what="roe 3d")
+
+
+def test_disc_gravity(env, oracle):
+    msh, I = env
+    p = I.disc(n=64, nsteps=15)
+    U, _, Uo, _ = _run(msh, oracle, p.n, p.lo, p.hi, p.bc, p.cfl, p.W, msh.FP64, steps=15, phi=p.phi)
+    assert_fp64(U, Uo, what="roe disc")
+
+
+@pytest.mark.parametrize("shape,n,bc,cfl", [((1, 12, 12), (12, 12), ((0, 0), (1, 2)), 0.5),
+                                            ((6, 7, 9), (9, 7, 6), ((2, 1), (0, 0), (1, 1)), 0.5)])
+def test_fallback(env, oracle, shape, n, bc, cfl):
+    msh, _ = env
+    nd = len(n)
+    U, _, Uo, _ = _run(msh, oracle, n, (0,) * nd, (1,) * nd, bc, cfl, _extreme(shape, 0), msh.FP64, steps=20)
+    assert_fp64(U, Uo, what=f"roe fallback {n}")
+
+
+def test_stationary_contact_is_exact(env):
+    msh, _ = env
+    n = 64
+    x = (np.arange(n) + 0.5) / n
+    W = np.zeros((10, 1, 1, n))
+    W[0, 0, 0] = np.where(np.abs(x - 0.5) < 0.25, 2.0, 0.5)
+    W[4] = W[7] = W[9] = 1.0
+    W[5] = 0.1
+    for prec in (msh.FP64, msh.FP32):
+        g = msh.Grid((n,), (0.0,), (1.0,), ((0, 0),), 0.5, prec)
+        g.set_scheme(msh.MUSCL_HANCOCK_ROE)
+        g.set_state(W.astype(g.dtype), msh.PRIMITIVE)
+        g.run(max_steps=40)
+        rho = g.get_state(msh.PRIMITIVE)[0, 0, 0].astype(np.float64)
+        np.testing.assert_allclose(rho, W[0, 0, 0], rtol=1e-13 if prec == msh.FP64 else 1e-6)
+        g.close()
+
+
+def test_adjoint_refuses_roe(env):
+    msh, I = env
+    p = I.sod(32)
+    g = msh.Grid.from_problem(p, msh.FP64)
+    g.set_state(p.W, msh.PRIMITIVE)
+    g.set_scheme(msh.MUSCL_HANCOCK_ROE)
+    U0 = g.get_state()
+    with pytest.raises(msh.MshError) as ei:
+        g.adjoint_run(U0, [1e-3], U0, K=1)
+    assert ei.value.status == msh.MSH_E_STATE
+    g.close()

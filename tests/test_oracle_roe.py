@@ -4,6 +4,7 @@ exactly); a stationary contact is kept exactly (the contact waves have speed 0 a
 entropy-fixed) while HLL smears it; the moving contact of the gamma = 3 Sod problem is
 sharper than HLL's; convergence to the exact Sod solution; conservation of every total."""
 import numpy as np
+import pytest
 
 from oracle import exact_riemann
 
@@ -106,3 +107,51 @@ def test_conservation_periodic(oracle):
     t0, t1 = oracle.diagnostics(g, U0)[0], oracle.diagnostics(g, U)[0]
     scale = np.array([t0[0]] * 4 + [abs(t0[4]) + abs(t0[7]) + abs(t0[9])] * 6)
     assert np.all(np.abs(t1 - t0) / scale < 1e-13)
+
+
+def test_roe_flux_matches_bruteforce(oracle):
+    """Against the flux built from a numerically computed eigen-system (SVD null spaces of
+    the complex-step Jacobian), for near and far state pairs in every direction."""
+    from tests import bruteforce as BF
+    rng = np.random.default_rng(5)
+    Ws = _rand_states(rng, 12)
+    for i in range(0, 12, 2):
+        WL = Ws[i]
+        for WR in (WL * (1 + 0.05 * rng.normal(size=10)), Ws[i + 1]):
+            for d in range(3):
+                F, B = oracle.roe_flux(WL, WR, d), BF.roe(WL, WR, d)
+                assert np.abs(F - B).max() <= 1e-9 * (np.abs(B).max() + 1), (d, np.abs(F - B).max())
+
+
+@pytest.mark.parametrize("seed", [1, 13])
+def test_fallback_takes_hll_on_first_order_faces(oracle, seed):
+    """Extreme states: the Roe-type second-order update leaves cells non-realizable; the
+    fallback passes (first-order states and the HLL flux on every face of a tagged cell, the
+    Roe-type flux elsewhere) make it realizable and conservative, and match the brute-force
+    step with the same rule."""
+    from tests import bruteforce as BF
+    from tests.test_oracle_pins import _extreme_tiny
+    W = _extreme_tiny(seed)
+    g = oracle.Grid((8,), (0,), (1,), ((0, 0),), 0.8, scheme=ROE)
+    U = oracle.prim_to_cons(W)
+    dt = oracle.cfl_dt(g, U)
+    assert not oracle.diagnostics(g, oracle.step_second_order_only(g, U, dt))[1]
+    A = oracle.step(g, U, dt)
+    tot0 = oracle.diagnostics(g, U)[0]
+    tot1, ok, _ = oracle.diagnostics(g, A)
+    assert ok
+    assert np.all(np.abs(tot1 - tot0) <= 1e-13 * np.abs(tot0).max())
+    B = BF.step(U, 1, [1 / 8] * 3, ((0, 0),), dt, flux="roe")
+    scale = np.abs(B).reshape(10, -1).max(axis=1)[:, None, None, None] + 1e-300
+    assert np.max(np.abs(A - B) / scale) < 1e-10
+
+
+def test_kt_contact_wider_than_roe(oracle):
+    """Sec. 4.1 finds the central scheme's contact about twice as wide as that of a
+    contact-resolving upwind flux: the Kurganov-Tadmor contact of the gamma = 3 Sod problem
+    is wider than the Roe-type one at every resolution."""
+    KT = 1
+    for n in (256, 512):
+        Wr, x = _sod(oracle, n, ROE)
+        Wk, _ = _sod(oracle, n, KT)
+        assert _contact_width(Wk, x) > _contact_width(Wr, x)
