@@ -60,7 +60,8 @@ typedef struct {
     double dx[3];        /* cell widths */
     int32_t bc[6];       /* bc[2d+0] lower face, bc[2d+1] upper face: 0 periodic, 1 outflow, 2 reflect */
     double cfl;
-    int32_t scheme;      /* OG_SCHEME_MH (Sec. 3.3) or OG_SCHEME_KT (Sec. 3.2) */
+    int32_t scheme;      /* OG_SCHEME_MH (Sec. 3.3, HLL), OG_SCHEME_KT (Sec. 3.2) or
+                            OG_SCHEME_MH_ROE (Sec. 3.3, Roe-type flux, eqs 40-43 tracing) */
     int32_t pad1;
 } og_grid;
 
@@ -278,6 +279,68 @@ void og_reconstruct(const double *Wm, const double *W0, const double *Wp, int d,
     }
     /* face-state fallback (reading): revert to first order if a face state
      * has non-positive density or non-positive normal dispersion            */
+    if (!(hi_l[0] > 0.0 && lo_l[0] > 0.0 && hi_l[4] > 0.0 && lo_l[4] > 0.0)) {
+        for (int k = 0; k < NV; k++) hi_l[k] = lo_l[k] = w0[k];
+    }
+    for (int k = 0; k < NV; k++) {
+        lo[p[k]] = lo_l[k];
+        hi[p[k]] = hi_l[k];
+    }
+}
+
+/* Characteristic tracing for a Riemann solver that resolves every wave (Sec. 3.3, eqs 40-43;
+ * Colella 1990, Stone et al. 2008): the limited slope dw^m as in og_reconstruct; reference
+ * states traced with the fastest wave towards each face,
+ *   wt_L(i+1/2) = w + [1/2 - max(lam^M, 0) dt/(2dx)] dw^m                          (eq 40)
+ *   wt_R(i-1/2) = w - [1/2 + min(lam^0, 0) dt/(2dx)] dw^m                          (eq 41)
+ * (eq 41 read in the mirror form of eq 40: the printed -max(lam^0, 0) leaves the reference
+ * state untraced whenever lam^0 < 0), then every wave that reaches the face within dt/2
+ * corrected from the reference speed to its own,
+ *   w_L = wt_L + dt/(2dx) sum_{lam^a > 0} (lam^M - lam^a) (L^a . dw^m) R^a           (eq 42)
+ *   w_R = wt_R + dt/(2dx) sum_{lam^a < 0} (lam^0 - lam^a) (L^a . dw^m) R^a           (eq 43)
+ * lam^M, lam^0 the largest and smallest eigenvalues of cell i; L^a the rows of L, R^a the
+ * columns of R.  No eq 44-45 terms (those belong to HLL).  Face-state fallback as in
+ * og_reconstruct. */
+void og_reconstruct_upwind(const double *Wm, const double *W0, const double *Wp, int d,
+                           double dtdx, double *lo, double *hi)
+{
+    const int *p = perm[d];
+    double w0[NV], dwL[NV], dwC[NV], dwR[NV];
+    for (int k = 0; k < NV; k++) {
+        w0[k] = W0[p[k]];
+        dwL[k] = W0[p[k]] - Wm[p[k]];
+        dwC[k] = 0.5 * (Wp[p[k]] - Wm[p[k]]);
+        dwR[k] = Wp[p[k]] - W0[p[k]];
+    }
+    double L[NV][NV], R[NV][NV], lam[NV];
+    og_left_x(w0, L);
+    og_right_x(w0, R);
+    og_eigenvalues_x(w0, lam);
+    double daL[NV], daC[NV], daR[NV], dam[NV], dwm[NV];
+    matvec(L, dwL, daL);
+    matvec(L, dwC, daC);
+    matvec(L, dwR, daR);
+    for (int k = 0; k < NV; k++) dam[k] = mc_limit(daL[k], daC[k], daR[k]);
+    matvec(R, dam, dwm);
+    double lmax = lam[0], lmin = lam[0];
+    for (int k = 1; k < NV; k++) {
+        lmax = fmax(lmax, lam[k]);
+        lmin = fmin(lmin, lam[k]);
+    }
+    double hi_l[NV], lo_l[NV];
+    const double h = 0.5 * dtdx;
+    for (int k = 0; k < NV; k++) {
+        hi_l[k] = w0[k] + (0.5 - fmax(lmax, 0.0) * h) * dwm[k];                   /* eq 40 */
+        lo_l[k] = w0[k] - (0.5 + fmin(lmin, 0.0) * h) * dwm[k];                   /* eq 41 */
+    }
+    for (int a = 0; a < NV; a++) {
+        double la = 0.0; /* L^a . dw^m */
+        for (int k = 0; k < NV; k++) la += L[a][k] * dwm[k];
+        if (lam[a] > 0.0)
+            for (int k = 0; k < NV; k++) hi_l[k] += h * (lmax - lam[a]) * la * R[k][a];   /* eq 42 */
+        if (lam[a] < 0.0)
+            for (int k = 0; k < NV; k++) lo_l[k] += h * (lmin - lam[a]) * la * R[k][a];   /* eq 43 */
+    }
     if (!(hi_l[0] > 0.0 && lo_l[0] > 0.0 && hi_l[4] > 0.0 && lo_l[4] > 0.0)) {
         for (int k = 0; k < NV; k++) hi_l[k] = lo_l[k] = w0[k];
     }
@@ -539,8 +602,12 @@ static int step_pass(const og_grid *Gr, const double *U, const double *phi, doub
                         int64_t pi = pidx(&P, c3[0], c3[1], c3[2]);
                         for (int k = 0; k < NV; k++) Wc[o + 1][k] = Wp[k * NP + pi];
                     }
-                    og_reconstruct(Wc[0], Wc[1], Wc[2], d, dtdx,
-                                   lo + NV * (i + 1), hi + NV * (i + 1));
+                    if (Gr->scheme == OG_SCHEME_MH_ROE)
+                        og_reconstruct_upwind(Wc[0], Wc[1], Wc[2], d, dtdx,
+                                              lo + NV * (i + 1), hi + NV * (i + 1));
+                    else
+                        og_reconstruct(Wc[0], Wc[1], Wc[2], d, dtdx,
+                                       lo + NV * (i + 1), hi + NV * (i + 1));
                 }
                 if (flag) {
                     /* first-order states on every face that touches a flagged cell */

@@ -71,6 +71,7 @@ def _load():
             lib.og_roe.argtypes = [dp, dp, C.c_int, dp]
             lib.og_kt_reconstruct.argtypes = [dp, dp, dp, C.c_int, dp, dp]
             lib.og_reconstruct.argtypes = [dp, dp, dp, C.c_int, C.c_double, dp, dp]
+            lib.og_reconstruct_upwind.argtypes = [dp, dp, dp, C.c_int, C.c_double, dp, dp]
             for f in ("og_jacobian_x", "og_right_x", "og_left_x"):
                 getattr(lib, f).argtypes = [dp, dp]
             lib.og_eigenvalues_x.argtypes = [dp, dp]
@@ -258,6 +259,14 @@ def reconstruct(Wm, W0, Wp, d, dtdx):
     lo, hi = np.empty(NV), np.empty(NV)
     _load().og_reconstruct(_p(_f64(Wm)), _p(_f64(W0)), _p(_f64(Wp)), int(d), float(dtdx),
                            _p(lo), _p(hi))
+    return lo, hi
+
+
+def reconstruct_upwind(Wm, W0, Wp, d, dtdx):
+    """(lo, hi) face states with the upwind characteristic tracing of the Roe-type scheme."""
+    lo, hi = np.empty(NV), np.empty(NV)
+    _load().og_reconstruct_upwind(_p(_f64(Wm)), _p(_f64(W0)), _p(_f64(Wp)), int(d), float(dtdx),
+                                  _p(lo), _p(hi))
     return lo, hi
 
 

@@ -210,6 +210,55 @@ __device__ __forceinline__ void reconstruct(const T (&wm)[NV], const T (&w0)[NV]
   }
 }
 
+// Upwind characteristic tracing for the Roe-type flux (Sec. 3.3, eqs 40-43: reference
+// states traced with the fastest wave towards each face, then each wave that reaches the
+// face corrected to its own speed; no eq 44-45 terms).  Summed per wave a with amplitude
+// c_a = (L dw^m)_a and speed lam_a = u + s_a:
+//   hi = w0 + sum_a (1/2 - nu x_a) c_a R^a,   x_a = lam_a if lam_a > 0, else max(u + cf, 0)
+//   lo = w0 + sum_a (-1/2 - nu y_a) c_a R^a,  y_a = lam_a if lam_a < 0, else min(u - cf, 0)
+// (eq 41 read in the mirror form of eq 40).  Same limiter and face-state fallback as
+// reconstruct.
+template <typename T>
+__device__ __forceinline__ void reconstruct_upwind(const T (&wm)[NV], const T (&w0)[NV], const T (&wp)[NV],
+                                                   T nu, T (&lo)[NV], T (&hi)[NV]) {
+  Eig<T> E;
+  E.init(w0);
+  T d[NV], cl[NV], cr[NV];
+#pragma unroll
+  for (int k = 0; k < NV; k++) d[k] = w0[k] - wm[k];
+  E.project(d, cl);
+#pragma unroll
+  for (int k = 0; k < NV; k++) d[k] = wp[k] - w0[k];
+  E.project(d, cr);
+  // doubled limited amplitudes: the coefficients below carry the factor 1/2
+  T m[NV];
+#pragma unroll
+  for (int k = 0; k < NV; k++) m[k] = mc_limit2(cl[k], cr[k]);
+  const T u = E.u;
+  const T s[NV] = {-E.cf, -E.cs, -E.cs, T(0), T(0), T(0), T(0), E.cs, E.cs, E.cf};
+  const T xM = fmax(u + E.cf, T(0)), y0 = fmin(u - E.cf, T(0)), nu2 = T(0.5) * nu;
+  T ch[NV], cl2[NV];
+#pragma unroll
+  for (int k = 0; k < NV; k++) {
+    const T lam = u + s[k];
+    ch[k] = (T(0.25) - nu2 * (lam > T(0) ? lam : xM)) * m[k];
+    cl2[k] = (T(-0.25) - nu2 * (lam < T(0) ? lam : y0)) * m[k];
+  }
+  T dh[NV], dl[NV];
+  E.back(ch, dh);
+  E.back(cl2, dl);
+#pragma unroll
+  for (int k = 0; k < NV; k++) {
+    hi[k] = w0[k] + dh[k];
+    lo[k] = w0[k] + dl[k];
+  }
+  const bool ok = hi[0] > T(0) && lo[0] > T(0) && hi[4] > T(0) && lo[4] > T(0);
+  if (!ok) {
+#pragma unroll
+    for (int k = 0; k < NV; k++) { hi[k] = w0[k]; lo[k] = w0[k]; }
+  }
+}
+
 // A-posteriori fallback: every face that touches a cell whose second-order update was
 // not realizable takes first-order states (the cell-centred primitive state).  fm, f0,
 // fp: tags of cells i-1, i, i+1 along the sweep.
@@ -371,7 +420,8 @@ template <int SCH> constexpr bool kCharacteristic = SCH == 0 || SCH == 3;
 template <int SCH, typename T>
 __device__ __forceinline__ void recon(const T (&wm)[NV], const T (&w0)[NV], const T (&wp)[NV], T nu, T (&lo)[NV],
                                       T (&hi)[NV]) {
-  if constexpr (kCharacteristic<SCH>) reconstruct(wm, w0, wp, nu, lo, hi);
+  if constexpr (SCH == 0) reconstruct(wm, w0, wp, nu, lo, hi);
+  else if constexpr (SCH == 3) reconstruct_upwind(wm, w0, wp, nu, lo, hi);
   else kt_reconstruct(wm, w0, wp, lo, hi);
 }
 

@@ -177,6 +177,26 @@ def recon(Wm, W0, Wp, d, dtdx):
     return lo, hi
 
 
+def recon_upwind(Wm, W0, Wp, d, dtdx):
+    """Upwind characteristic tracing (eqs 40-43 with eq 41 in the mirror form of eq 40),
+    summed per wave: with a = R^-1 dw^m, nu = dt / 2dx,
+      hi = W0 + sum_a (1/2 - nu s_a) a_a R^a,  s_a = lam_a if lam_a > 0 else max(lam_max, 0)
+      lo = W0 + sum_a (-1/2 - nu t_a) a_a R^a, t_a = lam_a if lam_a < 0 else min(lam_min, 0)."""
+    _, lam, R = eigen(W0, d)
+    Linv = np.linalg.inv(R)
+    dL, dR, dC = W0 - Wm, Wp - W0, 0.5 * (Wp - Wm)
+    a = mc(Linv @ dL, Linv @ dC, Linv @ dR)
+    nu = 0.5 * dtdx
+    s = np.where(lam > 0, lam, max(lam.max(), 0.0))
+    t = np.where(lam < 0, lam, min(lam.min(), 0.0))
+    hi = W0 + R @ ((0.5 - nu * s) * a)
+    lo = W0 + R @ ((-0.5 - nu * t) * a)
+    nn = tidx(d, d)
+    if not (hi[0] > 0 and lo[0] > 0 and hi[nn] > 0 and lo[nn] > 0):
+        hi, lo = W0.copy(), W0.copy()
+    return lo, hi
+
+
 def speeds(W, d):
     lam = np.linalg.eigvals(prim_jacobian(W, d)).real
     return lam.min(), lam.max()
@@ -244,8 +264,8 @@ def _pad_line(Uline, bclo, bchi, d):
 def step(U, ndim, dx, bc, dt, phi=None, flux="hll"):
     """One unsplit step on a tiny grid, with the a-posteriori fallback: if the second-order
     update leaves cells non-realizable, recompute with first-order face states on every
-    face of those cells.  flux="roe": the Roe-type flux on every face except the
-    first-order faces of a fallback pass, which take HLL."""
+    face of those cells.  flux="roe": upwind tracing (recon_upwind) and the Roe-type flux
+    on every face except the first-order faces of a fallback pass, which take HLL."""
     Un = _step_pass(U, ndim, dx, bc, dt, phi, None, flux)
     nz, ny, nx = Un.shape[1:]
     bad = np.zeros((nz, ny, nx), dtype=bool)
@@ -280,7 +300,8 @@ def _step_pass(U, ndim, dx, bc, dt, phi, bad, flux="hll"):
                 P = _pad_line(np.array(line), bc[d][0], bc[d][1], d)
                 Wl = [prim(u) for u in P]
                 n = shape[d]
-                faces = [list(recon(Wl[k - 1], Wl[k], Wl[k + 1], d, dt / dx[d])) for k in range(1, n + 3)]
+                rc = recon_upwind if flux == "roe" else recon
+                faces = [list(rc(Wl[k - 1], Wl[k], Wl[k + 1], d, dt / dx[d])) for k in range(1, n + 3)]
                 if bad is not None:
                     # flag of padded cell k (k = i + 2 for cell i), ghosts take their source cell's
                     def flag(k):

@@ -158,3 +158,15 @@ def test_adjoint_refuses_roe(env):
         g.adjoint_run(U0, [1e-3], U0, K=1)
     assert ei.value.status == msh.MSH_E_STATE
     g.close()
+
+
+@pytest.mark.parametrize("sgn", [1.0, -1.0])
+def test_supersonic_drift(env, oracle, sgn):
+    """Every wave moving one way (|u|, |v| > cf): the one-sided branches of the upwind tracing."""
+    msh, _ = env
+    shape = (1, 19, 37)
+    W = _random(shape, 5)
+    W[1] += sgn * 3.0 * np.sqrt(3 * W[4] / W[0])
+    W[2] -= sgn * 3.0 * np.sqrt(3 * W[7] / W[0])
+    U, _, Uo, _ = _run(msh, oracle, (37, 19), (0.0, 0.0), (1.0, 1.0), ((0, 0), (1, 1)), 0.5, W, msh.FP64, steps=6)
+    assert_fp64(U, Uo, what=f"roe supersonic {sgn}")

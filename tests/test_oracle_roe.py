@@ -155,3 +155,47 @@ def test_kt_contact_wider_than_roe(oracle):
         Wr, x = _sod(oracle, n, ROE)
         Wk, _ = _sod(oracle, n, KT)
         assert _contact_width(Wk, x) > _contact_width(Wr, x)
+
+
+def _triples(rng, m):
+    """m (Wm, W0, Wp) triples of nearby realizable states."""
+    return [[W * (1 + 0.05 * rng.normal(size=10)) for _ in range(3)] for W in _rand_states(rng, m)]
+
+
+@pytest.mark.parametrize("d", [0, 1, 2])
+def test_upwind_tracing_matches_bruteforce(oracle, d):
+    """The oracle's tracing, written as eqs 40-43, equals the per-wave form on a numerically
+    computed eigen-system, subsonic and supersonic."""
+    from tests import bruteforce as BF
+    rng = np.random.default_rng(20 + d)
+    for Wm, W0, Wp in _triples(rng, 6):
+        for shift in (0.0, 4.0, -4.0):
+            s = np.zeros(10)
+            s[1 + d] = shift * np.sqrt(3 * W0[4 + [0, 3, 5][d]] / W0[0])
+            lo, hi = oracle.reconstruct_upwind(Wm + s, W0 + s, Wp + s, d, 0.3)
+            blo, bhi = BF.recon_upwind(Wm + s, W0 + s, Wp + s, d, 0.3)
+            scale = np.abs(W0 + s).max()
+            assert np.abs(lo - blo).max() <= 1e-10 * scale and np.abs(hi - bhi).max() <= 1e-10 * scale
+
+
+def test_upwind_tracing_supersonic_closed_forms(oracle):
+    """All waves moving right (u > cf): the i+1/2 state is the full Hancock predictor and the
+    i-1/2 state is untraced, w - dw^m / 2.  All waves moving left: the mirror.  (The second
+    case fixes the reading of eq 41: its printed form would leave the traced i-1/2 state off
+    the Hancock one.)"""
+    rng = np.random.default_rng(8)
+    for Wm, W0, Wp in _triples(rng, 6):
+        for sgn in (1.0, -1.0):
+            s = np.zeros(10)
+            s[1] = sgn * 3.0 * np.sqrt(3 * W0[4] / W0[0])
+            A = [w + s for w in (Wm, W0, Wp)]
+            hlo, hhi = oracle.reconstruct(*A, 0, 0.3)
+            dwm = hhi - hlo  # the Hancock states differ by exactly dw^m
+            lo, hi = oracle.reconstruct_upwind(*A, 0, 0.3)
+            tol = 1e-12 * np.abs(A[1]).max()
+            if sgn > 0:
+                assert np.abs(hi - hhi).max() <= tol
+                assert np.abs(lo - (A[1] - 0.5 * dwm)).max() <= tol
+            else:
+                assert np.abs(lo - hlo).max() <= tol
+                assert np.abs(hi - (A[1] + 0.5 * dwm)).max() <= tol
