@@ -23,6 +23,11 @@
  *   a9  CFL time step from the wave speeds a = sqrt(3 P_dd / rho) (Sec. 3.2/3.3)
  *   a10 FP64 conserved totals and realizability (rho > 0, P SPD)
  *
+ * Other schemes of the paper, selected by og_grid.scheme: the Kurganov-Tadmor central
+ * scheme with second-order Runge-Kutta (Sec. 3.2, og_step_kt); the characteristic step with
+ * upwind tracing (eqs 40-43, og_reconstruct_upwind) and a Roe-type flux (og_roe); the
+ * characteristic step with the Hancock predictor and an HLLC flux (og_hllc).
+ *
  * Readings where the paper is silent or garbled (each listed in the design doc):
  *   - full ten-moment system (the paper prints only the diagonal 7-variable case);
  *   - the ten-moment Jacobian / eigenvectors derived from eqs contin/moment/dispers
@@ -37,7 +42,8 @@
  *     OG_FALLBACK_PASSES passes);
  *   - CFL: dt = C / max_cells sum_d (|u_d| + sqrt(3 P_dd/rho)) / dx_d;
  *   - gravity: a = -grad(Phi) by central differences, m += dt rho a,
- *     E += dt (mbar a^T + a mbar^T) with mbar the mean of m before/after.
+ *     E += dt (mbar a^T + a mbar^T) with mbar the mean of m before/after;
+ *   - Roe-type and HLLC fluxes: faces with first-order states in a fallback pass take HLL.
  */
 #include <math.h>
 #include <stdint.h>
@@ -60,13 +66,14 @@ typedef struct {
     double dx[3];        /* cell widths */
     int32_t bc[6];       /* bc[2d+0] lower face, bc[2d+1] upper face: 0 periodic, 1 outflow, 2 reflect */
     double cfl;
-    int32_t scheme;      /* OG_SCHEME_MH (Sec. 3.3, HLL), OG_SCHEME_KT (Sec. 3.2) or
-                            OG_SCHEME_MH_ROE (Sec. 3.3, Roe-type flux, eqs 40-43 tracing) */
+    int32_t scheme;      /* OG_SCHEME_MH (Sec. 3.3, HLL), OG_SCHEME_KT (Sec. 3.2),
+                            OG_SCHEME_MH_ROE (Sec. 3.3, Roe-type flux, eqs 40-43 tracing) or
+                            OG_SCHEME_MH_HLLC (Sec. 3.3, HLLC flux, eqs 40-45 tracing) */
     int32_t pad1;
 } og_grid;
 
 enum { OG_PERIODIC = 0, OG_OUTFLOW = 1, OG_REFLECT = 2 };
-enum { OG_SCHEME_MH = 0, OG_SCHEME_KT = 1, OG_SCHEME_MH_ROE = 2 };
+enum { OG_SCHEME_MH = 0, OG_SCHEME_KT = 1, OG_SCHEME_MH_ROE = 2, OG_SCHEME_MH_HLLC = 3 };
 
 /* index of the symmetric tensor component (i,j) inside the 10-vector */
 static int tens_idx(int i, int j)
@@ -422,14 +429,100 @@ void og_roe(const double *WL, const double *WR, int d, double *F)
     for (int k = 0; k < NV; k++) F[k] = 0.5 * (FL[k] + FR[k]) - 0.5 * dU[k];
 }
 
-/* Face flux of the characteristic scheme: HLL (the hot path) or the Roe-type flux.  A
- * face with first-order states in a fallback pass (first != 0) takes HLL in both: the
+/* ------------------------------------------------------------- HLLC ---- */
+/* Three-wave HLLC flux (Toro, Spruce & Speares 1994; Batten et al. 1997) for the ten-moment
+ * system through a face normal to d.  The flux is F = u_d U + Pi with
+ *   Pi = (0; P_id; P_id u_j + P_jd u_i),
+ * and Pi depends only on u and on the stresses P_id on the face, the quantities that are
+ * continuous across the contact wave (rho, P_tt' jump there).  Readings: the outer waves
+ * S_L, S_R are HLL's (Davis speeds from the fast eigenvalue) and carry the fast and shear
+ * waves together; the middle wave is the contact S_M.  The star values of every pair
+ * (u_i, P_id) are common to both star states and follow from the momentum jump
+ * conditions across S_L and S_R, u*_i = u_i,K + (P*_id - P_id,K) / C_K with
+ * C_K = rho_K (S_K - u_d,K):
+ *   P*_id = (C_L C_R (u_i,R - u_i,L) + C_R P_id,L - C_L P_id,R) / (C_R - C_L),
+ * for i = d the usual contact speed S_M = u*_d and normal stress.  Each star state then
+ * follows from the jump conditions across its outer wave,
+ *   U*_K = (U_K (S_K - u_d,K) + Pi* - Pi_K) / (S_K - S_M),
+ * so that (S_M - S_L) U*_L + (S_R - S_M) U*_R equals (S_R - S_L) times the HLL state and
+ * the two star fluxes satisfy the contact's jump condition.  With diagonal stresses and no
+ * transverse velocity jump this is the gamma = 3 HLLC of gas dynamics (E_dd / 2 as the
+ * energy); an isolated contact is resolved exactly.  Where S_M is not strictly inside
+ * (S_L, S_R) the flux is HLL's.  Returns 1 if the star states were formed, 0 otherwise. */
+int og_hllc_star(const double *WL, const double *WR, int d, double *UsL, double *UsR, double *S)
+{
+    int nn = tens_idx(d, d);
+    double cL = sqrt(3.0 * WL[nn] / WL[0]);
+    double cR = sqrt(3.0 * WR[nn] / WR[0]);
+    double SL = fmin(WL[1 + d] - cL, WR[1 + d] - cR);
+    double SR = fmax(WL[1 + d] + cL, WR[1 + d] + cR);
+    double CL = WL[0] * (SL - WL[1 + d]), CR = WR[0] * (SR - WR[1 + d]);
+    double us[3], Ps[3]; /* star u_i and P_id */
+    for (int i = 0; i < 3; i++) {
+        int id = tens_idx(i, d);
+        Ps[i] = (CL * CR * (WR[1 + i] - WL[1 + i]) + CR * WL[id] - CL * WR[id]) / (CR - CL);
+        us[i] = WL[1 + i] + (Ps[i] - WL[id]) / CL;
+    }
+    double SM = us[d];
+    S[0] = SL; S[1] = SM; S[2] = SR;
+    if (!(SL < SM && SM < SR)) return 0;
+    /* Pi at the star values and at each side */
+    double Pis[NV], PiL[NV], PiR[NV];
+    const double *W2[2] = {WL, WR};
+    double *Pi2[2] = {PiL, PiR};
+    for (int side = 0; side < 3; side++) {
+        double *Pi = side < 2 ? Pi2[side] : Pis;
+        double u[3], Pd[3];
+        for (int i = 0; i < 3; i++) {
+            u[i] = side < 2 ? W2[side][1 + i] : us[i];
+            Pd[i] = side < 2 ? W2[side][tens_idx(i, d)] : Ps[i];
+        }
+        Pi[0] = 0.0;
+        for (int i = 0; i < 3; i++) Pi[1 + i] = Pd[i];
+        for (int i = 0; i < 3; i++)
+            for (int j = i; j < 3; j++) Pi[tens_idx(i, j)] = Pd[i] * u[j] + Pd[j] * u[i];
+    }
+    double UL[NV], UR[NV];
+    prim_to_cons(WL, UL);
+    prim_to_cons(WR, UR);
+    for (int k = 0; k < NV; k++) {
+        UsL[k] = (UL[k] * (SL - WL[1 + d]) + Pis[k] - PiL[k]) / (SL - SM);
+        UsR[k] = (UR[k] * (SR - WR[1 + d]) + Pis[k] - PiR[k]) / (SR - SM);
+    }
+    return 1;
+}
+
+void og_hllc(const double *WL, const double *WR, int d, double *F)
+{
+    double UsL[NV], UsR[NV], S[3], UL[NV], UR[NV], FL[NV], FR[NV];
+    if (!og_hllc_star(WL, WR, d, UsL, UsR, S)) {
+        og_hll(WL, WR, d, F);
+        return;
+    }
+    og_flux(WL, d, FL);
+    og_flux(WR, d, FR);
+    prim_to_cons(WL, UL);
+    prim_to_cons(WR, UR);
+    if (S[0] >= 0.0) {
+        for (int k = 0; k < NV; k++) F[k] = FL[k];
+    } else if (S[2] <= 0.0) {
+        for (int k = 0; k < NV; k++) F[k] = FR[k];
+    } else if (S[1] >= 0.0) {
+        for (int k = 0; k < NV; k++) F[k] = FL[k] + S[0] * (UsL[k] - UL[k]);
+    } else {
+        for (int k = 0; k < NV; k++) F[k] = FR[k] + S[2] * (UsR[k] - UR[k]);
+    }
+}
+
+/* Face flux of the characteristic scheme: HLL (the hot path), the Roe-type or the HLLC flux.  A
+ * face with first-order states in a fallback pass (first != 0) takes HLL in all three: the
  * fallback has to make the update realizable, and a linearised Roe flux is not positively
  * conservative (Einfeldt, Munz, Roe & Sjogreen 1991) where HLL with bounding wave speeds
- * is. */
+ * is; HLLC's star states, formed from the jump conditions, need not be realizable either. */
 static void face_flux(const og_grid *Gr, const double *WL, const double *WR, int d, int first, double *F)
 {
     if (Gr->scheme == OG_SCHEME_MH_ROE && !first) og_roe(WL, WR, d, F);
+    else if (Gr->scheme == OG_SCHEME_MH_HLLC && !first) og_hllc(WL, WR, d, F);
     else og_hll(WL, WR, d, F);
 }
 

@@ -21,7 +21,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "liboracle.so")
 
 PERIODIC, OUTFLOW, REFLECT = 0, 1, 2
-SCHEME_MH, SCHEME_KT, SCHEME_MH_ROE = 0, 1, 2
+SCHEME_MH, SCHEME_KT, SCHEME_MH_ROE, SCHEME_MH_HLLC = 0, 1, 2, 3
 NV = 10
 
 _lock = threading.Lock()
@@ -69,6 +69,9 @@ def _load():
             lib.og_hll.argtypes = [dp, dp, C.c_int, dp]
             lib.og_kt_flux.argtypes = [dp, dp, C.c_int, dp]
             lib.og_roe.argtypes = [dp, dp, C.c_int, dp]
+            lib.og_hllc.argtypes = [dp, dp, C.c_int, dp]
+            lib.og_hllc_star.argtypes = [dp, dp, C.c_int, dp, dp, dp]
+            lib.og_hllc_star.restype = C.c_int
             lib.og_kt_reconstruct.argtypes = [dp, dp, dp, C.c_int, dp, dp]
             lib.og_reconstruct.argtypes = [dp, dp, dp, C.c_int, C.c_double, dp, dp]
             lib.og_reconstruct_upwind.argtypes = [dp, dp, dp, C.c_int, C.c_double, dp, dp]
@@ -97,7 +100,8 @@ class Grid:
 
     def __init__(self, n, lo, hi, bc, cfl, scheme=0):
         """scheme: SCHEME_MH (MUSCL-Hancock + HLL, Sec. 3.3), SCHEME_KT (Kurganov-Tadmor
-        + RK2, Sec. 3.2) or SCHEME_MH_ROE (MUSCL-Hancock with the Roe-type flux)."""
+        + RK2, Sec. 3.2), SCHEME_MH_ROE (MUSCL-Hancock with upwind tracing and the Roe-type
+        flux) or SCHEME_MH_HLLC (MUSCL-Hancock with the HLLC flux)."""
         n = list(n)
         self.ndim = len(n)
         self.n = tuple(n) + (1,) * (3 - len(n))
@@ -239,6 +243,20 @@ def roe_flux(WL, WR, d):
     F = np.zeros(NV)
     _load().og_roe(_p(_f64(WL)), _p(_f64(WR)), int(d), _p(F))
     return F
+
+
+def hllc_flux(WL, WR, d):
+    """HLLC flux between the face states WL and WR (primitive, global order)."""
+    F = np.zeros(NV)
+    _load().og_hllc(_p(_f64(WL)), _p(_f64(WR)), int(d), _p(F))
+    return F
+
+
+def hllc_star(WL, WR, d):
+    """(ok, U*_L, U*_R, (S_L, S_M, S_R)) of the HLLC flux; ok False where HLLC reverts to HLL."""
+    UsL, UsR, S = np.zeros(NV), np.zeros(NV), np.zeros(3)
+    ok = _load().og_hllc_star(_p(_f64(WL)), _p(_f64(WR)), int(d), _p(UsL), _p(UsR), _p(S))
+    return bool(ok), UsL, UsR, tuple(S)
 
 
 def kt_flux(WL, WR, d):
