@@ -454,12 +454,14 @@ def run_suite(args):
             steps = 50 if only is None else args.steps
             mh = grid_rate(p, msh.FP32, steps)
             roe = grid_rate(p, msh.FP32, steps, scheme=msh.MUSCL_HANCOCK_ROE)
+            hllc = grid_rate(p, msh.FP32, steps, scheme=msh.MUSCL_HANCOCK_HLLC)
             kt = grid_rate(p, msh.FP32, steps, scheme=msh.KT)
-            emit({"workload": f"{name} {p.n[0]}^{p.ndim} FP32, CFL 0.4, {steps} steps: MUSCL-Hancock (HLL, Roe-type) "
-                              "vs Kurganov-Tadmor",
-                  "muscl_hancock": mh, "muscl_hancock_roe": roe, "kurganov_tadmor": kt,
+            emit({"workload": f"{name} {p.n[0]}^{p.ndim} FP32, CFL 0.4, {steps} steps: MUSCL-Hancock (HLL, Roe-type, "
+                              "HLLC) vs Kurganov-Tadmor",
+                  "muscl_hancock": mh, "muscl_hancock_roe": roe, "muscl_hancock_hllc": hllc, "kurganov_tadmor": kt,
                   "kt_ms_over_mh_ms": kt["ms_per_step"] / mh["ms_per_step"],
-                  "roe_ms_over_hll_ms": roe["ms_per_step"] / mh["ms_per_step"]})
+                  "roe_ms_over_hll_ms": roe["ms_per_step"] / mh["ms_per_step"],
+                  "hllc_ms_over_hll_ms": hllc["ms_per_step"] / mh["ms_per_step"]})
     # periodic self-gravity: the cost of the FFT Poisson solve and acceleration per step
     if only in (None, "selfgrav"):
         p = inputs.turb(n=args.n or 256)

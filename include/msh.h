@@ -59,6 +59,7 @@ typedef int32_t msh_status;
 #define MSH_SCHEME_MUSCL_HANCOCK 0     /* characteristic MUSCL-Hancock + HLL (Sec. 3.3)     */
 #define MSH_SCHEME_KT 1                /* Kurganov-Tadmor central scheme + RK2 (Sec. 3.2)   */
 #define MSH_SCHEME_MUSCL_HANCOCK_ROE 2 /* characteristic MUSCL-Hancock + Roe-type flux     */
+#define MSH_SCHEME_MUSCL_HANCOCK_HLLC 3 /* characteristic MUSCL-Hancock + HLLC flux        */
 
 #define MSH_HOST 0
 #define MSH_DEVICE 1
@@ -227,11 +228,19 @@ msh_status msh_adjoint_tape(msh_grid *g, const void *dL_dUN, void *dL_dU0, int32
  * (u1 = u + dt L(u), u_new = (u + u1 + dt L(u1)) / 2), the gravity source after them and
  * the same CFL rule; it has no a-posteriori fallback.  Selecting it allocates one more
  * state buffer.  MSH_SCHEME_MUSCL_HANCOCK_ROE is the characteristic step of Sec. 3.3 with
- * a Roe-type flux (Roe 1981) in place of HLL:
+ * the tracing a Riemann solver that resolves every wave takes (eqs 40-43: the reference
+ * states traced with the fastest wave towards each face, each wave that reaches the face
+ * corrected to its own speed; eq 41 in the mirror form of eq 40) and a Roe-type flux
+ * (Roe 1981) in place of HLL:
  *   F = (f(wl) + f(wr)) / 2 - (dU/dW)(wm) R |Lambda| L (wr - wl) / 2,  wm = (wl + wr) / 2,
  * the closed-form eigen-system of wm and Harten's entropy fix on the two fast waves
- * (delta = cf / 10); the a-posteriori fallback as for HLL.  The adjoint (msh_adjoint_run,
- * msh_set_tape) covers MUSCL-Hancock with HLL only: MSH_E_STATE otherwise.
+ * (delta = cf / 10).  MSH_SCHEME_MUSCL_HANCOCK_HLLC is the characteristic step with the
+ * Hancock predictor and a three-wave HLLC flux: outer waves as in HLL, the contact between
+ * them; the pairs (u_i, P_in) take common star values from the momentum jump conditions
+ * across the outer waves, the star states follow from the jump conditions (HLL where the
+ * contact speed is not strictly between the outer ones).  Both have the a-posteriori
+ * fallback of HLL, whose faces with first-order states take the HLL flux.  The adjoint
+ * (msh_adjoint_run, msh_set_tape) covers MUSCL-Hancock with HLL only: MSH_E_STATE otherwise.
  */
 msh_status msh_set_scheme(msh_grid *g, int32_t scheme);
 

@@ -412,15 +412,86 @@ __device__ __forceinline__ void roe_flux(const T (&wl)[NV], const T (&wr)[NV], T
   for (int k = 0; k < NV; k++) F[k] = T(0.5) * (Fl[k] + Fr[k]) - T(0.5) * dU[k];
 }
 
+// ------------------------------------------------------------------- HLLC
+// The part Pi of the normal flux F = u U + Pi (local frame) that depends only on the
+// quantities continuous across a contact, u_i and P_ix:
+//   Pi = (0; P_ix; P_ix u_j + P_jx u_i).
+template <typename T>
+__device__ __forceinline__ void pi_terms(T u, T v, T w, T pxx, T pxy, T pxz, T (&P)[NV]) {
+  P[0] = T(0);
+  P[1] = pxx;
+  P[2] = pxy;
+  P[3] = pxz;
+  P[4] = T(2) * pxx * u;
+  P[5] = pxy * u + pxx * v;
+  P[6] = pxz * u + pxx * w;
+  P[7] = T(2) * pxy * v;
+  P[8] = pxy * w + pxz * v;
+  P[9] = T(2) * pxz * w;
+}
+
+// Three-wave HLLC flux for the ten-moment system (local frame).  Outer waves S_L, S_R as in
+// HLL (they carry the fast and shear waves), the contact S_M in between (it carries rho and
+// the transverse stresses).  Every pair (u_i, P_ix) takes one star value on both sides of
+// the contact, from the momentum jump conditions across S_L and S_R with C_K = rho_K
+// (S_K - u_K):  u*_i = (C_R u_i,R - C_L u_i,L - (P_ix,R - P_ix,L)) / (C_R - C_L),
+// P*_ix = P_ix,L + C_L (u*_i - u_i,L);  S_M = u*_x.  The star state of side K follows from
+// the jump conditions across S_K, U*_K = (U_K (S_K - u_K) + Pi* - Pi_K) / (S_K - S_M), so
+// the flux F_K + S_K (U*_K - U_K) of the side of the face that holds x/t = 0 is
+//   F = a U_K + b Pi_K + c Pi*,  (a, b, c) = (S_M (S_K - u_K), -S_M, S_K) / (S_K - S_M),
+// or (u_K, 1, 0) (the physical flux) when both waves move away from the face.  Where S_M is
+// not strictly inside (S_L, S_R) the flux is HLL's.
+template <typename T>
+__device__ __forceinline__ void hllc_flux(const T (&wl)[NV], const T (&wr)[NV], T (&F)[NV]) {
+  const T cl = T(1.7320508075688772) * sqrt_ratio(wl[4], wl[0]);
+  const T cr = T(1.7320508075688772) * sqrt_ratio(wr[4], wr[0]);
+  const T SL = fmin(wl[1] - cl, wr[1] - cr);
+  const T SR = fmax(wl[1] + cl, wr[1] + cr);
+  const T CL = wl[0] * (SL - wl[1]), CR = wr[0] * (SR - wr[1]);
+  const T inv = frcp(CR - CL);
+  T us[3], ps[3];
+#pragma unroll
+  for (int i = 0; i < 3; i++) {
+    us[i] = (CR * wr[1 + i] - CL * wl[1 + i] - (wr[4 + i] - wl[4 + i])) * inv;
+    ps[i] = wl[4 + i] + CL * (us[i] - wl[1 + i]);
+  }
+  const T SM = us[0];
+  if (!(SL < SM && SM < SR)) {
+    hll(wl, wr, F);
+    return;
+  }
+  const bool left = SM >= T(0);
+  T wk[NV];
+#pragma unroll
+  for (int k = 0; k < NV; k++) wk[k] = left ? wl[k] : wr[k];
+  const T SK = left ? SL : SR, uk = wk[1];
+  T a, b, c;
+  if (SL >= T(0) || SR <= T(0)) {
+    a = uk; b = T(1); c = T(0);
+  } else {
+    const T i2 = frcp(SK - SM);
+    a = SM * (SK - uk) * i2;
+    b = -SM * i2;
+    c = SK * i2;
+  }
+  T Uk[NV], Fk[NV], Pk[NV], Ps[NV];
+  phys(wk, Uk, Fk);
+  pi_terms(wk[1], wk[2], wk[3], wk[4], wk[5], wk[6], Pk);
+  pi_terms(us[0], us[1], us[2], ps[0], ps[1], ps[2], Ps);
+#pragma unroll
+  for (int k = 0; k < NV; k++) F[k] = a * Uk[k] + (b * Pk[k] + c * Ps[k]);
+}
+
 // Scheme of a step kernel: 0 the characteristic MUSCL-Hancock step with HLL (Sec. 3.3);
 // 1 and 2 the two Runge-Kutta stages of the Kurganov-Tadmor scheme (Sec. 3.2); 3 the
-// characteristic step with the Roe-type flux.  0 and 3 have the a-posteriori fallback.
-template <int SCH> constexpr bool kCharacteristic = SCH == 0 || SCH == 3;
+// characteristic step with upwind tracing and the Roe-type flux; 4 the characteristic step
+// with the HLLC flux.  0, 3 and 4 have the a-posteriori fallback.
+template <int SCH> constexpr bool kCharacteristic = SCH == 0 || SCH == 3 || SCH == 4;
 
 template <int SCH, typename T>
 __device__ __forceinline__ void recon(const T (&wm)[NV], const T (&w0)[NV], const T (&wp)[NV], T nu, T (&lo)[NV],
                                       T (&hi)[NV]) {
-  if constexpr (SCH == 0) reconstruct(wm, w0, wp, nu, lo, hi);
+  if constexpr (SCH == 0 || SCH == 4) reconstruct(wm, w0, wp, nu, lo, hi);
   else if constexpr (SCH == 3) reconstruct_upwind(wm, w0, wp, nu, lo, hi);
   else kt_reconstruct(wm, w0, wp, lo, hi);
 }
@@ -429,18 +500,20 @@ template <int SCH, typename T>
 __device__ __forceinline__ void face_flux(const T (&wl)[NV], const T (&wr)[NV], T (&F)[NV]) {
   if constexpr (SCH == 0) hll(wl, wr, F);
   else if constexpr (SCH == 3) roe_flux(wl, wr, F);
+  else if constexpr (SCH == 4) hllc_flux(wl, wr, F);
   else kt_flux(wl, wr, F);
 }
 
 // Flux through a face in a step pass: in a fallback pass (RETRY) a face with first-order
-// states (it touches a tagged cell) takes HLL under the Roe-type scheme too.  The fallback
-// has to make the update realizable; HLL with bounding wave speeds is positively
-// conservative, a linearised Roe flux is not (Einfeldt, Munz, Roe & Sjogreen 1991).
+// states (it touches a tagged cell) takes HLL under the Roe-type and HLLC schemes too.  The
+// fallback has to make the update realizable; HLL with bounding wave speeds is positively
+// conservative, a linearised Roe flux is not (Einfeldt, Munz, Roe & Sjogreen 1991), and
+// HLLC's star states, formed from jump conditions, need not be realizable.
 template <int SCH, bool RETRY, typename T>
 __device__ __forceinline__ void face_flux(const T (&wl)[NV], const T (&wr)[NV], bool first, T (&F)[NV]) {
-  if constexpr (SCH == 3 && RETRY) {
+  if constexpr ((SCH == 3 || SCH == 4) && RETRY) {
     if (first) hll(wl, wr, F);
-    else roe_flux(wl, wr, F);
+    else face_flux<SCH>(wl, wr, F);
   } else {
     face_flux<SCH>(wl, wr, F);
   }

@@ -134,6 +134,16 @@ void free_tape(msh_grid *g) {
   g->tape_valid = false;
 }
 
+// One pass of the characteristic step with the grid's flux (HLL, Roe-type or HLLC).
+template <typename T>
+static cudaError_t launch_characteristic(msh_grid *g, const StepArgs<T> &a, bool retry, int *nblocks_out) {
+  if (g->scheme == MSH_SCHEME_MUSCL_HANCOCK_ROE)
+    return launch_step_roe<T>(a, g->ndim, g->rows, retry, g->stream, nblocks_out);
+  if (g->scheme == MSH_SCHEME_MUSCL_HANCOCK_HLLC)
+    return launch_step_hllc<T>(a, g->ndim, g->rows, retry, g->stream, nblocks_out);
+  return launch_step<T>(a, g->ndim, g->rows, retry, g->stream, nblocks_out);
+}
+
 msh_status launch_one_step(msh_grid *g, int ev_slot) {
   int nb = 0;
   cudaError_t e;
@@ -157,21 +167,18 @@ msh_status launch_one_step(msh_grid *g, int ev_slot) {
     if (g->profiling && ev_slot >= 0) CUDA_TRY(cudaEventRecord(g->ev[3 * ev_slot + 2], g->stream));
     return MSH_OK;
   }
-  // the characteristic step (HLL or Roe-type flux), then its fallback passes: each returns at
-  // once unless the previous pass tagged new cells
-  const bool roe = g->scheme == MSH_SCHEME_MUSCL_HANCOCK_ROE;
+  // the characteristic step (HLL, Roe-type or HLLC flux), then its fallback passes: each
+  // returns at once unless the previous pass tagged new cells
   for (int level = 0; level <= kFallbackPasses; level++) {
     const bool retry = level > 0;
     if (g->prec == MSH_FP32) {
       StepArgs<float> a = make_args<float>(g);
       a.level = level;
-      e = roe ? launch_step_roe<float>(a, g->ndim, g->rows, retry, g->stream, retry ? nullptr : &nb)
-              : launch_step<float>(a, g->ndim, g->rows, retry, g->stream, retry ? nullptr : &nb);
+      e = launch_characteristic(g, a, retry, retry ? nullptr : &nb);
     } else {
       StepArgs<double> a = make_args<double>(g);
       a.level = level;
-      e = roe ? launch_step_roe<double>(a, g->ndim, g->rows, retry, g->stream, retry ? nullptr : &nb)
-              : launch_step<double>(a, g->ndim, g->rows, retry, g->stream, retry ? nullptr : &nb);
+      e = launch_characteristic(g, a, retry, retry ? nullptr : &nb);
     }
     if (e != cudaSuccess)
       return fail(MSH_E_CUDA, "%s kernel launch: %s", retry ? "fallback" : "step", cudaGetErrorString(e));
@@ -500,7 +507,8 @@ msh_status msh_set_potential(msh_grid *g, const double *phi, int32_t where) {
 msh_status msh_set_scheme(msh_grid *g, int32_t scheme) {
   begin();
   if (!g) return fail(MSH_E_INVALID_ARG, "null grid");
-  if (scheme != MSH_SCHEME_MUSCL_HANCOCK && scheme != MSH_SCHEME_KT && scheme != MSH_SCHEME_MUSCL_HANCOCK_ROE)
+  if (scheme != MSH_SCHEME_MUSCL_HANCOCK && scheme != MSH_SCHEME_KT && scheme != MSH_SCHEME_MUSCL_HANCOCK_ROE &&
+      scheme != MSH_SCHEME_MUSCL_HANCOCK_HLLC)
     return fail(MSH_E_INVALID_ARG, "unknown scheme");
   if (scheme != MSH_SCHEME_MUSCL_HANCOCK && g->tape_valid)
     return fail(MSH_E_STATE, "the adjoint tape covers the MUSCL-Hancock scheme with HLL only");

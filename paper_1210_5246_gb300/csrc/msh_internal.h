@@ -77,6 +77,8 @@ template <typename T> cudaError_t launch_step(const StepArgs<T> &a, int ndim, in
 // the characteristic step with the Roe-type flux (same contract as launch_step)
 template <typename T> cudaError_t launch_step_roe(const StepArgs<T> &a, int ndim, int rows, bool retry, cudaStream_t s,
                                                   int *nblocks_out);
+template <typename T> cudaError_t launch_step_hllc(const StepArgs<T> &a, int ndim, int rows, bool retry, cudaStream_t s,
+                                                  int *nblocks_out);
 // stage 1 or 2 of the Kurganov-Tadmor scheme (a.U1 must be set)
 template <typename T> cudaError_t launch_step_kt(const StepArgs<T> &a, int ndim, int rows, int stage, cudaStream_t s);
 template <typename T> int step_blocks(int ndim, int rows, int nx, int ny, int nz, int zchunk);

@@ -20,7 +20,7 @@ from . import build as _build
 MSH_OK, MSH_E_INVALID_ARG, MSH_E_CUDA, MSH_E_NOMEM, MSH_E_REALIZABILITY, MSH_E_TIMEOUT, MSH_E_STATE = range(7)
 PERIODIC, OUTFLOW, REFLECT = 0, 1, 2
 FP32, FP64 = 0, 1
-MUSCL_HANCOCK, KT, MUSCL_HANCOCK_ROE = 0, 1, 2
+MUSCL_HANCOCK, KT, MUSCL_HANCOCK_ROE, MUSCL_HANCOCK_HLLC = 0, 1, 2, 3
 HOST, DEVICE = 0, 1
 CONSERVED, PRIMITIVE = 0, 1
 
@@ -317,7 +317,8 @@ class Grid:
         _check(load().msh_set_self_gravity(self.h, float(G)))
 
     def set_scheme(self, scheme):
-        """MUSCL_HANCOCK (default, HLL), MUSCL_HANCOCK_ROE or KT (see ``msh_set_scheme``)."""
+        """MUSCL_HANCOCK (default, HLL), MUSCL_HANCOCK_ROE, MUSCL_HANCOCK_HLLC or KT (see
+        ``msh_set_scheme``)."""
         _check(load().msh_set_scheme(self.h, int(scheme)))
 
     # -- slab decomposition -------------------------------------------------------

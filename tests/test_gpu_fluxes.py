@@ -1,7 +1,7 @@
-"""The characteristic step with the Roe-type flux on the GPU against the oracle's: FP64 <=
-1e-10 relative L_inf per field, FP32 within the FP32 tolerances; 1D/2D/3D, every boundary
-kind, tile shapes, gravity, the a-posteriori fallback; a stationary contact stays exact;
-the adjoint refuses the scheme."""
+"""The characteristic step with the Roe-type flux (upwind tracing) and with the HLLC flux on
+the GPU against the oracle's: FP64 <= 1e-10 relative L_inf per field, FP32 within the FP32
+tolerances; 1D/2D/3D, every boundary kind, tile shapes, gravity, the a-posteriori fallback,
+supersonic drifts; a stationary contact stays exact; the adjoint refuses both schemes."""
 import numpy as np
 import pytest
 
@@ -9,7 +9,8 @@ from tests.parity import assert_fp32, assert_fp64
 from tests.test_gpu_parity import _extreme
 
 pytestmark = pytest.mark.gpu
-ROE = 2
+# (name of the scheme in the binding, oracle scheme number)
+SCHEMES = [("MUSCL_HANCOCK_ROE", 2), ("MUSCL_HANCOCK_HLLC", 3)]
 
 
 @pytest.fixture(scope="module")
@@ -21,9 +22,14 @@ def env():
     return msh, inputs
 
 
-def _run(msh, oracle, n, lo, hi, bc, cfl, W, precision, steps=None, t_end=np.inf, phi=None, tiling=None):
+@pytest.fixture(params=SCHEMES, ids=[s[0] for s in SCHEMES])
+def scheme(request):
+    return request.param
+
+
+def _run(msh, oracle, scheme, n, lo, hi, bc, cfl, W, precision, steps=None, t_end=np.inf, phi=None, tiling=None):
     g = msh.Grid(n, lo, hi, bc, cfl, precision)
-    g.set_scheme(msh.MUSCL_HANCOCK_ROE)
+    g.set_scheme(getattr(msh, scheme[0]))
     if phi is not None:
         g.set_potential(phi)
     if tiling:
@@ -33,7 +39,7 @@ def _run(msh, oracle, n, lo, hi, bc, cfl, W, precision, steps=None, t_end=np.inf
     ns, t = g.run(t_end, steps if steps is not None else (1 << 62))
     U, Wout = g.get_state().astype(np.float64), g.get_state(msh.PRIMITIVE).astype(np.float64)
     g.close()
-    og = oracle.Grid(n, lo, hi, bc, cfl, scheme=ROE)
+    og = oracle.Grid(n, lo, hi, bc, cfl, scheme=scheme[1])
     Uo, no, to, rc, _ = oracle.run(og, oracle.prim_to_cons(Wg.astype(np.float64)), t_end,
                                    max_steps=steps if steps is not None else (1 << 62), phi=phi)
     assert rc == 0 and ns == no and abs(t - to) <= (1e-13 if precision == msh.FP64 else 1e-5) * to
@@ -51,85 +57,85 @@ def _random(shape, seed):
     return W
 
 
-def test_sod(env, oracle):
+def test_sod(env, oracle, scheme):
     msh, I = env
     p = I.sod(256)
-    U, _, Uo, _ = _run(msh, oracle, p.n, p.lo, p.hi, p.bc, p.cfl, p.W, msh.FP64, t_end=p.t_end)
-    assert_fp64(U, Uo, what="roe sod fp64")
-    _, W, _, Wo = _run(msh, oracle, p.n, p.lo, p.hi, p.bc, p.cfl, p.W, msh.FP32, t_end=p.t_end)
-    assert_fp32(W, Wo, what="roe sod fp32")
+    U, _, Uo, _ = _run(msh, oracle, scheme, p.n, p.lo, p.hi, p.bc, p.cfl, p.W, msh.FP64, t_end=p.t_end)
+    assert_fp64(U, Uo, what=f"{scheme[0]} sod fp64")
+    _, W, _, Wo = _run(msh, oracle, scheme, p.n, p.lo, p.hi, p.bc, p.cfl, p.W, msh.FP32, t_end=p.t_end)
+    assert_fp32(W, Wo, what=f"{scheme[0]} sod fp32")
 
 
 @pytest.mark.parametrize("n,bc", [(5, (0, 0)), (127, (1, 2)), (300, (2, 1))])
-def test_1d(env, oracle, n, bc):
+def test_1d(env, oracle, scheme, n, bc):
     msh, _ = env
-    U, _, Uo, _ = _run(msh, oracle, (n,), (0.0,), (1.0,), (bc,), 0.5, _random((1, 1, n), n), msh.FP64, steps=7)
-    assert_fp64(U, Uo, what=f"roe 1d {n}")
+    U, _, Uo, _ = _run(msh, oracle, scheme, (n,), (0.0,), (1.0,), (bc,), 0.5, _random((1, 1, n), n), msh.FP64, steps=7)
+    assert_fp64(U, Uo, what=f"{scheme[0]} 1d {n}")
 
 
 @pytest.mark.parametrize("tiling", [(4, 8), (16, 64)])
-def test_blast(env, oracle, tiling):
+def test_blast(env, oracle, scheme, tiling):
     msh, I = env
     p = I.blast(n=97, nsteps=15)
-    U, _, Uo, _ = _run(msh, oracle, p.n, p.lo, p.hi, p.bc, p.cfl, p.W, msh.FP64, steps=15, tiling=tiling)
-    assert_fp64(U, Uo, what=f"roe blast {tiling}")
+    U, _, Uo, _ = _run(msh, oracle, scheme, p.n, p.lo, p.hi, p.bc, p.cfl, p.W, msh.FP64, steps=15, tiling=tiling)
+    assert_fp64(U, Uo, what=f"{scheme[0]} blast {tiling}")
 
 
-def test_blast_fp32(env, oracle):
+def test_blast_fp32(env, oracle, scheme):
     msh, I = env
     p = I.blast(n=97, nsteps=15)
-    _, W, _, Wo = _run(msh, oracle, p.n, p.lo, p.hi, p.bc, p.cfl, p.W, msh.FP32, steps=15)
-    assert_fp32(W, Wo, what="roe blast fp32")
+    _, W, _, Wo = _run(msh, oracle, scheme, p.n, p.lo, p.hi, p.bc, p.cfl, p.W, msh.FP32, steps=15)
+    assert_fp32(W, Wo, what=f"{scheme[0]} blast fp32")
 
 
 @pytest.mark.parametrize("shape,bc", [((31, 7), ((1, 1), (2, 2))), ((61, 45), ((2, 2), (1, 2)))])
-def test_2d_shapes(env, oracle, shape, bc):
+def test_2d_shapes(env, oracle, scheme, shape, bc):
     msh, _ = env
     W = _random((1, shape[1], shape[0]), shape[0] * 100 + shape[1])
-    U, _, Uo, _ = _run(msh, oracle, shape, (0.0, 0.0), (1.0, 2.0), bc, 0.5, W, msh.FP64, steps=5)
-    assert_fp64(U, Uo, what=f"roe 2d {shape}")
+    U, _, Uo, _ = _run(msh, oracle, scheme, shape, (0.0, 0.0), (1.0, 2.0), bc, 0.5, W, msh.FP64, steps=5)
+    assert_fp64(U, Uo, what=f"{scheme[0]} 2d {shape}")
 
 
 @pytest.mark.parametrize("tiling", [(8, 32), (4, 5)])
-def test_turb(env, oracle, tiling):
+def test_turb(env, oracle, scheme, tiling):
     msh, I = env
     p = I.turb(n=24, nsteps=5)
-    U, _, Uo, _ = _run(msh, oracle, p.n, p.lo, p.hi, p.bc, p.cfl, p.W, msh.FP64, steps=5, tiling=tiling)
-    assert_fp64(U, Uo, what=f"roe turb {tiling}")
+    U, _, Uo, _ = _run(msh, oracle, scheme, p.n, p.lo, p.hi, p.bc, p.cfl, p.W, msh.FP64, steps=5, tiling=tiling)
+    assert_fp64(U, Uo, what=f"{scheme[0]} turb {tiling}")
 
 
-def test_turb_fp32_rows16(env, oracle):
+def test_turb_fp32_rows16(env, oracle, scheme):
     msh, I = env
     p = I.turb(n=32, nsteps=8)
-    _, W, _, Wo = _run(msh, oracle, p.n, p.lo, p.hi, p.bc, p.cfl, p.W, msh.FP32, steps=8, tiling=(16, 7))
-    assert_fp32(W, Wo, what="roe turb fp32")
+    _, W, _, Wo = _run(msh, oracle, scheme, p.n, p.lo, p.hi, p.bc, p.cfl, p.W, msh.FP32, steps=8, tiling=(16, 7))
+    assert_fp32(W, Wo, what=f"{scheme[0]} turb fp32")
 
 
-def test_3d_shapes(env, oracle):
+def test_3d_shapes(env, oracle, scheme):
     msh, _ = env
     shape, bc = (33, 17, 9), ((1, 2), (2, 1), (0, 0))
     W = _random((9, 17, 33), 99)
-    U, _, Uo, _ = _run(msh, oracle, shape, (0, 0, 0), (1, 1.5, 0.5), bc, 0.5, W, msh.FP64, steps=4, tiling=(8, 4))
-    assert_fp64(U, Uo, what="roe 3d")
+    U, _, Uo, _ = _run(msh, oracle, scheme, shape, (0, 0, 0), (1, 1.5, 0.5), bc, 0.5, W, msh.FP64, steps=4, tiling=(8, 4))
+    assert_fp64(U, Uo, what=f"{scheme[0]} 3d")
 
 
-def test_disc_gravity(env, oracle):
+def test_disc_gravity(env, oracle, scheme):
     msh, I = env
     p = I.disc(n=64, nsteps=15)
-    U, _, Uo, _ = _run(msh, oracle, p.n, p.lo, p.hi, p.bc, p.cfl, p.W, msh.FP64, steps=15, phi=p.phi)
-    assert_fp64(U, Uo, what="roe disc")
+    U, _, Uo, _ = _run(msh, oracle, scheme, p.n, p.lo, p.hi, p.bc, p.cfl, p.W, msh.FP64, steps=15, phi=p.phi)
+    assert_fp64(U, Uo, what=f"{scheme[0]} disc")
 
 
 @pytest.mark.parametrize("shape,n,bc,cfl", [((1, 12, 12), (12, 12), ((0, 0), (1, 2)), 0.5),
                                             ((6, 7, 9), (9, 7, 6), ((2, 1), (0, 0), (1, 1)), 0.5)])
-def test_fallback(env, oracle, shape, n, bc, cfl):
+def test_fallback(env, oracle, scheme, shape, n, bc, cfl):
     msh, _ = env
     nd = len(n)
-    U, _, Uo, _ = _run(msh, oracle, n, (0,) * nd, (1,) * nd, bc, cfl, _extreme(shape, 0), msh.FP64, steps=20)
-    assert_fp64(U, Uo, what=f"roe fallback {n}")
+    U, _, Uo, _ = _run(msh, oracle, scheme, n, (0,) * nd, (1,) * nd, bc, cfl, _extreme(shape, 0), msh.FP64, steps=20)
+    assert_fp64(U, Uo, what=f"{scheme[0]} fallback {n}")
 
 
-def test_stationary_contact_is_exact(env):
+def test_stationary_contact_is_exact(env, scheme):
     msh, _ = env
     n = 64
     x = (np.arange(n) + 0.5) / n
@@ -139,7 +145,7 @@ def test_stationary_contact_is_exact(env):
     W[5] = 0.1
     for prec in (msh.FP64, msh.FP32):
         g = msh.Grid((n,), (0.0,), (1.0,), ((0, 0),), 0.5, prec)
-        g.set_scheme(msh.MUSCL_HANCOCK_ROE)
+        g.set_scheme(getattr(msh, scheme[0]))
         g.set_state(W.astype(g.dtype), msh.PRIMITIVE)
         g.run(max_steps=40)
         rho = g.get_state(msh.PRIMITIVE)[0, 0, 0].astype(np.float64)
@@ -147,12 +153,12 @@ def test_stationary_contact_is_exact(env):
         g.close()
 
 
-def test_adjoint_refuses_roe(env):
+def test_adjoint_refuses_scheme(env, scheme):
     msh, I = env
     p = I.sod(32)
     g = msh.Grid.from_problem(p, msh.FP64)
     g.set_state(p.W, msh.PRIMITIVE)
-    g.set_scheme(msh.MUSCL_HANCOCK_ROE)
+    g.set_scheme(getattr(msh, scheme[0]))
     U0 = g.get_state()
     with pytest.raises(msh.MshError) as ei:
         g.adjoint_run(U0, [1e-3], U0, K=1)
@@ -161,12 +167,12 @@ def test_adjoint_refuses_roe(env):
 
 
 @pytest.mark.parametrize("sgn", [1.0, -1.0])
-def test_supersonic_drift(env, oracle, sgn):
+def test_supersonic_drift(env, oracle, scheme, sgn):
     """Every wave moving one way (|u|, |v| > cf): the one-sided branches of the upwind tracing."""
     msh, _ = env
     shape = (1, 19, 37)
     W = _random(shape, 5)
     W[1] += sgn * 3.0 * np.sqrt(3 * W[4] / W[0])
     W[2] -= sgn * 3.0 * np.sqrt(3 * W[7] / W[0])
-    U, _, Uo, _ = _run(msh, oracle, (37, 19), (0.0, 0.0), (1.0, 1.0), ((0, 0), (1, 1)), 0.5, W, msh.FP64, steps=6)
-    assert_fp64(U, Uo, what=f"roe supersonic {sgn}")
+    U, _, Uo, _ = _run(msh, oracle, scheme, (37, 19), (0.0, 0.0), (1.0, 1.0), ((0, 0), (1, 1)), 0.5, W, msh.FP64, steps=6)
+    assert_fp64(U, Uo, what=f"{scheme[0]} supersonic {sgn}")
