@@ -142,6 +142,29 @@ msh_status msh_step(msh_grid *g, double dt_max, double *dt_taken);
 msh_status msh_run(msh_grid *g, double t_end, int64_t max_steps, int64_t *steps, double *t_out);
 
 /*
+ * Ensemble of independent states through host memory: each of the `count` states is
+ * uploaded, advanced from t = 0 by exactly `nsteps` CFL steps of the grid's scheme (same
+ * geometry, boundaries, potential, self-gravity and CFL number as msh_run; Sec. 3.3 per
+ * step) and downloaded.  Uploads, steps and downloads of different states overlap: four
+ * device slots of one state each, a copy-in and a copy-out stream besides the grid's
+ * stream.
+ *   in[k]    host pointer to state k, [10][nz][ny][nx] in the grid's precision, `kind`
+ *            (MSH_CONSERVED or MSH_PRIMITIVE); page-locked memory lets the copies overlap
+ *   out[k]   host pointer receiving the result of state k (same layout and kind); no out[j]
+ *            may overlap any in[k] (a download can run during a later upload); out[j] may
+ *            repeat (downloads run in order)
+ *   status   NULL or count int32: MSH_OK, or MSH_E_REALIZABILITY if state k's input was not
+ *            realizable (it is not stepped) or one of its steps produced a non-realizable
+ *            cell; the content of out[k] is then unspecified
+ * Returns MSH_E_INVALID_ARG (null pointers, count < 0, nsteps < 1), MSH_E_NOMEM (four
+ * more state buffers), MSH_E_REALIZABILITY if any state failed (the others are complete),
+ * MSH_E_CUDA.  Afterwards the grid holds the last state's result, its time and a step
+ * counter advanced by count * nsteps; a recording tape ends (as with msh_set_state).
+ */
+msh_status msh_run_ensemble(msh_grid *g, int64_t count, const void *const *in, void *const *out, int32_t kind,
+                            int64_t nsteps, int32_t *status);
+
+/*
  * FP64 totals of the ten conserved fields over the grid (pairwise reduced, fixed order)
  * as of the last step or set_state, realizability flag (1 = every cell has rho > 0 and
  * P positive definite) and the first offending cell's linear index (-1 if none).

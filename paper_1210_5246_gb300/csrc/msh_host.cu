@@ -5,6 +5,7 @@
 // graph holding kGraphSteps consecutive (step, finalize) launch pairs.  msh_run launches
 // that graph until the device control block reports completion; kernels of a finished
 // run return immediately, so over-launching past t_end is harmless.
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstddef>
@@ -252,6 +253,51 @@ msh_status prime(msh_grid *g, int which) {
 
 int cur_buf(msh_grid *g) { return (int)(g->hctrl->step & 1); }
 
+void free_ensemble(msh_grid *g) {
+  if (g->ens_in) cudaStreamSynchronize(g->ens_in);
+  if (g->ens_out) cudaStreamSynchronize(g->ens_out);
+  for (auto &b : g->ens_slot) {
+    if (b) cudaFree(b);
+    b = nullptr;
+  }
+  for (auto &e : g->ens_ev) {
+    if (e) cudaEventDestroy(e);
+    e = nullptr;
+  }
+  if (g->ens_in) cudaStreamDestroy(g->ens_in);
+  if (g->ens_out) cudaStreamDestroy(g->ens_out);
+  if (g->ens_status) cudaFree(g->ens_status);
+  g->ens_in = g->ens_out = nullptr;
+  g->ens_status = nullptr;
+  g->ens_status_cap = 0;
+}
+
+// Slots, streams, events and a status array for `count` states.
+msh_status ensure_ensemble(msh_grid *g, int64_t count) {
+  const size_t bytes = g->N * 10 * g->esize;
+  for (auto &b : g->ens_slot)
+    if (!b && cudaMalloc(&b, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      free_ensemble(g);
+      return fail(MSH_E_NOMEM, "ensemble slots (%d x %zu bytes)", kEnsembleSlots, bytes);
+    }
+  if (!g->ens_in) CUDA_TRY(cudaStreamCreateWithFlags(&g->ens_in, cudaStreamNonBlocking));
+  if (!g->ens_out) CUDA_TRY(cudaStreamCreateWithFlags(&g->ens_out, cudaStreamNonBlocking));
+  for (auto &e : g->ens_ev)
+    if (!e) CUDA_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+  if (g->ens_status_cap < count) {
+    if (g->ens_status) cudaFree(g->ens_status);
+    g->ens_status = nullptr;
+    g->ens_status_cap = 0;
+    if (cudaMalloc(&g->ens_status, sizeof(int32_t) * (size_t)count) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(MSH_E_NOMEM, "ensemble statuses");
+    }
+    g->ens_status_cap = count;
+  }
+  return MSH_OK;
+}
+
 // After msh_set_slab the planned CFL step belongs to the state before the copy.
 msh_status refresh_dt(msh_grid *g) {
   if (!g->dt_stale) return MSH_OK;
@@ -385,6 +431,7 @@ msh_status msh_destroy(msh_grid *g) {
   if (g->U1) cudaFree(g->U1);
   free_self_gravity(g);
   free_tape(g);
+  free_ensemble(g);
   if (g->own_stream && g->stream) cudaStreamDestroy(g->stream);
   delete g;
   return MSH_OK;
@@ -444,6 +491,87 @@ msh_status msh_get_state(msh_grid *g, void *U, int32_t where, int32_t kind) {
   CUDA_TRY(cudaMemcpyAsync(U, src, bytes, where == MSH_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice,
                            g->stream));
   CUDA_TRY(cudaStreamSynchronize(g->stream));
+  return MSH_OK;
+}
+
+msh_status msh_run_ensemble(msh_grid *g, int64_t count, const void *const *in, void *const *out, int32_t kind,
+                            int64_t nsteps, int32_t *status) {
+  begin();
+  if (!g || (count > 0 && (!in || !out))) return fail(MSH_E_INVALID_ARG, "null argument");
+  if (count < 0 || nsteps < 1) return fail(MSH_E_INVALID_ARG, "count must be >= 0 and nsteps >= 1");
+  if (kind != MSH_CONSERVED && kind != MSH_PRIMITIVE) return fail(MSH_E_INVALID_ARG, "bad kind");
+  for (int64_t k = 0; k < count; k++)
+    if (!in[k] || !out[k]) return fail(MSH_E_INVALID_ARG, "null state pointer %lld", (long long)k);
+  if (count == 0) return MSH_OK;
+  msh_status st = stop_tape(g);
+  if (st) return st;
+  st = ensure_ensemble(g, count);
+  if (st) return st;
+  st = ensure_partials(g, std::max(kScanBlocks, blocks_for(g, g->rows, g->zchunk)));
+  if (st) return st;
+  const size_t bytes = g->N * 10 * g->esize;
+  const bool fp32 = g->prec == MSH_FP32;
+  // the device step counter continues from the grid's; state k starts at base + k * nsteps,
+  // so its input goes to buffer (step & 1) and its result comes from ((step + nsteps) & 1)
+  int64_t base = g->hctrl->step;
+  cudaEvent_t *ev_in = g->ens_ev, *ev_done = g->ens_ev + kEnsembleSlots, *ev_free = g->ens_ev + 2 * kEnsembleSlots;
+  for (int64_t k = 0; k < count; k++) {
+    const int j = (int)(k % kEnsembleSlots);
+    void *slot = g->ens_slot[j];
+    // upload: slot j is free once the download of state k - kEnsembleSlots has finished
+    if (k >= kEnsembleSlots) CUDA_TRY(cudaStreamWaitEvent(g->ens_in, ev_free[j], 0));
+    CUDA_TRY(cudaMemcpyAsync(slot, in[k], bytes, cudaMemcpyHostToDevice, g->ens_in));
+    CUDA_TRY(cudaEventRecord(ev_in[j], g->ens_in));
+    // the steps, on the grid's stream
+    CUDA_TRY(cudaStreamWaitEvent(g->stream, ev_in[j], 0));
+    cudaError_t e = cudaSuccess;
+    if (kind == MSH_PRIMITIVE)
+      e = fp32 ? launch_convert<float>((float *)slot, g->N, 0, g->stream)
+               : launch_convert<double>((double *)slot, g->N, 0, g->stream);
+    if (e != cudaSuccess) return fail(MSH_E_CUDA, "convert: %s", cudaGetErrorString(e));
+    const int64_t s0 = base + k * nsteps;
+    void *src = g->U[s0 & 1];
+    CUDA_TRY(cudaMemcpyAsync(src, slot, bytes, cudaMemcpyDeviceToDevice, g->stream));
+    e = fp32 ? launch_scan<float>((const float *)src, g->N, (int)g->n[0], (int)g->n[1], g->ndim, g->dx, g->part,
+                                  kScanBlocks, g->stream)
+             : launch_scan<double>((const double *)src, g->N, (int)g->n[0], (int)g->n[1], g->ndim, g->dx, g->part,
+                                   kScanBlocks, g->stream);
+    if (e == cudaSuccess) e = launch_finalize(g->ctrl, g->part, kScanBlocks, 1, g->stream);
+    if (e == cudaSuccess) e = launch_ensemble_start(g->ctrl, s0, nsteps, g->ens_status + k, g->stream);
+    if (e != cudaSuccess) return fail(MSH_E_CUDA, "ensemble start: %s", cudaGetErrorString(e));
+    for (int64_t i = 0; i < nsteps; i++) {
+      st = launch_one_step(g, -1);
+      if (st) return st;
+    }
+    e = launch_ensemble_end(g->ctrl, g->ens_status + k, g->stream);
+    if (e != cudaSuccess) return fail(MSH_E_CUDA, "ensemble end: %s", cudaGetErrorString(e));
+    CUDA_TRY(cudaMemcpyAsync(slot, g->U[(s0 + nsteps) & 1], bytes, cudaMemcpyDeviceToDevice, g->stream));
+    if (kind == MSH_PRIMITIVE)
+      e = fp32 ? launch_convert<float>((float *)slot, g->N, 1, g->stream)
+               : launch_convert<double>((double *)slot, g->N, 1, g->stream);
+    if (e != cudaSuccess) return fail(MSH_E_CUDA, "convert: %s", cudaGetErrorString(e));
+    CUDA_TRY(cudaEventRecord(ev_done[j], g->stream));
+    // download
+    CUDA_TRY(cudaStreamWaitEvent(g->ens_out, ev_done[j], 0));
+    CUDA_TRY(cudaMemcpyAsync(out[k], slot, bytes, cudaMemcpyDeviceToHost, g->ens_out));
+    CUDA_TRY(cudaEventRecord(ev_free[j], g->ens_out));
+  }
+  CUDA_TRY(cudaStreamSynchronize(g->ens_out));
+  CUDA_TRY(cudaStreamSynchronize(g->stream));
+  std::vector<int32_t> hs((size_t)count);
+  CUDA_TRY(cudaMemcpy(hs.data(), g->ens_status, sizeof(int32_t) * (size_t)count, cudaMemcpyDeviceToHost));
+  st = read_ctrl(g);
+  if (st) return st;
+  // the grid now holds the last state's result
+  g->has_state = true;
+  g->hctrl->sg_hist = 0;
+  int64_t first_bad = -1;
+  for (int64_t k = 0; k < count; k++) {
+    if (status) status[k] = hs[(size_t)k];
+    if (hs[(size_t)k] != 0 && first_bad < 0) first_bad = k;
+  }
+  if (first_bad >= 0)
+    return fail(MSH_E_REALIZABILITY, "ensemble state %lld is not realizable (input or result)", (long long)first_bad);
   return MSH_OK;
 }
 

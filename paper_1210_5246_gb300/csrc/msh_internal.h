@@ -90,11 +90,16 @@ template <typename T> cudaError_t launch_scan(const T *U, size_t N, int nx, int 
 cudaError_t launch_set_dt(Ctrl *ctrl, double dt, cudaStream_t s);
 cudaError_t launch_finalize(Ctrl *ctrl, const Partial *part, int nparts, int mode, cudaStream_t s);
 cudaError_t launch_run_start(Ctrl *ctrl, double t_end, int64_t max_steps, double dt_max, cudaStream_t s);
+cudaError_t launch_ensemble_start(Ctrl *ctrl, int64_t step_base, int64_t nsteps, int32_t *status, cudaStream_t s);
+cudaError_t launch_ensemble_end(const Ctrl *ctrl, int32_t *status, cudaStream_t s);
 template <typename T> cudaError_t launch_convert(T *U, size_t N, int to_primitive, cudaStream_t s);
 template <typename T> cudaError_t launch_gravity_field(const double *phi, T *acc, int ndim, int nx, int ny, int nz,
                                                        const double *dx, cudaStream_t s);
 
 constexpr int kScanBlocks = 608;  // 4 x 152 SMs
+// States in flight in an ensemble run: one uploading, one computing, one downloading and
+// one spare, so that no stage waits for a slot while the other two are busy.
+constexpr int kEnsembleSlots = 4;
 
 // Thread-local error text behind msh_last_error(), shared by every translation unit.
 // clear_error() also resets a stale non-sticky CUDA error so that the cudaGetLastError()
@@ -159,6 +164,13 @@ struct msh_grid {
   double prof_ms = 0.0;      // summed step-kernel time
   double prof_fin_ms = 0.0;  // summed time from the step kernel's end to the finalize kernel's end
   int64_t prof_launches = 0;
+  // ensemble runs: kEnsembleSlots device slots of one state each, copy-in and copy-out
+  // streams, per-slot events (uploaded, result ready, downloaded) and per-state statuses
+  void *ens_slot[msh::kEnsembleSlots] = {};
+  cudaStream_t ens_in = nullptr, ens_out = nullptr;
+  cudaEvent_t ens_ev[3 * msh::kEnsembleSlots] = {};
+  int32_t *ens_status = nullptr;
+  int64_t ens_status_cap = 0;
 };
 
 namespace msh {

@@ -150,6 +150,44 @@ __global__ void run_start_kernel(Ctrl *c, double t_end, int64_t max_steps, doubl
   plan(c);
 }
 
+// Ensemble runs: after the scan of a new state (finalize mode 1), start it at t = 0 with the
+// step counter at step_base (the host knows every state's base, hence its buffer parity and
+// fallback tags, without reading the device); a non-realizable input is not stepped and its
+// status is MSH_E_REALIZABILITY.  ensemble_end records the status of the state's steps.
+__global__ void ensemble_start_kernel(Ctrl *c, int64_t step_base, int64_t nsteps, int32_t *status) {
+  c->t = 0.0;
+  c->step = step_base;
+  c->sg_hist = 0;  // a new state has no previous self-gravity acceleration
+  for (int p = 0; p <= kFallbackPasses; p++) c->nbad[p] = 0;
+  if (!c->realizable) {
+    c->done = 1;
+    c->status = 4;  // MSH_E_REALIZABILITY
+    *status = 4;
+    return;
+  }
+  *status = 0;
+  c->t_end = INFINITY;
+  c->max_step = step_base + nsteps;
+  c->dt_max = INFINITY;
+  c->done = 0;
+  c->status = 0;
+  plan(c);
+}
+
+__global__ void ensemble_end_kernel(const Ctrl *c, int32_t *status) {
+  if (*status == 0) *status = c->status;
+}
+
+cudaError_t launch_ensemble_start(Ctrl *ctrl, int64_t step_base, int64_t nsteps, int32_t *status, cudaStream_t s) {
+  ensemble_start_kernel<<<1, 1, 0, s>>>(ctrl, step_base, nsteps, status);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ensemble_end(const Ctrl *ctrl, int32_t *status, cudaStream_t s) {
+  ensemble_end_kernel<<<1, 1, 0, s>>>(ctrl, status);
+  return cudaGetLastError();
+}
+
 // ------------------------------------------------------------- conversions
 template <typename T>
 __global__ void convert_kernel(T *U, size_t N, int to_primitive) {

@@ -52,6 +52,7 @@ SIGNATURES = {
     "msh_set_potential": [_vp, _vp, _i32],
     "msh_step": [_vp, _dbl, _P(_dbl)],
     "msh_run": [_vp, _dbl, _i64, _P(_i64), _P(_dbl)],
+    "msh_run_ensemble": [_vp, _i64, _P(_vp), _P(_vp), _i32, _i64, _P(_i32)],
     "msh_diagnostics": [_vp, _P(_dbl), _P(_i32), _P(_i64)],
     "msh_set_recording": [_vp, _i64],
     "msh_get_dt_history": [_vp, _P(_dbl), _i64, _P(_i64)],
@@ -252,6 +253,32 @@ class Grid:
 
     def run(self, t_end=float("inf"), max_steps=(1 << 62)):
         return msh_run(self.h, t_end, max_steps)
+
+    def run_ensemble(self, inputs, outputs, kind=CONSERVED, nsteps=1, check=True):
+        """Advance every host state inputs[k] by nsteps CFL steps from t = 0 into outputs[k],
+        uploads, steps and downloads overlapped (see ``msh_run_ensemble``); page-locked
+        arrays (e.g. ``torch.empty(...).pin_memory().numpy()``) let the copies overlap.
+        Returns the per-state statuses; check=True raises MshError if a state failed."""
+        n = len(inputs)
+        if len(outputs) != n:
+            raise ValueError("inputs and outputs differ in length")
+        size = int(np.prod(self.shape))
+
+        def ptr(a, writable):
+            ok = (isinstance(a, np.ndarray) and a.dtype == self.dtype and a.flags.c_contiguous and a.size == size
+                  and (a.flags.writeable or not writable))
+            if not ok:
+                raise ValueError("ensemble states must be C-contiguous host arrays of the grid's dtype and size")
+            return a.ctypes.data
+
+        ins = (C.c_void_p * max(n, 1))(*[ptr(a, False) for a in inputs])
+        outs = (C.c_void_p * max(n, 1))(*[ptr(a, True) for a in outputs])
+        status = np.zeros(max(n, 1), dtype=np.int32)
+        st = load().msh_run_ensemble(self.h, n, ins, outs, int(kind), int(nsteps),
+                                     status.ctypes.data_as(C.POINTER(C.c_int32)))
+        if check or st != MSH_E_REALIZABILITY:
+            _check(st)
+        return status[:n]
 
     def diagnostics(self):
         tot = np.zeros(10)
