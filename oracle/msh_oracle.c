@@ -69,7 +69,8 @@ typedef struct {
     int32_t scheme;      /* OG_SCHEME_MH (Sec. 3.3, HLL), OG_SCHEME_KT (Sec. 3.2),
                             OG_SCHEME_MH_ROE (Sec. 3.3, Roe-type flux, eqs 40-43 tracing) or
                             OG_SCHEME_MH_HLLC (Sec. 3.3, HLLC flux, eqs 40-45 tracing) */
-    int32_t pad1;
+    int32_t ctu;         /* characteristic schemes: 1 adds the transverse terms to the face
+                            states and takes the max-form CFL rule (og_transverse) */
 } og_grid;
 
 enum { OG_PERIODIC = 0, OG_OUTFLOW = 1, OG_REFLECT = 2 };
@@ -257,8 +258,8 @@ static double mc_limit(double dL, double dC, double dR)
 /* Reconstruction of cell i along direction d from its neighbours Wm, W0, Wp
  * (global primitive order).  dtdx = dt/dx_d.  Writes the face states at i-1/2
  * (lo) and i+1/2 (hi) in global primitive order.                             */
-void og_reconstruct(const double *Wm, const double *W0, const double *Wp, int d,
-                    double dtdx, double *lo, double *hi)
+static void hancock_states(const double *Wm, const double *W0, const double *Wp, int d,
+                           double dtdx, double *lo, double *hi)
 {
     const int *p = perm[d];
     double w0[NV], dwL[NV], dwC[NV], dwR[NV];
@@ -279,20 +280,56 @@ void og_reconstruct(const double *Wm, const double *W0, const double *Wp, int d,
     for (int k = 0; k < NV; k++) dam[k] = mc_limit(daL[k], daC[k], daR[k]);
     matvec(R, dam, dwm);
     matvec(A, dwm, Adw);
-    double lo_l[NV], hi_l[NV];
     for (int k = 0; k < NV; k++) {
-        hi_l[k] = w0[k] + 0.5 * dwm[k] - 0.5 * dtdx * Adw[k];
-        lo_l[k] = w0[k] - 0.5 * dwm[k] - 0.5 * dtdx * Adw[k];
+        hi[p[k]] = w0[k] + 0.5 * dwm[k] - 0.5 * dtdx * Adw[k];
+        lo[p[k]] = w0[k] - 0.5 * dwm[k] - 0.5 * dtdx * Adw[k];
     }
-    /* face-state fallback (reading): revert to first order if a face state
-     * has non-positive density or non-positive normal dispersion            */
-    if (!(hi_l[0] > 0.0 && lo_l[0] > 0.0 && hi_l[4] > 0.0 && lo_l[4] > 0.0)) {
-        for (int k = 0; k < NV; k++) hi_l[k] = lo_l[k] = w0[k];
+}
+
+/* face-state fallback (reading): revert to first order if a face state along d has
+ * non-positive density or non-positive normal dispersion */
+static void face_state_check(const double *W0, int d, double *lo, double *hi)
+{
+    int nn = tens_idx(d, d);
+    if (!(hi[0] > 0.0 && lo[0] > 0.0 && hi[nn] > 0.0 && lo[nn] > 0.0)) {
+        for (int k = 0; k < NV; k++) hi[k] = lo[k] = W0[k];
     }
+}
+
+void og_reconstruct(const double *Wm, const double *W0, const double *Wp, int d,
+                    double dtdx, double *lo, double *hi)
+{
+    hancock_states(Wm, W0, Wp, d, dtdx, lo, hi);
+    face_state_check(W0, d, lo, hi);
+}
+
+/* Transverse term of a cell along direction t for the corner-transport-upwind form of the
+ * unsplit step (the data reconstruction of Lee & Deane 2009, which FLASH's unsplit
+ * MUSCL-Hancock solver used by Sec. 3.3 follows; the paper prints none of it): the
+ * quasi-linear transverse derivative -(dt/2) A_t dW/dx_t taken wave by wave from the
+ * upwind side,
+ *   T_t = -(dt / (2 dx_t)) sum_a lam^a (L^a . dW^a) R^a,
+ *   dW^a = W_i - W_{i-e_t} if lam^a > 0, W_{i+e_t} - W_i otherwise,
+ * with the eigen-system of cell i along t.  The face states along d then take
+ * sum_{t != d} T_t before the face-state check.  dtdx = dt / dx_t. */
+void og_transverse(const double *Wm, const double *W0, const double *Wp, int t, double dtdx, double *T)
+{
+    const int *p = perm[t];
+    double w0[NV], dL[NV], dR[NV];
     for (int k = 0; k < NV; k++) {
-        lo[p[k]] = lo_l[k];
-        hi[p[k]] = hi_l[k];
+        w0[k] = W0[p[k]];
+        dL[k] = W0[p[k]] - Wm[p[k]];
+        dR[k] = Wp[p[k]] - W0[p[k]];
     }
+    double L[NV][NV], R[NV][NV], lam[NV], aL[NV], aR[NV], c[NV], o[NV];
+    og_left_x(w0, L);
+    og_right_x(w0, R);
+    og_eigenvalues_x(w0, lam);
+    matvec(L, dL, aL);
+    matvec(L, dR, aR);
+    for (int a = 0; a < NV; a++) c[a] = lam[a] * (lam[a] > 0.0 ? aL[a] : aR[a]);
+    matvec(R, c, o);
+    for (int k = 0; k < NV; k++) T[p[k]] = -0.5 * dtdx * o[k];
 }
 
 /* Characteristic tracing for a Riemann solver that resolves every wave (Sec. 3.3, eqs 40-43;
@@ -307,9 +344,9 @@ void og_reconstruct(const double *Wm, const double *W0, const double *Wp, int d,
  *   w_R = wt_R + dt/(2dx) sum_{lam^a < 0} (lam^0 - lam^a) (L^a . dw^m) R^a           (eq 43)
  * lam^M, lam^0 the largest and smallest eigenvalues of cell i; L^a the rows of L, R^a the
  * columns of R.  No eq 44-45 terms (those belong to HLL).  Face-state fallback as in
- * og_reconstruct. */
-void og_reconstruct_upwind(const double *Wm, const double *W0, const double *Wp, int d,
-                           double dtdx, double *lo, double *hi)
+ * og_reconstruct (og_reconstruct_upwind). */
+static void upwind_states(const double *Wm, const double *W0, const double *Wp, int d,
+                          double dtdx, double *lo, double *hi)
 {
     const int *p = perm[d];
     double w0[NV], dwL[NV], dwC[NV], dwR[NV];
@@ -348,13 +385,17 @@ void og_reconstruct_upwind(const double *Wm, const double *W0, const double *Wp,
         if (lam[a] < 0.0)
             for (int k = 0; k < NV; k++) lo_l[k] += h * (lmin - lam[a]) * la * R[k][a];   /* eq 43 */
     }
-    if (!(hi_l[0] > 0.0 && lo_l[0] > 0.0 && hi_l[4] > 0.0 && lo_l[4] > 0.0)) {
-        for (int k = 0; k < NV; k++) hi_l[k] = lo_l[k] = w0[k];
-    }
     for (int k = 0; k < NV; k++) {
         lo[p[k]] = lo_l[k];
         hi[p[k]] = hi_l[k];
     }
+}
+
+void og_reconstruct_upwind(const double *Wm, const double *W0, const double *Wp, int d,
+                           double dtdx, double *lo, double *hi)
+{
+    upwind_states(Wm, W0, Wp, d, dtdx, lo, hi);
+    face_state_check(W0, d, lo, hi);
 }
 
 /* ---------------------------------------------------------------- a6 ----- */
@@ -608,8 +649,10 @@ double og_cfl_dt(const og_grid *G, const double *U)
         for (int k = 0; k < NV; k++) Uc[k] = U[k * N + c];
         cons_to_prim(Uc, W);
         double s = 0.0;
-        for (int d = 0; d < G->ndim; d++)
-            s += (fabs(W[1 + d]) + sqrt(3.0 * W[tens_idx(d, d)] / W[0])) / G->dx[d];
+        for (int d = 0; d < G->ndim; d++) {
+            double sd = (fabs(W[1 + d]) + sqrt(3.0 * W[tens_idx(d, d)] / W[0])) / G->dx[d];
+            s = G->ctu ? fmax(s, sd) : s + sd; /* CTU: max over directions, else the sum */
+        }
         if (s > smax) smax = s;
     }
     return G->cfl / smax;
@@ -676,6 +719,25 @@ static int step_pass(const og_grid *Gr, const double *U, const double *phi, doub
         cons_to_prim(Uc, W);
         for (int k = 0; k < NV; k++) Wp[k * NP + c] = W[k];
     }
+    /* transverse terms of every padded cell whose neighbours along t exist (CTU form) */
+    double *Ttr = NULL;
+    if (Gr->ctu && Gr->ndim > 1 && Gr->scheme != OG_SCHEME_KT) {
+        Ttr = (double *)calloc((size_t)Gr->ndim * NV * NP, sizeof(double));
+        if (!Ttr) { free(G); free(Wp); free(dU); return 1; }
+        for (int t = 0; t < Gr->ndim; t++) {
+            int64_t st = (t == 0) ? 1 : (t == 1 ? P.p[0] : P.p[0] * P.p[1]);
+#pragma omp parallel for
+            for (int64_t c = 0; c < NP; c++) {
+                int64_t q[3] = {c % P.p[0], (c / P.p[0]) % P.p[1], c / (P.p[0] * P.p[1])};
+                if (q[t] < 1 || q[t] > P.p[t] - 2) continue;
+                double Wc[3][NV], T[NV];
+                for (int o = -1; o <= 1; o++)
+                    for (int k = 0; k < NV; k++) Wc[o + 1][k] = Wp[k * NP + c + o * st];
+                og_transverse(Wc[0], Wc[1], Wc[2], t, dt / Gr->dx[t], T);
+                for (int k = 0; k < NV; k++) Ttr[((size_t)t * NV + k) * NP + c] = T[k];
+            }
+        }
+    }
     for (int d = 0; d < Gr->ndim; d++) {                               /* a3-a7 */
         int a1 = (d == 0) ? 1 : 0, a2 = (d == 2) ? 1 : 2;              /* the other axes */
         int64_t n1 = P.n[a1], n2 = P.n[a2], nd = P.n[d];
@@ -695,12 +757,25 @@ static int step_pass(const og_grid *Gr, const double *U, const double *phi, doub
                         int64_t pi = pidx(&P, c3[0], c3[1], c3[2]);
                         for (int k = 0; k < NV; k++) Wc[o + 1][k] = Wp[k * NP + pi];
                     }
+                    double *li = lo + NV * (i + 1), *hi_ = hi + NV * (i + 1);
                     if (Gr->scheme == OG_SCHEME_MH_ROE)
-                        og_reconstruct_upwind(Wc[0], Wc[1], Wc[2], d, dtdx,
-                                              lo + NV * (i + 1), hi + NV * (i + 1));
+                        upwind_states(Wc[0], Wc[1], Wc[2], d, dtdx, li, hi_);
                     else
-                        og_reconstruct(Wc[0], Wc[1], Wc[2], d, dtdx,
-                                       lo + NV * (i + 1), hi + NV * (i + 1));
+                        hancock_states(Wc[0], Wc[1], Wc[2], d, dtdx, li, hi_);
+                    if (Ttr) {
+                        int64_t c3[3];
+                        c3[d] = i; c3[a1] = j1; c3[a2] = j2;
+                        int64_t pc = pidx(&P, c3[0], c3[1], c3[2]);
+                        for (int t = 0; t < Gr->ndim; t++) {
+                            if (t == d) continue;
+                            for (int k = 0; k < NV; k++) {
+                                double v = Ttr[((size_t)t * NV + k) * NP + pc];
+                                li[k] += v;
+                                hi_[k] += v;
+                            }
+                        }
+                    }
+                    face_state_check(Wc[1], d, li, hi_);
                 }
                 if (flag) {
                     /* first-order states on every face that touches a flagged cell */
@@ -743,6 +818,7 @@ static int step_pass(const og_grid *Gr, const double *U, const double *phi, doub
     free(G);
     free(Wp);
     free(dU);
+    free(Ttr);
     return 0;
 }
 

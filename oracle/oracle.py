@@ -42,7 +42,7 @@ def build(force: bool = False) -> str:
 class OgGrid(C.Structure):
     _fields_ = [("ndim", C.c_int32), ("pad0", C.c_int32), ("n", C.c_int64 * 3),
                 ("dx", C.c_double * 3), ("bc", C.c_int32 * 6), ("cfl", C.c_double),
-                ("scheme", C.c_int32), ("pad1", C.c_int32)]
+                ("scheme", C.c_int32), ("ctu", C.c_int32)]
 
 
 def _load():
@@ -98,10 +98,12 @@ class Grid:
     """Uniform grid description: ``n`` cells per dim on [lo, hi], boundaries
     ``bc[d] = (lower, upper)`` (PERIODIC / OUTFLOW / REFLECT), CFL number ``cfl``."""
 
-    def __init__(self, n, lo, hi, bc, cfl, scheme=0):
+    def __init__(self, n, lo, hi, bc, cfl, scheme=0, ctu=False):
         """scheme: SCHEME_MH (MUSCL-Hancock + HLL, Sec. 3.3), SCHEME_KT (Kurganov-Tadmor
         + RK2, Sec. 3.2), SCHEME_MH_ROE (MUSCL-Hancock with upwind tracing and the Roe-type
-        flux) or SCHEME_MH_HLLC (MUSCL-Hancock with the HLLC flux)."""
+        flux) or SCHEME_MH_HLLC (MUSCL-Hancock with the HLLC flux).  ctu: the characteristic
+        schemes add the transverse terms of ``og_transverse`` to the face states and take
+        the max-form CFL rule."""
         n = list(n)
         self.ndim = len(n)
         self.n = tuple(n) + (1,) * (3 - len(n))
@@ -120,7 +122,9 @@ class Grid:
             g.bc[2 * d + 1] = self.bc[d][1]
         g.cfl = self.cfl
         g.scheme = int(scheme)
+        g.ctu = int(bool(ctu))
         self.scheme = int(scheme)
+        self.ctu = bool(ctu)
         self._g = g
 
     @property

@@ -164,20 +164,36 @@ def realizable(U):
     return bool(P[0, 0] > 0 and np.linalg.det(P[:2, :2]) > 0 and np.linalg.det(P) > 0)
 
 
-def recon(Wm, W0, Wp, d, dtdx):
+def recon(Wm, W0, Wp, d, dtdx, check=True):
     A, lam, R = eigen(W0, d)
     Linv = np.linalg.inv(R)
     dL, dR, dC = W0 - Wm, Wp - W0, 0.5 * (Wp - Wm)
     dm = R @ mc(Linv @ dL, Linv @ dC, Linv @ dR)
     hi = W0 + 0.5 * dm - 0.5 * dtdx * (A @ dm)
     lo = W0 - 0.5 * dm - 0.5 * dtdx * (A @ dm)
+    return check_states(W0, d, lo, hi) if check else (lo, hi)
+
+
+def check_states(W0, d, lo, hi):
+    """First-order states where a face state has rho <= 0 or P_dd <= 0."""
     nn = tidx(d, d)
     if not (hi[0] > 0 and lo[0] > 0 and hi[nn] > 0 and lo[nn] > 0):
-        hi, lo = W0.copy(), W0.copy()
+        return W0.copy(), W0.copy()
     return lo, hi
 
 
-def recon_upwind(Wm, W0, Wp, d, dtdx):
+def transverse(Wm, W0, Wp, t, dtdx):
+    """Corner-transport-upwind transverse term along t, wave by wave on the numerical
+    eigen-system: -(dt / 2dx_t) sum_a lam_a a_a R^a with a_a the amplitude of the upwind
+    one-sided difference (backward for lam_a > 0, forward otherwise)."""
+    _, lam, R = eigen(W0, t)
+    Linv = np.linalg.inv(R)
+    aL, aR = Linv @ (W0 - Wm), Linv @ (Wp - W0)
+    a = np.where(lam > 0, aL, aR)
+    return -0.5 * dtdx * (R @ (lam * a))
+
+
+def recon_upwind(Wm, W0, Wp, d, dtdx, check=True):
     """Upwind characteristic tracing (eqs 40-43 with eq 41 in the mirror form of eq 40),
     summed per wave: with a = R^-1 dw^m, nu = dt / 2dx,
       hi = W0 + sum_a (1/2 - nu s_a) a_a R^a,  s_a = lam_a if lam_a > 0 else max(lam_max, 0)
@@ -191,10 +207,7 @@ def recon_upwind(Wm, W0, Wp, d, dtdx):
     t = np.where(lam < 0, lam, min(lam.min(), 0.0))
     hi = W0 + R @ ((0.5 - nu * s) * a)
     lo = W0 + R @ ((-0.5 - nu * t) * a)
-    nn = tidx(d, d)
-    if not (hi[0] > 0 and lo[0] > 0 and hi[nn] > 0 and lo[nn] > 0):
-        hi, lo = W0.copy(), W0.copy()
-    return lo, hi
+    return check_states(W0, d, lo, hi) if check else (lo, hi)
 
 
 def speeds(W, d):
@@ -261,12 +274,32 @@ def _pad_line(Uline, bclo, bchi, d):
     return out
 
 
-def step(U, ndim, dx, bc, dt, phi=None, flux="hll"):
+def _pad_grid(U, ndim, bc):
+    """Conserved array with two ghost layers on every active axis, filled axis by axis with
+    the rules of _pad_line (corner ghosts combine the rules of both axes)."""
+    out = np.asarray(U, dtype=np.float64)
+    for d in range(ndim):
+        ax = 3 - d  # array axis of dimension d in [10][z][y][x]
+        moved = np.moveaxis(out, ax, -1)  # [10, ..., n_d]
+        rows = int(np.prod(moved.shape[1:-1]))
+        lines = moved.reshape(10, rows, moved.shape[-1])
+        padded = np.zeros((10, rows, moved.shape[-1] + 4))
+        for r in range(rows):
+            padded[:, r, :] = _pad_line(lines[:, r, :].T, bc[d][0], bc[d][1], d).T
+        shape = list(moved.shape)
+        shape[-1] += 4
+        out = np.moveaxis(padded.reshape(shape), -1, ax)
+    return out
+
+
+def step(U, ndim, dx, bc, dt, phi=None, flux="hll", ctu=False):
     """One unsplit step on a tiny grid, with the a-posteriori fallback: if the second-order
     update leaves cells non-realizable, recompute with first-order face states on every
     face of those cells.  flux="roe": upwind tracing (recon_upwind) and the Roe-type flux
-    on every face except the first-order faces of a fallback pass, which take HLL."""
-    Un = _step_pass(U, ndim, dx, bc, dt, phi, None, flux)
+    on every face except the first-order faces of a fallback pass, which take HLL.
+    ctu=True: every face state along d takes the transverse terms along the other axes
+    (``transverse``) before the face-state check."""
+    Un = _step_pass(U, ndim, dx, bc, dt, phi, None, flux, ctu)
     nz, ny, nx = Un.shape[1:]
     bad = np.zeros((nz, ny, nx), dtype=bool)
     for _ in range(5):  # the first check plus at most four fallback passes
@@ -278,15 +311,31 @@ def step(U, ndim, dx, bc, dt, phi=None, flux="hll"):
         if not new.any() or _ == 4:
             break
         bad |= new
-        Un = _step_pass(U, ndim, dx, bc, dt, phi, bad, flux)
+        Un = _step_pass(U, ndim, dx, bc, dt, phi, bad, flux, ctu)
     return Un
 
 
-def _step_pass(U, ndim, dx, bc, dt, phi, bad, flux="hll"):
+def _step_pass(U, ndim, dx, bc, dt, phi, bad, flux="hll", ctu=False):
     U = np.asarray(U, dtype=np.float64)
     dU = np.zeros_like(U)
     nz, ny, nx = U.shape[1:]
     shape = (nx, ny, nz)
+    g = [2 if d < ndim else 0 for d in range(3)]
+    Wpad = None
+    if ctu and ndim > 1:
+        Up = _pad_grid(U, ndim, bc)
+        Wpad = np.zeros_like(Up)
+        for z in range(Up.shape[1]):
+            for y in range(Up.shape[2]):
+                for x in range(Up.shape[3]):
+                    Wpad[:, z, y, x] = prim(Up[:, z, y, x])
+
+    def T(t, q):  # transverse term along t of the padded cell q = (x, y, z)
+        qm, qp = list(q), list(q)
+        qm[t] -= 1
+        qp[t] += 1
+        return transverse(Wpad[:, qm[2], qm[1], qm[0]], Wpad[:, q[2], q[1], q[0]], Wpad[:, qp[2], qp[1], qp[0]],
+                          t, dt / dx[t])
     for d in range(ndim):
         other = [a for a in range(3) if a != d]
         for j1 in range(shape[other[0]]):
@@ -301,7 +350,17 @@ def _step_pass(U, ndim, dx, bc, dt, phi, bad, flux="hll"):
                 Wl = [prim(u) for u in P]
                 n = shape[d]
                 rc = recon_upwind if flux == "roe" else recon
-                faces = [list(rc(Wl[k - 1], Wl[k], Wl[k + 1], d, dt / dx[d])) for k in range(1, n + 3)]
+                if Wpad is None:
+                    faces = [list(rc(Wl[k - 1], Wl[k], Wl[k + 1], d, dt / dx[d])) for k in range(1, n + 3)]
+                else:
+                    faces = []
+                    for k in range(1, n + 3):
+                        lo, hi = rc(Wl[k - 1], Wl[k], Wl[k + 1], d, dt / dx[d], check=False)
+                        q = [0, 0, 0]
+                        q[d] = k
+                        q[other[0]], q[other[1]] = j1 + g[other[0]], j2 + g[other[1]]
+                        tr = sum(T(t, q) for t in range(ndim) if t != d)
+                        faces.append(list(check_states(Wl[k], d, lo + tr, hi + tr)))
                 if bad is not None:
                     # flag of padded cell k (k = i + 2 for cell i), ghosts take their source cell's
                     def flag(k):
@@ -354,7 +413,7 @@ def _step_pass(U, ndim, dx, bc, dt, phi, bad, flux="hll"):
     return Un
 
 
-def cfl_dt(U, ndim, dx, cfl):
+def cfl_dt(U, ndim, dx, cfl, ctu=False):
     nz, ny, nx = U.shape[1:]
     smax = 0.0
     for z in range(nz):
@@ -364,6 +423,7 @@ def cfl_dt(U, ndim, dx, cfl):
                 s = 0.0
                 for d in range(ndim):
                     a, b = speeds(W, d)
-                    s += max(abs(a), abs(b)) / dx[d]
+                    sd = max(abs(a), abs(b)) / dx[d]
+                    s = max(s, sd) if ctu else s + sd
                 smax = max(smax, s)
     return cfl / smax
