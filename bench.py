@@ -63,7 +63,7 @@ def parse():
     ap.add_argument("--fp32-only", action="store_true", help="skip the FP64 measurement")
     ap.add_argument("--tiling", default=None, help="rows,zchunk instead of autotuning (e.g. 8,32)")
     ap.add_argument("--suite", action="store_true", help="one JSON line per workload instead of the bench line")
-    ap.add_argument("--only", default=None, choices=["sod", "blast", "box", "schemes", "selfgrav", "tubes", "disc"],
+    ap.add_argument("--only", default=None, choices=["sod", "blast", "box", "schemes", "ctu", "selfgrav", "tubes", "disc"],
                     help="with --suite: run one workload (--n and --steps then size it)")
     return ap.parse_args()
 
@@ -406,10 +406,15 @@ def run_suite(args):
     def emit(d):
         print(json.dumps(d), flush=True)
 
-    def grid_rate(p, precision, steps, t_end=math.inf, scheme=0):
-        g = msh.Grid.from_problem(p, precision, stream=stream.cuda_stream)
+    def grid_rate(p, precision, steps, t_end=math.inf, scheme=0, ctu=False, cfl=None):
+        if cfl is None:
+            g = msh.Grid.from_problem(p, precision, stream=stream.cuda_stream)
+        else:
+            g = msh.Grid(p.n, p.lo, p.hi, p.bc, cfl, precision, stream=stream.cuda_stream)
         if scheme:
             g.set_scheme(scheme)
+        if ctu:
+            g.set_ctu(True)
         W = p.W.astype(np.float32) if precision == msh.FP32 else p.W
         g.set_state(W, msh.PRIMITIVE)
         if p.ndim > 1:
@@ -432,7 +437,8 @@ def run_suite(args):
         g.close()
         cells = int(np.prod(p.n))
         bpc = 80 if precision == msh.FP32 else 160
-        return {"value": cells * ns / (ms * 1e-3), "steps": ns, "ms_per_step": ms / ns,
+        return {"value": cells * ns / (ms * 1e-3), "steps": ns, "ms_per_step": ms / ns, "t": t,
+                "sim_time_per_s": t / (ms * 1e-3),
                 "kernel_ms": kms / max(kn, 1), "hbm_frac": bpc * cells / (kms / max(kn, 1) * 1e-3) / 1e9 / hbm}
 
     only = args.only
@@ -476,6 +482,20 @@ def run_suite(args):
                   "kt_ms_over_mh_ms": kt["ms_per_step"] / mh["ms_per_step"],
                   "roe_ms_over_hll_ms": roe["ms_per_step"] / mh["ms_per_step"],
                   "hllc_ms_over_hll_ms": hllc["ms_per_step"] / mh["ms_per_step"]})
+    # the corner-transport-upwind form: its max-form CFL rule allows longer steps (CFL 0.8
+    # against the plain unsplit step's 0.5 with the sum over directions), at a higher cost
+    # per step; compared by simulated time per second
+    if only in (None, "ctu"):
+        for name, p in (("box", inputs.turb(n=args.n or 256)), ("blast", inputs.blast(n=args.n or 1024))):
+            steps = 50 if only is None else args.steps
+            plain = grid_rate(p, msh.FP32, steps, cfl=0.5)
+            ctu = grid_rate(p, msh.FP32, steps, ctu=True, cfl=0.8)
+            ctu_same = grid_rate(p, msh.FP32, steps, ctu=True, cfl=0.5)
+            emit({"workload": f"{name} {p.n[0]}^{p.ndim} FP32, {steps} steps: plain unsplit step (CFL 0.5, sum "
+                              "rule) vs corner transport upwind (CFL 0.8, max rule; and at 0.5)",
+                  "plain": plain, "ctu": ctu, "ctu_cfl05": ctu_same,
+                  "ctu_ms_over_plain_ms": ctu["ms_per_step"] / plain["ms_per_step"],
+                  "ctu_sim_time_rate_over_plain": ctu["sim_time_per_s"] / plain["sim_time_per_s"]})
     # periodic self-gravity: the cost of the FFT Poisson solve and acceleration per step
     if only in (None, "selfgrav"):
         p = inputs.turb(n=args.n or 256)

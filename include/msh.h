@@ -268,6 +268,25 @@ msh_status msh_adjoint_tape(msh_grid *g, const void *dL_dUN, void *dL_dU0, int32
 msh_status msh_set_scheme(msh_grid *g, int32_t scheme);
 
 /*
+ * Corner-transport-upwind (CTU) form of the characteristic schemes (on = 1; 0 switches it
+ * off, the default).  Sec. 3.3 uses FLASH's unsplit MUSCL-Hancock solver (Lee & Deane 2009)
+ * but prints no transverse coupling; with CTU every face state along d also takes
+ *   sum_{t != d} T_t,  T_t = -(dt / (2 dx_t)) sum_a lam^a (L^a . dW^a) R^a,
+ *   dW^a = W_i - W_{i-e_t} if lam^a > 0, else W_{i+e_t} - W_i,
+ * the quasi-linear transverse derivative -(dt/2) A_t dW/dx_t of cell i taken wave by wave
+ * from the upwind side (eigen-system of cell i along t), before the face-state check; the
+ * first-order faces of the a-posteriori fallback take none.  The CFL rule becomes
+ *   dt = C / max_cells max_d (|u_d| + sqrt(3 P_dd / rho)) / dx_d
+ * (the maximum over the directions instead of the sum), so a step can be up to ndim times
+ * longer.  No effect in 1D.  Switching it re-plans the next step of the current state.
+ * Errors: MSH_E_STATE with the central scheme (MSH_SCHEME_KT) or a recording adjoint tape;
+ * the adjoint (msh_adjoint_run, msh_set_tape) refuses a 2D/3D grid with CTU on.
+ * msh_get_ctu reads the setting.
+ */
+msh_status msh_set_ctu(msh_grid *g, int32_t on);
+msh_status msh_get_ctu(const msh_grid *g, int32_t *on);
+
+/*
  * Periodic self-gravity with the gravitational constant G (> 0; 0 switches it off).  Needs
  * periodic boundaries on every active dimension (MSH_E_INVALID_ARG otherwise).  Before every
  * step the potential of the density of U^n solves the 3-point discrete Poisson equation

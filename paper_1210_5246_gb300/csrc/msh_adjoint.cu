@@ -644,6 +644,8 @@ extern "C" msh_status msh_adjoint_run(msh_grid *g, const void *U0, int64_t nstep
     if (!(dt_sched[s] > 0.0) || !std::isfinite(dt_sched[s]))
       return afail(MSH_E_INVALID_ARG, "dt_sched[%lld] must be finite and > 0", (long long)s);
   if (g->scheme != MSH_SCHEME_MUSCL_HANCOCK) return afail(MSH_E_STATE, "the adjoint covers the MUSCL-Hancock scheme only");
+  if (g->ctu && g->ndim > 1)
+    return afail(MSH_E_STATE, "the adjoint covers the step without transverse (CTU) terms only");
   if (g->sg_G > 0.0) return afail(MSH_E_STATE, "the adjoint covers external potentials only");
   if (g->prec == MSH_FP32)
     return adjoint_impl<float>(g, U0, nsteps, dt_sched, K, dL_dUN, dL_dU0, where, kind);

@@ -164,15 +164,32 @@ template <typename T> struct Eig {
   }
 };
 
-// Reconstruction of one cell along the sweep direction, in the local frame.
-//   wm, w0, wp   primitive states of cells i-1, i, i+1
-//   nu           dt / (2 dx)
-// Output: face states lo (at i-1/2) and hi (at i+1/2):
-//   dw^m = R mc(L dw_L, L dw_R);   w0 -+ dw^m/2 - nu A dw^m,   A dw^m = R Lambda mc(...)
-// If a face state has rho <= 0 or P_nn <= 0 both revert to w0 (first order).
+// ------------------------------------------------- corner transport upwind
+// Transverse term of a cell along direction t for the corner-transport-upwind form of the
+// unsplit step (the data reconstruction of Lee & Deane 2009, on which FLASH's unsplit
+// MUSCL-Hancock solver of Sec. 3.3 is built; the paper prints none of it): the
+// quasi-linear transverse derivative -(dt/2) A_t dW/dx_t taken wave by wave from the
+// upwind side,
+//   T_t = -nu sum_a lam^a (L^a . dW^a) R^a,   dW^a = w0 - wm if lam^a > 0, else wp - w0,
+// nu = dt / (2 dx_t), with the eigen-system of the cell along t (local frame of t).  The
+// face states along d take sum_{t != d} T_t before the face-state check.
+// cl, cr: the amplitudes L (w0 - wm) and L (wp - w0).
 template <typename T>
-__device__ __forceinline__ void reconstruct(const T (&wm)[NV], const T (&w0)[NV], const T (&wp)[NV],
-                                            T nu, T (&lo)[NV], T (&hi)[NV]) {
+__device__ __forceinline__ void upwind_terms(const Eig<T> &E, const T (&cl)[NV], const T (&cr)[NV], T nu,
+                                             T (&o)[NV]) {
+  const T s[NV] = {-E.cf, -E.cs, -E.cs, T(0), T(0), T(0), T(0), E.cs, E.cs, E.cf};
+  T c[NV];
+#pragma unroll
+  for (int k = 0; k < NV; k++) {
+    const T lam = E.u + s[k];
+    c[k] = -nu * lam * (lam > T(0) ? cl[k] : cr[k]);
+  }
+  E.back(c, o);
+}
+
+template <typename T>
+__device__ __forceinline__ void transverse(const T (&wm)[NV], const T (&w0)[NV], const T (&wp)[NV], T nu,
+                                           T (&o)[NV]) {
   Eig<T> E;
   E.init(w0);
   T d[NV], cl[NV], cr[NV];
@@ -182,6 +199,47 @@ __device__ __forceinline__ void reconstruct(const T (&wm)[NV], const T (&w0)[NV]
 #pragma unroll
   for (int k = 0; k < NV; k++) d[k] = wp[k] - w0[k];
   E.project(d, cr);
+  upwind_terms(E, cl, cr, nu, o);
+}
+
+// Face-state check: if a face state has rho <= 0 or P_nn <= 0 both revert to w0 (first
+// order).
+template <typename T>
+__device__ __forceinline__ void face_state_check(const T (&w0)[NV], T (&lo)[NV], T (&hi)[NV]) {
+  const bool ok = hi[0] > T(0) && lo[0] > T(0) && hi[4] > T(0) && lo[4] > T(0);
+  if (!ok) {
+#pragma unroll
+    for (int k = 0; k < NV; k++) { hi[k] = w0[k]; lo[k] = w0[k]; }
+  }
+}
+
+// Reconstruction of one cell along the sweep direction, in the local frame.
+//   wm, w0, wp   primitive states of cells i-1, i, i+1
+//   nu           dt / (2 dx)
+// Output: face states lo (at i-1/2) and hi (at i+1/2):
+//   dw^m = R mc(L dw_L, L dw_R);   w0 -+ dw^m/2 - nu A dw^m,   A dw^m = R Lambda mc(...)
+// CTU: both face states also take X (the other directions' transverse terms, local frame;
+// xget(k) returns X_k) and the cell's own transverse term along this direction is handed to
+// tput(k, T_k) (upwind_terms).  Then the face-state check.  The accessors let a kernel keep
+// X and T in shared memory, read and written where they are used.
+template <typename T, bool CTU, typename XG, typename TP>
+__device__ __forceinline__ void reconstruct(const T (&wm)[NV], const T (&w0)[NV], const T (&wp)[NV], T nu,
+                                            T (&lo)[NV], T (&hi)[NV], XG &&xget, TP &&tput) {
+  Eig<T> E;
+  E.init(w0);
+  T d[NV], cl[NV], cr[NV];
+#pragma unroll
+  for (int k = 0; k < NV; k++) d[k] = w0[k] - wm[k];
+  E.project(d, cl);
+#pragma unroll
+  for (int k = 0; k < NV; k++) d[k] = wp[k] - w0[k];
+  E.project(d, cr);
+  if constexpr (CTU) {
+    T o[NV];
+    upwind_terms(E, cl, cr, nu, o);
+#pragma unroll
+    for (int k = 0; k < NV; k++) tput(k, o[k]);
+  }
   // limited amplitudes, doubled (every quantity below up to the predictor is exactly twice
   // its unscaled value, so the face states are bit for bit those of the unscaled form)
   T m[NV];
@@ -199,15 +257,18 @@ __device__ __forceinline__ void reconstruct(const T (&wm)[NV], const T (&w0)[NV]
 #pragma unroll
   for (int k = 0; k < NV; k++) {
     const T adw = E.u * dw[k] + g[k];
-    const T pred = w0[k] - nu2 * adw;
+    T pred = w0[k] - nu2 * adw;
+    if constexpr (CTU) pred += xget(k);
     hi[k] = pred + T(0.25) * dw[k];
     lo[k] = pred - T(0.25) * dw[k];
   }
-  const bool ok = hi[0] > T(0) && lo[0] > T(0) && hi[4] > T(0) && lo[4] > T(0);
-  if (!ok) {
-#pragma unroll
-    for (int k = 0; k < NV; k++) { hi[k] = w0[k]; lo[k] = w0[k]; }
-  }
+  face_state_check(w0, lo, hi);
+}
+
+template <typename T>
+__device__ __forceinline__ void reconstruct(const T (&wm)[NV], const T (&w0)[NV], const T (&wp)[NV], T nu,
+                                            T (&lo)[NV], T (&hi)[NV]) {
+  reconstruct<T, false>(wm, w0, wp, nu, lo, hi, [](int) { return T(0); }, [](int, T) {});
 }
 
 // Upwind characteristic tracing for the Roe-type flux (Sec. 3.3, eqs 40-43: reference
@@ -216,11 +277,11 @@ __device__ __forceinline__ void reconstruct(const T (&wm)[NV], const T (&w0)[NV]
 // c_a = (L dw^m)_a and speed lam_a = u + s_a:
 //   hi = w0 + sum_a (1/2 - nu x_a) c_a R^a,   x_a = lam_a if lam_a > 0, else max(u + cf, 0)
 //   lo = w0 + sum_a (-1/2 - nu y_a) c_a R^a,  y_a = lam_a if lam_a < 0, else min(u - cf, 0)
-// (eq 41 read in the mirror form of eq 40).  Same limiter and face-state fallback as
-// reconstruct.
-template <typename T>
+// (eq 41 read in the mirror form of eq 40).  Same limiter, transverse terms (CTU) and
+// face-state check as reconstruct.
+template <typename T, bool CTU, typename XG, typename TP>
 __device__ __forceinline__ void reconstruct_upwind(const T (&wm)[NV], const T (&w0)[NV], const T (&wp)[NV],
-                                                   T nu, T (&lo)[NV], T (&hi)[NV]) {
+                                                   T nu, T (&lo)[NV], T (&hi)[NV], XG &&xget, TP &&tput) {
   Eig<T> E;
   E.init(w0);
   T d[NV], cl[NV], cr[NV];
@@ -230,6 +291,12 @@ __device__ __forceinline__ void reconstruct_upwind(const T (&wm)[NV], const T (&
 #pragma unroll
   for (int k = 0; k < NV; k++) d[k] = wp[k] - w0[k];
   E.project(d, cr);
+  if constexpr (CTU) {
+    T o[NV];
+    upwind_terms(E, cl, cr, nu, o);
+#pragma unroll
+    for (int k = 0; k < NV; k++) tput(k, o[k]);
+  }
   // doubled limited amplitudes: the coefficients below carry the factor 1/2
   T m[NV];
 #pragma unroll
@@ -249,14 +316,18 @@ __device__ __forceinline__ void reconstruct_upwind(const T (&wm)[NV], const T (&
   E.back(cl2, dl);
 #pragma unroll
   for (int k = 0; k < NV; k++) {
-    hi[k] = w0[k] + dh[k];
-    lo[k] = w0[k] + dl[k];
+    T base = w0[k];
+    if constexpr (CTU) base += xget(k);
+    hi[k] = base + dh[k];
+    lo[k] = base + dl[k];
   }
-  const bool ok = hi[0] > T(0) && lo[0] > T(0) && hi[4] > T(0) && lo[4] > T(0);
-  if (!ok) {
-#pragma unroll
-    for (int k = 0; k < NV; k++) { hi[k] = w0[k]; lo[k] = w0[k]; }
-  }
+  face_state_check(w0, lo, hi);
+}
+
+template <typename T>
+__device__ __forceinline__ void reconstruct_upwind(const T (&wm)[NV], const T (&w0)[NV], const T (&wp)[NV],
+                                                   T nu, T (&lo)[NV], T (&hi)[NV]) {
+  reconstruct_upwind<T, false>(wm, w0, wp, nu, lo, hi, [](int) { return T(0); }, [](int, T) {});
 }
 
 // A-posteriori fallback: every face that touches a cell whose second-order update was
@@ -339,11 +410,7 @@ __device__ __forceinline__ void kt_reconstruct(const T (&wm)[NV], const T (&w0)[
     hi[k] = w0[k] + T(0.25) * s2;
     lo[k] = w0[k] - T(0.25) * s2;
   }
-  const bool ok = hi[0] > T(0) && lo[0] > T(0) && hi[4] > T(0) && lo[4] > T(0);
-  if (!ok) {
-#pragma unroll
-    for (int k = 0; k < NV; k++) { hi[k] = w0[k]; lo[k] = w0[k]; }
-  }
+  face_state_check(w0, lo, hi);
 }
 
 // Central flux H = (f(wl) + f(wr))/2 - a (U(wr) - U(wl))/2 through a face with the value wl
@@ -494,6 +561,17 @@ __device__ __forceinline__ void recon(const T (&wm)[NV], const T (&w0)[NV], cons
   if constexpr (SCH == 0 || SCH == 4) reconstruct(wm, w0, wp, nu, lo, hi);
   else if constexpr (SCH == 3) reconstruct_upwind(wm, w0, wp, nu, lo, hi);
   else kt_reconstruct(wm, w0, wp, lo, hi);
+}
+
+// The characteristic schemes' reconstruction with the transverse terms X (local frame,
+// xget(k) = X_k) in the face states; the cell's own transverse term along the sweep goes to
+// tput(k, T_k).
+template <int SCH, typename T, typename XG, typename TP>
+__device__ __forceinline__ void recon_ctu(const T (&wm)[NV], const T (&w0)[NV], const T (&wp)[NV], T nu,
+                                          XG &&xget, TP &&tput, T (&lo)[NV], T (&hi)[NV]) {
+  static_assert(kCharacteristic<SCH>, "transverse terms belong to the characteristic schemes");
+  if constexpr (SCH == 3) reconstruct_upwind<T, true>(wm, w0, wp, nu, lo, hi, xget, tput);
+  else reconstruct<T, true>(wm, w0, wp, nu, lo, hi, xget, tput);
 }
 
 template <int SCH, typename T>

@@ -138,6 +138,13 @@ void free_tape(msh_grid *g) {
 // One pass of the characteristic step with the grid's flux (HLL, Roe-type or HLLC).
 template <typename T>
 static cudaError_t launch_characteristic(msh_grid *g, const StepArgs<T> &a, bool retry, int *nblocks_out) {
+  if (g->ctu) {  // the corner-transport-upwind form
+    if (g->scheme == MSH_SCHEME_MUSCL_HANCOCK_ROE)
+      return launch_step_ctu<T, 3>(a, g->ndim, g->rows, retry, g->stream, nblocks_out);
+    if (g->scheme == MSH_SCHEME_MUSCL_HANCOCK_HLLC)
+      return launch_step_ctu<T, 4>(a, g->ndim, g->rows, retry, g->stream, nblocks_out);
+    return launch_step_ctu<T, 0>(a, g->ndim, g->rows, retry, g->stream, nblocks_out);
+  }
   if (g->scheme == MSH_SCHEME_MUSCL_HANCOCK_ROE)
     return launch_step_roe<T>(a, g->ndim, g->rows, retry, g->stream, nblocks_out);
   if (g->scheme == MSH_SCHEME_MUSCL_HANCOCK_HLLC)
@@ -241,10 +248,10 @@ msh_status prime(msh_grid *g, int which) {
   cudaError_t e;
   if (g->prec == MSH_FP32)
     e = launch_scan<float>((const float *)g->U[which], g->N, (int)g->n[0], (int)g->n[1], g->ndim, g->dx, g->part,
-                           kScanBlocks, g->stream);
+                           kScanBlocks, g->stream, 0, 0, g->ctu);
   else
     e = launch_scan<double>((const double *)g->U[which], g->N, (int)g->n[0], (int)g->n[1], g->ndim, g->dx,
-                            g->part, kScanBlocks, g->stream);
+                            g->part, kScanBlocks, g->stream, 0, 0, g->ctu);
   if (e != cudaSuccess) return fail(MSH_E_CUDA, "scan launch: %s", cudaGetErrorString(e));
   e = launch_finalize(g->ctrl, g->part, kScanBlocks, 1, g->stream);
   if (e != cudaSuccess) return fail(MSH_E_CUDA, "finalize launch: %s", cudaGetErrorString(e));
@@ -533,9 +540,9 @@ msh_status msh_run_ensemble(msh_grid *g, int64_t count, const void *const *in, v
     void *src = g->U[s0 & 1];
     CUDA_TRY(cudaMemcpyAsync(src, slot, bytes, cudaMemcpyDeviceToDevice, g->stream));
     e = fp32 ? launch_scan<float>((const float *)src, g->N, (int)g->n[0], (int)g->n[1], g->ndim, g->dx, g->part,
-                                  kScanBlocks, g->stream)
+                                  kScanBlocks, g->stream, 0, 0, g->ctu)
              : launch_scan<double>((const double *)src, g->N, (int)g->n[0], (int)g->n[1], g->ndim, g->dx, g->part,
-                                   kScanBlocks, g->stream);
+                                   kScanBlocks, g->stream, 0, 0, g->ctu);
     if (e == cudaSuccess) e = launch_finalize(g->ctrl, g->part, kScanBlocks, 1, g->stream);
     if (e == cudaSuccess) e = launch_ensemble_start(g->ctrl, s0, nsteps, g->ens_status + k, g->stream);
     if (e != cudaSuccess) return fail(MSH_E_CUDA, "ensemble start: %s", cudaGetErrorString(e));
@@ -640,10 +647,36 @@ msh_status msh_set_scheme(msh_grid *g, int32_t scheme) {
     return fail(MSH_E_INVALID_ARG, "unknown scheme");
   if (scheme != MSH_SCHEME_MUSCL_HANCOCK && g->tape_valid)
     return fail(MSH_E_STATE, "the adjoint tape covers the MUSCL-Hancock scheme with HLL only");
+  if (scheme == MSH_SCHEME_KT && g->ctu)
+    return fail(MSH_E_STATE, "the transverse (CTU) terms belong to the characteristic schemes: switch CTU off first");
   CUDA_TRY(cudaStreamSynchronize(g->stream));
   if (scheme == MSH_SCHEME_KT && !g->U1) CUDA_TRY(cudaMalloc(&g->U1, g->N * 10 * g->esize));
   if (scheme != g->scheme) drop_graph(g);
   g->scheme = scheme;
+  return MSH_OK;
+}
+
+msh_status msh_set_ctu(msh_grid *g, int32_t on) {
+  begin();
+  if (!g) return fail(MSH_E_INVALID_ARG, "null grid");
+  if (on != 0 && on != 1) return fail(MSH_E_INVALID_ARG, "on must be 0 or 1");
+  if (on && g->scheme == MSH_SCHEME_KT)
+    return fail(MSH_E_STATE, "the transverse (CTU) terms belong to the characteristic schemes, not the central one");
+  if (on && g->tape_valid && g->ndim > 1)
+    return fail(MSH_E_STATE, "the adjoint tape covers the step without transverse (CTU) terms only");
+  CUDA_TRY(cudaStreamSynchronize(g->stream));
+  if ((bool)on == g->ctu) return MSH_OK;
+  drop_graph(g);
+  g->ctu = on != 0;
+  // the CFL rule changed: plan the next step of the current state again
+  if (g->has_state) return prime(g, cur_buf(g));
+  return MSH_OK;
+}
+
+msh_status msh_get_ctu(const msh_grid *g, int32_t *on) {
+  begin();
+  if (!g || !on) return fail(MSH_E_INVALID_ARG, "null argument");
+  *on = g->ctu ? 1 : 0;
   return MSH_OK;
 }
 
@@ -814,6 +847,8 @@ msh_status msh_set_tape(msh_grid *g, int32_t K, int64_t max_steps) {
   if (K < 0 || (K > 0 && max_steps < 1)) return fail(MSH_E_INVALID_ARG, "need K >= 1 and max_steps >= 1 (K = 0 frees)");
   if (K > 0 && g->scheme != MSH_SCHEME_MUSCL_HANCOCK)
     return fail(MSH_E_STATE, "the adjoint covers the MUSCL-Hancock scheme only");
+  if (K > 0 && g->ctu && g->ndim > 1)
+    return fail(MSH_E_STATE, "the adjoint covers the step without transverse (CTU) terms only");
   if (K > 0 && g->sg_G > 0.0) return fail(MSH_E_STATE, "the adjoint covers external potentials only");
   if (!g->has_state && K > 0) return fail(MSH_E_STATE, "msh_set_tape before msh_set_state");
   CUDA_TRY(cudaStreamSynchronize(g->stream));
@@ -902,9 +937,9 @@ msh_status msh_reduce_layers(msh_grid *g, int64_t start, int64_t count, double t
   const int which = cur_buf(g);
   cudaError_t e = g->prec == MSH_FP32
                       ? launch_scan<float>((const float *)g->U[which], g->N, (int)g->n[0], (int)g->n[1], g->ndim,
-                                           g->dx, g->part, kScanBlocks, g->stream, c0, c1)
+                                           g->dx, g->part, kScanBlocks, g->stream, c0, c1, g->ctu)
                       : launch_scan<double>((const double *)g->U[which], g->N, (int)g->n[0], (int)g->n[1], g->ndim,
-                                            g->dx, g->part, kScanBlocks, g->stream, c0, c1);
+                                            g->dx, g->part, kScanBlocks, g->stream, c0, c1, g->ctu);
   if (e == cudaSuccess) e = launch_finalize(g->ctrl_aux, g->part, kScanBlocks, 1, g->stream);
   if (e != cudaSuccess) return fail(MSH_E_CUDA, "layer reduction: %s", cudaGetErrorString(e));
   CUDA_TRY(cudaMemcpyAsync(&c, g->ctrl_aux, sizeof c, cudaMemcpyDeviceToHost, g->stream));

@@ -79,14 +79,19 @@ template <typename T> cudaError_t launch_step_roe(const StepArgs<T> &a, int ndim
                                                   int *nblocks_out);
 template <typename T> cudaError_t launch_step_hllc(const StepArgs<T> &a, int ndim, int rows, bool retry, cudaStream_t s,
                                                   int *nblocks_out);
+// the corner-transport-upwind form of the characteristic step, SCH = 0 (HLL), 3 (Roe-type)
+// or 4 (HLLC); same contract as launch_step
+template <typename T, int SCH> cudaError_t launch_step_ctu(const StepArgs<T> &a, int ndim, int rows, bool retry,
+                                                           cudaStream_t s, int *nblocks_out);
 // stage 1 or 2 of the Kurganov-Tadmor scheme (a.U1 must be set)
 template <typename T> cudaError_t launch_step_kt(const StepArgs<T> &a, int ndim, int rows, int stage, cudaStream_t s);
 template <typename T> int step_blocks(int ndim, int rows, int nx, int ny, int nz, int zchunk);
-template <typename T> size_t step_smem(int ndim, int rows);
-// partials of cells [c0, c1) (c1 = 0: all N)
+template <typename T> size_t step_smem(int ndim, int rows, bool ctu);
+// partials of cells [c0, c1) (c1 = 0: all N); maxf: the corner-transport-upwind CFL speed
 template <typename T> cudaError_t launch_scan(const T *U, size_t N, int nx, int ny, int ndim,
                                               const double *dx, Partial *part, int nparts,
-                                              cudaStream_t s, size_t c0 = 0, size_t c1 = 0);
+                                              cudaStream_t s, size_t c0 = 0, size_t c1 = 0,
+                                              bool maxf = false);
 cudaError_t launch_set_dt(Ctrl *ctrl, double dt, cudaStream_t s);
 cudaError_t launch_finalize(Ctrl *ctrl, const Partial *part, int nparts, int mode, cudaStream_t s);
 cudaError_t launch_run_start(Ctrl *ctrl, double t_end, int64_t max_steps, double dt_max, cudaStream_t s);
@@ -145,6 +150,7 @@ struct msh_grid {
   // block for reductions over a range of layers
   bool dt_stale = false;
   int scheme = MSH_SCHEME_MUSCL_HANCOCK;
+  bool ctu = false;    // corner-transport-upwind form of the characteristic schemes
   void *U1 = nullptr;  // first Runge-Kutta stage of the central scheme
   // periodic self-gravity (msh_set_self_gravity): G > 0 when on, cuFFT plans, the FFT
   // input / spectrum / potential, the previous and the used acceleration [3][N], and a

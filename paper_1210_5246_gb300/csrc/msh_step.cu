@@ -12,8 +12,9 @@ namespace msh {
 
 // ----------------------------------------------------------------- scan kernel
 // Partials (totals, max signal speed sum, first non-realizable cell) of the cells
-// [c0, c1) of a state whose fields are N apart.
-template <typename T, int NDIM>
+// [c0, c1) of a state whose fields are N apart.  MAXF: the corner-transport-upwind speed
+// (the maximum over the dims instead of the sum).
+template <typename T, int NDIM, bool MAXF>
 __global__ void __launch_bounds__(256) scan_kernel(const T *__restrict__ U, size_t N, size_t c0, size_t c1, T idx,
                                                    T idy, T idz, Partial *part) {
   double diag[NV];
@@ -27,7 +28,7 @@ __global__ void __launch_bounds__(256) scan_kernel(const T *__restrict__ U, size
     for (int k = 0; k < NV; k++) Uc[k] = U[k * N + c];
     cons_to_prim(Uc, W);
     if (!realizable(W)) bad = min(bad, (long long)c);
-    smax = fmax(smax, speed_sum<T, NDIM>(W, idx, idy, idz));
+    smax = fmax(smax, speed_sum<T, NDIM, MAXF>(W, idx, idy, idz));
 #pragma unroll
     for (int k = 0; k < NV; k++) diag[k] += (double)Uc[k];
   }
@@ -210,12 +211,14 @@ cudaError_t launch_step(const StepArgs<T> &a, int ndim, int rows, bool retry, cu
 
 template <typename T>
 cudaError_t launch_scan(const T *U, size_t N, int nx, int ny, int ndim, const double *dx, Partial *part,
-                        int nparts, cudaStream_t s, size_t c0, size_t c1) {
+                        int nparts, cudaStream_t s, size_t c0, size_t c1, bool maxf) {
   const T ix = (T)(1.0 / dx[0]), iy = (T)(1.0 / dx[1]), iz = (T)(1.0 / dx[2]);
   if (c1 == 0) c1 = N;
-  if (ndim == 1) scan_kernel<T, 1><<<nparts, 256, 0, s>>>(U, N, c0, c1, ix, iy, iz, part);
-  else if (ndim == 2) scan_kernel<T, 2><<<nparts, 256, 0, s>>>(U, N, c0, c1, ix, iy, iz, part);
-  else scan_kernel<T, 3><<<nparts, 256, 0, s>>>(U, N, c0, c1, ix, iy, iz, part);
+  if (ndim == 1) scan_kernel<T, 1, false><<<nparts, 256, 0, s>>>(U, N, c0, c1, ix, iy, iz, part);
+  else if (ndim == 2 && maxf) scan_kernel<T, 2, true><<<nparts, 256, 0, s>>>(U, N, c0, c1, ix, iy, iz, part);
+  else if (ndim == 2) scan_kernel<T, 2, false><<<nparts, 256, 0, s>>>(U, N, c0, c1, ix, iy, iz, part);
+  else if (maxf) scan_kernel<T, 3, true><<<nparts, 256, 0, s>>>(U, N, c0, c1, ix, iy, iz, part);
+  else scan_kernel<T, 3, false><<<nparts, 256, 0, s>>>(U, N, c0, c1, ix, iy, iz, part);
   return cudaGetLastError();
 }
 
@@ -250,9 +253,9 @@ template <typename T> cudaError_t launch_convert(T *U, size_t N, int to_primitiv
 #define MSH_INST(T)                                                                                   \
   template cudaError_t launch_step<T>(const StepArgs<T> &, int, int, bool, cudaStream_t, int *);     \
   template int step_blocks<T>(int, int, int, int, int, int);                                         \
-  template size_t step_smem<T>(int, int);                                                            \
+  template size_t step_smem<T>(int, int, bool);                                                          \
   template cudaError_t launch_scan<T>(const T *, size_t, int, int, int, const double *, Partial *, int, \
-                                      cudaStream_t, size_t, size_t);                                 \
+                                      cudaStream_t, size_t, size_t, bool);                           \
   template cudaError_t launch_convert<T>(T *, size_t, int, cudaStream_t);                            \
   template cudaError_t launch_gravity_field<T>(const double *, T *, int, int, int, int, const double *, cudaStream_t);
 MSH_INST(float)

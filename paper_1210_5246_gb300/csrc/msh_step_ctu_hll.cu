@@ -1,0 +1,11 @@
+// msh_step_ctu_hll.cu -- launchers of the corner-transport-upwind form of the characteristic
+// step with HLL (the step kernels of msh_step_kernels.cuh with SCH = 0 and CTU,
+// compiled apart in parallel).
+#include "msh_step_kernels.cuh"
+
+namespace msh {
+
+template cudaError_t launch_step_ctu<float, 0>(const StepArgs<float> &, int, int, bool, cudaStream_t, int *);
+template cudaError_t launch_step_ctu<double, 0>(const StepArgs<double> &, int, int, bool, cudaStream_t, int *);
+
+}  // namespace msh

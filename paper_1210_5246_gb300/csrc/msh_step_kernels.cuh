@@ -68,13 +68,18 @@ __device__ __forceinline__ void block_partial(double (&diag)[NV], double smax, l
 }
 
 // Sum over active dims of (|u_d| + sqrt(3 P_dd / rho)) / dx_d: the CFL signal-speed sum.
-template <typename T, int NDIM>
+// MAXF (the corner-transport-upwind step): the maximum over the dims instead of the sum.
+template <typename T, int NDIM, bool MAXF = false>
 __device__ __forceinline__ T speed_sum(const T (&W)[NV], T idx, T idy, T idz) {
-  const T r3 = T(3) * frcp(W[0]);
   T s = (fabs(W[1]) + sqrt_ratio(W[4], W[0]) * T(1.7320508075688772)) * idx;
-  if (NDIM > 1) s += (fabs(W[2]) + sqrt_ratio(W[7], W[0]) * T(1.7320508075688772)) * idy;
-  if (NDIM > 2) s += (fabs(W[3]) + sqrt_ratio(W[9], W[0]) * T(1.7320508075688772)) * idz;
-  (void)r3;
+  if (NDIM > 1) {
+    const T sy = (fabs(W[2]) + sqrt_ratio(W[7], W[0]) * T(1.7320508075688772)) * idy;
+    s = MAXF ? fmax(s, sy) : s + sy;
+  }
+  if (NDIM > 2) {
+    const T sz = (fabs(W[3]) + sqrt_ratio(W[9], W[0]) * T(1.7320508075688772)) * idz;
+    s = MAXF ? fmax(s, sz) : s + sz;
+  }
   return s;
 }
 
@@ -93,7 +98,7 @@ template <typename T> __device__ __forceinline__ T *tape_slot(const StepArgs<T> 
 // SCH 0: U^{n+1} = U^n + dt L (MUSCL-Hancock); SCH 1: U1 = U^n + dt L(U^n) (the first
 // Runge-Kutta stage, stored without sources or partials); SCH 2: U^{n+1} =
 // (U^n + U1 + dt L(U1)) / 2 with src = U1 and un0 = U^n of the cell (fields N apart).
-template <typename T, int NDIM, int SCH, bool RETRY>
+template <typename T, int NDIM, int SCH, bool RETRY, bool CTU = false>
 __device__ __forceinline__ void finish_cell(const StepArgs<T> &a, const T *src, size_t stride, const T *un0,
                                             T *__restrict__ Ud, size_t N, size_t c,
                                             const T (&acc)[NV], T dt, T idx, T idy, T idz, Acc<T> &diag,
@@ -148,7 +153,7 @@ __device__ __forceinline__ void finish_cell(const StepArgs<T> &a, const T *src, 
     }
   }
 done:
-  smax = fmax(smax, speed_sum<T, NDIM>(W, idx, idy, idz));
+  smax = fmax(smax, speed_sum<T, NDIM, CTU>(W, idx, idy, idz));
   diag.add(Un);
 }
 
@@ -247,7 +252,10 @@ __global__ void __launch_bounds__(kTile1D) step1d_kernel(StepArgs<T> a) {
 // memory (FP32, 16 rows: 224 KB with everything else); two otherwise (the update re-reads
 // U^n from global memory), which keeps two FP32 blocks of 8 rows per SM and FP64 within
 // the shared memory of a block.
-template <typename T, int BY> constexpr int kRawPlanes = (sizeof(T) == 4 && BY == 16) ? 4 : 2;
+// The corner-transport-upwind form keeps two (its shared memory holds per-thread transverse
+// terms instead).
+template <typename T, int BY, bool CTU = false>
+constexpr int kRawPlanes = (sizeof(T) == 4 && BY == 16 && !CTU) ? 4 : 2;
 // Asynchronous global -> shared copy of one element (cp.async, completion tracked per
 // thread by commit groups).
 template <typename T> __device__ __forceinline__ void cp_async_elem(T *smem, const T *gmem) {
@@ -269,12 +277,17 @@ __device__ __forceinline__ void gather(const T *__restrict__ pl, int sy, int sx,
   for (int k = 0; k < NV; k++) w[k] = pl[(Frame<D>::g(k) * SY + sy) * SX + sx];
 }
 
-template <typename T, int NDIM, int BY, int SCH, bool RETRY>
+// CTU: the corner-transport-upwind form (transverse terms in the face states, max-form CFL
+// speed).  Every thread's own cell is then staged too (the four cells diagonal to the
+// tile's corners join the staged box), every thread but the four corner ones forms the
+// transverse terms of its cell plane by plane, and the sums each sweep needs, X_x = T_y +
+// T_z and X_y = T_x + T_z, wait in thread-private shared memory from the plane before.
+template <typename T, int NDIM, int BY, int SCH, bool RETRY, bool CTU = false>
 __global__ void __launch_bounds__(32 * BY, (BY <= 8 ? 2 : 1)) step_tile_kernel(StepArgs<T> a) {
   static_assert(NDIM == 3, "the 2D step runs in step_strip2d_kernel");
   constexpr int SX = 34, SY = BY + 2, NQ = SY * SX;
   constexpr int PL = NV * NQ;  // one staged plane, all fields: [NV][SY][SX]
-  constexpr int RAW = kRawPlanes<T, BY>;  // raw staging slots (4: U^n of the update from shared memory)
+  constexpr int RAW = kRawPlanes<T, BY, CTU>;  // raw staging slots (4: U^n of the update from shared memory)
   const Ctrl *ctrl = a.ctrl;
   if (ctrl->done) return;
   if (RETRY && ctrl->nbad[a.level - 1] == 0) return;
@@ -300,7 +313,9 @@ __global__ void __launch_bounds__(32 * BY, (BY <= 8 ? 2 : 1)) step_tile_kernel(S
   T *sR = sW + 3 * PL;
   T *sXh = sR + RAW * PL;        // [NV][BY][32]
   T *sXf = sXh + NV * BY * 32;   // [NV][BY][32]
-  unsigned *sMeta = reinterpret_cast<unsigned *>(sXf + NV * BY * 32);  // [RAW][NQ]
+  T *sCx = sXf + NV * BY * 32;   // CTU: X_x of the thread's cell, [NV][BY * 32]
+  T *sCy = sCx + (CTU ? NV * BY * 32 : 0);  // CTU: X_y, [NV][BY * 32]
+  unsigned *sMeta = reinterpret_cast<unsigned *>(sCy + (CTU ? NV * BY * 32 : 0));  // [RAW][NQ]
   auto slot = [](int p) { return ((p % RAW) + RAW) % RAW; };
   const int tx = threadIdx.x, ty = threadIdx.y;
   const int tid = ty * 32 + tx;
@@ -318,8 +333,15 @@ __global__ void __launch_bounds__(32 * BY, (BY <= 8 ? 2 : 1)) step_tile_kernel(S
   const int sx = tx + 1, sy = ty + 1;
   const bool interior = tx >= 1 && tx <= kTileX && ty >= 1 && ty <= BY - 2;
   const bool valid = interior && gx < nx && gy < ny;
+  // CTU: the threads whose cell's face states are used (all but the four corner threads)
+  const bool tneed = CTU && ((ty >= 1 && ty <= BY - 2) || (tx >= 1 && tx <= kTileX));
+  // staged cells: the box without its corners (CTU: without its outer corners)
+  auto staged = [](int qy, int qx) {
+    return (qy >= 2 && qy <= BY - 1) || (qx >= 2 && qx <= 31) || (CTU && qy >= 1 && qy <= BY && qx >= 1 && qx <= 32);
+  };
 
-  // Staged cells: the 34 x (BY+2) box (x0-2 .. x0+31, y0-2 .. y0+BY-1) without its corners.
+  // Staged cells: the 34 x (BY+2) box (x0-2 .. x0+31, y0-2 .. y0+BY-1) without its corners
+  // (staged()).
   // A thread stages and later converts the same cells, so the copies it waits for are its
   // own and no barrier separates staging from conversion.
   auto stage = [&](int z) {
@@ -329,7 +351,7 @@ __global__ void __launch_bounds__(32 * BY, (BY <= 8 ? 2 : 1)) step_tile_kernel(S
     unsigned *meta = sMeta + slot(z) * NQ;
     for (int i = tid; i < NQ; i += 32 * BY) {
       const int qy = i / SX, qx = i - qy * SX;
-      if (!((qy >= 2 && qy <= BY - 1) || (qx >= 2 && qx <= 31))) continue;
+      if (!staged(qy, qx)) continue;
       bool mx, my;
       const int xx = map_index(x0 - 2 + qx, nx, a.bc[0], a.bc[1], mx);
       const int yy = map_index(y0 - 2 + qy, ny, a.bc[2], a.bc[3], my);
@@ -349,7 +371,7 @@ __global__ void __launch_bounds__(32 * BY, (BY <= 8 ? 2 : 1)) step_tile_kernel(S
     T *dst = sW + b * PL;
     for (int i = tid; i < NQ; i += 32 * BY) {
       const int qy = i / SX, qx = i - qy * SX;
-      if (!((qy >= 2 && qy <= BY - 1) || (qx >= 2 && qx <= 31))) continue;
+      if (!staged(qy, qx)) continue;
       const unsigned m = meta[i];
       T U[NV], W[NV];
 #pragma unroll
@@ -374,6 +396,61 @@ __global__ void __launch_bounds__(32 * BY, (BY <= 8 ? 2 : 1)) step_tile_kernel(S
     recon<SCH>(wm, w0, wp, nuz, lo, hi);
     if (RETRY) first_order_faces(fl(buf(p - 1), sy, sx), fl(buf(p), sy, sx), fl(buf(p + 1), sy, sx), w0, lo, hi);
   };
+  // CTU: z reconstruction of cell p with the transverse terms X_z = T_x + T_y (global order,
+  // xg in the thread's slot of free shared memory); the cell's own T_z is added to X_x and
+  // X_y in its private slots when `keep`
+  auto recon_z_ctu = [&](int p, const T *xg, bool keep, T (&lo)[NV], T (&hi)[NV]) {
+    T wm[NV], w0[NV], wp[NV];
+    gather<T, 2, SY, SX>(sW + buf(p - 1) * PL, sy, sx, wm);
+    gather<T, 2, SY, SX>(sW + buf(p) * PL, sy, sx, w0);
+    gather<T, 2, SY, SX>(sW + buf(p + 1) * PL, sy, sx, wp);
+    if constexpr (CTU)
+      recon_ctu<SCH>(
+          wm, w0, wp, nuz, [&](int k) { return xg[Frame<2>::g(k) * BY * 32 + tid]; },
+          [&](int k, T v) {
+            if (keep) {
+              sCx[Frame<2>::g(k) * BY * 32 + tid] += v;
+              sCy[Frame<2>::g(k) * BY * 32 + tid] += v;
+            }
+          },
+          lo, hi);
+    if (RETRY) first_order_faces(fl(buf(p - 1), sy, sx), fl(buf(p), sy, sx), fl(buf(p + 1), sy, sx), w0, lo, hi);
+  };
+  // CTU: T_x and T_y of the thread's cell in plane p (global order): X_z = T_x + T_y to xz,
+  // and T_y to its X_x slot, T_x to its X_y slot (all thread-private)
+  auto trans_x_y = [&](int p, T *xz) {
+    const T *pl = sW + buf(p) * PL;
+    T wm[NV], w0[NV], wp[NV], o[NV];
+    gather<T, 0, SY, SX>(pl, sy, sx - 1, wm);
+    gather<T, 0, SY, SX>(pl, sy, sx, w0);
+    gather<T, 0, SY, SX>(pl, sy, sx + 1, wp);
+    transverse(wm, w0, wp, nux, o);  // the x frame is the global order
+#pragma unroll
+    for (int k = 0; k < NV; k++) {
+      xz[k * BY * 32 + tid] = o[k];
+      sCy[k * BY * 32 + tid] = o[k];
+    }
+    gather<T, 1, SY, SX>(pl, sy - 1, sx, wm);
+    gather<T, 1, SY, SX>(pl, sy, sx, w0);
+    gather<T, 1, SY, SX>(pl, sy + 1, sx, wp);
+    transverse(wm, w0, wp, nuy, o);
+#pragma unroll
+    for (int k = 0; k < NV; k++) {
+      const int gk = Frame<1>::g(k);
+      xz[gk * BY * 32 + tid] += o[k];
+      sCx[gk * BY * 32 + tid] = o[k];
+    }
+  };
+  // CTU: the z face states of cell p (interior threads: lo, hi) and, for every thread whose
+  // cell is used (keep), X_x = T_y + T_z and X_y = T_x + T_z of cell p in its private slots.
+  // X_z = T_x + T_y waits in the raw staging slot of plane p + 1, which holds no pending
+  // data here (its plane is converted and the next copy into it comes after the next
+  // barrier), in the thread's own cells.
+  auto ctu_plane = [&](int p, bool keep, T (&lo)[NV], T (&hi)[NV]) {
+    T *xz = sR + slot(p + 1) * PL;
+    trans_x_y(p, xz);
+    recon_z_ctu(p, xz, keep, lo, hi);
+  };
 
   Acc<T> diag;
   diag.zero();
@@ -395,7 +472,13 @@ __global__ void __launch_bounds__(32 * BY, (BY <= 8 ? 2 : 1)) step_tile_kernel(S
   T hprev[NV], Fprev[NV];
   if (interior) {
     T lo[NV];
-    recon_z(z0 - 1, lo, hprev);
+    if constexpr (CTU) {
+      // X_z of cell z0-1 in the raw slot of plane z0+1, which is staged only below; the X_x,
+      // X_y slots written here are rewritten for plane z0 before their first use
+      ctu_plane(z0 - 1, false, lo, hprev);
+    } else {
+      recon_z(z0 - 1, lo, hprev);
+    }
   }
   stage(z0 + 1);
   cp_async_wait<0>();
@@ -403,12 +486,18 @@ __global__ void __launch_bounds__(32 * BY, (BY <= 8 ? 2 : 1)) step_tile_kernel(S
   convert(z0 + 1);
   stage(z0 + 2);
   __syncthreads();
-  if (interior) {
+  {
     T lo[NV], hi[NV];
-    recon_z(z0, lo, hi);
-    face_flux<SCH, RETRY>(hprev, lo, fl(buf(z0 - 1), sy, sx) || fl(buf(z0), sy, sx), Fprev);
+    if constexpr (CTU) {
+      if (tneed) ctu_plane(z0, true, lo, hi);
+    } else if (interior) {
+      recon_z(z0, lo, hi);
+    }
+    if (interior) {
+      face_flux<SCH, RETRY>(hprev, lo, fl(buf(z0 - 1), sy, sx) || fl(buf(z0), sy, sx), Fprev);
 #pragma unroll
-    for (int k = 0; k < NV; k++) hprev[k] = hi[k];
+      for (int k = 0; k < NV; k++) hprev[k] = hi[k];
+    }
   }
   cp_async_wait<0>();
   __syncthreads();  // plane z0-1 is no longer read
@@ -426,7 +515,12 @@ __global__ void __launch_bounds__(32 * BY, (BY <= 8 ? 2 : 1)) step_tile_kernel(S
       gather<T, 0, SY, SX>(pl, sy, sx - 1, wm);
       gather<T, 0, SY, SX>(pl, sy, sx, w0);
       gather<T, 0, SY, SX>(pl, sy, sx + 1, wp);
-      recon<SCH>(wm, w0, wp, nux, lo, hi);
+      if constexpr (CTU) {
+        recon_ctu<SCH>(
+            wm, w0, wp, nux, [&](int k) { return sCx[k * BY * 32 + tid]; }, [](int, T) {}, lo, hi);
+      } else {
+        recon<SCH>(wm, w0, wp, nux, lo, hi);
+      }
       if (RETRY) first_order_faces(fl(buf(z), sy, sx - 1), fl(buf(z), sy, sx), fl(buf(z), sy, sx + 1), w0, lo, hi);
 #pragma unroll
       for (int k = 0; k < NV; k++) hl[k] = __shfl_up_sync(FULL, hi[k], 1);
@@ -441,7 +535,12 @@ __global__ void __launch_bounds__(32 * BY, (BY <= 8 ? 2 : 1)) step_tile_kernel(S
       gather<T, 1, SY, SX>(pl, sy - 1, sx, wm);
       gather<T, 1, SY, SX>(pl, sy, sx, w0);
       gather<T, 1, SY, SX>(pl, sy + 1, sx, wp);
-      recon<SCH>(wm, w0, wp, nuy, ylo, hi);
+      if constexpr (CTU) {
+        recon_ctu<SCH>(
+            wm, w0, wp, nuy, [&](int k) { return sCy[Frame<1>::g(k) * BY * 32 + tid]; }, [](int, T) {}, ylo, hi);
+      } else {
+        recon<SCH>(wm, w0, wp, nuy, ylo, hi);
+      }
       if (RETRY) first_order_faces(fl(buf(z), sy - 1, sx), fl(buf(z), sy, sx), fl(buf(z), sy + 1, sx), w0, ylo, hi);
 #pragma unroll
       for (int k = 0; k < NV; k++) sXh[(k * BY + ty) * 32 + tx] = hi[k];
@@ -458,15 +557,21 @@ __global__ void __launch_bounds__(32 * BY, (BY <= 8 ? 2 : 1)) step_tile_kernel(S
 #pragma unroll
       for (int k = 0; k < NV; k++) sXf[(k * BY + ty) * 32 + tx] = Fy[k];
     }
-    if (interior) {  // z: reconstruct cell z+1, flux through the upper z face of cell z
+    {  // z: reconstruct cell z+1, flux through the upper z face of cell z
       T lo[NV], hi[NV], F[NV];
-      recon_z(z + 1, lo, hi);
+      if constexpr (CTU) {
+        if (tneed) ctu_plane(z + 1, true, lo, hi);
+      } else if (interior) {
+        recon_z(z + 1, lo, hi);
+      }
+      if (interior) {
       face_flux<SCH, RETRY>(hprev, lo, fl(buf(z), sy, sx) || fl(buf(z + 1), sy, sx), F);
 #pragma unroll
       for (int k = 0; k < NV; k++) {
         acc[Frame<2>::g(k)] += (Fprev[k] - F[k]) * idz;
         hprev[k] = hi[k];
         Fprev[k] = F[k];
+      }
       }
     }
     __syncthreads();
@@ -477,11 +582,11 @@ __global__ void __launch_bounds__(32 * BY, (BY <= 8 ? 2 : 1)) step_tile_kernel(S
     if (valid) {
       const size_t c = ((size_t)z * ny + gy) * nx + gx;
       if (RAW == 4)  // the swept state as staged (an interior cell is never a reflect image)
-        finish_cell<T, NDIM, SCH, RETRY>(a, sR + slot(z) * PL + sy * SX + sx, NQ, U0 + c, Ud, N, c, acc, dt, idx,
-                                         idy, idz, diag, smax, bad, tag, ck);
+        finish_cell<T, NDIM, SCH, RETRY, CTU>(a, sR + slot(z) * PL + sy * SX + sx, NQ, U0 + c, Ud, N, c, acc, dt,
+                                              idx, idy, idz, diag, smax, bad, tag, ck);
       else
-        finish_cell<T, NDIM, SCH, RETRY>(a, Us + c, N, U0 + c, Ud, N, c, acc, dt, idx, idy, idz, diag, smax, bad,
-                                         tag, ck);
+        finish_cell<T, NDIM, SCH, RETRY, CTU>(a, Us + c, N, U0 + c, Ud, N, c, acc, dt, idx, idy, idz, diag, smax,
+                                              bad, tag, ck);
     }
     // Plane z is no longer read (every read of the primitive planes precedes the second
     // barrier); plane z+3 replaces it.  The next iteration reads it only after its first
@@ -504,8 +609,12 @@ __global__ void __launch_bounds__(32 * BY, (BY <= 8 ? 2 : 1)) step_tile_kernel(S
 // face state and flux of the previous row carried, so every cell is reconstructed once
 // per direction.  Warps never wait on one another inside a tile; a thread block of WARPS
 // strips writes one partial.
-template <typename T, int WARPS, int SCH, bool RETRY>
+// CTU: the corner-transport-upwind form.  The y reconstruction of cell y+1 takes X_y = T_x
+// of its row (formed from the row's shuffled neighbours) and yields the cell's own T_y,
+// which waits in lane-private shared memory as X_x of the next row's x sweep.
+template <typename T, int WARPS, int SCH, bool RETRY, bool CTU = false>
 __global__ void __launch_bounds__(32 * WARPS) step_strip2d_kernel(StepArgs<T> a) {
+  __shared__ T sTy[CTU ? WARPS : 1][NV][32];  // CTU: T_y of the lane's cell in the row of the x sweep
   const Ctrl *ctrl = a.ctrl;
   if (ctrl->done) return;
   if (RETRY && ctrl->nbad[a.level - 1] == 0) return;
@@ -556,6 +665,33 @@ __global__ void __launch_bounds__(32 * WARPS) step_strip2d_kernel(StepArgs<T> a)
 #pragma unroll
         for (int k = 0; k < NV; k++) o[k] = w[Frame<1>::g(k)];
       };
+      // CTU: T_x of a row held in the y frame, returned in the y frame (all lanes take part)
+      auto trans_x = [&](const T (&ry)[NV], T (&Xy)[NV]) {
+        T w0[NV], wm[NV], wp[NV], o[NV];
+#pragma unroll
+        for (int k = 0; k < NV; k++) w0[k] = ry[Frame<1>::g(k)];  // Frame<1> is an involution
+#pragma unroll
+        for (int k = 0; k < NV; k++) {
+          wm[k] = __shfl_up_sync(FULL, w0[k], 1);
+          wp[k] = __shfl_down_sync(FULL, w0[k], 1);
+        }
+        transverse(wm, w0, wp, nux, o);
+#pragma unroll
+        for (int k = 0; k < NV; k++) Xy[k] = o[Frame<1>::g(k)];
+      };
+      // y reconstruction (y frame), with CTU the transverse term X_y = T_x of the cell's row
+      // and the cell's own T_y stored (global order) for the x sweep of that row
+      auto recon_y = [&](const T (&wm)[NV], const T (&w0)[NV], const T (&wp)[NV], T (&lo)[NV], T (&hi)[NV]) {
+        if constexpr (CTU) {
+          T Xy[NV];
+          trans_x(w0, Xy);
+          recon_ctu<SCH>(
+              wm, w0, wp, nuy, [&](int k) { return Xy[k]; },
+              [&](int k, T v) { sTy[CTU ? warp : 0][Frame<1>::g(k)][lane] = v; }, lo, hi);
+        } else {
+          recon<SCH>(wm, w0, wp, nuy, lo, hi);
+        }
+      };
       // ring: rows y, y+1, y+2 (primitive, y local frame) and their tags
       T r0[NV], r1[NV], r2[NV], hprev[NV], Fprev[NV];
       bool f0 = false, f1 = false, f2 = false;
@@ -567,9 +703,9 @@ __global__ void __launch_bounds__(32 * WARPS) step_strip2d_kernel(StepArgs<T> a)
         fetch(y0, U, f1); cons_to_prim(U, w); ylocal(w, r1);
         fetch(y0 + 1, U, f2); cons_to_prim(U, w); ylocal(w, r2);
         T lo[NV], hi[NV];
-        recon<SCH>(wa, r0, r1, nuy, lo, hprev);  // cell y0-1
+        recon_y(wa, r0, r1, lo, hprev);  // cell y0-1
         if (RETRY) first_order_faces(fa, f0, f1, r0, lo, hprev);
-        recon<SCH>(r0, r1, r2, nuy, lo, hi);     // cell y0
+        recon_y(r0, r1, r2, lo, hi);     // cell y0 (CTU: its T_y for the first x sweep)
         if (RETRY) first_order_faces(f0, f1, f2, r1, lo, hi);
         face_flux<SCH, RETRY>(hprev, lo, f0 || f1, Fprev);  // flux through y0 - 1/2
 #pragma unroll
@@ -595,7 +731,12 @@ __global__ void __launch_bounds__(32 * WARPS) step_strip2d_kernel(StepArgs<T> a)
             wm[k] = __shfl_up_sync(FULL, w0[k], 1);
             wp[k] = __shfl_down_sync(FULL, w0[k], 1);
           }
-          recon<SCH>(wm, w0, wp, nux, lo, hi);
+          if constexpr (CTU) {
+            recon_ctu<SCH>(
+                wm, w0, wp, nux, [&](int k) { return sTy[CTU ? warp : 0][k][lane]; }, [](int, T) {}, lo, hi);
+          } else {
+            recon<SCH>(wm, w0, wp, nux, lo, hi);
+          }
           bool fxlo = false;  // the lower x face has first-order states
           if (RETRY) {
             const bool fm = __shfl_up_sync(FULL, f0, 1), fp = __shfl_down_sync(FULL, f0, 1);
@@ -614,7 +755,7 @@ __global__ void __launch_bounds__(32 * WARPS) step_strip2d_kernel(StepArgs<T> a)
           cons_to_prim(Un2, w);
           ylocal(w, r2);
           T lo[NV], hi[NV], F[NV];
-          recon<SCH>(r0, r1, r2, nuy, lo, hi);
+          recon_y(r0, r1, r2, lo, hi);
           if (RETRY) first_order_faces(f0, f1, f2, r1, lo, hi);
           face_flux<SCH, RETRY>(hprev, lo, f0 || f1, F);
 #pragma unroll
@@ -625,8 +766,8 @@ __global__ void __launch_bounds__(32 * WARPS) step_strip2d_kernel(StepArgs<T> a)
           }
         }
         if (upd)
-          finish_cell<T, 2, SCH, RETRY>(a, Us + ((size_t)y * nx + gx), N, U0 + ((size_t)y * nx + gx), Ud, N,
-                                        (size_t)y * nx + gx, acc, dt, idx, idy, T(0), diag, smax, bad, tag, ck);
+          finish_cell<T, 2, SCH, RETRY, CTU>(a, Us + ((size_t)y * nx + gx), N, U0 + ((size_t)y * nx + gx), Ud, N,
+                                             (size_t)y * nx + gx, acc, dt, idx, idy, T(0), diag, smax, bad, tag, ck);
 #pragma unroll
         for (int k = 0; k < NV; k++) {
           r0[k] = r1[k];
@@ -655,12 +796,14 @@ inline int fallback_blocks() {
 }
 
 // 3D: 3 + RAW staged planes (three primitive, RAW raw) of NV x (rows+2) x 34, the y-sweep
-// face states and fluxes (2 x NV x rows x 32) and RAW planes of per-cell flags.
-template <typename T> size_t step_smem(int ndim, int rows) {
+// face states and fluxes (2 x NV x rows x 32), with CTU the per-thread X_x and X_y
+// (2 x NV x rows x 32), and RAW planes of per-cell flags.
+template <typename T> size_t step_smem(int ndim, int rows, bool ctu) {
   if (ndim < 3) return 0;
   const size_t nq = (size_t)(rows + 2) * 34;
-  const size_t raw = rows == 16 ? kRawPlanes<T, 16> : rows == 8 ? kRawPlanes<T, 8> : kRawPlanes<T, 4>;
-  return sizeof(T) * ((3 + raw) * NV * nq + (size_t)2 * NV * rows * 32) + raw * nq * sizeof(unsigned);
+  const size_t raw = ctu ? 2 : rows == 16 ? kRawPlanes<T, 16> : rows == 8 ? kRawPlanes<T, 8> : kRawPlanes<T, 4>;
+  const size_t per_thread = ctu ? 4 : 2;
+  return sizeof(T) * ((3 + raw) * NV * nq + per_thread * NV * rows * 32) + raw * nq * sizeof(unsigned);
 }
 
 template <typename T> int step_blocks(int ndim, int rows, int nx, int ny, int nz, int zchunk) {
@@ -675,35 +818,37 @@ template <typename T> int step_blocks(int ndim, int rows, int nx, int ny, int nz
   return bx * by * bz;
 }
 
-template <typename T, int NDIM, int BY, int SCH, bool RETRY>
+template <typename T, int NDIM, int BY, int SCH, bool RETRY, bool CTU>
 static cudaError_t launch_tile(const StepArgs<T> &a, cudaStream_t s) {
   if constexpr (sizeof(T) == 8 && BY == 16) {
     return cudaErrorInvalidConfiguration;  // 326 KB of shared memory: not offered for FP64
   } else {
-  const size_t smem = step_smem<T>(NDIM, BY);
+  const size_t smem = step_smem<T>(NDIM, BY, CTU);
   static bool attr_set = false;  // one attribute call per instantiation and process
   if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(step_tile_kernel<T, NDIM, BY, SCH, RETRY>,
+    cudaError_t e = cudaFuncSetAttribute(step_tile_kernel<T, NDIM, BY, SCH, RETRY, CTU>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     attr_set = true;
   }
   const int ntiles = step_blocks<T>(NDIM, BY, a.nx, a.ny, a.nz, a.zchunk);
   const int blocks = RETRY ? std::min(ntiles, fallback_blocks()) : ntiles;
-  step_tile_kernel<T, NDIM, BY, SCH, RETRY><<<blocks, dim3(32, BY), smem, s>>>(a);
+  step_tile_kernel<T, NDIM, BY, SCH, RETRY, CTU><<<blocks, dim3(32, BY), smem, s>>>(a);
   return cudaGetLastError();
   }
 }
 
-template <typename T, int WARPS, int SCH, bool RETRY>
+template <typename T, int WARPS, int SCH, bool RETRY, bool CTU>
 static cudaError_t launch_strip2d(const StepArgs<T> &a, cudaStream_t s) {
   const int groups = step_blocks<T>(2, WARPS, a.nx, a.ny, 1, a.zchunk);
   const int blocks = RETRY ? std::min(groups, fallback_blocks()) : groups;
-  step_strip2d_kernel<T, WARPS, SCH, RETRY><<<blocks, 32 * WARPS, 0, s>>>(a);
+  step_strip2d_kernel<T, WARPS, SCH, RETRY, CTU><<<blocks, 32 * WARPS, 0, s>>>(a);
   return cudaGetLastError();
 }
 
-template <typename T, int SCH, bool RETRY>
+// CTU: the corner-transport-upwind form of the 2D and 3D kernels (in 1D there is no
+// transverse direction and the max-form CFL rule is the sum; the plain kernel runs).
+template <typename T, int SCH, bool RETRY, bool CTU = false>
 static cudaError_t launch_step_mode(const StepArgs<T> &a, int ndim, int rows, cudaStream_t s) {
   if (ndim == 1) {
     const int ntiles = (a.nx + kTile1D - 3) / (kTile1D - 2);
@@ -711,13 +856,23 @@ static cudaError_t launch_step_mode(const StepArgs<T> &a, int ndim, int rows, cu
     return cudaGetLastError();
   }
   if (ndim == 2) {
-    if (rows == 4) return launch_strip2d<T, 4, SCH, RETRY>(a, s);
-    if (rows == 16) return launch_strip2d<T, 16, SCH, RETRY>(a, s);
-    return launch_strip2d<T, 8, SCH, RETRY>(a, s);
+    if (rows == 4) return launch_strip2d<T, 4, SCH, RETRY, CTU>(a, s);
+    if (rows == 16) return launch_strip2d<T, 16, SCH, RETRY, CTU>(a, s);
+    return launch_strip2d<T, 8, SCH, RETRY, CTU>(a, s);
   }
-  if (rows == 4) return launch_tile<T, 3, 4, SCH, RETRY>(a, s);
-  if (rows == 16) return launch_tile<T, 3, 16, SCH, RETRY>(a, s);
-  return launch_tile<T, 3, 8, SCH, RETRY>(a, s);
+  if (rows == 4) return launch_tile<T, 3, 4, SCH, RETRY, CTU>(a, s);
+  if (rows == 16) return launch_tile<T, 3, 16, SCH, RETRY, CTU>(a, s);
+  return launch_tile<T, 3, 8, SCH, RETRY, CTU>(a, s);
+}
+
+// The corner-transport-upwind form of the characteristic step with the flux of scheme SCH
+// (0 HLL, 3 Roe-type, 4 HLLC); same contract as launch_step.  Instantiated once per
+// scheme in its own translation unit (msh_step_ctu_*.cu).
+template <typename T, int SCH>
+cudaError_t launch_step_ctu(const StepArgs<T> &a, int ndim, int rows, bool retry, cudaStream_t s, int *nblocks_out) {
+  if (nblocks_out) *nblocks_out = step_blocks<T>(ndim, rows, a.nx, a.ny, a.nz, a.zchunk);
+  return retry ? launch_step_mode<T, SCH, true, true>(a, ndim, rows, s)
+               : launch_step_mode<T, SCH, false, true>(a, ndim, rows, s);
 }
 
 }  // namespace msh

@@ -64,6 +64,8 @@ SIGNATURES = {
     "msh_adjoint_run": [_vp, _vp, _i64, _P(_dbl), _i32, _vp, _vp, _i32, _i32],
     "msh_set_tape": [_vp, _i32, _i64],
     "msh_set_scheme": [_vp, _i32],
+    "msh_set_ctu": [_vp, _i32],
+    "msh_get_ctu": [_vp, _P(_i32)],
     "msh_set_self_gravity": [_vp, _dbl],
     "msh_set_cell_width": [_vp, _P(_dbl)],
     "msh_get_slab": [_vp, _i64, _i64, _vp, _i32],
@@ -347,6 +349,16 @@ class Grid:
         """MUSCL_HANCOCK (default, HLL), MUSCL_HANCOCK_ROE, MUSCL_HANCOCK_HLLC or KT (see
         ``msh_set_scheme``)."""
         _check(load().msh_set_scheme(self.h, int(scheme)))
+
+    def set_ctu(self, on=True):
+        """Corner-transport-upwind form of the characteristic schemes (transverse terms in
+        the face states, max-form CFL rule; see ``msh_set_ctu``)."""
+        _check(load().msh_set_ctu(self.h, 1 if on else 0))
+
+    def get_ctu(self):
+        r = C.c_int32()
+        _check(load().msh_get_ctu(self.h, C.byref(r)))
+        return bool(r.value)
 
     # -- slab decomposition -------------------------------------------------------
     def set_cell_width(self, dx):
