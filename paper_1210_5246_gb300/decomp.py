@@ -319,8 +319,10 @@ class GridStepper:
 
 
 def make_grid_steppers(msh, n, lo, hi, bc, cfl, precision, U, slabs: Slabs, ranks, phi=None, stream=None,
-                       scheme=0):
-    """Local libmsh grids (state set, potential sliced, scheme selected) for the given ranks."""
+                       scheme=0, ctu=False):
+    """Local libmsh grids (state set, potential sliced, scheme and its corner-transport-upwind
+    form selected) for the given ranks.  The transverse terms of a cell reach one cell along
+    each axis, inside the two halo layers of the characteristic step."""
     parts = split_state(U, n, slabs)
     a = len(n) - 1
     periodic = bc[a][0] == 0
@@ -332,6 +334,8 @@ def make_grid_steppers(msh, n, lo, hi, bc, cfl, precision, U, slabs: Slabs, rank
         g.set_cell_width(dx)
         if scheme:
             g.set_scheme(scheme)
+        if ctu:
+            g.set_ctu(True)
         if phi is not None:
             g.set_potential(local_potential(phi, n, sl, periodic))
         g.set_state(parts[r].astype(g.dtype), msh.CONSERVED)

@@ -17,9 +17,10 @@ from paper_1210_5246_gb300 import decomp, inputs
 class OracleStepper:
     """A slab stepped by the oracle (test helper)."""
 
-    def __init__(self, oracle, n, lo, hi, bc, cfl, U, dx, phi=None):
+    def __init__(self, oracle, n, lo, hi, bc, cfl, U, dx, phi=None, scheme=0, ctu=False):
         self.o = oracle
         self.n, self.bc, self.cfl, self.dx = tuple(n), tuple(bc), cfl, tuple(dx)
+        self.scheme, self.ctu = scheme, ctu
         self.g = self._grid(self.n)
         self.U = np.array(U, dtype=np.float64).reshape((10,) + (1,) * (3 - len(n)) + tuple(reversed(n)))
         self.phi = phi
@@ -27,7 +28,8 @@ class OracleStepper:
 
     def _grid(self, n):
         """Oracle grid of n cells with this slab's cell widths set exactly."""
-        g = self.o.Grid(n, (0.0,) * len(n), tuple(m * d for m, d in zip(n, self.dx)), self.bc, self.cfl)
+        g = self.o.Grid(n, (0.0,) * len(n), tuple(m * d for m, d in zip(n, self.dx)), self.bc, self.cfl,
+                        scheme=self.scheme, ctu=self.ctu)
         for d, w in enumerate(self.dx):
             g._g.dx[d] = w
         return g
@@ -226,3 +228,26 @@ def test_kt_slabs_need_four_halo_layers(oracle):
         ns, t = drv.run(steps)
         got = decomp.join_owned([st[r].U for r in range(3)], n, S)
         assert np.array_equal(got, ref.reshape(got.shape)) == equal
+
+
+@pytest.mark.parametrize("name,scheme", [("box3d", 0), ("blast2d", 2), ("box3d", 3)])
+def test_ctu_slabs_equal_single_grid(oracle, name, scheme):
+    """The corner-transport-upwind form (transverse terms reach one cell along each axis,
+    max-form CFL reduced over the slabs) stays inside the two halo layers: three slabs
+    reproduce the single grid bit for bit."""
+    p = inputs.turb(n=16) if name == "box3d" else inputs.blast(n=32)
+    n, steps = p.n, 3
+    og = oracle.Grid(n, p.lo, p.hi, p.bc, 0.8, scheme=scheme, ctu=True)
+    ref, _, t_ref, rc, _ = oracle.run(og, oracle.prim_to_cons(p.W), np.inf, max_steps=steps)
+    assert rc == 0
+    S = decomp.Slabs(n[-1], 3, True)
+    parts = decomp.split_state(oracle.prim_to_cons(p.W), n, S)
+    st = {}
+    for r in range(3):
+        n_l, lo_l, hi_l, bc_l, dx = decomp.local_geometry(n, p.lo, p.hi, p.bc, S[r])
+        st[r] = OracleStepper(oracle, n_l, lo_l, hi_l, bc_l, 0.8, parts[r], dx, scheme=scheme, ctu=True)
+    drv = decomp.SlabDriver(S, st)
+    ns, t = drv.run(steps)
+    got = decomp.join_owned([st[r].U for r in range(3)], n, S)
+    assert ns == steps and t == t_ref
+    np.testing.assert_array_equal(got, ref.reshape(got.shape))

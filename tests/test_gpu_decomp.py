@@ -115,3 +115,31 @@ def test_cell_width_override(env):
     np.testing.assert_array_equal(a.get_state(), b.get_state())
     a.close()
     b.close()
+
+
+@pytest.mark.parametrize("name,world,cfl", [("box3d", 3, 0.5), ("blast2d", 4, 0.8)])
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_ctu_slabs_equal_single_grid(env, name, world, cfl, prec):
+    """The corner-transport-upwind form across slabs: bit-identical to the single grid (at
+    CFL numbers whose steps tag no fallback cell, which would couple the slabs within a
+    step; the box tags one in its third step at 0.8)."""
+    msh, I = env
+    p, steps = _problem(I, name)
+    precision = msh.FP64 if prec == "fp64" else msh.FP32
+    W = p.W.astype(np.float32) if precision == msh.FP32 else p.W
+    g = msh.Grid(p.n, p.lo, p.hi, p.bc, cfl, precision)
+    g.set_ctu(True)
+    g.set_state(W, msh.PRIMITIVE)
+    U0 = g.get_state()
+    g.run(max_steps=steps)
+    ref, (t_ref, _) = g.get_state(), g.time()
+    g.close()
+    S = decomp.Slabs(p.n[-1], world, p.bc[-1][0] == 0)
+    st = decomp.make_grid_steppers(msh, p.n, p.lo, p.hi, p.bc, cfl, precision, U0, S, range(world), ctu=True)
+    drv = decomp.SlabDriver(S, st)
+    ns, t = drv.run(steps)
+    got = decomp.join_owned([st[r].g.get_state() for r in range(world)], p.n, S)
+    assert ns == steps and t == t_ref
+    np.testing.assert_array_equal(got, ref)
+    for s in st.values():
+        s.g.close()
