@@ -62,6 +62,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--fp32-only", action="store_true", help="skip the FP64 measurement")
     ap.add_argument("--tiling", default=None, help="rows,zchunk instead of autotuning (e.g. 8,32)")
+    ap.add_argument("--ctu", action="store_true",
+                    help="the corner-transport-upwind form of the step (a profiling case, not the benchmark)")
     ap.add_argument("--suite", action="store_true", help="one JSON line per workload instead of the bench line")
     ap.add_argument("--only", default=None, choices=["sod", "blast", "box", "schemes", "ctu", "selfgrav", "tubes", "disc"],
                     help="with --suite: run one workload (--n and --steps then size it)")
@@ -195,6 +197,8 @@ def run_gpu(args):
 
     def timed(precision, Wdev, steps, warmup, profile):
         g = msh.Grid.from_problem(p, precision, stream=stream.cuda_stream)
+        if args.ctu:
+            g.set_ctu(True)
         g.set_state(Wdev, msh.PRIMITIVE)
         if args.tiling:
             g.set_tiling(*[int(v) for v in args.tiling.split(",")])
@@ -298,7 +302,7 @@ def run_gpu(args):
         "ms_per_step": ms32 / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": DATA[args.workload],
         "config": {"workload": desc.format(n=n_axis) + f", steps 1..{args.steps}",
-                   "cells": ncells, "parallelism": f"replicas x{world}",
+                   "cells": ncells, "parallelism": f"replicas x{world}", "ctu": bool(args.ctu),
                    "l2": (f"state ({state_mb:.0f} MB per buffer) larger than L2; no flush" if state_mb > 129
                           else f"state ({state_mb:.0f} MB per buffer) fits in L2; no flush (L2-assisted)"),
                    "tiling": list(tiling)},

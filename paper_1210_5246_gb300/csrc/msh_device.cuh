@@ -234,17 +234,17 @@ __device__ __forceinline__ void reconstruct(const T (&wm)[NV], const T (&w0)[NV]
 #pragma unroll
   for (int k = 0; k < NV; k++) d[k] = wp[k] - w0[k];
   E.project(d, cr);
+  // limited amplitudes, doubled (every quantity below up to the predictor is exactly twice
+  // its unscaled value, so the face states are bit for bit those of the unscaled form)
+  T m[NV];
+#pragma unroll
+  for (int k = 0; k < NV; k++) m[k] = mc_limit2(cl[k], cr[k]);
   if constexpr (CTU) {
     T o[NV];
     upwind_terms(E, cl, cr, nu, o);
 #pragma unroll
     for (int k = 0; k < NV; k++) tput(k, o[k]);
   }
-  // limited amplitudes, doubled (every quantity below up to the predictor is exactly twice
-  // its unscaled value, so the face states are bit for bit those of the unscaled form)
-  T m[NV];
-#pragma unroll
-  for (int k = 0; k < NV; k++) m[k] = mc_limit2(cl[k], cr[k]);
   // wave speeds relative to u: (-cf, -cs, -cs, 0, 0, 0, 0, cs, cs, cf)
   T lm[NV];
   lm[0] = -E.cf * m[0]; lm[1] = -E.cs * m[1]; lm[2] = -E.cs * m[2];
@@ -291,16 +291,16 @@ __device__ __forceinline__ void reconstruct_upwind(const T (&wm)[NV], const T (&
 #pragma unroll
   for (int k = 0; k < NV; k++) d[k] = wp[k] - w0[k];
   E.project(d, cr);
+  // doubled limited amplitudes: the coefficients below carry the factor 1/2
+  T m[NV];
+#pragma unroll
+  for (int k = 0; k < NV; k++) m[k] = mc_limit2(cl[k], cr[k]);
   if constexpr (CTU) {
     T o[NV];
     upwind_terms(E, cl, cr, nu, o);
 #pragma unroll
     for (int k = 0; k < NV; k++) tput(k, o[k]);
   }
-  // doubled limited amplitudes: the coefficients below carry the factor 1/2
-  T m[NV];
-#pragma unroll
-  for (int k = 0; k < NV; k++) m[k] = mc_limit2(cl[k], cr[k]);
   const T u = E.u;
   const T s[NV] = {-E.cf, -E.cs, -E.cs, T(0), T(0), T(0), T(0), E.cs, E.cs, E.cf};
   const T xM = fmax(u + E.cf, T(0)), y0 = fmin(u - E.cf, T(0)), nu2 = T(0.5) * nu;

@@ -507,9 +507,11 @@ __global__ void __launch_bounds__(32 * BY, (BY <= 8 ? 2 : 1)) step_tile_kernel(S
   for (int z = z0; z < z1; z++) {
     // planes z, z+1, z+2 are converted
     const T *pl = sW + buf(z) * PL;
+    // flux divergence of the cell, accumulated as each face flux becomes known (the lower z
+    // face first; the flux registers die at once, which keeps the register count down)
     T acc[NV];
 #pragma unroll
-    for (int k = 0; k < NV; k++) acc[k] = T(0);
+    for (int k = 0; k < NV; k++) acc[Frame<2>::g(k)] = Fprev[k] * idz;
     if (ty >= 1 && ty <= BY - 2) {  // x sweep, warp-uniform: one warp per row
       T wm[NV], w0[NV], wp[NV], lo[NV], hi[NV], hl[NV], F[NV];
       gather<T, 0, SY, SX>(pl, sy, sx - 1, wm);
@@ -529,7 +531,7 @@ __global__ void __launch_bounds__(32 * BY, (BY <= 8 ? 2 : 1)) step_tile_kernel(S
       for (int k = 0; k < NV; k++) acc[k] += (F[k] - __shfl_down_sync(FULL, F[k], 1)) * idx;
     }
     const bool ycol = tx >= 1 && tx <= kTileX;
-    T ylo[NV], Fy[NV];
+    T ylo[NV];
     if (ycol) {  // y reconstruction of this cell; its upper face state goes to shared memory
       T wm[NV], w0[NV], wp[NV], hi[NV];
       gather<T, 1, SY, SX>(pl, sy - 1, sx, wm);
@@ -550,12 +552,15 @@ __global__ void __launch_bounds__(32 * BY, (BY <= 8 ? 2 : 1)) step_tile_kernel(S
     // slots, z+1 with two) is free for plane z+3.
     if (z + 3 <= z1 + 1) stage(z + 3);
     if (ycol && ty >= 1) {  // flux through the lower y face
-      T hl[NV];
+      T hl[NV], Fy[NV];
 #pragma unroll
       for (int k = 0; k < NV; k++) hl[k] = sXh[(k * BY + ty - 1) * 32 + tx];
       face_flux<SCH, RETRY>(hl, ylo, fl(buf(z), sy - 1, sx) || fl(buf(z), sy, sx), Fy);
 #pragma unroll
-      for (int k = 0; k < NV; k++) sXf[(k * BY + ty) * 32 + tx] = Fy[k];
+      for (int k = 0; k < NV; k++) {
+        sXf[(k * BY + ty) * 32 + tx] = Fy[k];
+        acc[Frame<1>::g(k)] += Fy[k] * idy;
+      }
     }
     {  // z: reconstruct cell z+1, flux through the upper z face of cell z
       T lo[NV], hi[NV], F[NV];
@@ -568,7 +573,7 @@ __global__ void __launch_bounds__(32 * BY, (BY <= 8 ? 2 : 1)) step_tile_kernel(S
       face_flux<SCH, RETRY>(hprev, lo, fl(buf(z), sy, sx) || fl(buf(z + 1), sy, sx), F);
 #pragma unroll
       for (int k = 0; k < NV; k++) {
-        acc[Frame<2>::g(k)] += (Fprev[k] - F[k]) * idz;
+        acc[Frame<2>::g(k)] -= F[k] * idz;
         hprev[k] = hi[k];
         Fprev[k] = F[k];
       }
@@ -577,7 +582,7 @@ __global__ void __launch_bounds__(32 * BY, (BY <= 8 ? 2 : 1)) step_tile_kernel(S
     __syncthreads();
     if (interior) {
 #pragma unroll
-      for (int k = 0; k < NV; k++) acc[Frame<1>::g(k)] += (Fy[k] - sXf[(k * BY + ty + 1) * 32 + tx]) * idy;
+      for (int k = 0; k < NV; k++) acc[Frame<1>::g(k)] -= sXf[(k * BY + ty + 1) * 32 + tx] * idy;
     }
     if (valid) {
       const size_t c = ((size_t)z * ny + gy) * nx + gx;
@@ -720,7 +725,10 @@ __global__ void __launch_bounds__(32 * WARPS) step_strip2d_kernel(StepArgs<T> a)
       for (int y = y0; y < y1; y++) {
         T Un2[NV];
         fetch(y + 2, Un2, f2);  // issued before the x sweep hides its latency
+        // flux divergence of the cell, the lower y face first (Fprev dies at once)
         T acc[NV];
+#pragma unroll
+        for (int k = 0; k < NV; k++) acc[Frame<1>::g(k)] = Fprev[k] * idy;
         {
           // x sweep of row y: local x frame = natural order
           T w0[NV], wm[NV], wp[NV], lo[NV], hi[NV], hl[NV], F[NV];
@@ -747,7 +755,7 @@ __global__ void __launch_bounds__(32 * WARPS) step_strip2d_kernel(StepArgs<T> a)
           for (int k = 0; k < NV; k++) hl[k] = __shfl_up_sync(FULL, hi[k], 1);
           face_flux<SCH, RETRY>(hl, lo, fxlo, F);  // flux through the lower x face of this cell
 #pragma unroll
-          for (int k = 0; k < NV; k++) acc[k] = (F[k] - __shfl_down_sync(FULL, F[k], 1)) * idx;
+          for (int k = 0; k < NV; k++) acc[k] += (F[k] - __shfl_down_sync(FULL, F[k], 1)) * idx;
         }
         {
           // y: reconstruct cell y+1, flux through y + 1/2
@@ -760,7 +768,7 @@ __global__ void __launch_bounds__(32 * WARPS) step_strip2d_kernel(StepArgs<T> a)
           face_flux<SCH, RETRY>(hprev, lo, f0 || f1, F);
 #pragma unroll
           for (int k = 0; k < NV; k++) {
-            acc[Frame<1>::g(k)] += (Fprev[k] - F[k]) * idy;
+            acc[Frame<1>::g(k)] -= F[k] * idy;
             hprev[k] = hi[k];
             Fprev[k] = F[k];
           }

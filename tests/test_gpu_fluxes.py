@@ -46,6 +46,20 @@ def _run(msh, oracle, scheme, n, lo, hi, bc, cfl, W, precision, steps=None, t_en
     return U, Wout, Uo, oracle.cons_to_prim(Uo)
 
 
+def _blast_W(p, scheme):
+    """The blast's initial state; for the Roe-type scheme with a uniform drift.  Its upwind
+    tracing (eqs 40-43) is discontinuous where an eigenvalue crosses zero (a wave of speed
+    0+ enters the face state with weight 1/2, one of speed 0- with 1/2 - nu max(u + cf, 0)),
+    and the blast's contact waves sit at exactly u = 0 in a noisy density: which side of
+    zero their speeds fall on after the first step is decided by rounding, so the GPU and the
+    oracle could take different branches.  A drift moves the eigenvalues off zero."""
+    W = p.W.copy()
+    if scheme[0] == "MUSCL_HANCOCK_ROE":
+        W[1] += 0.25
+        W[2] -= 0.15
+    return W
+
+
 def _random(shape, seed):
     rng = np.random.default_rng(seed)
     W = np.zeros((10,) + shape)
@@ -77,14 +91,15 @@ def test_1d(env, oracle, scheme, n, bc):
 def test_blast(env, oracle, scheme, tiling):
     msh, I = env
     p = I.blast(n=97, nsteps=15)
-    U, _, Uo, _ = _run(msh, oracle, scheme, p.n, p.lo, p.hi, p.bc, p.cfl, p.W, msh.FP64, steps=15, tiling=tiling)
+    U, _, Uo, _ = _run(msh, oracle, scheme, p.n, p.lo, p.hi, p.bc, p.cfl, _blast_W(p, scheme), msh.FP64, steps=15,
+                       tiling=tiling)
     assert_fp64(U, Uo, what=f"{scheme[0]} blast {tiling}")
 
 
 def test_blast_fp32(env, oracle, scheme):
     msh, I = env
     p = I.blast(n=97, nsteps=15)
-    _, W, _, Wo = _run(msh, oracle, scheme, p.n, p.lo, p.hi, p.bc, p.cfl, p.W, msh.FP32, steps=15)
+    _, W, _, Wo = _run(msh, oracle, scheme, p.n, p.lo, p.hi, p.bc, p.cfl, _blast_W(p, scheme), msh.FP32, steps=15)
     assert_fp32(W, Wo, what=f"{scheme[0]} blast fp32")
 
 
