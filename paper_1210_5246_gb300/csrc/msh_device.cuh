@@ -46,6 +46,53 @@ template <> __device__ __forceinline__ float frsqrt<float>(float x) { return rsq
 template <typename T> __device__ __forceinline__ T sqrt_ratio(T p, T r) { return sqrt(p / r); }
 template <> __device__ __forceinline__ float sqrt_ratio<float>(float p, float r) { return p * rsqrtf(p * r); }
 
+// ------------------------------------------------------- paired FP32 arithmetic
+// Componentwise operations on 10-vectors, d_k = a_k s + c_k (v_fma), d_k = a_k s (v_mul) and
+// d_k = a_k - b_k (v_sub).  In FP32 components (k, k+1) go through the packed f32x2 instructions of sm_100
+// (__ffma2_rn, __fadd2_rn: two single-precision operations per issued instruction, each
+// rounded as its scalar form); FP64 stays scalar.
+template <typename T>
+__device__ __forceinline__ void v_fma(T (&d)[NV], const T (&a)[NV], T s, const T (&c)[NV]) {
+#pragma unroll
+  for (int k = 0; k < NV; k++) d[k] = fma(a[k], s, c[k]);
+}
+template <>
+__device__ __forceinline__ void v_fma<float>(float (&d)[NV], const float (&a)[NV], float s, const float (&c)[NV]) {
+  const float2 ss = make_float2(s, s);
+#pragma unroll
+  for (int k = 0; k < NV; k += 2) {
+    const float2 r = __ffma2_rn(make_float2(a[k], a[k + 1]), ss, make_float2(c[k], c[k + 1]));
+    d[k] = r.x;
+    d[k + 1] = r.y;
+  }
+}
+template <typename T> __device__ __forceinline__ void v_mul(T (&d)[NV], const T (&a)[NV], T s) {
+#pragma unroll
+  for (int k = 0; k < NV; k++) d[k] = a[k] * s;
+}
+template <> __device__ __forceinline__ void v_mul<float>(float (&d)[NV], const float (&a)[NV], float s) {
+  const float2 ss = make_float2(s, s);
+#pragma unroll
+  for (int k = 0; k < NV; k += 2) {
+    const float2 r = __fmul2_rn(make_float2(a[k], a[k + 1]), ss);
+    d[k] = r.x;
+    d[k + 1] = r.y;
+  }
+}
+template <typename T> __device__ __forceinline__ void v_sub(T (&d)[NV], const T (&a)[NV], const T (&b)[NV]) {
+#pragma unroll
+  for (int k = 0; k < NV; k++) d[k] = a[k] - b[k];
+}
+template <>
+__device__ __forceinline__ void v_sub<float>(float (&d)[NV], const float (&a)[NV], const float (&b)[NV]) {
+#pragma unroll
+  for (int k = 0; k < NV; k += 2) {
+    const float2 r = __fadd2_rn(make_float2(a[k], a[k + 1]), make_float2(-b[k], -b[k + 1]));
+    d[k] = r.x;
+    d[k + 1] = r.y;
+  }
+}
+
 // ---------------------------------------------------------------- conversions
 // E_ij = P_ij + rho u_i u_j (Sec. 2).  The FP32 path recomputes a diagonal dispersion
 // in FP64 when the kinetic part cancels more than 99.9 % of E_ii, i.e. where P_ii/rho
@@ -109,6 +156,26 @@ template <typename T> __device__ __forceinline__ T mc_limit(T dl, T dr) {
 template <typename T> __device__ __forceinline__ T mc_limit2(T dl, T dr) {
   const T m = fmin(T(4) * fmin(fabs(dl), fabs(dr)), fabs(dl + dr));
   return (dl * dr > T(0)) ? copysign(m, dl) : T(0);
+}
+
+// The doubled limiter on every amplitude of a 10-vector (FP32: the sum, the product and the
+// factor 4 in packed f32x2 instructions; the same values as mc_limit2).
+template <typename T> __device__ __forceinline__ void mc_limit2_v(const T (&dl)[NV], const T (&dr)[NV], T (&m)[NV]) {
+#pragma unroll
+  for (int k = 0; k < NV; k++) m[k] = mc_limit2(dl[k], dr[k]);
+}
+template <>
+__device__ __forceinline__ void mc_limit2_v<float>(const float (&dl)[NV], const float (&dr)[NV], float (&m)[NV]) {
+#pragma unroll
+  for (int k = 0; k < NV; k += 2) {
+    const float2 a = make_float2(dl[k], dl[k + 1]), b = make_float2(dr[k], dr[k + 1]);
+    const float2 sum = __fadd2_rn(a, b), prod = __fmul2_rn(a, b);
+    const float2 q = __fmul2_rn(make_float2(4.0f, 4.0f), make_float2(fminf(fabsf(a.x), fabsf(b.x)),
+                                                                        fminf(fabsf(a.y), fabsf(b.y))));
+    const float m0 = fminf(q.x, fabsf(sum.x)), m1 = fminf(q.y, fabsf(sum.y));
+    m[k] = prod.x > 0.0f ? copysignf(m0, a.x) : 0.0f;
+    m[k + 1] = prod.y > 0.0f ? copysignf(m1, a.y) : 0.0f;
+  }
 }
 
 // Eigen-quantities of the local-frame state w0 shared by projection and back-projection.
@@ -228,17 +295,14 @@ __device__ __forceinline__ void reconstruct(const T (&wm)[NV], const T (&w0)[NV]
   Eig<T> E;
   E.init(w0);
   T d[NV], cl[NV], cr[NV];
-#pragma unroll
-  for (int k = 0; k < NV; k++) d[k] = w0[k] - wm[k];
+  v_sub(d, w0, wm);
   E.project(d, cl);
-#pragma unroll
-  for (int k = 0; k < NV; k++) d[k] = wp[k] - w0[k];
+  v_sub(d, wp, w0);
   E.project(d, cr);
   // limited amplitudes, doubled (every quantity below up to the predictor is exactly twice
   // its unscaled value, so the face states are bit for bit those of the unscaled form)
   T m[NV];
-#pragma unroll
-  for (int k = 0; k < NV; k++) m[k] = mc_limit2(cl[k], cr[k]);
+  mc_limit2_v(cl, cr, m);
   if constexpr (CTU) {
     T o[NV];
     upwind_terms(E, cl, cr, nu, o);
@@ -254,14 +318,15 @@ __device__ __forceinline__ void reconstruct(const T (&wm)[NV], const T (&w0)[NV]
   E.back(m, dw);   // 2 dw^m, dw^m the limited primitive slope
   E.back(lm, g);   // 2 (A dw^m - u dw^m)
   const T nu2 = T(0.5) * nu;
+  T adw[NV], pred[NV];
+  v_fma(adw, dw, E.u, g);
+  v_fma(pred, adw, -nu2, w0);
+  if constexpr (CTU) {
 #pragma unroll
-  for (int k = 0; k < NV; k++) {
-    const T adw = E.u * dw[k] + g[k];
-    T pred = w0[k] - nu2 * adw;
-    if constexpr (CTU) pred += xget(k);
-    hi[k] = pred + T(0.25) * dw[k];
-    lo[k] = pred - T(0.25) * dw[k];
+    for (int k = 0; k < NV; k++) pred[k] += xget(k);
   }
+  v_fma(hi, dw, T(0.25), pred);
+  v_fma(lo, dw, T(-0.25), pred);
   face_state_check(w0, lo, hi);
 }
 
@@ -293,8 +358,7 @@ __device__ __forceinline__ void reconstruct_upwind(const T (&wm)[NV], const T (&
   E.project(d, cr);
   // doubled limited amplitudes: the coefficients below carry the factor 1/2
   T m[NV];
-#pragma unroll
-  for (int k = 0; k < NV; k++) m[k] = mc_limit2(cl[k], cr[k]);
+  mc_limit2_v(cl, cr, m);
   if constexpr (CTU) {
     T o[NV];
     upwind_terms(E, cl, cr, nu, o);
@@ -392,8 +456,11 @@ __device__ __forceinline__ void hll(const T (&wl)[NV], const T (&wr)[NV], T (&F)
     b = -SL * inv;
     c = SL * SR * inv;
   }
-#pragma unroll
-  for (int k = 0; k < NV; k++) F[k] = a * Fl[k] + (b * Fr[k] + c * (Ur[k] - Ul[k]));
+  T t[NV];
+  v_sub(t, Ur, Ul);
+  v_mul(t, t, c);
+  v_fma(t, Fr, b, t);
+  v_fma(F, Fl, a, t);
 }
 
 // ------------------------------------------------------- Kurganov-Tadmor
@@ -627,7 +694,11 @@ template <> struct Acc<float> {
   }
   __device__ __forceinline__ void add(const float (&x)[NV]) {
 #pragma unroll
-    for (int k = 0; k < NV; k++) v[k] += x[k];
+    for (int k = 0; k < NV; k += 2) {
+      const float2 r = __fadd2_rn(make_float2(v[k], v[k + 1]), make_float2(x[k], x[k + 1]));
+      v[k] = r.x;
+      v[k + 1] = r.y;
+    }
   }
   __device__ __forceinline__ void get(double (&o)[NV]) const {
 #pragma unroll

@@ -109,7 +109,7 @@ __device__ __forceinline__ void finish_cell(const StepArgs<T> &a, const T *src, 
     const T u = src[k * stride];
     if (SCH == 0 && !RETRY && ck != nullptr) ck[k * N + c] = u;
     if (SCH == 2) Un[k] = T(0.5) * (un0[k * N] + (u + dt * acc[k]));
-    else Un[k] = u + dt * acc[k];
+    else Un[k] = fma(dt, acc[k], u);
   }
   if (SCH == 1) {
 #pragma unroll
@@ -510,8 +510,12 @@ __global__ void __launch_bounds__(32 * BY, (BY <= 8 ? 2 : 1)) step_tile_kernel(S
     // flux divergence of the cell, accumulated as each face flux becomes known (the lower z
     // face first; the flux registers die at once, which keeps the register count down)
     T acc[NV];
+    {
+      T Fg[NV];
 #pragma unroll
-    for (int k = 0; k < NV; k++) acc[Frame<2>::g(k)] = Fprev[k] * idz;
+      for (int k = 0; k < NV; k++) Fg[Frame<2>::g(k)] = Fprev[k];
+      v_mul(acc, Fg, idz);
+    }
     if (ty >= 1 && ty <= BY - 2) {  // x sweep, warp-uniform: one warp per row
       T wm[NV], w0[NV], wp[NV], lo[NV], hi[NV], hl[NV], F[NV];
       gather<T, 0, SY, SX>(pl, sy, sx - 1, wm);
@@ -527,8 +531,11 @@ __global__ void __launch_bounds__(32 * BY, (BY <= 8 ? 2 : 1)) step_tile_kernel(S
 #pragma unroll
       for (int k = 0; k < NV; k++) hl[k] = __shfl_up_sync(FULL, hi[k], 1);
       face_flux<SCH, RETRY>(hl, lo, fl(buf(z), sy, sx - 1) || fl(buf(z), sy, sx), F);  // lower x face
+      T Fu[NV];
 #pragma unroll
-      for (int k = 0; k < NV; k++) acc[k] += (F[k] - __shfl_down_sync(FULL, F[k], 1)) * idx;
+      for (int k = 0; k < NV; k++) Fu[k] = __shfl_down_sync(FULL, F[k], 1);
+      v_sub(F, F, Fu);
+      v_fma(acc, F, idx, acc);
     }
     const bool ycol = tx >= 1 && tx <= kTileX;
     T ylo[NV];
@@ -556,11 +563,13 @@ __global__ void __launch_bounds__(32 * BY, (BY <= 8 ? 2 : 1)) step_tile_kernel(S
 #pragma unroll
       for (int k = 0; k < NV; k++) hl[k] = sXh[(k * BY + ty - 1) * 32 + tx];
       face_flux<SCH, RETRY>(hl, ylo, fl(buf(z), sy - 1, sx) || fl(buf(z), sy, sx), Fy);
+      T Fg[NV];
 #pragma unroll
       for (int k = 0; k < NV; k++) {
         sXf[(k * BY + ty) * 32 + tx] = Fy[k];
-        acc[Frame<1>::g(k)] += Fy[k] * idy;
+        Fg[Frame<1>::g(k)] = Fy[k];
       }
+      v_fma(acc, Fg, idy, acc);
     }
     {  // z: reconstruct cell z+1, flux through the upper z face of cell z
       T lo[NV], hi[NV], F[NV];
@@ -571,18 +580,20 @@ __global__ void __launch_bounds__(32 * BY, (BY <= 8 ? 2 : 1)) step_tile_kernel(S
       }
       if (interior) {
       face_flux<SCH, RETRY>(hprev, lo, fl(buf(z), sy, sx) || fl(buf(z + 1), sy, sx), F);
+      T Fg[NV];
 #pragma unroll
       for (int k = 0; k < NV; k++) {
-        acc[Frame<2>::g(k)] -= F[k] * idz;
+        Fg[Frame<2>::g(k)] = F[k];
         hprev[k] = hi[k];
         Fprev[k] = F[k];
       }
+      v_fma(acc, Fg, -idz, acc);
       }
     }
     __syncthreads();
     if (interior) {
 #pragma unroll
-      for (int k = 0; k < NV; k++) acc[Frame<1>::g(k)] -= sXf[(k * BY + ty + 1) * 32 + tx] * idy;
+      for (int k = 0; k < NV; k++) acc[Frame<1>::g(k)] -= sXf[(k * BY + ty + 1) * 32 + tx] * idy;  // upper y face
     }
     if (valid) {
       const size_t c = ((size_t)z * ny + gy) * nx + gx;
@@ -727,8 +738,12 @@ __global__ void __launch_bounds__(32 * WARPS) step_strip2d_kernel(StepArgs<T> a)
         fetch(y + 2, Un2, f2);  // issued before the x sweep hides its latency
         // flux divergence of the cell, the lower y face first (Fprev dies at once)
         T acc[NV];
+        {
+          T Fg[NV];
 #pragma unroll
-        for (int k = 0; k < NV; k++) acc[Frame<1>::g(k)] = Fprev[k] * idy;
+          for (int k = 0; k < NV; k++) Fg[Frame<1>::g(k)] = Fprev[k];
+          v_mul(acc, Fg, idy);
+        }
         {
           // x sweep of row y: local x frame = natural order
           T w0[NV], wm[NV], wp[NV], lo[NV], hi[NV], hl[NV], F[NV];
@@ -755,7 +770,9 @@ __global__ void __launch_bounds__(32 * WARPS) step_strip2d_kernel(StepArgs<T> a)
           for (int k = 0; k < NV; k++) hl[k] = __shfl_up_sync(FULL, hi[k], 1);
           face_flux<SCH, RETRY>(hl, lo, fxlo, F);  // flux through the lower x face of this cell
 #pragma unroll
-          for (int k = 0; k < NV; k++) acc[k] += (F[k] - __shfl_down_sync(FULL, F[k], 1)) * idx;
+          for (int k = 0; k < NV; k++) hl[k] = __shfl_down_sync(FULL, F[k], 1);  // upper x face
+          v_sub(F, F, hl);
+          v_fma(acc, F, idx, acc);
         }
         {
           // y: reconstruct cell y+1, flux through y + 1/2
@@ -766,12 +783,14 @@ __global__ void __launch_bounds__(32 * WARPS) step_strip2d_kernel(StepArgs<T> a)
           recon_y(r0, r1, r2, lo, hi);
           if (RETRY) first_order_faces(f0, f1, f2, r1, lo, hi);
           face_flux<SCH, RETRY>(hprev, lo, f0 || f1, F);
+          T Fg[NV];
 #pragma unroll
           for (int k = 0; k < NV; k++) {
-            acc[Frame<1>::g(k)] -= F[k] * idy;
+            Fg[Frame<1>::g(k)] = F[k];
             hprev[k] = hi[k];
             Fprev[k] = F[k];
           }
+          v_fma(acc, Fg, -idy, acc);
         }
         if (upd)
           finish_cell<T, 2, SCH, RETRY, CTU>(a, Us + ((size_t)y * nx + gx), N, U0 + ((size_t)y * nx + gx), Ud, N,
