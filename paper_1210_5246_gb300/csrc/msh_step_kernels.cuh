@@ -278,12 +278,13 @@ __device__ __forceinline__ void gather(const T *__restrict__ pl, int sy, int sx,
 }
 
 // CTU: the corner-transport-upwind form (transverse terms in the face states, max-form CFL
-// speed).  Every thread's own cell is then staged too (the four cells diagonal to the
+// speed; 8-row tiles take one block per SM and the registers that allows, 16-row tiles keep
+// 16 warps per SM and spill some).  Every thread's own cell is then staged too (the four cells diagonal to the
 // tile's corners join the staged box), every thread but the four corner ones forms the
 // transverse terms of its cell plane by plane, and the sums each sweep needs, X_x = T_y +
 // T_z and X_y = T_x + T_z, wait in thread-private shared memory from the plane before.
 template <typename T, int NDIM, int BY, int SCH, bool RETRY, bool CTU = false>
-__global__ void __launch_bounds__(32 * BY, (BY <= 8 ? 2 : 1)) step_tile_kernel(StepArgs<T> a) {
+__global__ void __launch_bounds__(32 * BY, (BY <= 8 && !CTU ? 2 : 1)) step_tile_kernel(StepArgs<T> a) {
   static_assert(NDIM == 3, "the 2D step runs in step_strip2d_kernel");
   constexpr int SX = 34, SY = BY + 2, NQ = SY * SX;
   constexpr int PL = NV * NQ;  // one staged plane, all fields: [NV][SY][SX]
