@@ -308,7 +308,9 @@ __global__ void __launch_bounds__(32 * BY, (BY <= 8 && !CTU ? 2 : 1)) step_tile_
   T *const ck = (RETRY || SCH != 0) ? nullptr : tape_slot(a, step, (size_t)a.nx * a.ny * a.nz);
   // shared memory: three primitive planes (ring), RAW raw conserved planes filled by
   // cp.async one plane ahead, the y-sweep face states and fluxes, per staged cell the sign
-  // flips of reflect images (bits 0..9) and the fallback tag (bit 16)
+  // flips of reflect images (bits 0..9) and the fallback tag (bit 16), and per staged
+  // position of the tile its in-plane source offset (yy nx + xx, -1 where nothing is
+  // staged) and x/y reflect flips, which are the same for every plane of the tile
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T *sW = reinterpret_cast<T *>(smem_raw);
   T *sR = sW + 3 * PL;
@@ -317,6 +319,8 @@ __global__ void __launch_bounds__(32 * BY, (BY <= 8 && !CTU ? 2 : 1)) step_tile_
   T *sCx = sXf + NV * BY * 32;   // CTU: X_x of the thread's cell, [NV][BY * 32]
   T *sCy = sCx + (CTU ? NV * BY * 32 : 0);  // CTU: X_y, [NV][BY * 32]
   unsigned *sMeta = reinterpret_cast<unsigned *>(sCy + (CTU ? NV * BY * 32 : 0));  // [RAW][NQ]
+  int *sXY = reinterpret_cast<int *>(sMeta + RAW * NQ);                            // [NQ]
+  unsigned *sFxy = reinterpret_cast<unsigned *>(sXY + NQ);                         // [NQ]
   auto slot = [](int p) { return ((p % RAW) + RAW) % RAW; };
   const int tx = threadIdx.x, ty = threadIdx.y;
   const int tid = ty * 32 + tx;
@@ -342,7 +346,17 @@ __global__ void __launch_bounds__(32 * BY, (BY <= 8 && !CTU ? 2 : 1)) step_tile_
   };
 
   // Staged cells: the 34 x (BY+2) box (x0-2 .. x0+31, y0-2 .. y0+BY-1) without its corners
-  // (staged()).
+  // (staged()).  Their in-plane offsets and x/y flips are mapped once per tile, by the
+  // threads that stage them (i = tid + k * 32 BY, the stride of every stage and convert
+  // below), so no barrier is needed before their use.
+  for (int i = tid; i < NQ; i += 32 * BY) {
+    const int qy = i / SX, qx = i - qy * SX;
+    bool mx, my;
+    const int xx = map_index(x0 - 2 + qx, nx, a.bc[0], a.bc[1], mx);
+    const int yy = map_index(y0 - 2 + qy, ny, a.bc[2], a.bc[3], my);
+    sXY[i] = staged(qy, qx) ? yy * nx + xx : -1;
+    sFxy[i] = (mx ? flip_mask(0) : 0u) ^ (my ? flip_mask(1) : 0u);
+  }
   // A thread stages and later converts the same cells, so the copies it waits for are its
   // own and no barrier separates staging from conversion.
   auto stage = [&](int z) {
@@ -350,16 +364,15 @@ __global__ void __launch_bounds__(32 * BY, (BY <= 8 && !CTU ? 2 : 1)) step_tile_
     const int zz = map_index(z, nz, a.bc[4], a.bc[5], mz);
     T *dst = sR + slot(z) * PL;
     unsigned *meta = sMeta + slot(z) * NQ;
+    const size_t zoff = (size_t)zz * ny * nx;
+    const unsigned fz = mz ? flip_mask(2) : 0u;
     for (int i = tid; i < NQ; i += 32 * BY) {
-      const int qy = i / SX, qx = i - qy * SX;
-      if (!staged(qy, qx)) continue;
-      bool mx, my;
-      const int xx = map_index(x0 - 2 + qx, nx, a.bc[0], a.bc[1], mx);
-      const int yy = map_index(y0 - 2 + qy, ny, a.bc[2], a.bc[3], my);
-      const size_t c = ((size_t)zz * ny + yy) * nx + xx;
+      const int off = sXY[i];
+      if (off < 0) continue;
+      const size_t c = zoff + (size_t)off;
 #pragma unroll
       for (int k = 0; k < NV; k++) cp_async_elem(dst + k * NQ + i, Us + k * N + c);
-      unsigned m = (mx ? flip_mask(0) : 0u) ^ (my ? flip_mask(1) : 0u) ^ (mz ? flip_mask(2) : 0u);
+      unsigned m = sFxy[i] ^ fz;
       if (RETRY && tagged(a.flags[c], tag, a.level)) m |= 1u << 16;
       meta[i] = m;
     }
@@ -371,14 +384,14 @@ __global__ void __launch_bounds__(32 * BY, (BY <= 8 && !CTU ? 2 : 1)) step_tile_
     const int b = ((z % 3) + 3) % 3;
     T *dst = sW + b * PL;
     for (int i = tid; i < NQ; i += 32 * BY) {
-      const int qy = i / SX, qx = i - qy * SX;
-      if (!staged(qy, qx)) continue;
+      if (sXY[i] < 0) continue;
       const unsigned m = meta[i];
       T U[NV], W[NV];
 #pragma unroll
-      for (int k = 0; k < NV; k++) {
-        const T v = src[k * NQ + i];
-        U[k] = ((m >> k) & 1u) ? -v : v;
+      for (int k = 0; k < NV; k++) U[k] = src[k * NQ + i];
+      if (m & 0x3ffu) {  // a reflect image (never inside a periodic or outflow grid)
+#pragma unroll
+        for (int k = 0; k < NV; k++) U[k] = ((m >> k) & 1u) ? -U[k] : U[k];
       }
       cons_to_prim(U, W);
 #pragma unroll
@@ -825,13 +838,14 @@ inline int fallback_blocks() {
 
 // 3D: 3 + RAW staged planes (three primitive, RAW raw) of NV x (rows+2) x 34, the y-sweep
 // face states and fluxes (2 x NV x rows x 32), with CTU the per-thread X_x and X_y
-// (2 x NV x rows x 32), and RAW planes of per-cell flags.
+// (2 x NV x rows x 32), RAW planes of per-cell flags and the tile's in-plane offsets and
+// flips (2 x (rows+2) x 34 words).
 template <typename T> size_t step_smem(int ndim, int rows, bool ctu) {
   if (ndim < 3) return 0;
   const size_t nq = (size_t)(rows + 2) * 34;
   const size_t raw = ctu ? 2 : rows == 16 ? kRawPlanes<T, 16> : rows == 8 ? kRawPlanes<T, 8> : kRawPlanes<T, 4>;
   const size_t per_thread = ctu ? 4 : 2;
-  return sizeof(T) * ((3 + raw) * NV * nq + per_thread * NV * rows * 32) + raw * nq * sizeof(unsigned);
+  return sizeof(T) * ((3 + raw) * NV * nq + per_thread * NV * rows * 32) + (raw + 2) * nq * sizeof(unsigned);
 }
 
 template <typename T> int step_blocks(int ndim, int rows, int nx, int ny, int nz, int zchunk) {

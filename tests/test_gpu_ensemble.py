@@ -26,10 +26,12 @@ def _pinned(torch, shape, dtype):
     return t.numpy()
 
 
-def _alone(msh, p, W, prec, kind, nsteps, scheme=None):
+def _alone(msh, p, W, prec, kind, nsteps, scheme=None, ctu=False):
     g = msh.Grid.from_problem(p, prec)
     if scheme is not None:
         g.set_scheme(scheme)
+    if ctu:
+        g.set_ctu(True)
     if kind == msh.CONSERVED:
         g.set_state(W, msh.PRIMITIVE)
         U = g.get_state()
@@ -37,6 +39,8 @@ def _alone(msh, p, W, prec, kind, nsteps, scheme=None):
         g = msh.Grid.from_problem(p, prec)
         if scheme is not None:
             g.set_scheme(scheme)
+        if ctu:
+            g.set_ctu(True)
         g.set_state(U, msh.CONSERVED)
     else:
         g.set_state(W, msh.PRIMITIVE)
@@ -145,3 +149,22 @@ def test_arguments(env):
     with pytest.raises(ValueError):
         g.run_ensemble([W], [])
     g.close()
+
+
+@pytest.mark.parametrize("prec_name", ["FP64", "FP32"])
+def test_ctu_equals_states_run_alone(env, prec_name):
+    """The corner-transport-upwind step in an ensemble: each state's start re-plans with the
+    max-form CFL rule; every result equals the state run alone, bit for bit."""
+    msh, inputs, torch = env
+    prec = getattr(msh, prec_name)
+    dtype = np.float32 if prec == msh.FP32 else np.float64
+    ps = _states(inputs, 20, 5)
+    g = msh.Grid.from_problem(ps[0], prec)
+    g.set_ctu(True)
+    ins = [np.ascontiguousarray(p.W.astype(dtype)) for p in ps]
+    outs = [np.empty_like(w) for w in ins]
+    st = g.run_ensemble(ins, outs, kind=msh.PRIMITIVE, nsteps=4)
+    g.close()
+    assert list(st) == [0] * len(ps)
+    for p, w, o in zip(ps, ins, outs):
+        np.testing.assert_array_equal(o, _alone(msh, p, w, prec, msh.PRIMITIVE, 4, ctu=True))

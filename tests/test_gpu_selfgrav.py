@@ -29,7 +29,8 @@ def _periodic_field(shape, seed, sigma2=0.3):
     return W
 
 
-def _compare(msh, oracle, n, W, steps, G, precision=None, scheme=0, phi_ext=None, cfl=0.4, profiled=False):
+def _compare(msh, oracle, n, W, steps, G, precision=None, scheme=0, phi_ext=None, cfl=0.4, profiled=False,
+             ctu=False):
     from oracle import selfgrav
     precision = msh.FP64 if precision is None else precision
     nd = len(n)
@@ -38,6 +39,8 @@ def _compare(msh, oracle, n, W, steps, G, precision=None, scheme=0, phi_ext=None
     g = msh.Grid(n, lo, hi, bc, cfl, precision)
     if scheme:
         g.set_scheme(scheme)
+    if ctu:
+        g.set_ctu(True)
     if phi_ext is not None:
         g.set_potential(phi_ext)
     g.set_self_gravity(G)
@@ -48,7 +51,7 @@ def _compare(msh, oracle, n, W, steps, G, precision=None, scheme=0, phi_ext=None
     assert ns == steps
     U, Wout = g.get_state().astype(np.float64), g.get_state(msh.PRIMITIVE).astype(np.float64)
     g.close()
-    og = oracle.Grid(n, lo, hi, bc, cfl, scheme=scheme)
+    og = oracle.Grid(n, lo, hi, bc, cfl, scheme=scheme, ctu=ctu)
     Uo, _ = selfgrav.run(og, oracle.prim_to_cons(Wg.astype(np.float64)), steps, G, phi_ext=phi_ext)
     return U, Wout, Uo, oracle.cons_to_prim(Uo)
 
@@ -157,3 +160,12 @@ def test_errors(env):
     g.set_self_gravity(0.0)
     g.adjoint_run(U0, [1e-3], U0, K=1)  # allowed again without self-gravity
     g.close()
+
+
+@pytest.mark.parametrize("shape,n,steps", [((1, 24, 40), (40, 24), 10), ((12, 10, 16), (16, 10, 12), 6)])
+def test_ctu_matches_oracle(env, oracle, shape, n, steps):
+    """Self-gravity with the corner-transport-upwind step (max-form CFL, CFL 0.7)."""
+    msh, _ = env
+    W = _periodic_field(shape, len(n) + 7)
+    U, _, Uo, _ = _compare(msh, oracle, n, W, steps, G=2.0, cfl=0.7, ctu=True)
+    assert_fp64(U, Uo, what=f"self-gravity ctu {n}")
