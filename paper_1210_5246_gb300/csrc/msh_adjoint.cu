@@ -634,6 +634,7 @@ done:
 
 extern "C" msh_status msh_adjoint_run(msh_grid *g, const void *U0, int64_t nsteps, const double *dt_sched, int32_t K,
                                       const void *dL_dUN, void *dL_dU0, int32_t where, int32_t kind) {
+  msh::NvtxRange nvtx_range("msh_adjoint_run");
   clear_error();
   if (!g || !U0 || !dL_dUN || !dL_dU0) return afail(MSH_E_INVALID_ARG, "null argument");
   if (nsteps < 0 || (nsteps > 0 && !dt_sched)) return afail(MSH_E_INVALID_ARG, "bad nsteps or dt schedule");
@@ -653,6 +654,7 @@ extern "C" msh_status msh_adjoint_run(msh_grid *g, const void *U0, int64_t nstep
 }
 
 extern "C" msh_status msh_adjoint_tape(msh_grid *g, const void *dL_dUN, void *dL_dU0, int32_t where, int32_t kind) {
+  msh::NvtxRange nvtx_range("msh_adjoint_tape");
   clear_error();
   if (!g || !dL_dUN || !dL_dU0) return afail(MSH_E_INVALID_ARG, "null argument");
   if (where != MSH_HOST && where != MSH_DEVICE) return afail(MSH_E_INVALID_ARG, "bad where");

@@ -446,6 +446,7 @@ msh_status msh_batch_reset(msh_batch *b) {
 }
 
 msh_status msh_batch_run(msh_batch *b, int32_t threads, int64_t max_steps) {
+  msh::NvtxRange nvtx_range("msh_batch_run");
   clear_error();
   if (!b) return bfail(MSH_E_INVALID_ARG, "null batch");
   if (threads != 0 && threads != 128 && threads != 256 && threads != 512)
@@ -507,6 +508,7 @@ msh_status msh_batch_run(msh_batch *b, int32_t threads, int64_t max_steps) {
 }
 
 msh_status msh_batch_run_per_tube(msh_batch *b, const int32_t *tubes, int32_t count, int64_t max_steps) {
+  msh::NvtxRange nvtx_range("msh_batch_run_per_tube");
   clear_error();
   if (!b) return bfail(MSH_E_INVALID_ARG, "null batch");
   if (tubes && count < 0) return bfail(MSH_E_INVALID_ARG, "bad count");

@@ -445,6 +445,7 @@ msh_status msh_destroy(msh_grid *g) {
 }
 
 msh_status msh_set_state(msh_grid *g, const void *U, int32_t where, int32_t kind) {
+  msh::NvtxRange nvtx_range("msh_set_state");
   begin();
   if (!g || !U) return fail(MSH_E_INVALID_ARG, "null argument");
   if (where != MSH_HOST && where != MSH_DEVICE) return fail(MSH_E_INVALID_ARG, "bad where");
@@ -480,6 +481,7 @@ msh_status msh_set_state(msh_grid *g, const void *U, int32_t where, int32_t kind
 }
 
 msh_status msh_get_state(msh_grid *g, void *U, int32_t where, int32_t kind) {
+  msh::NvtxRange nvtx_range("msh_get_state");
   begin();
   if (!g || !U) return fail(MSH_E_INVALID_ARG, "null argument");
   if (where != MSH_HOST && where != MSH_DEVICE) return fail(MSH_E_INVALID_ARG, "bad where");
@@ -503,6 +505,7 @@ msh_status msh_get_state(msh_grid *g, void *U, int32_t where, int32_t kind) {
 
 msh_status msh_run_ensemble(msh_grid *g, int64_t count, const void *const *in, void *const *out, int32_t kind,
                             int64_t nsteps, int32_t *status) {
+  msh::NvtxRange nvtx_range("msh_run_ensemble");
   begin();
   if (!g || (count > 0 && (!in || !out))) return fail(MSH_E_INVALID_ARG, "null argument");
   if (count < 0 || nsteps < 1) return fail(MSH_E_INVALID_ARG, "count must be >= 0 and nsteps >= 1");
@@ -727,6 +730,7 @@ msh_status msh_set_cell_width(msh_grid *g, const double dx[3]) {
 }
 
 msh_status msh_step(msh_grid *g, double dt_max, double *dt_taken) {
+  msh::NvtxRange nvtx_range("msh_step");
   begin();
   if (!g) return fail(MSH_E_INVALID_ARG, "null grid");
   if (!g->has_state) return fail(MSH_E_STATE, "msh_step before msh_set_state");
@@ -748,6 +752,7 @@ msh_status msh_step(msh_grid *g, double dt_max, double *dt_taken) {
 }
 
 msh_status msh_run(msh_grid *g, double t_end, int64_t max_steps, int64_t *steps, double *t_out) {
+  msh::NvtxRange nvtx_range("msh_run");
   begin();
   if (!g) return fail(MSH_E_INVALID_ARG, "null grid");
   if (!g->has_state) return fail(MSH_E_STATE, "msh_run before msh_set_state");
@@ -951,6 +956,7 @@ msh_status msh_reduce_layers(msh_grid *g, int64_t start, int64_t count, double t
 }
 
 msh_status msh_step_dt(msh_grid *g, double dt, int32_t *tagged_cells) {
+  msh::NvtxRange nvtx_range("msh_step_dt");
   begin();
   if (!g) return fail(MSH_E_INVALID_ARG, "null grid");
   if (!g->has_state) return fail(MSH_E_STATE, "msh_step_dt before msh_set_state");
@@ -1013,6 +1019,7 @@ msh_status msh_get_tiling(msh_grid *g, int32_t *rows, int32_t *zchunk) {
 // Time each tile shape on copies of the current state (the state, time and step
 // counter are restored afterwards) and keep the fastest.
 msh_status msh_autotune(msh_grid *g, int32_t *rows_out, int32_t *zchunk_out) {
+  msh::NvtxRange nvtx_range("msh_autotune");
   begin();
   if (!g) return fail(MSH_E_INVALID_ARG, "null grid");
   if (!g->has_state) return fail(MSH_E_STATE, "msh_autotune before msh_set_state");

@@ -5,9 +5,20 @@
 
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/msh.h"
 
 namespace msh {
+
+// NVTX range over a call of the ABI (visible in nsys / ncu timelines; a no-op without a
+// tool attached).
+struct NvtxRange {
+  explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange &) = delete;
+  NvtxRange &operator=(const NvtxRange &) = delete;
+};
 
 // A-posteriori fallback passes per step (see the step kernels).
 constexpr int kFallbackPasses = 4;
