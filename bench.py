@@ -475,7 +475,21 @@ def run_suite(args):
         p = inputs.sod(args.n or 256)
         r = grid_rate(p, msh.FP64, 1 << 20, p.t_end)
         orc, cores, _ = _oracle_rate(p, steps=r["steps"])
-        emit({"workload": f"sod {p.n[0]} cells FP64 to t=0.2", "gpu_fp64": r, "oracle": orc, "oracle_cores": cores})
+        # the same problem as one tube of the batched kernel: every step in one persistent
+        # launch (the grid path pays six launches per step, which a 256-cell step cannot hide)
+        WL, WR = p.W[:, 0, 0, 0], p.W[:, 0, 0, -1]
+        b = msh.Batch([p.n[0]], WL[None, :], WR[None, :], p.t_end, p.cfl, msh.FP64, stream=stream.cuda_stream)
+        b.run()
+        b.reset()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        b.run()
+        torch.cuda.synchronize()
+        el = time.perf_counter() - t0
+        steps_b, _, cu = b.info()
+        b.close()
+        emit({"workload": f"sod {p.n[0]} cells FP64 to t=0.2", "gpu_fp64": r, "oracle": orc, "oracle_cores": cores,
+              "gpu_fp64_one_tube_batch": {"value": cu / el, "steps": int(steps_b[0]), "ms_total": el * 1e3}})
     # 2D blast 1024^2, 200 steps
     if only in (None, "blast"):
         p = inputs.blast(n=args.n or 1024)
