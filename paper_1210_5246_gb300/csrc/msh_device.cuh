@@ -47,8 +47,8 @@ template <typename T> __device__ __forceinline__ T sqrt_ratio(T p, T r) { return
 template <> __device__ __forceinline__ float sqrt_ratio<float>(float p, float r) { return p * rsqrtf(p * r); }
 
 // ------------------------------------------------------- paired FP32 arithmetic
-// Componentwise operations on 10-vectors, d_k = a_k s + c_k (v_fma), d_k = a_k s (v_mul) and
-// d_k = a_k - b_k (v_sub).  In FP32 components (k, k+1) go through the packed f32x2 instructions of sm_100
+// Componentwise operations on 10-vectors, d_k = a_k s + c_k (v_fma), d_k = a_k s (v_mul),
+// d_k = a_k + b_k (v_add) and d_k = a_k - b_k (v_sub).  In FP32 components (k, k+1) go through the packed f32x2 instructions of sm_100
 // (__ffma2_rn, __fadd2_rn: two single-precision operations per issued instruction, each
 // rounded as its scalar form); FP64 stays scalar.
 template <typename T>
@@ -75,6 +75,19 @@ template <> __device__ __forceinline__ void v_mul<float>(float (&d)[NV], const f
 #pragma unroll
   for (int k = 0; k < NV; k += 2) {
     const float2 r = __fmul2_rn(make_float2(a[k], a[k + 1]), ss);
+    d[k] = r.x;
+    d[k + 1] = r.y;
+  }
+}
+template <typename T> __device__ __forceinline__ void v_add(T (&d)[NV], const T (&a)[NV], const T (&b)[NV]) {
+#pragma unroll
+  for (int k = 0; k < NV; k++) d[k] = a[k] + b[k];
+}
+template <>
+__device__ __forceinline__ void v_add<float>(float (&d)[NV], const float (&a)[NV], const float (&b)[NV]) {
+#pragma unroll
+  for (int k = 0; k < NV; k += 2) {
+    const float2 r = __fadd2_rn(make_float2(a[k], a[k + 1]), make_float2(b[k], b[k + 1]));
     d[k] = r.x;
     d[k + 1] = r.y;
   }
@@ -471,12 +484,12 @@ __device__ __forceinline__ void hll(const T (&wl)[NV], const T (&wr)[NV], T (&F)
 template <typename T>
 __device__ __forceinline__ void kt_reconstruct(const T (&wm)[NV], const T (&w0)[NV], const T (&wp)[NV],
                                                T (&lo)[NV], T (&hi)[NV]) {
-#pragma unroll
-  for (int k = 0; k < NV; k++) {
-    const T s2 = mc_limit2(w0[k] - wm[k], wp[k] - w0[k]);
-    hi[k] = w0[k] + T(0.25) * s2;
-    lo[k] = w0[k] - T(0.25) * s2;
-  }
+  T dl[NV], dr[NV], s2[NV];
+  v_sub(dl, w0, wm);
+  v_sub(dr, wp, w0);
+  mc_limit2_v(dl, dr, s2);
+  v_fma(hi, s2, T(0.25), w0);
+  v_fma(lo, s2, T(-0.25), w0);
   face_state_check(w0, lo, hi);
 }
 
@@ -491,8 +504,11 @@ __device__ __forceinline__ void kt_flux(const T (&wl)[NV], const T (&wr)[NV], T 
   const T al = fabs(wl[1]) + T(1.7320508075688772) * sqrt_ratio(wl[4], wl[0]);
   const T ar = fabs(wr[1]) + T(1.7320508075688772) * sqrt_ratio(wr[4], wr[0]);
   const T h = T(0.5) * fmax(al, ar);
-#pragma unroll
-  for (int k = 0; k < NV; k++) F[k] = T(0.5) * (Fr[k] + Fl[k]) - h * (Ur[k] - Ul[k]);
+  T dU[NV], Fs[NV];
+  v_sub(dU, Ur, Ul);
+  v_add(Fs, Fl, Fr);
+  v_mul(Fs, Fs, T(0.5));
+  v_fma(F, dU, -h, Fs);
 }
 
 // ------------------------------------------------------------ Roe-type flux
@@ -542,8 +558,10 @@ __device__ __forceinline__ void roe_flux(const T (&wl)[NV], const T (&wr)[NV], T
   T Ul[NV], Fl[NV], Ur[NV], Fr[NV];
   phys(wl, Ul, Fl);
   phys(wr, Ur, Fr);
-#pragma unroll
-  for (int k = 0; k < NV; k++) F[k] = T(0.5) * (Fl[k] + Fr[k]) - T(0.5) * dU[k];
+  T Fs[NV];
+  v_add(Fs, Fl, Fr);
+  v_sub(Fs, Fs, dU);
+  v_mul(F, Fs, T(0.5));
 }
 
 // ------------------------------------------------------------------- HLLC
@@ -612,8 +630,10 @@ __device__ __forceinline__ void hllc_flux(const T (&wl)[NV], const T (&wr)[NV], 
   phys(wk, Uk, Fk);
   pi_terms(wk[1], wk[2], wk[3], wk[4], wk[5], wk[6], Pk);
   pi_terms(us[0], us[1], us[2], ps[0], ps[1], ps[2], Ps);
-#pragma unroll
-  for (int k = 0; k < NV; k++) F[k] = a * Uk[k] + (b * Pk[k] + c * Ps[k]);
+  T t[NV];
+  v_mul(t, Ps, c);
+  v_fma(t, Pk, b, t);
+  v_fma(F, Uk, a, t);
 }
 
 // Scheme of a step kernel: 0 the characteristic MUSCL-Hancock step with HLL (Sec. 3.3);
