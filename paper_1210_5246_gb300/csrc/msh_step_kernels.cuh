@@ -309,8 +309,7 @@ __global__ void __launch_bounds__(32 * BY, (BY <= 8 && !CTU ? 2 : 1)) step_tile_
   // shared memory: three primitive planes (ring), RAW raw conserved planes filled by
   // cp.async one plane ahead, the y-sweep face states and fluxes, per staged cell the sign
   // flips of reflect images (bits 0..9) and the fallback tag (bit 16), and per staged
-  // position of the tile its in-plane source offset (yy nx + xx, -1 where nothing is
-  // staged) and x/y reflect flips, which are the same for every plane of the tile
+  // position of the tile its x/y reflect flips, which are the same for every plane
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T *sW = reinterpret_cast<T *>(smem_raw);
   T *sR = sW + 3 * PL;
@@ -319,8 +318,7 @@ __global__ void __launch_bounds__(32 * BY, (BY <= 8 && !CTU ? 2 : 1)) step_tile_
   T *sCx = sXf + NV * BY * 32;   // CTU: X_x of the thread's cell, [NV][BY * 32]
   T *sCy = sCx + (CTU ? NV * BY * 32 : 0);  // CTU: X_y, [NV][BY * 32]
   unsigned *sMeta = reinterpret_cast<unsigned *>(sCy + (CTU ? NV * BY * 32 : 0));  // [RAW][NQ]
-  int *sXY = reinterpret_cast<int *>(sMeta + RAW * NQ);                            // [NQ]
-  unsigned *sFxy = reinterpret_cast<unsigned *>(sXY + NQ);                         // [NQ]
+  unsigned *sFxy = sMeta + RAW * NQ;  // [NQ]
   auto slot = [](int p) { return ((p % RAW) + RAW) % RAW; };
   const int tx = threadIdx.x, ty = threadIdx.y;
   const int tid = ty * 32 + tx;
@@ -346,16 +344,24 @@ __global__ void __launch_bounds__(32 * BY, (BY <= 8 && !CTU ? 2 : 1)) step_tile_
   };
 
   // Staged cells: the 34 x (BY+2) box (x0-2 .. x0+31, y0-2 .. y0+BY-1) without its corners
-  // (staged()).  Their in-plane offsets and x/y flips are mapped once per tile, by the
-  // threads that stage them (i = tid + k * 32 BY, the stride of every stage and convert
-  // below), so no barrier is needed before their use.
-  for (int i = tid; i < NQ; i += 32 * BY) {
-    const int qy = i / SX, qx = i - qy * SX;
-    bool mx, my;
-    const int xx = map_index(x0 - 2 + qx, nx, a.bc[0], a.bc[1], mx);
-    const int yy = map_index(y0 - 2 + qy, ny, a.bc[2], a.bc[3], my);
-    sXY[i] = staged(qy, qx) ? yy * nx + xx : -1;
-    sFxy[i] = (mx ? flip_mask(0) : 0u) ^ (my ? flip_mask(1) : 0u);
+  // (staged()).  A thread stages positions i = tid and tid + 32 BY (two cover the box);
+  // their in-plane source offsets (yy nx + xx; -1 where nothing is staged) stay in its
+  // registers and their x/y flips in shared memory, mapped once per tile by the thread that
+  // uses them (no barrier needed).
+  static_assert(NQ <= 2 * 32 * BY, "two staged positions per thread");
+  int soff[2];
+#pragma unroll
+  for (int j = 0; j < 2; j++) {
+    const int i = tid + j * 32 * BY;
+    soff[j] = -1;
+    if (i < NQ) {
+      const int qy = i / SX, qx = i - qy * SX;
+      bool mx, my;
+      const int xx = map_index(x0 - 2 + qx, nx, a.bc[0], a.bc[1], mx);
+      const int yy = map_index(y0 - 2 + qy, ny, a.bc[2], a.bc[3], my);
+      if (staged(qy, qx)) soff[j] = yy * nx + xx;
+      sFxy[i] = (mx ? flip_mask(0) : 0u) ^ (my ? flip_mask(1) : 0u);
+    }
   }
   // A thread stages and later converts the same cells, so the copies it waits for are its
   // own and no barrier separates staging from conversion.
@@ -366,10 +372,11 @@ __global__ void __launch_bounds__(32 * BY, (BY <= 8 && !CTU ? 2 : 1)) step_tile_
     unsigned *meta = sMeta + slot(z) * NQ;
     const size_t zoff = (size_t)zz * ny * nx;
     const unsigned fz = mz ? flip_mask(2) : 0u;
-    for (int i = tid; i < NQ; i += 32 * BY) {
-      const int off = sXY[i];
-      if (off < 0) continue;
-      const size_t c = zoff + (size_t)off;
+#pragma unroll
+    for (int j = 0; j < 2; j++) {
+      if (soff[j] < 0) continue;
+      const int i = tid + j * 32 * BY;
+      const size_t c = zoff + (size_t)soff[j];
 #pragma unroll
       for (int k = 0; k < NV; k++) cp_async_elem(dst + k * NQ + i, Us + k * N + c);
       unsigned m = sFxy[i] ^ fz;
@@ -383,8 +390,10 @@ __global__ void __launch_bounds__(32 * BY, (BY <= 8 && !CTU ? 2 : 1)) step_tile_
     const unsigned *meta = sMeta + slot(z) * NQ;
     const int b = ((z % 3) + 3) % 3;
     T *dst = sW + b * PL;
-    for (int i = tid; i < NQ; i += 32 * BY) {
-      if (sXY[i] < 0) continue;
+#pragma unroll
+    for (int j = 0; j < 2; j++) {
+      if (soff[j] < 0) continue;
+      const int i = tid + j * 32 * BY;
       const unsigned m = meta[i];
       T U[NV], W[NV];
 #pragma unroll
@@ -838,14 +847,14 @@ inline int fallback_blocks() {
 
 // 3D: 3 + RAW staged planes (three primitive, RAW raw) of NV x (rows+2) x 34, the y-sweep
 // face states and fluxes (2 x NV x rows x 32), with CTU the per-thread X_x and X_y
-// (2 x NV x rows x 32), RAW planes of per-cell flags and the tile's in-plane offsets and
-// flips (2 x (rows+2) x 34 words).
+// (2 x NV x rows x 32), RAW planes of per-cell flags and the tile's x/y flips ((rows+2) x
+// 34 words).
 template <typename T> size_t step_smem(int ndim, int rows, bool ctu) {
   if (ndim < 3) return 0;
   const size_t nq = (size_t)(rows + 2) * 34;
   const size_t raw = ctu ? 2 : rows == 16 ? kRawPlanes<T, 16> : rows == 8 ? kRawPlanes<T, 8> : kRawPlanes<T, 4>;
   const size_t per_thread = ctu ? 4 : 2;
-  return sizeof(T) * ((3 + raw) * NV * nq + per_thread * NV * rows * 32) + (raw + 2) * nq * sizeof(unsigned);
+  return sizeof(T) * ((3 + raw) * NV * nq + per_thread * NV * rows * 32) + (raw + 1) * nq * sizeof(unsigned);
 }
 
 template <typename T> int step_blocks(int ndim, int rows, int nx, int ny, int nz, int zchunk) {
