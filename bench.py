@@ -62,6 +62,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--fp32-only", action="store_true", help="skip the FP64 measurement")
     ap.add_argument("--tiling", default=None, help="rows,zchunk instead of autotuning (e.g. 8,32)")
+    ap.add_argument("--persistent-only", action="store_true",
+                    help="with --suite --only tubes: skip the one-launch-per-step-per-tube baseline")
     ap.add_argument("--ctu", action="store_true",
                     help="the corner-transport-upwind form of the step (a profiling case, not the benchmark)")
     ap.add_argument("--suite", action="store_true", help="one JSON line per workload instead of the bench line")
@@ -574,13 +576,13 @@ def run_suite(args):
               "self_gravity_ms_per_step": ms - base["ms_per_step"],
               "cell_updates_per_s": int(np.prod(p.n)) * ns / (ms * ns * 1e-3)})
     if only in (None, "tubes"):
-        run_suite_tubes(msh, inputs, stream, emit)
+        run_suite_tubes(msh, inputs, stream, emit, per_tube=not args.persistent_only)
     if only in (None, "disc"):
         n = args.n or 512
         run_suite_disc(msh, disc, stream, emit, n, 2000 if only is None else args.steps)
 
 
-def run_suite_tubes(msh, inputs, stream, emit):
+def run_suite_tubes(msh, inputs, stream, emit, per_tube=True):
     """Batched tubes: one persistent launch vs one launch per step per tube."""
     import torch
     tb = inputs.tubes()
@@ -593,6 +595,11 @@ def run_suite_tubes(msh, inputs, stream, emit):
     torch.cuda.synchronize()
     el = time.perf_counter() - t0
     _, _, cu = b.info()
+    if not per_tube:
+        b.close()
+        emit({"workload": "4096 tubes 128..2048 cells FP32 to t=0.1", "persistent": cu / el,
+              "cell_updates": cu, "seconds": el})
+        return
     sample = np.argsort(tb.length)[:: len(tb.length) // 32][:32]
     b.reset()
     b.run_per_tube(sample)  # builds the per-tube grids
