@@ -6,8 +6,9 @@
 // into shared memory and advances it to its own t_end with a block-local CFL reduction;
 // the tube never leaves shared memory until it is finished.  Per step the block sweeps the
 // tube in chunks of NT cells: reconstruction of the chunk's cells, HLL fluxes through their
-// lower faces, and an in-place conservative update that trails the chunk front by one
-// cell (a cell is updated once both of its faces are known, and no later chunk reads it).
+// lower faces, and the conservative update into the second tube buffer, trailing the chunk
+// front by one cell (a cell is updated once both of its faces are known); the buffers swap
+// roles after each step, so U^n stays intact for the fallback passes without a copy.
 // The step is the same as the grid kernels': MUSCL-Hancock on the characteristic
 // variables (Sec. 3.3), HLL flux, outflow boundaries by index clamping, CFL time step
 // dt = C dx / max(|u| + sqrt(3 P_xx/rho)) with the last step clipped to t_end.
@@ -66,8 +67,8 @@ template <typename T, int NT> __device__ __forceinline__ T block_max(T v, T *red
 }
 
 // One sweep of a tube over all its faces: reconstruction, HLL fluxes and the conservative
-// update, chunk by chunk.  src holds U^n; dst receives U^{n+1} (dst may equal src: each
-// cell is updated after the last chunk that reads it).  With FALLBACK, every face that
+// update, chunk by chunk.  src holds U^n; dst receives U^{n+1} (dst may also equal src:
+// each cell is updated after the last chunk that reads it).  With FALLBACK, every face that
 // touches a cell tagged by an earlier pass (sFl == 2) takes first-order states.  Cells whose
 // update is not realizable and that carry no active tag are tagged (sFl = 1) and *s_nbad
 // is set.  Returns the thread's maximum signal-speed sum of the new state.
@@ -139,8 +140,10 @@ template <typename T, int NT>
 __global__ void __launch_bounds__(NT) tubes_kernel(TubeArgs<T> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int cap = a.cap;
-  T *sU = reinterpret_cast<T *>(smem_raw);  // [NV][cap] the tube
-  T *sUo = sU + (size_t)NV * cap;           // [NV][cap] U^n kept for the fallback pass
+  // two tube buffers: a step reads U^n from one and writes U^{n+1} to the other (the
+  // fallback passes re-read the untouched U^n), then the two swap roles
+  T *sU = reinterpret_cast<T *>(smem_raw);  // [NV][cap]
+  T *sUo = sU + (size_t)NV * cap;           // [NV][cap]
   T *sF = sUo + (size_t)NV * cap;           // [NV][NT+1]: sF[0] = carried face, sF[t+1] = lower face of cell b+t
   T *sH = sF + NV * (NT + 1);               // [NV][NT]: hi face states of the chunk
   T *sHc = sH + NV * NT;                    // [NV]: hi face state of the cell before the chunk
@@ -158,9 +161,10 @@ __global__ void __launch_bounds__(NT) tubes_kernel(TubeArgs<T> a) {
     const int k = a.order[q];
     const int n = a.len[k];
     const int64_t off = a.off[k];
+    T *cur = sU, *nxt = sUo;  // U^n and U^{n+1} of the current step
     for (int c = t; c < n; c += NT) {
 #pragma unroll
-      for (int v = 0; v < NV; v++) sU[v * cap + c] = a.U[v * a.total + off + c];
+      for (int v = 0; v < NV; v++) cur[v * cap + c] = a.U[v * a.total + off + c];
       sFl[c] = 0;
     }
     __syncthreads();
@@ -169,7 +173,7 @@ __global__ void __launch_bounds__(NT) tubes_kernel(TubeArgs<T> a) {
     T sm = T(0);
     for (int c = t; c < n; c += NT) {
       T W[NV];
-      load_w(sU, cap, c, n, W);
+      load_w(cur, cap, c, n, W);
       sm = fmax(sm, (fabs(W[1]) + T(1.7320508075688772) * sqrt_ratio(W[4], W[0])) * idx);
     }
     sm = block_max<T, NT>(sm, red);
@@ -183,12 +187,9 @@ __global__ void __launch_bounds__(NT) tubes_kernel(TubeArgs<T> a) {
       double tn = tt + dt;
       if (tn >= te) { dt = te - tt; tn = te; }
       const T nu = (T)dt * half_idx, dtdx = (T)dt * idx;
-      for (int c = t; c < n; c += NT)
-#pragma unroll
-        for (int v = 0; v < NV; v++) sUo[v * cap + c] = sU[v * cap + c];
       if (t == 0) { s_nbad = 0; s_any = 0; }
       __syncthreads();
-      T smax = tube_pass<T, NT, false>(sU, sU, sFl, n, cap, nu, dtdx, idx, sF, sH, sHc, &s_nbad, &s_any);
+      T smax = tube_pass<T, NT, false>(cur, nxt, sFl, n, cap, nu, dtdx, idx, sF, sH, sHc, &s_nbad, &s_any);
       sm = block_max<T, NT>(smax, red);  // its barriers also order the carries and s_nbad
       // a-posteriori fallback: redo the step from U^n with first-order faces at every tagged
       // cell; cells still failing are tagged too (at most kFallbackPasses passes)
@@ -199,12 +200,15 @@ __global__ void __launch_bounds__(NT) tubes_kernel(TubeArgs<T> a) {
         for (int c = t; c < n; c += NT)
           if (sFl[c] == 1) sFl[c] = 2;  // tags of earlier passes become active
         __syncthreads();
-        smax = tube_pass<T, NT, true>(sUo, sU, sFl, n, cap, nu, dtdx, idx, sF, sH, sHc, &s_nbad, &s_any);
+        smax = tube_pass<T, NT, true>(cur, nxt, sFl, n, cap, nu, dtdx, idx, sF, sH, sHc, &s_nbad, &s_any);
         sm = block_max<T, NT>(smax, red);
       }
       const bool still_bad = s_any != 0;  // some cell of the last pass is not realizable
       for (int c = t; c < n; c += NT) sFl[c] = 0;
       __syncthreads();
+      T *sw = cur;  // U^{n+1} becomes the next step's U^n
+      cur = nxt;
+      nxt = sw;
       if (still_bad) { status = 4; tt = tn; steps++; break; }
       tt = tn;
       steps++;
@@ -212,7 +216,7 @@ __global__ void __launch_bounds__(NT) tubes_kernel(TubeArgs<T> a) {
     __syncthreads();
     for (int c = t; c < n; c += NT)
 #pragma unroll
-      for (int v = 0; v < NV; v++) a.U[v * a.total + off + c] = sU[v * cap + c];
+      for (int v = 0; v < NV; v++) a.U[v * a.total + off + c] = cur[v * cap + c];
     if (t == 0) {
       a.steps[k] = steps;
       a.t_out[k] = tt;
