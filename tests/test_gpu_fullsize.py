@@ -10,6 +10,8 @@
   FP32 against FP64 after 50 steps.
 * Disc, 512^2 outflow with gravity, FP32, all 2000 steps against the oracle; FP64 for
   the first 200 steps.
+* Corner transport upwind: the blast's first 50 steps at CFL 0.8 (FP64 and FP32) and the
+  box's first 2 steps at CFL 0.6 (FP32) against the oracle's CTU step.
 """
 import numpy as np
 import pytest
@@ -142,3 +144,53 @@ def test_disc_512_fp64_first_200_steps(env, oracle):
     G = _gpu_run(msh, p, msh.FP64, s, 200)
     Uo, _, _ = _oracle_run(oracle, p, p.W, 200)
     assert_fp64(G["U"], Uo, what="disc 512^2 fp64, 200 steps")
+
+
+# ------------------------------------------------- corner transport upwind
+def _gpu_run_ctu(msh, p, precision, stream, steps, cfl):
+    g = msh.Grid(p.n, p.lo, p.hi, p.bc, cfl, precision, stream=stream.cuda_stream)
+    g.set_ctu(True)
+    W = p.W.astype(np.float32) if precision == msh.FP32 else p.W
+    g.set_state(W, msh.PRIMITIVE)
+    g.autotune()
+    g.set_state(W, msh.PRIMITIVE)
+    g.set_time(0.0, 0)
+    ns, t = g.run(max_steps=steps)
+    assert ns == steps
+    out = {"U": g.get_state().astype(np.float64), "W": g.get_state(msh.PRIMITIVE).astype(np.float64), "t": t,
+           "tiling": g.tiling()}
+    g.close()
+    return out
+
+
+def _oracle_run_ctu(oracle, p, W, steps, cfl):
+    og = oracle.Grid(p.n, p.lo, p.hi, p.bc, cfl, ctu=True)
+    U, ns, t, rc, _ = oracle.run(og, oracle.prim_to_cons(W.astype(np.float64)), np.inf, max_steps=steps)
+    assert rc == 0 and ns == steps
+    return U, t
+
+
+def test_ctu_blast_1024_first_50_steps(env, oracle):
+    """The corner-transport-upwind step at CFL 0.8 (the CTU line of the benchmark suite) on
+    the full 1024^2 blast: FP64 element by element, FP32 against the FP32-rounded input."""
+    msh, I, s = env
+    p = I.blast()
+    G = _gpu_run_ctu(msh, p, msh.FP64, s, 50, 0.8)
+    Uo, to = _oracle_run_ctu(oracle, p, p.W, 50, 0.8)
+    assert abs(G["t"] - to) <= 1e-13 * to
+    assert_fp64(G["U"], Uo, what=f"ctu blast 1024^2 fp64 tiling={G['tiling']}")
+    G = _gpu_run_ctu(msh, p, msh.FP32, s, 50, 0.8)
+    Uo, _ = _oracle_run_ctu(oracle, p, p.W.astype(np.float32), 50, 0.8)
+    assert_fp32(G["W"], oracle.cons_to_prim(Uo), what=f"ctu blast 1024^2 fp32 tiling={G['tiling']}")
+
+
+def test_ctu_box_256_first_steps_fp32(env, oracle):
+    """The corner-transport-upwind step at CFL 0.6 (the largest realizable one of the
+    benchmark suite's ladder) on the full 256^3 box, FP32, its first two steps element by
+    element against the oracle run from the FP32-rounded input."""
+    msh, I, s = env
+    p = I.turb()
+    G = _gpu_run_ctu(msh, p, msh.FP32, s, 2, 0.6)
+    Uo, to = _oracle_run_ctu(oracle, p, p.W.astype(np.float32), 2, 0.6)
+    assert abs(G["t"] - to) <= 1e-5 * to
+    assert_fp32(G["W"], oracle.cons_to_prim(Uo), what=f"ctu box 256^3 fp32 tiling={G['tiling']}")
