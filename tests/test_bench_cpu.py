@@ -1,0 +1,45 @@
+"""The benchmark's host-side contract, without a GPU: the reference arm (the oracle timed on
+the host cores) prints one JSON line with the keys the driver reads; the issue-rate roofline
+is the committed record's instructions per cell over the kernel time against the derived
+peak, and both it and the traffic are null without a record for the current source."""
+import json
+import os
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+import bench  # noqa: E402
+
+
+def test_reference_arm_json_line(oracle):
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--workload", "blast",
+                        "--n", "64", "--steps", "2", "--warmup", "1"], capture_output=True, text=True, timeout=600,
+                       cwd=ROOT)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [l for l in r.stdout.splitlines() if l.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    for k in ("impl", "metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+              "scaling", "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e"):
+        assert k in d, k
+    assert d["impl"] == "reference" and d["metric"] == "cell-updates/s" and d["value"] > 0
+    assert d["steps"] == 2 and d["warmup"] == 1 and d["config"]["cells"] == 64 * 64
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
+    assert d["e2e"]["value"] == d["value"] and d["e2e"]["h2d_bytes_per_step"] == 0
+
+
+def test_issue_roofline_arithmetic(monkeypatch):
+    rec = {"source_hash": "x", "dram_bytes_per_cell": 75.0, "warp_inst_per_cell": 80.0}
+    monkeypatch.setattr(bench, "traffic_record", lambda: rec)
+    r = bench.issue_roofline(1_000_000, 1e-4)
+    peak = 152 * 4 * 2070e6
+    assert r["bound"] == "alu" and r["peak"] == pytest.approx(peak)
+    assert r["achieved"] == pytest.approx(80.0 * 1e6 / 1e-4)
+    assert r["frac"] == pytest.approx(80.0 * 1e6 / 1e-4 / peak)
+    assert bench.measured_traffic(1000) == pytest.approx(75_000.0)
+    monkeypatch.setattr(bench, "traffic_record", lambda: None)
+    assert bench.issue_roofline(1_000_000, 1e-4) is None and bench.measured_traffic(1000) is None
+
