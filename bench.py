@@ -421,6 +421,18 @@ def _oracle_rate(p, steps=1, crop=None):
     return int(np.prod(n)) * steps / el, oracle.num_threads(), el
 
 
+def _oracle_rate_1core(p, steps=1, crop=None):
+    """The same on one host core (the oracle's OpenMP pool restored afterwards)."""
+    from oracle import oracle
+    n0 = oracle.num_threads()
+    oracle.set_num_threads(1)
+    try:
+        v, _, el = _oracle_rate(p, steps=steps, crop=crop)
+    finally:
+        oracle.set_num_threads(n0)
+    return v, el
+
+
 def run_suite(args):
     """One JSON line per workload: GPU cell-updates/s in FP32/FP64, the HBM fraction of the
     step kernel, the oracle's rate on the host cores, and for the batched tubes and the disc
@@ -477,6 +489,7 @@ def run_suite(args):
         p = inputs.sod(args.n or 256)
         r = grid_rate(p, msh.FP64, 1 << 20, p.t_end)
         orc, cores, _ = _oracle_rate(p, steps=r["steps"])
+        orc1, _ = _oracle_rate_1core(p, steps=r["steps"])
         # the same problem as one tube of the batched kernel: every step in one persistent
         # launch (the grid path pays six launches per step, which a 256-cell step cannot hide)
         WL, WR = p.W[:, 0, 0, 0], p.W[:, 0, 0, -1]
@@ -491,6 +504,7 @@ def run_suite(args):
         steps_b, _, cu = b.info()
         b.close()
         emit({"workload": f"sod {p.n[0]} cells FP64 to t=0.2", "gpu_fp64": r, "oracle": orc, "oracle_cores": cores,
+              "oracle_1core": orc1,
               "gpu_fp64_one_tube_batch": {"value": cu / el, "steps": int(steps_b[0]), "ms_total": el * 1e3}})
     # 2D blast 1024^2, 200 steps
     if only in (None, "blast"):
@@ -499,8 +513,10 @@ def run_suite(args):
         r32 = grid_rate(p, msh.FP32, steps)
         r64 = grid_rate(p, msh.FP64, steps)
         orc, cores, _ = _oracle_rate(p, steps=2)
+        orc1, _ = _oracle_rate_1core(p, steps=1, crop=(slice(0, 1), slice(0, 256), slice(0, 256)))
         emit({"workload": f"blast {p.n[0]}^2, {steps} steps", "gpu_fp32": r32, "gpu_fp64": r64, "oracle": orc,
-              "oracle_cores": cores, "oracle_sample": "2 FP64 steps of the full grid"})
+              "oracle_cores": cores, "oracle_sample": "2 FP64 steps of the full grid",
+              "oracle_1core": orc1, "oracle_1core_sample": "1 FP64 step of a 256^2 periodic crop"})
     # 3D box 256^3, 50 steps
     if only in (None, "box"):
         p = inputs.turb(n=args.n or 256)
@@ -508,8 +524,10 @@ def run_suite(args):
         r32 = grid_rate(p, msh.FP32, steps)
         r64 = grid_rate(p, msh.FP64, min(steps, 20))
         orc, cores, _ = _oracle_rate(p, steps=1)
+        orc1, _ = _oracle_rate_1core(p, steps=1, crop=(slice(0, 64), slice(0, 64), slice(0, 64)))
         emit({"workload": f"turb {p.n[0]}^3, {steps} steps (FP64: {min(steps, 20)})", "gpu_fp32": r32,
               "gpu_fp64": r64, "oracle": orc, "oracle_cores": cores, "oracle_sample": "1 FP64 step of the full grid",
+              "oracle_1core": orc1, "oracle_1core_sample": "1 FP64 step of a 64^3 periodic crop",
               "gpu_fp32_over_oracle": r32["value"] / orc})
     # the two schemes at the same CFL number: time per step (Sec. 4.1 reports the central
     # scheme about 22 % cheaper than the characteristic one on the CPU)
