@@ -207,3 +207,16 @@ def test_refusals(env):
         g.set_tape(1, 4)
     assert ei.value.status == msh.MSH_E_STATE
     g.close()
+
+
+@pytest.mark.parametrize("n,bc", [((2, 3), ((2, 2), (2, 1))), ((3, 2), ((1, 2), (0, 0))),
+                                  ((2, 2, 2), ((2, 2), (2, 2), (2, 2))), ((3, 2, 4), ((2, 1), (0, 0), (2, 2)))])
+def test_tiny_grids(env, oracle, scheme, n, bc):
+    """Grids of two or three cells per axis: nearly every neighbour a transverse term reads is
+    a boundary image, the corner images with reflections along two axes at once."""
+    msh, _ = env
+    nd = len(n)
+    shape = tuple(reversed(n)) if nd == 3 else (1,) + tuple(reversed(n))
+    W = _random(shape, sum(n) + 11)
+    U, _, Uo, _ = _run(msh, oracle, scheme, n, (0,) * nd, (1,) * nd, bc, 0.7, W, msh.FP64, steps=6)
+    assert_fp64(U, Uo, what=f"ctu {scheme[0]} tiny {n}")
