@@ -361,6 +361,11 @@ msh_status msh_batch_run_per_tube(msh_batch *b, const int32_t *tubes, int32_t co
 msh_status msh_batch_get_state(msh_batch *b, void *U, int32_t where, int32_t kind);
 /* steps[ntubes] and t[ntubes] (host, either may be NULL); *cell_updates = sum steps*len. */
 msh_status msh_batch_info(msh_batch *b, int64_t *steps, double *t, int64_t *cell_updates);
+/* Per tube, the number of steps of the last msh_batch_run whose second-order update left
+ * cells non-realizable, i.e. that took the a-posteriori fallback passes (counts[ntubes],
+ * host).  Zero after msh_batch_init / msh_batch_reset, and for tubes stepped by
+ * msh_batch_run_per_tube. */
+msh_status msh_batch_fallback_steps(msh_batch *b, int64_t *counts);
 msh_status msh_batch_destroy(msh_batch *b);
 
 /*
@@ -375,6 +380,13 @@ msh_status msh_batch_destroy(msh_batch *b);
  *   U_out      device pointer receiving U after one step (must not alias U_in)
  *   stream     cudaStream_t to run on (NULL: the default stream); the call synchronises it
  *   dt_taken   host pointer receiving the step size (may be NULL)
+ * The step is always the default one of a new grid: characteristic MUSCL-Hancock with the
+ * HLL flux, no corner-transport-upwind terms, the a-posteriori fallback, the default tiling
+ * (8 rows); a grid set to another scheme, to CTU or to another tiling steps differently.
+ * A non-realizable U_in (rho <= 0 or P not positive definite in some cell) is rejected with
+ * MSH_E_REALIZABILITY before any step, U_out untouched; a step whose result stays
+ * non-realizable after the fallback passes also returns MSH_E_REALIZABILITY (U_out then
+ * holds that result).  msh_last_error() names the first offending cell.
  * The working memory (control block, reduction partials, fallback tags) is one file-scope
  * device array of about 5.6 MB that every GPU holds from the moment it loads the library
  * until the process exits; grids of more than 1,048,576 cells (or needing more than 16384

@@ -28,7 +28,7 @@
  * upwind tracing (eqs 40-43, og_reconstruct_upwind) and a Roe-type flux (og_roe); the
  * characteristic step with the Hancock predictor and an HLLC flux (og_hllc).
  *
- * Readings where the paper is silent or garbled (each listed in the design doc):
+ * Readings where the paper is silent or garbled:
  *   - full ten-moment system (the paper prints only the diagonal 7-variable case);
  *   - the ten-moment Jacobian / eigenvectors derived from eqs contin/moment/dispers
  *     with zero heat flux (the printed 7x7 Jacobian misses rho in row 1 and the

@@ -12,6 +12,8 @@
 // That array is shared by every call: each call clears what must start at zero (the
 // control block and the tags of its cells) before using it, and two calls whose work
 // overlaps on the GPU (other streams, other host threads) race on it.
+#include <atomic>
+#include <cstdio>
 #include <cstring>
 
 #include "../../include/msh.h"
@@ -33,7 +35,30 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocBytes];
 
 namespace {
 constexpr int kMaxDevices = 64;
-void *g_scratch_addr[kMaxDevices] = {};  // device address of g_noalloc_scratch per device
+// device address of g_noalloc_scratch per device; two host threads making the first call on
+// a device at once both store the same address
+std::atomic<void *> g_scratch_addr[kMaxDevices] = {};
+
+// Start the step after the scan of U_in: a non-realizable input (rho <= 0 or P not positive
+// definite in some cell; the scan's finalize has set ctrl->realizable and first_bad) is not
+// stepped: the step kernels see done = 1 and return, U_out is not written, and the status is
+// MSH_E_REALIZABILITY.  Otherwise the step is planned as a one-step run with dt <= dt_max.
+__global__ void noalloc_start_kernel(Ctrl *c, double dt_max) {
+  if (!c->realizable) {
+    c->done = 1;
+    c->status = MSH_E_REALIZABILITY;
+    return;
+  }
+  c->t_end = INFINITY;
+  c->max_step = c->step + 1;
+  c->dt_max = dt_max;
+  c->done = 0;
+  c->status = 0;
+  double dt = c->dt_cfl;
+  if (dt > dt_max) dt = dt_max;
+  c->dt = dt;
+  c->t_next = c->t + dt;
+}
 
 template <typename T>
 msh_status noalloc_step(int ndim, const int64_t n[3], const double dx[3], const int32_t bc[6], double cfl,
@@ -80,7 +105,10 @@ msh_status noalloc_step(int ndim, const int64_t n[3], const double dx[3], const 
   // CFL dt of the input state, then one step with dt = min(CFL dt, dt_max)
   if (e == cudaSuccess) e = launch_scan<T>(Uin, N, a.nx, a.ny, ndim, dx, part, kScanBlocks, s);
   if (e == cudaSuccess) e = launch_finalize(ctrl, part, kScanBlocks, 1, s);
-  if (e == cudaSuccess) e = launch_run_start(ctrl, INFINITY, 1, dt_max, s);
+  if (e == cudaSuccess) {
+    noalloc_start_kernel<<<1, 1, 0, s>>>(ctrl, dt_max);
+    e = cudaGetLastError();
+  }
   for (int level = 0; e == cudaSuccess && level <= kFallbackPasses; level++) {
     a.level = level;
     e = launch_step<T>(a, ndim, rows, level > 0, s, nullptr);
@@ -93,11 +121,15 @@ msh_status noalloc_step(int ndim, const int64_t n[3], const double dx[3], const 
     set_error_text(cudaGetErrorString(e));
     return MSH_E_CUDA;
   }
-  if (dt_taken) *dt_taken = out.dt_last;
   if (out.status == MSH_E_REALIZABILITY) {
-    set_error_text("msh_step_noalloc: the step produced a non-realizable cell");
+    char msg[160];
+    snprintf(msg, sizeof msg, "msh_step_noalloc: %s (first cell %lld)",
+             out.step == 0 ? "U_in is not realizable; nothing was stepped" : "the step produced a non-realizable cell",
+             (long long)out.first_bad);
+    set_error_text(msg);
     return MSH_E_REALIZABILITY;
   }
+  if (dt_taken) *dt_taken = out.dt_last;
   return MSH_OK;
 }
 }  // namespace
@@ -138,16 +170,16 @@ extern "C" msh_status msh_step_noalloc(int32_t ndim, const int64_t n[3], const d
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess || dev < 0 || dev >= kMaxDevices)
     return set_error_text("msh_step_noalloc: no usable CUDA device"), MSH_E_CUDA;
-  if (!g_scratch_addr[dev]) {  // first call on this device: look up the array's device address
-    void *p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-    if (e != cudaSuccess || !p) {
+  void *addr = g_scratch_addr[dev].load(std::memory_order_acquire);
+  if (!addr) {  // first call on this device: look up the array's device address
+    e = cudaGetSymbolAddress(&addr, g_noalloc_scratch);
+    if (e != cudaSuccess || !addr) {
       set_error_text(cudaGetErrorString(e));
       return MSH_E_CUDA;
     }
-    g_scratch_addr[dev] = p;
+    g_scratch_addr[dev].store(addr, std::memory_order_release);
   }
-  unsigned char *base = static_cast<unsigned char *>(g_scratch_addr[dev]);
+  unsigned char *base = static_cast<unsigned char *>(addr);
   cudaStream_t s = (cudaStream_t)stream;
   if (precision == MSH_FP32)
     return noalloc_step<float>(ndim, n, dx, bc, cfl, dt_max, (const float *)U_in, (float *)U_out, s, dt_taken, base);

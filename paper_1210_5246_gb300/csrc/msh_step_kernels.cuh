@@ -20,6 +20,7 @@
 // (U^n + U1 + dt L(U1)) / 2 with the source and the partials).
 #pragma once
 #include <algorithm>
+#include <atomic>
 #include <cfloat>
 #include <climits>
 
@@ -833,16 +834,30 @@ __global__ void __launch_bounds__(32 * WARPS) step_strip2d_kernel(StepArgs<T> a)
 }
 
 // ---------------------------------------------------------------- launchers
-// grid of the fallback passes: two blocks per SM, looping over the tiles
+// grid of the fallback passes: two blocks per SM, looping over the tiles (any grid size
+// covers every tile; the SM count of the first device asked sizes it)
 inline int fallback_blocks() {
-  static int blocks = 0;
-  if (blocks == 0) {
+  static const int blocks = [] {
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    blocks = 2 * (sms > 0 ? sms : 152);
-  }
+    return 2 * (sms > 0 ? sms : 152);
+  }();
   return blocks;
+}
+
+// cudaFuncSetAttribute acts on the current device only: a kernel's launches on every device
+// need their own call.  One bit per device records it (devices 64 and up set it on every
+// launch; a repeated call is harmless, so two host threads racing on a bit are too).
+inline cudaError_t set_smem_once(std::atomic<uint64_t> &done, const void *kernel, size_t smem) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  const uint64_t bit = (dev >= 0 && dev < 64) ? (uint64_t(1) << dev) : 0;
+  if (bit != 0 && (done.load(std::memory_order_acquire) & bit)) return cudaSuccess;
+  e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e == cudaSuccess) done.fetch_or(bit, std::memory_order_acq_rel);
+  return e;
 }
 
 // 3D: 3 + RAW staged planes (three primitive, RAW raw) of NV x (rows+2) x 34, the y-sweep
@@ -875,13 +890,9 @@ static cudaError_t launch_tile(const StepArgs<T> &a, cudaStream_t s) {
     return cudaErrorInvalidConfiguration;  // 326 KB of shared memory: not offered for FP64
   } else {
   const size_t smem = step_smem<T>(NDIM, BY, CTU);
-  static bool attr_set = false;  // one attribute call per instantiation and process
-  if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(step_tile_kernel<T, NDIM, BY, SCH, RETRY, CTU>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    attr_set = true;
-  }
+  static std::atomic<uint64_t> attr_done{0};  // devices whose attribute is set, per instantiation
+  cudaError_t e = set_smem_once(attr_done, (const void *)step_tile_kernel<T, NDIM, BY, SCH, RETRY, CTU>, smem);
+  if (e != cudaSuccess) return e;
   const int ntiles = step_blocks<T>(NDIM, BY, a.nx, a.ny, a.nz, a.zchunk);
   const int blocks = RETRY ? std::min(ntiles, fallback_blocks()) : ntiles;
   step_tile_kernel<T, NDIM, BY, SCH, RETRY, CTU><<<blocks, dim3(32, BY), smem, s>>>(a);

@@ -168,6 +168,42 @@ def test_3d_shapes_and_boundaries(msh, oracle, shape, bc):
     g.close()
 
 
+def test_3d_step_on_a_second_device(msh):
+    """The 3D FP32 step kernels need more than 48 KB of dynamic shared memory, an attribute
+    that is set per device: a grid on device 0, then one on device 1 (and the allocation-free
+    step there), all with the same result.  Skipped where only one GPU is visible."""
+    import torch
+    if torch.cuda.device_count() < 2:
+        pytest.skip("one GPU visible")
+    shape, bc = (45, 30, 20), ((0, 0), (1, 1), (2, 2))
+    rng = np.random.default_rng(17)
+    W = np.zeros((10,) + shape[::-1])
+    W[0] = np.exp(rng.uniform(-0.5, 0.5, shape[::-1]))
+    W[1:4] = rng.uniform(-0.3, 0.3, (3,) + shape[::-1])
+    W[4], W[7], W[9] = 0.8, 0.7, 0.6
+    out = []
+    prev = torch.cuda.current_device()
+    try:
+        for dev in (0, 1):
+            torch.cuda.set_device(dev)
+            for rows in (16, 8):
+                g = msh.Grid(shape, (0, 0, 0), (1, 1, 1), bc, 0.5, msh.FP32)
+                g.set_tiling(rows, 8)
+                g.set_state(W.astype(np.float32), msh.PRIMITIVE)
+                g.run(max_steps=2)
+                out.append(g.get_state())
+                if rows == 8:
+                    u0 = torch.tensor(g.get_state(), device=f"cuda:{dev}")
+                    u1 = torch.empty_like(u0)
+                    msh.msh_step_noalloc(shape, (0, 0, 0), (1, 1, 1), bc, msh.FP32, 0.5, u0, u1)
+                    g.step()
+                    assert np.array_equal(u1.cpu().numpy(), g.get_state())
+                g.close()
+    finally:
+        torch.cuda.set_device(prev)
+    assert np.array_equal(out[0], out[2]) and np.array_equal(out[1], out[3])
+
+
 # ------------------------------------------------------------------ 2D disc
 def test_disc_gravity_fp64(msh, oracle, I):
     """Stellar disc in the fixed logarithmic potential, 64^2, 20 steps (gravity source)."""

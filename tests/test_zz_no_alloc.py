@@ -85,3 +85,31 @@ def test_noalloc_rejects_oversized_grid(msh):
         msh.msh_step_noalloc((1100, 1000), (0, 0), (1, 1), ((0, 0), (0, 0)), msh.FP64, 0.5, u,
                              torch.zeros_like(u))
     assert ei.value.status == msh.MSH_E_INVALID_ARG and "1048576" in str(ei.value)
+
+
+def test_noalloc_rejects_non_realizable_input(msh):
+    """A state with one cell whose P_xx P_yy < P_xy^2 is refused before any step, the
+    output buffer untouched; the next call on a realizable state steps normally."""
+    import torch
+    n, lo, hi, bc = (40, 24), (0.0, 0.0), (1.0, 1.0), ((0, 0), (1, 1))
+    W = _state((1, n[1], n[0]), seed=11)
+    W[5, 0, 7, 13] = 2.0  # P_xy^2 = 4 > P_xx P_yy = 0.56
+    U = W.copy()
+    r = W[0]
+    U[1:4] = r * W[1:4]
+    pairs = {4: (1, 1), 5: (1, 2), 6: (1, 3), 7: (2, 2), 8: (2, 3), 9: (3, 3)}
+    for k, (i, j) in pairs.items():
+        U[k] = W[k] + r * W[i] * W[j]
+    u0 = torch.tensor(U, device="cuda", dtype=torch.float64)
+    u1 = torch.full_like(u0, 7.0)
+    with pytest.raises(msh.MshError) as ei:
+        msh.msh_step_noalloc(n, lo, hi, bc, msh.FP64, 0.5, u0, u1)
+    assert ei.value.status == msh.MSH_E_REALIZABILITY
+    assert f"first cell {7 * n[0] + 13}" in str(ei.value)
+    assert bool((u1 == 7.0).all())
+    W[5, 0, 7, 13] = 0.0
+    U[5] = W[5] + r * W[1] * W[2]
+    u0 = torch.tensor(U, device="cuda", dtype=torch.float64)
+    assert msh.msh_step_noalloc(n, lo, hi, bc, msh.FP64, 0.5, u0, u1) > 0
+    assert bool(torch.isfinite(u1).all()) and not bool((u1 == 7.0).any())
+
