@@ -61,6 +61,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--fp32-only", action="store_true", help="skip the FP64 measurement")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the adjoint (disc 512^2 x 2000 steps) and batched-tubes measurements")
     ap.add_argument("--tiling", default=None, help="rows,zchunk instead of autotuning (e.g. 8,32)")
     ap.add_argument("--persistent-only", action="store_true",
                     help="with --suite --only tubes: skip the one-launch-per-step-per-tube baseline")
@@ -313,7 +315,8 @@ def run_gpu(args):
                      "kernel": kernel_name, "peak_source": peak_kind,
                      "kernel_ms": kms / kn, "bytes_per_cell": BYTES_PER_CELL["f32"],
                      "eager_ms_per_step": timed.eager_ms / args.steps, "finalize_ms": timed.fin_ms},
-        "issue_roofline": issue_roofline(ncells, avg_kernel_s) if args.workload == "box" else None,
+        "issue_roofline": (issue_roofline(ncells, avg_kernel_s, torch.cuda.get_device_properties(local).multi_processor_count,
+                                          clocks) if args.workload == "box" else None),
         "fp64": None if args.fp32_only else {
             "value": value64, "unit": "cell-updates/s", "steps": steps64, "ms_per_step": ms64 / steps64,
             "tiling": list(tiling64), "hbm_frac": BYTES_PER_CELL["f64"] * value64 / 1e9 / hbm},
@@ -321,6 +324,11 @@ def run_gpu(args):
         "clocks": clocks,
         "e2e": e2e,
     }
+    if rank == 0 and args.workload == "box" and not args.no_extras:
+        # the adjoint and batching targets, measured in the same run (outside the timed region)
+        from paper_1210_5246_gb300 import disc, inputs
+        out["adjoint"] = adjoint_costs(msh, disc, stream)
+        out["tubes"] = tubes_rates(msh, inputs, stream)
     if rank == 0 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(p)
     if world > 1:
@@ -329,20 +337,26 @@ def run_gpu(args):
         print(json.dumps(out))
 
 
-def issue_roofline(ncells, kernel_s):
-    """The bound the step kernel actually meets: instruction issue.  Peak = 152 SMs x 4 warp
-    schedulers x 1 warp instruction per cycle x the maximum SM clock (2070 MHz) =
-    1.259e12 warp instructions/s; achieved = the warp instructions per cell of the committed
-    ncu record x cells / the kernel's CUDA-event time (None without a record for the current
-    source)."""
+def issue_roofline(ncells, kernel_s, sms, clocks):
+    """The bound the step kernel actually meets: instruction issue.  Peak = the device's SM
+    count `sms` (cudaDeviceProp.multiProcessorCount) x 4 warp schedulers x 1 warp
+    instruction per cycle x the SM clock: the median sampled during the timed region (the
+    maximum clock when no sample was taken, said so in `clock_source`); achieved = the warp
+    instructions per cell of the committed ncu record x cells / the kernel's CUDA-event time
+    (None without a record for the current source)."""
     rec = traffic_record()
     if rec is None or "warp_inst_per_cell" not in rec:
         return None
-    peak = 152 * 4 * 2070e6
+    if clocks and clocks.get("sm_mhz"):
+        mhz, src = float(clocks["sm_mhz"]), "median SM clock sampled by nvidia-smi during the timed region"
+    else:
+        mhz, src = 2070.0, "maximum SM clock (no clock sample)"
+    peak = sms * 4 * mhz * 1e6
     achieved = rec["warp_inst_per_cell"] * ncells / kernel_s
     return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "warp-instructions/s",
             "frac": achieved / peak, "warp_inst_per_cell": rec["warp_inst_per_cell"],
-            "peak_source": "derived: 152 SMs x 4 schedulers x 2070 MHz"}
+            "sms": sms, "sm_mhz": mhz, "clock_source": src,
+            "peak_source": f"derived: {sms} SMs x 4 schedulers x {mhz:.0f} MHz"}
 
 
 def cpu_baseline(p):
@@ -513,10 +527,14 @@ def run_suite(args):
         r32 = grid_rate(p, msh.FP32, steps)
         r64 = grid_rate(p, msh.FP64, steps)
         orc, cores, _ = _oracle_rate(p, steps=2)
-        orc1, _ = _oracle_rate_1core(p, steps=1, crop=(slice(0, 1), slice(0, 256), slice(0, 256)))
+        crop = (slice(0, 1), slice(0, 256), slice(0, 256))
+        orc_crop, _, _ = _oracle_rate(p, steps=1, crop=crop)
+        orc1, _ = _oracle_rate_1core(p, steps=1, crop=crop)
         emit({"workload": f"blast {p.n[0]}^2, {steps} steps", "gpu_fp32": r32, "gpu_fp64": r64, "oracle": orc,
               "oracle_cores": cores, "oracle_sample": "2 FP64 steps of the full grid",
-              "oracle_1core": orc1, "oracle_1core_sample": "1 FP64 step of a 256^2 periodic crop"})
+              "oracle_crop": orc_crop, "oracle_1core": orc1,
+              "oracle_crop_sample": "1 FP64 step of a 256^2 periodic crop (oracle_crop: all cores, "
+                                    "oracle_1core: one core)"})
     # 3D box 256^3, 50 steps
     if only in (None, "box"):
         p = inputs.turb(n=args.n or 256)
@@ -524,10 +542,14 @@ def run_suite(args):
         r32 = grid_rate(p, msh.FP32, steps)
         r64 = grid_rate(p, msh.FP64, min(steps, 20))
         orc, cores, _ = _oracle_rate(p, steps=1)
-        orc1, _ = _oracle_rate_1core(p, steps=1, crop=(slice(0, 64), slice(0, 64), slice(0, 64)))
+        crop = (slice(0, 64), slice(0, 64), slice(0, 64))
+        orc_crop, _, _ = _oracle_rate(p, steps=1, crop=crop)
+        orc1, _ = _oracle_rate_1core(p, steps=1, crop=crop)
         emit({"workload": f"turb {p.n[0]}^3, {steps} steps (FP64: {min(steps, 20)})", "gpu_fp32": r32,
               "gpu_fp64": r64, "oracle": orc, "oracle_cores": cores, "oracle_sample": "1 FP64 step of the full grid",
-              "oracle_1core": orc1, "oracle_1core_sample": "1 FP64 step of a 64^3 periodic crop",
+              "oracle_crop": orc_crop, "oracle_1core": orc1,
+              "oracle_crop_sample": "1 FP64 step of a 64^3 periodic crop (oracle_crop: all cores, "
+                                    "oracle_1core: one core)",
               "gpu_fp32_over_oracle": r32["value"] / orc})
     # the two schemes at the same CFL number: time per step (Sec. 4.1 reports the central
     # scheme about 22 % cheaper than the characteristic one on the CPU)
@@ -600,8 +622,11 @@ def run_suite(args):
         run_suite_disc(msh, disc, stream, emit, n, 2000 if only is None else args.steps)
 
 
-def run_suite_tubes(msh, inputs, stream, emit, per_tube=True):
-    """Batched tubes: one persistent launch vs one launch per step per tube."""
+def tubes_rates(msh, inputs, stream, per_tube=True):
+    """Batched tubes (4096 tubes of 128..2048 cells, FP32, to t = 0.1): cell-updates/s of the
+    persistent launch (the whole workload, wall time around msh_batch_run after its
+    autotuning run) and, on 32 tubes spread over the length range, of one step-kernel launch
+    per step per tube (msh_batch_run_per_tube)."""
     import torch
     tb = inputs.tubes()
     b = msh.Batch(tb.length, tb.WL, tb.WR, tb.t_end, tb.cfl, msh.FP32, stream=stream.cuda_stream)
@@ -613,59 +638,76 @@ def run_suite_tubes(msh, inputs, stream, emit, per_tube=True):
     torch.cuda.synchronize()
     el = time.perf_counter() - t0
     _, _, cu = b.info()
-    if not per_tube:
-        b.close()
-        emit({"workload": "4096 tubes 128..2048 cells FP32 to t=0.1", "persistent": cu / el,
-              "cell_updates": cu, "seconds": el})
-        return
-    sample = np.argsort(tb.length)[:: len(tb.length) // 32][:32]
-    b.reset()
-    b.run_per_tube(sample)  # builds the per-tube grids
-    b.reset()
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    b.run_per_tube(sample)
-    torch.cuda.synchronize()
-    el_pt = time.perf_counter() - t0
-    steps_pt, _, _ = b.info()
-    cu_pt = int((steps_pt[sample] * tb.length[sample]).sum())
+    out = {"workload": "4096 tubes 128..2048 cells FP32 to t=0.1", "unit": "cell-updates/s",
+           "persistent": cu / el, "cell_updates": cu, "seconds": el}
+    if per_tube:
+        sample = np.argsort(tb.length)[:: len(tb.length) // 32][:32]
+        b.reset()
+        b.run_per_tube(sample)  # builds the per-tube grids
+        b.reset()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        b.run_per_tube(sample)
+        torch.cuda.synchronize()
+        el_pt = time.perf_counter() - t0
+        steps_pt, _, _ = b.info()
+        cu_pt = int((steps_pt[sample] * tb.length[sample]).sum())
+        out.update({"per_tube_launches": cu_pt / el_pt,
+                    "per_tube_sample": "32 tubes spread over the length range",
+                    "speedup": (cu / el) / (cu_pt / el_pt)})
     b.close()
-    emit({"workload": "4096 tubes 128..2048 cells FP32 to t=0.1", "persistent": cu / el,
-          "per_tube_launches": cu_pt / el_pt, "per_tube_sample": "32 tubes spread over the length range",
-          "speedup": (cu / el) / (cu_pt / el_pt), "cell_updates": cu, "seconds": el})
+    return out
+
+
+def run_suite_tubes(msh, inputs, stream, emit, per_tube=True):
+    """Batched tubes: one persistent launch vs one launch per step per tube."""
+    emit(tubes_rates(msh, inputs, stream, per_tube))
+
+
+def adjoint_costs(msh, disc, stream, n=512, nsteps=2000, K=50, precisions=("fp32", "fp64")):
+    """Differentiable disc (n^2, nsteps steps, checkpoints every K): wall time per step of the
+    forward run (BMERun: the recorded graph-launched run) and of the backward
+    (msh_adjoint_tape: segment recomputation from the checkpoints, reverse steps), each after
+    one warm-up; backward cell-updates/s = cells x steps / backward time.  FP32 and FP64, and
+    the FP32 loss and gradients' errors against FP64."""
+    import torch
+    from paper_1210_5246_gb300 import autograd as ag
+    res, grads = {}, {}
+    for name in precisions:
+        prec = msh.FP32 if name == "fp32" else msh.FP64
+        D = disc.DiscProblem(n=n, nsteps=nsteps, precision=prec, K=K, stream=stream.cuda_stream)
+        D.value_and_grad()  # warm-up (builds graphs, allocates)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        W0 = D.initial_state(D.delta0, torch.tensor(0.0, dtype=torch.float64, device="cuda")).to(D.dtype).contiguous()
+        ag.BMERun.apply(W0, D.grid, D.nsteps, D.K)
+        torch.cuda.synchronize()
+        t_fwd = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        L, gd, gb = D.value_and_grad()
+        torch.cuda.synchronize()
+        t_both = time.perf_counter() - t0
+        D.close()
+        t_bwd = t_both - t_fwd
+        cells = n * n
+        res[name] = {"forward_ms_per_step": t_fwd * 1e3 / nsteps, "backward_ms_per_step": t_bwd * 1e3 / nsteps,
+                     "backward_over_forward": t_bwd / t_fwd,
+                     "forward_cell_updates_per_s": cells * nsteps / t_fwd,
+                     "backward_cell_updates_per_s": cells * nsteps / t_bwd,
+                     "loss": L, "dL_dbeta": gb}
+        grads[name] = (L, gd, gb)
+    out = {"workload": f"disc {n}^2, {nsteps} steps, checkpoints every K={K}", **res}
+    if "fp32" in grads and "fp64" in grads:
+        (L, gd, gb), (L64, gd64, gb64) = grads["fp32"], grads["fp64"]
+        out["fp32_error_vs_fp64"] = {"loss_rel": abs(L - L64) / abs(L64), "dL_dbeta_rel": abs(gb - gb64) / abs(gb64),
+                                     "dL_ddelta_rel_l2": float(torch.linalg.norm(gd - gd64) / torch.linalg.norm(gd64))}
+    return out
 
 
 def run_suite_disc(msh, disc, stream, emit, n, nsteps, K=50):
     """Differentiable disc: cost per step of the forward run and of the backward
     (msh_adjoint_run: checkpointed forward, segment recomputation, reverse steps)."""
-    import torch
-    from paper_1210_5246_gb300 import autograd as ag
-    D = disc.DiscProblem(n=n, nsteps=nsteps, precision=msh.FP32, K=K, stream=stream.cuda_stream)
-    D.value_and_grad()  # warm-up (builds graphs, allocates)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    W0 = D.initial_state(D.delta0, torch.tensor(0.0, dtype=torch.float64, device="cuda")).float().contiguous()
-    ag.BMERun.apply(W0, D.grid, D.nsteps, D.K)
-    torch.cuda.synchronize()
-    t_fwd = time.perf_counter() - t0
-    t0 = time.perf_counter()
-    L, gd, gb = D.value_and_grad()
-    torch.cuda.synchronize()
-    t_both = time.perf_counter() - t0
-    D.close()
-    # the same loss and gradients in FP64 (the FP32 error is stated against them)
-    D64 = disc.DiscProblem(n=n, nsteps=nsteps, precision=msh.FP64, K=K, stream=stream.cuda_stream)
-    L64, gd64, gb64 = D64.value_and_grad()
-    D64.close()
-    gd_rel = float(torch.linalg.norm(gd - gd64) / torch.linalg.norm(gd64))
-    cells = n * n
-    emit({"workload": f"disc {n}^2 FP32, {nsteps} steps, K={K}", "loss": L, "dL_dbeta": gb,
-          "forward_ms_per_step": t_fwd * 1e3 / nsteps, "adjoint_ms_per_step": (t_both - t_fwd) * 1e3 / nsteps,
-          "adjoint_over_forward": (t_both - t_fwd) / t_fwd, "forward_cell_updates_per_s": cells * nsteps / t_fwd,
-          "adjoint_cell_updates_per_s": cells * nsteps / (t_both - t_fwd),
-          "fp64": {"loss": L64, "dL_dbeta": gb64},
-          "fp32_error": {"loss_rel": abs(L - L64) / abs(L64), "dL_dbeta_rel": abs(gb - gb64) / abs(gb64),
-                         "dL_ddelta_rel_l2": gd_rel}})
+    emit(adjoint_costs(msh, disc, stream, n, nsteps, K))
 
 
 if __name__ == "__main__":

@@ -38,6 +38,7 @@ template <typename T> struct TubeArgs {
   int64_t *steps;          // [ntubes] out
   double *t_out;           // [ntubes] out
   int32_t *status;         // [ntubes] out: 0 ok, 4 non-realizable, 5 step cap reached
+  int64_t *fallback;       // [ntubes] out: steps whose second-order update tagged cells
   int64_t total;
   int32_t ntubes;
   int32_t cap;             // shared-memory capacity in cells (>= max len)
@@ -179,7 +180,7 @@ __global__ void __launch_bounds__(NT) tubes_kernel(TubeArgs<T> a) {
     sm = block_max<T, NT>(sm, red);
     double tt = 0.0;
     const double te = a.t_end[k];
-    int64_t steps = 0;
+    int64_t steps = 0, fb_steps = 0;
     int status = 0;
     while (tt < te) {
       if (steps >= a.max_steps) { status = 5; break; }
@@ -191,6 +192,7 @@ __global__ void __launch_bounds__(NT) tubes_kernel(TubeArgs<T> a) {
       __syncthreads();
       T smax = tube_pass<T, NT, false>(cur, nxt, sFl, n, cap, nu, dtdx, idx, sF, sH, sHc, &s_nbad, &s_any);
       sm = block_max<T, NT>(smax, red);  // its barriers also order the carries and s_nbad
+      fb_steps += s_nbad != 0;
       // a-posteriori fallback: redo the step from U^n with first-order faces at every tagged
       // cell; cells still failing are tagged too (at most kFallbackPasses passes)
       for (int pass = 1; pass <= kFallbackPasses && s_nbad; pass++) {
@@ -221,6 +223,7 @@ __global__ void __launch_bounds__(NT) tubes_kernel(TubeArgs<T> a) {
       a.steps[k] = steps;
       a.t_out[k] = tt;
       a.status[k] = status;
+      a.fallback[k] = fb_steps;
     }
     __syncthreads();
   }
@@ -299,6 +302,7 @@ struct msh_batch {
   int32_t *d_len = nullptr, *d_order = nullptr, *d_queue = nullptr, *d_status = nullptr;
   double *d_tend = nullptr, *d_t = nullptr;
   int64_t *d_steps = nullptr;
+  int64_t *d_fallback = nullptr;
   std::vector<msh_grid *> grids;  // per-tube grids of the per-launch baseline (lazily built)
 };
 
@@ -323,6 +327,7 @@ msh_status upload_initial(msh_batch *b) {
                                       : launch_convert<double>((double *)b->U, (size_t)b->total, 0, b->stream);
   if (e != cudaSuccess) return bfail(MSH_E_CUDA, "convert: %s", cudaGetErrorString(e));
   B_TRY(cudaMemsetAsync(b->d_steps, 0, sizeof(int64_t) * b->ntubes, b->stream));
+  B_TRY(cudaMemsetAsync(b->d_fallback, 0, sizeof(int64_t) * b->ntubes, b->stream));
   B_TRY(cudaMemsetAsync(b->d_t, 0, sizeof(double) * b->ntubes, b->stream));
   B_TRY(cudaMemsetAsync(b->d_status, 0, sizeof(int32_t) * b->ntubes, b->stream));
   B_TRY(cudaStreamSynchronize(b->stream));
@@ -334,11 +339,11 @@ msh_status run_once(msh_batch *b, int nt, int64_t max_steps) {
   cudaError_t e;
   if (b->prec == MSH_FP32) {
     TubeArgs<float> a{(float *)b->U, b->d_off, b->d_len, b->d_tend, b->d_order, b->d_queue, b->d_steps, b->d_t,
-                      b->d_status, b->total, b->ntubes, b->cap, b->cfl, max_steps};
+                      b->d_status, b->d_fallback, b->total, b->ntubes, b->cap, b->cfl, max_steps};
     e = launch_tubes<float>(a, nt, b->stream);
   } else {
     TubeArgs<double> a{(double *)b->U, b->d_off, b->d_len, b->d_tend, b->d_order, b->d_queue, b->d_steps, b->d_t,
-                       b->d_status, b->total, b->ntubes, b->cap, b->cfl, max_steps};
+                       b->d_status, b->d_fallback, b->total, b->ntubes, b->cap, b->cfl, max_steps};
     e = launch_tubes<double>(a, nt, b->stream);
   }
   if (e != cudaSuccess) return bfail(MSH_E_CUDA, "tube kernel launch: %s", cudaGetErrorString(e));
@@ -429,6 +434,7 @@ msh_status msh_batch_init(msh_batch **out, int32_t ntubes, const int32_t *len, c
   if (e == cudaSuccess) e = cudaMalloc(&b->d_tend, sizeof(double) * ntubes);
   if (e == cudaSuccess) e = cudaMalloc(&b->d_t, sizeof(double) * ntubes);
   if (e == cudaSuccess) e = cudaMalloc(&b->d_steps, sizeof(int64_t) * ntubes);
+  if (e == cudaSuccess) e = cudaMalloc(&b->d_fallback, sizeof(int64_t) * ntubes);
   if (e != cudaSuccess) return cleanup(bfail(MSH_E_NOMEM, "batch allocation: %s", cudaGetErrorString(e)));
   e = cudaMemcpyAsync(b->d_off, b->off.data(), sizeof(int64_t) * ntubes, cudaMemcpyHostToDevice, b->stream);
   if (e == cudaSuccess) e = cudaMemcpyAsync(b->d_len, len, sizeof(int32_t) * ntubes, cudaMemcpyHostToDevice, b->stream);
@@ -596,6 +602,14 @@ msh_status msh_batch_info(msh_batch *b, int64_t *steps, double *t, int64_t *cell
   return MSH_OK;
 }
 
+msh_status msh_batch_fallback_steps(msh_batch *b, int64_t *counts) {
+  clear_error();
+  if (!b || !counts) return bfail(MSH_E_INVALID_ARG, "null argument");
+  B_TRY(cudaMemcpyAsync(counts, b->d_fallback, sizeof(int64_t) * b->ntubes, cudaMemcpyDeviceToHost, b->stream));
+  B_TRY(cudaStreamSynchronize(b->stream));
+  return MSH_OK;
+}
+
 msh_status msh_batch_destroy(msh_batch *b) {
   if (!b) return MSH_OK;
   if (b->stream) cudaStreamSynchronize(b->stream);
@@ -610,6 +624,7 @@ msh_status msh_batch_destroy(msh_batch *b) {
   cudaFree(b->d_tend);
   cudaFree(b->d_t);
   cudaFree(b->d_steps);
+  cudaFree(b->d_fallback);
   if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
   delete b;
   return MSH_OK;

@@ -79,6 +79,7 @@ SIGNATURES = {
     "msh_batch_run_per_tube": [_vp, _P(_i32), _i32, _i64],
     "msh_batch_get_state": [_vp, _vp, _i32, _i32],
     "msh_batch_info": [_vp, _P(_i64), _P(_dbl), _P(_i64)],
+    "msh_batch_fallback_steps": [_vp, _P(_i64)],
     "msh_batch_destroy": [_vp],
     "msh_step_noalloc": [_i32, _P(_i64), _P(_dbl), _P(_dbl), _P(_i32), _i32, _dbl, _dbl, _vp, _vp, _vp, _P(_dbl)],
 }
@@ -489,3 +490,9 @@ class Batch:
         _check(load().msh_batch_info(self.h, steps.ctypes.data_as(C.POINTER(C.c_int64)), _ptr_dbl(t),
                                      C.byref(cu)))
         return steps, t, cu.value
+
+    def fallback_steps(self):
+        """Per tube, the steps of the last run that took the a-posteriori fallback passes."""
+        counts = np.zeros(self.ntubes, dtype=np.int64)
+        _check(load().msh_batch_fallback_steps(self.h, counts.ctypes.data_as(C.POINTER(C.c_int64))))
+        return counts

@@ -34,12 +34,17 @@ def test_reference_arm_json_line(oracle):
 def test_issue_roofline_arithmetic(monkeypatch):
     rec = {"source_hash": "x", "dram_bytes_per_cell": 75.0, "warp_inst_per_cell": 80.0}
     monkeypatch.setattr(bench, "traffic_record", lambda: rec)
-    r = bench.issue_roofline(1_000_000, 1e-4)
-    peak = 152 * 4 * 2070e6
+    # the peak follows the device's SM count and the clock sampled during the timed region
+    r = bench.issue_roofline(1_000_000, 1e-4, 148, {"sm_mhz": 1800.0, "sm_max_mhz": 2070.0, "reasons": []})
+    peak = 148 * 4 * 1800e6
     assert r["bound"] == "alu" and r["peak"] == pytest.approx(peak)
+    assert r["sms"] == 148 and r["sm_mhz"] == 1800.0
     assert r["achieved"] == pytest.approx(80.0 * 1e6 / 1e-4)
     assert r["frac"] == pytest.approx(80.0 * 1e6 / 1e-4 / peak)
+    # without a clock sample: the maximum SM clock, said so
+    r = bench.issue_roofline(1_000_000, 1e-4, 152, None)
+    assert r["peak"] == pytest.approx(152 * 4 * 2070e6) and "no clock sample" in r["clock_source"]
     assert bench.measured_traffic(1000) == pytest.approx(75_000.0)
     monkeypatch.setattr(bench, "traffic_record", lambda: None)
-    assert bench.issue_roofline(1_000_000, 1e-4) is None and bench.measured_traffic(1000) is None
+    assert bench.issue_roofline(1_000_000, 1e-4, 152, None) is None and bench.measured_traffic(1000) is None
 

@@ -118,24 +118,65 @@ def test_rejects_bad_tubes(msh):
     assert ei.value.status == msh.MSH_E_REALIZABILITY
 
 
+def _oracle_tubes(oracle, tubes, ks, dtype):
+    """Oracle runs of tubes ks (from the initial states rounded to dtype), in parallel threads
+    (the oracle's C code is re-entrant and runs without the GIL; one OpenMP thread each)."""
+    import concurrent.futures as cf
+    import os
+
+    def one(k):
+        oracle.set_num_threads(1)
+        return k, _oracle_tube(oracle, tubes, k, dtype)
+    with cf.ThreadPoolExecutor(max_workers=max(1, min(32, os.cpu_count() or 1))) as ex:
+        return dict(ex.map(one, ks))
+
+
 def test_full_workload_4096_tubes(msh, oracle):
-    """The full batched workload (4096 tubes, 128..2048 cells, FP32, t = 0.1): every tube
-    reaches t_end; the longest, shortest and a seeded sample match the oracle."""
+    """The full batched workload (4096 tubes, 128..2048 cells, FP32, t = 0.1) in one persistent
+    launch: every tube reaches t_end, every cell stays realizable, and against the oracle run
+    from the FP32-rounded input (relative L1 2e-4 on rho, 5e-4 on each P_ij, step counts
+    within one): every tube whose run took the a-posteriori fallback, the 10 longest, the
+    shortest and a seeded random sample, at least 64 tubes.  The same tubes of up to 1024
+    cells (the FP64 batch limit) also run as one FP64 batch against the oracle at 1e-10."""
     from paper_1210_5246_gb300 import inputs
     tubes = inputs.tubes()
     b = msh.Batch(tubes.length, tubes.WL, tubes.WR, tubes.t_end, tubes.cfl, msh.FP32)
     b.run()
     steps, t, cu = b.info()
+    fb = b.fallback_steps()
     assert np.all(t == tubes.t_end)
     W = b.get_state(msh.PRIMITIVE).astype(np.float64)
-    assert np.all(W[0] > 0) and np.all(W[4] > 0)
-    rng = np.random.default_rng(4)
-    pick = {int(np.argmax(tubes.length)), int(np.argmin(tubes.length))} | set(rng.choice(4096, 4, replace=False).tolist())
-    for k in sorted(pick):
-        Uo, so, to, rc = _oracle_tube(oracle, tubes, k, np.float32)
-        assert abs(int(steps[k]) - so) <= 1
-        assert_fp32(b.tube(W, k), oracle.cons_to_prim(Uo), what=f"tube {k}")
     b.close()
+    assert np.all(W[0] > 0) and np.all(W[4] > 0)
+    longest = np.argsort(tubes.length, kind="stable")[::-1][:10]
+    pick = set(np.nonzero(fb)[0].tolist()) | set(longest.tolist()) | {int(np.argmin(tubes.length))}
+    assert len(np.nonzero(fb)[0]) > 0  # the workload exercises the fallback
+    rng = np.random.default_rng(4)
+    rest = np.setdiff1d(np.arange(4096), sorted(pick))
+    pick |= set(rng.choice(rest, max(16, 64 - len(pick)), replace=False).tolist())
+    ks = sorted(pick)
+    assert len(ks) >= 64
+    ref = _oracle_tubes(oracle, tubes, ks, np.float32)
+    for k in ks:
+        Uo, so, to, rc = ref[k]
+        assert rc == 0 and to == tubes.t_end, (k, rc)
+        assert abs(int(steps[k]) - so) <= 1, (k, int(steps[k]), so)
+        assert_fp32(b.tube(W, k), oracle.cons_to_prim(Uo), what=f"tube {k} (len {tubes.length[k]}, "
+                                                                f"{fb[k]} fallback steps)")
+    # FP64: the picked tubes that fit an FP64 batch, element by element
+    from paper_1210_5246_gb300 import inputs as I
+    k64 = [k for k in ks if tubes.length[k] <= 1024]
+    sub = I.Tubes(tubes.length[k64], tubes.WL[k64], tubes.WR[k64], tubes.t_end, tubes.cfl)
+    b64 = msh.Batch(sub.length, sub.WL, sub.WR, sub.t_end, sub.cfl, msh.FP64)
+    b64.run()
+    s64, t64, _ = b64.info()
+    U64 = b64.get_state()
+    ref64 = _oracle_tubes(oracle, sub, list(range(len(k64))), np.float64)
+    for i, k in enumerate(k64):
+        Uo, so, to, rc = ref64[i]
+        assert rc == 0 and s64[i] == so and t64[i] == to, (k, s64[i], so)
+        assert_fp64(b64.tube(U64, i), Uo, what=f"fp64 tube {k} (len {tubes.length[k]})")
+    b64.close()
 
 
 def test_iterated_fallback_tube_fp64(msh, oracle):

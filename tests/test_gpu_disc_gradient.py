@@ -53,6 +53,32 @@ def test_disc_gradient_fp64_matches_central_fd(mods, oracle):
     D.close()
 
 
+def test_disc_gradient_full_size_fp64_matches_central_fd(mods, oracle):
+    """The configured workload itself: 512^2 disc, 2000 steps, checkpoints every K = 50 (40
+    recomputed segments), FP64 through BMERun / msh_adjoint_tape, against central finite
+    differences of the FP64 oracle replaying the forward run's dt schedule: dL/dbeta and
+    dL/ddelta along one seeded random direction, each to 1e-3 relative over the whole
+    2000-step horizon (each oracle run takes ~1 min on 16 host cores; four runs)."""
+    disc, msh = mods
+    D = disc.DiscProblem(n=512, nsteps=2000, precision=msh.FP64, K=50)
+    beta = 0.05
+    L0, gd, gb = D.value_and_grad(beta=beta)
+    dts = D.grid.dt_history()
+    delta0 = D.delta0.cpu().numpy()
+    gd = gd.cpu().numpy()
+    D.close()
+    assert 0 < L0 < 1 and len(dts) == 2000
+    h = 1e-6
+    fd_b = (_oracle_loss(oracle, D, delta0, beta + h, dts) - _oracle_loss(oracle, D, delta0, beta - h, dts)) / (2 * h)
+    assert abs(fd_b - gb) <= 1e-3 * abs(fd_b), (fd_b, gb)
+    v = np.random.default_rng(7).normal(size=delta0.shape) * 0.01
+    h = 1e-5
+    fd_d = (_oracle_loss(oracle, D, delta0 + h * v, beta, dts)
+            - _oracle_loss(oracle, D, delta0 - h * v, beta, dts)) / (2 * h)
+    ad_d = float((gd * v).sum())
+    assert abs(fd_d - ad_d) <= 1e-3 * abs(fd_d), (fd_d, ad_d)
+
+
 def _beta_terms_magnitude(disc, D):
     """sum over cells and fields of |dL/dW0 * dW0/dbeta| of an FP64 problem: the size of the
     per-cell terms whose (cancelling) sum is dL/dbeta.  dW0/dbeta by a central difference of

@@ -3,13 +3,14 @@
 
 * 2D blast, 1024^2 periodic, all 200 steps: FP64 against the oracle (rel L_inf <= 1e-10),
   FP32 against the oracle run from the FP32-rounded input (rel L1 <= 2e-4 / 5e-4).
-* 3D box, 256^3 periodic: the first 3 steps element by element in FP64 and FP32 (the
-  oracle needs ~3 s per full step on 16 cores); the full 50-step FP32 and FP64 runs by
-  properties that hold at any size: all ten totals conserved to round-off (periodic),
-  every cell realizable, the dt sequence of the first steps equal to the oracle's, and
-  FP32 against FP64 after 50 steps.
-* Disc, 512^2 outflow with gravity, FP32, all 2000 steps against the oracle; FP64 for
-  the first 200 steps.
+* 3D box, 256^3 periodic, all 50 steps: FP64 element by element against the oracle
+  (rel L_inf <= 1e-10, the dt sequence to 1e-12) and FP32 against the same FP64 oracle run
+  (rel L1 <= 2e-4 / 5e-4; the FP32 input is the rounded FP64 one, a 6e-8 perturbation far
+  below the tolerance; the oracle needs ~3 s per step on 16 cores, so one oracle run
+  serves both); the full runs also by properties that hold at any size: all ten totals
+  conserved to round-off (periodic), every cell realizable, device totals against an FP64
+  sum of the state, FP32 against FP64.
+* Disc, 512^2 outflow with gravity, all 2000 steps: FP32 and FP64 against the oracle.
 * Corner transport upwind: the blast's first 50 steps at CFL 0.8 (FP64 and FP32) and the
   box's first 2 steps at CFL 0.6 (FP32) against the oracle's CTU step.
 """
@@ -83,17 +84,19 @@ def box(env):
     return I.turb()
 
 
-def test_box_256_first_steps_elementwise(env, oracle, box):
+def test_box_256_all_50_steps_elementwise(env, oracle, box):
     msh, I, s = env
-    p, k = box, 3
-    G64 = _gpu_run(msh, p, msh.FP64, s, k, record=k)
-    Uo, _, ho = _oracle_run(oracle, p, p.W, k, record=True)
+    p = box
+    Uo, to, ho = _oracle_run(oracle, p, p.W, p.nsteps, record=True)
+    G64 = _gpu_run(msh, p, msh.FP64, s, p.nsteps, record=p.nsteps)
     np.testing.assert_allclose(G64["dts"], ho, rtol=1e-12)
-    assert_fp64(G64["U"], Uo, what=f"box 256^3 fp64, {k} steps")
-    del G64, Uo
-    G32 = _gpu_run(msh, p, msh.FP32, s, k)
-    Uo32, _, _ = _oracle_run(oracle, p, p.W.astype(np.float32), k)
-    assert_fp32(G32["W"], oracle.cons_to_prim(Uo32), what=f"box 256^3 fp32, {k} steps")
+    assert abs(G64["t"] - to) <= 1e-12 * to
+    assert_fp64(G64["U"], Uo, what=f"box 256^3 fp64, {p.nsteps} steps, tiling={G64['tiling']}")
+    del G64
+    Wo = oracle.cons_to_prim(Uo)
+    del Uo
+    G32 = _gpu_run(msh, p, msh.FP32, s, p.nsteps)
+    assert_fp32(G32["W"], Wo, what=f"box 256^3 fp32, {p.nsteps} steps, tiling={G32['tiling']}")
 
 
 def test_box_256_full_run_properties(env, box):
@@ -138,12 +141,13 @@ def test_disc_512_fp32_all_steps(env, oracle):
     assert_fp32(G["W"], oracle.cons_to_prim(Uo), what=f"disc 512^2 fp32, {p.nsteps} steps")
 
 
-def test_disc_512_fp64_first_200_steps(env, oracle):
+def test_disc_512_fp64_all_steps(env, oracle):
     msh, I, s = env
     p = I.disc()
-    G = _gpu_run(msh, p, msh.FP64, s, 200)
-    Uo, _, _ = _oracle_run(oracle, p, p.W, 200)
-    assert_fp64(G["U"], Uo, what="disc 512^2 fp64, 200 steps")
+    G = _gpu_run(msh, p, msh.FP64, s, p.nsteps)
+    Uo, to, _ = _oracle_run(oracle, p, p.W, p.nsteps)
+    assert abs(G["t"] - to) <= 1e-12 * to
+    assert_fp64(G["U"], Uo, what=f"disc 512^2 fp64, {p.nsteps} steps")
 
 
 # ------------------------------------------------- corner transport upwind
