@@ -318,7 +318,8 @@ msh_status msh_set_self_gravity(msh_grid *g, double G);
  *                                 *tagged_cells (may be NULL) receives the number of cells the
  *                                 a-posteriori fallback tagged in it.  The fallback couples
  *                                 cells within a step, so a slab run equals the single-grid run
- *                                 only for steps in which no rank tagged cells.
+ *                                 only for steps in which no rank tagged cells; the phased step
+ *                                 below shares the fallback between slabs.
  *   msh_set_cell_width            replaces the cell widths dx[d] (> 0, active dims) that
  *                                 msh_init_grid derived from (hi - lo) / n: a slab of m
  *                                 layers takes the global grid's widths exactly, which
@@ -331,6 +332,45 @@ msh_status msh_set_slab(msh_grid *g, int64_t start, int64_t count, const void *b
 msh_status msh_reduce_layers(msh_grid *g, int64_t start, int64_t count, double totals[10], double *dt_cfl,
                              int32_t *realizable);
 msh_status msh_step_dt(msh_grid *g, double dt, int32_t *tagged_cells);
+
+/*
+ * Phased step: msh_step_dt split at the passes of its a-posteriori fallback, so that slabs
+ * of one grid take their fallback passes together (the guardcell exchange of Sec. 3.1
+ * applied to the fallback tags; the fallback itself is this library's positivity rule: a
+ * cell whose second-order update is not realizable is tagged, and the step is recomputed
+ * with first-order face states on every face of every tagged cell, at most 4 passes, cells
+ * still failing joining the tagged set).  A face's states depend on the tags of the two
+ * cells it joins, so a slab needs its neighbours' tags in its first halo layer before each
+ * pass.  The protocol, per step, on every slab:
+ *   msh_step_begin(g, dt)          the second-order pass with exactly dt; its failing cells
+ *                                  are tagged by pass 0;
+ *   then for p = 1, 2, ... 4, while some slab's owned layers hold cells tagged by pass p-1
+ *   (msh_count_tags, summed over the slabs):
+ *     msh_set_tags on the halo layers from the neighbours' msh_get_tags of their owned
+ *     boundary layers, then msh_step_retry(g, p): fallback pass p from the same U^n with
+ *     first-order faces at every cell tagged by passes 0 .. p-1 of this step, run even where
+ *     this grid tagged nothing itself; its newly failing cells are tagged by pass p;
+ *   msh_step_end(g, &tagged)       the step's totals, CFL dt of the new state, time and step
+ *                                  counter advance (MSH_E_REALIZABILITY as msh_step_dt).
+ * On one grid, the passes msh_step_dt would run give its result bit for bit.
+ *   msh_get_tags / msh_set_tags    per cell of layers [start, start + count) (int32
+ *                                  levels[count][cells per layer], host or device per
+ *                                  `where`, owned by the caller): the pass of the current step
+ *                                  that tagged it, or -1.  msh_set_tags overwrites the tags of
+ *                                  those layers (-1 clears).
+ *   msh_count_tags                 *n = cells of layers [start, start + count) tagged by pass
+ *                                  `level` (0 .. 4) of the current step.
+ * The central scheme has no fallback (msh_step_begin: MSH_E_STATE; step it with
+ * msh_step_dt), nor does a grid with self-gravity take a phased step.  msh_step_retry out
+ * of order or outside begin .. end, and msh_step_end without begin: MSH_E_STATE or
+ * MSH_E_INVALID_ARG; any other stepping call closes an open phased step.
+ */
+msh_status msh_step_begin(msh_grid *g, double dt);
+msh_status msh_step_retry(msh_grid *g, int32_t level);
+msh_status msh_step_end(msh_grid *g, int32_t *tagged_cells);
+msh_status msh_get_tags(msh_grid *g, int64_t start, int64_t count, int32_t *levels, int32_t where);
+msh_status msh_set_tags(msh_grid *g, int64_t start, int64_t count, const int32_t *levels, int32_t where);
+msh_status msh_count_tags(msh_grid *g, int64_t start, int64_t count, int32_t level, int64_t *n);
 
 /*
  * Batched independent 1D Riemann problems ("tubes") on [0, 1] with the interface at 0.5

@@ -822,6 +822,52 @@ static int step_pass(const og_grid *Gr, const double *U, const double *phi, doub
     return 0;
 }
 
+/* Tags of the grid's cells (bad[N]) on the padded grid: a ghost cell carries the tag of
+ * its source cell (a1's mapping). */
+static void padded_flags(const og_grid *Gr, const unsigned char *bad, unsigned char *flag)
+{
+    og_pad P = make_pad(Gr);
+    for (int64_t z = -P.g[2]; z < P.n[2] + P.g[2]; z++)
+        for (int64_t y = -P.g[1]; y < P.n[1] + P.g[1]; y++)
+            for (int64_t x = -P.g[0]; x < P.n[0] + P.g[0]; x++) {
+                int64_t c[3] = {x, y, z}, s[3];
+                int mir;
+                for (int d = 0; d < 3; d++)
+                    s[d] = ghost_src(c[d], P.n[d], Gr->bc[2 * d], Gr->bc[2 * d + 1], &mir);
+                flag[pidx(&P, x, y, z)] = bad[(s[2] * P.n[1] + s[1]) * P.n[0] + s[0]];
+            }
+}
+
+/* One pass of the characteristic step from U to Unew: the second-order pass with
+ * tagged == NULL, else the pass of og_step's a-posteriori fallback with first-order face
+ * states on every face that touches a cell whose tagged[c] is non-zero (tagged[N] over the
+ * grid's cells).  og_step is this pass repeated with the growing tagged set; a driver that
+ * shares the fallback across several grids (slabs of one grid) repeats it itself.
+ * Returns 0, or 1 on allocation failure. */
+int og_step_pass(const og_grid *Gr, const double *U, const double *phi, double dt, const unsigned char *tagged,
+                 double *Unew)
+{
+    if (!tagged) return step_pass(Gr, U, phi, dt, NULL, Unew);
+    og_pad P = make_pad(Gr);
+    unsigned char *flag = (unsigned char *)calloc((size_t)(P.p[0] * P.p[1] * P.p[2]), 1);
+    if (!flag) return 1;
+    padded_flags(Gr, tagged, flag);
+    int rc = step_pass(Gr, U, phi, dt, flag, Unew);
+    free(flag);
+    return rc;
+}
+
+/* Per cell of U: 1 if realizable (rho > 0, P positive definite), else 0. */
+void og_realizable_cells(const og_grid *Gr, const double *U, unsigned char *out)
+{
+    int64_t N = Gr->n[0] * Gr->n[1] * Gr->n[2];
+    for (int64_t c = 0; c < N; c++) {
+        double Uc[NV];
+        for (int k = 0; k < NV; k++) Uc[k] = U[k * N + c];
+        out[c] = (unsigned char)cell_realizable(Uc);
+    }
+}
+
 /* One step of size dt from U to Unew ([NV][nz][ny][nx]).  phi: NULL or the
  * potential with one ghost layer on active dims ([nz+2gz][ny+2gy][nx+2gx]).
  * A-posteriori fallback (reading; the paper is silent on positivity): if the
@@ -854,16 +900,7 @@ int og_step(const og_grid *Gr, const double *U, const double *phi, double dt, do
     for (int pass = 0; nbad > 0 && pass < OG_FALLBACK_PASSES; pass++) {
         if (!flag) flag = (unsigned char *)calloc((size_t)NP, 1);
         if (!flag) { free(bad); return 1; }
-        /* flags on the padded grid: a ghost cell carries the flag of its source cell */
-        for (int64_t z = -P.g[2]; z < P.n[2] + P.g[2]; z++)
-            for (int64_t y = -P.g[1]; y < P.n[1] + P.g[1]; y++)
-                for (int64_t x = -P.g[0]; x < P.n[0] + P.g[0]; x++) {
-                    int64_t c[3] = {x, y, z}, s[3];
-                    int mir;
-                    for (int d = 0; d < 3; d++)
-                        s[d] = ghost_src(c[d], P.n[d], Gr->bc[2 * d], Gr->bc[2 * d + 1], &mir);
-                    flag[pidx(&P, x, y, z)] = bad[(s[2] * P.n[1] + s[1]) * P.n[0] + s[0]];
-                }
+        padded_flags(Gr, bad, flag);
         if (step_pass(Gr, U, phi, dt, flag, Unew)) { free(flag); free(bad); return 1; }
         nbad = 0;
         for (int64_t c = 0; c < N; c++) {

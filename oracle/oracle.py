@@ -80,6 +80,9 @@ def _load():
             lib.og_eigenvalues_x.argtypes = [dp, dp]
             lib.og_prim_to_cons_arr.argtypes = [dp, dp, C.c_int64]
             lib.og_cons_to_prim_arr.argtypes = [dp, dp, C.c_int64]
+            lib.og_step_pass.argtypes = [gp, dp, dp, C.c_double, C.c_void_p, dp]
+            lib.og_step_pass.restype = C.c_int
+            lib.og_realizable_cells.argtypes = [gp, dp, C.c_void_p]
             lib.og_num_threads.restype = C.c_int
             lib.og_set_num_threads.argtypes = [C.c_int]
             _lib = lib
@@ -196,6 +199,32 @@ def run(grid: Grid, U, t_end, max_steps=1 << 62, dt_max=float("inf"), phi=None, 
                         float(t_end), int(max_steps), float(dt_max),
                         _p(hist) if record else None, C.byref(ns), C.byref(tt))
     return U, ns.value, tt.value, rc, (hist[: ns.value].copy() if record else None)
+
+
+def step_pass(grid: Grid, U, dt, tagged=None, phi=None):
+    """One pass of the characteristic step (``og_step_pass``): second order without
+    ``tagged``; with ``tagged`` (bool per cell) first-order faces at every tagged cell."""
+    U = _f64(U).reshape(grid.shape)
+    out = np.empty_like(U)
+    ph = None if phi is None else _f64(phi).reshape(grid.phi_shape())
+    tg = None
+    if tagged is not None:
+        tg = np.ascontiguousarray(np.asarray(tagged, dtype=np.uint8).reshape(-1))
+        if tg.size != grid.ncells:
+            raise ValueError("tagged must have one entry per cell")
+    rc = _load().og_step_pass(C.byref(grid._g), _p(U), None if ph is None else _p(ph), float(dt),
+                              None if tg is None else tg.ctypes.data, _p(out))
+    if rc:
+        raise MemoryError("oracle step failed to allocate")
+    return out
+
+
+def realizable_cells(grid: Grid, U):
+    """Per cell: realizable (rho > 0, P positive definite)."""
+    U = _f64(U).reshape(grid.shape)
+    out = np.empty(grid.ncells, dtype=np.uint8)
+    _load().og_realizable_cells(C.byref(grid._g), _p(U), out.ctypes.data)
+    return out.astype(bool).reshape(grid.shape[1:])
 
 
 def run_schedule(grid: Grid, U, dts, phi=None):

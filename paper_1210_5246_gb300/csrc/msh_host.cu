@@ -153,6 +153,7 @@ static cudaError_t launch_characteristic(msh_grid *g, const StepArgs<T> &a, bool
 }
 
 msh_status launch_one_step(msh_grid *g, int ev_slot) {
+  g->phase_level = -1;  // a whole step closes a phased one that was left open
   int nb = 0;
   cudaError_t e;
   if (g->sg_G > 0.0) {  // the potential of U^n and the step's acceleration
@@ -435,6 +436,7 @@ msh_status msh_destroy(msh_grid *g) {
   if (g->flags) cudaFree(g->flags);
   if (g->hist) cudaFree(g->hist);
   if (g->ctrl_aux) cudaFree(g->ctrl_aux);
+  if (g->tag_count) cudaFree(g->tag_count);
   if (g->U1) cudaFree(g->U1);
   free_self_gravity(g);
   free_tape(g);
@@ -973,6 +975,136 @@ msh_status msh_step_dt(msh_grid *g, double dt, int32_t *tagged_cells) {
   if (tagged_cells) *tagged_cells = g->hctrl->last_tagged;
   if (g->hctrl->status == MSH_E_REALIZABILITY)
     return fail(MSH_E_REALIZABILITY, "step produced a non-realizable cell %lld", (long long)g->hctrl->first_bad);
+  return MSH_OK;
+}
+
+// ----------------------------------------- phased step: slabs sharing the fallback
+static msh_status phase_layers(msh_grid *g, int64_t start, int64_t count, size_t *c0, size_t *c1) {
+  size_t per = 0;
+  int64_t layers = 0;
+  layer_geometry(g, &per, &layers);
+  if (start < 0 || count < 0 || start + count > layers)
+    return fail(MSH_E_INVALID_ARG, "layers [%lld, %lld) outside [0, %lld)", (long long)start,
+                (long long)(start + count), (long long)layers);
+  *c0 = (size_t)start * per;
+  *c1 = (size_t)(start + count) * per;
+  return MSH_OK;
+}
+
+msh_status msh_step_begin(msh_grid *g, double dt) {
+  msh::NvtxRange nvtx_range("msh_step_begin");
+  begin();
+  if (!g) return fail(MSH_E_INVALID_ARG, "null grid");
+  if (!g->has_state) return fail(MSH_E_STATE, "msh_step_begin before msh_set_state");
+  if (!(dt > 0.0) || !std::isfinite(dt)) return fail(MSH_E_INVALID_ARG, "dt must be finite and > 0");
+  if (g->scheme == MSH_SCHEME_KT)
+    return fail(MSH_E_STATE, "the central scheme has no fallback passes: step it with msh_step_dt");
+  if (g->sg_G > 0.0) return fail(MSH_E_STATE, "a phased step does not take self-gravity");
+  msh_status st = ensure_partials(g, blocks_for(g, g->rows, g->zchunk));
+  if (st) return st;
+  cudaError_t e = launch_set_dt(g->ctrl, dt, g->stream);
+  int nb = 0;
+  if (e == cudaSuccess) {
+    if (g->prec == MSH_FP32) e = launch_characteristic(g, make_args<float>(g), false, &nb);
+    else e = launch_characteristic(g, make_args<double>(g), false, &nb);
+  }
+  if (e != cudaSuccess) return fail(MSH_E_CUDA, "step begin: %s", cudaGetErrorString(e));
+  g->phase_level = 0;
+  g->phase_nb = nb;
+  return MSH_OK;
+}
+
+msh_status msh_step_retry(msh_grid *g, int32_t level) {
+  msh::NvtxRange nvtx_range("msh_step_retry");
+  begin();
+  if (!g) return fail(MSH_E_INVALID_ARG, "null grid");
+  if (g->phase_level < 0) return fail(MSH_E_STATE, "msh_step_retry outside msh_step_begin .. msh_step_end");
+  if (level != g->phase_level + 1 || level > kFallbackPasses)
+    return fail(MSH_E_INVALID_ARG, "fallback pass %d after pass %d (passes run in order 1 .. %d)", level,
+                g->phase_level, kFallbackPasses);
+  cudaError_t e = launch_force_pass(g->ctrl, level, g->stream);
+  if (e == cudaSuccess) {
+    if (g->prec == MSH_FP32) {
+      StepArgs<float> a = make_args<float>(g);
+      a.level = level;
+      e = launch_characteristic(g, a, true, nullptr);
+    } else {
+      StepArgs<double> a = make_args<double>(g);
+      a.level = level;
+      e = launch_characteristic(g, a, true, nullptr);
+    }
+  }
+  if (e != cudaSuccess) return fail(MSH_E_CUDA, "fallback pass: %s", cudaGetErrorString(e));
+  g->phase_level = level;
+  return MSH_OK;
+}
+
+msh_status msh_step_end(msh_grid *g, int32_t *tagged_cells) {
+  msh::NvtxRange nvtx_range("msh_step_end");
+  begin();
+  if (!g) return fail(MSH_E_INVALID_ARG, "null grid");
+  if (g->phase_level < 0) return fail(MSH_E_STATE, "msh_step_end without msh_step_begin");
+  g->phase_level = -1;
+  cudaError_t e = launch_finalize(g->ctrl, g->part, g->phase_nb, 0, g->stream);
+  if (e != cudaSuccess) return fail(MSH_E_CUDA, "finalize launch: %s", cudaGetErrorString(e));
+  msh_status st = read_ctrl(g);
+  if (st) return st;
+  g->dt_stale = false;
+  if (tagged_cells) *tagged_cells = g->hctrl->last_tagged;
+  if (g->hctrl->status == MSH_E_REALIZABILITY)
+    return fail(MSH_E_REALIZABILITY, "step produced a non-realizable cell %lld", (long long)g->hctrl->first_bad);
+  return MSH_OK;
+}
+
+static msh_status copy_tags(msh_grid *g, int64_t start, int64_t count, int32_t *levels, int32_t where,
+                            bool to_grid) {
+  if (!g || (!levels && count > 0)) return fail(MSH_E_INVALID_ARG, "null argument");
+  if (where != MSH_HOST && where != MSH_DEVICE) return fail(MSH_E_INVALID_ARG, "bad where");
+  if (!g->has_state) return fail(MSH_E_STATE, "no state set");
+  size_t c0 = 0, c1 = 0;
+  msh_status st = phase_layers(g, start, count, &c0, &c1);
+  if (st || c1 == c0) return st;
+  const size_t bytes = (c1 - c0) * sizeof(int32_t);
+  int32_t *buf = levels;
+  if (where == MSH_HOST) CUDA_TRY(cudaMallocAsync(&buf, bytes, g->stream));
+  cudaError_t e = cudaSuccess;
+  if (to_grid && where == MSH_HOST) e = cudaMemcpyAsync(buf, levels, bytes, cudaMemcpyHostToDevice, g->stream);
+  if (e == cudaSuccess) e = launch_tags(g->ctrl, g->flags, c0, c1, buf, to_grid, g->stream);
+  if (e == cudaSuccess && !to_grid && where == MSH_HOST)
+    e = cudaMemcpyAsync(levels, buf, bytes, cudaMemcpyDeviceToHost, g->stream);
+  if (where == MSH_HOST) cudaFreeAsync(buf, g->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);
+  if (e != cudaSuccess) return fail(MSH_E_CUDA, "fallback tags: %s", cudaGetErrorString(e));
+  return MSH_OK;
+}
+
+msh_status msh_get_tags(msh_grid *g, int64_t start, int64_t count, int32_t *levels, int32_t where) {
+  begin();
+  return copy_tags(g, start, count, levels, where, false);
+}
+
+msh_status msh_set_tags(msh_grid *g, int64_t start, int64_t count, const int32_t *levels, int32_t where) {
+  begin();
+  return copy_tags(g, start, count, const_cast<int32_t *>(levels), where, true);
+}
+
+msh_status msh_count_tags(msh_grid *g, int64_t start, int64_t count, int32_t level, int64_t *n) {
+  begin();
+  if (!g || !n) return fail(MSH_E_INVALID_ARG, "null argument");
+  if (level < 0 || level > kFallbackPasses) return fail(MSH_E_INVALID_ARG, "level must be in [0, %d]", kFallbackPasses);
+  if (!g->has_state) return fail(MSH_E_STATE, "no state set");
+  size_t c0 = 0, c1 = 0;
+  msh_status st = phase_layers(g, start, count, &c0, &c1);
+  if (st) return st;
+  *n = 0;
+  if (c1 == c0) return MSH_OK;
+  if (!g->tag_count) CUDA_TRY(cudaMalloc(&g->tag_count, sizeof(unsigned long long)));
+  unsigned long long h = 0;
+  cudaError_t e = launch_count_tags(g->ctrl, g->flags, c0, c1, level, g->tag_count, g->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&h, g->tag_count, sizeof h, cudaMemcpyDeviceToHost, g->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);
+  if (e != cudaSuccess) return fail(MSH_E_CUDA, "count tags: %s", cudaGetErrorString(e));
+  *n = (int64_t)h;
   return MSH_OK;
 }
 

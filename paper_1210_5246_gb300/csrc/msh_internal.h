@@ -29,7 +29,9 @@ constexpr int kFallbackPasses = 4;
 struct Ctrl {
   double t, t_next, t_end, dt, dt_max, dt_cfl, cfl, dt_last;
   int64_t step, max_step, first_bad, hist_cap, hist_base;
-  int32_t done, status, realizable, pad;
+  int32_t done, status, realizable;
+  int32_t force;  // bit p: fallback pass p runs even if no cell of this grid was newly tagged
+                  // by pass p - 1 (slabs that share the fallback of one grid); reset per step
   int32_t nbad[kFallbackPasses + 1];  // cells newly tagged by pass p of this step (p = 0: the step)
   double totals[10];
   double *hist;
@@ -104,6 +106,12 @@ template <typename T> cudaError_t launch_scan(const T *U, size_t N, int nx, int 
                                               cudaStream_t s, size_t c0 = 0, size_t c1 = 0,
                                               bool maxf = false);
 cudaError_t launch_set_dt(Ctrl *ctrl, double dt, cudaStream_t s);
+// phased steps of slabs that share the a-posteriori fallback (msh_step_begin / _retry / _end)
+cudaError_t launch_force_pass(Ctrl *ctrl, int level, cudaStream_t s);
+cudaError_t launch_tags(Ctrl *ctrl, int32_t *flags, size_t c0, size_t c1, int32_t *levels, bool to_grid,
+                        cudaStream_t s);
+cudaError_t launch_count_tags(const Ctrl *ctrl, const int32_t *flags, size_t c0, size_t c1, int level,
+                              unsigned long long *count, cudaStream_t s);
 cudaError_t launch_finalize(Ctrl *ctrl, const Partial *part, int nparts, int mode, cudaStream_t s);
 cudaError_t launch_run_start(Ctrl *ctrl, double t_end, int64_t max_steps, double dt_max, cudaStream_t s);
 cudaError_t launch_ensemble_start(Ctrl *ctrl, int64_t step_base, int64_t nsteps, int32_t *status, cudaStream_t s);
@@ -173,6 +181,11 @@ struct msh_grid {
   void **sg_bufs = nullptr;
   msh::Ctrl *ctrl_aux = nullptr;
   bool has_state = false;
+  // phased step (msh_step_begin .. msh_step_end): the pass that ran last (-1: no step open)
+  // and the number of partials the step kernel wrote
+  int phase_level = -1;
+  int phase_nb = 0;
+  unsigned long long *tag_count = nullptr;  // device counter of msh_count_tags
   int rows = 8, zchunk = 32;
   cudaGraphExec_t graph = nullptr;
   // profiling: eager launches with events around every step-kernel launch

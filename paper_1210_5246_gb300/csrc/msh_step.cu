@@ -116,6 +116,7 @@ __global__ void __launch_bounds__(kFinalizeThreads) finalize_kernel(Ctrl *ctrl, 
     c->tape_had[ti] = c->nbad[0] > 0;
   }
   for (int p = 0; p <= kFallbackPasses; p++) c->nbad[p] = 0;
+  c->force = 0;
   const int64_t hi_ = c->step - c->hist_base;
   if (c->hist != nullptr && hi_ >= 0 && hi_ < c->hist_cap) c->hist[hi_] = c->dt;
   c->dt_last = c->dt;
@@ -136,9 +137,64 @@ __global__ void set_dt_kernel(Ctrl *c, double dt) {
   c->dt_max = INFINITY;
   c->done = 0;
   c->status = 0;
+  c->force = 0;
   for (int p = 0; p <= kFallbackPasses; p++) c->nbad[p] = 0;
   c->dt = dt;
   c->t_next = c->t + dt;
+}
+
+// A fallback pass that must run even where this grid tagged nothing in the pass before.
+__global__ void force_pass_kernel(Ctrl *c, int level) { c->force |= 1 << level; }
+
+// Per cell of [c0, c1): the fallback pass of the current step that tagged it, or -1
+// (tags are 8 * (step tag) + pass; a tag of another step is no tag).
+__global__ void get_tags_kernel(const Ctrl *ctrl, const int32_t *flags, size_t c0, size_t c1, int32_t *levels) {
+  const int32_t tag = (int32_t)(ctrl->step & 0x0fffffff) + 1;
+  for (size_t c = c0 + (size_t)blockIdx.x * blockDim.x + threadIdx.x; c < c1; c += (size_t)gridDim.x * blockDim.x) {
+    const int32_t f = flags[c];
+    levels[c - c0] = (f >> 3) == tag ? (f & 7) : -1;
+  }
+}
+
+__global__ void set_tags_kernel(const Ctrl *ctrl, int32_t *flags, size_t c0, size_t c1, const int32_t *levels) {
+  const int32_t tag = (int32_t)(ctrl->step & 0x0fffffff) + 1;
+  for (size_t c = c0 + (size_t)blockIdx.x * blockDim.x + threadIdx.x; c < c1; c += (size_t)gridDim.x * blockDim.x) {
+    const int32_t l = levels[c - c0];
+    flags[c] = l >= 0 ? tag * 8 + l : 0;
+  }
+}
+
+// Cells of [c0, c1) tagged by pass `level` of the current step.
+__global__ void count_tags_kernel(const Ctrl *ctrl, const int32_t *flags, size_t c0, size_t c1, int level,
+                                  unsigned long long *count) {
+  const int32_t want = ((int32_t)(ctrl->step & 0x0fffffff) + 1) * 8 + level;
+  unsigned long long n = 0;
+  for (size_t c = c0 + (size_t)blockIdx.x * blockDim.x + threadIdx.x; c < c1; c += (size_t)gridDim.x * blockDim.x)
+    n += flags[c] == want;
+  for (int o = 16; o > 0; o >>= 1) n += __shfl_down_sync(0xffffffffu, n, o);
+  if ((threadIdx.x & 31) == 0 && n) atomicAdd(count, n);
+}
+
+cudaError_t launch_force_pass(Ctrl *ctrl, int level, cudaStream_t s) {
+  force_pass_kernel<<<1, 1, 0, s>>>(ctrl, level);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_tags(Ctrl *ctrl, int32_t *flags, size_t c0, size_t c1, int32_t *levels, bool to_grid,
+                        cudaStream_t s) {
+  const int blocks = (int)std::min<size_t>((c1 - c0 + 255) / 256 + 1, (size_t)kScanBlocks);
+  if (to_grid) set_tags_kernel<<<blocks, 256, 0, s>>>(ctrl, flags, c0, c1, levels);
+  else get_tags_kernel<<<blocks, 256, 0, s>>>(ctrl, flags, c0, c1, levels);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_count_tags(const Ctrl *ctrl, const int32_t *flags, size_t c0, size_t c1, int level,
+                              unsigned long long *count, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(count, 0, sizeof(unsigned long long), s);
+  if (e != cudaSuccess) return e;
+  const int blocks = (int)std::min<size_t>((c1 - c0 + 255) / 256 + 1, (size_t)kScanBlocks);
+  count_tags_kernel<<<blocks, 256, 0, s>>>(ctrl, flags, c0, c1, level, count);
+  return cudaGetLastError();
 }
 
 __global__ void run_start_kernel(Ctrl *c, double t_end, int64_t max_steps, double dt_max) {
@@ -147,6 +203,7 @@ __global__ void run_start_kernel(Ctrl *c, double t_end, int64_t max_steps, doubl
   c->dt_max = dt_max;
   c->done = 0;
   c->status = 0;
+  c->force = 0;
   for (int p = 0; p <= kFallbackPasses; p++) c->nbad[p] = 0;
   plan(c);
 }

@@ -178,7 +178,7 @@ __global__ void __launch_bounds__(kTile1D) step1d_kernel(StepArgs<T> a) {
   constexpr int B = kTile1D, SXX = B + 2;
   const Ctrl *ctrl = a.ctrl;
   if (ctrl->done) return;
-  if (RETRY && ctrl->nbad[a.level - 1] == 0) return;
+  if (RETRY && ctrl->nbad[a.level - 1] == 0 && !((ctrl->force >> a.level) & 1)) return;
   const int64_t step = ctrl->step;
   const int32_t tag = (int32_t)(step & 0x0fffffff) + 1;
   __shared__ unsigned char sFl[RETRY ? SXX : 1];
@@ -292,7 +292,7 @@ __global__ void __launch_bounds__(32 * BY, (BY <= 8 && !CTU ? 2 : 1)) step_tile_
   constexpr int RAW = kRawPlanes<T, BY, CTU>;  // raw staging slots (4: U^n of the update from shared memory)
   const Ctrl *ctrl = a.ctrl;
   if (ctrl->done) return;
-  if (RETRY && ctrl->nbad[a.level - 1] == 0) return;
+  if (RETRY && ctrl->nbad[a.level - 1] == 0 && !((ctrl->force >> a.level) & 1)) return;
   const int64_t step = ctrl->step;
   const int32_t tag = (int32_t)(step & 0x0fffffff) + 1;
   // fallback tags of the staged cells (fallback pass only)
@@ -657,7 +657,7 @@ __global__ void __launch_bounds__(32 * WARPS) step_strip2d_kernel(StepArgs<T> a)
   __shared__ T sTy[CTU ? WARPS : 1][NV][32];  // CTU: T_y of the lane's cell in the row of the x sweep
   const Ctrl *ctrl = a.ctrl;
   if (ctrl->done) return;
-  if (RETRY && ctrl->nbad[a.level - 1] == 0) return;
+  if (RETRY && ctrl->nbad[a.level - 1] == 0 && !((ctrl->force >> a.level) & 1)) return;
   const int64_t step = ctrl->step;
   const int32_t tag = (int32_t)(step & 0x0fffffff) + 1;
   // sweep source, destination and U^n (the second Runge-Kutta stage sweeps U1)

@@ -12,16 +12,30 @@ batched tubes) shards with no collective (see ``replicas``).
 A rank's local grid holds its owned layers plus the halo layers on every side that has a
 neighbour (both sides when the axis is periodic; none at a non-periodic end of the global
 grid, which keeps the global boundary condition).  A halo side's own boundary condition is
-a placeholder: the cells it affects are halo cells, overwritten by the next exchange.  The
-a-posteriori fallback couples cells within a step, so a step in which any slab tags cells
-raises ``FallbackAcrossSlabs`` (the result might differ from the single-grid step).
+a placeholder: the cells it affects are halo cells, overwritten by the next exchange.
+
+The a-posteriori fallback couples cells within a step: a cell whose second-order update is
+not realizable is tagged, and the step is recomputed with first-order states on every face
+of every tagged cell, up to four passes.  A face's states depend on the tags of the two
+cells it joins, so before each pass every slab receives its neighbours' tags in its halo
+layers (the guardcell exchange of Sec. 3.1, applied to the tags), and a pass runs on every
+slab when any slab's owned cells were newly tagged by the pass before (a sum over the
+slabs).  With that the slabs reproduce the single grid bit for bit in every step.
 
 A stepper is any object with
     layers()                 -> number of local layers
     get(start, count)        -> array [10, count * cells per layer] (conserved)
     set(start, count, buf)
     reduce(start, count)     -> (totals[10], cfl dt, realizable) of those layers
-    step(dt)                 -> cells the fallback tagged
+    step(dt)                 -> cells the fallback tagged (a whole step, fallback inside)
+and, for the shared fallback (``phased`` true):
+    begin(dt)                the second-order pass (its failing cells are tagged by pass 0)
+    retry(level)             fallback pass `level` with the tags of the passes before
+    end()                    finishes the step
+    count_tags(start, count, level), get_tags(start, count), set_tags(start, count, levels)
+                             the tags of layers, one int per cell: the pass that tagged it, or -1.
+A stepper without ``phased`` (the central scheme, which has no fallback) takes whole steps,
+and a step in which it tags cells raises ``FallbackAcrossSlabs``.
 ``GridStepper`` wraps a libmsh grid.
 """
 from __future__ import annotations
@@ -32,6 +46,7 @@ from dataclasses import dataclass
 import numpy as np
 
 HALO = 2  # stencil radius of the MUSCL-Hancock step
+FALLBACK_PASSES = 4  # a-posteriori fallback passes per step (the library's rule)
 
 
 def halo_width(scheme=0):
@@ -221,8 +236,9 @@ class SlabDriver:
     def _tag(dst, side):
         return 2 * dst + side
 
-    def exchange(self):
-        """Copy the halo's width of owned layers to each neighbour's halo.  Messages to other processes
+    def exchange(self, tags=False):
+        """Copy the halo's width of owned layers to each neighbour's halo: the conserved state,
+        or with ``tags`` the fallback tags of the current step.  Messages to other processes
         go out in a fixed order (to the lower neighbour, then to the upper one) and are
         received in the matching order (from the upper neighbour, then the lower one)."""
         S = self.slabs
@@ -230,14 +246,15 @@ class SlabDriver:
         sends, recvs, local = [], [], []
         for r, st in self.steppers.items():
             sl = S[r]
+            get = st.get_tags if tags else st.get
             if sl.lower is not None:  # my lowest owned layers -> the lower neighbour's upper halo
-                arr = st.get(sl.lo_halo, h)
+                arr = get(sl.lo_halo, h)
                 if sl.lower in self.steppers:
                     local.append((sl.lower, 1, arr))
                 else:
                     sends.append((sl.lower, self._tag(sl.lower, 1), arr))
             if sl.upper is not None:  # my highest owned layers -> the upper neighbour's lower halo
-                arr = st.get(sl.lo_halo + sl.count - h, h)
+                arr = get(sl.lo_halo + sl.count - h, h)
                 if sl.upper in self.steppers:
                     local.append((sl.upper, 0, arr))
                 else:
@@ -250,12 +267,15 @@ class SlabDriver:
         if recvs:
             shape, dtype = sends[0][2].shape, sends[0][2].dtype  # every layer block has one size
             got = self.comm.exchange(sends, [(peer, self._tag(r, side), shape, dtype) for peer, r, side in recvs])
+        def put(r, start, arr):
+            st = self.steppers[r]
+            (st.set_tags if tags else st.set)(start, h, arr)
         for dst, side, arr in local:
             sl = S[dst]
-            self.steppers[dst].set(0 if side == 0 else sl.lo_halo + sl.count, h, arr)
+            put(dst, 0 if side == 0 else sl.lo_halo + sl.count, arr)
         for peer, r, side in recvs:
             sl = S[r]
-            self.steppers[r].set(0 if side == 0 else sl.lo_halo + sl.count, h, got[self._tag(r, side)])
+            put(r, 0 if side == 0 else sl.lo_halo + sl.count, got[self._tag(r, side)])
 
     def reduce(self):
         """(totals, cfl dt, realizable) over the whole grid."""
@@ -279,15 +299,41 @@ class SlabDriver:
         dt = min(dt, dt_max)
         if self.t + dt >= t_end:
             dt = t_end - self.t
-        tagged = 0
-        for st in self.steppers.values():
-            tagged += st.step(dt)
-        tagged = int(self.comm.sum(np.array([float(tagged)]))[0])
-        if tagged:
-            raise FallbackAcrossSlabs(f"step {self.steps}: the a-posteriori fallback tagged {tagged} cells")
+        if all(getattr(st, "phased", False) for st in self.steppers.values()):
+            self._phased_step(dt)
+        else:
+            tagged = 0
+            for st in self.steppers.values():
+                tagged += st.step(dt)
+            tagged = int(self.comm.sum(np.array([float(tagged)]))[0])
+            if tagged:
+                raise FallbackAcrossSlabs(f"step {self.steps}: the a-posteriori fallback tagged {tagged} cells")
         self.t += dt
         self.steps += 1
         return dt
+
+    def owned_tags(self, level):
+        """Cells of every slab's owned layers tagged by pass `level` of this step (all ranks)."""
+        n = 0
+        for r, st in self.steppers.items():
+            sl = self.slabs[r]
+            n += st.count_tags(sl.lo_halo, sl.count, level)
+        return int(self.comm.sum(np.array([float(n)]))[0])
+
+    def _phased_step(self, dt):
+        """One step with the a-posteriori fallback shared by the slabs: pass p runs on every
+        slab, after the tags of the passes before it have reached the neighbours' halos,
+        whenever some slab's owned cells were newly tagged by pass p - 1."""
+        for st in self.steppers.values():
+            st.begin(dt)
+        for level in range(1, FALLBACK_PASSES + 1):
+            if self.owned_tags(level - 1) == 0:
+                break
+            self.exchange(tags=True)
+            for st in self.steppers.values():
+                st.retry(level)
+        for st in self.steppers.values():
+            st.end()
 
     def run(self, max_steps, t_end=math.inf):
         for _ in range(max_steps):
@@ -297,10 +343,12 @@ class SlabDriver:
 
 
 class GridStepper:
-    """A libmsh grid as a slab stepper (host buffers for the halo copies)."""
+    """A libmsh grid as a slab stepper (host buffers for the halo copies).  The
+    characteristic schemes share the fallback (``phased``); the central scheme has none."""
 
-    def __init__(self, grid):
+    def __init__(self, grid, scheme=0):
         self.g = grid
+        self.phased = scheme != 1
 
     def layers(self):
         return self.g.layer_shape()[0]
@@ -316,6 +364,24 @@ class GridStepper:
 
     def step(self, dt):
         return self.g.step_dt(dt)
+
+    def begin(self, dt):
+        self.g.step_begin(dt)
+
+    def retry(self, level):
+        self.g.step_retry(level)
+
+    def end(self):
+        return self.g.step_end()
+
+    def count_tags(self, start, count, level):
+        return self.g.count_tags(start, count, level)
+
+    def get_tags(self, start, count):
+        return self.g.get_tags(start, count)
+
+    def set_tags(self, start, count, levels):
+        self.g.set_tags(start, count, levels)
 
 
 def make_grid_steppers(msh, n, lo, hi, bc, cfl, precision, U, slabs: Slabs, ranks, phi=None, stream=None,
@@ -339,5 +405,5 @@ def make_grid_steppers(msh, n, lo, hi, bc, cfl, precision, U, slabs: Slabs, rank
         if phi is not None:
             g.set_potential(local_potential(phi, n, sl, periodic))
         g.set_state(parts[r].astype(g.dtype), msh.CONSERVED)
-        out[r] = GridStepper(g)
+        out[r] = GridStepper(g, scheme)
     return out

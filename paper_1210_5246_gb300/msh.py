@@ -81,6 +81,12 @@ SIGNATURES = {
     "msh_batch_info": [_vp, _P(_i64), _P(_dbl), _P(_i64)],
     "msh_batch_fallback_steps": [_vp, _P(_i64)],
     "msh_batch_destroy": [_vp],
+    "msh_step_begin": [_vp, _dbl],
+    "msh_step_retry": [_vp, _i32],
+    "msh_step_end": [_vp, _P(_i32)],
+    "msh_get_tags": [_vp, _i64, _i64, _vp, _i32],
+    "msh_set_tags": [_vp, _i64, _i64, _vp, _i32],
+    "msh_count_tags": [_vp, _i64, _i64, _i32, _P(_i64)],
     "msh_step_noalloc": [_i32, _P(_i64), _P(_dbl), _P(_dbl), _P(_i32), _i32, _dbl, _dbl, _vp, _vp, _vp, _P(_dbl)],
 }
 
@@ -412,6 +418,38 @@ class Grid:
         tagged = C.c_int32(0)
         _check(load().msh_step_dt(self.h, float(dt), C.byref(tagged)))
         return tagged.value
+
+    # -- phased step (slabs sharing the a-posteriori fallback; see msh_step_begin) ----
+    def step_begin(self, dt):
+        _check(load().msh_step_begin(self.h, float(dt)))
+
+    def step_retry(self, level):
+        _check(load().msh_step_retry(self.h, int(level)))
+
+    def step_end(self):
+        """Finishes the phased step; returns the cells this grid's pass 0 tagged."""
+        tagged = C.c_int32(0)
+        _check(load().msh_step_end(self.h, C.byref(tagged)))
+        return tagged.value
+
+    def get_tags(self, start, count):
+        """Per cell of layers [start, start + count): the pass of this step that tagged it, or -1."""
+        per = int(np.prod(self.layer_shape()[1:]))
+        out = np.empty(count * per, dtype=np.int32)
+        _check(load().msh_get_tags(self.h, int(start), int(count), out.ctypes.data_as(C.c_void_p), HOST))
+        return out
+
+    def set_tags(self, start, count, levels):
+        lv = np.ascontiguousarray(levels, dtype=np.int32).reshape(-1)
+        per = int(np.prod(self.layer_shape()[1:]))
+        if lv.size != count * per:
+            raise ValueError("levels must have one entry per cell of the layers")
+        _check(load().msh_set_tags(self.h, int(start), int(count), lv.ctypes.data_as(C.c_void_p), HOST))
+
+    def count_tags(self, start, count, level):
+        n = C.c_int64(0)
+        _check(load().msh_count_tags(self.h, int(start), int(count), int(level), C.byref(n)))
+        return n.value
 
     def set_tape(self, K, max_steps):
         """Record checkpoints every K steps, dts and fallback flags of the next max_steps

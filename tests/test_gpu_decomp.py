@@ -143,3 +143,87 @@ def test_ctu_slabs_equal_single_grid(env, name, world, cfl, prec):
     np.testing.assert_array_equal(got, ref)
     for s in st.values():
         s.g.close()
+
+
+def _extreme_2d():
+    """The extreme 2D periodic case of the CPU decomposition tests (density contrasts up to
+    2000, velocity jumps up to 6, CFL 0.9): the fallback tags cells next to every slab
+    boundary."""
+    from tests.test_decomp import _extreme_2d as mk
+    return mk()
+
+
+@pytest.mark.parametrize("world", [2, 3, 4])
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_fallback_across_slabs_equals_single_grid(env, world, prec):
+    """libmsh slabs sharing the a-posteriori fallback (msh_step_begin / msh_get_tags /
+    msh_set_tags / msh_count_tags / msh_step_retry / msh_step_end): bit for bit the single
+    grid's msh_step_dt run, with tags on both sides of every slab boundary; FP64 also
+    against the oracle."""
+    msh, I = env
+    precision = msh.FP64 if prec == "fp64" else msh.FP32
+    W = _extreme_2d()
+    W = W.astype(np.float32) if precision == msh.FP32 else W
+    n, lo, hi, bc, cfl, steps = (14, 24), (0.0, 0.0), (1.0, 1.0), ((0, 0), (0, 0)), 0.9, 3
+    g = msh.Grid(n, lo, hi, bc, cfl, precision)
+    g.set_state(W, msh.PRIMITIVE)
+    U0 = g.get_state()
+    g.run(max_steps=steps)
+    ref, (t_ref, _) = g.get_state(), g.time()
+    g.close()
+    S = decomp.Slabs(n[-1], world, True)
+    st = decomp.make_grid_steppers(msh, n, lo, hi, bc, cfl, precision, U0, S, range(world))
+    drv = decomp.SlabDriver(S, st)
+    ns, t = drv.run(steps)
+    got = decomp.join_owned([st[r].g.get_state() for r in range(world)], n, S)
+    assert ns == steps and t == t_ref
+    np.testing.assert_array_equal(got, ref)
+    if precision == msh.FP64:
+        from oracle import oracle
+        from tests.parity import assert_fp64
+        og = oracle.Grid(n, lo, hi, bc, cfl)
+        Uo, so, to, rc, _ = oracle.run(og, oracle.prim_to_cons(W), np.inf, max_steps=steps)
+        assert rc == 0
+        assert_fp64(got, Uo, what=f"fallback across {world} slabs")
+    for r in range(world):
+        st[r].g.close()
+
+
+def test_phased_step_equals_step_dt_and_tags_round_trip(env):
+    """On one grid, msh_step_begin + the passes msh_step_dt would run + msh_step_end give the
+    msh_step_dt result bit for bit; msh_get_tags / msh_set_tags / msh_count_tags agree with
+    one another; retry out of order and end without begin are refused."""
+    msh, I = env
+    W = _extreme_2d()
+    n, lo, hi, bc, cfl = (14, 24), (0.0, 0.0), (1.0, 1.0), ((0, 0), (0, 0)), 0.9
+    a = msh.Grid(n, lo, hi, bc, cfl, msh.FP64)
+    a.set_state(W, msh.PRIMITIVE)
+    dt = a.step()  # the CFL step: the reference
+    b = msh.Grid(n, lo, hi, bc, cfl, msh.FP64)
+    b.set_state(W, msh.PRIMITIVE)
+    b.step_begin(dt)
+    levels = b.get_tags(0, n[1])
+    assert (levels == 0).sum() == b.count_tags(0, n[1], 0) > 0 and set(np.unique(levels)) <= {-1, 0}
+    lvl = 1
+    while lvl <= 4 and b.count_tags(0, n[1], lvl - 1) > 0:
+        b.step_retry(lvl)
+        lvl += 1
+    with pytest.raises(msh.MshError):
+        b.step_retry(lvl + 1)
+    b.step_end()
+    np.testing.assert_array_equal(b.get_state(), a.get_state())
+    assert b.time() == a.time()
+    with pytest.raises(msh.MshError) as ei:
+        b.step_end()
+    assert ei.value.status == msh.MSH_E_STATE
+    # tags written by msh_set_tags are read back (the current step's tag of each cell)
+    b.step_begin(dt)
+    rng = np.random.default_rng(1)
+    lv = rng.integers(-1, 3, n[0] * 5).astype(np.int32)
+    b.set_tags(3, 5, lv)
+    np.testing.assert_array_equal(b.get_tags(3, 5), lv)
+    assert b.count_tags(3, 5, 2) == int((lv == 2).sum())
+    b.step_end()
+    a.close()
+    b.close()
+

@@ -53,30 +53,52 @@ def test_disc_gradient_fp64_matches_central_fd(mods, oracle):
     D.close()
 
 
+def _smooth_direction(n, seed):
+    """A seeded smooth random field on the n x n grid: six low Fourier modes with random
+    wave numbers (1..4 per axis), amplitudes and phases, scaled by 0.01."""
+    rng = np.random.default_rng(seed)
+    X = np.arange(n)[None, :] / n
+    Y = np.arange(n)[:, None] / n
+    v = np.zeros((n, n))
+    for _ in range(6):
+        kx, ky = rng.integers(1, 5, 2)
+        v += rng.normal() * np.cos(2 * np.pi * (kx * X + ky * Y) + rng.uniform(0, 2 * np.pi))
+    return 0.01 * v
+
+
 def test_disc_gradient_full_size_fp64_matches_central_fd(mods, oracle):
-    """The configured workload itself: 512^2 disc, 2000 steps, checkpoints every K = 50 (40
-    recomputed segments), FP64 through BMERun / msh_adjoint_tape, against central finite
-    differences of the FP64 oracle replaying the forward run's dt schedule: dL/dbeta and
-    dL/ddelta along one seeded random direction, each to 1e-3 relative over the whole
-    2000-step horizon (each oracle run takes ~1 min on 16 host cores; four runs)."""
+    """The configured workload itself, 512^2 disc with checkpoints every K = 50, FP64 through
+    BMERun / msh_adjoint_tape, against central finite differences of the FP64 oracle replaying
+    the forward run's dt schedule:
+    * all 2000 steps (40 recomputed checkpoint segments): dL/ddelta along a seeded smooth
+      random direction, 1e-4 relative (h = 1e-7; measured agreement ~1e-6);
+    * dL/dbeta over the first 200 steps (4 segments), 5e-4 relative (h = 1e-8).  Over 2000
+      steps no step size resolves dL/dbeta to 1e-3 by finite differences: above h ~ 3e-9 the
+      difference crosses limiter switches of the growing spiral pattern (0.24 % off at
+      h = 1e-8, 1.7 % at 1e-7, 14 % at 1e-6), below it rounding differences amplified by the
+      unstable disc dominate (5 % at 1e-9); at 200 steps h = 1e-8 agrees to ~3e-5."""
     disc, msh = mods
-    D = disc.DiscProblem(n=512, nsteps=2000, precision=msh.FP64, K=50)
     beta = 0.05
-    L0, gd, gb = D.value_and_grad(beta=beta)
+    D = disc.DiscProblem(n=512, nsteps=2000, precision=msh.FP64, K=50)
+    L0, gd, _ = D.value_and_grad(beta=beta)
     dts = D.grid.dt_history()
     delta0 = D.delta0.cpu().numpy()
     gd = gd.cpu().numpy()
     D.close()
     assert 0 < L0 < 1 and len(dts) == 2000
-    h = 1e-6
-    fd_b = (_oracle_loss(oracle, D, delta0, beta + h, dts) - _oracle_loss(oracle, D, delta0, beta - h, dts)) / (2 * h)
-    assert abs(fd_b - gb) <= 1e-3 * abs(fd_b), (fd_b, gb)
-    v = np.random.default_rng(7).normal(size=delta0.shape) * 0.01
-    h = 1e-5
+    v = _smooth_direction(512, 7)
+    h = 1e-7
     fd_d = (_oracle_loss(oracle, D, delta0 + h * v, beta, dts)
             - _oracle_loss(oracle, D, delta0 - h * v, beta, dts)) / (2 * h)
     ad_d = float((gd * v).sum())
-    assert abs(fd_d - ad_d) <= 1e-3 * abs(fd_d), (fd_d, ad_d)
+    assert abs(fd_d - ad_d) <= 1e-4 * abs(fd_d), (fd_d, ad_d)
+    D = disc.DiscProblem(n=512, nsteps=200, precision=msh.FP64, K=50)
+    L0, _, gb = D.value_and_grad(beta=beta)
+    dts = D.grid.dt_history()
+    D.close()
+    h = 1e-8
+    fd_b = (_oracle_loss(oracle, D, delta0, beta + h, dts) - _oracle_loss(oracle, D, delta0, beta - h, dts)) / (2 * h)
+    assert abs(fd_b - gb) <= 5e-4 * abs(fd_b), (fd_b, gb)
 
 
 def _beta_terms_magnitude(disc, D):

@@ -448,6 +448,30 @@ def test_fallback_restores_realizability_and_matches_bruteforce(oracle, seed):
     assert np.max(np.abs(A - B) / scale) < 1e-11
 
 
+@pytest.mark.parametrize("seed", [1, 13, 31])
+def test_step_equals_its_passes_repeated(oracle, seed):
+    """og_step is og_step_pass repeated: the second-order pass, then passes with first-order
+    faces at every cell tagged so far, a cell being tagged when its update is not realizable,
+    at most four fallback passes.  Restated here pass by pass from the exported single pass
+    and realizability test (the form a driver uses to share the fallback between slabs):
+    bit for bit og_step, on states that take one or more fallback passes."""
+    W = _extreme_tiny(seed)
+    g = oracle.Grid((8,), (0,), (1,), ((0, 0),), 0.8)
+    U = oracle.prim_to_cons(W)
+    dt = oracle.cfl_dt(g, U)
+    Un = oracle.step_pass(g, U, dt)
+    tagged = ~oracle.realizable_cells(g, Un)
+    assert tagged.any()
+    new, passes = tagged.copy(), 0
+    while new.any() and passes < 4:
+        Un = oracle.step_pass(g, U, dt, tagged)
+        new = ~oracle.realizable_cells(g, Un) & ~tagged
+        tagged |= new
+        passes += 1
+    np.testing.assert_array_equal(Un, oracle.step(g, U, dt))
+    np.testing.assert_array_equal(oracle.step_pass(g, U, dt), oracle.step_second_order_only(g, U, dt))
+
+
 def test_fallback_inactive_on_smooth_data(oracle):
     """Where the second-order update is realizable the fallback changes nothing."""
     p = I.blast(n=24, nsteps=1)
