@@ -5,12 +5,11 @@
 // fallback, HLL branch and min/max of the signal speeds, a-posteriori fallback tags):
 //   1. lam* = G^T lam^{n+1}           gravity source (linear in U* for a fixed -grad Phi),
 //                                     evaluated where the passes below need it
-//   2. per direction d:
-//      face pass   F^bar = (dt/dx)(lam*_j - lam*_{j-1}) through the HLL flux at face j-1/2
-//                  -> adjoints of the face states hi_{j-1}, lo_j
-//      cell pass   reconstruction of cell j reversed -> adjoints of W_{j-1}, W_j, W_{j+1}
-//      gather      summed onto the padded primitive adjoint (deterministic, no atomics;
-//                  the first direction writes, later ones add)
+//   2. per direction d, one fused pass over pencils along d (adj_pencil_kernel):
+//      F^bar = (dt/dx)(lam*_j - lam*_{j-1}) through the HLL flux at face j-1/2 -> adjoints of
+//      the face states hi_{j-1}, lo_j; the reconstruction of cell j reversed -> adjoints of
+//      W_{j-1}, W_j, W_{j+1}; summed per cell by warp shuffles onto the padded primitive
+//      adjoint (deterministic, no atomics; the first direction writes, later ones add)
 //   3. fold        lam^n_i = lam*_i + (dW/dU)^T W^bar_i, plus the ghost images of cell i
 //                  (periodic wrap, outflow copy, reflect mirror with its sign flips)
 // Forward states are checkpointed every K steps (by a forward sweep here, or by the step
@@ -39,8 +38,6 @@ template <typename T> struct AdjArgs {
   const int32_t *flags;
   const Ctrl *ctrl;    // fallback pass counters of the re-run forward step
   int32_t tag;
-  T *HB, *LB;          // face-state adjoints [NV][Next], local frame of the sweep
-  T *GM, *G0, *GP;     // reconstruction adjoints to cells j-1, j, j+1 [NV][Next], global order
   T *Wb;               // primitive adjoint on the padded grid [NV][Npad]
   int n[3], ndim, bc[6];
   double dx[3], dt;
@@ -55,27 +52,6 @@ __device__ __forceinline__ int last_pass(const Ctrl *c) {
   }
   return p;
 }
-
-// extended index along d: cells j in [-1, n_d] along d, interior along the other dims
-struct ExtIdx {
-  int n[3], d;
-  __device__ __forceinline__ size_t count() const {
-    return (size_t)(n[0] + (d == 0 ? 2 : 0)) * (n[1] + (d == 1 ? 2 : 0)) * (n[2] + (d == 2 ? 2 : 0));
-  }
-  __device__ __forceinline__ void coords(size_t e, int (&c)[3]) const {
-    const int m0 = n[0] + (d == 0 ? 2 : 0), m1 = n[1] + (d == 1 ? 2 : 0);
-    c[0] = (int)(e % m0);
-    c[1] = (int)((e / m0) % m1);
-    c[2] = (int)(e / ((size_t)m0 * m1));
-    c[d] -= 1;
-  }
-  __device__ __forceinline__ size_t index(const int (&c)[3]) const {
-    const int m0 = n[0] + (d == 0 ? 2 : 0), m1 = n[1] + (d == 1 ? 2 : 0);
-    int q[3] = {c[0], c[1], c[2]};
-    q[d] += 1;
-    return ((size_t)q[2] * m1 + q[1]) * m0 + q[0];
-  }
-};
 
 // padded index: 2 ghost layers on every active dim
 __device__ __forceinline__ size_t pad_index(const int (&n)[3], int ndim, const int (&c)[3]) {
@@ -137,156 +113,94 @@ __device__ __forceinline__ void lam_star(const AdjArgs<T> &a, size_t N, size_t c
   }
 }
 
-// face pass: thread per extended cell j, handling the face j-1/2
+// Reverse of one sweep direction D, fused: one warp per segment of a pencil along D, lane l
+// holding the extended position j = -2 + 26 seg - 3 + l.  Each lane converts its own cell
+// once and takes its neighbours' primitive states, tags and lam* by shuffles; it recomputes
+// its reconstruction (the face states lo_j, hi_j, forward branches), reverses the HLL flux
+// through its lower face j-1/2 with F^bar = (dt/dx)(lam*_j - lam*_{j-1}) (faces j in
+// [0, n_D]; ghost cells are not updated, so their lam* is zero), reverses its
+// reconstruction with the adjoints of its two face states (the upper one from lane l+1;
+// extended cells j in [-1, n_D]), and sums the three reconstruction adjoints that reach its
+// cell (its own and its neighbours').  That sum is complete in lanes 3..28 (each needs
+// the faces of lanes l-1 .. l+2 and the states of lanes l-3 .. l+3), which own the padded
+// positions [-2, n_D + 1] segment by segment: direction 0 writes them, a later direction
+// adds where the cell is inside the grid along D and writes its own ghost layers.
+constexpr int kAdjSeg = 26;  // complete positions per warp segment
+
 template <typename T, int D>
-__global__ void adj_face_kernel(AdjArgs<T> a) {
-  const ExtIdx X{{a.n[0], a.n[1], a.n[2]}, D};
-  const size_t Ne = X.count();
-  const size_t N = (size_t)a.n[0] * a.n[1] * a.n[2];
-  const int pass = last_pass(a.ctrl);
+__global__ void __launch_bounds__(256) adj_pencil_kernel(AdjArgs<T> a) {
+  const int lane = threadIdx.x & 31;
   const int nd = a.n[D];
+  const int nseg = (nd + 4 + kAdjSeg - 1) / kAdjSeg;
+  constexpr int O1 = D == 0 ? 1 : 0, O2 = D == 2 ? 1 : 2;  // the other two axes
+  const long nwarps = (long)a.n[O1] * a.n[O2] * nseg;
+  const size_t N = (size_t)a.n[0] * a.n[1] * a.n[2];
+  const int g1 = a.ndim > 1 ? 2 : 0, g2 = a.ndim > 2 ? 2 : 0;
+  const size_t Npad = (size_t)(a.n[0] + 4) * (a.n[1] + 2 * g1) * (a.n[2] + 2 * g2);
+  const int pass = last_pass(a.ctrl);
   const T nu = (T)(0.5 * a.dt / a.dx[D]);
   const T dtdx = (T)(a.dt / a.dx[D]);
-  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < Ne; e += (size_t)gridDim.x * blockDim.x) {
+  const long wstride = (long)gridDim.x * (blockDim.x >> 5);
+  for (long w = (long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); w < nwarps; w += wstride) {
+    const int seg = (int)(w % nseg);
+    const long pen = w / nseg;
     int c[3];
-    X.coords(e, c);
-    const int j = c[D];
-    if (j == nd) {  // no face above the last ghost cell
-      int cc[3] = {c[0], c[1], c[2]};
-#pragma unroll
-      for (int k = 0; k < NV; k++) a.HB[k * Ne + X.index(cc)] = T(0);
-    }
-    if (j < 0) {
-#pragma unroll
-      for (int k = 0; k < NV; k++) a.LB[k * Ne + e] = T(0);
-      continue;
-    }
-    // face states hi_{j-1} and lo_j
-    T w[4][NV];
-    bool f[4];
-    for (int o = 0; o < 4; o++) local_w<T, D>(a, c, j - 2 + o, w[o], f[o], pass);
-    c[D] = j;
-    T lo0[NV], hi0[NV], lo1[NV], hi1[NV];
-    reconstruct(w[0], w[1], w[2], nu, lo0, hi0);  // cell j-1
-    first_order_faces(f[0], f[1], f[2], w[1], lo0, hi0);
-    reconstruct(w[1], w[2], w[3], nu, lo1, hi1);  // cell j
-    first_order_faces(f[1], f[2], f[3], w[2], lo1, hi1);
-    // flux adjoint: U*_{j-1} -= (dt/dx) F, U*_j += (dt/dx) F (ghost cells are not updated)
-    T Fb[NV];
-    const size_t cj = ((size_t)c[2] * a.n[1] + c[1]) * a.n[0] + c[0];
-    int cm[3] = {c[0], c[1], c[2]};
-    cm[D] = j - 1;
-    const size_t cjm = ((size_t)cm[2] * a.n[1] + cm[1]) * a.n[0] + cm[0];
-    T lsj[NV], lsm[NV];
-    if (j < nd) lam_star(a, N, cj, lsj);
-    else {
-#pragma unroll
-      for (int k = 0; k < NV; k++) lsj[k] = T(0);
-    }
-    if (j >= 1) lam_star(a, N, cjm, lsm);
-    else {
-#pragma unroll
-      for (int k = 0; k < NV; k++) lsm[k] = T(0);
-    }
-#pragma unroll
-    for (int k = 0; k < NV; k++) {
-      const int gk = Frame<D>::g(k);
-      Fb[k] = dtdx * (lsj[gk] - lsm[gk]);
-    }
-    T hb[NV], lb[NV];
-#pragma unroll
-    for (int k = 0; k < NV; k++) { hb[k] = T(0); lb[k] = T(0); }
-    hll_vjp(hi0, lo1, Fb, hb, lb);
-    const size_t em = X.index(cm);
-#pragma unroll
-    for (int k = 0; k < NV; k++) {
-      a.HB[k * Ne + em] = hb[k];
-      a.LB[k * Ne + e] = lb[k];
-    }
-  }
-}
-
-// cell pass: thread per extended cell j, reverse of its reconstruction
-template <typename T, int D>
-__global__ void adj_cell_kernel(AdjArgs<T> a) {
-  const ExtIdx X{{a.n[0], a.n[1], a.n[2]}, D};
-  const size_t Ne = X.count();
-  const int pass = last_pass(a.ctrl);
-  const T nu = (T)(0.5 * a.dt / a.dx[D]);
-  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < Ne; e += (size_t)gridDim.x * blockDim.x) {
-    int c[3];
-    X.coords(e, c);
-    const int j = c[D];
-    T wm[NV], w0[NV], wp[NV];
-    bool fm, f0, fp;
-    local_w<T, D>(a, c, j - 1, wm, fm, pass);
-    local_w<T, D>(a, c, j, w0, f0, pass);
-    local_w<T, D>(a, c, j + 1, wp, fp, pass);
-    T lb[NV], hb[NV], gm[NV], g0[NV], gp[NV];
-#pragma unroll
-    for (int k = 0; k < NV; k++) {
-      lb[k] = a.LB[k * Ne + e];
-      hb[k] = a.HB[k * Ne + e];
-      gm[k] = g0[k] = gp[k] = T(0);
-    }
-    reconstruct_vjp(wm, w0, wp, nu, fm, f0, fp, lb, hb, gm, g0, gp);
-#pragma unroll
-    for (int k = 0; k < NV; k++) {
-      const int gk = Frame<D>::g(k);
-      a.GM[gk * Ne + e] = gm[k];
-      a.G0[gk * Ne + e] = g0[k];
-      a.GP[gk * Ne + e] = gp[k];
-    }
-  }
-}
-
-// gather: padded positions p in [-2, n_d+1] along d (interior along the other dims)
-template <typename T, int D>
-__global__ void adj_gather_kernel(AdjArgs<T> a) {
-  const ExtIdx X{{a.n[0], a.n[1], a.n[2]}, D};
-  const size_t Ne = X.count();
-  int m[3] = {a.n[0], a.n[1], a.n[2]};
-  m[D] += 4;
-  const size_t Ng = (size_t)m[0] * m[1] * m[2];
-  int np[3] = {a.n[0], a.n[1], a.n[2]};
-  int g[3] = {2, a.ndim > 1 ? 2 : 0, a.ndim > 2 ? 2 : 0};
-  const size_t Npad = (size_t)(np[0] + 2 * g[0]) * (np[1] + 2 * g[1]) * (np[2] + 2 * g[2]);
-  const int nd = a.n[D];
-  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < Ng; e += (size_t)gridDim.x * blockDim.x) {
-    int c[3] = {(int)(e % m[0]), (int)((e / m[0]) % m[1]), (int)(e / ((size_t)m[0] * m[1]))};
-    c[D] -= 2;
-    const int p = c[D];
-    T s[NV];
-#pragma unroll
-    for (int k = 0; k < NV; k++) s[k] = T(0);
-    int q[3] = {c[0], c[1], c[2]};
-    if (p - 1 >= -1 && p - 1 <= nd) {
-      q[D] = p - 1;
-      const size_t i = X.index(q);
-#pragma unroll
-      for (int k = 0; k < NV; k++) s[k] += a.GP[k * Ne + i];
-    }
-    if (p >= -1 && p <= nd) {
-      q[D] = p;
-      const size_t i = X.index(q);
-#pragma unroll
-      for (int k = 0; k < NV; k++) s[k] += a.G0[k * Ne + i];
-    }
-    if (p + 1 >= -1 && p + 1 <= nd) {
-      q[D] = p + 1;
-      const size_t i = X.index(q);
-#pragma unroll
-      for (int k = 0; k < NV; k++) s[k] += a.GM[k * Ne + i];
-    }
-    const size_t pi = pad_index(a.n, a.ndim, c);
-    // direction 0 writes every position it covers; a later direction adds where the cell
-    // is inside the grid along D (covered by direction 0) and writes its own ghost layers
-    if (D == 0 || p < 0 || p >= nd) {
-#pragma unroll
-      for (int k = 0; k < NV; k++) a.Wb[k * Npad + pi] = s[k];
+    c[O1] = (int)(pen % a.n[O1]);
+    c[O2] = (int)(pen / a.n[O1]);
+    const int j = -2 + seg * kAdjSeg - 3 + lane;
+    T w0[NV], ls[NV];
+    bool f0;
+    local_w<T, D>(a, c, j, w0, f0, pass);  // also sets c[D] = j
+    if (j >= 0 && j < nd) {
+      lam_star(a, N, ((size_t)c[2] * a.n[1] + c[1]) * a.n[0] + c[0], ls);
     } else {
 #pragma unroll
-      for (int k = 0; k < NV; k++) a.Wb[k * Npad + pi] += s[k];
+      for (int k = 0; k < NV; k++) ls[k] = T(0);
+    }
+    T wm[NV], wp[NV];
+#pragma unroll
+    for (int k = 0; k < NV; k++) {
+      wm[k] = __shfl_up_sync(0xffffffffu, w0[k], 1);
+      wp[k] = __shfl_down_sync(0xffffffffu, w0[k], 1);
+    }
+    const bool fm = __shfl_up_sync(0xffffffffu, (int)f0, 1) != 0;
+    const bool fp = __shfl_down_sync(0xffffffffu, (int)f0, 1) != 0;
+    // forward face states of this cell
+    T lo[NV], hi[NV];
+    reconstruct(wm, w0, wp, nu, lo, hi);
+    first_order_faces(fm, f0, fp, w0, lo, hi);
+    // the flux adjoint at the lower face j-1/2: hb to hi_{j-1} (lane l-1), lb to lo_j
+    T hm[NV], Fb[NV], hb[NV], lb[NV];
+#pragma unroll
+    for (int k = 0; k < NV; k++) {
+      hm[k] = __shfl_up_sync(0xffffffffu, hi[k], 1);
+      const int gk = Frame<D>::g(k);
+      Fb[k] = dtdx * (ls[gk] - __shfl_up_sync(0xffffffffu, ls[gk], 1));
+      hb[k] = T(0);
+      lb[k] = T(0);
+    }
+    if (j >= 0 && j <= nd) hll_vjp(hm, lo, Fb, hb, lb);
+    T hib[NV], gm[NV], g0[NV], gp[NV];
+#pragma unroll
+    for (int k = 0; k < NV; k++) {
+      hib[k] = __shfl_down_sync(0xffffffffu, hb[k], 1);
+      gm[k] = g0[k] = gp[k] = T(0);
+    }
+    if (j >= -1 && j <= nd) reconstruct_vjp(wm, w0, wp, nu, fm, f0, fp, lb, hib, gm, g0, gp);
+    // the primitive adjoint of this cell from this direction: g0 + gm of lane l+1 + gp of lane l-1
+    T s[NV];
+#pragma unroll
+    for (int k = 0; k < NV; k++)
+      s[Frame<D>::g(k)] = g0[k] + __shfl_down_sync(0xffffffffu, gm[k], 1) + __shfl_up_sync(0xffffffffu, gp[k], 1);
+    if (lane >= 3 && lane <= 28 && j <= nd + 1) {
+      const size_t pi = pad_index(a.n, a.ndim, c);
+      if (D == 0 || j < 0 || j >= nd) {
+#pragma unroll
+        for (int k = 0; k < NV; k++) a.Wb[k * Npad + pi] = s[k];
+      } else {
+#pragma unroll
+        for (int k = 0; k < NV; k++) a.Wb[k * Npad + pi] += s[k];
+      }
     }
   }
 }
@@ -448,25 +362,18 @@ msh_status reverse_sweep(msh_grid *g, const T *ck, int64_t nsteps, const double 
   const cudaMemcpyKind out_kind = where == MSH_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
   const int64_t nck = nsteps > 0 ? (nsteps + K - 1) / K : 0;
   const int64_t seg_len = std::min<int64_t>(K, std::max<int64_t>(nsteps, 1));
-  size_t Ne_max = 0;
-  for (int d = 0; d < g->ndim; d++) Ne_max = std::max(Ne_max, N / g->n[d] * (g->n[d] + 2));
   size_t Npad = 1;
   for (int d = 0; d < 3; d++) Npad *= (size_t)(g->n[d] + (d < g->ndim ? 4 : 0));
   const int nb = std::max(step_blocks<T>(g->ndim, g->rows, (int)g->n[0], (int)g->n[1], (int)g->n[2], g->zchunk),
                           1);
   T *seg = nullptr, *la = nullptr, *lb = nullptr, *scratch = nullptr;
-  T *HB = nullptr, *LB = nullptr, *GM = nullptr, *G0 = nullptr, *GP = nullptr, *Wb = nullptr;
+  T *Wb = nullptr;
   Ctrl *ctl = nullptr;
   Partial *part = nullptr;
   A_TRY(cudaMalloc(&seg, S * (size_t)seg_len));
   A_TRY(cudaMalloc(&la, S));
   A_TRY(cudaMalloc(&lb, S));
   A_TRY(cudaMalloc(&scratch, S));
-  A_TRY(cudaMalloc(&HB, Ne_max * NV * sizeof(T)));
-  A_TRY(cudaMalloc(&LB, Ne_max * NV * sizeof(T)));
-  A_TRY(cudaMalloc(&GM, Ne_max * NV * sizeof(T)));
-  A_TRY(cudaMalloc(&G0, Ne_max * NV * sizeof(T)));
-  A_TRY(cudaMalloc(&GP, Ne_max * NV * sizeof(T)));
   A_TRY(cudaMalloc(&Wb, Npad * NV * sizeof(T)));
   A_TRY(cudaMalloc(&ctl, sizeof(Ctrl)));
   A_TRY(cudaMalloc(&part, sizeof(Partial) * (size_t)nb));
@@ -491,11 +398,6 @@ msh_status reverse_sweep(msh_grid *g, const T *ck, int64_t nsteps, const double 
       a.flags = g->flags;
       a.ctrl = ctl;
       a.tag = (int32_t)(n & 0x0fffffff) + 1;
-      a.HB = HB;
-      a.LB = LB;
-      a.GM = GM;
-      a.G0 = G0;
-      a.GP = GP;
       a.Wb = Wb;
       for (int i = 0; i < 3; i++) {
         a.n[i] = (int)g->n[i];
@@ -506,21 +408,11 @@ msh_status reverse_sweep(msh_grid *g, const T *ck, int64_t nsteps, const double 
       a.dt = dts[n];
       for (int d = 0; d < g->ndim; d++) {
         a.d = d;
-        const size_t Ne = N / g->n[d] * (g->n[d] + 2);
-        const size_t Ng = N / g->n[d] * (g->n[d] + 4);
-        if (d == 0) {
-          adj_face_kernel<T, 0><<<grid_blocks(Ne), 256, 0, g->stream>>>(a);
-          adj_cell_kernel<T, 0><<<grid_blocks(Ne), 256, 0, g->stream>>>(a);
-          adj_gather_kernel<T, 0><<<grid_blocks(Ng), 256, 0, g->stream>>>(a);
-        } else if (d == 1) {
-          adj_face_kernel<T, 1><<<grid_blocks(Ne), 256, 0, g->stream>>>(a);
-          adj_cell_kernel<T, 1><<<grid_blocks(Ne), 256, 0, g->stream>>>(a);
-          adj_gather_kernel<T, 1><<<grid_blocks(Ng), 256, 0, g->stream>>>(a);
-        } else {
-          adj_face_kernel<T, 2><<<grid_blocks(Ne), 256, 0, g->stream>>>(a);
-          adj_cell_kernel<T, 2><<<grid_blocks(Ne), 256, 0, g->stream>>>(a);
-          adj_gather_kernel<T, 2><<<grid_blocks(Ng), 256, 0, g->stream>>>(a);
-        }
+        const long warps = (long)(N / g->n[d]) * ((g->n[d] + 4 + kAdjSeg - 1) / kAdjSeg);
+        const int blocks = (int)std::min<long>((warps + 7) / 8, 1L << 20);
+        if (d == 0) adj_pencil_kernel<T, 0><<<blocks, 256, 0, g->stream>>>(a);
+        else if (d == 1) adj_pencil_kernel<T, 1><<<blocks, 256, 0, g->stream>>>(a);
+        else adj_pencil_kernel<T, 2><<<blocks, 256, 0, g->stream>>>(a);
         A_TRY(cudaGetLastError());
       }
       adj_fold_kernel<T><<<grid_blocks(N), 256, 0, g->stream>>>(a);
@@ -537,8 +429,7 @@ msh_status reverse_sweep(msh_grid *g, const T *ck, int64_t nsteps, const double 
   A_TRY(cudaStreamSynchronize(g->stream));
 done:
   cudaStreamSynchronize(g->stream);
-  for (void *p : {(void *)seg, (void *)la, (void *)lb, (void *)scratch, (void *)HB, (void *)LB, (void *)GM,
-                  (void *)G0, (void *)GP, (void *)Wb, (void *)ctl, (void *)part})
+  for (void *p : {(void *)seg, (void *)la, (void *)lb, (void *)scratch, (void *)Wb, (void *)ctl, (void *)part})
     if (p) cudaFree(p);
   return st;
 }

@@ -4,11 +4,14 @@
 // Each thread block repeatedly takes the next tube from a device work queue (tubes are
 // ordered longest first on the host, since the work of a tube grows as len^2), loads it
 // into shared memory and advances it to its own t_end with a block-local CFL reduction;
-// the tube never leaves shared memory until it is finished.  Per step the block sweeps the
-// tube in chunks of NT cells: reconstruction of the chunk's cells, HLL fluxes through their
-// lower faces, and the conservative update into the second tube buffer, trailing the chunk
-// front by one cell (a cell is updated once both of its faces are known); the buffers swap
-// roles after each step, so U^n stays intact for the fallback passes without a copy.
+// the tube never leaves shared memory until it is finished.  In shared memory a tube is held
+// in primitive variables W, so the reconstruction reads its three cells without
+// conversions; per step the block sweeps the tube in chunks of NT cells: reconstruction of
+// the chunk's cells, HLL fluxes through their lower faces, and the conservative update
+// U^{n+1} = U(W^n) - dt/dx (F_{i+1/2} - F_{i-1/2}) of the cell one behind the chunk front (a
+// cell is updated once both of its faces are known; its W^n is the thread's left neighbour,
+// already in registers), stored as W^{n+1} into the second tube buffer; the buffers swap
+// roles after each step, so W^n stays intact for the fallback passes without a copy.
 // The step is the same as the grid kernels': MUSCL-Hancock on the characteristic
 // variables (Sec. 3.3), HLL flux, outflow boundaries by index clamping, CFL time step
 // dt = C dx / max(|u| + sqrt(3 P_xx/rho)) with the last step clipped to t_end.
@@ -46,12 +49,10 @@ template <typename T> struct TubeArgs {
   int64_t max_steps;
 };
 
-template <typename T> __device__ __forceinline__ void load_w(const T *sU, int cap, int c, int n, T (&W)[NV]) {
+template <typename T> __device__ __forceinline__ void load_w(const T *sW, int cap, int c, int n, T (&W)[NV]) {
   const int cc = min(max(c, 0), n - 1);  // outflow: zero-gradient copy of the edge cell
-  T U[NV];
 #pragma unroll
-  for (int k = 0; k < NV; k++) U[k] = sU[k * cap + cc];
-  cons_to_prim(U, W);
+  for (int k = 0; k < NV; k++) W[k] = sW[k * cap + cc];
 }
 
 template <typename T, int NT> __device__ __forceinline__ T block_max(T v, T *red) {
@@ -68,8 +69,7 @@ template <typename T, int NT> __device__ __forceinline__ T block_max(T v, T *red
 }
 
 // One sweep of a tube over all its faces: reconstruction, HLL fluxes and the conservative
-// update, chunk by chunk.  src holds U^n; dst receives U^{n+1} (dst may also equal src:
-// each cell is updated after the last chunk that reads it).  With FALLBACK, every face that
+// update, chunk by chunk.  src holds W^n; dst receives W^{n+1} (a different buffer).  With FALLBACK, every face that
 // touches a cell tagged by an earlier pass (sFl == 2) takes first-order states.  Cells whose
 // update is not realizable and that carry no active tag are tagged (sFl = 1) and *s_nbad
 // is set.  Returns the thread's maximum signal-speed sum of the new state.
@@ -80,9 +80,9 @@ __device__ T tube_pass(const T *src, T *dst, unsigned char *sFl, int n, int cap,
   T smax = T(0);
   for (int b = -1; b <= n; b += NT) {
     const int c = b + t;
-    T lo[NV], hi[NV];
+    T lo[NV], hi[NV], wm[NV];  // wm: W^n of the cell this thread updates (c - 1)
     if (c <= n) {
-      T wm[NV], w0[NV], wp[NV];
+      T w0[NV], wp[NV];
       load_w(src, cap, c - 1, n, wm);
       load_w(src, cap, c, n, w0);
       load_w(src, cap, c + 1, n, wp);
@@ -110,15 +110,15 @@ __device__ T tube_pass(const T *src, T *dst, unsigned char *sFl, int n, int cap,
 #pragma unroll
       for (int v = 0; v < NV; v++) sHc[v] = hi[v];
     }
-    const int cu = b - 1 + t;  // cell whose two faces are now known
+    const int cu = b - 1 + t;  // cell whose two faces are now known (= c - 1: its W^n is wm)
     if (cu >= 0 && cu < n) {
       T U[NV], W[NV];
+      prim_to_cons(wm, U);
 #pragma unroll
-      for (int v = 0; v < NV; v++) {
-        U[v] = src[v * cap + cu] - dtdx * (sF[v * (NT + 1) + t + 1] - sF[v * (NT + 1) + t]);
-        dst[v * cap + cu] = U[v];
-      }
+      for (int v = 0; v < NV; v++) U[v] -= dtdx * (sF[v * (NT + 1) + t + 1] - sF[v * (NT + 1) + t]);
       cons_to_prim(U, W);
+#pragma unroll
+      for (int v = 0; v < NV; v++) dst[v * cap + cu] = W[v];
       if (!realizable(W)) {
         *s_any = 1;
         if (sFl[cu] != 2) {  // newly failing cell: tag it for the next pass
@@ -141,8 +141,8 @@ template <typename T, int NT>
 __global__ void __launch_bounds__(NT) tubes_kernel(TubeArgs<T> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int cap = a.cap;
-  // two tube buffers: a step reads U^n from one and writes U^{n+1} to the other (the
-  // fallback passes re-read the untouched U^n), then the two swap roles
+  // two tube buffers (primitive): a step reads W^n from one and writes W^{n+1} to the other
+  // (the fallback passes re-read the untouched W^n), then the two swap roles
   T *sU = reinterpret_cast<T *>(smem_raw);  // [NV][cap]
   T *sUo = sU + (size_t)NV * cap;           // [NV][cap]
   T *sF = sUo + (size_t)NV * cap;           // [NV][NT+1]: sF[0] = carried face, sF[t+1] = lower face of cell b+t
@@ -162,10 +162,14 @@ __global__ void __launch_bounds__(NT) tubes_kernel(TubeArgs<T> a) {
     const int k = a.order[q];
     const int n = a.len[k];
     const int64_t off = a.off[k];
-    T *cur = sU, *nxt = sUo;  // U^n and U^{n+1} of the current step
+    T *cur = sU, *nxt = sUo;  // W^n and W^{n+1} of the current step
     for (int c = t; c < n; c += NT) {
+      T U[NV], W[NV];
 #pragma unroll
-      for (int v = 0; v < NV; v++) cur[v * cap + c] = a.U[v * a.total + off + c];
+      for (int v = 0; v < NV; v++) U[v] = a.U[v * a.total + off + c];
+      cons_to_prim(U, W);
+#pragma unroll
+      for (int v = 0; v < NV; v++) cur[v * cap + c] = W[v];
       sFl[c] = 0;
     }
     __syncthreads();
@@ -216,9 +220,14 @@ __global__ void __launch_bounds__(NT) tubes_kernel(TubeArgs<T> a) {
       steps++;
     }
     __syncthreads();
-    for (int c = t; c < n; c += NT)
+    for (int c = t; c < n; c += NT) {
+      T W[NV], U[NV];
 #pragma unroll
-      for (int v = 0; v < NV; v++) a.U[v * a.total + off + c] = cur[v * cap + c];
+      for (int v = 0; v < NV; v++) W[v] = cur[v * cap + c];
+      prim_to_cons(W, U);
+#pragma unroll
+      for (int v = 0; v < NV; v++) a.U[v * a.total + off + c] = U[v];
+    }
     if (t == 0) {
       a.steps[k] = steps;
       a.t_out[k] = tt;

@@ -59,6 +59,11 @@ class FallbackAcrossSlabs(RuntimeError):
     pass
 
 
+class NotRealizable(RuntimeError):
+    """A step left an owned cell of some slab non-realizable (rho <= 0 or P not positive
+    definite) after every fallback pass."""
+
+
 @dataclass
 class Slab:
     rank: int
@@ -308,6 +313,15 @@ class SlabDriver:
             tagged = int(self.comm.sum(np.array([float(tagged)]))[0])
             if tagged:
                 raise FallbackAcrossSlabs(f"step {self.steps}: the a-posteriori fallback tagged {tagged} cells")
+        # A stepper checks every local cell, its halo cells too, whose update is discarded;
+        # where one reported a non-realizable cell, the owned layers decide (all ranks).
+        flagged = sum(1.0 for st in self.steppers.values() if getattr(st, "local_bad", False))
+        for st in self.steppers.values():
+            st.local_bad = False
+        if self.comm.sum(np.array([flagged]))[0] > 0:
+            _, _, ok = self.reduce()
+            if not ok:
+                raise NotRealizable(f"step {self.steps}: an owned cell is not realizable after the fallback")
         self.t += dt
         self.steps += 1
         return dt
@@ -349,6 +363,19 @@ class GridStepper:
     def __init__(self, grid, scheme=0):
         self.g = grid
         self.phased = scheme != 1
+        self.local_bad = False
+
+    def _checked(self, call, *args):
+        """A step call whose MSH_E_REALIZABILITY (some local cell, halo cells included) is
+        left to the driver's check of the owned layers; the step itself has been taken."""
+        from . import msh
+        try:
+            return call(*args)
+        except msh.MshError as e:
+            if e.status != msh.MSH_E_REALIZABILITY:
+                raise
+            self.local_bad = True
+            return 0
 
     def layers(self):
         return self.g.layer_shape()[0]
@@ -363,7 +390,7 @@ class GridStepper:
         return self.g.reduce_layers(start, count)
 
     def step(self, dt):
-        return self.g.step_dt(dt)
+        return self._checked(self.g.step_dt, dt)
 
     def begin(self, dt):
         self.g.step_begin(dt)
@@ -372,7 +399,7 @@ class GridStepper:
         self.g.step_retry(level)
 
     def end(self):
-        return self.g.step_end()
+        return self._checked(self.g.step_end)
 
     def count_tags(self, start, count, level):
         return self.g.count_tags(start, count, level)

@@ -223,7 +223,9 @@ def test_phased_step_equals_step_dt_and_tags_round_trip(env):
     b.set_tags(3, 5, lv)
     np.testing.assert_array_equal(b.get_tags(3, 5), lv)
     assert b.count_tags(3, 5, 2) == int((lv == 2).sum())
-    b.step_end()
+    with pytest.raises(msh.MshError) as ei:  # no fallback pass ran: the update is not realizable
+        b.step_end()
+    assert ei.value.status == msh.MSH_E_REALIZABILITY
     a.close()
     b.close()
 
