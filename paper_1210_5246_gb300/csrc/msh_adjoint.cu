@@ -10,8 +10,10 @@
 //      the face states hi_{j-1}, lo_j; the reconstruction of cell j reversed -> adjoints of
 //      W_{j-1}, W_j, W_{j+1}; summed per cell by warp shuffles onto the padded primitive
 //      adjoint (deterministic, no atomics; the first direction writes, later ones add)
-//   3. fold        lam^n_i = lam*_i + (dW/dU)^T W^bar_i, plus the ghost images of cell i
-//                  (periodic wrap, outflow copy, reflect mirror with its sign flips)
+//   3. fold        lam^n_i = lam*_i + (dW/dU)^T W^bar_i: in the last direction's pass for a
+//                  cell no ghost cell maps to; else (within two cells of an edge) plus the
+//                  ghost images of cell i (periodic wrap, outflow copy, reflect mirror with
+//                  its sign flips) in adj_fold_kernel
 // Forward states are checkpointed every K steps (by a forward sweep here, or by the step
 // kernels of the recorded run: msh_adjoint_tape) and recomputed segment by segment during
 // the reverse sweep.  Which steps tagged cells for the a-posteriori fallback is known on
@@ -27,6 +29,7 @@
 #include "msh_adjoint.cuh"
 #include "msh_device.cuh"
 #include "msh_internal.h"
+#include "msh_step_kernels.cuh"
 
 namespace msh {
 
@@ -127,7 +130,78 @@ __device__ __forceinline__ void lam_star(const AdjArgs<T> &a, size_t N, size_t c
 // adds where the cell is inside the grid along D and writes its own ghost layers.
 constexpr int kAdjSeg = 26;  // complete positions per warp segment
 
+// A cell that some ghost cell maps to (within two cells of the grid's edge along an active
+// axis, for every kind of boundary): its adjoint also collects its ghost images, which the
+// fold kernel adds.
+__device__ __forceinline__ bool ghost_source(const int (&n)[3], int ndim, const int (&c)[3]) {
+  for (int d = 0; d < ndim; d++)
+    if (c[d] <= 1 || c[d] >= n[d] - 2) return true;
+  return false;
+}
+
+// The last direction's pass finishes a cell that is no ghost source at once:
+// lam^n = lam* + (dW/dU)^T (W^bar of the earlier directions + s).
+template <typename T>
+__device__ __forceinline__ void fold_cell(const AdjArgs<T> &a, size_t N, size_t Npad, size_t ci, size_t pi,
+                                          bool first, const T (&s)[NV], const T (&ls)[NV]) {
+  T U[NV], Ub[NV], Wb[NV];
+#pragma unroll
+  for (int k = 0; k < NV; k++) {
+    U[k] = a.U[k * N + ci];
+    Wb[k] = first ? s[k] : a.Wb[k * Npad + pi] + s[k];
+    Ub[k] = T(0);
+  }
+  cons_to_prim_vjp(U, Wb, Ub);
+#pragma unroll
+  for (int k = 0; k < NV; k++) a.out[k * N + ci] = ls[k] + Ub[k];
+}
+
+// The warp-wide part of the fused pass: lane l holds extended position j of one pencil along
+// D with its primitive state w0 (local frame), tag f0 and lam* ls (global order); returns
+// in s (global order) the primitive adjoint of its cell from this direction, complete in
+// lanes 3..28.
 template <typename T, int D>
+__device__ __forceinline__ void adj_pencil_lane(int j, int nd, T nu, T dtdx, const T (&w0)[NV], bool f0,
+                                                const T (&ls)[NV], T (&s)[NV]) {
+  T wm[NV], wp[NV];
+#pragma unroll
+  for (int k = 0; k < NV; k++) {
+    wm[k] = __shfl_up_sync(0xffffffffu, w0[k], 1);
+    wp[k] = __shfl_down_sync(0xffffffffu, w0[k], 1);
+  }
+  const bool fm = __shfl_up_sync(0xffffffffu, (int)f0, 1) != 0;
+  const bool fp = __shfl_down_sync(0xffffffffu, (int)f0, 1) != 0;
+  // forward face states of this cell
+  T lo[NV], hi[NV];
+  reconstruct(wm, w0, wp, nu, lo, hi);
+  first_order_faces(fm, f0, fp, w0, lo, hi);
+  // the flux adjoint at the lower face j-1/2: hb to hi_{j-1} (lane l-1), lb to lo_j
+  T hm[NV], Fb[NV], hb[NV], lb[NV];
+#pragma unroll
+  for (int k = 0; k < NV; k++) {
+    hm[k] = __shfl_up_sync(0xffffffffu, hi[k], 1);
+    const int gk = Frame<D>::g(k);
+    Fb[k] = dtdx * (ls[gk] - __shfl_up_sync(0xffffffffu, ls[gk], 1));
+    hb[k] = T(0);
+    lb[k] = T(0);
+  }
+  if (j >= 0 && j <= nd) hll_vjp(hm, lo, Fb, hb, lb);
+  T hib[NV], gm[NV], g0[NV], gp[NV];
+#pragma unroll
+  for (int k = 0; k < NV; k++) {
+    hib[k] = __shfl_down_sync(0xffffffffu, hb[k], 1);
+    gm[k] = g0[k] = gp[k] = T(0);
+  }
+  if (j >= -1 && j <= nd) reconstruct_vjp(wm, w0, wp, nu, fm, f0, fp, lb, hib, gm, g0, gp);
+  // g0 + gm of lane l+1 + gp of lane l-1
+#pragma unroll
+  for (int k = 0; k < NV; k++)
+    s[Frame<D>::g(k)] = g0[k] + __shfl_down_sync(0xffffffffu, gm[k], 1) + __shfl_up_sync(0xffffffffu, gp[k], 1);
+}
+
+// Direction 0: one warp per segment of a pencil along x (lanes along x, coalesced).  LAST: x
+// is the grid's only direction (1D), and the pass finishes the cells that are no ghost source.
+template <typename T, int D, bool LAST>
 __global__ void __launch_bounds__(256) adj_pencil_kernel(AdjArgs<T> a) {
   const int lane = threadIdx.x & 31;
   const int nd = a.n[D];
@@ -141,14 +215,15 @@ __global__ void __launch_bounds__(256) adj_pencil_kernel(AdjArgs<T> a) {
   const T nu = (T)(0.5 * a.dt / a.dx[D]);
   const T dtdx = (T)(a.dt / a.dx[D]);
   const long wstride = (long)gridDim.x * (blockDim.x >> 5);
+  const long npen = (long)a.n[O1] * a.n[O2];
   for (long w = (long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); w < nwarps; w += wstride) {
-    const int seg = (int)(w % nseg);
-    const long pen = w / nseg;
+    const long pen = w % npen;
+    const int seg = (int)(w / npen);
     int c[3];
     c[O1] = (int)(pen % a.n[O1]);
     c[O2] = (int)(pen / a.n[O1]);
     const int j = -2 + seg * kAdjSeg - 3 + lane;
-    T w0[NV], ls[NV];
+    T w0[NV], ls[NV], s[NV];
     bool f0;
     local_w<T, D>(a, c, j, w0, f0, pass);  // also sets c[D] = j
     if (j >= 0 && j < nd) {
@@ -157,44 +232,12 @@ __global__ void __launch_bounds__(256) adj_pencil_kernel(AdjArgs<T> a) {
 #pragma unroll
       for (int k = 0; k < NV; k++) ls[k] = T(0);
     }
-    T wm[NV], wp[NV];
-#pragma unroll
-    for (int k = 0; k < NV; k++) {
-      wm[k] = __shfl_up_sync(0xffffffffu, w0[k], 1);
-      wp[k] = __shfl_down_sync(0xffffffffu, w0[k], 1);
-    }
-    const bool fm = __shfl_up_sync(0xffffffffu, (int)f0, 1) != 0;
-    const bool fp = __shfl_down_sync(0xffffffffu, (int)f0, 1) != 0;
-    // forward face states of this cell
-    T lo[NV], hi[NV];
-    reconstruct(wm, w0, wp, nu, lo, hi);
-    first_order_faces(fm, f0, fp, w0, lo, hi);
-    // the flux adjoint at the lower face j-1/2: hb to hi_{j-1} (lane l-1), lb to lo_j
-    T hm[NV], Fb[NV], hb[NV], lb[NV];
-#pragma unroll
-    for (int k = 0; k < NV; k++) {
-      hm[k] = __shfl_up_sync(0xffffffffu, hi[k], 1);
-      const int gk = Frame<D>::g(k);
-      Fb[k] = dtdx * (ls[gk] - __shfl_up_sync(0xffffffffu, ls[gk], 1));
-      hb[k] = T(0);
-      lb[k] = T(0);
-    }
-    if (j >= 0 && j <= nd) hll_vjp(hm, lo, Fb, hb, lb);
-    T hib[NV], gm[NV], g0[NV], gp[NV];
-#pragma unroll
-    for (int k = 0; k < NV; k++) {
-      hib[k] = __shfl_down_sync(0xffffffffu, hb[k], 1);
-      gm[k] = g0[k] = gp[k] = T(0);
-    }
-    if (j >= -1 && j <= nd) reconstruct_vjp(wm, w0, wp, nu, fm, f0, fp, lb, hib, gm, g0, gp);
-    // the primitive adjoint of this cell from this direction: g0 + gm of lane l+1 + gp of lane l-1
-    T s[NV];
-#pragma unroll
-    for (int k = 0; k < NV; k++)
-      s[Frame<D>::g(k)] = g0[k] + __shfl_down_sync(0xffffffffu, gm[k], 1) + __shfl_up_sync(0xffffffffu, gp[k], 1);
+    adj_pencil_lane<T, D>(j, nd, nu, dtdx, w0, f0, ls, s);
     if (lane >= 3 && lane <= 28 && j <= nd + 1) {
       const size_t pi = pad_index(a.n, a.ndim, c);
-      if (D == 0 || j < 0 || j >= nd) {
+      if (LAST && j >= 0 && j < nd && !ghost_source(a.n, a.ndim, c)) {
+        fold_cell(a, N, Npad, ((size_t)c[2] * a.n[1] + c[1]) * a.n[0] + c[0], pi, D == 0, s, ls);
+      } else if (D == 0 || j < 0 || j >= nd) {
 #pragma unroll
         for (int k = 0; k < NV; k++) a.Wb[k * Npad + pi] = s[k];
       } else {
@@ -205,14 +248,135 @@ __global__ void __launch_bounds__(256) adj_pencil_kernel(AdjArgs<T> a) {
   }
 }
 
-// fold: lam^n_i = lam*_i + (dW/dU)^T Wb_i + images of ghost cells whose source is i
+// Directions 1 and 2: the same pass with the pencils' data staged through shared memory so
+// that every global access runs along x.  A block of eight warps takes 8 cells along x and
+// the 32 extended positions of one segment along D (26 complete, a 3-cell halo at each end),
+// for one index of the remaining axis: each thread loads one cell of the tile (the conserved
+// state converted to the local frame of D, lam*, tag; a row of 8 cells is one 32-byte sector
+// in FP32), each warp then runs one column as a pencil (lanes along D, neighbours by
+// shuffles), leaving the column's result in place of its state, and the block adds the 26
+// complete rows to the padded adjoint row by row (the last direction finishes the cells
+// that are no ghost source instead).  One column per warp gives several waves of tiles, so
+// the last, partly filled wave is short.
+constexpr int kAdjTileX = 8, kAdjTileP = 9;  // tile columns; padded row pitch (no bank conflicts)
+constexpr int kAdjTileThreads = 256;
+
+template <typename T> size_t adj_tile_smem() {
+  return (2 * (size_t)NV * 32 * kAdjTileP) * sizeof(T) + 32 * kAdjTileP * sizeof(int);
+}
+
+template <typename T, int D, bool LAST>
+__global__ void __launch_bounds__(kAdjTileThreads, sizeof(T) == 4 ? 2 : 1) adj_tile_kernel(AdjArgs<T> a) {
+  static_assert(D == 1 || D == 2, "the staged pass runs along y or z");
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T *sW = reinterpret_cast<T *>(smem_raw);            // [NV][32 along D][kAdjTileP along x]
+  T *sL = sW + (size_t)NV * 32 * kAdjTileP;           // lam*, same layout (global order)
+  int *sF = reinterpret_cast<int *>(sL + (size_t)NV * 32 * kAdjTileP);  // tags
+  const int nd = a.n[D];
+  const int nseg = (nd + 4 + kAdjSeg - 1) / kAdjSeg;
+  constexpr int O = D == 1 ? 2 : 1;  // the remaining axis
+  const int tilesx = (a.n[0] + kAdjTileX - 1) / kAdjTileX;
+  const long ntiles = (long)tilesx * nseg * a.n[O];
+  const size_t N = (size_t)a.n[0] * a.n[1] * a.n[2];
+  const int g1 = a.ndim > 1 ? 2 : 0, g2 = a.ndim > 2 ? 2 : 0;
+  const size_t Npad = (size_t)(a.n[0] + 4) * (a.n[1] + 2 * g1) * (a.n[2] + 2 * g2);
+  const int pass = last_pass(a.ctrl);
+  const T nu = (T)(0.5 * a.dt / a.dx[D]);
+  const T dtdx = (T)(a.dt / a.dx[D]);
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  for (long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int bx = (int)(tile % tilesx);
+    const int seg = (int)((tile / tilesx) % nseg);
+    const int o = (int)(tile / ((long)tilesx * nseg));
+    const int x0 = bx * kAdjTileX, jb = -2 + seg * kAdjSeg - 3;
+    for (int i = tid; i < 32 * kAdjTileX; i += blockDim.x) {
+      const int r = i / kAdjTileX, x = i - r * kAdjTileX;
+      int c[3];
+      c[0] = min(x0 + x, a.n[0] - 1);
+      c[O] = o;
+      const int j = jb + r;
+      T w[NV], ls[NV];
+      bool f;
+      local_w<T, D>(a, c, j, w, f, pass);  // sets c[D] = j
+      if (j >= 0 && j < nd) {
+        lam_star(a, N, ((size_t)c[2] * a.n[1] + c[1]) * a.n[0] + c[0], ls);
+      } else {
+#pragma unroll
+        for (int k = 0; k < NV; k++) ls[k] = T(0);
+      }
+#pragma unroll
+      for (int k = 0; k < NV; k++) {
+        sW[(k * 32 + r) * kAdjTileP + x] = w[k];
+        sL[(k * 32 + r) * kAdjTileP + x] = ls[k];
+      }
+      sF[r * kAdjTileP + x] = f;
+    }
+    __syncthreads();
+    for (int x = warp; x < kAdjTileX; x += blockDim.x >> 5) {
+      T w0[NV], ls[NV], s[NV];
+#pragma unroll
+      for (int k = 0; k < NV; k++) {
+        w0[k] = sW[(k * 32 + lane) * kAdjTileP + x];
+        ls[k] = sL[(k * 32 + lane) * kAdjTileP + x];
+      }
+      const bool f0 = sF[lane * kAdjTileP + x] != 0;
+      adj_pencil_lane<T, D>(jb + lane, nd, nu, dtdx, w0, f0, ls, s);
+#pragma unroll
+      for (int k = 0; k < NV; k++) sW[(k * 32 + lane) * kAdjTileP + x] = s[k];  // only this lane read it
+    }
+    __syncthreads();
+    for (int i = tid; i < kAdjSeg * kAdjTileX; i += blockDim.x) {
+      const int r = 3 + i / kAdjTileX, x = i % kAdjTileX;
+      const int j = jb + r;
+      if (x0 + x >= a.n[0] || j > nd + 1) continue;
+      int c[3];
+      c[0] = x0 + x;
+      c[O] = o;
+      c[D] = j;
+      const size_t pi = pad_index(a.n, a.ndim, c);
+      if (LAST && j >= 0 && j < nd && !ghost_source(a.n, a.ndim, c)) {
+        T sv[NV], ls[NV];
+#pragma unroll
+        for (int k = 0; k < NV; k++) {
+          sv[k] = sW[(k * 32 + r) * kAdjTileP + x];
+          ls[k] = sL[(k * 32 + r) * kAdjTileP + x];
+        }
+        fold_cell(a, N, Npad, ((size_t)c[2] * a.n[1] + c[1]) * a.n[0] + c[0], pi, false, sv, ls);
+      } else if (j < 0 || j >= nd) {
+#pragma unroll
+        for (int k = 0; k < NV; k++) a.Wb[k * Npad + pi] = sW[(k * 32 + r) * kAdjTileP + x];
+      } else {
+#pragma unroll
+        for (int k = 0; k < NV; k++) a.Wb[k * Npad + pi] += sW[(k * 32 + r) * kAdjTileP + x];
+      }
+    }
+    __syncthreads();  // the next tile restages the shared arrays
+  }
+}
+
+template <typename T, int D, bool LAST> cudaError_t launch_adj_tile(const AdjArgs<T> &a, cudaStream_t st) {
+  static std::atomic<uint64_t> attr_done{0};
+  cudaError_t e = set_smem_once(attr_done, (const void *)adj_tile_kernel<T, D, LAST>, adj_tile_smem<T>());
+  if (e != cudaSuccess) return e;
+  const int nseg = (a.n[D] + 4 + kAdjSeg - 1) / kAdjSeg;
+  const long tiles = (long)((a.n[0] + kAdjTileX - 1) / kAdjTileX) * nseg * a.n[D == 1 ? 2 : 1];
+  adj_tile_kernel<T, D, LAST><<<(int)std::min<long>(tiles, 1L << 20), kAdjTileThreads, adj_tile_smem<T>(), st>>>(a);
+  return cudaGetLastError();
+}
+
+// fold of the ghost sources: lam^n_i = lam*_i + (dW/dU)^T Wb_i + images of ghost cells whose
+// source is i (the other cells are finished by the last direction's pass)
 template <typename T>
 __global__ void adj_fold_kernel(AdjArgs<T> a) {
   const size_t N = (size_t)a.n[0] * a.n[1] * a.n[2];
   int g[3] = {2, a.ndim > 1 ? 2 : 0, a.ndim > 2 ? 2 : 0};
   const size_t Npad = (size_t)(a.n[0] + 2 * g[0]) * (a.n[1] + 2 * g[1]) * (a.n[2] + 2 * g[2]);
+  const unsigned n0 = (unsigned)a.n[0], n1 = (unsigned)a.n[1];
   for (size_t ci = (size_t)blockIdx.x * blockDim.x + threadIdx.x; ci < N; ci += (size_t)gridDim.x * blockDim.x) {
-    int c[3] = {(int)(ci % a.n[0]), (int)((ci / a.n[0]) % a.n[1]), (int)(ci / ((size_t)a.n[0] * a.n[1]))};
+    // (N < 2^32 cells: the grid's own limit)
+    const unsigned q = (unsigned)ci / n0;
+    int c[3] = {(int)((unsigned)ci - q * n0), (int)(q % n1), (int)(q / n1)};
+    if (!ghost_source(a.n, a.ndim, c)) continue;  // finished by the last direction's pass
     T U[NV], Ub[NV], Wb[NV];
 #pragma unroll
     for (int k = 0; k < NV; k++) {
@@ -410,10 +574,16 @@ msh_status reverse_sweep(msh_grid *g, const T *ck, int64_t nsteps, const double 
         a.d = d;
         const long warps = (long)(N / g->n[d]) * ((g->n[d] + 4 + kAdjSeg - 1) / kAdjSeg);
         const int blocks = (int)std::min<long>((warps + 7) / 8, 1L << 20);
-        if (d == 0) adj_pencil_kernel<T, 0><<<blocks, 256, 0, g->stream>>>(a);
-        else if (d == 1) adj_pencil_kernel<T, 1><<<blocks, 256, 0, g->stream>>>(a);
-        else adj_pencil_kernel<T, 2><<<blocks, 256, 0, g->stream>>>(a);
-        A_TRY(cudaGetLastError());
+        if (d == 0) {
+          if (g->ndim == 1) adj_pencil_kernel<T, 0, true><<<blocks, 256, 0, g->stream>>>(a);
+          else adj_pencil_kernel<T, 0, false><<<blocks, 256, 0, g->stream>>>(a);
+          A_TRY(cudaGetLastError());
+        } else if (d == 1) {
+          if (g->ndim == 2) A_TRY((launch_adj_tile<T, 1, true>(a, g->stream)));
+          else A_TRY((launch_adj_tile<T, 1, false>(a, g->stream)));
+        } else {
+          A_TRY((launch_adj_tile<T, 2, true>(a, g->stream)));
+        }
       }
       adj_fold_kernel<T><<<grid_blocks(N), 256, 0, g->stream>>>(a);
       A_TRY(cudaGetLastError());
