@@ -199,9 +199,9 @@ template <typename T> struct Eig {
     rho = w[0]; u = w[1];
     Pxx = w[4]; Pxy = w[5]; Pxz = w[6]; Pyy = w[7]; Pyz = w[8]; Pzz = w[9];
     ip = frcp(Pxx);
-    const T q = Pxx * frcp(rho);         // P_xx / rho
-    const T rs = frsqrt(q);              // 1 / cs
-    cs = q * rs;
+    const T s = frsqrt(Pxx * rho);       // 1 / sqrt(P_xx rho)
+    cs = Pxx * s;                        // sqrt(P_xx / rho)
+    const T rs = rho * s;                // 1 / cs
     cf = T(1.7320508075688772) * cs;
     a = Pxy * ip;
     b = Pxz * ip;

@@ -337,6 +337,11 @@ __global__ void __launch_bounds__(32 * BY, (BY <= 8 && !CTU ? 2 : 1)) step_tile_
   const int sx = tx + 1, sy = ty + 1;
   const bool interior = tx >= 1 && tx <= kTileX && ty >= 1 && ty <= BY - 2;
   const bool valid = interior && gx < nx && gy < ny;
+  // Rows of a tile that overhangs the grid in y: a row beyond it (gy > ny) feeds no updated
+  // cell and skips its sweeps (warp-uniform; the barriers and the staging stay); the row
+  // just above the last one (gy = ny) still reconstructs along y for that row's upper face.
+  // The corner-transport-upwind form keeps every row (its transverse terms reach along x).
+  const bool rowvalid = CTU || gy < ny, rowneed = CTU || gy <= ny;
   // CTU: the threads whose cell's face states are used (all but the four corner threads)
   const bool tneed = CTU && ((ty >= 1 && ty <= BY - 2) || (tx >= 1 && tx <= kTileX));
   // staged cells: the box without its corners (CTU: without its outer corners)
@@ -494,7 +499,7 @@ __global__ void __launch_bounds__(32 * BY, (BY <= 8 && !CTU ? 2 : 1)) step_tile_
   convert(z0);
   __syncthreads();
   T hprev[NV], Fprev[NV];
-  if (interior) {
+  if (interior && rowvalid) {
     T lo[NV];
     if constexpr (CTU) {
       // X_z of cell z0-1 in the raw slot of plane z0+1, which is staged only below; the X_x,
@@ -514,10 +519,10 @@ __global__ void __launch_bounds__(32 * BY, (BY <= 8 && !CTU ? 2 : 1)) step_tile_
     T lo[NV], hi[NV];
     if constexpr (CTU) {
       if (tneed) ctu_plane(z0, true, lo, hi);
-    } else if (interior) {
+    } else if (interior && rowvalid) {
       recon_z(z0, lo, hi);
     }
-    if (interior) {
+    if (interior && rowvalid) {
       face_flux<SCH, RETRY>(hprev, lo, fl(buf(z0 - 1), sy, sx) || fl(buf(z0), sy, sx), Fprev);
 #pragma unroll
       for (int k = 0; k < NV; k++) hprev[k] = hi[k];
@@ -540,7 +545,7 @@ __global__ void __launch_bounds__(32 * BY, (BY <= 8 && !CTU ? 2 : 1)) step_tile_
       for (int k = 0; k < NV; k++) Fg[Frame<2>::g(k)] = Fprev[k];
       v_mul(acc, Fg, idz);
     }
-    if (ty >= 1 && ty <= BY - 2) {  // x sweep, warp-uniform: one warp per row
+    if (ty >= 1 && ty <= BY - 2 && rowvalid) {  // x sweep, warp-uniform: one warp per row
       T wm[NV], w0[NV], wp[NV], lo[NV], hi[NV], hl[NV], F[NV];
       gather<T, 0, SY, SX>(pl, sy, sx - 1, wm);
       gather<T, 0, SY, SX>(pl, sy, sx, w0);
@@ -561,7 +566,7 @@ __global__ void __launch_bounds__(32 * BY, (BY <= 8 && !CTU ? 2 : 1)) step_tile_
       v_sub(F, F, Fu);
       v_fma(acc, F, idx, acc);
     }
-    const bool ycol = tx >= 1 && tx <= kTileX;
+    const bool ycol = tx >= 1 && tx <= kTileX && rowneed;
     T ylo[NV];
     if (ycol) {  // y reconstruction of this cell; its upper face state goes to shared memory
       T wm[NV], w0[NV], wp[NV], hi[NV];
@@ -599,10 +604,10 @@ __global__ void __launch_bounds__(32 * BY, (BY <= 8 && !CTU ? 2 : 1)) step_tile_
       T lo[NV], hi[NV], F[NV];
       if constexpr (CTU) {
         if (tneed) ctu_plane(z + 1, true, lo, hi);
-      } else if (interior) {
+      } else if (interior && rowvalid) {
         recon_z(z + 1, lo, hi);
       }
-      if (interior) {
+      if (interior && rowvalid) {
       face_flux<SCH, RETRY>(hprev, lo, fl(buf(z), sy, sx) || fl(buf(z + 1), sy, sx), F);
       T Fg[NV];
 #pragma unroll
@@ -615,7 +620,7 @@ __global__ void __launch_bounds__(32 * BY, (BY <= 8 && !CTU ? 2 : 1)) step_tile_
       }
     }
     __syncthreads();
-    if (interior) {
+    if (interior && rowvalid) {
 #pragma unroll
       for (int k = 0; k < NV; k++) acc[Frame<1>::g(k)] -= sXf[(k * BY + ty + 1) * 32 + tx] * idy;  // upper y face
     }
