@@ -57,6 +57,16 @@ def _case(name, oracle):
     if name == "fallback1d":
         from tests.test_oracle_pins import _extreme_tiny
         return _extreme_tiny(1), (8,), (0,), (1,), ((0, 0),), 0.8, None, 2
+    if name == "tiles2d":
+        # several x tiles of the staged pass (8 columns, the last one ragged) and three
+        # 26-position segments along y; periodic x, reflect y
+        W = _smooth((1, 61, 70), 2)
+        W[3] = 0.0
+        return W, (70, 61), (0, 0), (1, 1), ((0, 0), (2, 2)), 0.4, None, 2
+    if name == "tiles3d":
+        # segments along y and z, ragged x tiles; outflow x, periodic y, reflect/outflow z
+        W = _smooth((33, 30, 19), 3)
+        return W, (19, 30, 33), (0, 0, 0), (1, 1, 1), ((1, 1), (0, 0), (2, 1)), 0.4, None, 2
     raise KeyError(name)
 
 
@@ -74,7 +84,8 @@ def _oracle_adjoint(W, n, bc, dx, dts, lam, phi, kind):
     return g.numpy()
 
 
-@pytest.mark.parametrize("name", ["sod", "smooth2d_gravity_reflect", "turb3d", "disc", "fallback1d"])
+@pytest.mark.parametrize("name", ["sod", "smooth2d_gravity_reflect", "turb3d", "disc", "fallback1d", "tiles2d",
+                                  "tiles3d"])
 def test_adjoint_fp64_matches_oracle(msh, oracle, name):
     W, n, lo, hi, bc, cfl, phi, steps = _case(name, oracle)
     og = oracle.Grid(n, lo, hi, bc, cfl)
