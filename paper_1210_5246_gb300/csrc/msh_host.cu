@@ -582,6 +582,9 @@ msh_status msh_run_ensemble(msh_grid *g, int64_t count, const void *const *in, v
     if (status) status[k] = hs[(size_t)k];
     if (hs[(size_t)k] != 0 && first_bad < 0) first_bad = k;
   }
+  for (int64_t k = 0; k < count; k++)
+    if (hs[(size_t)k] == MSH_E_TIMEOUT)
+      return fail(MSH_E_TIMEOUT, "ensemble state %lld: a step kernel gave up waiting for a bulk copy", (long long)k);
   if (first_bad >= 0)
     return fail(MSH_E_REALIZABILITY, "ensemble state %lld is not realizable (input or result)", (long long)first_bad);
   return MSH_OK;
@@ -748,6 +751,8 @@ msh_status msh_step(msh_grid *g, double dt_max, double *dt_taken) {
   st = read_ctrl(g);
   if (st) return st;
   if (dt_taken) *dt_taken = g->hctrl->dt_last;
+  if (g->hctrl->status == MSH_E_TIMEOUT)
+    return fail(MSH_E_TIMEOUT, "a step kernel gave up waiting for a bulk copy of its staged planes");
   if (g->hctrl->status == MSH_E_REALIZABILITY)
     return fail(MSH_E_REALIZABILITY, "step produced a non-realizable cell %lld", (long long)g->hctrl->first_bad);
   return MSH_OK;
@@ -813,6 +818,8 @@ msh_status msh_run(msh_grid *g, double t_end, int64_t max_steps, int64_t *steps,
   }
   if (steps) *steps = g->hctrl->step - s0;
   if (t_out) *t_out = g->hctrl->t;
+  if (g->hctrl->status == MSH_E_TIMEOUT)
+    return fail(MSH_E_TIMEOUT, "a step kernel gave up waiting for a bulk copy of its staged planes");
   if (g->hctrl->status == MSH_E_REALIZABILITY)
     return fail(MSH_E_REALIZABILITY, "non-realizable cell %lld at step %lld", (long long)g->hctrl->first_bad,
                 (long long)g->hctrl->step);
@@ -973,6 +980,8 @@ msh_status msh_step_dt(msh_grid *g, double dt, int32_t *tagged_cells) {
   if (st) return st;
   g->dt_stale = false;  // the finalize planned from the new state
   if (tagged_cells) *tagged_cells = g->hctrl->last_tagged;
+  if (g->hctrl->status == MSH_E_TIMEOUT)
+    return fail(MSH_E_TIMEOUT, "a step kernel gave up waiting for a bulk copy of its staged planes");
   if (g->hctrl->status == MSH_E_REALIZABILITY)
     return fail(MSH_E_REALIZABILITY, "step produced a non-realizable cell %lld", (long long)g->hctrl->first_bad);
   return MSH_OK;
@@ -1051,6 +1060,8 @@ msh_status msh_step_end(msh_grid *g, int32_t *tagged_cells) {
   if (st) return st;
   g->dt_stale = false;
   if (tagged_cells) *tagged_cells = g->hctrl->last_tagged;
+  if (g->hctrl->status == MSH_E_TIMEOUT)
+    return fail(MSH_E_TIMEOUT, "a step kernel gave up waiting for a bulk copy of its staged planes");
   if (g->hctrl->status == MSH_E_REALIZABILITY)
     return fail(MSH_E_REALIZABILITY, "step produced a non-realizable cell %lld", (long long)g->hctrl->first_bad);
   return MSH_OK;

@@ -42,6 +42,8 @@ struct Ctrl {
   int64_t tape_base, tape_len;
   int32_t last_tagged;  // cells the a-posteriori fallback tagged in the last step
   int32_t sg_hist;      // self-gravity: the previous step's acceleration is stored
+  int32_t stage_timeout;  // a 3D step kernel's bounded wait for a bulk tensor copy ran out
+                          // (the step's result is void; finalize reports MSH_E_TIMEOUT)
 };
 
 // Per-thread-block partial reductions written by the step and scan kernels.
@@ -99,7 +101,7 @@ template <typename T, int SCH> cudaError_t launch_step_ctu(const StepArgs<T> &a,
 // stage 1 or 2 of the Kurganov-Tadmor scheme (a.U1 must be set)
 template <typename T> cudaError_t launch_step_kt(const StepArgs<T> &a, int ndim, int rows, int stage, cudaStream_t s);
 template <typename T> int step_blocks(int ndim, int rows, int nx, int ny, int nz, int zchunk);
-template <typename T> size_t step_smem(int ndim, int rows, bool ctu);
+template <typename T> size_t step_smem(int ndim, int rows, bool ctu, bool retry);
 // partials of cells [c0, c1) (c1 = 0: all N); maxf: the corner-transport-upwind CFL speed
 template <typename T> cudaError_t launch_scan(const T *U, size_t N, int nx, int ny, int ndim,
                                               const double *dx, Partial *part, int nparts,

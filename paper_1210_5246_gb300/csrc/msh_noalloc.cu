@@ -121,6 +121,10 @@ msh_status noalloc_step(int ndim, const int64_t n[3], const double dx[3], const 
     set_error_text(cudaGetErrorString(e));
     return MSH_E_CUDA;
   }
+  if (out.status == MSH_E_TIMEOUT) {
+    set_error_text("msh_step_noalloc: the step kernel gave up waiting for a bulk copy of its staged planes");
+    return MSH_E_TIMEOUT;
+  }
   if (out.status == MSH_E_REALIZABILITY) {
     char msg[160];
     snprintf(msg, sizeof msg, "msh_step_noalloc: %s (first cell %lld)",

@@ -100,6 +100,11 @@ __global__ void __launch_bounds__(kFinalizeThreads) finalize_kernel(Ctrl *ctrl, 
   }
   if (t != 0) return;
   Ctrl *c = ctrl;
+  if (mode == 0 && c->stage_timeout) {  // the step kernel gave up waiting for staged data
+    c->status = 5;                     // MSH_E_TIMEOUT
+    c->done = 1;
+    return;
+  }
   for (int k = 0; k < NV; k++) c->totals[k] = sd[0][k];
   const long long b = sb[0];
   c->realizable = (b == LLONG_MAX);
@@ -137,6 +142,7 @@ __global__ void set_dt_kernel(Ctrl *c, double dt) {
   c->dt_max = INFINITY;
   c->done = 0;
   c->status = 0;
+  c->stage_timeout = 0;
   c->force = 0;
   for (int p = 0; p <= kFallbackPasses; p++) c->nbad[p] = 0;
   c->dt = dt;
@@ -203,6 +209,7 @@ __global__ void run_start_kernel(Ctrl *c, double t_end, int64_t max_steps, doubl
   c->dt_max = dt_max;
   c->done = 0;
   c->status = 0;
+  c->stage_timeout = 0;
   c->force = 0;
   for (int p = 0; p <= kFallbackPasses; p++) c->nbad[p] = 0;
   plan(c);
@@ -229,6 +236,7 @@ __global__ void ensemble_start_kernel(Ctrl *c, int64_t step_base, int64_t nsteps
   c->dt_max = INFINITY;
   c->done = 0;
   c->status = 0;
+  c->stage_timeout = 0;
   plan(c);
 }
 
@@ -310,7 +318,7 @@ template <typename T> cudaError_t launch_convert(T *U, size_t N, int to_primitiv
 #define MSH_INST(T)                                                                                   \
   template cudaError_t launch_step<T>(const StepArgs<T> &, int, int, bool, cudaStream_t, int *);     \
   template int step_blocks<T>(int, int, int, int, int, int);                                         \
-  template size_t step_smem<T>(int, int, bool);                                                          \
+  template size_t step_smem<T>(int, int, bool, bool);                                                    \
   template cudaError_t launch_scan<T>(const T *, size_t, int, int, int, const double *, Partial *, int, \
                                       cudaStream_t, size_t, size_t, bool);                           \
   template cudaError_t launch_convert<T>(T *, size_t, int, cudaStream_t);                            \

@@ -23,6 +23,12 @@
 #include <atomic>
 #include <cfloat>
 #include <climits>
+#include <cstdint>
+#include <cstring>
+#include <utility>
+
+#include <cuda.h>
+#include <cudaTypedefs.h>
 
 #include "msh_device.cuh"
 #include "msh_internal.h"
@@ -137,8 +143,14 @@ __device__ __forceinline__ void finish_cell(const StepArgs<T> &a, const T *src, 
     Un[8] += dt * (mb[1] * g[2] + g[1] * mb[2]);
     Un[9] += dt * T(2) * mb[2] * g[2];
   }
+  {  // a running pointer: one 64-bit add per field instead of an index product
+    T *d = Ud + c;
 #pragma unroll
-  for (int k = 0; k < NV; k++) Ud[k * N + c] = Un[k];
+    for (int k = 0; k < NV; k++) {
+      *d = Un[k];
+      d += N;
+    }
+  }
   T W[NV];
   cons_to_prim(Un, W);
   if (!realizable(W)) {
@@ -257,19 +269,79 @@ __global__ void __launch_bounds__(kTile1D) step1d_kernel(StepArgs<T> a) {
 // terms instead).
 template <typename T, int BY, bool CTU = false>
 constexpr int kRawPlanes = (sizeof(T) == 4 && BY == 16 && !CTU) ? 4 : 2;
-// Asynchronous global -> shared copy of one element (cp.async, completion tracked per
-// thread by commit groups).
-template <typename T> __device__ __forceinline__ void cp_async_elem(T *smem, const T *gmem) {
-  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
-  if constexpr (sizeof(T) == 4)
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem) : "memory");
-  else
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem) : "memory");
+// Asynchronous global -> shared copies (cp.async, completion tracked per thread by commit
+// groups).
+// The NV fields of one staged cell: field k lands at byte k * FSTRIDE past the shared address
+// s (immediate offsets) and comes from g + k N (a running pointer: one 64-bit add per field
+// instead of an index product).
+template <typename T, int OFF> __device__ __forceinline__ void cp_async_at(unsigned s, const T *g) {
+  asm volatile("cp.async.ca.shared.global [%0+%2], [%1], %3;\n" ::"r"(s), "l"(g), "n"(OFF), "n"((int)sizeof(T))
+               : "memory");
+}
+template <typename T, int FSTRIDE, int... K>
+__device__ __forceinline__ void cp_async_fields(unsigned s, const T *g, size_t N, std::integer_sequence<int, K...>) {
+  ((cp_async_at<T, K * FSTRIDE>(s, g), g += N), ...);
+}
+template <typename T, int FSTRIDE> __device__ __forceinline__ void cp_async_cell(T *smem, const T *g, size_t N) {
+  cp_async_fields<T, FSTRIDE>((unsigned)__cvta_generic_to_shared(smem), g, N, std::make_integer_sequence<int, NV>{});
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 // wait until at most N of this thread's most recent groups are pending
 template <int N> __device__ __forceinline__ void cp_async_wait() {
   asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+// Bulk tensor staging of the 3D kernel.  The state is a 4D tensor [NV][nz][ny][nx]; one
+// copy moves a box of kTmaBoxX x (rows + 2) x 1 plane x NV fields into a raw staging slot
+// ([NV][rows+2][kTmaBoxX], dense) and completes the transaction count of the slot's
+// mbarrier.  The box starts at a multiple of 4 cells in x (16-byte rule of the copy), so
+// it is two columns wider than the 34 the tile needs.  Tensor maps: one per state buffer
+// (U[0], U[1], U1), passed as a grid-constant kernel parameter.
+constexpr int kTmaBoxX = 36;
+struct TileMaps {
+  CUtensorMap map[3];
+  int ok;  // 1: the maps are valid and interior tiles stage by bulk tensor copies
+};
+__device__ __forceinline__ unsigned smem_u32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(uint64_t *bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+// make initialised mbarriers visible to the other threads and to the copy engine
+__device__ __forceinline__ void mbar_init_fence() {
+  asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+}
+// order this thread's earlier shared-memory accesses before later bulk copies into it
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory"); }
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Wait for the phase of `bar` with parity `parity`; false if it has not completed within
+// 2^31 clocks (about a second), so a copy that never lands cannot hang the kernel.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, unsigned parity) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const long long t0 = clock64();
+  while (!mbar_try_wait(bar, parity)) {
+    if (clock64() - t0 > (1ll << 31)) return false;
+  }
+  return true;
+}
+__device__ __forceinline__ void tma_load_4d(void *dst, const CUtensorMap *map, int x, int y, int z, int f,
+                                            uint64_t *bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cta.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], "
+      "[%6];\n" ::"r"(smem_u32(dst)),
+      "l"(map), "r"(x), "r"(y), "r"(z), "r"(f), "r"(smem_u32(bar))
+      : "memory");
 }
 
 template <typename T, int D, int SY, int SX>
@@ -285,11 +357,20 @@ __device__ __forceinline__ void gather(const T *__restrict__ pl, int sy, int sx,
 // transverse terms of its cell plane by plane, and the sums each sweep needs, X_x = T_y +
 // T_z and X_y = T_x + T_z, wait in thread-private shared memory from the plane before.
 template <typename T, int NDIM, int BY, int SCH, bool RETRY, bool CTU = false>
-__global__ void __launch_bounds__(32 * BY, (BY <= 8 && !CTU ? 2 : 1)) step_tile_kernel(StepArgs<T> a) {
+__global__ void __launch_bounds__(32 * BY, (BY <= 8 && !CTU ? 2 : 1))
+    step_tile_kernel(StepArgs<T> a, const __grid_constant__ TileMaps tm) {
   static_assert(NDIM == 3, "the 2D step runs in step_strip2d_kernel");
+  static_assert(kTileX % 2 == 0, "bulk-copy boxes start at most two cells before the staged box");
   constexpr int SX = 34, SY = BY + 2, NQ = SY * SX;
-  constexpr int PL = NV * NQ;  // one staged plane, all fields: [NV][SY][SX]
+  constexpr int PL = NV * NQ;  // one primitive plane, all fields: [NV][SY][SX]
   constexpr int RAW = kRawPlanes<T, BY, CTU>;  // raw staging slots (4: U^n of the update from shared memory)
+  // Raw slots: [NV][SY][RSX].  The step stages interior tiles by bulk tensor copies (rows
+  // RSX = kTmaBoxX wide, slots 128-byte aligned); the fallback passes and the
+  // corner-transport-upwind form stage cell by cell (rows of SX).
+  constexpr bool kTma = !RETRY && !CTU;
+  constexpr int RSX = kTma ? kTmaBoxX : SX, RNQ = SY * RSX;
+  constexpr int RSTR = kTma ? (NV * RNQ * (int)sizeof(T) + 127) / 128 * 128 / (int)sizeof(T) : NV * RNQ;
+  constexpr unsigned kTmaBytes = (unsigned)(kTmaBoxX * SY * NV * sizeof(T));
   const Ctrl *ctrl = a.ctrl;
   if (ctrl->done) return;
   if (RETRY && ctrl->nbad[a.level - 1] == 0 && !((ctrl->force >> a.level) & 1)) return;
@@ -307,22 +388,41 @@ __global__ void __launch_bounds__(32 * BY, (BY <= 8 && !CTU ? 2 : 1)) step_tile_
   const T nuy = (T)(0.5 * dtd / a.dx[1]), idy = (T)(1.0 / a.dx[1]);
   const T nuz = (T)(0.5 * dtd / a.dx[2]), idz = (T)(1.0 / a.dx[2]);
   T *const ck = (RETRY || SCH != 0) ? nullptr : tape_slot(a, step, (size_t)a.nx * a.ny * a.nz);
-  // shared memory: three primitive planes (ring), RAW raw conserved planes filled by
-  // cp.async one plane ahead, the y-sweep face states and fluxes, per staged cell the sign
-  // flips of reflect images (bits 0..9) and the fallback tag (bit 16), and per staged
-  // position of the tile its x/y reflect flips, which are the same for every plane
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  T *sW = reinterpret_cast<T *>(smem_raw);
-  T *sR = sW + 3 * PL;
-  T *sXh = sR + RAW * PL;        // [NV][BY][32]
+  // shared memory: RAW raw conserved planes filled one plane ahead (bulk tensor copies or
+  // cp.async), three primitive planes (ring), the y-sweep face states and fluxes, per staged
+  // cell of the cell-by-cell staging the sign flips of reflect images (bits 0..9) and the
+  // fallback tag (bit 10), and per staged position of the tile its x/y reflect flips, which
+  // are the same for every plane
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  T *sR = reinterpret_cast<T *>(smem_raw);
+  T *sW = sR + RAW * RSTR;
+  T *sXh = sW + 3 * PL;          // [NV][BY][32]
   T *sXf = sXh + NV * BY * 32;   // [NV][BY][32]
   T *sCx = sXf + NV * BY * 32;   // CTU: X_x of the thread's cell, [NV][BY * 32]
   T *sCy = sCx + (CTU ? NV * BY * 32 : 0);  // CTU: X_y, [NV][BY * 32]
-  unsigned *sMeta = reinterpret_cast<unsigned *>(sCy + (CTU ? NV * BY * 32 : 0));  // [RAW][NQ]
-  unsigned *sFxy = sMeta + RAW * NQ;  // [NQ]
+  uint16_t *sMeta = reinterpret_cast<uint16_t *>(sCy + (CTU ? NV * BY * 32 : 0));  // [RAW][NQ]
+  uint16_t *sFxy = sMeta + RAW * NQ;  // [NQ]
+  // one mbarrier per raw slot (bulk tensor staging)
+  __shared__ __align__(8) uint64_t sBar[kTma ? RAW : 1];
   auto slot = [](int p) { return ((p % RAW) + RAW) % RAW; };
+  // raw-slot index of staged position i (row pitch RSX instead of SX)
+  auto rawi = [](int i) { return RSX == SX ? i : i + (i / SX) * (RSX - SX); };
   const int tx = threadIdx.x, ty = threadIdx.y;
   const int tid = ty * 32 + tx;
+  // Bulk tensor staging: on when the maps are valid (block-uniform); the mbarriers keep their
+  // phases across the tiles of a block, tracked by parity bits per slot (every thread waits
+  // for every copy; thread 0 issues them).
+  const bool tma_on = kTma && tm.ok != 0 && (smem_u32(smem_raw) & 127u) == 0;
+  unsigned tma_ph = 0, tma_iss = 0;
+  bool tma_dead = false;  // a wait ran out: no more copies are issued or waited for
+  if (kTma && tma_on) {
+    if (tid == 0) {
+#pragma unroll
+      for (int q = 0; q < (kTma ? RAW : 1); q++) mbar_init(&sBar[q], 1);
+      mbar_init_fence();
+    }
+    __syncthreads();
+  }
   const int nx = a.nx, ny = a.ny, nz = a.nz;
   const size_t N = (size_t)nx * ny * nz;
   // One thread block per tile for the step; the fallback passes run on a small grid that
@@ -337,6 +437,11 @@ __global__ void __launch_bounds__(32 * BY, (BY <= 8 && !CTU ? 2 : 1)) step_tile_
   const int sx = tx + 1, sy = ty + 1;
   const bool interior = tx >= 1 && tx <= kTileX && ty >= 1 && ty <= BY - 2;
   const bool valid = interior && gx < nx && gy < ny;
+  // a tile whose staged box lies inside the grid in x and y takes one bulk tensor copy per
+  // plane (box from xs, the staged box at column xo of it); the others map their cells one
+  // by one (periodic wrap, mirror images)
+  const bool use_tma = tma_on && x0 >= 2 && x0 + kTileX + 1 < nx && y0 >= 2 && y0 + BY - 1 < ny;
+  const int xs = (x0 - 2) & ~3, xo = use_tma ? x0 - 2 - xs : 0;
   // Rows of a tile that overhangs the grid in y: a row beyond it (gy > ny) feeds no updated
   // cell and skips its sweeps (warp-uniform; the barriers and the staging stay); the row
   // just above the last one (gy = ny) still reconstructs along y for that row's upper face.
@@ -374,8 +479,20 @@ __global__ void __launch_bounds__(32 * BY, (BY <= 8 && !CTU ? 2 : 1)) step_tile_
   auto stage = [&](int z) {
     bool mz = false;
     const int zz = map_index(z, nz, a.bc[4], a.bc[5], mz);
-    T *dst = sR + slot(z) * PL;
-    unsigned *meta = sMeta + slot(z) * NQ;
+    if constexpr (kTma) {
+      if (use_tma) {  // thread 0 issues the plane's copy; every thread waits for it in convert
+        if (tid == 0 && !tma_dead) {
+          const int q = slot(z);
+          fence_proxy_async();  // the slot's last reads (before the barrier) precede the copy
+          mbar_expect_tx(&sBar[q], kTmaBytes);
+          tma_load_4d(sR + q * RSTR, &tm.map[SCH == 2 ? 2 : (int)(step & 1)], xs, y0 - 2, zz, 0, &sBar[q]);
+          tma_iss ^= 1u << q;
+        }
+        return;
+      }
+    }
+    T *dst = sR + slot(z) * RSTR;
+    uint16_t *meta = sMeta + slot(z) * NQ;
     const size_t zoff = (size_t)zz * ny * nx;
     const unsigned fz = mz ? flip_mask(2) : 0u;
 #pragma unroll
@@ -383,27 +500,41 @@ __global__ void __launch_bounds__(32 * BY, (BY <= 8 && !CTU ? 2 : 1)) step_tile_
       if (soff[j] < 0) continue;
       const int i = tid + j * 32 * BY;
       const size_t c = zoff + (size_t)soff[j];
-#pragma unroll
-      for (int k = 0; k < NV; k++) cp_async_elem(dst + k * NQ + i, Us + k * N + c);
+      cp_async_cell<T, RNQ * (int)sizeof(T)>(dst + rawi(i), Us + c, N);
       unsigned m = sFxy[i] ^ fz;
-      if (RETRY && tagged(a.flags[c], tag, a.level)) m |= 1u << 16;
-      meta[i] = m;
+      if (RETRY && tagged(a.flags[c], tag, a.level)) m |= 1u << 10;
+      meta[i] = (uint16_t)m;
     }
     cp_async_commit();
   };
   auto convert = [&](int z) {  // raw plane z -> primitive plane in ring slot z mod 3
-    const T *src = sR + slot(z) * PL;
-    const unsigned *meta = sMeta + slot(z) * NQ;
+    const int q = slot(z);
+    const T *src = sR + q * RSTR;
+    const uint16_t *meta = sMeta + q * NQ;
     const int b = ((z % 3) + 3) % 3;
     T *dst = sW + b * PL;
+    unsigned mt = 0u;  // a bulk-copied plane: its cells' flips (a mirror plane in z) are the same
+    if constexpr (kTma) {
+      if (use_tma) {
+        if (!tma_dead && !mbar_wait_bounded(&sBar[q], (tma_ph >> q) & 1u)) {
+          tma_dead = true;
+          atomicExch(&a.ctrl->stage_timeout, 1);
+        }
+        tma_ph ^= 1u << q;
+        bool mz = false;
+        (void)map_index(z, nz, a.bc[4], a.bc[5], mz);
+        mt = mz ? flip_mask(2) : 0u;
+      }
+    }
 #pragma unroll
     for (int j = 0; j < 2; j++) {
       if (soff[j] < 0) continue;
       const int i = tid + j * 32 * BY;
-      const unsigned m = meta[i];
+      const unsigned m = (kTma && use_tma) ? mt : (unsigned)meta[i];
+      const int ri = rawi(i) + xo;
       T U[NV], W[NV];
 #pragma unroll
-      for (int k = 0; k < NV; k++) U[k] = src[k * NQ + i];
+      for (int k = 0; k < NV; k++) U[k] = src[k * RNQ + ri];
       if (m & 0x3ffu) {  // a reflect image (never inside a periodic or outflow grid)
 #pragma unroll
         for (int k = 0; k < NV; k++) U[k] = ((m >> k) & 1u) ? -U[k] : U[k];
@@ -411,7 +542,7 @@ __global__ void __launch_bounds__(32 * BY, (BY <= 8 && !CTU ? 2 : 1)) step_tile_
       cons_to_prim(U, W);
 #pragma unroll
       for (int k = 0; k < NV; k++) dst[k * NQ + i] = W[k];
-      if (RETRY) sFl[RETRY ? b : 0][i] = (m >> 16) & 1u;
+      if (RETRY) sFl[RETRY ? b : 0][i] = (m >> 10) & 1u;
     }
   };
   auto buf = [](int p) { return ((p % 3) + 3) % 3; };
@@ -476,7 +607,7 @@ __global__ void __launch_bounds__(32 * BY, (BY <= 8 && !CTU ? 2 : 1)) step_tile_
   // data here (its plane is converted and the next copy into it comes after the next
   // barrier), in the thread's own cells.
   auto ctu_plane = [&](int p, bool keep, T (&lo)[NV], T (&hi)[NV]) {
-    T *xz = sR + slot(p + 1) * PL;
+    T *xz = sR + slot(p + 1) * RSTR;
     trans_x_y(p, xz);
     recon_z_ctu(p, xz, keep, lo, hi);
   };
@@ -494,6 +625,10 @@ __global__ void __launch_bounds__(32 * BY, (BY <= 8 && !CTU ? 2 : 1)) step_tile_
   cp_async_wait<0>();
   convert(z0 - 2);
   convert(z0 - 1);
+  // two raw slots: plane z0 takes the slot of plane z0-2, which a bulk copy may overwrite
+  // only after every thread has converted it (cell-by-cell staging rewrites only the
+  // thread's own cells)
+  if (RAW == 2 && use_tma) __syncthreads();
   stage(z0);
   cp_async_wait<0>();
   convert(z0);
@@ -627,7 +762,7 @@ __global__ void __launch_bounds__(32 * BY, (BY <= 8 && !CTU ? 2 : 1)) step_tile_
     if (valid) {
       const size_t c = ((size_t)z * ny + gy) * nx + gx;
       if (RAW == 4)  // the swept state as staged (an interior cell is never a reflect image)
-        finish_cell<T, NDIM, SCH, RETRY, CTU>(a, sR + slot(z) * PL + sy * SX + sx, NQ, U0 + c, Ud, N, c, acc, dt,
+        finish_cell<T, NDIM, SCH, RETRY, CTU>(a, sR + slot(z) * RSTR + sy * RSX + sx + xo, RNQ, U0 + c, Ud, N, c, acc, dt,
                                               idx, idy, idz, diag, smax, bad, tag, ck);
       else
         finish_cell<T, NDIM, SCH, RETRY, CTU>(a, Us + c, N, U0 + c, Ud, N, c, acc, dt, idx, idy, idz, diag, smax,
@@ -644,6 +779,11 @@ __global__ void __launch_bounds__(32 * BY, (BY <= 8 && !CTU ? 2 : 1)) step_tile_
   cp_async_wait<0>();
   write_partial<T, 32 * BY>(diag, smax, bad, a.part + tile);
   __syncthreads();  // the next tile restages every buffer
+  }
+  if (kTma && tma_on && tid == 0 && tma_dead) {
+    // a wait ran out: let copies still in flight land (bounded) before the block exits
+#pragma unroll
+    for (int q = 0; q < (kTma ? RAW : 1); q++) (void)mbar_wait_bounded(&sBar[q], ((tma_iss >> q) & 1u) ^ 1u);
   }
 }
 
@@ -865,16 +1005,80 @@ inline cudaError_t set_smem_once(std::atomic<uint64_t> &done, const void *kernel
   return e;
 }
 
-// 3D: 3 + RAW staged planes (three primitive, RAW raw) of NV x (rows+2) x 34, the y-sweep
-// face states and fluxes (2 x NV x rows x 32), with CTU the per-thread X_x and X_y
-// (2 x NV x rows x 32), RAW planes of per-cell flags and the tile's x/y flips ((rows+2) x
-// 34 words).
-template <typename T> size_t step_smem(int ndim, int rows, bool ctu) {
+// 3D: RAW raw slots of NV x (rows+2) x 34 (the step: x kTmaBoxX, each rounded up to 128
+// bytes), three primitive planes of NV x (rows+2) x 34, the y-sweep face states and fluxes
+// (2 x NV x rows x 32), with CTU the per-thread X_x and X_y (2 x NV x rows x 32), RAW planes
+// of per-cell flags and the tile's x/y flips ((rows+2) x 34 half-words).
+template <typename T> size_t step_smem(int ndim, int rows, bool ctu, bool retry) {
   if (ndim < 3) return 0;
   const size_t nq = (size_t)(rows + 2) * 34;
   const size_t raw = ctu ? 2 : rows == 16 ? kRawPlanes<T, 16> : rows == 8 ? kRawPlanes<T, 8> : kRawPlanes<T, 4>;
+  const bool tma = !ctu && !retry;
+  const size_t slot = tma ? ((size_t)NV * (rows + 2) * kTmaBoxX * sizeof(T) + 127) / 128 * 128 : NV * nq * sizeof(T);
   const size_t per_thread = ctu ? 4 : 2;
-  return sizeof(T) * ((3 + raw) * NV * nq + per_thread * NV * rows * 32) + (raw + 1) * nq * sizeof(unsigned);
+  return raw * slot + sizeof(T) * (3 * NV * nq + per_thread * NV * rows * 32) + (raw + 1) * nq * sizeof(uint16_t);
+}
+
+// The driver's tensor-map encoder, looked up once per process (nullptr if unavailable:
+// the step then stages every tile cell by cell).
+inline PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static const PFN_cuTensorMapEncodeTiled_v12000 fn = [] {
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) !=
+            cudaSuccess ||
+        q != cudaDriverEntryPointSuccess) {
+      (void)cudaGetLastError();
+      return (PFN_cuTensorMapEncodeTiled_v12000) nullptr;
+    }
+    return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }();
+  return fn;
+}
+
+// Tensor maps of the state buffers for the bulk tensor staging of rows-row tiles: each
+// buffer as a [NV][nz][ny][nx] tensor of T, box kTmaBoxX x (rows+2) x 1 x NV.  ok = 0 (cell-
+// by-cell staging) when the copy's rules are not met: a buffer not 16-byte aligned, a row
+// of nx cells not a multiple of 16 bytes, or no encoder.  The last maps are kept per host
+// thread and instantiation, so repeated launches on the same buffers encode nothing.
+template <typename T, int BY> TileMaps make_tile_maps(const StepArgs<T> &a) {
+  struct Key {
+    const void *p[3];
+    int n[3];
+  };
+  static thread_local Key key{};
+  static thread_local TileMaps cached{};
+  static thread_local bool have = false;
+  const Key k = {{a.U[0], a.U[1], a.U1}, {a.nx, a.ny, a.nz}};
+  if (have && std::memcmp(&k, &key, sizeof k) == 0) return cached;
+  TileMaps tm;
+  std::memset(&tm, 0, sizeof tm);
+  const PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+  const size_t es = sizeof(T);
+  bool ok = enc != nullptr && ((size_t)a.nx * es) % 16 == 0;
+  const T *bufs[3] = {a.U[0], a.U[1], a.U1};
+  for (int i = 0; i < 3 && ok; i++) {
+    if (bufs[i] == nullptr) continue;
+    if (reinterpret_cast<uintptr_t>(bufs[i]) % 16 != 0) {
+      ok = false;
+      break;
+    }
+    const cuuint64_t dim[4] = {(cuuint64_t)a.nx, (cuuint64_t)a.ny, (cuuint64_t)a.nz, (cuuint64_t)NV};
+    const cuuint64_t str[3] = {(cuuint64_t)a.nx * es, (cuuint64_t)a.nx * a.ny * es,
+                               (cuuint64_t)a.nx * a.ny * a.nz * es};
+    const cuuint32_t box[4] = {(cuuint32_t)kTmaBoxX, (cuuint32_t)(BY + 2), 1u, (cuuint32_t)NV};
+    const cuuint32_t estr[4] = {1u, 1u, 1u, 1u};
+    const CUresult r =
+        enc(&tm.map[i], es == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 4,
+            const_cast<T *>(bufs[i]), dim, str, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) ok = false;
+  }
+  tm.ok = ok ? 1 : 0;
+  key = k;
+  cached = tm;
+  have = true;
+  return tm;
 }
 
 template <typename T> int step_blocks(int ndim, int rows, int nx, int ny, int nz, int zchunk) {
@@ -894,13 +1098,20 @@ static cudaError_t launch_tile(const StepArgs<T> &a, cudaStream_t s) {
   if constexpr (sizeof(T) == 8 && BY == 16) {
     return cudaErrorInvalidConfiguration;  // 326 KB of shared memory: not offered for FP64
   } else {
-  const size_t smem = step_smem<T>(NDIM, BY, CTU);
+  const size_t smem = step_smem<T>(NDIM, BY, CTU, RETRY);
   static std::atomic<uint64_t> attr_done{0};  // devices whose attribute is set, per instantiation
   cudaError_t e = set_smem_once(attr_done, (const void *)step_tile_kernel<T, NDIM, BY, SCH, RETRY, CTU>, smem);
   if (e != cudaSuccess) return e;
   const int ntiles = step_blocks<T>(NDIM, BY, a.nx, a.ny, a.nz, a.zchunk);
   const int blocks = RETRY ? std::min(ntiles, fallback_blocks()) : ntiles;
-  step_tile_kernel<T, NDIM, BY, SCH, RETRY, CTU><<<blocks, dim3(32, BY), smem, s>>>(a);
+  TileMaps tm;
+  if constexpr (!RETRY && !CTU) {
+    tm = make_tile_maps<T, BY>(a);
+    if (SCH == 2 && a.U1 == nullptr) tm.ok = 0;  // the second central-scheme stage sweeps U1
+  } else {
+    std::memset(&tm, 0, sizeof tm);
+  }
+  step_tile_kernel<T, NDIM, BY, SCH, RETRY, CTU><<<blocks, dim3(32, BY), smem, s>>>(a, tm);
   return cudaGetLastError();
   }
 }

@@ -1,0 +1,137 @@
+"""3D steps whose interior tiles stage their planes by bulk tensor copies, against the oracle.
+
+The 3D step stages a tile's planes with one bulk tensor copy per plane when the tile's
+staged box (x0-2 .. x0+31, y0-2 .. y0+rows-1) lies inside the grid in x and y and a row of
+nx cells is a multiple of 16 bytes; the other tiles (those at the x and y edges, whose
+staged cells wrap or mirror) stage cell by cell.  The grids here are wide enough to hold
+both kinds side by side (x tiles at x0 = 30 and 60, whose boxes start 0 and 2 cells into
+the 4-cell-aligned copy box, and y tiles inside), with every boundary kind in z (mirror
+planes take the z sign flips of the copied plane), every tiling of the step (16, 8 and 4
+rows; two raw slots for 8 and 4 rows), every scheme that stages this way (MUSCL-Hancock
+with HLL, Roe-type and HLLC fluxes, both stages of the central scheme) and a run whose
+a-posteriori fallback tags cells.  FP64 <= 1e-10 relative L_inf per field, FP32 within
+2e-4 (rho) / 5e-4 (P_ij) relative L1 of the FP64 oracle from the FP32-rounded input.
+A grid whose rows are not a multiple of 16 bytes (nx = 94 in FP32, 97 in both precisions)
+stages every tile cell by cell and must give the same answer."""
+import numpy as np
+import pytest
+
+from tests.parity import assert_fp32, assert_fp64
+from tests.test_gpu_parity import _extreme
+
+pytestmark = pytest.mark.gpu
+
+# (name in the binding, oracle scheme number, CFL)
+SCHEMES = {"MH": ("MUSCL_HANCOCK", 0, 0.5), "ROE": ("MUSCL_HANCOCK_ROE", 2, 0.5),
+           "HLLC": ("MUSCL_HANCOCK_HLLC", 3, 0.5), "KT": ("KT", 1, 0.4)}
+
+
+@pytest.fixture(scope="module")
+def msh():
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1210_5246_gb300 import msh as m
+    m.load()
+    return m
+
+
+def _state(shape, seed):
+    nz, ny, nx = shape
+    rng = np.random.default_rng(seed)
+    W = np.zeros((10, nz, ny, nx))
+    W[0] = np.exp(rng.uniform(-0.5, 0.5, (nz, ny, nx)))
+    W[1:4] = rng.uniform(-0.3, 0.3, (3, nz, ny, nx))
+    W[4], W[7], W[9] = 0.8, 0.7, 0.6
+    for k in (5, 6, 8):
+        W[k] = rng.uniform(-0.1, 0.1, (nz, ny, nx))
+    return W
+
+
+def _run(msh, oracle, n, bc, W, precision, scheme, rows, zchunk, steps):
+    name, osch, cfl = SCHEMES[scheme]
+    lo, hi = (0.0, 0.0, 0.0), (1.0, 0.5, 0.125)
+    g = msh.Grid(n, lo, hi, bc, cfl, precision)
+    if scheme != "MH":
+        g.set_scheme(getattr(msh, name))
+    g.set_tiling(rows, zchunk)
+    Wg = W.astype(np.float32) if precision == msh.FP32 else W
+    g.set_state(Wg, msh.PRIMITIVE)
+    ns, t = g.run(np.inf, steps)
+    U = g.get_state().astype(np.float64)
+    Wout = g.get_state(msh.PRIMITIVE).astype(np.float64)
+    g.close()
+    og = oracle.Grid(n, lo, hi, bc, cfl, scheme=osch)
+    Uo, no, to, rc, _ = oracle.run(og, oracle.prim_to_cons(Wg.astype(np.float64)), np.inf, max_steps=steps)
+    assert rc == 0 and ns == no == steps
+    assert abs(t - to) <= (1e-13 if precision == msh.FP64 else 1e-5) * to
+    return U, Wout, Uo, oracle.cons_to_prim(Uo)
+
+
+# z boundaries: periodic, mirror on both sides, outflow below and mirror above
+BCS = {"zper": ((0, 0), (0, 0), (0, 0)), "zrefl": ((1, 1), (0, 0), (2, 2)), "zmix": ((2, 1), (1, 2), (1, 2))}
+
+
+@pytest.mark.parametrize("bcname", sorted(BCS))
+@pytest.mark.parametrize("rows,zchunk", [(8, 5), (4, 12)])
+def test_mh_fp64_mixed_tiles(msh, oracle, bcname, rows, zchunk):
+    n = (96, 46, 12)
+    W = _state(n[::-1], 11)
+    U, _, Uo, _ = _run(msh, oracle, n, BCS[bcname], W, msh.FP64, "MH", rows, zchunk, 4)
+    assert_fp64(U, Uo, what=f"bulk-staged mh fp64 {bcname} rows={rows}")
+
+
+@pytest.mark.parametrize("bcname", sorted(BCS))
+@pytest.mark.parametrize("rows,zchunk", [(16, 5), (8, 12), (4, 3)])
+def test_mh_fp32_mixed_tiles(msh, oracle, bcname, rows, zchunk):
+    n = (96, 46, 12)
+    W = _state(n[::-1], 12)
+    _, Wg, _, Wo = _run(msh, oracle, n, BCS[bcname], W, msh.FP32, "MH", rows, zchunk, 4)
+    assert_fp32(Wg, Wo, what=f"bulk-staged mh fp32 {bcname} rows={rows}")
+
+
+@pytest.mark.parametrize("scheme", ["ROE", "HLLC", "KT"])
+@pytest.mark.parametrize("precision", ["FP64", "FP32"])
+def test_other_schemes_mixed_tiles(msh, oracle, scheme, precision):
+    n = (96, 46, 10)
+    W = _state(n[::-1], 13)
+    if scheme == "ROE":  # eigenvalues off zero (the upwind tracing switches at zero speed)
+        W[1] += 0.25
+        W[2] -= 0.15
+    p = getattr(msh, precision)
+    rows = 16 if precision == "FP32" else 8
+    U, Wg, Uo, Wo = _run(msh, oracle, n, BCS["zmix"], W, p, scheme, rows, 4, 3)
+    if precision == "FP64":
+        assert_fp64(U, Uo, what=f"bulk-staged {scheme} fp64")
+    else:
+        assert_fp32(Wg, Wo, what=f"bulk-staged {scheme} fp32")
+
+
+@pytest.mark.parametrize("nx", [94, 97])
+@pytest.mark.parametrize("precision", ["FP64", "FP32"])
+def test_rows_off_the_copy_alignment(msh, oracle, nx, precision):
+    n = (nx, 40, 8)
+    W = _state(n[::-1], nx)
+    p = getattr(msh, precision)
+    U, Wg, Uo, Wo = _run(msh, oracle, n, BCS["zrefl"], W, p, "MH", 16 if precision == "FP32" else 8, 8, 3)
+    if precision == "FP64":
+        assert_fp64(U, Uo, what=f"nx={nx} fp64")
+    else:
+        assert_fp32(Wg, Wo, what=f"nx={nx} fp32")
+
+
+def test_fallback_with_bulk_staged_tiles_fp64(msh, oracle):
+    """Extreme states over 3 steps of the oracle's dt schedule: the step stages by bulk
+    copies, the fallback passes (which tag cells here) stage cell by cell."""
+    n = (92, 44, 8)
+    W = _extreme(n[::-1], 5)
+    bc = ((0, 0), (1, 2), (2, 2))
+    og = oracle.Grid(n, (0, 0, 0), (1, 1, 1), bc, 0.5)
+    Uo, no, to, rc, dts = oracle.run(og, oracle.prim_to_cons(W), np.inf, max_steps=3, record=True)
+    assert rc == 0 and no == 3
+    g = msh.Grid(n, (0, 0, 0), (1, 1, 1), bc, 0.5, msh.FP64)
+    g.set_tiling(8, 8)
+    g.set_state(W, msh.PRIMITIVE)
+    tagged = [g.step_dt(float(dt)) for dt in dts]
+    assert sum(tagged) > 0, "the extreme state should make the fallback tag cells"
+    assert_fp64(g.get_state(), Uo, what="bulk-staged fallback fp64")
+    g.close()
