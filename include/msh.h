@@ -183,11 +183,14 @@ msh_status msh_get_dt_history(msh_grid *g, double *dts, int64_t capacity, int64_
 
 /*
  * Tile shape of the 2D/3D step kernels.  3D: `rows` = thread rows per block (4, 8 or 16,
- * each a warp of 32 cells in x) and `zchunk` = z planes each block streams.  2D: `rows` =
- * warps per block (4, 8 or 16, each a strip of 28 updated columns) and `zchunk` = grid
- * rows each warp streams in y.  1D ignores both.  `zchunk` >= 1, clipped to the streamed
- * axis.  3D FP64 grids take rows 4 or 8 (rows 16 would need more shared memory than a
- * thread block has).  Defaults: rows 8; zchunk 32 (3D) or 16 (2D).  msh_autotune times
+ * each a warp of 32 cells in x) and `zchunk` = z planes each block streams, or 0 for the
+ * balanced tiling: one block per block slot of the device's SMs, each streaming the same
+ * number of planes (whole columns of tiles first, then equal runs of the rest, at least 8
+ * planes each).  2D: `rows` = warps per block (4, 8 or 16, each a strip of 28 updated
+ * columns) and `zchunk` = grid rows each warp streams in y.  1D ignores both.  `zchunk` >=
+ * 1 (3D: >= 0), clipped to the streamed axis.  3D FP64 grids take rows 4 or 8 (rows 16
+ * would need more shared memory than a thread block has).  Defaults: rows 8; zchunk 0
+ * (3D) or 16 (2D).  msh_autotune times
  * the candidates on this grid's current state (without changing it or the tape) and keeps
  * the fastest; the chosen values are returned in *rows / *zchunk (may be NULL).
  */

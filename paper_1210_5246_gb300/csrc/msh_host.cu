@@ -1140,7 +1140,8 @@ msh_status msh_set_tiling(msh_grid *g, int32_t rows, int32_t zchunk) {
   if (rows != 4 && rows != 8 && rows != 16) return fail(MSH_E_INVALID_ARG, "rows must be 4, 8 or 16");
   if (rows == 16 && g->ndim == 3 && g->prec == MSH_FP64)
     return fail(MSH_E_INVALID_ARG, "rows 16 in 3D needs FP32 (its FP64 staging exceeds shared memory)");
-  if (zchunk < 1) return fail(MSH_E_INVALID_ARG, "zchunk must be >= 1");
+  if (zchunk < 0 || (zchunk == 0 && g->ndim != 3))
+    return fail(MSH_E_INVALID_ARG, "zchunk must be >= 1 (or 0 in 3D: the balanced tiling)");
   const int64_t stream_len = g->ndim == 3 ? g->n[2] : g->ndim == 2 ? g->n[1] : 1;
   if (zchunk > stream_len) zchunk = (int)stream_len;
   msh_status st = ensure_partials(g, blocks_for(g, rows, zchunk));
@@ -1202,6 +1203,9 @@ msh_status msh_autotune(msh_grid *g, int32_t *rows_out, int32_t *zchunk_out) {
     for (int z : zc_c)
       if ((z <= stream_len || z == zc_c[0]) && !(r == 16 && g->ndim == 3 && g->prec == MSH_FP64))
         cands.push_back({r, z});
+  if (g->ndim == 3)  // the balanced tiling
+    for (int r : rows_c)
+      if (!(r == 16 && g->prec == MSH_FP64)) cands.push_back({r, 0});
   float best = 1e30f;
   std::pair<int, int> best_c = {g->rows, g->zchunk};
   const int reps = 3;

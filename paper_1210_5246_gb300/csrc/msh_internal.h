@@ -64,6 +64,7 @@ template <typename T> struct StepArgs {
   int bc[6];
   double dx[3];
   int zchunk;
+  int units;            // 3D: work units of the launch, one partial each (set by the launcher)
   // adjoint tape: the step kernel stores U^s in ck[(s - ck_base) / ck_K] when s - ck_base
   // is a multiple of ck_K in [0, ck_len); ck = nullptr: no tape
   T *ck;
@@ -76,9 +77,10 @@ constexpr int kTile1D = 128;   // threads per block of the 1D step kernel
 constexpr int kTileX = 30;     // interior cells per warp row of the 3D kernel
 constexpr int kStripX = 28;    // updated cells per warp strip of the 2D kernel
 
-// Default length of the chunk a thread block streams: z planes (3D) or rows (2D).
+// Default length of the chunk a thread block streams: rows (2D); 3D: 0, the balanced
+// tiling (work units of equal plane counts, one per resident block).
 inline int default_chunk(int ndim, const int64_t n[3]) {
-  if (ndim == 3) return (int)(n[2] < 32 ? n[2] : 32);
+  if (ndim == 3) return 0;
   if (ndim == 2) return (int)(n[1] < 16 ? n[1] : 16);
   return 1;
 }

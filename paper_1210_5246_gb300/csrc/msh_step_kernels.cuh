@@ -40,7 +40,7 @@ constexpr unsigned FULL = 0xffffffffu;
 // ------------------------------------------------------------ block partials
 template <int NT>
 __device__ __forceinline__ void block_partial(double (&diag)[NV], double smax, long long bad,
-                                              Partial *out) {
+                                              Partial *out, const double *base = nullptr) {
   __shared__ double red[NT / 32][NV + 1];
   __shared__ long long redb[NT / 32];
   const int lane = threadIdx.x & 31;
@@ -62,7 +62,7 @@ __device__ __forceinline__ void block_partial(double (&diag)[NV], double smax, l
   __syncthreads();
   if (tid == 0) {
     Partial p;
-    for (int k = 0; k < NV; k++) p.diag[k] = 0.0;
+    for (int k = 0; k < NV; k++) p.diag[k] = base != nullptr ? base[k] : 0.0;
     p.smax = 0.0;
     p.bad = LLONG_MAX;
     for (int w = 0; w < NT / 32; w++) {
@@ -175,6 +175,46 @@ __device__ __forceinline__ void write_partial(const Acc<T> &diag, T smax, long l
   double d[NV];
   diag.get(d);
   block_partial<NT>(d, (double)smax, bad, out);
+}
+// The same with FP64 totals `base` (block_totals) added to the threads' sums.
+template <typename T, int NT>
+__device__ __forceinline__ void write_partial(const Acc<T> &diag, T smax, long long bad, Partial *out,
+                                              const double *base) {
+  double d[NV];
+  diag.get(d);
+  block_partial<NT>(d, (double)smax, bad, out, base);
+}
+
+// FP64 running totals of a thread block, in shared memory (thread 0 writes them).
+__device__ __forceinline__ double *block_totals() {
+  __shared__ double tot[NV];
+  return tot;
+}
+
+// Move the threads' running sums into the block's FP64 totals (fixed order: warps by
+// shuffles, then thread 0 over the warps) and restart them from zero.  Every thread of the
+// block calls it.
+template <typename T, int NT> __device__ __forceinline__ void flush_totals(Acc<T> &diag, double *tot) {
+  __shared__ double red[NT / 32][NV];
+  double d[NV];
+  diag.get(d);
+  const int lane = threadIdx.x & 31;
+  const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+    for (int k = 0; k < NV; k++) d[k] += __shfl_down_sync(FULL, d[k], o);
+  }
+  if (lane == 0) {
+#pragma unroll
+    for (int k = 0; k < NV; k++) red[tid >> 5][k] = d[k];
+  }
+  __syncthreads();
+  if (tid == 0) {
+    for (int w = 0; w < NT / 32; w++)
+      for (int k = 0; k < NV; k++) tot[k] += red[w][k];
+  }
+  diag.zero();
 }
 
 // A cell takes first-order faces in fallback pass `level` if an earlier pass of this step
@@ -425,13 +465,67 @@ __global__ void __launch_bounds__(32 * BY, (BY <= 8 && !CTU ? 2 : 1))
   }
   const int nx = a.nx, ny = a.ny, nz = a.nz;
   const size_t N = (size_t)nx * ny * nz;
-  // One thread block per tile for the step; the fallback passes run on a small grid that
-  // loops over the tiles, so a pass with nothing to do costs only its launch.
+  // Work units (one partial each).  Chunked tiling (zchunk > 0): a unit is one chunk of
+  // zchunk planes of one column of tiles (x-y tile, all of z).  Balanced tiling (zchunk =
+  // 0): the columns are dealt out whole, column c to unit c mod units, as long as every unit
+  // gets one; the planes of the columns left over are ordered window by window (windows of
+  // wz planes, the share of one unit; within a window column by column, so that units
+  // running at the same time stream neighbouring columns at the same heights and share
+  // their halos in L2) and cut into `units` equal runs.  Every unit so streams the same
+  // number of planes (to one), in one to three stretches, each with its own prologue.  The
+  // step launches one thread block per unit; the fallback passes run on a small grid that
+  // loops over the units, so a pass with nothing to do costs only its launch.
   const int tilesx = (nx + kTileX - 1) / kTileX, tilesy = (ny + BY - 3) / (BY - 2);
-  const int tilesz = (nz + a.zchunk - 1) / a.zchunk;
-  const int ntiles = tilesx * tilesy * tilesz;
-  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-  const int bxi = tile % tilesx, byi = (tile / tilesx) % tilesy, bzi = tile / (tilesx * tilesy);
+  const int ncols = tilesx * tilesy, units = a.units, zc = a.zchunk;
+  const int nfull = zc > 0 ? 0 : ncols / units;
+  const int nrcol = ncols - nfull * units;  // columns left over (balanced tiling)
+  const long long nrest = zc > 0 ? 0 : (long long)nrcol * nz;
+  const int wz = zc > 0 ? 1 : (int)std::max<long long>(1, (nrest + units - 1) / units);
+  const int nwf = nz / wz, wlast = nz - nwf * wz;  // whole windows, planes of the last one
+  for (int u = blockIdx.x; u < units; u += gridDim.x) {
+  Acc<T> diag;
+  diag.zero();
+  T smax = T(0);
+  long long bad = LLONG_MAX;
+  double *const tot = block_totals();  // FP64 running totals of the unit (FP32 states)
+  if (tid == 0) {
+#pragma unroll
+    for (int k = 0; k < NV; k++) tot[k] = 0.0;
+  }
+  long long rp = nrest * u / units;
+  const long long rend = nrest * (u + 1) / units;
+  for (int item = 0;; item++) {
+  int col, z0, z1;
+  if (zc > 0) {  // chunked tiling: one chunk
+    if (item > 0) break;
+    col = u % ncols;
+    z0 = (u / ncols) * zc;
+    z1 = min(nz, z0 + zc);
+  } else if (item < nfull) {  // a whole column
+    col = u + item * units;
+    z0 = 0;
+    z1 = nz;
+  } else {  // a run of the left-over columns' planes, up to the end of its window
+    if (rp >= rend) break;
+    const long long inwhole = (long long)nrcol * wz * nwf;
+    int j, zend;
+    if (rp < inwhole) {
+      const int k = (int)(rp / ((long long)nrcol * wz));
+      const int r = (int)(rp - (long long)k * nrcol * wz);
+      j = r / wz;
+      z0 = k * wz + (r - j * wz);
+      zend = (k + 1) * wz;
+    } else {
+      const int r = (int)(rp - inwhole);
+      j = r / wlast;
+      z0 = nwf * wz + (r - j * wlast);
+      zend = nz;
+    }
+    z1 = (int)std::min<long long>(zend, z0 + (rend - rp));
+    col = nfull * units + j;
+    rp += z1 - z0;
+  }
+  const int bxi = col % tilesx, byi = col / tilesx;
   const int x0 = bxi * kTileX, y0 = byi * (BY - 2);
   const int gx = x0 - 1 + tx, gy = y0 - 1 + ty;
   const int sx = tx + 1, sy = ty + 1;
@@ -612,26 +706,32 @@ __global__ void __launch_bounds__(32 * BY, (BY <= 8 && !CTU ? 2 : 1))
     recon_z_ctu(p, xz, keep, lo, hi);
   };
 
-  Acc<T> diag;
-  diag.zero();
-  T smax = T(0);
-  long long bad = LLONG_MAX;
-  const int z0 = bzi * a.zchunk;
-  const int z1 = min(z0 + a.zchunk, nz);
   // prologue: planes z0-2 .. z0+2 converted; the z face state of cell z0 and the flux
   // through its lower face in registers
-  stage(z0 - 2);
-  stage(z0 - 1);
-  cp_async_wait<0>();
-  convert(z0 - 2);
-  convert(z0 - 1);
-  // two raw slots: plane z0 takes the slot of plane z0-2, which a bulk copy may overwrite
-  // only after every thread has converted it (cell-by-cell staging rewrites only the
-  // thread's own cells)
-  if (RAW == 2 && use_tma) __syncthreads();
-  stage(z0);
-  cp_async_wait<0>();
-  convert(z0);
+  if constexpr (RAW == 4) {  // the first four planes in flight at once
+    stage(z0 - 2);
+    stage(z0 - 1);
+    stage(z0);
+    stage(z0 + 1);
+    cp_async_wait<2>();  // this thread's copies of planes z0-2 and z0-1 have landed
+    convert(z0 - 2);
+    convert(z0 - 1);
+    cp_async_wait<1>();
+    convert(z0);
+  } else {
+    stage(z0 - 2);
+    stage(z0 - 1);
+    cp_async_wait<0>();
+    convert(z0 - 2);
+    convert(z0 - 1);
+    // two raw slots: plane z0 takes the slot of plane z0-2, which a bulk copy may overwrite
+    // only after every thread has converted it (cell-by-cell staging rewrites only the
+    // thread's own cells)
+    if (use_tma) __syncthreads();
+    stage(z0);
+    cp_async_wait<0>();
+    convert(z0);
+  }
   __syncthreads();
   T hprev[NV], Fprev[NV];
   if (interior && rowvalid) {
@@ -644,7 +744,7 @@ __global__ void __launch_bounds__(32 * BY, (BY <= 8 && !CTU ? 2 : 1))
       recon_z(z0 - 1, lo, hprev);
     }
   }
-  stage(z0 + 1);
+  if constexpr (RAW != 4) stage(z0 + 1);
   cp_async_wait<0>();
   __syncthreads();  // plane z0-2 is no longer read
   convert(z0 + 1);
@@ -775,10 +875,16 @@ __global__ void __launch_bounds__(32 * BY, (BY <= 8 && !CTU ? 2 : 1))
       cp_async_wait<0>();
       convert(z + 3);
     }
+    // FP32 states: every 64 planes the threads' FP32 sums move into the unit's FP64 totals
+    // (the barrier inside comes after every thread has finished the plane)
+    if constexpr (sizeof(T) == 4) {
+      if (((z + 1 - z0) & 63) == 0 && z + 1 < z1) flush_totals<T, 32 * BY>(diag, tot);
+    }
   }
   cp_async_wait<0>();
-  write_partial<T, 32 * BY>(diag, smax, bad, a.part + tile);
-  __syncthreads();  // the next tile restages every buffer
+  __syncthreads();  // the next stretch restages every buffer
+  }
+  write_partial<T, 32 * BY>(diag, smax, bad, a.part + u, tot);
   }
   if (kTma && tma_on && tid == 0 && tma_dead) {
     // a wait ran out: let copies still in flight land (bounded) before the block exits
@@ -1081,16 +1187,75 @@ template <typename T, int BY> TileMaps make_tile_maps(const StepArgs<T> &a) {
   return tm;
 }
 
+// SM count of the current device, looked up once per device.
+inline int device_sms() {
+  static std::atomic<int> cache[64];
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    (void)cudaGetLastError();
+    dev = -1;
+  }
+  if (dev >= 0 && dev < 64) {
+    const int c = cache[dev].load(std::memory_order_relaxed);
+    if (c > 0) return c;
+  }
+  int n = 0;
+  if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev < 0 ? 0 : dev) != cudaSuccess || n < 1) {
+    (void)cudaGetLastError();
+    n = 1;
+  }
+  if (dev >= 0 && dev < 64) cache[dev].store(n, std::memory_order_relaxed);
+  return n;
+}
+
+// Thread blocks of the rows-row 3D step kernel (MUSCL-Hancock, the step pass) resident on
+// one SM of the current device, from the occupancy calculator; looked up once per device.
+template <typename T, int BY> int resident_tiles() {
+  if constexpr (sizeof(T) == 8 && BY == 16) {
+    return 1;  // not offered
+  } else {
+    static std::atomic<int> cache[64];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+      (void)cudaGetLastError();
+      dev = -1;
+    }
+    if (dev >= 0 && dev < 64) {
+      const int c = cache[dev].load(std::memory_order_relaxed);
+      if (c > 0) return c;
+    }
+    const void *k = (const void *)step_tile_kernel<T, 3, BY, 0, false, false>;
+    const size_t smem = step_smem<T>(3, BY, false, false);
+    int nb = 0;
+    if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, 32 * BY, smem) != cudaSuccess || nb < 1) {
+      (void)cudaGetLastError();
+      nb = 1;
+    }
+    if (dev >= 0 && dev < 64) cache[dev].store(nb, std::memory_order_relaxed);
+    return nb;
+  }
+}
+
+// Work units of a 3D launch.  Chunked tiling (zchunk > 0): one per chunk of zchunk planes
+// of a column of tiles.  Balanced tiling (zchunk = 0): as many as the SMs hold step
+// blocks, but at least kMinUnitPlanes planes each and at least one.
+constexpr int kMinUnitPlanes = 8;
+template <typename T> int tile_units(int rows, int nx, int ny, int nz, int zchunk) {
+  const long long ncols = (long long)((nx + kTileX - 1) / kTileX) * ((ny + rows - 3) / (rows - 2));
+  if (zchunk > 0) return (int)(ncols * ((nz + zchunk - 1) / zchunk));
+  const int per_sm = rows == 16 ? resident_tiles<T, 16>() : rows == 8 ? resident_tiles<T, 8>() : resident_tiles<T, 4>();
+  const long long full = (long long)device_sms() * per_sm;
+  return (int)std::max<long long>(1, std::min(full, ncols * nz / kMinUnitPlanes));
+}
+
 template <typename T> int step_blocks(int ndim, int rows, int nx, int ny, int nz, int zchunk) {
   if (ndim == 1) return (nx + kTile1D - 3) / (kTile1D - 2);
   if (ndim == 2) {
     const long tiles = (long)((nx + kStripX - 1) / kStripX) * ((ny + zchunk - 1) / zchunk);
     return (int)((tiles + rows - 1) / rows);
   }
-  const int bx = (nx + kTileX - 1) / kTileX;
-  const int by = (ny + rows - 3) / (rows - 2);
-  const int bz = ndim == 3 ? (nz + zchunk - 1) / zchunk : 1;
-  return bx * by * bz;
+  return tile_units<T>(rows, nx, ny, nz, zchunk);
 }
 
 template <typename T, int NDIM, int BY, int SCH, bool RETRY, bool CTU>
@@ -1102,8 +1267,9 @@ static cudaError_t launch_tile(const StepArgs<T> &a, cudaStream_t s) {
   static std::atomic<uint64_t> attr_done{0};  // devices whose attribute is set, per instantiation
   cudaError_t e = set_smem_once(attr_done, (const void *)step_tile_kernel<T, NDIM, BY, SCH, RETRY, CTU>, smem);
   if (e != cudaSuccess) return e;
-  const int ntiles = step_blocks<T>(NDIM, BY, a.nx, a.ny, a.nz, a.zchunk);
-  const int blocks = RETRY ? std::min(ntiles, fallback_blocks()) : ntiles;
+  StepArgs<T> b = a;
+  b.units = step_blocks<T>(NDIM, BY, a.nx, a.ny, a.nz, a.zchunk);
+  const int blocks = RETRY ? std::min(b.units, fallback_blocks()) : b.units;
   TileMaps tm;
   if constexpr (!RETRY && !CTU) {
     tm = make_tile_maps<T, BY>(a);
@@ -1111,7 +1277,7 @@ static cudaError_t launch_tile(const StepArgs<T> &a, cudaStream_t s) {
   } else {
     std::memset(&tm, 0, sizeof tm);
   }
-  step_tile_kernel<T, NDIM, BY, SCH, RETRY, CTU><<<blocks, dim3(32, BY), smem, s>>>(a, tm);
+  step_tile_kernel<T, NDIM, BY, SCH, RETRY, CTU><<<blocks, dim3(32, BY), smem, s>>>(b, tm);
   return cudaGetLastError();
   }
 }

@@ -12,7 +12,10 @@ with HLL, Roe-type and HLLC fluxes, both stages of the central scheme) and a run
 a-posteriori fallback tags cells.  FP64 <= 1e-10 relative L_inf per field, FP32 within
 2e-4 (rho) / 5e-4 (P_ij) relative L1 of the FP64 oracle from the FP32-rounded input.
 A grid whose rows are not a multiple of 16 bytes (nx = 94 in FP32, 97 in both precisions)
-stages every tile cell by cell and must give the same answer."""
+stages every tile cell by cell and must give the same answer.  zchunk 0 is the balanced
+tiling (equal plane counts per block: whole columns, then runs of the rest window by
+window); a grid with more columns of tiles than the device has block slots takes both
+parts."""
 import numpy as np
 import pytest
 
@@ -72,7 +75,7 @@ BCS = {"zper": ((0, 0), (0, 0), (0, 0)), "zrefl": ((1, 1), (0, 0), (2, 2)), "zmi
 
 
 @pytest.mark.parametrize("bcname", sorted(BCS))
-@pytest.mark.parametrize("rows,zchunk", [(8, 5), (4, 12)])
+@pytest.mark.parametrize("rows,zchunk", [(8, 5), (4, 12), (8, 0)])
 def test_mh_fp64_mixed_tiles(msh, oracle, bcname, rows, zchunk):
     n = (96, 46, 12)
     W = _state(n[::-1], 11)
@@ -81,7 +84,7 @@ def test_mh_fp64_mixed_tiles(msh, oracle, bcname, rows, zchunk):
 
 
 @pytest.mark.parametrize("bcname", sorted(BCS))
-@pytest.mark.parametrize("rows,zchunk", [(16, 5), (8, 12), (4, 3)])
+@pytest.mark.parametrize("rows,zchunk", [(16, 5), (8, 12), (4, 3), (16, 0), (4, 0)])
 def test_mh_fp32_mixed_tiles(msh, oracle, bcname, rows, zchunk):
     n = (96, 46, 12)
     W = _state(n[::-1], 12)
@@ -135,3 +138,19 @@ def test_fallback_with_bulk_staged_tiles_fp64(msh, oracle):
     assert sum(tagged) > 0, "the extreme state should make the fallback tag cells"
     assert_fp64(g.get_state(), Uo, what="bulk-staged fallback fp64")
     g.close()
+
+
+@pytest.mark.parametrize("precision", ["FP64", "FP32"])
+def test_balanced_tiling_whole_columns_and_runs(msh, oracle, precision):
+    """600 x 120 x 12 cells: 20 x 9 = 180 columns of 16-row tiles (8-row in FP64: 20 x 20),
+    more than one per block slot, so blocks stream whole columns and then runs of the
+    columns left over."""
+    n = (600, 120, 12)
+    W = _state(n[::-1], 21)
+    p = getattr(msh, precision)
+    rows = 16 if precision == "FP32" else 8
+    U, Wg, Uo, Wo = _run(msh, oracle, n, BCS["zmix"], W, p, "MH", rows, 0, 3)
+    if precision == "FP64":
+        assert_fp64(U, Uo, what="balanced fp64")
+    else:
+        assert_fp32(Wg, Wo, what="balanced fp32")
