@@ -190,8 +190,9 @@ msh_status msh_get_dt_history(msh_grid *g, double *dts, int64_t capacity, int64_
  * columns) and `zchunk` = grid rows each warp streams in y.  1D ignores both.  `zchunk` >=
  * 1 (3D: >= 0), clipped to the streamed axis.  3D FP64 grids take rows 4 or 8 (rows 16
  * would need more shared memory than a thread block has).  Defaults: rows 8; zchunk 0
- * (3D) or 16 (2D).  msh_autotune times
- * the candidates on this grid's current state (without changing it or the tape) and keeps
+ * (3D) or 16 (2D).  msh_autotune times the candidates (3D: rows 4/8/16 with the balanced
+ * tiling and with chunks cutting z into 1..8 near-equal windows; 2D: rows 4/8/16 with
+ * zchunk 8..64) on this grid's current state (without changing it or the tape) and keeps
  * the fastest; the chosen values are returned in *rows / *zchunk (may be NULL).
  */
 msh_status msh_set_tiling(msh_grid *g, int32_t rows, int32_t zchunk);

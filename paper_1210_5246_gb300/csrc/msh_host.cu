@@ -1199,13 +1199,22 @@ msh_status msh_autotune(msh_grid *g, int32_t *rows_out, int32_t *zchunk_out) {
   const int rows_c[3] = {4, 8, 16};
   const int zc_c[4] = {8, 16, 32, 64};
   const int64_t stream_len = g->ndim == 3 ? g->n[2] : g->n[1];
-  for (int r : rows_c)
+  // 2D: rows of 8..64; 3D: the balanced tiling (0) and chunks that cut z into m = 1..8
+  // near-equal windows
+  std::vector<int> zcs;
+  if (g->ndim == 3) {
+    zcs.push_back(0);
+    for (int m = 1; m <= 8; m++) {
+      const int z = (int)((stream_len + m - 1) / m);
+      if (std::find(zcs.begin(), zcs.end(), z) == zcs.end()) zcs.push_back(z);
+    }
+  } else {
     for (int z : zc_c)
-      if ((z <= stream_len || z == zc_c[0]) && !(r == 16 && g->ndim == 3 && g->prec == MSH_FP64))
-        cands.push_back({r, z});
-  if (g->ndim == 3)  // the balanced tiling
-    for (int r : rows_c)
-      if (!(r == 16 && g->prec == MSH_FP64)) cands.push_back({r, 0});
+      if (z <= stream_len || z == zc_c[0]) zcs.push_back(z);
+  }
+  for (int r : rows_c)
+    for (int z : zcs)
+      if (!(r == 16 && g->ndim == 3 && g->prec == MSH_FP64)) cands.push_back({r, z});
   float best = 1e30f;
   std::pair<int, int> best_c = {g->rows, g->zchunk};
   const int reps = 3;

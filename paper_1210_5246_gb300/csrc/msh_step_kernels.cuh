@@ -335,12 +335,13 @@ template <int N> __device__ __forceinline__ void cp_async_wait() {
 // copy moves a box of kTmaBoxX x (rows + 2) x 1 plane x NV fields into a raw staging slot
 // ([NV][rows+2][kTmaBoxX], dense) and completes the transaction count of the slot's
 // mbarrier.  The box starts at a multiple of 4 cells in x (16-byte rule of the copy), so
-// it is two columns wider than the 34 the tile needs.  Tensor maps: one per state buffer
-// (U[0], U[1], U1), passed as a grid-constant kernel parameter.
+// it is two columns wider than the 34 the tile needs.  Its cells outside the grid arrive
+// as zeros (tiles at the grid's edges) and are fixed up cell by cell afterwards.  Tensor
+// maps: one per state buffer (U[0], U[1], U1), passed as a grid-constant kernel parameter.
 constexpr int kTmaBoxX = 36;
 struct TileMaps {
   CUtensorMap map[3];
-  int ok;  // 1: the maps are valid and interior tiles stage by bulk tensor copies
+  int ok;  // 1: the maps are valid and the step stages by bulk tensor copies
 };
 __device__ __forceinline__ unsigned smem_u32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
 __device__ __forceinline__ void mbar_init(uint64_t *bar, unsigned count) {
@@ -404,7 +405,7 @@ __global__ void __launch_bounds__(32 * BY, (BY <= 8 && !CTU ? 2 : 1))
   constexpr int SX = 34, SY = BY + 2, NQ = SY * SX;
   constexpr int PL = NV * NQ;  // one primitive plane, all fields: [NV][SY][SX]
   constexpr int RAW = kRawPlanes<T, BY, CTU>;  // raw staging slots (4: U^n of the update from shared memory)
-  // Raw slots: [NV][SY][RSX].  The step stages interior tiles by bulk tensor copies (rows
+  // Raw slots: [NV][SY][RSX].  The step stages by bulk tensor copies (rows
   // RSX = kTmaBoxX wide, slots 128-byte aligned); the fallback passes and the
   // corner-transport-upwind form stage cell by cell (rows of SX).
   constexpr bool kTma = !RETRY && !CTU;
@@ -430,9 +431,9 @@ __global__ void __launch_bounds__(32 * BY, (BY <= 8 && !CTU ? 2 : 1))
   T *const ck = (RETRY || SCH != 0) ? nullptr : tape_slot(a, step, (size_t)a.nx * a.ny * a.nz);
   // shared memory: RAW raw conserved planes filled one plane ahead (bulk tensor copies or
   // cp.async), three primitive planes (ring), the y-sweep face states and fluxes, per staged
-  // cell of the cell-by-cell staging the sign flips of reflect images (bits 0..9) and the
-  // fallback tag (bit 10), and per staged position of the tile its x/y reflect flips, which
-  // are the same for every plane
+  // position of the tile its x/y reflect flips (the same for every plane) and, for the
+  // cell-by-cell staging of the fallback passes and the corner-transport-upwind form, per
+  // staged cell its sign flips (bits 0..9) and fallback tag (bit 10)
   extern __shared__ __align__(128) unsigned char smem_raw[];
   T *sR = reinterpret_cast<T *>(smem_raw);
   T *sW = sR + RAW * RSTR;
@@ -440,8 +441,9 @@ __global__ void __launch_bounds__(32 * BY, (BY <= 8 && !CTU ? 2 : 1))
   T *sXf = sXh + NV * BY * 32;   // [NV][BY][32]
   T *sCx = sXf + NV * BY * 32;   // CTU: X_x of the thread's cell, [NV][BY * 32]
   T *sCy = sCx + (CTU ? NV * BY * 32 : 0);  // CTU: X_y, [NV][BY * 32]
-  uint16_t *sMeta = reinterpret_cast<uint16_t *>(sCy + (CTU ? NV * BY * 32 : 0));  // [RAW][NQ]
-  uint16_t *sFxy = sMeta + RAW * NQ;  // [NQ]
+  // [RAW][NQ] but for the step, which forms the flips from sFxy and the plane
+  uint16_t *sMeta = reinterpret_cast<uint16_t *>(sCy + (CTU ? NV * BY * 32 : 0));
+  uint16_t *sFxy = sMeta + (kTma ? 0 : RAW * NQ);  // [NQ]
   // one mbarrier per raw slot (bulk tensor staging)
   __shared__ __align__(8) uint64_t sBar[kTma ? RAW : 1];
   auto slot = [](int p) { return ((p % RAW) + RAW) % RAW; };
@@ -531,10 +533,10 @@ __global__ void __launch_bounds__(32 * BY, (BY <= 8 && !CTU ? 2 : 1))
   const int sx = tx + 1, sy = ty + 1;
   const bool interior = tx >= 1 && tx <= kTileX && ty >= 1 && ty <= BY - 2;
   const bool valid = interior && gx < nx && gy < ny;
-  // a tile whose staged box lies inside the grid in x and y takes one bulk tensor copy per
-  // plane (box from xs, the staged box at column xo of it); the others map their cells one
-  // by one (periodic wrap, mirror images)
-  const bool use_tma = tma_on && x0 >= 2 && x0 + kTileX + 1 < nx && y0 >= 2 && y0 + BY - 1 < ny;
+  // Bulk staging: one bulk tensor copy per plane of the box from (xs, y0-2), the staged
+  // box at column xo of it; cells of the box outside the grid arrive as zeros and are then
+  // fixed up one by one from their mapped cells (periodic wrap, mirror images, outflow).
+  const bool use_tma = tma_on;
   const int xs = (x0 - 2) & ~3, xo = use_tma ? x0 - 2 - xs : 0;
   // Rows of a tile that overhangs the grid in y: a row beyond it (gy > ny) feeds no updated
   // cell and skips its sweeps (warp-uniform; the barriers and the staging stay); the row
@@ -555,16 +557,21 @@ __global__ void __launch_bounds__(32 * BY, (BY <= 8 && !CTU ? 2 : 1))
   // uses them (no barrier needed).
   static_assert(NQ <= 2 * 32 * BY, "two staged positions per thread");
   int soff[2];
+  unsigned fixm = 0u;  // bit j: staged position j lies outside the grid (a fix-up of the bulk copy)
 #pragma unroll
   for (int j = 0; j < 2; j++) {
     const int i = tid + j * 32 * BY;
     soff[j] = -1;
     if (i < NQ) {
       const int qy = i / SX, qx = i - qy * SX;
+      const int rx = x0 - 2 + qx, ry = y0 - 2 + qy;
       bool mx, my;
-      const int xx = map_index(x0 - 2 + qx, nx, a.bc[0], a.bc[1], mx);
-      const int yy = map_index(y0 - 2 + qy, ny, a.bc[2], a.bc[3], my);
-      if (staged(qy, qx)) soff[j] = yy * nx + xx;
+      const int xx = map_index(rx, nx, a.bc[0], a.bc[1], mx);
+      const int yy = map_index(ry, ny, a.bc[2], a.bc[3], my);
+      if (staged(qy, qx)) {
+        soff[j] = yy * nx + xx;
+        if (rx < 0 || rx >= nx || ry < 0 || ry >= ny) fixm |= 1u << j;
+      }
       sFxy[i] = (mx ? flip_mask(0) : 0u) ^ (my ? flip_mask(1) : 0u);
     }
   }
@@ -595,11 +602,35 @@ __global__ void __launch_bounds__(32 * BY, (BY <= 8 && !CTU ? 2 : 1))
       const int i = tid + j * 32 * BY;
       const size_t c = zoff + (size_t)soff[j];
       cp_async_cell<T, RNQ * (int)sizeof(T)>(dst + rawi(i), Us + c, N);
-      unsigned m = sFxy[i] ^ fz;
-      if (RETRY && tagged(a.flags[c], tag, a.level)) m |= 1u << 10;
-      meta[i] = (uint16_t)m;
+      if constexpr (!kTma) {
+        unsigned m = sFxy[i] ^ fz;
+        if (RETRY && tagged(a.flags[c], tag, a.level)) m |= 1u << 10;
+        meta[i] = (uint16_t)m;
+      }
     }
     cp_async_commit();
+  };
+  // Fix-ups of a bulk-copied plane: once its copy has landed, the threads whose staged cells
+  // lie outside the grid overwrite them with their mapped cells (cp.async, waited for in
+  // convert).  A thread without such cells does nothing.
+  auto fixups = [&](int z) {
+    if constexpr (kTma) {
+      if (use_tma && fixm != 0u) {
+        const int q = slot(z);
+        if (!tma_dead && !mbar_wait_bounded(&sBar[q], (tma_ph >> q) & 1u)) {
+          tma_dead = true;
+          atomicExch(&a.ctrl->stage_timeout, 1);
+        }
+        bool mz = false;
+        const size_t zoff = (size_t)map_index(z, nz, a.bc[4], a.bc[5], mz) * ny * nx;
+        T *dst = sR + q * RSTR + xo;
+#pragma unroll
+        for (int j = 0; j < 2; j++)
+          if ((fixm >> j) & 1u)
+            cp_async_cell<T, RNQ * (int)sizeof(T)>(dst + rawi(tid + j * 32 * BY), Us + zoff + (size_t)soff[j], N);
+        cp_async_commit();
+      }
+    }
   };
   auto convert = [&](int z) {  // raw plane z -> primitive plane in ring slot z mod 3
     const int q = slot(z);
@@ -607,24 +638,25 @@ __global__ void __launch_bounds__(32 * BY, (BY <= 8 && !CTU ? 2 : 1))
     const uint16_t *meta = sMeta + q * NQ;
     const int b = ((z % 3) + 3) % 3;
     T *dst = sW + b * PL;
-    unsigned mt = 0u;  // a bulk-copied plane: its cells' flips (a mirror plane in z) are the same
+    unsigned fz = 0u;  // the step: flips of the cell = its x/y flips ^ those of a mirror plane
     if constexpr (kTma) {
-      if (use_tma) {
+      if (use_tma) {  // the plane's copy, then this thread's fix-ups
         if (!tma_dead && !mbar_wait_bounded(&sBar[q], (tma_ph >> q) & 1u)) {
           tma_dead = true;
           atomicExch(&a.ctrl->stage_timeout, 1);
         }
         tma_ph ^= 1u << q;
-        bool mz = false;
-        (void)map_index(z, nz, a.bc[4], a.bc[5], mz);
-        mt = mz ? flip_mask(2) : 0u;
+        if (fixm != 0u) cp_async_wait<0>();
       }
+      bool mz = false;
+      (void)map_index(z, nz, a.bc[4], a.bc[5], mz);
+      fz = mz ? flip_mask(2) : 0u;
     }
 #pragma unroll
     for (int j = 0; j < 2; j++) {
       if (soff[j] < 0) continue;
       const int i = tid + j * 32 * BY;
-      const unsigned m = (kTma && use_tma) ? mt : (unsigned)meta[i];
+      const unsigned m = kTma ? (unsigned)sFxy[i] ^ fz : (unsigned)meta[i];
       const int ri = rawi(i) + xo;
       T U[NV], W[NV];
 #pragma unroll
@@ -713,7 +745,11 @@ __global__ void __launch_bounds__(32 * BY, (BY <= 8 && !CTU ? 2 : 1))
     stage(z0 - 1);
     stage(z0);
     stage(z0 + 1);
-    cp_async_wait<2>();  // this thread's copies of planes z0-2 and z0-1 have landed
+    fixups(z0 - 2);
+    fixups(z0 - 1);
+    fixups(z0);
+    fixups(z0 + 1);
+    cp_async_wait<2>();  // cell by cell: this thread's copies of planes z0-2 and z0-1 have landed
     convert(z0 - 2);
     convert(z0 - 1);
     cp_async_wait<1>();
@@ -721,6 +757,8 @@ __global__ void __launch_bounds__(32 * BY, (BY <= 8 && !CTU ? 2 : 1))
   } else {
     stage(z0 - 2);
     stage(z0 - 1);
+    fixups(z0 - 2);
+    fixups(z0 - 1);
     cp_async_wait<0>();
     convert(z0 - 2);
     convert(z0 - 1);
@@ -729,6 +767,7 @@ __global__ void __launch_bounds__(32 * BY, (BY <= 8 && !CTU ? 2 : 1))
     // thread's own cells)
     if (use_tma) __syncthreads();
     stage(z0);
+    fixups(z0);
     cp_async_wait<0>();
     convert(z0);
   }
@@ -744,7 +783,10 @@ __global__ void __launch_bounds__(32 * BY, (BY <= 8 && !CTU ? 2 : 1))
       recon_z(z0 - 1, lo, hprev);
     }
   }
-  if constexpr (RAW != 4) stage(z0 + 1);
+  if constexpr (RAW != 4) {
+    stage(z0 + 1);
+    fixups(z0 + 1);
+  }
   cp_async_wait<0>();
   __syncthreads();  // plane z0-2 is no longer read
   convert(z0 + 1);
@@ -763,6 +805,7 @@ __global__ void __launch_bounds__(32 * BY, (BY <= 8 && !CTU ? 2 : 1))
       for (int k = 0; k < NV; k++) hprev[k] = hi[k];
     }
   }
+  fixups(z0 + 2);
   cp_async_wait<0>();
   __syncthreads();  // plane z0-1 is no longer read
   convert(z0 + 2);
@@ -854,6 +897,9 @@ __global__ void __launch_bounds__(32 * BY, (BY <= 8 && !CTU ? 2 : 1))
       v_fma(acc, Fg, -idz, acc);
       }
     }
+    // the copy of plane z+3 has had the z sweep to land: the fix-ups of its cells outside
+    // the grid go out now, to land during the update
+    if (z + 1 < z1) fixups(z + 3);
     __syncthreads();
     if (interior && rowvalid) {
 #pragma unroll
@@ -1122,7 +1168,8 @@ template <typename T> size_t step_smem(int ndim, int rows, bool ctu, bool retry)
   const bool tma = !ctu && !retry;
   const size_t slot = tma ? ((size_t)NV * (rows + 2) * kTmaBoxX * sizeof(T) + 127) / 128 * 128 : NV * nq * sizeof(T);
   const size_t per_thread = ctu ? 4 : 2;
-  return raw * slot + sizeof(T) * (3 * NV * nq + per_thread * NV * rows * 32) + (raw + 1) * nq * sizeof(uint16_t);
+  return raw * slot + sizeof(T) * (3 * NV * nq + per_thread * NV * rows * 32) +
+         ((tma ? 0 : raw) + 1) * nq * sizeof(uint16_t);
 }
 
 // The driver's tensor-map encoder, looked up once per process (nullptr if unavailable:

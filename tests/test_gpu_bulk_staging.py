@@ -1,21 +1,21 @@
-"""3D steps whose interior tiles stage their planes by bulk tensor copies, against the oracle.
+"""3D steps that stage their planes by bulk tensor copies, against the oracle.
 
-The 3D step stages a tile's planes with one bulk tensor copy per plane when the tile's
-staged box (x0-2 .. x0+31, y0-2 .. y0+rows-1) lies inside the grid in x and y and a row of
-nx cells is a multiple of 16 bytes; the other tiles (those at the x and y edges, whose
-staged cells wrap or mirror) stage cell by cell.  The grids here are wide enough to hold
-both kinds side by side (x tiles at x0 = 30 and 60, whose boxes start 0 and 2 cells into
-the 4-cell-aligned copy box, and y tiles inside), with every boundary kind in z (mirror
-planes take the z sign flips of the copied plane), every tiling of the step (16, 8 and 4
-rows; two raw slots for 8 and 4 rows), every scheme that stages this way (MUSCL-Hancock
-with HLL, Roe-type and HLLC fluxes, both stages of the central scheme) and a run whose
-a-posteriori fallback tags cells.  FP64 <= 1e-10 relative L_inf per field, FP32 within
-2e-4 (rho) / 5e-4 (P_ij) relative L1 of the FP64 oracle from the FP32-rounded input.
-A grid whose rows are not a multiple of 16 bytes (nx = 94 in FP32, 97 in both precisions)
-stages every tile cell by cell and must give the same answer.  zchunk 0 is the balanced
-tiling (equal plane counts per block: whole columns, then runs of the rest window by
-window); a grid with more columns of tiles than the device has block slots takes both
-parts."""
+The 3D step stages every plane of a tile with one bulk tensor copy of the box from the
+4-cell-aligned column xs = (x0 - 2) & ~3 and row y0 - 2 when a row of nx cells is a
+multiple of 16 bytes; cells of the box outside the grid arrive as zeros and are fixed up
+from their mapped cells (periodic wrap, mirror images, outflow) once the copy has landed.
+The grids here hold tiles of every kind (x tiles at x0 = 0, 30 and 60: boxes from -4, 28
+and 56, the staged box 2, 0 and 2 columns into them; edge tiles in x and y; tiles inside),
+with every boundary kind in x, y and z (mirror planes take the z sign flips of the copied
+plane), every tiling of the step (16, 8 and 4 rows; two raw slots for 8 and 4 rows), every
+scheme that stages this way (MUSCL-Hancock with HLL, Roe-type and HLLC fluxes, both stages
+of the central scheme) and a run whose a-posteriori fallback tags cells.  FP64 <= 1e-10
+relative L_inf per field, FP32 within 2e-4 (rho) / 5e-4 (P_ij) relative L1 of the FP64
+oracle from the FP32-rounded input.  A grid whose rows are not a multiple of 16 bytes
+(nx = 94 in FP32, 97 in both precisions) stages every tile cell by cell and must give the
+same answer.  zchunk 0 is the balanced tiling (equal plane counts per block: whole
+columns, then runs of the rest window by window); a grid with more columns of tiles than
+the device has block slots takes both parts."""
 import numpy as np
 import pytest
 
