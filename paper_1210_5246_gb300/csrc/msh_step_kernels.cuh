@@ -991,10 +991,15 @@ __global__ void __launch_bounds__(32 * WARPS) step_strip2d_kernel(StepArgs<T> a)
         const int yy = map_index(y, ny, a.bc[2], a.bc[3], my);
         const unsigned flip = (mx ? flip_mask(0) : 0u) ^ (my ? flip_mask(1) : 0u);
         const size_t c = (size_t)yy * nx + xx;
+        const T *__restrict__ src = Us + c;  // a running pointer: one 64-bit add per field
 #pragma unroll
         for (int k = 0; k < NV; k++) {
-          const T v = Us[k * N + c];
-          U[k] = ((flip >> k) & 1u) ? -v : v;
+          U[k] = *src;
+          src += N;
+        }
+        if (flip) {  // a mirror image (never inside a periodic or outflow grid)
+#pragma unroll
+          for (int k = 0; k < NV; k++) U[k] = ((flip >> k) & 1u) ? -U[k] : U[k];
         }
         fl = RETRY ? tagged(a.flags[c], tag, a.level) : false;
       };
