@@ -242,6 +242,27 @@ template <typename T> struct Eig {
     o[8] = (Pyz + T(2) * a * Pxz) * A + Pxz * C + Pxy * E + c[5];
     o[9] = (Pzz + T(2) * b * Pxz) * A + T(2) * Pxz * E + c[6];
   }
+  // R c and R (s c), s the wave speeds relative to u (-cf, -cs, -cs, 0 x 4, cs, cs, cf),
+  // sharing the wave-pair sums: with A = c_f+ + c_f-, B = (c_f+ - c_f-) cf and so on, the
+  // speed-weighted amplitudes give A' = B, B' = cf^2 A (cf^2 = 3 cs^2), C' = Dv, Dv' = cs^2 C,
+  // E' = Fw, Fw' = cs^2 E, and no contact amplitudes.
+  __device__ __forceinline__ void back2(const T (&c)[NV], T (&o)[NV], T (&os)[NV]) const {
+    back(c, o);
+    const T A = c[9] + c[0], C = c[7] + c[1], E = c[8] + c[2];
+    const T A2 = (c[9] - c[0]) * cf, C2 = (c[7] - c[1]) * cs, E2 = (c[8] - c[2]) * cs;
+    const T cs2 = cs * cs;
+    const T B2 = T(3) * cs2 * A, D2 = cs2 * C, F2 = cs2 * E;
+    os[0] = rho * A2;
+    os[1] = B2;
+    os[2] = a * B2 + D2;
+    os[3] = b * B2 + F2;
+    os[4] = T(3) * Pxx * A2;
+    os[5] = T(3) * Pxy * A2 + Pxx * C2;
+    os[6] = T(3) * Pxz * A2 + Pxx * E2;
+    os[7] = (Pyy + T(2) * a * Pxy) * A2 + T(2) * Pxy * C2;
+    os[8] = (Pyz + T(2) * a * Pxz) * A2 + Pxz * C2 + Pxy * E2;
+    os[9] = (Pzz + T(2) * b * Pxz) * A2 + T(2) * Pxz * E2;
+  }
 };
 
 // ------------------------------------------------- corner transport upwind
@@ -322,24 +343,18 @@ __device__ __forceinline__ void reconstruct(const T (&wm)[NV], const T (&w0)[NV]
 #pragma unroll
     for (int k = 0; k < NV; k++) tput(k, o[k]);
   }
-  // wave speeds relative to u: (-cf, -cs, -cs, 0, 0, 0, 0, cs, cs, cf)
-  T lm[NV];
-  lm[0] = -E.cf * m[0]; lm[1] = -E.cs * m[1]; lm[2] = -E.cs * m[2];
-  lm[3] = T(0); lm[4] = T(0); lm[5] = T(0); lm[6] = T(0);
-  lm[7] = E.cs * m[7]; lm[8] = E.cs * m[8]; lm[9] = E.cf * m[9];
   T dw[NV], g[NV];
-  E.back(m, dw);   // 2 dw^m, dw^m the limited primitive slope
-  E.back(lm, g);   // 2 (A dw^m - u dw^m)
+  E.back2(m, dw, g);  // 2 dw^m (dw^m the limited primitive slope) and 2 (A dw^m - u dw^m)
+  // hi, lo = w0 -+ dw^m/2 - nu A dw^m = (w0 - nu g / 2) + (+-1/4 - nu u / 2) 2 dw^m
   const T nu2 = T(0.5) * nu;
-  T adw[NV], pred[NV];
-  v_fma(adw, dw, E.u, g);
-  v_fma(pred, adw, -nu2, w0);
+  T base[NV];
+  v_fma(base, g, -nu2, w0);
   if constexpr (CTU) {
 #pragma unroll
-    for (int k = 0; k < NV; k++) pred[k] += xget(k);
+    for (int k = 0; k < NV; k++) base[k] += xget(k);
   }
-  v_fma(hi, dw, T(0.25), pred);
-  v_fma(lo, dw, T(-0.25), pred);
+  v_fma(hi, dw, T(0.25) - nu2 * E.u, base);
+  v_fma(lo, dw, T(-0.25) - nu2 * E.u, base);
   face_state_check(w0, lo, hi);
 }
 
