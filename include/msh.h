@@ -210,6 +210,20 @@ msh_status msh_set_profiling(msh_grid *g, int32_t on);
 msh_status msh_get_profile(msh_grid *g, double *step_kernel_ms, double *finalize_ms, int64_t *launches);
 
 /*
+ * Test hook for the bounded waits of the 3D step (no counterpart in the paper).  kind 1:
+ * in the next characteristic step (HLL, Roe-type or HLLC flux) taken eagerly (msh_step,
+ * msh_step_dt, msh_step_begin; never inside the CUDA graph of msh_run), thread block 0 of
+ * the step kernel does not issue its bulk tensor copy of plane -2 (the first copy of a
+ * stretch from z = 0, which every tiling gives block 0 first), so the threads waiting for
+ * that plane give up after about 2^31 SM clocks (about a second), the step's result is
+ * void and the call returns MSH_E_TIMEOUT; the grid stays usable after msh_set_state.
+ * Grids whose 3D step stages cell by cell (rows not a multiple of 16 bytes), 1D and 2D
+ * grids ignore it.  kind 0 clears it.  The hook applies to one step.  Errors:
+ * MSH_E_INVALID_ARG for a null grid or another kind.
+ */
+msh_status msh_set_test_fault(msh_grid *g, int32_t kind);
+
+/*
  * Discrete adjoint (vector-Jacobian product) of `nsteps` forward steps taken from U0
  * with the frozen time-step schedule dt_sched[nsteps] (host doubles), limiter branches,
  * HLL branches and face-state fallbacks frozen at their forward values:

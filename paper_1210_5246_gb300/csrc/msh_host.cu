@@ -178,15 +178,19 @@ msh_status launch_one_step(msh_grid *g, int ev_slot) {
   }
   // the characteristic step (HLL, Roe-type or HLLC flux), then its fallback passes: each
   // returns at once unless the previous pass tagged new cells
+  const int32_t test_fault = g->test_fault;
+  g->test_fault = 0;  // a test hook applies to one step
   for (int level = 0; level <= kFallbackPasses; level++) {
     const bool retry = level > 0;
     if (g->prec == MSH_FP32) {
       StepArgs<float> a = make_args<float>(g);
       a.level = level;
+      a.test_skip = level == 0 && test_fault == 1;
       e = launch_characteristic(g, a, retry, retry ? nullptr : &nb);
     } else {
       StepArgs<double> a = make_args<double>(g);
       a.level = level;
+      a.test_skip = level == 0 && test_fault == 1;
       e = launch_characteristic(g, a, retry, retry ? nullptr : &nb);
     }
     if (e != cudaSuccess)
@@ -201,6 +205,13 @@ msh_status launch_one_step(msh_grid *g, int ev_slot) {
 
 msh_status build_graph(msh_grid *g) {
   if (g->graph) return MSH_OK;
+  const int32_t test_fault = g->test_fault;  // test hooks never enter a graph
+  g->test_fault = 0;
+  struct Restore {
+    msh_grid *g;
+    int32_t v;
+    ~Restore() { g->test_fault = v; }
+  } restore{g, test_fault};
   msh_status st = ensure_partials(g, blocks_for(g, g->rows, g->zchunk));
   if (st) return st;
   cudaGraph_t graph;
@@ -1014,8 +1025,17 @@ msh_status msh_step_begin(msh_grid *g, double dt) {
   cudaError_t e = launch_set_dt(g->ctrl, dt, g->stream);
   int nb = 0;
   if (e == cudaSuccess) {
-    if (g->prec == MSH_FP32) e = launch_characteristic(g, make_args<float>(g), false, &nb);
-    else e = launch_characteristic(g, make_args<double>(g), false, &nb);
+    const int32_t test_fault = g->test_fault;
+    g->test_fault = 0;  // a test hook applies to one step
+    if (g->prec == MSH_FP32) {
+      StepArgs<float> a = make_args<float>(g);
+      a.test_skip = test_fault == 1;
+      e = launch_characteristic(g, a, false, &nb);
+    } else {
+      StepArgs<double> a = make_args<double>(g);
+      a.test_skip = test_fault == 1;
+      e = launch_characteristic(g, a, false, &nb);
+    }
   }
   if (e != cudaSuccess) return fail(MSH_E_CUDA, "step begin: %s", cudaGetErrorString(e));
   g->phase_level = 0;
@@ -1268,6 +1288,14 @@ msh_status msh_autotune(msh_grid *g, int32_t *rows_out, int32_t *zchunk_out) {
   if (st) return st;
   if (rows_out) *rows_out = g->rows;
   if (zchunk_out) *zchunk_out = g->zchunk;
+  return MSH_OK;
+}
+
+msh_status msh_set_test_fault(msh_grid *g, int32_t kind) {
+  begin();
+  if (!g) return fail(MSH_E_INVALID_ARG, "null grid");
+  if (kind != 0 && kind != 1) return fail(MSH_E_INVALID_ARG, "test fault kind must be 0 or 1");
+  g->test_fault = kind;
   return MSH_OK;
 }
 

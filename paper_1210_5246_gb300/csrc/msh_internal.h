@@ -64,13 +64,14 @@ template <typename T> struct StepArgs {
   int bc[6];
   double dx[3];
   int zchunk;
-  int units;            // 3D: work units of the launch, one partial each (set by the launcher)
   // adjoint tape: the step kernel stores U^s in ck[(s - ck_base) / ck_K] when s - ck_base
   // is a multiple of ck_K in [0, ck_len); ck = nullptr: no tape
   T *ck;
   int64_t ck_base, ck_len;
   int ck_K;
   T *U1;                // the central scheme's first-stage state (nullptr for MUSCL-Hancock)
+  int units = 0;        // 3D: work units of the launch (set by the launcher)
+  int test_skip = 0;    // test hook: thread block 0 does not issue its bulk copy of plane -2
 };
 
 constexpr int kTile1D = 128;   // threads per block of the 1D step kernel
@@ -189,6 +190,7 @@ struct msh_grid {
   // and the number of partials the step kernel wrote
   int phase_level = -1;
   int phase_nb = 0;
+  int32_t test_fault = 0;  // msh_set_test_fault: applied to the next eager step launch
   unsigned long long *tag_count = nullptr;  // device counter of msh_count_tags
   int rows = 8, zchunk = 32;
   cudaGraphExec_t graph = nullptr;

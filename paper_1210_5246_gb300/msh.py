@@ -60,6 +60,7 @@ SIGNATURES = {
     "msh_get_tiling": [_vp, _P(_i32), _P(_i32)],
     "msh_autotune": [_vp, _P(_i32), _P(_i32)],
     "msh_set_profiling": [_vp, _i32],
+    "msh_set_test_fault": [_vp, _i32],
     "msh_get_profile": [_vp, _P(_dbl), _P(_dbl), _P(_i64)],
     "msh_adjoint_run": [_vp, _vp, _i64, _P(_dbl), _i32, _vp, _vp, _i32, _i32],
     "msh_set_tape": [_vp, _i32, _i64],
@@ -322,6 +323,10 @@ class Grid:
 
     def set_profiling(self, on=True):
         _check(load().msh_set_profiling(self.h, int(bool(on))))
+
+    def set_test_fault(self, kind):
+        """Test hook of the bounded bulk-copy waits of the 3D step (see msh_set_test_fault)."""
+        _check(load().msh_set_test_fault(self.h, int(kind)))
 
     def profile(self):
         """(summed step-kernel ms, summed finalize ms, timed launches) since profiling began."""

@@ -154,3 +154,35 @@ def test_balanced_tiling_whole_columns_and_runs(msh, oracle, precision):
         assert_fp64(U, Uo, what="balanced fp64")
     else:
         assert_fp32(Wg, Wo, what="balanced fp32")
+
+
+def test_bulk_copy_wait_runs_out(msh):
+    """The bound on the waits for bulk copies: with the test hook, thread block 0 of the next
+    step leaves its first copy out, the threads waiting for that plane give up after about
+    2^31 SM clocks, and the step returns MSH_E_TIMEOUT instead of hanging.  The context stays
+    usable: after msh_set_state the grid steps exactly as a fresh grid does, and a second
+    step without the hook succeeds."""
+    n = (96, 46, 12)
+    W = _state(n[::-1], 31).astype(np.float32)
+    lo, hi = (0.0, 0.0, 0.0), (1.0, 0.5, 0.125)
+
+    def grid():
+        g = msh.Grid(n, lo, hi, BCS["zper"], 0.5, msh.FP32)
+        g.set_tiling(16, 0)
+        g.set_state(W, msh.PRIMITIVE)
+        return g
+
+    g = grid()
+    g.set_test_fault(1)
+    with pytest.raises(msh.MshError) as ei:
+        g.step()
+    assert ei.value.status == msh.MSH_E_TIMEOUT
+    g.set_state(W, msh.PRIMITIVE)
+    g.step()
+    g.step()
+    ref = grid()
+    ref.step()
+    ref.step()
+    assert np.array_equal(g.get_state(), ref.get_state())
+    g.close()
+    ref.close()
