@@ -23,6 +23,7 @@ import hashlib
 import json
 import math
 import os
+import re
 import statistics
 import subprocess
 import sys
@@ -78,16 +79,27 @@ def dist_env():
     return replicas.dist_env()
 
 
+def _code_only(text):
+    """Source text without // comments and blank lines (a comment edit does not change the
+    compiled kernel, so it keeps the record valid)."""
+    out = []
+    for line in text.splitlines():
+        code = re.sub(r"//.*$", "", line).rstrip()
+        if code:
+            out.append(code)
+    return "\n".join(out)
+
+
 def kernel_source_hash():
-    """Hash of the source the 3D step kernel is compiled from: the per-cell arithmetic
+    """Hash of the code the 3D step kernel is compiled from: the per-cell arithmetic
     (msh_device.cuh) and msh_step_kernels.cuh up to the 2D kernel (helpers and
-    step_tile_kernel)."""
+    step_tile_kernel), comments left out."""
     csrc = os.path.join(ROOT, "paper_1210_5246_gb300", "csrc")
     step = open(os.path.join(csrc, "msh_step_kernels.cuh")).read()
     cut = step.find("// ---------------------------------------------------------------- 2D kernel")
     h = hashlib.sha256()
-    h.update(open(os.path.join(csrc, "msh_device.cuh"), "rb").read())
-    h.update(step[: cut if cut >= 0 else len(step)].encode())
+    h.update(_code_only(open(os.path.join(csrc, "msh_device.cuh")).read()).encode())
+    h.update(_code_only(step[: cut if cut >= 0 else len(step)]).encode())
     return h.hexdigest()[:16]
 
 

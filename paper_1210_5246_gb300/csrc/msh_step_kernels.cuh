@@ -12,8 +12,11 @@
 // ring of halo threads reconstructs the neighbours whose face states the interior needs.
 // z planes stream through a three-plane shared-memory ring (2.5D): x and y fluxes come
 // from the current plane, the z flux is carried in registers from plane to plane, so
-// every cell is reconstructed once per direction.  2D: one warp per 32-column strip
-// streamed in y (step_strip2d_kernel).
+// every cell is reconstructed once per direction.  Each plane of a tile's staged box
+// arrives one plane ahead by one bulk tensor copy (TMA) completed on an mbarrier, the
+// cells of the box outside the grid fixed up afterwards from their mapped cells; a block
+// streams whole columns of tiles or equal runs of planes (balanced tiling), or chunks of
+// zchunk planes.  2D: one warp per 32-column strip streamed in y (step_strip2d_kernel).
 //
 // Template parameter SCH: 0 MUSCL-Hancock (the step); 1, 2 the two stages of the central
 // scheme (stage 1 writes U1 = U^n + dt L(U^n), stage 2 sweeps U1 and writes
