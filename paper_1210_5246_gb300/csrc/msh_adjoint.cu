@@ -268,8 +268,8 @@ template <typename T> size_t adj_tile_smem() {
 template <typename T, int D, bool LAST>
 __global__ void __launch_bounds__(kAdjTileThreads, sizeof(T) == 4 ? 2 : 1) adj_tile_kernel(AdjArgs<T> a) {
   static_assert(D == 1 || D == 2, "the staged pass runs along y or z");
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  T *sW = reinterpret_cast<T *>(smem_raw);            // [NV][32 along D][kAdjTileP along x]
+  extern __shared__ __align__(16) unsigned char adj_smem[];
+  T *sW = reinterpret_cast<T *>(adj_smem);            // [NV][32 along D][kAdjTileP along x]
   T *sL = sW + (size_t)NV * 32 * kAdjTileP;           // lam*, same layout (global order)
   int *sF = reinterpret_cast<int *>(sL + (size_t)NV * 32 * kAdjTileP);  // tags
   const int nd = a.n[D];

@@ -25,13 +25,11 @@ namespace {
 template <typename T> struct Fft;
 template <> struct Fft<float> {
   using C = cufftComplex;
-  static constexpr cufftType r2c = CUFFT_R2C, c2r = CUFFT_C2R;
   static cufftResult fwd(cufftHandle p, float *in, C *out) { return cufftExecR2C(p, in, out); }
   static cufftResult inv(cufftHandle p, C *in, float *out) { return cufftExecC2R(p, in, out); }
 };
 template <> struct Fft<double> {
   using C = cufftDoubleComplex;
-  static constexpr cufftType r2c = CUFFT_D2Z, c2r = CUFFT_Z2D;
   static cufftResult fwd(cufftHandle p, double *in, C *out) { return cufftExecD2Z(p, in, out); }
   static cufftResult inv(cufftHandle p, C *in, double *out) { return cufftExecZ2D(p, in, out); }
 };
