@@ -401,7 +401,7 @@ __device__ __forceinline__ void gather(const T *__restrict__ pl, int sy, int sx,
 // transverse terms of its cell plane by plane, and the sums each sweep needs, X_x = T_y +
 // T_z and X_y = T_x + T_z, wait in thread-private shared memory from the plane before.
 template <typename T, int NDIM, int BY, int SCH, bool RETRY, bool CTU = false>
-__global__ void __launch_bounds__(32 * BY, (BY <= 8 && !CTU ? 2 : 1))
+__global__ void __launch_bounds__(32 * BY, (BY <= 8 && !CTU && sizeof(T) == 4 ? 2 : 1))
     step_tile_kernel(StepArgs<T> a, const __grid_constant__ TileMaps tm) {
   static_assert(NDIM == 3, "the 2D step runs in step_strip2d_kernel");
   static_assert(kTileX % 2 == 0, "bulk-copy boxes start at most two cells before the staged box");
