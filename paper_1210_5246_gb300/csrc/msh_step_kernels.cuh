@@ -578,8 +578,9 @@ __global__ void __launch_bounds__(32 * BY, (BY <= 8 && !CTU && sizeof(T) == 4 ? 
       sFxy[i] = (mx ? flip_mask(0) : 0u) ^ (my ? flip_mask(1) : 0u);
     }
   }
-  // A thread stages and later converts the same cells, so the copies it waits for are its
-  // own and no barrier separates staging from conversion.
+  // Cell by cell, a thread stages and later converts the same cells, so the copies it waits
+  // for are its own and no barrier separates staging from conversion; a bulk copy is
+  // issued by thread 0 and every thread waits for it on the slot's mbarrier.
   auto stage = [&](int z) {
     bool mz = false;
     const int zz = map_index(z, nz, a.bc[4], a.bc[5], mz);
