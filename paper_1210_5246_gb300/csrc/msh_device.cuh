@@ -705,8 +705,8 @@ __device__ __forceinline__ void face_flux(const T (&wl)[NV], const T (&wr)[NV], 
 // k-term sum below k 2^-24, random in sign across threads) and in FP64 from the block
 // reduction on, so the totals need no FP64 arithmetic per cell (FP64 throughput is a small
 // fraction of FP32 on this GPU).  The 3D step moves a thread's FP32 sum into FP64 block
-// totals every 64 planes of a stretch, so one FP32 sum spans fewer than 128 cells (the end
-// of one stretch and the start of the next); 2D strips and 1D tiles stream one chunk.
+// totals every 64 planes of a stretch and at its end, so one FP32 sum spans at most 64
+// cells; 2D strips and 1D tiles stream one chunk.
 template <typename T> struct Acc {
   double v[NV];
   __device__ __forceinline__ void zero() {

@@ -927,14 +927,15 @@ __global__ void __launch_bounds__(32 * BY, (BY <= 8 && !CTU && sizeof(T) == 4 ? 
       cp_async_wait<0>();
       convert(z + 3);
     }
-    // FP32 states: every 64 planes of a stretch the threads' FP32 sums move into the job's
-    // FP64 totals (a sum so spans fewer than 128 planes across two stretches)
+    // FP32 states: every 64 planes of a stretch, and at its end, the threads' FP32 sums
+    // move into the job's FP64 totals (a sum spans at most 64 planes)
     // (the barrier inside comes after every thread has finished the plane)
     if constexpr (sizeof(T) == 4) {
       if (((z + 1 - z0) & 63) == 0 && z + 1 < z1) flush_totals<T, 32 * BY>(diag, tot);
     }
   }
   cp_async_wait<0>();
+  if constexpr (sizeof(T) == 4) flush_totals<T, 32 * BY>(diag, tot);  // its barrier also ends the stretch
   __syncthreads();  // the next stretch restages every buffer
   }
   write_partial<T, 32 * BY>(diag, smax, bad, a.part + u, tot);
