@@ -48,3 +48,23 @@ def test_issue_roofline_arithmetic(monkeypatch):
     monkeypatch.setattr(bench, "traffic_record", lambda: None)
     assert bench.issue_roofline(1_000_000, 1e-4, 152, None) is None and bench.measured_traffic(1000) is None
 
+
+
+def test_source_hash_ignores_comments_only(tmp_path, monkeypatch):
+    """The traffic record stays valid across comment edits of the kernel source and not
+    across code edits (the hash covers the code with // comments and blank lines left out)."""
+    csrc = tmp_path / "paper_1210_5246_gb300" / "csrc"
+    csrc.mkdir(parents=True)
+    dev = "inline int f(int x) { return x + 1; }  // one more\n"
+    step = ("// header\ntemplate <int N> int g() { return N; }\n\n"
+            "// ---------------------------------------------------------------- 2D kernel\n"
+            "int after_the_cut = 0;\n")
+    (csrc / "msh_device.cuh").write_text(dev)
+    (csrc / "msh_step_kernels.cuh").write_text(step)
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    h0 = bench.kernel_source_hash()
+    (csrc / "msh_device.cuh").write_text("// a new comment\n" + dev.replace("one more", "plus one") + "\n\n")
+    (csrc / "msh_step_kernels.cuh").write_text(step.replace("after_the_cut = 0", "after_the_cut = 1"))
+    assert bench.kernel_source_hash() == h0  # comments, blank lines, code past the 2D kernel
+    (csrc / "msh_device.cuh").write_text(dev.replace("x + 1", "x + 2"))
+    assert bench.kernel_source_hash() != h0
